@@ -1,0 +1,298 @@
+"""CPU FP64 oracle for the tree-gravity path (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+package; the CUDA library never imports, links or calls it, and it shares no
+code with it. The heavy loops are plain C in ``orc.c`` (built here with gcc,
+OpenMP, ``-ffp-contract=off``); this module marshals numpy arrays and adds the
+few steps that are one line of numpy (the leapfrog kick/drift, the energy and
+momentum sums, error percentiles).
+
+Every function cites the part of the paper it restates; the readings of the
+points the paper leaves open are documented in ``orc.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``orc.c`` into ``_build/liborc.so`` (gcc, FP64, OpenMP)."""
+    src = os.path.join(_HERE, "orc.c")
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", src, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            _LIB = C.CDLL(build())
+            _declare(_LIB)
+    return _LIB
+
+
+_d = C.POINTER(C.c_double)
+_f = C.POINTER(C.c_float)
+_i64 = C.POINTER(C.c_int64)
+_u64 = C.POINTER(C.c_uint64)
+
+
+def _declare(L):
+    L.orc_direct.argtypes = [C.c_int64, _d, _d, _d, _d, _d, C.c_int64, _i64, _d, _d, _d, _d]
+    L.orc_bounds.argtypes = [C.c_int64, _f, _f, _f, _d, _d, _d]
+    L.orc_keys.argtypes = [C.c_int64, _f, _f, _f, _d, C.c_double, _u64]
+    L.orc_sort.argtypes = [C.c_int64, _u64, _u64, _i64]
+    L.orc_tree_build.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_int32, C.c_int32]
+    L.orc_tree_build.restype = C.c_void_p
+    L.orc_tree_free.argtypes = [C.c_void_p]
+    L.orc_tree_sizes.argtypes = [C.c_void_p, _i64]
+    L.orc_tree_bounds.argtypes = [C.c_void_p, _d]
+    L.orc_tree_keys.argtypes = [C.c_void_p, _u64, _i64]
+    L.orc_tree_cells.argtypes = [C.c_void_p, _i64]
+    L.orc_tree_moments.argtypes = [C.c_void_p, _d]
+    L.orc_tree_groups.argtypes = [C.c_void_p, _i64]
+    L.orc_tree_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                  _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64]
+    L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d]
+    L.orc_knn.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_int64, _i64]
+    L.orc_knn.restype = C.c_int64
+    L.orc_radius.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_float, C.c_int64, _i64]
+    L.orc_radius.restype = C.c_int64
+
+
+def _p(a, ty):
+    return a.ctypes.data_as(ty)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+# ---------------------------------------------------------------------------
+# Direct sum
+# ---------------------------------------------------------------------------
+def direct(pos, mass, eps, targets=None):
+    """Direct-summation acceleration and potential (G = 1, Plummer softening,
+    Sect. 3) on ``targets`` (indices; default all) from all particles.
+
+    ``pos`` (3, n) float64, ``mass`` (n,), ``eps`` scalar or (n,) where 0 marks
+    an unsoftened particle (the chain centre of mass, Sect. 2/3). Pair
+    softening is max(eps_i, eps_j), 0 if either is 0. Returns (acc (3, nt), pot (nt,))."""
+    pos = _c(pos, np.float64)
+    n = pos.shape[1]
+    m = _c(mass, np.float64)
+    e = _c(np.broadcast_to(np.asarray(eps, dtype=np.float64), (n,)), np.float64)
+    t = np.arange(n, dtype=np.int64) if targets is None else _c(targets, np.int64)
+    x, y, z = (_c(pos[a], np.float64) for a in range(3))
+    out = [np.zeros(t.shape[0]) for _ in range(4)]
+    lib().orc_direct(n, _p(x, _d), _p(y, _d), _p(z, _d), _p(m, _d), _p(e, _d), t.shape[0], _p(t, _i64),
+                     *[_p(o, _d) for o in out])
+    return np.stack(out[:3]), out[3]
+
+
+# ---------------------------------------------------------------------------
+# Keys and sort
+# ---------------------------------------------------------------------------
+def bounds(pos32):
+    """(min[3], L, scale) of FP32 positions (3, n)."""
+    x, y, z = (_c(pos32[a], np.float32) for a in range(3))
+    lo = np.zeros(3)
+    L = C.c_double()
+    s = C.c_double()
+    lib().orc_bounds(x.shape[0], _p(x, _f), _p(y, _f), _p(z, _f), _p(lo, _d), C.byref(L), C.byref(s))
+    return lo, L.value, s.value
+
+
+def keys(pos32):
+    """63-bit Morton keys of FP32 positions (3, n), unsorted, caller order."""
+    x, y, z = (_c(pos32[a], np.float32) for a in range(3))
+    lo, L, s = bounds(pos32)
+    k = np.zeros(x.shape[0], dtype=np.uint64)
+    lib().orc_keys(x.shape[0], _p(x, _f), _p(y, _f), _p(z, _f), _p(lo, _d), s, _p(k, _u64))
+    return k
+
+
+def stable_sort(key):
+    """Stable sort of keys; returns (sorted keys, permutation: sorted slot -> index)."""
+    key = _c(key, np.uint64)
+    sk = np.zeros_like(key)
+    perm = np.zeros(key.shape[0], dtype=np.int64)
+    lib().orc_sort(key.shape[0], _p(key, _u64), _p(sk, _u64), _p(perm, _i64))
+    return sk, perm
+
+
+# ---------------------------------------------------------------------------
+# Tree
+# ---------------------------------------------------------------------------
+class Tree:
+    """The oracle octree of FP32 stars (positions (3, n), masses (n,)).
+
+    Attributes after construction (numpy arrays):
+      key, perm         sorted keys and sorted slot -> caller index
+      cells [ncell, 9]  level, first, count, child, nchild, parent, ox, oy, oz
+      moments [ncell,10] M, com x/y/z, Q xx, yy, zz, xy, xz, yz (FP64)
+      groups [ngroup,3] first, count, box cell
+      lo, L, scale      bounding cube
+    """
+
+    def __init__(self, pos32, mass32, n_leaf: int = 16, group: int = 32):
+        self.x, self.y, self.z = (_c(pos32[a], np.float32) for a in range(3))
+        self.m = _c(mass32, np.float32)
+        self.n = self.x.shape[0]
+        self.n_leaf, self.group = n_leaf, group
+        self._h = lib().orc_tree_build(self.n, _p(self.x, _f), _p(self.y, _f), _p(self.z, _f), _p(self.m, _f),
+                                       n_leaf, group)
+        sz = np.zeros(3, dtype=np.int64)
+        lib().orc_tree_sizes(self._h, _p(sz, _i64))
+        self.ncell, self.ngroup = int(sz[1]), int(sz[2])
+        b = np.zeros(5)
+        lib().orc_tree_bounds(self._h, _p(b, _d))
+        self.lo, self.L, self.scale = b[:3].copy(), float(b[3]), float(b[4])
+        self.key = np.zeros(self.n, dtype=np.uint64)
+        self.perm = np.zeros(self.n, dtype=np.int64)
+        lib().orc_tree_keys(self._h, _p(self.key, _u64), _p(self.perm, _i64))
+        self.cells = np.zeros((self.ncell, 9), dtype=np.int64)
+        lib().orc_tree_cells(self._h, _p(self.cells, _i64))
+        self.moments = np.zeros((self.ncell, 10))
+        lib().orc_tree_moments(self._h, _p(self.moments, _d))
+        self.groups = np.zeros((self.ngroup, 3), dtype=np.int64)
+        lib().orc_tree_groups(self._h, _p(self.groups, _i64))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_tree_free(h)
+            self._h = None
+
+    def forces(self, theta: float, eps_star: float, quadrupole: bool = True,
+               extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False):
+        """Tree acceleration/potential on every star (caller order), FP64.
+
+        Walk under the box-box opening-angle test at ``theta``; ``extra_*``
+        are particles outside the tree (chain centres of mass; eps 0 =
+        unsoftened) that act on the stars and each other directly and feel the
+        tree through their own walk. Returns (acc (3,n), pot (n,), xacc (3,k),
+        xpot (k,)[, counts (n,2) = P2P, M2P interactions])."""
+        k = 0 if extra_mass is None else int(np.asarray(extra_mass).shape[0])
+        ex = np.zeros((3, max(k, 1)), dtype=np.float32)
+        xm = np.zeros(max(k, 1))
+        xe = np.zeros(max(k, 1))
+        if k:
+            ex[:, :k] = np.asarray(extra_pos32, dtype=np.float32)
+            xm[:k] = np.asarray(extra_mass, dtype=np.float64)
+            xe[:k] = np.asarray(extra_eps, dtype=np.float64)
+        exx, exy, exz = (_c(ex[a], np.float32) for a in range(3))
+        out = [np.zeros(self.n) for _ in range(4)]
+        xout = [np.zeros(max(k, 1)) for _ in range(4)]
+        cnt = np.zeros((self.n, 2), dtype=np.int64) if counts else None
+        lib().orc_tree_forces(self._h, float(np.float32(theta)), float(eps_star), int(quadrupole), k,
+                              _p(exx, _f), _p(exy, _f), _p(exz, _f), _p(xm, _d), _p(xe, _d),
+                              *[_p(o, _d) for o in out], *[_p(o, _d) for o in xout],
+                              _p(cnt, _i64) if counts else None)
+        res = (np.stack(out[:3]), out[3], np.stack(xout[:3])[:, :k], xout[3][:k])
+        return res + (cnt,) if counts else res
+
+
+# ---------------------------------------------------------------------------
+# Chain / perturber coupling (Sect. 2, Eq. 3)
+# ---------------------------------------------------------------------------
+def perturber(chain_mass, chain_pos, pert_mass, pert_pos):
+    """Unsoftened FP64 couplings of a chain (k members, pos (k,3)) and its
+    perturbers (p, pos (p,3)). Returns dict with a_pert (p,3), a_chain (k,3),
+    corr (3,) = Eq. 3 correction, sub (3,) = perturbers' direct terms on the
+    centre-of-mass particle."""
+    cm = _c(chain_mass, np.float64)
+    cx = _c(chain_pos, np.float64).reshape(-1)
+    pm = _c(pert_mass, np.float64)
+    px = _c(pert_pos, np.float64).reshape(-1)
+    nch, npt = cm.shape[0], pm.shape[0]
+    ap = np.zeros(3 * max(npt, 1))
+    ac = np.zeros(3 * max(nch, 1))
+    corr = np.zeros(3)
+    sub = np.zeros(3)
+    lib().orc_perturber(nch, _p(cm, _d), _p(cx, _d), npt, _p(pm, _d), _p(px, _d), _p(ap, _d), _p(ac, _d),
+                        _p(corr, _d), _p(sub, _d))
+    return {"a_pert": ap[:3 * npt].reshape(npt, 3), "a_chain": ac[:3 * nch].reshape(nch, 3),
+            "corr": corr, "sub": sub}
+
+
+def knn(pos32, centre32, k):
+    """Indices of the k stars nearest to centre (FP32 distances, ties by index)."""
+    x, y, z = (_c(pos32[a], np.float32) for a in range(3))
+    c = _c(centre32, np.float32)
+    out = np.zeros(max(k, 1), dtype=np.int64)
+    got = lib().orc_knn(x.shape[0], _p(x, _f), _p(y, _f), _p(z, _f), _p(c, _f), k, _p(out, _i64))
+    return out[:got]
+
+
+def radius(pos32, centre32, r2_32):
+    """Indices (ascending) of stars with FP32 squared distance below r2."""
+    x, y, z = (_c(pos32[a], np.float32) for a in range(3))
+    c = _c(centre32, np.float32)
+    n = x.shape[0]
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    got = lib().orc_radius(n, _p(x, _f), _p(y, _f), _p(z, _f), _p(c, _f), np.float32(r2_32), n, _p(out, _i64))
+    return out[:got]
+
+
+# ---------------------------------------------------------------------------
+# Integration and diagnostics
+# ---------------------------------------------------------------------------
+def energy(pos, vel, mass, pot):
+    """FP64 totals (Sect. 3/4 energy diagnostic): E_kin = sum m v^2/2,
+    E_pot = sum m phi / 2, momentum P = sum m v, angular momentum
+    L = sum m x cross v. Exactly rounded sums (math.fsum)."""
+    import math
+    pos, vel = np.asarray(pos, np.float64), np.asarray(vel, np.float64)
+    m, p = np.asarray(mass, np.float64), np.asarray(pot, np.float64)
+    ek = math.fsum(0.5 * m * (vel * vel).sum(0))
+    ep = math.fsum(0.5 * m * p)
+    P = [math.fsum(m * vel[a]) for a in range(3)]
+    Lv = np.cross(pos.T, vel.T).T
+    Lm = [math.fsum(m * Lv[a]) for a in range(3)]
+    return {"ekin": ek, "epot": ep, "etot": ek + ep, "P": np.array(P), "L": np.array(Lm)}
+
+
+def kdk(pos, vel, acc, dt, force_fn, nsteps=1):
+    """Kick-drift-kick leapfrog with a global step (the integrator used here
+    in place of the paper's DKD block steps): v += a dt/2; x += v dt;
+    a = force_fn(x); v += a dt/2. Returns (pos, vel, acc)."""
+    pos, vel, acc = pos.copy(), vel.copy(), acc.copy()
+    for _ in range(nsteps):
+        vel = vel + 0.5 * dt * acc
+        pos = pos + dt * vel
+        acc = force_fn(pos)
+        vel = vel + 0.5 * dt * acc
+    return pos, vel, acc
+
+
+def rel_err(a, ref):
+    """Per-particle relative error |a - ref| / |ref| of (3, n) vectors."""
+    a, ref = np.asarray(a, np.float64), np.asarray(ref, np.float64)
+    return np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+def percentile(e, p):
+    """Nearest-rank percentile: sorted ascending, index ceil(p n) - 1."""
+    import math
+    s = np.sort(np.asarray(e, np.float64))
+    if s.size == 0:
+        return float("nan")
+    return float(s[max(0, math.ceil(p * s.size) - 1)])

@@ -1,0 +1,634 @@
+/*
+ * orc.c -- plain FP64 CPU oracle for the tree-gravity path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do. It shares no code, header or table with the CUDA library.
+ *
+ * What it computes (G = 1, Sect. 3; Plummer softening, Sect. 3):
+ *   - the direct O(N^2) sum, the exact quantity the tree approximates;
+ *   - Morton keys, a stable sort, the octree topology, the cell multipoles
+ *     (monopole + traceless quadrupole about the centre of mass, the
+ *     expansion of Sect. 1), walk groups and the tree walk under a box-box
+ *     opening-angle test, each step written from its definition, slow and
+ *     obvious, in FP64 on the FP32 input values;
+ *   - the unsoftened FP64 chain/perturber couplings of Sect. 2 and Eq. 3;
+ *   - k-nearest / radius perturber selection.
+ *
+ * Readings where the paper is silent (octree instead of VINE's binary tree,
+ * key quantisation, leaf rule, group rule, MAC geometry, quadrupole form) are
+ * the ones stated at each function. Build with -ffp-contract=off: the key
+ * quantisation and the FP32 selection distances must round every operation
+ * separately.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_BITS 21
+#define ORC_MAXLEVEL 21
+#define ORC_GRID 2097152.0 /* 2^21 */
+
+/* ------------------------------------------------------------------ */
+/* Neumaier compensated sum (order-independent to ~1e-16)              */
+/* ------------------------------------------------------------------ */
+typedef struct { double s, c; } nsum;
+static void nadd(nsum *a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double nval(const nsum *a) { return a->s + a->c; }
+
+/* Pair softening (Sect. 3): stars and SMBHs have their own Plummer lengths,
+ * interactions with the chain centre-of-mass particle are not softened.
+ * Reading: eps_ij = max(eps_i, eps_j), and 0 if either particle is marked
+ * unsoftened (eps = 0). */
+static double pair_eps(double ei, double ej) {
+    if (ei == 0.0 || ej == 0.0) return 0.0;
+    return ei > ej ? ei : ej;
+}
+
+/* Softened point-mass acceleration on i from j and potential (G = 1):
+ * a = m_j r / (r^2+e^2)^{3/2}, phi = -m_j / (r^2+e^2)^{1/2}, r = x_j - x_i.
+ * A pair at zero softened distance contributes nothing. */
+static void p2p(double xi, double yi, double zi, double xj, double yj, double zj,
+                double mj, double e, nsum *ax, nsum *ay, nsum *az, nsum *ph) {
+    double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    double r2 = dx * dx + dy * dy + dz * dz + e * e;
+    if (r2 <= 0.0) return;
+    double rinv = 1.0 / sqrt(r2);
+    double mr3 = mj * rinv * rinv * rinv;
+    nadd(ax, mr3 * dx); nadd(ay, mr3 * dy); nadd(az, mr3 * dz);
+    nadd(ph, -mj * rinv);
+}
+
+/* ------------------------------------------------------------------ */
+/* 1. Direct sum                                                        */
+/* ------------------------------------------------------------------ */
+/* Acceleration and potential on targets tidx[0..nt) from all n particles,
+ * skipping j == i. eps[j] = 0 marks an unsoftened particle. */
+void orc_direct(int64_t n, const double *x, const double *y, const double *z,
+                const double *m, const double *eps, int64_t nt, const int64_t *tidx,
+                double *ax, double *ay, double *az, double *pot) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = tidx[t];
+        nsum sx = {0, 0}, sy = {0, 0}, sz = {0, 0}, sp = {0, 0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            p2p(x[i], y[i], z[i], x[j], y[j], z[j], m[j], pair_eps(eps[i], eps[j]), &sx, &sy, &sz, &sp);
+        }
+        ax[t] = nval(&sx); ay[t] = nval(&sy); az[t] = nval(&sz); pot[t] = nval(&sp);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* 2. Morton keys                                                       */
+/* ------------------------------------------------------------------ */
+/* Bounding cube of FP32 positions: per axis min (exact FP32 compare), side
+ * L = max_a (max_a - min_a) with each difference one FP64 subtraction, and
+ * scale = 2^21 / L as one FP64 division (0 when L = 0). */
+void orc_bounds(int64_t n, const float *x, const float *y, const float *z,
+                double out_min[3], double *out_L, double *out_scale) {
+    const float *c[3] = {x, y, z};
+    double L = 0.0;
+    for (int a = 0; a < 3; a++) {
+        float lo = 0.0f, hi = 0.0f;
+        for (int64_t i = 0; i < n; i++) {
+            float v = c[a][i];
+            if (i == 0 || v < lo) lo = v;
+            if (i == 0 || v > hi) hi = v;
+        }
+        out_min[a] = (double)lo;
+        double ext = (double)hi - (double)lo;
+        if (ext > L) L = ext;
+    }
+    *out_L = L;
+    *out_scale = (L > 0.0) ? ORC_GRID / L : 0.0;
+}
+
+/* Integer grid coordinate: q = min(floor((x - min) * scale), 2^21 - 1), the
+ * subtraction and the product each rounded once in FP64. */
+static uint64_t grid_coord(float v, double lo, double scale) {
+    double d = (double)v - lo;
+    double t = d * scale;
+    double f = floor(t);
+    if (f >= ORC_GRID - 1.0) return (uint64_t)(ORC_GRID - 1.0);
+    if (f < 0.0) return 0;
+    return (uint64_t)f;
+}
+
+/* 63-bit key: bit 3k = x_k, 3k+1 = y_k, 3k+2 = z_k (k = 0 least significant). */
+static uint64_t interleave(uint64_t qx, uint64_t qy, uint64_t qz) {
+    uint64_t key = 0;
+    for (int k = 0; k < ORC_BITS; k++) {
+        key |= ((qx >> k) & 1ull) << (3 * k);
+        key |= ((qy >> k) & 1ull) << (3 * k + 1);
+        key |= ((qz >> k) & 1ull) << (3 * k + 2);
+    }
+    return key;
+}
+
+static void deinterleave(uint64_t key, int64_t *qx, int64_t *qy, int64_t *qz) {
+    int64_t a = 0, b = 0, c = 0;
+    for (int k = 0; k < ORC_BITS; k++) {
+        a |= (int64_t)((key >> (3 * k)) & 1ull) << k;
+        b |= (int64_t)((key >> (3 * k + 1)) & 1ull) << k;
+        c |= (int64_t)((key >> (3 * k + 2)) & 1ull) << k;
+    }
+    *qx = a; *qy = b; *qz = c;
+}
+
+void orc_keys(int64_t n, const float *x, const float *y, const float *z,
+              const double lo[3], double scale, uint64_t *key) {
+    for (int64_t i = 0; i < n; i++)
+        key[i] = interleave(grid_coord(x[i], lo[0], scale), grid_coord(y[i], lo[1], scale),
+                            grid_coord(z[i], lo[2], scale));
+}
+
+/* ------------------------------------------------------------------ */
+/* 3. Stable sort of (key, index): equal keys keep ascending index       */
+/* ------------------------------------------------------------------ */
+typedef struct { uint64_t key; int64_t idx; } kv;
+static int kv_cmp(const void *a, const void *b) {
+    const kv *p = (const kv *)a, *q = (const kv *)b;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    return (p->idx > q->idx) - (p->idx < q->idx);
+}
+void orc_sort(int64_t n, const uint64_t *key, uint64_t *skey, int64_t *perm) {
+    kv *t = (kv *)malloc(sizeof(kv) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) { t[i].key = key[i]; t[i].idx = i; }
+    qsort(t, (size_t)n, sizeof(kv), kv_cmp);
+    for (int64_t i = 0; i < n; i++) { skey[i] = t[i].key; perm[i] = t[i].idx; }
+    free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* 4. Octree                                                            */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t n, ncell, cap, ngroup, gcap;
+    int32_t n_leaf, group_max;
+    double lo[3], L, scale;
+    uint64_t *key;        /* sorted keys */
+    int64_t *perm;        /* sorted slot -> caller index */
+    double *x, *y, *z, *m;/* sorted, FP64 copies of the FP32 inputs */
+    /* cells in breadth-first order: ascending level, then ascending first */
+    int32_t *level;
+    int64_t *first, *count, *child, *nchild, *parent;
+    int64_t *ox, *oy, *oz;          /* integer-grid origin of the cell box */
+    double *cm, *cx, *cy, *cz, *cq; /* mass, centre of mass, Q (xx,yy,zz,xy,xz,yz) */
+    /* walk groups */
+    int64_t *gfirst, *gcount, *gcell; /* gcell: cell whose box is the group box */
+} orc_tree;
+
+static void tree_push_cell(orc_tree *t, int32_t lev, int64_t first, int64_t count, int64_t parent) {
+    if (t->ncell == t->cap) {
+        t->cap = t->cap ? 2 * t->cap : 64;
+#define GROW(p, ty) t->p = (ty *)realloc(t->p, sizeof(ty) * (size_t)t->cap)
+        GROW(level, int32_t); GROW(first, int64_t); GROW(count, int64_t); GROW(child, int64_t);
+        GROW(nchild, int64_t); GROW(parent, int64_t); GROW(ox, int64_t); GROW(oy, int64_t); GROW(oz, int64_t);
+#undef GROW
+    }
+    int64_t c = t->ncell++;
+    t->level[c] = lev; t->first[c] = first; t->count[c] = count;
+    t->child[c] = -1; t->nchild[c] = 0; t->parent[c] = parent;
+    /* box origin: the key of the first particle with the bits below level lev cleared */
+    int sh = 3 * (ORC_MAXLEVEL - lev);
+    uint64_t pre = (sh >= 64) ? 0 : ((t->key[first] >> sh) << sh);
+    deinterleave(pre, &t->ox[c], &t->oy[c], &t->oz[c]);
+}
+
+static int cell_is_leaf(const orc_tree *t, int64_t c) { return t->nchild[c] == 0; }
+
+/* Topology (reading of the silent points): the root holds all particles; a
+ * cell is split iff it has more than n_leaf particles and level < 21; its
+ * children are the non-empty octants, i.e. maximal runs of equal 3-bit key
+ * digits at the next level, ordered by octant. Built level by level, which
+ * gives the breadth-first order directly. */
+static void build_topology(orc_tree *t) {
+    if (t->n == 0) return;
+    tree_push_cell(t, 0, 0, t->n, -1);
+    int64_t lev_begin = 0, lev_end = 1;
+    for (int32_t lev = 0; lev < ORC_MAXLEVEL; lev++) {
+        for (int64_t c = lev_begin; c < lev_end; c++) {
+            if (t->count[c] <= t->n_leaf) continue;
+            int sh = 3 * (ORC_MAXLEVEL - (lev + 1));
+            int64_t s = t->first[c], e = s + t->count[c];
+            int64_t run = s;
+            t->child[c] = t->ncell;
+            for (int64_t i = s + 1; i <= e; i++) {
+                if (i == e || ((t->key[i] >> sh) & 7u) != ((t->key[run] >> sh) & 7u)) {
+                    tree_push_cell(t, lev + 1, run, i - run, c);
+                    t->nchild[c]++;
+                    run = i;
+                }
+            }
+        }
+        lev_begin = lev_end;
+        lev_end = t->ncell;
+        if (lev_begin == lev_end) break;
+    }
+}
+
+/* Cell multipoles from the cell's own particles (Sect. 1: expansion about the
+ * group's centre of mass): M = sum m, COM = sum m x / M, traceless
+ * Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab), d = x - COM. A massless cell
+ * takes its geometric centre and Q = 0. */
+static void build_moments(orc_tree *t) {
+    t->cm = (double *)malloc(sizeof(double) * (size_t)(t->ncell + 1));
+    t->cx = (double *)malloc(sizeof(double) * (size_t)(t->ncell + 1));
+    t->cy = (double *)malloc(sizeof(double) * (size_t)(t->ncell + 1));
+    t->cz = (double *)malloc(sizeof(double) * (size_t)(t->ncell + 1));
+    t->cq = (double *)malloc(sizeof(double) * 6 * (size_t)(t->ncell + 1));
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < t->ncell; c++) {
+        int64_t s = t->first[c], e = s + t->count[c];
+        double M = 0, sx = 0, sy = 0, sz = 0;
+        for (int64_t i = s; i < e; i++) {
+            M += t->m[i]; sx += t->m[i] * t->x[i]; sy += t->m[i] * t->y[i]; sz += t->m[i] * t->z[i];
+        }
+        double gx, gy, gz;
+        if (M > 0) { gx = sx / M; gy = sy / M; gz = sz / M; }
+        else {
+            double side = ldexp(1.0, ORC_MAXLEVEL - t->level[c]);
+            double u = (t->L > 0) ? t->L / ORC_GRID : 0.0;
+            gx = t->lo[0] + ((double)t->ox[c] + 0.5 * side) * u;
+            gy = t->lo[1] + ((double)t->oy[c] + 0.5 * side) * u;
+            gz = t->lo[2] + ((double)t->oz[c] + 0.5 * side) * u;
+        }
+        double q[6] = {0, 0, 0, 0, 0, 0};
+        if (M > 0) {
+            for (int64_t i = s; i < e; i++) {
+                double dx = t->x[i] - gx, dy = t->y[i] - gy, dz = t->z[i] - gz;
+                double d2 = dx * dx + dy * dy + dz * dz, mi = t->m[i];
+                q[0] += mi * (3 * dx * dx - d2); q[1] += mi * (3 * dy * dy - d2);
+                q[2] += mi * (3 * dz * dz - d2); q[3] += mi * 3 * dx * dy;
+                q[4] += mi * 3 * dx * dz; q[5] += mi * 3 * dy * dz;
+            }
+        }
+        t->cm[c] = M; t->cx[c] = gx; t->cy[c] = gy; t->cz[c] = gz;
+        for (int k = 0; k < 6; k++) t->cq[6 * c + k] = q[k];
+    }
+}
+
+static void push_group(orc_tree *t, int64_t first, int64_t count, int64_t boxcell) {
+    if (t->ngroup == t->gcap) {
+        t->gcap = t->gcap ? 2 * t->gcap : 64;
+        t->gfirst = (int64_t *)realloc(t->gfirst, sizeof(int64_t) * (size_t)t->gcap);
+        t->gcount = (int64_t *)realloc(t->gcount, sizeof(int64_t) * (size_t)t->gcap);
+        t->gcell = (int64_t *)realloc(t->gcell, sizeof(int64_t) * (size_t)t->gcap);
+    }
+    t->gfirst[t->ngroup] = first; t->gcount[t->ngroup] = count; t->gcell[t->ngroup] = boxcell;
+    t->ngroup++;
+}
+
+static void chunk_cell(orc_tree *t, int64_t c) {
+    for (int64_t o = 0; o < t->count[c]; o += t->group_max) {
+        int64_t k = t->count[c] - o;
+        push_group(t, t->first[c] + o, k < t->group_max ? k : t->group_max, c);
+    }
+}
+
+/* Walk groups (reading): a "unit" is a cell with at most G particles whose
+ * parent has more; consecutive unit siblings are packed greedily while the
+ * total stays <= G. A pack of one unit uses that unit's box, a pack of
+ * several uses the parent's box. A leaf with more than G particles is cut
+ * into chunks of G that use the leaf's box. */
+static void visit_groups(orc_tree *t, int64_t p) {
+    int64_t pk_first = -1, pk_count = 0, pk_units = 0, pk_cell = -1;
+    for (int64_t k = 0; k < t->nchild[p]; k++) {
+        int64_t c = t->child[p] + k;
+        if (t->count[c] <= t->group_max) {
+            if (pk_units > 0 && pk_count + t->count[c] > t->group_max) {
+                push_group(t, pk_first, pk_count, pk_units == 1 ? pk_cell : p);
+                pk_units = 0;
+            }
+            if (pk_units == 0) { pk_first = t->first[c]; pk_count = 0; pk_cell = c; }
+            pk_count += t->count[c];
+            pk_units++;
+        } else {
+            if (pk_units > 0) { push_group(t, pk_first, pk_count, pk_units == 1 ? pk_cell : p); pk_units = 0; }
+            if (cell_is_leaf(t, c)) chunk_cell(t, c);
+            else visit_groups(t, c);
+        }
+    }
+    if (pk_units > 0) push_group(t, pk_first, pk_count, pk_units == 1 ? pk_cell : p);
+}
+
+static void build_groups(orc_tree *t) {
+    if (t->ncell == 0) return;
+    if (t->count[0] <= t->group_max) push_group(t, 0, t->count[0], 0);
+    else if (cell_is_leaf(t, 0)) chunk_cell(t, 0);
+    else visit_groups(t, 0);
+}
+
+orc_tree *orc_tree_build(int64_t n, const float *x, const float *y, const float *z, const float *m,
+                         int32_t n_leaf, int32_t group_max) {
+    orc_tree *t = (orc_tree *)calloc(1, sizeof(orc_tree));
+    t->n = n; t->n_leaf = n_leaf; t->group_max = group_max;
+    orc_bounds(n, x, y, z, t->lo, &t->L, &t->scale);
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    uint64_t *raw = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+    orc_keys(n, x, y, z, t->lo, t->scale, raw);
+    t->key = (uint64_t *)malloc(sizeof(uint64_t) * nn);
+    t->perm = (int64_t *)malloc(sizeof(int64_t) * nn);
+    orc_sort(n, raw, t->key, t->perm);
+    free(raw);
+    t->x = (double *)malloc(sizeof(double) * nn); t->y = (double *)malloc(sizeof(double) * nn);
+    t->z = (double *)malloc(sizeof(double) * nn); t->m = (double *)malloc(sizeof(double) * nn);
+    for (int64_t i = 0; i < n; i++) {
+        int64_t j = t->perm[i];
+        t->x[i] = x[j]; t->y[i] = y[j]; t->z[i] = z[j]; t->m[i] = m[j];
+    }
+    build_topology(t);
+    build_moments(t);
+    build_groups(t);
+    return t;
+}
+
+void orc_tree_free(orc_tree *t) {
+    if (!t) return;
+    free(t->key); free(t->perm); free(t->x); free(t->y); free(t->z); free(t->m);
+    free(t->level); free(t->first); free(t->count); free(t->child); free(t->nchild); free(t->parent);
+    free(t->ox); free(t->oy); free(t->oz); free(t->cm); free(t->cx); free(t->cy); free(t->cz); free(t->cq);
+    free(t->gfirst); free(t->gcount); free(t->gcell);
+    free(t);
+}
+
+void orc_tree_sizes(const orc_tree *t, int64_t out[3]) { out[0] = t->n; out[1] = t->ncell; out[2] = t->ngroup; }
+void orc_tree_bounds(const orc_tree *t, double out[5]) {
+    out[0] = t->lo[0]; out[1] = t->lo[1]; out[2] = t->lo[2]; out[3] = t->L; out[4] = t->scale;
+}
+void orc_tree_keys(const orc_tree *t, uint64_t *key, int64_t *perm) {
+    memcpy(key, t->key, sizeof(uint64_t) * (size_t)t->n);
+    memcpy(perm, t->perm, sizeof(int64_t) * (size_t)t->n);
+}
+/* cells: [ncell][9] = level, first, count, child, nchild, parent, ox, oy, oz */
+void orc_tree_cells(const orc_tree *t, int64_t *out) {
+    for (int64_t c = 0; c < t->ncell; c++) {
+        int64_t *o = out + 9 * c;
+        o[0] = t->level[c]; o[1] = t->first[c]; o[2] = t->count[c]; o[3] = t->child[c];
+        o[4] = t->nchild[c]; o[5] = t->parent[c]; o[6] = t->ox[c]; o[7] = t->oy[c]; o[8] = t->oz[c];
+    }
+}
+/* moments: [ncell][10] = M, cx, cy, cz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz */
+void orc_tree_moments(const orc_tree *t, double *out) {
+    for (int64_t c = 0; c < t->ncell; c++) {
+        double *o = out + 10 * c;
+        o[0] = t->cm[c]; o[1] = t->cx[c]; o[2] = t->cy[c]; o[3] = t->cz[c];
+        for (int k = 0; k < 6; k++) o[4 + k] = t->cq[6 * c + k];
+    }
+}
+/* groups: [ngroup][3] = first, count, box cell */
+void orc_tree_groups(const orc_tree *t, int64_t *out) {
+    for (int64_t g = 0; g < t->ngroup; g++) {
+        out[3 * g] = t->gfirst[g]; out[3 * g + 1] = t->gcount[g]; out[3 * g + 2] = t->gcell[g];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* 5. Tree walk                                                         */
+/* ------------------------------------------------------------------ */
+/* Opening test (reading of the opening-angle criterion): cell C of side
+ * s = 2^(21 - level) grid units is accepted for a group whose box is B iff
+ * s^2 < theta^2 d^2, with d the minimum Euclidean distance between the boxes
+ * of B and C in grid units and theta^2 = theta * theta, all in FP64 (integers
+ * below 2^53 are exact). A box that touches or contains the group has d = 0
+ * and is opened. */
+static int64_t gap1(int64_t blo, int64_t bhi, int64_t clo, int64_t chi) {
+    if (clo >= bhi) return clo - bhi;
+    if (blo >= chi) return blo - chi;
+    return 0;
+}
+static int mac_accept(const orc_tree *t, const int64_t blo[3], const int64_t bhi[3], int64_t c, double theta2) {
+    int64_t s = (int64_t)1 << (ORC_MAXLEVEL - t->level[c]);
+    int64_t gx = gap1(blo[0], bhi[0], t->ox[c], t->ox[c] + s);
+    int64_t gy = gap1(blo[1], bhi[1], t->oy[c], t->oy[c] + s);
+    int64_t gz = gap1(blo[2], bhi[2], t->oz[c], t->oz[c] + s);
+    double d2 = (double)(gx * gx + gy * gy + gz * gz);
+    double s2 = (double)s * (double)s;
+    return s2 < theta2 * d2;
+}
+
+/* Softened monopole + quadrupole field of cell c at (px,py,pz) (reading):
+ * r = x - COM, rho^2 = r.r + e^2, phi = -M/rho - (r.Q.r)/(2 rho^5),
+ * a = -M r/rho^3 + Q r/rho^5 - 5 (r.Q.r) r/(2 rho^7); for e = 0 this is the
+ * exact two-term multipole expansion about the centre of mass. */
+static void m2p(const orc_tree *t, int64_t c, double px, double py, double pz, double e, int quad,
+                nsum *ax, nsum *ay, nsum *az, nsum *ph) {
+    double M = t->cm[c];
+    if (M == 0.0) return;
+    double rx = px - t->cx[c], ry = py - t->cy[c], rz = pz - t->cz[c];
+    double r2 = rx * rx + ry * ry + rz * rz + e * e;
+    if (r2 <= 0.0) return;
+    double rinv = 1.0 / sqrt(r2), rinv2 = rinv * rinv, rinv3 = rinv * rinv2;
+    double fx = -M * rx * rinv3, fy = -M * ry * rinv3, fz = -M * rz * rinv3, p = -M * rinv;
+    if (quad) {
+        const double *q = t->cq + 6 * c;
+        double qx = q[0] * rx + q[3] * ry + q[4] * rz;
+        double qy = q[3] * rx + q[1] * ry + q[5] * rz;
+        double qz = q[4] * rx + q[5] * ry + q[2] * rz;
+        double rqr = rx * qx + ry * qy + rz * qz;
+        double rinv5 = rinv3 * rinv2, rinv7 = rinv5 * rinv2;
+        fx += qx * rinv5 - 2.5 * rqr * rx * rinv7;
+        fy += qy * rinv5 - 2.5 * rqr * ry * rinv7;
+        fz += qz * rinv5 - 2.5 * rqr * rz * rinv7;
+        p += -0.5 * rqr * rinv5;
+    }
+    nadd(ax, fx); nadd(ay, fy); nadd(az, fz); nadd(ph, p);
+}
+
+typedef struct {
+    const orc_tree *t;
+    int64_t blo[3], bhi[3];
+    double theta2;
+    int quad;
+    double px, py, pz, e;
+    int64_t self; /* sorted slot of the target, or -1 */
+    nsum ax, ay, az, ph;
+    int64_t n_p2p, n_m2p;
+} walk_state;
+
+static void walk_cell(walk_state *w, int64_t c) {
+    const orc_tree *t = w->t;
+    if (mac_accept(t, w->blo, w->bhi, c, w->theta2)) {
+        m2p(t, c, w->px, w->py, w->pz, w->e, w->quad, &w->ax, &w->ay, &w->az, &w->ph);
+        w->n_m2p++;
+        return;
+    }
+    if (cell_is_leaf(t, c)) {
+        for (int64_t j = t->first[c]; j < t->first[c] + t->count[c]; j++) {
+            if (j == w->self) continue;
+            p2p(w->px, w->py, w->pz, t->x[j], t->y[j], t->z[j], t->m[j], w->e, &w->ax, &w->ay, &w->az, &w->ph);
+            w->n_p2p++;
+        }
+        return;
+    }
+    for (int64_t k = 0; k < t->nchild[c]; k++) walk_cell(w, t->child[c] + k);
+}
+
+static void box_of_cell(const orc_tree *t, int64_t c, int64_t lo[3], int64_t hi[3]) {
+    int64_t s = (int64_t)1 << (ORC_MAXLEVEL - t->level[c]);
+    lo[0] = t->ox[c]; lo[1] = t->oy[c]; lo[2] = t->oz[c];
+    hi[0] = lo[0] + s; hi[1] = lo[1] + s; hi[2] = lo[2] + s;
+}
+
+/* Tree forces on every tree particle, written in caller order.
+ * eps_star softens every tree pair (all tree particles are stars).
+ * Extra particles (chain centres of mass, unsoftened when xeps = 0) are not in
+ * the tree: they act on every tree particle and on each other by the direct
+ * pair rule, and each feels the tree through its own walk whose group box is
+ * the grid cell [q, q+1)^3 of its position (q unclamped, limited to
+ * +-2^23). counts (optional, [n][2]) receives the P2P and M2P interaction
+ * counts per tree particle. */
+void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t quad,
+                     int32_t nx, const float *xx, const float *xy, const float *xz, const double *xm,
+                     const double *xeps,
+                     double *ax, double *ay, double *az, double *pot,
+                     double *xax, double *xay, double *xaz, double *xpot, int64_t *counts) {
+    double theta2 = theta * theta;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t g = 0; g < t->ngroup; g++) {
+        int64_t blo[3], bhi[3];
+        box_of_cell(t, t->gcell[g], blo, bhi);
+        for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
+            walk_state w;
+            memset(&w, 0, sizeof w);
+            w.t = t; w.theta2 = theta2; w.quad = quad; w.e = eps_star; w.self = i;
+            memcpy(w.blo, blo, sizeof blo); memcpy(w.bhi, bhi, sizeof bhi);
+            w.px = t->x[i]; w.py = t->y[i]; w.pz = t->z[i];
+            if (t->ncell > 0) walk_cell(&w, 0);
+            for (int32_t k = 0; k < nx; k++)
+                p2p(w.px, w.py, w.pz, xx[k], xy[k], xz[k], xm[k], pair_eps(eps_star, xeps[k]), &w.ax, &w.ay, &w.az, &w.ph);
+            int64_t o = t->perm[i];
+            ax[o] = nval(&w.ax); ay[o] = nval(&w.ay); az[o] = nval(&w.az); pot[o] = nval(&w.ph);
+            if (counts) { counts[2 * o] = w.n_p2p; counts[2 * o + 1] = w.n_m2p; }
+        }
+    }
+    for (int32_t k = 0; k < nx; k++) {
+        walk_state w;
+        memset(&w, 0, sizeof w);
+        w.t = t; w.theta2 = theta2; w.quad = quad; w.self = -1;
+        w.e = (xeps[k] == 0.0) ? 0.0 : (xeps[k] > eps_star ? xeps[k] : eps_star);
+        w.px = xx[k]; w.py = xy[k]; w.pz = xz[k];
+        const float pv[3] = {xx[k], xy[k], xz[k]};
+        for (int a = 0; a < 3; a++) {
+            double q = floor(((double)pv[a] - t->lo[a]) * t->scale);
+            if (q < -8388608.0) q = -8388608.0;
+            if (q > 8388608.0) q = 8388608.0;
+            w.blo[a] = (int64_t)q; w.bhi[a] = (int64_t)q + 1;
+        }
+        if (t->ncell > 0) walk_cell(&w, 0);
+        for (int32_t j = 0; j < nx; j++) {
+            if (j == k) continue;
+            p2p(w.px, w.py, w.pz, xx[j], xy[j], xz[j], xm[j], pair_eps(xeps[k], xeps[j]), &w.ax, &w.ay, &w.az, &w.ph);
+        }
+        xax[k] = nval(&w.ax); xay[k] = nval(&w.ay); xaz[k] = nval(&w.az); xpot[k] = nval(&w.ph);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* 6. Chain / perturber coupling, unsoftened FP64 (Sect. 2, Eq. 3)      */
+/* ------------------------------------------------------------------ */
+/* f(r) = r / |r|^3 (unsoftened); zero separation contributes nothing. */
+static void kepler_acc(double rx, double ry, double rz, double m, double out[3]) {
+    double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 <= 0.0) { out[0] = out[1] = out[2] = 0.0; return; }
+    double rinv = 1.0 / sqrt(r2);
+    double s = m * rinv * rinv * rinv;
+    out[0] = s * rx; out[1] = s * ry; out[2] = s * rz;
+}
+
+/* Chain members k (mass cm[k], position cx[3k..]) and perturbers p (mass pm[p],
+ * position px[3p..]) with the chain centre of mass com[3] and total mass
+ * M = sum cm:
+ *   a_pert[p]  = sum_k cm_k f(x_k - x_p) - M f(com - x_p)
+ *                (resolved chain replaces the centre-of-mass particle);
+ *   a_chain[k] = sum_p pm_p f(x_p - x_k)   (perturbers on each member);
+ *   corr       = (1/M) sum_k cm_k a_chain[k]  (Eq. 3);
+ *   sub        = sum_p pm_p f(x_p - com)   (the direct, unsoftened tree terms of
+ *                the perturbers on the centre-of-mass particle, to subtract). */
+void orc_perturber(int32_t nch, const double *cm, const double *cx, int32_t np, const double *pm,
+                   const double *px, double *a_pert, double *a_chain, double corr[3], double sub[3]) {
+    double M = 0, com[3] = {0, 0, 0};
+    for (int32_t k = 0; k < nch; k++) {
+        M += cm[k];
+        for (int a = 0; a < 3; a++) com[a] += cm[k] * cx[3 * k + a];
+    }
+    for (int a = 0; a < 3; a++) com[a] = (M > 0) ? com[a] / M : 0.0;
+#pragma omp parallel for schedule(static)
+    for (int32_t p = 0; p < np; p++) {
+        nsum s[3] = {{0, 0}, {0, 0}, {0, 0}};
+        double f[3];
+        for (int32_t k = 0; k < nch; k++) {
+            kepler_acc(cx[3 * k] - px[3 * p], cx[3 * k + 1] - px[3 * p + 1], cx[3 * k + 2] - px[3 * p + 2], cm[k], f);
+            for (int a = 0; a < 3; a++) nadd(&s[a], f[a]);
+        }
+        kepler_acc(com[0] - px[3 * p], com[1] - px[3 * p + 1], com[2] - px[3 * p + 2], M, f);
+        for (int a = 0; a < 3; a++) { nadd(&s[a], -f[a]); a_pert[3 * p + a] = nval(&s[a]); }
+    }
+    nsum cs[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int32_t k = 0; k < nch; k++) {
+        nsum s[3] = {{0, 0}, {0, 0}, {0, 0}};
+        double f[3];
+        for (int32_t p = 0; p < np; p++) {
+            kepler_acc(px[3 * p] - cx[3 * k], px[3 * p + 1] - cx[3 * k + 1], px[3 * p + 2] - cx[3 * k + 2], pm[p], f);
+            for (int a = 0; a < 3; a++) nadd(&s[a], f[a]);
+        }
+        for (int a = 0; a < 3; a++) {
+            a_chain[3 * k + a] = nval(&s[a]);
+            nadd(&cs[a], cm[k] * a_chain[3 * k + a]);
+        }
+    }
+    nsum ss[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int32_t p = 0; p < np; p++) {
+        double f[3];
+        kepler_acc(px[3 * p] - com[0], px[3 * p + 1] - com[1], px[3 * p + 2] - com[2], pm[p], f);
+        for (int a = 0; a < 3; a++) nadd(&ss[a], f[a]);
+    }
+    for (int a = 0; a < 3; a++) { corr[a] = (M > 0) ? nval(&cs[a]) / M : 0.0; sub[a] = nval(&ss[a]); }
+}
+
+/* ------------------------------------------------------------------ */
+/* 7. Perturber selection                                               */
+/* ------------------------------------------------------------------ */
+/* Squared distance in FP32, each operation rounded once in this order:
+ * d = x - c per axis, d2 = (dx*dx + dy*dy) + dz*dz. */
+static float dist2_f32(float x, float y, float z, float cx, float cy, float cz) {
+    float dx = x - cx, dy = y - cy, dz = z - cz;
+    float a = dx * dx, b = dy * dy, c = dz * dz;
+    float s = a + b;
+    return s + c;
+}
+
+typedef struct { float d2; int64_t idx; } fd;
+static int fd_cmp(const void *a, const void *b) {
+    const fd *p = (const fd *)a, *q = (const fd *)b;
+    if (p->d2 != q->d2) return p->d2 < q->d2 ? -1 : 1;
+    return (p->idx > q->idx) - (p->idx < q->idx);
+}
+
+/* The k particles nearest to c (ties by lower index), ascending (d2, index). */
+int64_t orc_knn(int64_t n, const float *x, const float *y, const float *z, const float c[3], int64_t k, int64_t *out) {
+    fd *t = (fd *)malloc(sizeof(fd) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) { t[i].d2 = dist2_f32(x[i], y[i], z[i], c[0], c[1], c[2]); t[i].idx = i; }
+    qsort(t, (size_t)n, sizeof(fd), fd_cmp);
+    if (k > n) k = n;
+    for (int64_t i = 0; i < k; i++) out[i] = t[i].idx;
+    free(t);
+    return k;
+}
+
+/* All particles with d2 < r2 (FP32), ascending index; returns the count
+ * (at most cap are written). */
+int64_t orc_radius(int64_t n, const float *x, const float *y, const float *z, const float c[3], float r2,
+                   int64_t cap, int64_t *out) {
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (dist2_f32(x[i], y[i], z[i], c[0], c[1], c[2]) < r2) { if (k < cap) out[k] = i; k++; }
+    return k;
+}

@@ -1,0 +1,398 @@
+"""Pins for the CPU oracle: each check ties it to something other than itself
+(closed forms, conservation laws, hand-derived fixtures, library routines,
+brute force on tiny inputs). A dropped term, a sign or index slip, or a
+transposed operand in the oracle fails at least one of these."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# direct sum
+# ---------------------------------------------------------------------------
+def test_two_body_closed_form():
+    """a = m r/(r^2+e^2)^{3/2} toward the other body, phi = -m/(r^2+e^2)^{1/2}."""
+    pos = np.array([[0.0, 3.0], [0.0, 4.0], [0.0, 0.0]])  # separation 5
+    m = np.array([2.0, 7.0])
+    for e in (0.0, 0.5):
+        a, p = oracle.direct(pos, m, e)
+        d2 = 25.0 + e * e
+        f0 = 7.0 / d2 ** 1.5
+        np.testing.assert_allclose(a[:, 0], [f0 * 3, f0 * 4, 0.0], rtol=1e-14)
+        f1 = 2.0 / d2 ** 1.5
+        np.testing.assert_allclose(a[:, 1], [-f1 * 3, -f1 * 4, 0.0], rtol=1e-14)
+        np.testing.assert_allclose(p, [-7.0 / math.sqrt(d2), -2.0 / math.sqrt(d2)], rtol=1e-14)
+
+
+def test_unsoftened_marker_and_max_rule():
+    """Pair softening is max(eps_i, eps_j), zero if either particle is marked 0."""
+    pos = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 2.0], [0.0, 0.0, 0.0]])
+    m = np.array([1.0, 1.0, 1.0])
+    eps = np.array([0.1, 0.3, 0.0])
+    a, _ = oracle.direct(pos, m, eps, targets=[0])
+    expect_x = 1.0 / (1.0 + 0.09) ** 1.5             # pair (0,1): max(0.1, 0.3)
+    expect_y = 1.0 * 2.0 / 2.0 ** 3                  # pair (0,2): unsoftened
+    np.testing.assert_allclose(a[:, 0], [expect_x, expect_y, 0.0], rtol=1e-14)
+
+
+def test_direct_momentum_conservation():
+    """Newton's third law: sum_i m_i a_i = 0 to rounding."""
+    w = ics.plummer(512, seed=11)
+    a, _ = oracle.direct(w.pos, w.mass, 0.01)
+    tot = (w.mass * a).sum(1)
+    scale = (w.mass * np.linalg.norm(a, axis=0)).sum()
+    assert np.abs(tot).max() <= 1e-13 * scale
+
+
+def test_plummer_potential_energy():
+    """W = -3 pi / 32 for a Plummer sphere with G = M = b = 1 (sampling noise ~2%)."""
+    w = ics.plummer(4096, seed=1)
+    _, p = oracle.direct(w.pos, w.mass, 1e-4)
+    W = 0.5 * (w.mass * p).sum()
+    assert abs(W / (-3 * math.pi / 32) - 1) < 0.05
+
+
+def _kepler_rel(t, a, e, M):
+    """Relative position of a Kepler orbit started at pericentre on +x, moving +y."""
+    n = math.sqrt(M / a ** 3)
+    Mean = n * t
+    E = Mean
+    for _ in range(50):
+        E -= (E - e * math.sin(E) - Mean) / (1 - e * math.cos(E))
+    return np.array([a * (math.cos(E) - e), a * math.sqrt(1 - e * e) * math.sin(E), 0.0])
+
+
+def _kepler_run(dt, T):
+    a, e, M = 1.0, 0.5, 1.0
+    m = np.array([0.5, 0.5])
+    rp = a * (1 - e)
+    vp = math.sqrt(M * (1 + e) / rp)
+    pos = np.array([[0.5 * rp, -0.5 * rp], [0.0, 0.0], [0.0, 0.0]])
+    vel = np.array([[0.0, 0.0], [0.5 * vp, -0.5 * vp], [0.0, 0.0]])
+    f = lambda x: oracle.direct(x, m, 0.0)[0]
+    nst = int(round(T / dt))
+    pos, vel, _ = oracle.kdk(pos, vel, f(pos), dt, f, nst)
+    rel = pos[:, 0] - pos[:, 1]
+    en = 0.5 * (m * (vel * vel).sum(0)).sum() - 0.25 / np.linalg.norm(rel)
+    return rel, en, _kepler_rel(nst * dt, a, e, M)
+
+
+def test_kdk_kepler_second_order():
+    """KDK on a Kepler orbit: position error vs Kepler's equation shrinks as dt^2,
+    and the energy stays at -G m1 m2 / (2a) = -1/8."""
+    r1, e1, x1 = _kepler_run(2e-3, 1.3)
+    r2, e2, x2 = _kepler_run(1e-3, 1.3)
+    err1, err2 = np.linalg.norm(r1 - x1), np.linalg.norm(r2 - x2)
+    assert 3.0 < err1 / err2 < 5.0
+    assert err2 < 1e-4
+    assert abs(e2 + 0.125) < 1e-5
+
+
+def test_energy_two_body_closed_form():
+    pos = np.array([[0.0, 2.0], [0.0, 0.0], [0.0, 0.0]])
+    vel = np.array([[0.0, 0.0], [1.0, -0.5], [0.0, 0.0]])
+    m = np.array([1.0, 2.0])
+    _, p = oracle.direct(pos, m, 0.0)
+    E = oracle.energy(pos, vel, m, p)
+    assert E["ekin"] == pytest.approx(0.5 * 1 * 1 + 0.5 * 2 * 0.25, rel=1e-15)
+    assert E["epot"] == pytest.approx(-1.0 * 2.0 / 2.0, rel=1e-15)
+    np.testing.assert_allclose(E["P"], [0.0, 0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(E["L"], [0.0, 0.0, 2 * 2 * (-0.5)], atol=1e-15)
+
+
+@pytest.mark.slow
+def test_plummer_leapfrog_energy_drift():
+    """100 KDK steps, dt = 1e-3, eps = 0.01 on a Plummer sphere: |dE/E| <= 1e-5."""
+    w = ics.plummer(1024, seed=5)
+    f = lambda x: oracle.direct(x, w.mass, 0.01)[0]
+    a0, p0 = oracle.direct(w.pos, w.mass, 0.01)
+    E0 = oracle.energy(w.pos, w.vel, w.mass, p0)["etot"]
+    pos, vel, _ = oracle.kdk(w.pos, w.vel, a0, 1e-3, f, 100)
+    _, p1 = oracle.direct(pos, w.mass, 0.01)
+    E1 = oracle.energy(pos, vel, w.mass, p1)["etot"]
+    assert abs(E1 / E0 - 1) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# keys and sort
+# ---------------------------------------------------------------------------
+def _read_golden_keys():
+    pts, kk = [], []
+    for line in open(os.path.join(GOLDEN, "morton_keys.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        a = line.split()
+        pts.append([float(v) for v in a[:3]])
+        kk.append(int(a[3]))
+    return np.array(pts, dtype=np.float32).T, np.array(kk, dtype=np.uint64)
+
+
+def test_keys_golden():
+    pos, expect = _read_golden_keys()
+    np.testing.assert_array_equal(oracle.keys(pos), expect)
+
+
+def _deinterleave(k):
+    k = int(k)
+    q = [0, 0, 0]
+    for b in range(21):
+        for a in range(3):
+            q[a] |= ((k >> (3 * b + a)) & 1) << b
+    return q
+
+
+def test_keys_quantisation_properties():
+    """Each axis code lies within one grid unit of (x - min) 2^21 / L, codes
+    are in range, and code order follows coordinate order."""
+    w = ics.hernquist(2000, seed=3)
+    p32 = w.pos.astype(np.float32)
+    k = oracle.keys(p32)
+    lo, L, s = oracle.bounds(p32)
+    assert L == max(float(p32[a].max()) - float(p32[a].min()) for a in range(3))
+    q = np.array([_deinterleave(v) for v in k]).T
+    assert q.min() >= 0 and q.max() <= 2 ** 21 - 1
+    exact = (p32.astype(np.float64) - lo[:, None]) * (2 ** 21 / L)
+    assert np.all(q <= exact + 1e-6) and np.all(q >= np.minimum(exact, 2 ** 21 - 1) - 1 - 1e-6)
+    for a in range(3):
+        o = np.argsort(p32[a], kind="stable")
+        assert np.all(np.diff(q[a][o]) >= 0)
+
+
+def test_sort_matches_library_stable_sort():
+    g = ics.rng(7)
+    key = g.integers(0, 50, 3000).astype(np.uint64)         # many ties
+    sk, perm = oracle.stable_sort(key)
+    ref = np.argsort(key, kind="stable")
+    np.testing.assert_array_equal(perm, ref)
+    np.testing.assert_array_equal(sk, key[ref])
+
+
+# ---------------------------------------------------------------------------
+# tree
+# ---------------------------------------------------------------------------
+def _read_sections(name):
+    sec, out = None, {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("["):
+            sec = line.strip("[]")
+            out[sec] = []
+            continue
+        out[sec].append([float(v) if sec == "points" else int(v) for v in line.split()])
+    return out
+
+
+def test_tiny_tree_golden():
+    g = _read_sections("tiny_tree.txt")
+    pos = np.array(g["points"], dtype=np.float32).T
+    T = oracle.Tree(pos, np.ones(pos.shape[1], np.float32), n_leaf=2, group=2)
+    np.testing.assert_array_equal(T.perm, np.array(g["perm"][0]))
+    np.testing.assert_array_equal(T.cells, np.array(g["cells"]))
+    np.testing.assert_array_equal(T.groups, np.array(g["groups"]))
+
+
+def _check_tree_invariants(T, n_leaf, G):
+    cells = T.cells
+    n = T.n
+    lev, first, cnt, child, nch, par = (cells[:, i] for i in range(6))
+    # breadth-first order
+    order = np.lexsort((first, lev))
+    np.testing.assert_array_equal(order, np.arange(T.ncell))
+    assert cnt[0] == n and first[0] == 0 and lev[0] == 0
+    leaf_cover = np.zeros(n, dtype=np.int64)
+    q = np.array([_deinterleave(k) for k in T.key]).T if n <= 5000 else None
+    for c in range(T.ncell):
+        if nch[c] == 0:
+            assert cnt[c] <= n_leaf or lev[c] == 21
+            leaf_cover[first[c]:first[c] + cnt[c]] += 1
+        else:
+            assert cnt[c] > n_leaf and lev[c] < 21
+            kids = np.arange(child[c], child[c] + nch[c])
+            assert np.all(par[kids] == c) and np.all(lev[kids] == lev[c] + 1)
+            assert first[kids[0]] == first[c]
+            assert np.all(first[kids][1:] == (first[kids] + cnt[kids])[:-1])
+            assert first[kids[-1]] + cnt[kids[-1]] == first[c] + cnt[c]
+        if q is not None:
+            s = 1 << (21 - lev[c])
+            sl = slice(first[c], first[c] + cnt[c])
+            for a in range(3):
+                o = cells[c, 6 + a]
+                assert np.all((q[a][sl] >= o) & (q[a][sl] < o + s))
+    assert np.all(leaf_cover == 1)
+    # groups partition the particles, each <= G
+    gs = T.groups[np.argsort(T.groups[:, 0])]
+    assert gs[0, 0] == 0 and np.all(gs[1:, 0] == gs[:-1, 0] + gs[:-1, 1]) and gs[-1, 0] + gs[-1, 1] == n
+    assert gs[:, 1].max() <= G
+    for f, k, c in gs:
+        assert first[c] <= f and f + k <= first[c] + cnt[c]
+
+
+@pytest.mark.parametrize("n,n_leaf,G", [(1, 16, 32), (2, 1, 1), (33, 16, 32), (1000, 8, 32), (3000, 16, 64)])
+def test_tree_invariants(n, n_leaf, G):
+    w = ics.hernquist(n, seed=n)
+    T = oracle.Tree(w.pos.astype(np.float32), w.mass.astype(np.float32), n_leaf, G)
+    _check_tree_invariants(T, n_leaf, G)
+
+
+def test_tree_coincident_particles():
+    """All particles at one point: one chain of single-child cells down to an
+    overflow leaf at level 21, cut into groups of G."""
+    pos = np.full((3, 100), 0.25, dtype=np.float32)
+    T = oracle.Tree(pos, np.ones(100, np.float32), 16, 32)
+    assert T.ncell == 22 and T.cells[-1, 0] == 21 and T.cells[-1, 2] == 100
+    assert list(T.groups[:, 1]) == [32, 32, 32, 4]
+
+
+def test_moments_two_point_closed_form():
+    """Two masses m at +-d on x about the origin: COM 0, Q_xx = 4 m d^2,
+    Q_yy = Q_zz = -2 m d^2, no off-diagonal terms."""
+    d = 0.25
+    pos = np.array([[-d, d], [0.0, 0.0], [0.0, 0.0]], dtype=np.float32)
+    T = oracle.Tree(pos, np.array([3.0, 3.0], np.float32), 16, 32)
+    mo = T.moments[0]
+    np.testing.assert_allclose(mo[:4], [6.0, 0.0, 0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(mo[4:], [4 * 3 * d * d, -2 * 3 * d * d, -2 * 3 * d * d, 0, 0, 0], atol=1e-15)
+
+
+def test_moments_far_field_convergence():
+    """Multipole field of a cell vs brute-force direct sum of its particles:
+    the monopole error falls as (s/r)^2 relative, the quadrupole one as (s/r)^3,
+    and adding the quadrupole term reduces the error."""
+    g = ics.rng(9)
+    pts = g.uniform(-0.5, 0.5, (3, 40))
+    m = g.uniform(0.5, 1.5, 40)
+    pos = pts.astype(np.float32)
+    T = oracle.Tree(pos, m.astype(np.float32), 64, 64)       # one leaf = the root
+    M = T.moments[0]
+    errs = {}
+    for quad in (False, True):
+        for R in (8.0, 16.0):
+            tgt = np.array([[R], [0.3 * R], [-0.2 * R]])
+            exact, _ = oracle.direct(np.concatenate([pos.astype(np.float64), tgt], 1),
+                                     np.concatenate([m.astype(np.float32).astype(np.float64), [0.0]]), 0.0,
+                                     targets=[40])
+            r = tgt[:, 0] - M[1:4]
+            rr = np.linalg.norm(r)
+            a = -M[0] * r / rr ** 3
+            if quad:
+                Q = np.array([[M[4], M[7], M[8]], [M[7], M[5], M[9]], [M[8], M[9], M[6]]])
+                Qr = Q @ r
+                a = a + Qr / rr ** 5 - 2.5 * (r @ Qr) * r / rr ** 7
+            errs[(quad, R)] = np.linalg.norm(a - exact[:, 0]) / np.linalg.norm(exact[:, 0])
+    assert errs[(True, 8.0)] < errs[(False, 8.0)]
+    assert 2.6 < errs[(False, 8.0)] / errs[(False, 16.0)] < 5.5     # ~ 2^2
+    assert 5.0 < errs[(True, 8.0)] / errs[(True, 16.0)] < 11.0      # ~ 2^3
+    assert abs(M[4] + M[5] + M[6]) < 1e-12 * abs(M[4:7]).max()       # traceless
+
+
+# ---------------------------------------------------------------------------
+# walk
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def plummer_case():
+    w = ics.plummer_workload()
+    p32 = w.stars.pos.astype(np.float32)
+    m32 = w.stars.mass.astype(np.float32)
+    ad, pd = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), 0.01)
+    return p32, m32, ad, pd
+
+
+def test_walk_small_theta_equals_direct(plummer_case):
+    p32, m32, ad, pd = plummer_case
+    T = oracle.Tree(p32, m32, 16, 32)
+    a, p, _, _ = T.forces(1e-6, 0.01)
+    assert oracle.rel_err(a, ad).max() < 1e-12
+    np.testing.assert_allclose(p, pd, rtol=1e-12)
+
+
+def test_walk_accuracy_ordering(plummer_case):
+    """p99 vs direct <= 1e-3 at theta = 0.5 with quadrupoles; error grows with
+    theta and is larger without the quadrupole term."""
+    p32, m32, ad, _ = plummer_case
+    T = oracle.Tree(p32, m32, 16, 32)
+    p99 = {}
+    for th in (0.3, 0.5, 0.7):
+        for q in (False, True):
+            a, _, _, _ = T.forces(th, 0.01, q)
+            p99[(th, q)] = oracle.percentile(oracle.rel_err(a, ad), 0.99)
+    assert p99[(0.5, True)] <= 1e-3
+    assert p99[(0.3, True)] < p99[(0.5, True)] < p99[(0.7, True)]
+    for th in (0.3, 0.5, 0.7):
+        assert p99[(th, True)] < p99[(th, False)]
+
+
+def test_walk_extra_particles_match_direct(plummer_case):
+    """An unsoftened centre-of-mass particle outside the tree: at small theta
+    the stars' forces and its own equal the direct sum with eps = 0 pairs."""
+    p32, m32, _, _ = plummer_case
+    xpos = np.array([[0.3], [-0.1], [0.05]], dtype=np.float32)
+    xm = np.array([0.01])
+    T = oracle.Tree(p32, m32, 16, 32)
+    a, p, xa, xp = T.forces(1e-6, 0.01, True, xpos, xm, [0.0])
+    allpos = np.concatenate([p32, xpos], 1).astype(np.float64)
+    allm = np.concatenate([m32.astype(np.float64), xm])
+    eps = np.concatenate([np.full(p32.shape[1], 0.01), [0.0]])
+    ad, pd = oracle.direct(allpos, allm, eps)
+    assert oracle.rel_err(a, ad[:, :-1]).max() < 1e-12
+    assert oracle.rel_err(xa, ad[:, -1:]).max() < 1e-12
+    np.testing.assert_allclose(xp, pd[-1:], rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# chain / perturbers (Sect. 2, Eq. 3)
+# ---------------------------------------------------------------------------
+def test_perturber_single_member_closed_form():
+    cm = np.array([0.005])
+    cx = np.array([[0.1, 0.0, 0.0]])
+    pm = np.array([1e-3, 2e-3])
+    px = np.array([[0.1, 0.02, 0.0], [0.1, 0.0, -0.04]])
+    r = oracle.perturber(cm, cx, pm, px)
+    np.testing.assert_allclose(r["a_pert"], 0.0, atol=1e-18)       # resolved == CoM for one member
+    expect = 1e-3 * np.array([0, 0.02, 0]) / 0.02 ** 3 + 2e-3 * np.array([0, 0, -0.04]) / 0.04 ** 3
+    np.testing.assert_allclose(r["a_chain"][0], expect, rtol=1e-14)
+    np.testing.assert_allclose(r["corr"], expect, rtol=1e-14)
+    np.testing.assert_allclose(r["sub"], expect, rtol=1e-14)
+
+
+def test_perturber_binary_newton_third_law():
+    """sum_k m_k a_chain[k] (perturbers on members) balances the resolved
+    members' pull on the perturbers; Eq. 3 gives M_chain corr = sum m_k a_k."""
+    b = ics.central_binary()
+    g = ics.rng(3)
+    px = g.normal(0, 0.02, (50, 3))
+    pm = np.full(50, 1e-5)
+    r = oracle.perturber(b.mass, b.pos, pm, px)
+    resolved_on_p = r["a_pert"].copy()
+    M = b.mass.sum()
+    com = b.com
+    for p in range(50):
+        d = com - px[p]
+        resolved_on_p[p] += M * d / np.linalg.norm(d) ** 3
+    f_members = (b.mass[:, None] * r["a_chain"]).sum(0)
+    f_perts = (pm[:, None] * resolved_on_p).sum(0)
+    np.testing.assert_allclose(f_members, -f_perts, rtol=1e-12, atol=1e-12 * np.abs(f_members).max())
+    np.testing.assert_allclose(M * r["corr"], f_members, rtol=1e-13)
+
+
+def test_knn_and_radius_selection():
+    w = ics.hernquist(3000, seed=21)
+    p32 = w.pos.astype(np.float32)
+    c = np.array([0.01, -0.02, 0.0], dtype=np.float32)
+    d = p32 - c[:, None]
+    d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+    assert d2.dtype == np.float32
+    sel = oracle.knn(p32, c, 64)
+    ref = np.lexsort((np.arange(3000), d2))[:64]
+    np.testing.assert_array_equal(sel, ref)
+    r2 = np.float32(0.3 * 0.3)
+    rs = oracle.radius(p32, c, r2)
+    np.testing.assert_array_equal(rs, np.nonzero(d2 < r2)[0])
