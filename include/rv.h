@@ -1,0 +1,220 @@
+/*
+ * rv.h -- C ABI of librv, the GB300 (sm_103a) tree-gravity library.
+ *
+ * librv computes the data-parallel part of a regularised tree code's force
+ * step (Karl et al., "introducing the regularized tree code rVINE"):
+ *   - softened Barnes-Hut tree forces on the field stars (Sect. 2: forces of
+ *     most particles from the tree with Plummer softening; Sect. 1: multipole
+ *     expansion of a distant group about its centre of mass; Sect. 3: Plummer
+ *     softening, G = 1) built from Morton keys, a radix sort and an octree
+ *     with monopole and quadrupole moments, walked under an opening-angle
+ *     test;
+ *   - the unsoftened FP64 couplings between a regularised chain and its
+ *     perturbers (Sect. 2, Eq. 3 and the text around it);
+ *   - a kick-drift-kick step and FP64 energy/momentum totals.
+ * The chain's own regularised integrator is not part of this library.
+ *
+ * Conventions (every entry point):
+ *   - Pointers marked "device" are CUDA device addresses owned by the caller;
+ *     librv never frees them. "host" pointers are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream). All
+ *     device work is enqueued asynchronously on it; a call returns once the
+ *     work is enqueued, except where a function says it synchronises.
+ *   - Arrays of stars are in the caller's order; internal sorting never
+ *     leaks out. Star data are FP32; chain data are FP64.
+ *   - Errors are returned as rv_status and never abort or trap. Errors found
+ *     by a kernel (a full walk stack, a tree larger than the workspace) are
+ *     latched in device memory and reported by rv_sync_status().
+ *   - Not thread safe per context; distinct contexts are independent.
+ */
+#ifndef RV_H
+#define RV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RV_OK = 0,
+    RV_E_INVAL = 1,     /* bad argument (null pointer, size out of range, bad config) */
+    RV_E_CUDA = 2,      /* a CUDA runtime call failed; rv_last_error() has the text */
+    RV_E_WORKSPACE = 3, /* workspace missing, too small, or the tree outgrew it */
+    RV_E_STACK = 4,     /* a walk's traversal stack filled up (results invalid) */
+    RV_E_TIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    RV_E_NOTBUILT = 6   /* forces asked before rv_build_tree */
+} rv_status;
+
+typedef struct rv_ctx rv_ctx; /* opaque; owned by librv */
+
+/* Tree parameters.
+ *   theta      opening angle: a cell of side s is used as a multipole for a
+ *              walk group when s < theta * d, d the distance between the
+ *              group's box and the cell's box (0 <= theta < 2).
+ *   eps_star   Plummer softening length of the stars (>= 0).
+ *   n_leaf     a cell with more than n_leaf stars is split (1..64).
+ *   group      stars per walk group, at most 32 (one warp lane each).
+ *   quadrupole 1: monopole + traceless quadrupole; 0: monopole only.
+ *   tile       interaction-list tile, a multiple of 32 in [32, 256]. */
+typedef struct {
+    float theta;
+    float eps_star;
+    int32_t n_leaf;
+    int32_t group;
+    int32_t quadrupole;
+    int32_t tile;
+} rv_config;
+
+/* Fills *cfg with the defaults: theta 0.5, eps 0.01, n_leaf 16, group 32,
+ * quadrupole 1, tile 64. */
+void rv_default_config(rv_config *cfg);
+
+/* Bytes of device workspace a context needs for up to n_max stars (0 if the
+ * config is invalid). */
+size_t rv_workspace_size(int64_t n_max, const rv_config *cfg);
+
+/* Creates a context for up to n_max stars on the current CUDA device.
+ * Allocates only small host state; device memory comes from
+ * rv_set_workspace. Returns RV_E_INVAL for a bad config or n_max < 0. */
+rv_status rv_create(rv_ctx **out, int64_t n_max, const rv_config *cfg);
+void rv_destroy(rv_ctx *ctx);
+
+/* Hands librv `bytes` of caller-owned device memory (256-byte aligned), at
+ * least rv_workspace_size(). Must stay valid until rv_destroy or the next
+ * rv_set_workspace. RV_E_WORKSPACE if too small or misaligned. */
+rv_status rv_set_workspace(rv_ctx *ctx, void *dev, size_t bytes);
+
+/* Builds the octree of n stars (device FP32 arrays x, y, z, m; n <= n_max).
+ * Steps: bounding cube; 63-bit Morton keys q_a = min(floor((x_a - min_a)
+ * 2^21 / L), 2^21 - 1) interleaved x, y, z from bit 0; stable radix sort;
+ * gather of (x, y, z, m) in key order; cells = key prefixes split while they
+ * hold more than n_leaf stars (down to level 21), breadth-first; per cell the
+ * mass, centre of mass and traceless quadrupole about it (Sect. 1); walk
+ * groups. Inputs are read during the call's stream work only. */
+rv_status rv_build_tree(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
+                        const float *m, void *stream);
+
+/* Tree forces on all stars of the last build (G = 1, Sect. 3):
+ *   a_i = sum_j m_j r_ij / (r_ij^2 + eps^2)^{3/2},  phi_i = -sum_j m_j (r^2+eps^2)^{-1/2}
+ * over the other stars, with distant cells replaced by their multipoles
+ * under the opening test at `theta`, evaluated in FP32 with positions taken
+ * relative to the target and compensated (Neumaier) accumulation per tile.
+ * Outputs ax, ay, az, pot (device FP32 [n], caller order) are overwritten.
+ *
+ * n_extra (0..8) particles outside the tree -- a chain's centre-of-mass
+ * particle (Sect. 2) -- are given as device FP32 xyzm[4 n_extra] and
+ * eps[n_extra] (0 = unsoftened; pair softening max(eps_i, eps_j), 0 if either
+ * is 0). They act on every star directly and feel the tree through their own
+ * walk; their acceleration and potential go to device extra_out[4 n_extra]
+ * (ax, ay, az, pot). extra pointers may be NULL when n_extra = 0. */
+rv_status rv_tree_forces(rv_ctx *ctx, float theta, float eps_star, int32_t n_extra,
+                         const float *extra_xyzm, const float *extra_eps, float *ax, float *ay,
+                         float *az, float *pot, float *extra_out, void *stream);
+
+/* Unsoftened FP64 chain/perturber coupling (Sect. 2, Eq. 3). Chain members k
+ * (n_ch <= 250; device chain_m[n_ch], chain_x[3 n_ch]) with centre of mass
+ * c and mass M; perturbers p (n_pert <= 5000; device FP64 pert_m[n_pert],
+ * pert_x[3 n_pert]). Device FP64 outputs:
+ *   a_pert[3p..], pot_pert[p]:  sum_k m_k f(x_k - x_p) - M f(c - x_p)
+ *                               (resolved chain replaces the centre of mass);
+ *   a_chain[3k..], pot_chain[k]: sum_p m_p f(x_p - x_k) (perturbers on members);
+ *   out8[0..3]  corr = (1/M) sum_k m_k a_chain[k]   (Eq. 3),
+ *   out8[3..6]  sub  = sum_p m_p f(x_p - c), the perturbers' direct terms on
+ *               the centre-of-mass particle that the tree force contains,
+ *   out8[6]     sum_k m_k pot_chain[k] / M, out8[7] = sum_p -m_p / |x_p - c|,
+ *   out8[8..11] c, out8[11] M   (out8 holds 12 doubles).
+ * f(r) = r / |r|^3; potentials are -m/|r|. Sums run in a fixed order.
+ * n_pert may be 0 (then a_pert/pot_pert/pert_* may be NULL). */
+rv_status rv_perturber_forces(rv_ctx *ctx, int32_t n_ch, const double *chain_m, const double *chain_x,
+                              int32_t n_pert, const double *pert_m, const double *pert_x, double *a_pert,
+                              double *pot_pert, double *a_chain, double *pot_chain, double *out8,
+                              void *stream);
+
+/* A system advanced by rv_kdk_step: n stars (device FP32, caller order) and
+ * at most one chain of n_chain members (device FP64; 0 = no chain).
+ * Perturbers of the chain: pert_mode 1 = stars with FP32 squared distance to
+ * the chain centre below pert_radius^2 (ascending index), 2 = the pert_k
+ * nearest stars (ties by lower index); at most 5000. */
+typedef struct {
+    int64_t n;
+    float *x, *y, *z, *vx, *vy, *vz;
+    const float *m;
+    float *ax, *ay, *az, *pot; /* forces at the current positions */
+    int32_t n_chain;
+    double *chain_m, *chain_x, *chain_v, *chain_a, *chain_pot; /* [n], [3n], [3n], [3n], [n] */
+    int32_t pert_mode;
+    float pert_radius;
+    int32_t pert_k;
+} rv_system;
+
+/* One full force evaluation of a system: tree build, perturber selection,
+ * tree forces with the chain's centre of mass as an unsoftened extra
+ * particle, FP64 perturber coupling, and the hand-off of the chain (member
+ * accelerations = mutual unsoftened FP64 + perturbers + tree force on the
+ * centre of mass minus the perturbers' direct terms, Sect. 2). Writes
+ * sys->ax..pot and chain_a, chain_pot. */
+rv_status rv_system_forces(rv_ctx *ctx, rv_system *sys, void *stream);
+
+/* nsteps kick-drift-kick steps of size dt (global step): v += a dt/2;
+ * x += v dt; rv_system_forces; v += a dt/2. Stars in FP32, chain members in
+ * FP64. sys->a* must hold the forces at the starting positions (call
+ * rv_system_forces once first). */
+rv_status rv_kdk_step(rv_ctx *ctx, rv_system *sys, double dt, int32_t nsteps, void *stream);
+
+/* FP64 totals of a system, written to device out[10]: E_kin, E_pot, E_tot,
+ * P (3), L (3), M. Stars: sum m v^2/2, sum m phi/2, sum m v, sum m x cross v;
+ * chain members added in FP64 with their potential chain_pot. Deterministic
+ * (fixed reduction order). */
+rv_status rv_energy(rv_ctx *ctx, const rv_system *sys, double *out, void *stream);
+
+/* Perturber selection on its own (see rv_system): writes ascending indices
+ * to device idx[cap] and the count to device count[1]. mode 1 radius, 2 k
+ * nearest. centre is a host FP32 point. A radius selection longer than cap
+ * is truncated and reported as RV_E_WORKSPACE by rv_sync_status. */
+rv_status rv_select_perturbers(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
+                               const float centre[3], int32_t mode, float radius, int32_t k, int32_t cap,
+                               int32_t *idx, int32_t *count, void *stream);
+
+/* Read-only views of the last tree (device pointers into the workspace,
+ * valid until the next build). Synchronises `stream` to read the sizes.
+ *   keys    uint64 [n] sorted keys;     perm int32 [n] sorted slot -> caller index
+ *   pos     float4 [n] sorted (x, y, z, m)
+ *   cbox    int4 [ncell] (ox, oy, oz, level) integer-grid box origin, side 2^(21-level)
+ *   clink   int4 [ncell] (child first, n children, first star, star count)
+ *   cmom    float4 [3 ncell] (M, com x, y, z), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0)
+ *   cparent int32 [ncell]
+ *   groups  int4 [ngroup] (first star, count, box cell, 0)
+ *   bounds  double [5] (min x, y, z, L, 2^21/L) */
+typedef struct {
+    int64_t n, ncell, ngroup;
+    const uint64_t *keys;
+    const int32_t *perm;
+    const float *pos;
+    const int32_t *cbox, *clink;
+    const float *cmom;
+    const int32_t *cparent, *groups;
+    const double *bounds;
+} rv_tree_view;
+rv_status rv_get_tree(rv_ctx *ctx, rv_tree_view *out, void *stream);
+
+/* Interaction counts of the last rv_tree_forces (synchronises `stream`):
+ * out[0] = P2P pairs, out[1] = multipole (M2P) pairs, over all targets. */
+rv_status rv_walk_stats(rv_ctx *ctx, int64_t out[2], void *stream);
+
+/* Synchronises `stream` and returns the first error latched by a kernel since
+ * the last call (and clears it), else RV_OK. */
+rv_status rv_sync_status(rv_ctx *ctx, void *stream);
+
+/* Number of kernels librv has launched through this context since it was
+ * created (host-side count, incremented at each launch). */
+int64_t rv_launch_count(const rv_ctx *ctx);
+
+/* Text of the last error on this context ("" if none). Never NULL. */
+const char *rv_last_error(const rv_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RV_H */

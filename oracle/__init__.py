@@ -69,8 +69,8 @@ def _declare(L):
     L.orc_tree_moments.argtypes = [C.c_void_p, _d]
     L.orc_tree_groups.argtypes = [C.c_void_p, _i64]
     L.orc_tree_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32,
-                                  _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64]
-    L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d]
+                                  _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64, C.c_int64, _i64]
+    L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d, _d]
     L.orc_knn.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_int64, _i64]
     L.orc_knn.restype = C.c_int64
     L.orc_radius.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_float, C.c_int64, _i64]
@@ -182,14 +182,16 @@ class Tree:
             self._h = None
 
     def forces(self, theta: float, eps_star: float, quadrupole: bool = True,
-               extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False):
+               extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False, targets=None):
         """Tree acceleration/potential on every star (caller order), FP64.
 
         Walk under the box-box opening-angle test at ``theta``; ``extra_*``
         are particles outside the tree (chain centres of mass; eps 0 =
         unsoftened) that act on the stars and each other directly and feel the
         tree through their own walk. Returns (acc (3,n), pot (n,), xacc (3,k),
-        xpot (k,)[, counts (n,2) = P2P, M2P interactions])."""
+        xpot (k,)[, counts (n,2) = P2P, M2P interactions]). With ``targets``
+        (caller indices) only those stars are computed; the rest of the
+        returned arrays is zero."""
         k = 0 if extra_mass is None else int(np.asarray(extra_mass).shape[0])
         ex = np.zeros((3, max(k, 1)), dtype=np.float32)
         xm = np.zeros(max(k, 1))
@@ -205,7 +207,9 @@ class Tree:
         lib().orc_tree_forces(self._h, float(np.float32(theta)), float(eps_star), int(quadrupole), k,
                               _p(exx, _f), _p(exy, _f), _p(exz, _f), _p(xm, _d), _p(xe, _d),
                               *[_p(o, _d) for o in out], *[_p(o, _d) for o in xout],
-                              _p(cnt, _i64) if counts else None)
+                              _p(cnt, _i64) if counts else None,
+                              -1 if targets is None else len(targets),
+                              None if targets is None else _p(_c(targets, np.int64), _i64))
         res = (np.stack(out[:3]), out[3], np.stack(xout[:3])[:, :k], xout[3][:k])
         return res + (cnt,) if counts else res
 
@@ -215,22 +219,26 @@ class Tree:
 # ---------------------------------------------------------------------------
 def perturber(chain_mass, chain_pos, pert_mass, pert_pos):
     """Unsoftened FP64 couplings of a chain (k members, pos (k,3)) and its
-    perturbers (p, pos (p,3)). Returns dict with a_pert (p,3), a_chain (k,3),
-    corr (3,) = Eq. 3 correction, sub (3,) = perturbers' direct terms on the
-    centre-of-mass particle."""
+    perturbers (p, pos (p,3)), Sect. 2 and Eq. 3. Returns dict with a_pert
+    (p,3), pot_pert (p,), a_chain (k,3), pot_chain (k,), corr (3,) = Eq. 3
+    correction, sub (3,) = perturbers' direct terms on the centre-of-mass
+    particle, corr_pot, sub_pot, com (3,), M."""
     cm = _c(chain_mass, np.float64)
     cx = _c(chain_pos, np.float64).reshape(-1)
     pm = _c(pert_mass, np.float64)
     px = _c(pert_pos, np.float64).reshape(-1)
     nch, npt = cm.shape[0], pm.shape[0]
     ap = np.zeros(3 * max(npt, 1))
+    pp = np.zeros(max(npt, 1))
     ac = np.zeros(3 * max(nch, 1))
-    corr = np.zeros(3)
-    sub = np.zeros(3)
-    lib().orc_perturber(nch, _p(cm, _d), _p(cx, _d), npt, _p(pm, _d), _p(px, _d), _p(ap, _d), _p(ac, _d),
-                        _p(corr, _d), _p(sub, _d))
-    return {"a_pert": ap[:3 * npt].reshape(npt, 3), "a_chain": ac[:3 * nch].reshape(nch, 3),
-            "corr": corr, "sub": sub}
+    pc = np.zeros(max(nch, 1))
+    out = np.zeros(12)
+    lib().orc_perturber(nch, _p(cm, _d), _p(cx, _d), npt, _p(pm, _d), _p(px, _d), _p(ap, _d), _p(pp, _d),
+                        _p(ac, _d), _p(pc, _d), _p(out, _d))
+    return {"a_pert": ap[:3 * npt].reshape(npt, 3), "pot_pert": pp[:npt],
+            "a_chain": ac[:3 * nch].reshape(nch, 3), "pot_chain": pc[:nch],
+            "corr": out[0:3].copy(), "sub": out[3:6].copy(), "corr_pot": float(out[6]),
+            "sub_pot": float(out[7]), "com": out[8:11].copy(), "M": float(out[11])}
 
 
 def knn(pos32, centre32, k):

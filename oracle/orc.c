@@ -484,18 +484,27 @@ static void box_of_cell(const orc_tree *t, int64_t c, int64_t lo[3], int64_t hi[
  * pair rule, and each feels the tree through its own walk whose group box is
  * the grid cell [q, q+1)^3 of its position (q unclamped, limited to
  * +-2^23). counts (optional, [n][2]) receives the P2P and M2P interaction
- * counts per tree particle. */
+ * counts per tree particle. With nsub >= 0 only the stars whose caller
+ * indices are listed in sub[0..nsub) are computed (others untouched). */
 void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t quad,
                      int32_t nx, const float *xx, const float *xy, const float *xz, const double *xm,
                      const double *xeps,
                      double *ax, double *ay, double *az, double *pot,
-                     double *xax, double *xay, double *xaz, double *xpot, int64_t *counts) {
+                     double *xax, double *xay, double *xaz, double *xpot, int64_t *counts,
+                     int64_t nsub, const int64_t *sub) {
     double theta2 = theta * theta;
+    /* optional subset: only sorted slots whose caller index is flagged */
+    char *want = NULL;
+    if (nsub >= 0) {
+        want = (char *)calloc((size_t)(t->n > 0 ? t->n : 1), 1);
+        for (int64_t s = 0; s < nsub; s++) want[sub[s]] = 1;
+    }
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < t->ngroup; g++) {
         int64_t blo[3], bhi[3];
         box_of_cell(t, t->gcell[g], blo, bhi);
         for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
+            if (want && !want[t->perm[i]]) continue;
             walk_state w;
             memset(&w, 0, sizeof w);
             w.t = t; w.theta2 = theta2; w.quad = quad; w.e = eps_star; w.self = i;
@@ -509,11 +518,12 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
             if (counts) { counts[2 * o] = w.n_p2p; counts[2 * o + 1] = w.n_m2p; }
         }
     }
+    free(want);
     for (int32_t k = 0; k < nx; k++) {
         walk_state w;
         memset(&w, 0, sizeof w);
         w.t = t; w.theta2 = theta2; w.quad = quad; w.self = -1;
-        w.e = (xeps[k] == 0.0) ? 0.0 : (xeps[k] > eps_star ? xeps[k] : eps_star);
+        w.e = pair_eps(xeps[k], eps_star);
         w.px = xx[k]; w.py = xy[k]; w.pz = xz[k];
         const float pv[3] = {xx[k], xy[k], xz[k]};
         for (int a = 0; a < 3; a++) {
@@ -534,26 +544,30 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
 /* ------------------------------------------------------------------ */
 /* 6. Chain / perturber coupling, unsoftened FP64 (Sect. 2, Eq. 3)      */
 /* ------------------------------------------------------------------ */
-/* f(r) = r / |r|^3 (unsoftened); zero separation contributes nothing. */
-static void kepler_acc(double rx, double ry, double rz, double m, double out[3]) {
+/* f(r) = r / |r|^3 and the potential -m / |r| (unsoftened). */
+static void kepler_pot(double rx, double ry, double rz, double m, double out[4]) {
     double r2 = rx * rx + ry * ry + rz * rz;
-    if (r2 <= 0.0) { out[0] = out[1] = out[2] = 0.0; return; }
+    if (r2 <= 0.0) { out[0] = out[1] = out[2] = out[3] = 0.0; return; }
     double rinv = 1.0 / sqrt(r2);
     double s = m * rinv * rinv * rinv;
-    out[0] = s * rx; out[1] = s * ry; out[2] = s * rz;
+    out[0] = s * rx; out[1] = s * ry; out[2] = s * rz; out[3] = -m * rinv;
 }
 
 /* Chain members k (mass cm[k], position cx[3k..]) and perturbers p (mass pm[p],
- * position px[3p..]) with the chain centre of mass com[3] and total mass
- * M = sum cm:
- *   a_pert[p]  = sum_k cm_k f(x_k - x_p) - M f(com - x_p)
- *                (resolved chain replaces the centre-of-mass particle);
- *   a_chain[k] = sum_p pm_p f(x_p - x_k)   (perturbers on each member);
- *   corr       = (1/M) sum_k cm_k a_chain[k]  (Eq. 3);
- *   sub        = sum_p pm_p f(x_p - com)   (the direct, unsoftened tree terms of
- *                the perturbers on the centre-of-mass particle, to subtract). */
+ * position px[3p..]) with the chain centre of mass com and total mass
+ * M = sum cm (Sect. 2: perturbers feel the resolved members; members feel
+ * the perturbers; the centre-of-mass particle's force is corrected, Eq. 3):
+ *   a_pert[p], pot_pert[p]   = sum_k cm_k f(x_k - x_p) - M f(com - x_p)
+ *                              (resolved chain replaces the centre-of-mass particle);
+ *   a_chain[k], pot_chain[k] = sum_p pm_p f(x_p - x_k)   (perturbers on each member);
+ *   out[0..3) corr = (1/M) sum_k cm_k a_chain[k]  (Eq. 3);
+ *   out[3..6) sub  = sum_p pm_p f(x_p - com), the direct unsoftened terms of the
+ *                perturbers on the centre-of-mass particle, to subtract;
+ *   out[6] = (1/M) sum_k cm_k pot_chain[k], out[7] = potential of sub;
+ *   out[8..11) com, out[11] M. */
 void orc_perturber(int32_t nch, const double *cm, const double *cx, int32_t np, const double *pm,
-                   const double *px, double *a_pert, double *a_chain, double corr[3], double sub[3]) {
+                   const double *px, double *a_pert, double *pot_pert, double *a_chain, double *pot_chain,
+                   double out[12]) {
     double M = 0, com[3] = {0, 0, 0};
     for (int32_t k = 0; k < nch; k++) {
         M += cm[k];
@@ -562,35 +576,40 @@ void orc_perturber(int32_t nch, const double *cm, const double *cx, int32_t np, 
     for (int a = 0; a < 3; a++) com[a] = (M > 0) ? com[a] / M : 0.0;
 #pragma omp parallel for schedule(static)
     for (int32_t p = 0; p < np; p++) {
-        nsum s[3] = {{0, 0}, {0, 0}, {0, 0}};
-        double f[3];
+        nsum s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        double f[4];
         for (int32_t k = 0; k < nch; k++) {
-            kepler_acc(cx[3 * k] - px[3 * p], cx[3 * k + 1] - px[3 * p + 1], cx[3 * k + 2] - px[3 * p + 2], cm[k], f);
-            for (int a = 0; a < 3; a++) nadd(&s[a], f[a]);
+            kepler_pot(cx[3 * k] - px[3 * p], cx[3 * k + 1] - px[3 * p + 1], cx[3 * k + 2] - px[3 * p + 2], cm[k], f);
+            for (int a = 0; a < 4; a++) nadd(&s[a], f[a]);
         }
-        kepler_acc(com[0] - px[3 * p], com[1] - px[3 * p + 1], com[2] - px[3 * p + 2], M, f);
-        for (int a = 0; a < 3; a++) { nadd(&s[a], -f[a]); a_pert[3 * p + a] = nval(&s[a]); }
+        kepler_pot(com[0] - px[3 * p], com[1] - px[3 * p + 1], com[2] - px[3 * p + 2], M, f);
+        for (int a = 0; a < 4; a++) nadd(&s[a], -f[a]);
+        for (int a = 0; a < 3; a++) a_pert[3 * p + a] = nval(&s[a]);
+        pot_pert[p] = nval(&s[3]);
     }
-    nsum cs[3] = {{0, 0}, {0, 0}, {0, 0}};
+    nsum cs[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int32_t k = 0; k < nch; k++) {
-        nsum s[3] = {{0, 0}, {0, 0}, {0, 0}};
-        double f[3];
+        nsum s[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        double f[4];
         for (int32_t p = 0; p < np; p++) {
-            kepler_acc(px[3 * p] - cx[3 * k], px[3 * p + 1] - cx[3 * k + 1], px[3 * p + 2] - cx[3 * k + 2], pm[p], f);
-            for (int a = 0; a < 3; a++) nadd(&s[a], f[a]);
+            kepler_pot(px[3 * p] - cx[3 * k], px[3 * p + 1] - cx[3 * k + 1], px[3 * p + 2] - cx[3 * k + 2], pm[p], f);
+            for (int a = 0; a < 4; a++) nadd(&s[a], f[a]);
         }
-        for (int a = 0; a < 3; a++) {
-            a_chain[3 * k + a] = nval(&s[a]);
-            nadd(&cs[a], cm[k] * a_chain[3 * k + a]);
-        }
+        for (int a = 0; a < 3; a++) a_chain[3 * k + a] = nval(&s[a]);
+        pot_chain[k] = nval(&s[3]);
+        for (int a = 0; a < 3; a++) nadd(&cs[a], cm[k] * a_chain[3 * k + a]);
+        nadd(&cs[3], cm[k] * pot_chain[k]);
     }
-    nsum ss[3] = {{0, 0}, {0, 0}, {0, 0}};
+    nsum ss[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     for (int32_t p = 0; p < np; p++) {
-        double f[3];
-        kepler_acc(px[3 * p] - com[0], px[3 * p + 1] - com[1], px[3 * p + 2] - com[2], pm[p], f);
-        for (int a = 0; a < 3; a++) nadd(&ss[a], f[a]);
+        double f[4];
+        kepler_pot(px[3 * p] - com[0], px[3 * p + 1] - com[1], px[3 * p + 2] - com[2], pm[p], f);
+        for (int a = 0; a < 4; a++) nadd(&ss[a], f[a]);
     }
-    for (int a = 0; a < 3; a++) { corr[a] = (M > 0) ? nval(&cs[a]) / M : 0.0; sub[a] = nval(&ss[a]); }
+    for (int a = 0; a < 3; a++) { out[a] = (M > 0) ? nval(&cs[a]) / M : 0.0; out[3 + a] = nval(&ss[a]); }
+    out[6] = (M > 0) ? nval(&cs[3]) / M : 0.0;
+    out[7] = nval(&ss[3]);
+    out[8] = com[0]; out[9] = com[1]; out[10] = com[2]; out[11] = M;
 }
 
 /* ------------------------------------------------------------------ */

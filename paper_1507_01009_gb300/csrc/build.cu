@@ -1,0 +1,692 @@
+// build.cu -- octree construction on the GPU: bounding cube, Morton keys,
+// stable LSD radix sort, gather into key order, topology, walk groups and
+// cell multipoles (monopole + traceless quadrupole about the centre of mass,
+// the expansion a tree code uses for distant groups, Sect. 1).
+//
+// Topology without per-level launches: for sorted keys, let D(j) be the first
+// level at which key[j-1] and key[j] differ (D(0) = D(n) = 0, 22 for equal
+// keys). At level l the key prefixes cut the sorted array at the positions
+// with D(j) <= l. A star i lies in a cell at level l iff every coarser cell
+// holding it has more than n_leaf stars, i.e. iff l <= lambda_i, the first
+// level whose segment around i holds at most n_leaf stars (capped at 21).
+// lambda_i only depends on D within n_leaf positions of i, so one pass over
+// a window finds it; cells starting at i are levels D(i)..lambda_i, and their
+// breadth-first index (level, first star) comes from per-level ballots and
+// one flat scan.
+#include <algorithm>
+
+#include "rv_internal.cuh"
+
+namespace rv {
+
+// ---------------------------------------------------------------------------
+// block helpers
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ int block_exclusive_scan(int v, int *smem_warp, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < NT / 32) ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) smem_warp[lane] = w;
+    }
+    __syncthreads();
+    int warp_base = (wid > 0) ? smem_warp[wid - 1] : 0;
+    total = smem_warp[NT / 32 - 1];
+    __syncthreads();
+    return warp_base + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 (in place), length *d_len (<= nmax) or nmax
+// ---------------------------------------------------------------------------
+__global__ void scan_reduce_k(const int *data, int64_t nmax, const int *d_len, int *partials) {
+    __shared__ int sw[8];
+    int64_t len = d_len ? min((int64_t)*d_len, nmax) : nmax;
+    int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    int sum = 0;
+    for (int i = threadIdx.x; i < kScanChunk; i += 256) {
+        int64_t j = base + i;
+        if (j < len) sum += data[j];
+    }
+    int total;
+    block_exclusive_scan<256>(sum, sw, total);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+__global__ void scan_partials_k(int *partials, int nb, int *d_total) {
+    __shared__ int sw[32];
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        int b = b0 + threadIdx.x;
+        int v = (b < nb) ? partials[b] : 0;
+        int total;
+        int ex = block_exclusive_scan<1024>(v, sw, total);
+        if (b < nb) partials[b] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
+__global__ void scan_down_k(int *data, int64_t nmax, const int *d_len, const int *partials) {
+    __shared__ int sw[8];
+    int64_t len = d_len ? min((int64_t)*d_len, nmax) : nmax;
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * 8;
+    int v[8], s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        int64_t j = base + k;
+        v[k] = (j < len) ? data[j] : 0;
+        s += v[k];
+    }
+    int total;
+    int ex = block_exclusive_scan<256>(s, sw, total) + partials[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        int64_t j = base + k;
+        if (j < len) data[j] = ex;
+        ex += v[k];
+    }
+}
+
+rv_status exclusive_scan(rv_ctx *c, int *data, int64_t nmax, const int *d_len, int *d_total, cudaStream_t s) {
+    if (nmax <= 0) {
+        if (d_total) return cuda_check(c, cudaMemsetAsync(d_total, 0, sizeof(int), s), "scan memset");
+        return RV_OK;
+    }
+    int nb = ceil_div(nmax, kScanChunk);
+    scan_reduce_k<<<nb, 256, 0, s>>>(data, nmax, d_len, c->w.partials);
+    count_launch(c);
+    scan_partials_k<<<1, 1024, 0, s>>>(c->w.partials, nb, d_total);
+    count_launch(c);
+    scan_down_k<<<nb, 256, 0, s>>>(data, nmax, d_len, c->w.partials);
+    count_launch(c);
+    return cuda_check(c, cudaGetLastError(), "scan");
+}
+
+// ---------------------------------------------------------------------------
+// bounding cube
+// ---------------------------------------------------------------------------
+__global__ void bounds_partial_k(int64_t n, const float *x, const float *y, const float *z, float *part) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            lo[a] = fminf(lo[a], v[a]);
+            hi[a] = fmaxf(hi[a], v[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    __shared__ float s[8][6];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; a++) { s[wid][a] = lo[a]; s[wid][3 + a] = hi[a]; }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float r = s[0][threadIdx.x];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+            r = (threadIdx.x < 3) ? fminf(r, s[w][threadIdx.x]) : fmaxf(r, s[w][threadIdx.x]);
+        part[6 * blockIdx.x + threadIdx.x] = r;
+    }
+}
+
+// min per axis; L = max_a (max_a - min_a) with FP64 differences; scale = 2^21 / L.
+__global__ void bounds_final_k(int nb, const float *part, DevState *st) {
+    if (threadIdx.x != 0) return;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; a++) { lo[a] = part[a]; hi[a] = part[3 + a]; }
+    for (int b = 1; b < nb; b++)
+        for (int a = 0; a < 3; a++) {
+            lo[a] = fminf(lo[a], part[6 * b + a]);
+            hi[a] = fmaxf(hi[a], part[6 * b + 3 + a]);
+        }
+    double L = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double e = __dsub_rn((double)hi[a], (double)lo[a]);
+        if (e > L) L = e;
+        st->bounds[a] = (double)lo[a];
+    }
+    st->bounds[3] = L;
+    st->bounds[4] = (L > 0.0) ? __ddiv_rn(2097152.0, L) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Morton keys
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x | (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x | (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x | (x >> 16)) & 0x1f00000000ffffull;
+    x = (x | (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+
+// q = min(floor((x - min) * scale), 2^21 - 1): one FP64 subtraction, one FP64 product.
+__device__ __forceinline__ uint32_t grid_coord(float v, double lo, double scale) {
+    double t = __dmul_rn(__dsub_rn((double)v, lo), scale);
+    double f = floor(t);
+    if (f >= 2097151.0) return 2097151u;
+    if (f < 0.0) return 0u;
+    return (uint32_t)f;
+}
+
+__global__ void keys_k(int64_t n, const float *x, const float *y, const float *z, const DevState *st,
+                       uint64_t *key) {
+    const double lx = st->bounds[0], ly = st->bounds[1], lz = st->bounds[2], sc = st->bounds[4];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = spread3(grid_coord(x[i], lx, sc)) | (spread3(grid_coord(y[i], ly, sc)) << 1) |
+                     (spread3(grid_coord(z[i], lz, sc)) << 2);
+        key[i] = k;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (key, index), 9-bit digits
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) sort_upsweep_k(int64_t n, const uint64_t *key, int shift,
+                                                               int ntiles, int *hist) {
+    __shared__ int h[kSortBins];
+    for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) h[b] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        int64_t j = base + k * kSortThreads + threadIdx.x;
+        if (j < n) atomicAdd(&h[(int)((key[j] >> shift) & (kSortBins - 1))], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) hist[(int64_t)b * ntiles + blockIdx.x] = h[b];
+}
+
+// Each warp ranks 256 consecutive keys in 8 rounds of 32 (warp-private digit
+// counters), so the in-tile order is (warp, round, lane) = input order and the
+// sort is stable.
+__global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, const uint64_t *key_in,
+                                                                 const int *idx_in, int shift, int ntiles,
+                                                                 const int *hist, uint64_t *key_out,
+                                                                 int *idx_out) {
+    constexpr int NW = kSortThreads / 32;
+    __shared__ unsigned short cnt[NW][kSortBins];
+    __shared__ int gbase[kSortBins];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b = lane; b < kSortBins; b += 32) cnt[wid][b] = 0;
+    for (int b = threadIdx.x; b < kSortBins; b += kSortThreads)
+        gbase[b] = hist[(int64_t)b * ntiles + blockIdx.x];
+    __syncwarp();
+    int64_t base = (int64_t)blockIdx.x * kSortTile + wid * (32 * kSortItems);
+    uint64_t kk[kSortItems];
+    int digit[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        int64_t j = base + r * 32 + lane;
+        bool ok = j < n;
+        kk[r] = ok ? key_in[j] : 0ull;
+        int d = ok ? (int)((kk[r] >> shift) & (kSortBins - 1)) : kSortBins;
+        digit[r] = d;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = (d < kSortBins) ? cnt[wid][d] : 0;
+        rank[r] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+        if (d < kSortBins && lane == __ffs(peers) - 1) cnt[wid][d] = (unsigned short)(before + __popc(peers));
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) {
+        int run = 0;
+        for (int w = 0; w < NW; w++) {
+            int t = cnt[w][b];
+            cnt[w][b] = (unsigned short)run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        int64_t j = base + r * 32 + lane;
+        if (j < n) {
+            int d = digit[r];
+            int64_t dst = (int64_t)gbase[d] + cnt[wid][d] + rank[r];
+            key_out[dst] = kk[r];
+            idx_out[dst] = idx_in ? idx_in[j] : (int)j;
+        }
+    }
+}
+
+rv_status radix_sort(rv_ctx *c, int64_t n, int passes, uint64_t **keys, int **idx, bool identity_idx,
+                     cudaStream_t s) {
+    if (n <= 0) return RV_OK;
+    int ntiles = ceil_div(n, kSortTile);
+    uint64_t *kin = c->w.key_a, *kout = c->w.key_b;
+    int *iin = identity_idx ? nullptr : c->w.idx_a, *iout = c->w.idx_b;
+    for (int p = 0; p < passes; p++) {
+        int shift = p * kSortBits;
+        sort_upsweep_k<<<ntiles, kSortThreads, 0, s>>>(n, kin, shift, ntiles, c->w.hist);
+        count_launch(c);
+        rv_status st = exclusive_scan(c, c->w.hist, (int64_t)kSortBins * ntiles, nullptr, nullptr, s);
+        if (st != RV_OK) return st;
+        sort_downsweep_k<<<ntiles, kSortThreads, 0, s>>>(n, kin, iin, shift, ntiles, c->w.hist, kout, iout);
+        count_launch(c);
+        // next pass reads what this one wrote
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        int *ti = (iin == nullptr) ? c->w.idx_a : iin;
+        iin = iout; iout = ti;
+    }
+    *keys = kin;
+    *idx = iin;
+    return cuda_check(c, cudaGetLastError(), "radix sort");
+}
+
+// ---------------------------------------------------------------------------
+// gather (x, y, z, m) into key order
+// ---------------------------------------------------------------------------
+__global__ void gather_k(int64_t n, const int *perm, const float *x, const float *y, const float *z,
+                         const float *m, float4 *pos) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int j = perm[i];
+        pos[i] = make_float4(x[j], y[j], z[j], m[j]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// topology
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int diff_level(uint64_t a, uint64_t b) {
+    uint64_t d = a ^ b;
+    if (d == 0) return kLevels;  // equal keys never separate
+    int h = 63 - __clzll((long long)d);
+    return (65 - h) / 3;
+}
+
+// Window of D values for one block: D(j) for j in [b0 - n_leaf + 1, b0 + NT + n_leaf].
+// Out-of-range positions are not boundaries (99); D(0) = D(n) = 0.
+__device__ void load_window(int64_t n, const uint64_t *key, int64_t b0, int n_leaf, unsigned char *win) {
+    int wlen = kTopoBlock + 2 * n_leaf;
+    for (int t = threadIdx.x; t < wlen; t += blockDim.x) {
+        int64_t j = b0 - n_leaf + 1 + t;
+        int d;
+        if (j < 0 || j > n) d = 99;
+        else if (j == 0 || j == n) d = 0;
+        else d = diff_level(key[j - 1], key[j]);
+        win[t] = (unsigned char)d;
+    }
+}
+
+// lambda_i from the window (i = b0 + threadIdx.x): the smallest level l such
+// that positions b1 <= i < b2, b2 - b1 <= n_leaf, are both cuts at l.
+__device__ __forceinline__ int leaf_level(const unsigned char *win, int t, int n_leaf) {
+    // win index of position j is j - (b0 - n_leaf + 1); i sits at t + n_leaf - 1
+    const int wi = t + n_leaf - 1;
+    int pm = 99, L = 99;
+    for (int s = n_leaf - 1; s >= 0; s--) {
+        int u = n_leaf - s;
+        pm = min(pm, (int)win[wi + u]);
+        L = min(L, max((int)win[wi - s], pm));
+    }
+    return min(L, kMaxLevel);
+}
+
+// Per-level ballots of "a cell starts at star i at level l" (D_i <= l <= lambda_i)
+// and their warp prefix counts (shared, [kLevels][NW]).
+struct TopoBallots {
+    unsigned mask[kLevels];
+};
+
+__device__ __forceinline__ void topo_ballots(bool valid, int Di, int lam, TopoBallots &b) {
+#pragma unroll
+    for (int l = 0; l < kLevels; l++) b.mask[l] = __ballot_sync(0xffffffffu, valid && Di <= l && l <= lam);
+}
+
+__global__ void __launch_bounds__(kTopoBlock) topo_count_k(int64_t n, const uint64_t *key, int n_leaf,
+                                                           uint8_t *dlev, uint8_t *lam_out, int *lvcnt,
+                                                           int nblk) {
+    extern __shared__ unsigned char win[];
+    __shared__ int wc[kLevels][kTopoBlock / 32];
+    int64_t b0 = (int64_t)blockIdx.x * kTopoBlock;
+    load_window(n, key, b0, n_leaf, win);
+    __syncthreads();
+    int64_t i = b0 + threadIdx.x;
+    bool valid = i < n;
+    int Di = 0, lam = -1;
+    if (valid) {
+        Di = win[threadIdx.x + n_leaf - 1];
+        lam = leaf_level(win, threadIdx.x, n_leaf);
+        dlev[i] = (uint8_t)Di;
+        lam_out[i] = (uint8_t)lam;
+    }
+    TopoBallots b;
+    topo_ballots(valid, Di, lam, b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int l = 0; l < kLevels; l++) wc[l][wid] = __popc(b.mask[l]);
+    __syncthreads();
+    if (threadIdx.x < kLevels) {
+        int s = 0;
+        for (int w = 0; w < kTopoBlock / 32; w++) s += wc[threadIdx.x][w];
+        lvcnt[(int64_t)threadIdx.x * nblk + blockIdx.x] = s;
+    }
+}
+
+__device__ __forceinline__ int4 cell_box(uint64_t key, int l) {
+    int sh = 3 * (kMaxLevel - l);
+    uint64_t pre = (sh >= 64) ? 0ull : ((key >> sh) << sh);
+    return make_int4((int)compact3(pre), (int)compact3(pre >> 1), (int)compact3(pre >> 2), l);
+}
+
+// Writes every cell's box, first star, child first, parent; and, as the star
+// that ends a cell, its end star and child end.
+__global__ void __launch_bounds__(kTopoBlock) topo_write_k(int64_t n, const uint64_t *key, const uint8_t *dlev,
+                                                           const uint8_t *lamv, const int *lvscan, int nblk,
+                                                           int64_t cap, int4 *cbox, int *clink, int *cparent,
+                                                           int *carrive, DevState *st) {
+    __shared__ int wp[kLevels][kTopoBlock / 32];
+    __shared__ int lvoff[kLevels + 1];
+    __shared__ int bbase[kLevels + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t i = (int64_t)blockIdx.x * kTopoBlock + threadIdx.x;
+    bool valid = i < n;
+    int Di = valid ? dlev[i] : 0, lam = valid ? lamv[i] : -1;
+    TopoBallots b;
+    topo_ballots(valid, Di, lam, b);
+    if (lane == 0)
+        for (int l = 0; l < kLevels; l++) wp[l][wid] = __popc(b.mask[l]);
+    if (threadIdx.x <= kLevels) {
+        int l = threadIdx.x;
+        // level offsets: scanned value at the first block of each level; total at the end
+        int tot = st->ncell;
+        lvoff[l] = (l < kLevels) ? lvscan[(int64_t)l * nblk] : tot;
+        bbase[l] = (l < kLevels) ? lvscan[(int64_t)l * nblk + blockIdx.x] : tot;
+    }
+    __syncthreads();
+    if (threadIdx.x < kLevels) {
+        int run = 0;
+        for (int w = 0; w < kTopoBlock / 32; w++) {
+            int t = wp[threadIdx.x][w];
+            wp[threadIdx.x][w] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x <= kLevels) st->lvoff[threadIdx.x] = lvoff[threadIdx.x];
+    if (!valid) return;
+    const unsigned lt = lanemask_lt();
+    // exclusive global rank of star i among cells of level l
+    auto rank = [&](int l) -> int { return bbase[l] + wp[l][wid] + __popc(b.mask[l] & lt); };
+    uint64_t k = key[i];
+    for (int l = Di; l <= lam; l++) {
+        int c = rank(l);
+        if (c >= cap) { latch_err(st, kErrCells); return; }
+        cbox[c] = cell_box(k, l);
+        clink[4 * c + 0] = (l < lam) ? rank(l + 1) : 0;  // first child: cell (l + 1, i)
+        if (l == lam) clink[4 * c + 1] = 0;
+        clink[4 * c + 2] = (int)i;
+        cparent[c] = (l == 0) ? -1 : rank(l - 1) - ((Di == l) ? 1 : 0);
+        carrive[c] = 0;
+    }
+    // cells containing star i-1 that end at i: levels D(i)..lambda_{i-1}
+    if (i > 0) {
+        int lp = lamv[i - 1];
+        for (int l = Di; l <= lp; l++) {
+            int c = rank(l) - 1;
+            if (c >= cap) { latch_err(st, kErrCells); return; }
+            clink[4 * c + 3] = (int)i;
+            if (l < lp) clink[4 * c + 1] = rank(l + 1);
+        }
+    }
+    // the last cell of every level that holds star n-1 ends at n
+    if (i == n - 1) {
+        for (int l = 0; l <= lam; l++) {
+            int c = lvoff[l + 1] - 1;
+            if (c >= cap) { latch_err(st, kErrCells); return; }
+            clink[4 * c + 3] = (int)n;
+            if (l < lam) clink[4 * c + 1] = lvoff[l + 2];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// walk groups
+// ---------------------------------------------------------------------------
+// A unit is a cell with <= G stars whose parent has more; consecutive unit
+// siblings are packed while the total stays <= G (box: the unit's own if the
+// pack has one unit, else the parent's); a leaf with more than G stars is
+// cut into chunks of G (box: the leaf). The root, if small, is one group.
+template <bool WRITE>
+__global__ void groups_k(const int *clink, const int *gofs, int G, int64_t cap, DevState *st, int *gcnt,
+                         int4 *groups) {
+    int ncell = (int)min((int64_t)st->ncell, cap);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        int4 lk = reinterpret_cast<const int4 *>(clink)[c];
+        int cnt = lk.w - lk.z;
+        int ng = 0;
+        int out = WRITE ? gofs[c] : 0;
+        auto emit = [&](int first, int count, int box) {
+            if (WRITE) groups[out + ng] = make_int4(first, count, box, 0);
+            ng++;
+        };
+        if (c == 0 && cnt <= G) {
+            emit(lk.z, cnt, 0);
+        } else if (cnt > G) {
+            if (lk.y == lk.x) {
+                for (int o = 0; o < cnt; o += G) emit(lk.z + o, min(G, cnt - o), c);
+            } else if (lk.x <= c || lk.y > ncell || lk.y - lk.x > 8) {
+                latch_err(st, kErrCells);
+            } else {
+                int pk_first = 0, pk_count = 0, pk_units = 0, pk_cell = 0;
+                for (int ch = lk.x; ch < lk.y; ch++) {
+                    int4 q = reinterpret_cast<const int4 *>(clink)[ch];
+                    int qc = q.w - q.z;
+                    if (qc <= G) {
+                        if (pk_units > 0 && pk_count + qc > G) {
+                            emit(pk_first, pk_count, pk_units == 1 ? pk_cell : c);
+                            pk_units = 0;
+                        }
+                        if (pk_units == 0) { pk_first = q.z; pk_count = 0; pk_cell = ch; }
+                        pk_count += qc;
+                        pk_units++;
+                    } else if (pk_units > 0) {
+                        emit(pk_first, pk_count, pk_units == 1 ? pk_cell : c);
+                        pk_units = 0;
+                    }
+                }
+                if (pk_units > 0) emit(pk_first, pk_count, pk_units == 1 ? pk_cell : c);
+            }
+        }
+        if (!WRITE) gcnt[c] = ng;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// multipoles, bottom-up: each leaf computes its moments from its stars; the
+// last child to finish a parent (atomic arrival count) computes the parent
+// from its children in child order, so the result does not depend on timing.
+// FP32, accumulated relative to the cell's geometric centre.
+// ---------------------------------------------------------------------------
+struct Mom {
+    float M, cx, cy, cz, q[6];  // q: xx, yy, zz, xy, xz, yz
+};
+
+__device__ __forceinline__ void store_mom(float4 *cmom, int c, const Mom &m) {
+    cmom[3 * c + 0] = make_float4(m.M, m.cx, m.cy, m.cz);
+    cmom[3 * c + 1] = make_float4(m.q[0], m.q[1], m.q[2], m.q[3]);
+    cmom[3 * c + 2] = make_float4(m.q[4], m.q[5], 0.f, 0.f);
+}
+
+__device__ __forceinline__ void geo_centre(const int4 b, const float lo[3], float unit, float g[3]) {
+    float half = 0.5f * (float)(1 << (kMaxLevel - b.w));
+    g[0] = lo[0] + ((float)b.x + half) * unit;
+    g[1] = lo[1] + ((float)b.y + half) * unit;
+    g[2] = lo[2] + ((float)b.z + half) * unit;
+}
+
+__device__ __forceinline__ void add_q(float q[6], float m, float dx, float dy, float dz) {
+    float d2 = dx * dx + dy * dy + dz * dz;
+    q[0] += m * (3.f * dx * dx - d2);
+    q[1] += m * (3.f * dy * dy - d2);
+    q[2] += m * (3.f * dz * dz - d2);
+    q[3] += m * 3.f * dx * dy;
+    q[4] += m * 3.f * dx * dz;
+    q[5] += m * 3.f * dy * dz;
+}
+
+__global__ void moments_k(int64_t n, const float4 *pos, const int4 *cbox, const int *clink, const int *cparent,
+                          int *carrive, float4 *cmom, int64_t cap, DevState *st) {
+    int ncell = (int)min((int64_t)st->ncell, cap);
+    float lo[3] = {(float)st->bounds[0], (float)st->bounds[1], (float)st->bounds[2]};
+    float unit = (float)(st->bounds[3] / 2097152.0);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        int4 lk = reinterpret_cast<const int4 *>(clink)[c];
+        if (lk.y != lk.x) continue;  // not a leaf
+        if (lk.z < 0 || lk.w > n || lk.z > lk.w) { latch_err(st, kErrCells); continue; }
+        float g[3];
+        geo_centre(cbox[c], lo, unit, g);
+        Mom m = {};
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int j = lk.z; j < lk.w; j++) {
+            float4 p = pos[j];
+            m.M += p.w;
+            sx += p.w * (p.x - g[0]);
+            sy += p.w * (p.y - g[1]);
+            sz += p.w * (p.z - g[2]);
+        }
+        if (m.M > 0.f) {
+            m.cx = g[0] + sx / m.M; m.cy = g[1] + sy / m.M; m.cz = g[2] + sz / m.M;
+            for (int j = lk.z; j < lk.w; j++) {
+                float4 p = pos[j];
+                add_q(m.q, p.w, p.x - m.cx, p.y - m.cy, p.z - m.cz);
+            }
+        } else {
+            m.cx = g[0]; m.cy = g[1]; m.cz = g[2];
+        }
+        store_mom(cmom, c, m);
+        // climb while this thread is the last child to arrive (at most 21 levels)
+        int cur = c;
+        for (int guard = 0; guard <= kMaxLevel; guard++) {
+            int p = cparent[cur];
+            if (p < 0) break;
+            if (p >= cur) { latch_err(st, kErrCells); break; }  // parents precede children
+            __threadfence();
+            int4 pl = reinterpret_cast<const int4 *>(clink)[p];
+            int nch = pl.y - pl.x;
+            if (pl.x <= p || pl.y > ncell || nch < 1 || nch > 8) { latch_err(st, kErrCells); break; }
+            if (atomicAdd(&carrive[p], 1) != nch - 1) break;
+            __threadfence();
+            float pg[3];
+            geo_centre(cbox[p], lo, unit, pg);
+            Mom P = {};
+            float px = 0.f, py = 0.f, pz = 0.f;
+            for (int ch = pl.x; ch < pl.y; ch++) {
+                float4 a = __ldcg(&cmom[3 * ch]);
+                P.M += a.x;
+                px += a.x * (a.y - pg[0]);
+                py += a.x * (a.z - pg[1]);
+                pz += a.x * (a.w - pg[2]);
+            }
+            if (P.M > 0.f) {
+                P.cx = pg[0] + px / P.M; P.cy = pg[1] + py / P.M; P.cz = pg[2] + pz / P.M;
+                for (int ch = pl.x; ch < pl.y; ch++) {
+                    float4 a = __ldcg(&cmom[3 * ch]);
+                    float4 b = __ldcg(&cmom[3 * ch + 1]);
+                    float4 e = __ldcg(&cmom[3 * ch + 2]);
+                    P.q[0] += b.x; P.q[1] += b.y; P.q[2] += b.z; P.q[3] += b.w; P.q[4] += e.x; P.q[5] += e.y;
+                    add_q(P.q, a.x, a.y - P.cx, a.z - P.cy, a.w - P.cz);
+                }
+            } else {
+                P.cx = pg[0]; P.cy = pg[1]; P.cz = pg[2];
+            }
+            store_mom(cmom, p, P);
+            cur = p;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// driver
+// ---------------------------------------------------------------------------
+static int grid_for(rv_ctx *c, int64_t n, int per_block) {
+    int64_t b = (n + per_block - 1) / per_block;
+    int64_t cap = (int64_t)c->num_sms * 8;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+rv_status build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *m,
+                     cudaStream_t s) {
+    Workspace &w = c->w;
+    c->n = n;
+    c->built = false;
+    rv_status r;
+    if (n == 0) {
+        r = cuda_check(c, cudaMemsetAsync(w.st, 0, sizeof(DevState), s), "state reset");
+        if (r == RV_OK) c->built = true;
+        return r;
+    }
+    // bounds
+    int nb = (int)std::min<int64_t>(ceil_div(n, 2048), 1024);
+    bounds_partial_k<<<nb, 256, 0, s>>>(n, x, y, z, reinterpret_cast<float *>(w.partials));
+    count_launch(c);
+    bounds_final_k<<<1, 32, 0, s>>>(nb, reinterpret_cast<float *>(w.partials), w.st);
+    count_launch(c);
+    keys_k<<<grid_for(c, n, 256), 256, 0, s>>>(n, x, y, z, w.st, w.key_a);
+    count_launch(c);
+    uint64_t *skey;
+    int *perm;
+    if ((r = radix_sort(c, n, 7, &skey, &perm, true, s)) != RV_OK) return r;
+    w.skey = skey;
+    w.perm = perm;
+    gather_k<<<grid_for(c, n, 256), 256, 0, s>>>(n, perm, x, y, z, m, w.pos);
+    count_launch(c);
+    // topology
+    int nblk = ceil_div(n, kTopoBlock);
+    size_t win = kTopoBlock + 2 * c->cfg.n_leaf;
+    topo_count_k<<<nblk, kTopoBlock, win, s>>>(n, skey, c->cfg.n_leaf, w.dlev, w.lam, w.lvcnt, nblk);
+    count_launch(c);
+    if ((r = exclusive_scan(c, w.lvcnt, (int64_t)kLevels * nblk, nullptr, &w.st->ncell, s)) != RV_OK) return r;
+    topo_write_k<<<nblk, kTopoBlock, 0, s>>>(n, skey, w.dlev, w.lam, w.lvcnt, nblk, c->cell_cap, w.cbox,
+                                             w.clink, w.cparent, w.carrive, w.st);
+    count_launch(c);
+    // groups
+    int gb = grid_for(c, c->cell_cap, 256);
+    groups_k<false><<<gb, 256, 0, s>>>(w.clink, nullptr, c->cfg.group, c->cell_cap, w.st, w.gcnt, nullptr);
+    count_launch(c);
+    if ((r = exclusive_scan(c, w.gcnt, c->cell_cap, &w.st->ncell, &w.st->ngroup, s)) != RV_OK) return r;
+    groups_k<true><<<gb, 256, 0, s>>>(w.clink, w.gcnt, c->cfg.group, c->cell_cap, w.st, nullptr, w.groups);
+    count_launch(c);
+    // multipoles
+    moments_k<<<gb, 128, 0, s>>>(n, w.pos, w.cbox, w.clink, w.cparent, w.carrive, w.cmom, c->cell_cap, w.st);
+    count_launch(c);
+    r = cuda_check(c, cudaGetLastError(), "build_tree");
+    if (r == RV_OK) c->built = true;
+    return r;
+}
+
+}  // namespace rv

@@ -1,0 +1,304 @@
+// rv_api.cu -- the extern "C" entry points of librv: argument checks,
+// workspace layout, and dispatch to the kernels in build.cu, walk.cu and
+// chain.cu.
+#include <stdarg.h>
+
+#include <algorithm>
+#include <stdlib.h>
+#include <string.h>
+
+#include "rv_internal.cuh"
+
+namespace rv {
+
+rv_status set_err(rv_ctx *c, rv_status s, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+rv_status cuda_check(rv_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return RV_OK;
+    return set_err(c, RV_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int64_t cell_capacity(int64_t n, int n_leaf) {
+    int64_t nn = n > 0 ? n : 1;
+    int64_t per_level = std::min<int64_t>(nn, 8 * nn / (n_leaf + 1) + 8);
+    int64_t worst = 2 + (int64_t)kMaxLevel * per_level;
+    int64_t typical = 96 + 3 * (8 * nn / (n_leaf + 1));
+    return std::min(worst, typical);
+}
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int64_t *cell_cap) {
+    int64_t n = n_max > 0 ? n_max : 1;
+    int64_t cap = cell_capacity(n, cfg.n_leaf);
+    if (cell_cap) *cell_cap = cap;
+    int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    int64_t nblk = (n + kTopoBlock - 1) / kTopoBlock;
+    int64_t scan_max = std::max<int64_t>(std::max<int64_t>((int64_t)kSortBins * ntiles, (int64_t)kLevels * nblk),
+                                         std::max<int64_t>(cap, n));
+    int64_t nparts = std::max<int64_t>(6 * 1024, scan_max / kScanChunk + 2);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return p;
+    };
+    Workspace t;
+    t.key_a = (uint64_t *)take(8 * n);
+    t.key_b = (uint64_t *)take(8 * n);
+    t.idx_a = (int *)take(4 * n);
+    t.idx_b = (int *)take(4 * n);
+    t.hist = (int *)take(4 * (size_t)kSortBins * ntiles);
+    t.skey = nullptr;
+    t.perm = nullptr;
+    t.pos = (float4 *)take(16 * n);
+    t.dlev = (uint8_t *)take(n);
+    t.lam = (uint8_t *)take(n);
+    t.lvcnt = (int *)take(4 * (size_t)kLevels * nblk);
+    t.cbox = (int4 *)take(16 * cap);
+    t.clink = (int *)take(16 * cap);
+    t.cmom = (float4 *)take(48 * cap);
+    t.cparent = (int *)take(4 * cap);
+    t.carrive = (int *)take(4 * cap);
+    t.gcnt = (int *)take(4 * cap);
+    t.groups = (int4 *)take(16 * (n + 1));
+    t.partials = (int *)take(4 * nparts);
+    t.pert_idx = (int *)take(4 * kMaxPert);
+    t.pert_m = (double *)take(8 * kMaxPert);
+    t.pert_x = (double *)take(24 * kMaxPert);
+    t.pert_a = (double *)take(24 * kMaxPert);
+    t.pert_pot = (double *)take(8 * kMaxPert);
+    t.chain_ext_a = (double *)take(24 * kMaxChain);
+    t.chain_ext_pot = (double *)take(8 * kMaxChain);
+    t.out8 = (double *)take(8 * 16);
+    t.extra_xyzm = (float *)take(16 * kMaxExtra);
+    t.extra_eps = (float *)take(4 * kMaxExtra);
+    t.extra_out = (float *)take(16 * kMaxExtra);
+    t.red = (double *)take(8 * 8 * 1024);
+    t.sel_flag = (int *)take(4 * n);
+    t.st = (DevState *)take(sizeof(DevState));
+    if (w) *w = t;
+    return off;
+}
+
+static bool config_ok(const rv_config *cfg) {
+    return cfg && cfg->theta >= 0.f && cfg->theta < 2.f && cfg->eps_star >= 0.f && cfg->n_leaf >= 1 &&
+           cfg->n_leaf <= 64 && cfg->group >= 1 && cfg->group <= 32 && (cfg->quadrupole == 0 || cfg->quadrupole == 1) &&
+           cfg->tile >= 32 && cfg->tile <= 256 && cfg->tile % 32 == 0;
+}
+
+static bool ready(rv_ctx *c) { return c && c->ws; }
+
+}  // namespace rv
+
+using namespace rv;
+
+extern "C" {
+
+void rv_default_config(rv_config *cfg) {
+    if (!cfg) return;
+    cfg->theta = 0.5f;
+    cfg->eps_star = 0.01f;
+    cfg->n_leaf = 16;
+    cfg->group = 32;
+    cfg->quadrupole = 1;
+    cfg->tile = 64;
+}
+
+size_t rv_workspace_size(int64_t n_max, const rv_config *cfg) {
+    if (!config_ok(cfg) || n_max < 0) return 0;
+    return layout(n_max, *cfg, nullptr, nullptr, nullptr);
+}
+
+rv_status rv_create(rv_ctx **out, int64_t n_max, const rv_config *cfg) {
+    if (!out) return RV_E_INVAL;
+    *out = nullptr;
+    if (!config_ok(cfg) || n_max < 0 || n_max > (int64_t)1 << 30) return RV_E_INVAL;
+    int64_t cap = cell_capacity(n_max, cfg->n_leaf);
+    if (cap >= ((int64_t)1 << 27)) return RV_E_INVAL;  // child ranges are packed as (first << 4 | count)
+    rv_ctx *c = (rv_ctx *)calloc(1, sizeof(rv_ctx));
+    if (!c) return RV_E_INVAL;
+    c->cfg = *cfg;
+    c->n_max = n_max;
+    c->cell_cap = cap;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        free(c);
+        return RV_E_CUDA;
+    }
+    *out = c;
+    return RV_OK;
+}
+
+void rv_destroy(rv_ctx *c) { free(c); }
+
+rv_status rv_set_workspace(rv_ctx *c, void *dev, size_t bytes) {
+    if (!c || !dev) return RV_E_INVAL;
+    size_t need = layout(c->n_max, c->cfg, nullptr, nullptr, nullptr);
+    if (bytes < need || ((uintptr_t)dev & 255))
+        return set_err(c, RV_E_WORKSPACE, "workspace: need %zu bytes, 256-aligned; got %zu", need, bytes);
+    c->ws = (char *)dev;
+    c->ws_bytes = bytes;
+    layout(c->n_max, c->cfg, c->ws, &c->w, &c->cell_cap);
+    c->built = false;
+    cudaError_t e = cudaMemset(c->w.st, 0, sizeof(DevState));
+    return cuda_check(c, e, "workspace init");
+}
+
+rv_status rv_build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *m,
+                        void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (n < 0 || n > c->n_max) return set_err(c, RV_E_INVAL, "n = %lld outside [0, %lld]", (long long)n, (long long)c->n_max);
+    if (n > 0 && (!x || !y || !z || !m)) return set_err(c, RV_E_INVAL, "null star array");
+    return build_tree(c, n, x, y, z, m, (cudaStream_t)stream);
+}
+
+rv_status rv_tree_forces(rv_ctx *c, float theta, float eps_star, int32_t n_extra, const float *extra_xyzm,
+                         const float *extra_eps, float *ax, float *ay, float *az, float *pot, float *extra_out,
+                         void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces before rv_build_tree");
+    if (!(theta >= 0.f && theta < 2.f) || !(eps_star >= 0.f)) return set_err(c, RV_E_INVAL, "bad theta/eps");
+    if (n_extra < 0 || n_extra > kMaxExtra) return set_err(c, RV_E_INVAL, "n_extra must be in [0, %d]", kMaxExtra);
+    if (n_extra > 0 && (!extra_xyzm || !extra_eps || !extra_out)) return set_err(c, RV_E_INVAL, "null extra array");
+    if (c->n > 0 && (!ax || !ay || !az || !pot)) return set_err(c, RV_E_INVAL, "null output array");
+    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, ax, ay, az, pot, extra_out,
+                     (cudaStream_t)stream);
+}
+
+rv_status rv_perturber_forces(rv_ctx *c, int32_t n_ch, const double *chain_m, const double *chain_x,
+                              int32_t n_pert, const double *pert_m, const double *pert_x, double *a_pert,
+                              double *pot_pert, double *a_chain, double *pot_chain, double *out8, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (n_ch < 1 || n_ch > kMaxChain || n_pert < 0 || n_pert > kMaxPert)
+        return set_err(c, RV_E_INVAL, "need 1 <= n_ch <= %d and 0 <= n_pert <= %d", kMaxChain, kMaxPert);
+    if (!chain_m || !chain_x || !a_chain || !pot_chain || !out8) return set_err(c, RV_E_INVAL, "null chain array");
+    if (n_pert > 0 && (!pert_m || !pert_x || !a_pert || !pot_pert)) return set_err(c, RV_E_INVAL, "null perturber array");
+    return perturber_forces(c, n_ch, chain_m, chain_x, n_pert, nullptr, pert_m, pert_x, a_pert, pot_pert, a_chain,
+                            pot_chain, out8, (cudaStream_t)stream);
+}
+
+static rv_status check_system(rv_ctx *c, const rv_system *s) {
+    if (!s) return set_err(c, RV_E_INVAL, "null system");
+    if (s->n < 0 || s->n > c->n_max) return set_err(c, RV_E_INVAL, "system n outside [0, n_max]");
+    if (s->n > 0 && (!s->x || !s->y || !s->z || !s->vx || !s->vy || !s->vz || !s->m || !s->ax || !s->ay || !s->az ||
+                     !s->pot))
+        return set_err(c, RV_E_INVAL, "null star array in system");
+    if (s->n_chain < 0 || s->n_chain > kMaxChain) return set_err(c, RV_E_INVAL, "n_chain outside [0, %d]", kMaxChain);
+    if (s->n_chain > 0 && (!s->chain_m || !s->chain_x || !s->chain_v || !s->chain_a || !s->chain_pot))
+        return set_err(c, RV_E_INVAL, "null chain array in system");
+    if (s->n_chain > 0 && (s->pert_mode < 0 || s->pert_mode > 2)) return set_err(c, RV_E_INVAL, "bad pert_mode");
+    if (s->pert_mode == 2 && (s->pert_k < 0 || s->pert_k > kMaxPert)) return set_err(c, RV_E_INVAL, "bad pert_k");
+    return RV_OK;
+}
+
+rv_status rv_system_forces(rv_ctx *c, rv_system *sys, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    rv_status r = check_system(c, sys);
+    if (r != RV_OK) return r;
+    return system_forces(c, sys, (cudaStream_t)stream);
+}
+
+rv_status rv_kdk_step(rv_ctx *c, rv_system *sys, double dt, int32_t nsteps, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    rv_status r = check_system(c, sys);
+    if (r != RV_OK) return r;
+    if (nsteps < 0 || !(dt == dt)) return set_err(c, RV_E_INVAL, "bad dt/nsteps");
+    return kdk(c, sys, dt, nsteps, (cudaStream_t)stream);
+}
+
+rv_status rv_energy(rv_ctx *c, const rv_system *sys, double *out, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    rv_status r = check_system(c, sys);
+    if (r != RV_OK) return r;
+    if (!out) return set_err(c, RV_E_INVAL, "null out");
+    return energy(c, sys, out, (cudaStream_t)stream);
+}
+
+rv_status rv_select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
+                               const float centre[3], int32_t mode, float radius, int32_t k, int32_t cap,
+                               int32_t *idx, int32_t *count, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (n < 0 || n > c->n_max || !centre || !idx || !count || cap < 0 || (mode != 1 && mode != 2))
+        return set_err(c, RV_E_INVAL, "bad selection arguments");
+    if (n > 0 && (!x || !y || !z)) return set_err(c, RV_E_INVAL, "null star array");
+    if (mode == 1 && !(radius >= 0.f)) return set_err(c, RV_E_INVAL, "bad radius");
+    return select_perturbers(c, n, x, y, z, nullptr, centre, mode, radius, k, cap, idx, count, (cudaStream_t)stream);
+}
+
+rv_status rv_get_tree(rv_ctx *c, rv_tree_view *out, void *stream) {
+    if (!c || !out) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (!c->built) return set_err(c, RV_E_NOTBUILT, "no tree");
+    cudaStream_t s = (cudaStream_t)stream;
+    int sz[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(sz, &c->w.st->ncell, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(c, e, "get tree");
+    out->n = c->n;
+    out->ncell = std::min<int64_t>(sz[0], c->cell_cap);
+    out->ngroup = sz[1];
+    out->keys = c->w.skey;
+    out->perm = c->w.perm;
+    out->pos = reinterpret_cast<const float *>(c->w.pos);
+    out->cbox = reinterpret_cast<const int32_t *>(c->w.cbox);
+    out->clink = c->w.clink;
+    out->cmom = reinterpret_cast<const float *>(c->w.cmom);
+    out->cparent = c->w.cparent;
+    out->groups = reinterpret_cast<const int32_t *>(c->w.groups);
+    out->bounds = c->w.st->bounds;
+    return RV_OK;
+}
+
+rv_status rv_walk_stats(rv_ctx *c, int64_t out[2], void *stream) {
+    if (!c || !out) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long v[2];
+    cudaError_t e = cudaMemcpyAsync(v, &c->w.st->n_p2p, sizeof(v), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(c, e, "walk stats");
+    out[0] = (int64_t)v[0];
+    out[1] = (int64_t)v[1];
+    return RV_OK;
+}
+
+rv_status rv_sync_status(rv_ctx *c, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    cudaStream_t s = (cudaStream_t)stream;
+    int err = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, &c->w.st->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(&c->w.st->err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_check(c, e, "sync status");
+    switch (err) {
+        case kErrNone: return RV_OK;
+        case kErrStack: return set_err(c, RV_E_STACK, "walk stack overflow (more than %d pending child ranges)", kStackCap);
+        case kErrCells: return set_err(c, RV_E_WORKSPACE, "tree has more cells than the workspace holds (%lld)", (long long)c->cell_cap);
+        case kErrPert: return set_err(c, RV_E_WORKSPACE, "more perturbers inside the radius than the output holds");
+        default: return set_err(c, RV_E_CUDA, "unknown device error %d", err);
+    }
+}
+
+int64_t rv_launch_count(const rv_ctx *c) { return c ? (int64_t)c->launches : 0; }
+
+const char *rv_last_error(const rv_ctx *c) { return c ? c->err : "null context"; }
+
+}  // extern "C"

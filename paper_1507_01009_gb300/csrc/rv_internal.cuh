@@ -1,0 +1,144 @@
+// rv_internal.cuh -- context, workspace layout and small device helpers of librv.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "rv.h"
+
+namespace rv {
+
+constexpr int kMaxLevel = 21;           // 21 bits per axis, levels 0..21
+constexpr int kLevels = kMaxLevel + 1;  // 22
+constexpr int kSortBits = 9;            // radix digit width
+constexpr int kSortBins = 1 << kSortBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per tile
+constexpr int kTopoBlock = 256;
+constexpr int kScanChunk = 2048;        // elements per scan block
+constexpr int kWalkWarps = 4;           // warps per walk block
+constexpr int kStackCap = 768;          // walk traversal stack entries per warp
+constexpr int kMaxExtra = 8;
+constexpr int kMaxChain = 250;
+constexpr int kMaxPert = 5000;
+
+// Error codes latched by kernels (first one wins).
+enum DevErr : int { kErrNone = 0, kErrStack = 1, kErrCells = 2, kErrPert = 3 };
+
+// Device-resident scalars (one small block in the workspace).
+struct DevState {
+    int ncell;        // cells of the last build
+    int ngroup;       // walk groups of the last build
+    int next_group;   // walk work counter
+    int err;          // latched DevErr
+    int n_pert;       // perturbers selected by the last selection
+    int stack_hwm;    // deepest walk stack seen
+    int pad[2];
+    unsigned long long n_p2p, n_m2p;  // interaction counts of the last walk
+    double bounds[5];                 // min x, y, z, L, 2^21 / L
+    int lvoff[kLevels + 1];           // first cell of each level, then ncell
+};
+
+struct Workspace {
+    // tree build
+    uint64_t *key_a, *key_b;
+    int *idx_a, *idx_b;
+    int *hist;            // radix histograms [bins x tiles]
+    uint64_t *skey;       // sorted keys of the last build (key_a or key_b)
+    int *perm;            // sorted slot -> caller index of the last build (idx_a or idx_b)
+    float4 *pos;          // sorted (x, y, z, m)
+    uint8_t *dlev, *lam;  // per sorted star: first differing level with its predecessor, leaf level
+    int *lvcnt;           // per (level, topo block) counts, scanned in place
+    int4 *cbox;           // (ox, oy, oz, level)
+    int *clink;           // [4 ncell] child first, child end, first star, end star
+    float4 *cmom;         // [3 ncell]
+    int *cparent, *carrive;
+    int *gcnt;            // groups started by each cell, scanned in place
+    int4 *groups;
+    int *partials;        // scan block sums
+    // perturbers and chain hand-off
+    int *pert_idx;        // [kMaxPert]
+    double *pert_m, *pert_x;           // [kMaxPert], [3 kMaxPert]
+    double *pert_a, *pert_pot;         // [3 kMaxPert], [kMaxPert]
+    double *chain_ext_a, *chain_ext_pot;  // [3 kMaxChain], [kMaxChain]
+    double *out8;         // Eq. 3 correction, sub, potentials
+    float *extra_xyzm, *extra_eps, *extra_out;  // [4 kMaxExtra], [kMaxExtra], [4 kMaxExtra]
+    double *red;          // energy partial sums
+    int *sel_flag;        // perturber selection flags (n)
+    DevState *st;
+};
+
+}  // namespace rv
+
+struct rv_ctx {
+    rv_config cfg;
+    int64_t n_max;
+    int64_t n;            // stars in the last build
+    int64_t cell_cap;
+    int device;
+    int num_sms;
+    bool built;
+    long long launches;   // kernels launched through this context
+    char *ws;
+    size_t ws_bytes;
+    rv::Workspace w;
+    char err[512];
+};
+
+namespace rv {
+
+// Workspace layout: one pass computes sizes (base == nullptr) or assigns pointers.
+size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int64_t *cell_cap);
+int64_t cell_capacity(int64_t n_max, int n_leaf);
+
+rv_status set_err(rv_ctx *c, rv_status s, const char *fmt, ...);
+rv_status cuda_check(rv_ctx *c, cudaError_t e, const char *what);
+
+// build.cu
+rv_status build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *m,
+                     cudaStream_t s);
+rv_status radix_sort(rv_ctx *c, int64_t n, int passes, uint64_t **keys, int **idx, bool identity_idx,
+                     cudaStream_t s);
+rv_status exclusive_scan(rv_ctx *c, int *data, int64_t nmax, const int *d_len, int *d_total, cudaStream_t s);
+
+// walk.cu
+rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
+                    float *ax, float *ay, float *az, float *pot, float *xout, cudaStream_t s);
+
+// chain.cu
+rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
+                            const float *centre_dev, const float *centre_host, int mode, float radius, int k,
+                            int cap, int *idx, int *count, cudaStream_t s);
+rv_status perturber_forces(rv_ctx *c, int n_ch, const double *cm, const double *cx, int n_pert_max,
+                           const int *d_npert, const double *pm, const double *px, double *a_pert,
+                           double *pot_pert, double *a_chain, double *pot_chain, double *out8, cudaStream_t s);
+rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s);
+rv_status kdk(rv_ctx *c, rv_system *sys, double dt, int nsteps, cudaStream_t s);
+rv_status energy(rv_ctx *c, const rv_system *sys, double *out, cudaStream_t s);
+
+inline void count_launch(rv_ctx *c) { c->launches++; }
+
+// ---- device helpers ----
+__device__ __forceinline__ void latch_err(DevState *st, int code) { atomicCAS(&st->err, 0, code); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Neumaier compensated accumulation of a tile sum x into (s, c).
+__device__ __forceinline__ void nadd(float &s, float &c, float x) {
+    float t = __fadd_rn(s, x);
+    if (fabsf(s) >= fabsf(x))
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
+    else
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+    s = t;
+}
+
+__host__ __device__ __forceinline__ int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace rv

@@ -1,0 +1,443 @@
+// walk.cu -- Barnes-Hut tree walk and interaction evaluation (FP32).
+//
+// One warp walks the tree for one group of up to 32 consecutive stars (one
+// star per lane). Cells are tested 32 at a time, one per lane, under the
+// box-box opening test; accepted cells are staged in shared memory as
+// multipole records, opened leaves stage their stars, opened internal cells
+// push their child range on a per-warp stack. Whenever a staged list holds a
+// full tile, every lane evaluates the tile against its own star with
+// broadcast shared-memory reads, adds the tile's sum to its running total
+// with Neumaier compensation, and the walk continues.
+//
+// Interactions (G = 1, Sect. 3 Plummer softening; multipoles about the cell's
+// centre of mass, Sect. 1):
+//   star j on star i:  a += m_j r / (r^2 + e^2)^{3/2},  phi -= m_j (r^2 + e^2)^{-1/2},  r = x_j - x_i
+//   cell on star i:    r = x_i - com, rho^2 = r.r + e^2,
+//                      a += -M r / rho^3 + Q r / rho^5 - 5 (r.Q.r) r / (2 rho^7),
+//                      phi -= M / rho + (r.Q.r) / (2 rho^5).
+// Flops per interaction in this source (add/mul 1, FMA 2, rsqrt 1):
+//   star-star 20, cell (monopole + quadrupole) 54, cell (monopole) 18.
+#include "rv_internal.cuh"
+
+namespace rv {
+
+struct MacTable {
+    unsigned long long thr[kLevels];  // accept iff d^2 >= thr[level]
+};
+
+struct WalkArgs {
+    const float4 *pos;   // sorted (x, y, z, m)
+    const int4 *cbox;
+    const int4 *clink;   // (child first, child end, first star, end star)
+    const float4 *cmom;
+    const int4 *groups;
+    const int *perm;
+    DevState *st;
+    int ncell;           // cells of the tree (bounded by the workspace)
+    int cell_cap;
+    int n;               // stars of the tree
+    MacTable mac;
+    float eps2;          // star-star and star-cell softening^2
+    float eps_star;
+    int tile;
+    int n_extra;
+    const float *xyzm;   // extra particles (x, y, z, m)
+    const float *xeps;
+    float *ax, *ay, *az, *pot;
+    float *xout;
+};
+
+// Per-warp shared memory: stack | lane_cell[32] | m2p staging (tile+32) x 3 float4 | p2p staging (tile+32) float4
+__host__ __device__ inline size_t warp_smem_bytes(int tile) {
+    return (size_t)kStackCap * 4 + 32 * 4 + (size_t)(tile + 32) * 48 + (size_t)(tile + 32) * 16;
+}
+
+struct Acc {
+    float ax, ay, az, ph;      // running sums
+    float cx, cy, cz, cp;      // Neumaier compensation
+};
+
+template <bool SOFT>
+__device__ __forceinline__ void eval_p2p(const float4 *src, int cnt, float xi, float yi, float zi, float eps2,
+                                         Acc &A) {
+    float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < cnt; j++) {
+        float4 s = src[j];
+        float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        float rinv = rsqrtf(r2);
+        if (!SOFT) rinv = (r2 > 0.f) ? rinv : 0.f;
+        float mr = s.w * rinv;
+        float mr3 = mr * (rinv * rinv);
+        tx = fmaf(mr3, dx, tx);
+        ty = fmaf(mr3, dy, ty);
+        tz = fmaf(mr3, dz, tz);
+        tp -= mr;
+    }
+    nadd(A.ax, A.cx, tx); nadd(A.ay, A.cy, ty); nadd(A.az, A.cz, tz); nadd(A.ph, A.cp, tp);
+}
+
+template <bool QUAD>
+__device__ __forceinline__ void eval_m2p(const float4 *src, int cnt, float xi, float yi, float zi, float eps2,
+                                         Acc &A) {
+    float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+#pragma unroll 2
+    for (int j = 0; j < cnt; j++) {
+        float4 a = src[3 * j];
+        float rx = xi - a.y, ry = yi - a.z, rz = zi - a.w;
+        float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
+        // r > 0: an accepted cell's box is separated from the group's box
+        float rinv = rsqrtf(r2);
+        float rinv2 = rinv * rinv;
+        float mr = a.x * rinv;
+        float mr3 = mr * rinv2;
+        if (QUAD) {
+            float4 b = src[3 * j + 1];
+            float4 e = src[3 * j + 2];
+            // Q r with Q = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
+            float qx = fmaf(b.x, rx, fmaf(b.w, ry, e.x * rz));
+            float qy = fmaf(b.w, rx, fmaf(b.y, ry, e.y * rz));
+            float qz = fmaf(e.x, rx, fmaf(e.y, ry, b.z * rz));
+            float rqr = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
+            float rinv5 = rinv * (rinv2 * rinv2);
+            float rinv7 = rinv5 * rinv2;
+            float A1 = fmaf(-2.5f * rqr, rinv7, -mr3);
+            tx = fmaf(A1, rx, fmaf(rinv5, qx, tx));
+            ty = fmaf(A1, ry, fmaf(rinv5, qy, ty));
+            tz = fmaf(A1, rz, fmaf(rinv5, qz, tz));
+            tp -= fmaf(0.5f * rqr, rinv5, mr);
+        } else {
+            tx = fmaf(-mr3, rx, tx);
+            ty = fmaf(-mr3, ry, ty);
+            tz = fmaf(-mr3, rz, tz);
+            tp -= mr;
+        }
+    }
+    nadd(A.ax, A.cx, tx); nadd(A.ay, A.cy, ty); nadd(A.az, A.cz, tz); nadd(A.ph, A.cp, tp);
+}
+
+__device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
+    return (clo >= bhi) ? clo - bhi : ((blo >= chi) ? blo - chi : 0);
+}
+
+// Walks the tree for one group; returns false if the stack overflowed.
+template <bool SOFT, bool QUAD>
+__device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3], float xi, float yi, float zi,
+                           float eps2, Acc &acc, unsigned long long &np2p, unsigned long long &nm2p) {
+    const int lane = threadIdx.x & 31;
+    const int T = A.tile;
+    int *stack = reinterpret_cast<int *>(wsm);
+    int *lane_cell = stack + kStackCap;
+    float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 32);
+    float4 *p2p = m2p + 3 * (T + 32);
+    const unsigned lt = lanemask_lt();
+
+    if (lane == 0) stack[0] = (0 << 4) | 1;  // root: a range of one cell starting at 0
+    int top = 1, nm = 0, np = 0, hwm = 1;
+    bool ok = true;
+    const int ncell = A.ncell;
+    // every pass tests at least one new cell, so a walk ends within ncell passes
+    int guard = ncell + 1;
+    __syncwarp();
+    while (top > 0) {
+        if (--guard < 0) { ok = false; break; }
+        // pop whole child ranges from the top while they fit in 32 lanes
+        int avail = min(top, 32);
+        int e = (lane < avail) ? stack[top - 1 - lane] : 0;
+        int cnt = e & 15;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        unsigned fit = __ballot_sync(0xffffffffu, lane < avail && incl <= 32);
+        int k = __popc(fit);
+        int total = __shfl_sync(0xffffffffu, incl, k - 1);
+        __syncwarp();
+        if (lane < k) {
+            int b = incl - cnt, c0 = e >> 4;
+            for (int t = 0; t < cnt; t++) lane_cell[b + t] = c0 + t;
+        }
+        top -= k;
+        __syncwarp();
+        int c = (lane < total) ? lane_cell[lane] : -1;
+        __syncwarp();
+        if (__any_sync(0xffffffffu, c >= ncell)) { ok = false; break; }
+
+        bool accept = false, leaf = false, open = false;
+        int4 lk = make_int4(0, 0, 0, 0);
+        if (c >= 0) {
+            int4 b = __ldg(&A.cbox[c]);
+            int side = 1 << (kMaxLevel - b.w);
+            long long gx = gap1(blo[0], bhi[0], b.x, b.x + side);
+            long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
+            long long gz = gap1(blo[2], bhi[2], b.z, b.z + side);
+            unsigned long long d2 = (unsigned long long)(gx * gx + gy * gy + gz * gz);
+            accept = d2 >= A.mac.thr[b.w];
+            if (!accept) {
+                lk = __ldg(&A.clink[c]);
+                leaf = (lk.x == lk.y);
+                open = !leaf;
+            }
+        }
+        // links must stay inside the tree (a violated bound ends the walk with an error)
+        bool bad = (open && (lk.x <= c || lk.y > ncell || lk.y - lk.x > 8)) ||
+                   (leaf && (lk.z < 0 || lk.w > A.n || lk.z > lk.w));
+        if (__any_sync(0xffffffffu, bad)) { ok = false; break; }
+        // opened internal cells: push their child ranges
+        unsigned om = __ballot_sync(0xffffffffu, open);
+        if (open) {
+            int p = top + __popc(om & lt);
+            if (p < kStackCap) stack[p] = (lk.x << 4) | (lk.y - lk.x);
+        }
+        top += __popc(om);
+        hwm = max(hwm, top);
+        if (top > kStackCap) { ok = false; break; }
+        // accepted cells: stage their multipole records
+        unsigned am = __ballot_sync(0xffffffffu, accept);
+        if (accept) {
+            int p = nm + __popc(am & lt);
+            m2p[3 * p + 0] = __ldg(&A.cmom[3 * c + 0]);
+            if (QUAD) {
+                m2p[3 * p + 1] = __ldg(&A.cmom[3 * c + 1]);
+                m2p[3 * p + 2] = __ldg(&A.cmom[3 * c + 2]);
+            }
+        }
+        nm += __popc(am);
+        nm2p += __popc(am);
+        // opened leaves: stage their stars
+        unsigned lm = __ballot_sync(0xffffffffu, leaf);
+        while (lm) {
+            int src = __ffs(lm) - 1;
+            lm &= lm - 1;
+            int f = __shfl_sync(0xffffffffu, lk.z, src);
+            int end = __shfl_sync(0xffffffffu, lk.w, src);
+            for (int o = f; o < end; o += 32) {
+                int cc = min(32, end - o);
+                if (lane < cc) p2p[np + lane] = __ldg(&A.pos[o + lane]);
+                np += cc;
+                np2p += cc;
+                if (np >= T) {
+                    __syncwarp();
+                    eval_p2p<SOFT>(p2p, T, xi, yi, zi, eps2, acc);
+                    __syncwarp();
+                    if (lane < np - T) p2p[lane] = p2p[T + lane];
+                    np -= T;
+                    __syncwarp();
+                }
+            }
+        }
+        if (nm >= T) {
+            __syncwarp();
+            eval_m2p<QUAD>(m2p, T, xi, yi, zi, eps2, acc);
+            __syncwarp();
+            if (lane < nm - T) {
+                m2p[3 * lane] = m2p[3 * (T + lane)];
+                m2p[3 * lane + 1] = m2p[3 * (T + lane) + 1];
+                m2p[3 * lane + 2] = m2p[3 * (T + lane) + 2];
+            }
+            nm -= T;
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    if (ok) {
+        if (np > 0) eval_p2p<SOFT>(p2p, np, xi, yi, zi, eps2, acc);
+        if (nm > 0) eval_m2p<QUAD>(m2p, nm, xi, yi, zi, eps2, acc);
+    }
+    __syncwarp();
+    if (lane == 0) atomicMax(&A.st->stack_hwm, hwm);
+    return ok;
+}
+
+// Unsoftened-or-softened direct terms of the extra particles on one target.
+__device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float yi, float zi, float ei, int skip,
+                                            Acc &acc) {
+    float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+    for (int k = 0; k < A.n_extra; k++) {
+        if (k == skip) continue;
+        float ek = A.xeps[k];
+        float e = (ei == 0.f || ek == 0.f) ? 0.f : fmaxf(ei, ek);
+        float dx = A.xyzm[4 * k] - xi, dy = A.xyzm[4 * k + 1] - yi, dz = A.xyzm[4 * k + 2] - zi;
+        float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e * e)));
+        if (r2 <= 0.f) continue;
+        float rinv = rsqrtf(r2);
+        float mr = A.xyzm[4 * k + 3] * rinv;
+        float mr3 = mr * rinv * rinv;
+        tx = fmaf(mr3, dx, tx); ty = fmaf(mr3, dy, ty); tz = fmaf(mr3, dz, tz);
+        tp -= mr;
+    }
+    nadd(acc.ax, acc.cx, tx); nadd(acc.ay, acc.cy, ty); nadd(acc.az, acc.cz, tz); nadd(acc.ph, acc.cp, tp);
+}
+
+template <bool SOFT, bool QUAD>
+__global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    char *wsm = smem + wib * warp_smem_bytes(A.tile);
+    const int ngroup = A.st->ngroup;
+    A.ncell = min(A.st->ncell, A.cell_cap);
+    unsigned long long np2p = 0, nm2p = 0;
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(&A.st->next_group, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ngroup) break;
+        int4 grp = __ldg(&A.groups[g]);
+        if (grp.z < 0 || grp.z >= A.ncell || grp.x < 0 || grp.y < 1 || grp.y > 32 || grp.x + grp.y > A.n) {
+            if (lane == 0) latch_err(A.st, kErrStack);
+            continue;
+        }
+        int4 b = __ldg(&A.cbox[grp.z]);
+        int side = 1 << (kMaxLevel - b.w);
+        int blo[3] = {b.x, b.y, b.z}, bhi[3] = {b.x + side, b.y + side, b.z + side};
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool has = lane < grp.y;
+        if (has) p = __ldg(&A.pos[grp.x + lane]);
+        Acc acc = {};
+        unsigned long long a2 = 0, a3 = 0;
+        bool ok = walk_group<SOFT, QUAD>(A, wsm, blo, bhi, p.x, p.y, p.z, A.eps2, acc, a2, a3);
+        if (!ok) {
+            if (lane == 0) latch_err(A.st, kErrStack);
+            continue;
+        }
+        np2p += a2 * (unsigned long long)grp.y;
+        nm2p += a3 * (unsigned long long)grp.y;
+        if (has) {
+            // the star's own pair was evaluated at r = 0: remove its -m/eps
+            if (SOFT) acc.ph += p.w * rsqrtf(A.eps2);
+            if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, acc);
+            int o = A.perm[grp.x + lane];
+            A.ax[o] = acc.ax + acc.cx;
+            A.ay[o] = acc.ay + acc.cy;
+            A.az[o] = acc.az + acc.cz;
+            A.pot[o] = acc.ph + acc.cp;
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&A.st->n_p2p, np2p);
+        atomicAdd(&A.st->n_m2p, nm2p);
+    }
+}
+
+// One warp per extra particle (lane 0 holds it); its group box is its own
+// grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited to +-2^23.
+template <bool QUAD>
+__global__ void __launch_bounds__(32) walk_extra_k(WalkArgs A) {
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x;
+    float xi = A.xyzm[4 * k], yi = A.xyzm[4 * k + 1], zi = A.xyzm[4 * k + 2];
+    A.ncell = min(A.st->ncell, A.cell_cap);
+    float ek = A.xeps[k];
+    float e = (ek == 0.f || A.eps_star == 0.f) ? 0.f : fmaxf(ek, A.eps_star);
+    int blo[3], bhi[3];
+    const float pv[3] = {xi, yi, zi};
+    for (int a = 0; a < 3; a++) {
+        double q = floor(__dmul_rn(__dsub_rn((double)pv[a], A.st->bounds[a]), A.st->bounds[4]));
+        q = fmin(fmax(q, -8388608.0), 8388608.0);
+        blo[a] = (int)q;
+        bhi[a] = (int)q + 1;
+    }
+    Acc acc = {};
+    unsigned long long a2 = 0, a3 = 0;
+    bool ok = true;
+    if (A.st->ncell > 0) ok = walk_group<false, QUAD>(A, smem, blo, bhi, xi, yi, zi, e * e, acc, a2, a3);
+    if (!ok) {
+        if (lane == 0) latch_err(A.st, kErrStack);
+        return;
+    }
+    if (lane == 0) {
+        extra_terms(A, xi, yi, zi, ek, k, acc);
+        A.xout[4 * k] = acc.ax + acc.cx;
+        A.xout[4 * k + 1] = acc.ay + acc.cy;
+        A.xout[4 * k + 2] = acc.az + acc.cz;
+        A.xout[4 * k + 3] = acc.ph + acc.cp;
+    }
+}
+
+// MAC thresholds: the smallest integer D with fl(theta^2 * D) > s^2 (FP64,
+// theta^2 = theta * theta rounded once), so that "d^2 >= thr" is exactly the
+// FP64 test s^2 < theta^2 d^2 on integer grid distances.
+static MacTable mac_table(float theta) {
+    MacTable t;
+    double th2 = (double)theta * (double)theta;
+    for (int l = 0; l < kLevels; l++) {
+        double s2 = ldexp(1.0, 2 * (kMaxLevel - l));
+        if (!(th2 > 0.0)) { t.thr[l] = ~0ull; continue; }
+        unsigned long long lo = 0, hi = 1ull << 53;  // th2 * 2^53 > s2 for th2 >= 2^-11
+        if (!(th2 * (double)hi > s2)) { t.thr[l] = ~0ull; continue; }
+        while (lo < hi) {
+            unsigned long long mid = lo + (hi - lo) / 2;
+            if (th2 * (double)mid > s2) hi = mid; else lo = mid + 1;
+        }
+        t.thr[l] = lo;
+    }
+    return t;
+}
+
+template <bool SOFT, bool QUAD>
+static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
+    size_t smem = warp_smem_bytes(A.tile) * kWalkWarps;
+    auto kern = walk_tree_k<SOFT, QUAD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    int grid = max(1, per_sm) * c->num_sms;
+    kern<<<grid, kWalkWarps * 32, smem, s>>>(A);
+    count_launch(c);
+    return cudaGetLastError();
+}
+
+rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
+                    float *ax, float *ay, float *az, float *pot, float *xout, cudaStream_t s) {
+    Workspace &w = c->w;
+    WalkArgs A;
+    A.pos = w.pos;
+    A.cbox = w.cbox;
+    A.clink = reinterpret_cast<const int4 *>(w.clink);
+    A.cmom = w.cmom;
+    A.groups = w.groups;
+    A.perm = w.perm;
+    A.st = w.st;
+    A.ncell = 0;         // set on the device side: see walk kernels
+    A.n = (int)c->n;
+    A.cell_cap = (int)c->cell_cap;
+    A.mac = mac_table(theta);
+    A.eps2 = eps_star * eps_star;
+    A.eps_star = eps_star;
+    A.tile = c->cfg.tile;
+    A.n_extra = n_extra;
+    A.xyzm = xyzm;
+    A.xeps = xeps;
+    A.ax = ax; A.ay = ay; A.az = az; A.pot = pot;
+    A.xout = xout;
+    // reset the work counter and statistics (next_group, n_p2p, n_m2p)
+    cudaError_t e = cudaMemsetAsync(&w.st->next_group, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&w.st->n_p2p, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_check(c, e, "walk reset");
+    const bool quad = c->cfg.quadrupole != 0;
+    if (c->n > 0) {
+        if (eps_star > 0.f) e = quad ? launch_walk<true, true>(c, A, s) : launch_walk<true, false>(c, A, s);
+        else e = quad ? launch_walk<false, true>(c, A, s) : launch_walk<false, false>(c, A, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "walk launch");
+    }
+    if (n_extra > 0) {
+        size_t smem = warp_smem_bytes(A.tile);
+        auto kern = quad ? walk_extra_k<true> : walk_extra_k<false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            kern<<<n_extra, 32, smem, s>>>(A);
+            count_launch(c);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return cuda_check(c, e, "extra walk launch");
+    }
+    return RV_OK;
+}
+
+}  // namespace rv

@@ -1,0 +1,313 @@
+"""Thin Python binding of librv (the C ABI in include/rv.h).
+
+Only argument marshalling lives here: every step of the tree-gravity path
+runs in librv's CUDA kernels. PyTorch provides device memory (the workspace
+and the user's arrays) and streams. There is no CPU fallback: if librv.so is
+missing or no GPU is present, loading fails with an error.
+
+The ``rv_*`` functions mirror the C entry points one to one; ``Context`` and
+``System`` are small conveniences over them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build_lib
+
+_LOCK = threading.Lock()
+_LIB = None
+
+RV_OK, RV_E_INVAL, RV_E_CUDA, RV_E_WORKSPACE, RV_E_STACK, RV_E_TIMEOUT, RV_E_NOTBUILT = range(7)
+STATUS_NAMES = ["RV_OK", "RV_E_INVAL", "RV_E_CUDA", "RV_E_WORKSPACE", "RV_E_STACK", "RV_E_TIMEOUT", "RV_E_NOTBUILT"]
+EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", "rv_set_workspace", "rv_build_tree",
+           "rv_tree_forces", "rv_perturber_forces", "rv_system_forces", "rv_kdk_step", "rv_energy",
+           "rv_select_perturbers", "rv_get_tree", "rv_walk_stats", "rv_sync_status", "rv_launch_count",
+           "rv_last_error"]
+
+
+class RvError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class rv_config(C.Structure):
+    _fields_ = [("theta", C.c_float), ("eps_star", C.c_float), ("n_leaf", C.c_int32), ("group", C.c_int32),
+                ("quadrupole", C.c_int32), ("tile", C.c_int32)]
+
+
+class rv_tree_view(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ncell", C.c_int64), ("ngroup", C.c_int64), ("keys", C.c_void_p),
+                ("perm", C.c_void_p), ("pos", C.c_void_p), ("cbox", C.c_void_p), ("clink", C.c_void_p),
+                ("cmom", C.c_void_p), ("cparent", C.c_void_p), ("groups", C.c_void_p), ("bounds", C.c_void_p)]
+
+
+class rv_system(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("vx", C.c_void_p),
+                ("vy", C.c_void_p), ("vz", C.c_void_p), ("m", C.c_void_p), ("ax", C.c_void_p), ("ay", C.c_void_p),
+                ("az", C.c_void_p), ("pot", C.c_void_p), ("n_chain", C.c_int32), ("chain_m", C.c_void_p),
+                ("chain_x", C.c_void_p), ("chain_v", C.c_void_p), ("chain_a", C.c_void_p),
+                ("chain_pot", C.c_void_p), ("pert_mode", C.c_int32), ("pert_radius", C.c_float),
+                ("pert_k", C.c_int32)]
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librv.so (building it first if asked). Raises if it cannot."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = build_lib.LIB
+            if build_if_missing and build_lib.stale():
+                build_lib.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"librv.so not found at {path}; run __graft_entry__.build()")
+            L = C.CDLL(path)
+            _declare(L)
+            _LIB = L
+    return _LIB
+
+
+def _declare(L):
+    vp, i64, i32, f32, f64 = C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_double
+    L.rv_default_config.argtypes = [C.POINTER(rv_config)]
+    L.rv_default_config.restype = None
+    L.rv_workspace_size.argtypes = [i64, C.POINTER(rv_config)]
+    L.rv_workspace_size.restype = C.c_size_t
+    L.rv_create.argtypes = [C.POINTER(vp), i64, C.POINTER(rv_config)]
+    L.rv_destroy.argtypes = [vp]
+    L.rv_destroy.restype = None
+    L.rv_set_workspace.argtypes = [vp, vp, C.c_size_t]
+    L.rv_build_tree.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.rv_tree_forces.argtypes = [vp, f32, f32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rv_perturber_forces.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rv_system_forces.argtypes = [vp, C.POINTER(rv_system), vp]
+    L.rv_kdk_step.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp]
+    L.rv_energy.argtypes = [vp, C.POINTER(rv_system), vp, vp]
+    L.rv_select_perturbers.argtypes = [vp, i64, vp, vp, vp, C.POINTER(C.c_float), i32, f32, i32, i32, vp, vp, vp]
+    L.rv_get_tree.argtypes = [vp, C.POINTER(rv_tree_view), vp]
+    L.rv_walk_stats.argtypes = [vp, C.POINTER(C.c_int64), vp]
+    L.rv_sync_status.argtypes = [vp, vp]
+    L.rv_launch_count.argtypes = [vp]
+    L.rv_launch_count.restype = C.c_int64
+    L.rv_last_error.argtypes = [vp]
+    L.rv_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("rv_default_config", "rv_workspace_size", "rv_destroy", "rv_last_error", "rv_launch_count"):
+            f.restype = C.c_int
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def default_config(**kw) -> rv_config:
+    cfg = rv_config()
+    load().rv_default_config(C.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def workspace_size(n_max: int, cfg: rv_config) -> int:
+    return int(load().rv_workspace_size(n_max, C.byref(cfg)))
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("librv takes CUDA tensors only")
+
+
+class Context:
+    """An rv_ctx with a torch-allocated workspace on the current device."""
+
+    def __init__(self, n_max: int, theta: float = 0.5, eps_star: float = 0.01, n_leaf: int = 16,
+                 group: int = 32, quadrupole: bool = True, tile: int = 64):
+        import torch
+        self.L = load()
+        self.cfg = default_config(theta=theta, eps_star=eps_star, n_leaf=n_leaf, group=group,
+                                  quadrupole=int(bool(quadrupole)), tile=tile)
+        self.n_max = int(n_max)
+        h = C.c_void_p()
+        st = self.L.rv_create(C.byref(h), self.n_max, C.byref(self.cfg))
+        if st != RV_OK:
+            raise RvError(st, "rv_create")
+        self.h = h
+        nbytes = workspace_size(self.n_max, self.cfg)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = (self.ws.data_ptr() + 255) & ~255
+        self._ws_off = base - self.ws.data_ptr()
+        self._check(self.L.rv_set_workspace(self.h, C.c_void_p(base), nbytes))
+        self.n = 0
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.rv_destroy(h)
+            self.h = None
+
+    def _check(self, st):
+        if st != RV_OK:
+            raise RvError(st, self.L.rv_last_error(self.h).decode())
+
+    def last_error(self) -> str:
+        return self.L.rv_last_error(self.h).decode()
+
+    def launch_count(self) -> int:
+        return int(self.L.rv_launch_count(self.h))
+
+    # --- tree ---
+    def build_tree(self, x, y, z, m, stream=None):
+        _need_cuda(x, y, z, m)
+        n = int(x.shape[0])
+        self._check(self.L.rv_build_tree(self.h, n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _stream(stream)))
+        self.n = n
+
+    def tree_forces(self, theta=None, eps_star=None, extra_xyzm=None, extra_eps=None, out=None, stream=None):
+        """Returns (ax, ay, az, pot[, extra_out (k,4)]) as new or given CUDA tensors."""
+        import torch
+        theta = self.cfg.theta if theta is None else theta
+        eps_star = self.cfg.eps_star if eps_star is None else eps_star
+        if out is None:
+            out = [torch.empty(self.n, dtype=torch.float32, device="cuda") for _ in range(4)]
+        k = 0 if extra_xyzm is None else int(extra_xyzm.shape[0])
+        xout = torch.empty((max(k, 1), 4), dtype=torch.float32, device="cuda") if k else None
+        _need_cuda(*out, extra_xyzm, extra_eps)
+        self._check(self.L.rv_tree_forces(self.h, float(theta), float(eps_star), k, _ptr(extra_xyzm),
+                                          _ptr(extra_eps), *[_ptr(o) for o in out], _ptr(xout), _stream(stream)))
+        return tuple(out) + ((xout[:k],) if k else ())
+
+    def tree_view(self, stream=None) -> dict:
+        """Copies of the last tree's arrays (as CUDA tensors)."""
+        import torch
+        v = rv_tree_view()
+        self._check(self.L.rv_get_tree(self.h, C.byref(v), _stream(stream)))
+        base = self.ws.data_ptr()
+
+        def view(ptr, count, dtype, width=1):
+            itemsize = torch.empty((), dtype=dtype).element_size()
+            off = ptr - base
+            nb = count * width * itemsize
+            return self.ws[off:off + nb].view(dtype).reshape(count, width).clone() if width > 1 else \
+                self.ws[off:off + nb].view(dtype).clone()
+
+        n, nc, ng = v.n, v.ncell, v.ngroup
+        return {
+            "n": n, "ncell": nc, "ngroup": ng,
+            "keys": view(v.keys, n, torch.int64),
+            "perm": view(v.perm, n, torch.int32),
+            "pos": view(v.pos, n, torch.float32, 4),
+            "cbox": view(v.cbox, nc, torch.int32, 4),
+            "clink": view(v.clink, nc, torch.int32, 4),
+            "cmom": view(v.cmom, 3 * nc, torch.float32, 4).reshape(nc, 12),
+            "cparent": view(v.cparent, nc, torch.int32),
+            "groups": view(v.groups, ng, torch.int32, 4),
+            "bounds": view(v.bounds, 5, torch.float64),
+        }
+
+    def walk_stats(self, stream=None):
+        out = (C.c_int64 * 2)()
+        self._check(self.L.rv_walk_stats(self.h, out, _stream(stream)))
+        return int(out[0]), int(out[1])
+
+    def sync_status(self, stream=None):
+        self._check(self.L.rv_sync_status(self.h, _stream(stream)))
+
+    # --- chain ---
+    def perturber_forces(self, chain_m, chain_x, pert_m, pert_x, stream=None):
+        """FP64 CUDA tensors in; dict of FP64 CUDA tensors out (see rv.h)."""
+        import torch
+        _need_cuda(chain_m, chain_x, pert_m, pert_x)
+        nch, npt = int(chain_m.shape[0]), int(pert_m.shape[0])
+        d = dict(a_pert=torch.zeros((max(npt, 1), 3), dtype=torch.float64, device="cuda"),
+                 pot_pert=torch.zeros(max(npt, 1), dtype=torch.float64, device="cuda"),
+                 a_chain=torch.zeros((nch, 3), dtype=torch.float64, device="cuda"),
+                 pot_chain=torch.zeros(nch, dtype=torch.float64, device="cuda"),
+                 out8=torch.zeros(16, dtype=torch.float64, device="cuda"))
+        self._check(self.L.rv_perturber_forces(self.h, nch, _ptr(chain_m), _ptr(chain_x), npt, _ptr(pert_m),
+                                               _ptr(pert_x), _ptr(d["a_pert"]), _ptr(d["pot_pert"]),
+                                               _ptr(d["a_chain"]), _ptr(d["pot_chain"]), _ptr(d["out8"]),
+                                               _stream(stream)))
+        d["a_pert"], d["pot_pert"] = d["a_pert"][:npt], d["pot_pert"][:npt]
+        return d
+
+    def select_perturbers(self, x, y, z, centre, mode, radius=0.0, k=0, cap=5000, stream=None):
+        import torch
+        _need_cuda(x, y, z)
+        idx = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        c3 = (C.c_float * 3)(*[float(v) for v in centre])
+        self._check(self.L.rv_select_perturbers(self.h, int(x.shape[0]), _ptr(x), _ptr(y), _ptr(z), c3, int(mode),
+                                                float(radius), int(k), int(cap), _ptr(idx), _ptr(cnt),
+                                                _stream(stream)))
+        return idx, cnt
+
+    def system_forces(self, sysobj, stream=None):
+        self._check(self.L.rv_system_forces(self.h, C.byref(sysobj.c()), _stream(stream)))
+
+    def kdk_step(self, sysobj, dt, nsteps=1, stream=None):
+        self._check(self.L.rv_kdk_step(self.h, C.byref(sysobj.c()), float(dt), int(nsteps), _stream(stream)))
+
+    def energy(self, sysobj, out=None, stream=None):
+        import torch
+        out = torch.zeros(10, dtype=torch.float64, device="cuda") if out is None else out
+        self._check(self.L.rv_energy(self.h, C.byref(sysobj.c()), _ptr(out), _stream(stream)))
+        return out
+
+
+class System:
+    """Device state of stars (FP32, caller order) and an optional chain (FP64)."""
+
+    def __init__(self, pos, vel, mass, chain_m=None, chain_x=None, chain_v=None, pert_mode=0, pert_radius=0.0,
+                 pert_k=0):
+        import torch
+        f32 = dict(dtype=torch.float32, device="cuda")
+        f64 = dict(dtype=torch.float64, device="cuda")
+        pos = torch.as_tensor(pos)
+        vel = torch.as_tensor(vel)
+        self.n = int(pos.shape[1])
+        self.x, self.y, self.z = (pos[a].to(**f32).contiguous() for a in range(3))
+        self.vx, self.vy, self.vz = (vel[a].to(**f32).contiguous() for a in range(3))
+        self.m = torch.as_tensor(mass).to(**f32).contiguous()
+        self.ax, self.ay, self.az, self.pot = (torch.zeros(self.n, **f32) for _ in range(4))
+        self.n_chain = 0 if chain_m is None else int(len(chain_m))
+        if self.n_chain:
+            self.chain_m = torch.as_tensor(chain_m).to(**f64).contiguous()
+            self.chain_x = torch.as_tensor(chain_x).to(**f64).reshape(-1).contiguous()
+            self.chain_v = torch.as_tensor(chain_v).to(**f64).reshape(-1).contiguous()
+            self.chain_a = torch.zeros(3 * self.n_chain, **f64)
+            self.chain_pot = torch.zeros(self.n_chain, **f64)
+        else:
+            self.chain_m = self.chain_x = self.chain_v = self.chain_a = self.chain_pot = None
+        self.pert_mode, self.pert_radius, self.pert_k = int(pert_mode), float(pert_radius), int(pert_k)
+        self._c = None
+
+    def c(self) -> rv_system:
+        s = rv_system()
+        s.n = self.n
+        for f in ("x", "y", "z", "vx", "vy", "vz", "m", "ax", "ay", "az", "pot"):
+            setattr(s, f, getattr(self, f).data_ptr())
+        s.n_chain = self.n_chain
+        for f in ("chain_m", "chain_x", "chain_v", "chain_a", "chain_pot"):
+            t = getattr(self, f)
+            setattr(s, f, t.data_ptr() if t is not None else None)
+        s.pert_mode, s.pert_radius, s.pert_k = self.pert_mode, self.pert_radius, self.pert_k
+        self._c = s
+        return s

@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI (no GPU needed): librv builds for sm_103a,
+loads, exports every entry point include/rv.h declares, and rejects bad
+arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rv_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1507_01009_gb300 import build_lib, rv
+    build_lib.build()
+    return rv.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    from paper_1507_01009_gb300 import rv
+    assert sorted(rv.EXPORTS) == _declared()
+
+
+def test_config_and_workspace_size(lib):
+    from paper_1507_01009_gb300 import rv
+    cfg = rv.default_config()
+    assert (cfg.n_leaf, cfg.group, cfg.quadrupole, cfg.tile) == (16, 32, 1, 64)
+    assert abs(cfg.theta - 0.5) < 1e-7
+    s1 = rv.workspace_size(1 << 20, cfg)
+    s2 = rv.workspace_size(1 << 21, cfg)
+    assert 0 < s1 < s2 < 2 * s1 + (1 << 20)
+    bad = rv.default_config(tile=48)
+    assert rv.workspace_size(1000, bad) == 0
+    bad = rv.default_config(group=33)
+    assert rv.workspace_size(1000, bad) == 0
+
+
+def test_create_rejects_bad_arguments(lib):
+    from paper_1507_01009_gb300 import rv
+    h = C.c_void_p()
+    cfg = rv.default_config(n_leaf=0)
+    assert lib.rv_create(C.byref(h), 100, C.byref(cfg)) == rv.RV_E_INVAL
+    cfg = rv.default_config()
+    assert lib.rv_create(C.byref(h), -1, C.byref(cfg)) == rv.RV_E_INVAL
+    assert lib.rv_build_tree(None, 0, None, None, None, None, None) == rv.RV_E_INVAL
+    assert lib.rv_last_error(None) == b"null context"

@@ -1,0 +1,397 @@
+"""GPU parity: librv (through its C ABI) against the CPU oracle on the same
+seeded inputs. Integer work (keys, permutation, topology, groups, perturber
+selection) must match bit for bit; forces must match the oracle tree at the
+same opening angle to a median relative error <= 1e-5 and a maximum <= 1e-4,
+and the FP64 direct sum at p99 <= 1e-3 (theta = 0.5, quadrupole)."""
+import math
+
+import numpy as np
+import pytest
+
+import ics
+import oracle
+from gpu_helpers import err_stats, gpu_cells_as_oracle, gpu_tree, hernquist32, sorted_groups, stars32, to_dev
+
+pytestmark = pytest.mark.gpu
+
+MED_TOL, MAX_TOL, P99_DIRECT = 1e-5, 1e-4, 1e-3
+
+
+@pytest.fixture(scope="module")
+def rvmod():
+    from paper_1507_01009_gb300 import rv
+    rv.load()
+    return rv
+
+
+def _ctx(rv, n, **kw):
+    return rv.Context(max(n, 1), **kw)
+
+
+def _inputs(kind, n, seed=0):
+    if kind == "hernquist":
+        return hernquist32(n, seed + n)
+    if kind == "plummer":
+        w = ics.plummer(n, seed + 1)
+        return stars32(w.pos, w.mass)
+    if kind == "coincident":
+        return np.full((3, n), 0.3, dtype=np.float32), np.full(n, 1.0 / n, dtype=np.float32)
+    if kind == "two_clusters":
+        g = ics.rng(seed + 7)
+        a = g.normal(0, 1e-3, (3, n // 2))
+        b = g.normal(0, 1e-3, (3, n - n // 2)) + 50.0
+        return stars32(np.concatenate([a, b], 1), np.full(n, 1.0 / n))
+    if kind == "ghosts":                                      # near-massless chain ghosts (Sect. 2)
+        p, m = hernquist32(n, seed + 3)
+        m = m.copy()
+        m[::5] = 1e-30
+        return p, m
+    raise ValueError(kind)
+
+
+TREE_CASES = [("hernquist", 1, 16, 32), ("hernquist", 2, 16, 32), ("hernquist", 3, 1, 1), ("hernquist", 7, 2, 4),
+              ("hernquist", 33, 16, 32), ("hernquist", 1000, 8, 32), ("hernquist", 4097, 16, 32),
+              ("hernquist", 65659, 16, 32), ("plummer", 4096, 16, 32), ("coincident", 100, 16, 32),
+              ("two_clusters", 3000, 16, 32), ("ghosts", 5000, 16, 32), ("hernquist", 20000, 32, 32),
+              ("hernquist", 20000, 4, 8)]
+
+
+@pytest.mark.parametrize("kind,n,n_leaf,G", TREE_CASES)
+def test_tree_bit_exact(rvmod, kind, n, n_leaf, G):
+    p32, m32 = _inputs(kind, n)
+    ctx = _ctx(rvmod, n, n_leaf=n_leaf, group=G)
+    gpu_tree(ctx, p32, m32)
+    v = ctx.tree_view()
+    ctx.sync_status()
+    T = oracle.Tree(p32, m32, n_leaf, G)
+    np.testing.assert_array_equal(v["bounds"].cpu().numpy(), np.array([*T.lo, T.L, T.scale]))
+    np.testing.assert_array_equal(v["keys"].cpu().numpy().view(np.uint64), T.key)
+    np.testing.assert_array_equal(v["perm"].cpu().numpy(), T.perm)
+    pos = v["pos"].cpu().numpy()
+    np.testing.assert_array_equal(pos[:, 0], p32[0][T.perm])
+    np.testing.assert_array_equal(pos[:, 3], m32[T.perm])
+    assert v["ncell"] == T.ncell
+    np.testing.assert_array_equal(gpu_cells_as_oracle(v), T.cells)
+    assert v["ngroup"] == T.ngroup
+    np.testing.assert_array_equal(sorted_groups(v["groups"].cpu().numpy()), sorted_groups(T.groups))
+
+
+def test_tiny_golden_tree_on_gpu(rvmod):
+    """The hand-derived five-point tree (tests/golden/tiny_tree.txt)."""
+    from test_oracle import _read_sections
+    g = _read_sections("tiny_tree.txt")
+    p32 = np.array(g["points"], dtype=np.float32).T
+    ctx = _ctx(rvmod, 5, n_leaf=2, group=2)
+    gpu_tree(ctx, p32, np.ones(5, np.float32))
+    v = ctx.tree_view()
+    np.testing.assert_array_equal(v["perm"].cpu().numpy(), np.array(g["perm"][0]))
+    np.testing.assert_array_equal(gpu_cells_as_oracle(v), np.array(g["cells"]))
+    np.testing.assert_array_equal(sorted_groups(v["groups"].cpu().numpy()), sorted_groups(g["groups"]))
+
+
+@pytest.mark.parametrize("kind,n", [("hernquist", 65659), ("plummer", 4096), ("ghosts", 5000), ("coincident", 100)])
+def test_moments(rvmod, kind, n):
+    """FP32 multipoles vs FP64 brute force per cell: mass to 1e-6 relative,
+    centre of mass to 1e-6 of the cell side, quadrupole to 1e-5 of M s^2."""
+    p32, m32 = _inputs(kind, n)
+    ctx = _ctx(rvmod, n)
+    gpu_tree(ctx, p32, m32)
+    v = ctx.tree_view()
+    T = oracle.Tree(p32, m32, 16, 32)
+    g = v["cmom"].cpu().numpy().astype(np.float64)
+    o = T.moments
+    side = T.L / 2 ** 21 * 2.0 ** (21 - T.cells[:, 0])
+    M = o[:, 0]
+    np.testing.assert_allclose(g[:, 0], M, rtol=1e-6, atol=1e-37)
+    scale = np.maximum(side, 1e-30)
+    assert np.all(np.abs(g[:, 1:4] - o[:, 1:4]).max(1) <= 1e-6 * scale + 2e-7 * np.abs(o[:, 1:4]).max(1))
+    gq = g[:, [4, 5, 6, 7, 8, 9]]
+    oq = o[:, 4:10]
+    qs = np.maximum(M * side * side, 1e-37)
+    assert np.all(np.abs(gq - oq).max(1) <= 1e-5 * qs)
+
+
+FORCE_CASES = [("plummer", 4096, 0.5, 0.01, 16, 32, 64, True), ("hernquist", 65659, 0.5, 0.005, 16, 32, 64, True),
+               ("hernquist", 65659, 0.7, 0.005, 8, 16, 32, True), ("hernquist", 30000, 0.5, 0.005, 16, 32, 128, False),
+               ("ghosts", 5000, 0.5, 0.005, 16, 32, 64, True), ("two_clusters", 3000, 0.6, 0.001, 4, 8, 64, True),
+               ("hernquist", 1000, 0.5, 0.0, 16, 32, 64, True)]
+
+
+@pytest.mark.parametrize("kind,n,theta,eps,n_leaf,G,tile,quad", FORCE_CASES)
+def test_forces_vs_oracle_tree(rvmod, kind, n, theta, eps, n_leaf, G, tile, quad):
+    p32, m32 = _inputs(kind, n)
+    eps = float(np.float32(eps))
+    ctx = _ctx(rvmod, n, theta=theta, eps_star=eps, n_leaf=n_leaf, group=G, tile=tile, quadrupole=quad)
+    gpu_tree(ctx, p32, m32)
+    ax, ay, az, pot = ctx.tree_forces()
+    ctx.sync_status()
+    a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)
+    p = pot.cpu().numpy().astype(np.float64)
+    T = oracle.Tree(p32, m32, n_leaf, G)
+    ao, po, _, _, cnt = T.forces(theta, eps, quad, counts=True)
+    med, p99, mx = err_stats(a, ao)
+    assert med <= MED_TOL and mx <= MAX_TOL, (med, p99, mx)
+    ep = np.abs(p - po) / np.abs(po)
+    assert np.median(ep) <= MED_TOL and ep.max() <= MAX_TOL
+    # identical opening decisions: same interaction counts (the GPU also counts each star's own pair)
+    n_p2p, n_m2p = ctx.walk_stats()
+    assert n_p2p == int(cnt[:, 0].sum()) + n
+    assert n_m2p == int(cnt[:, 1].sum())
+
+
+def test_forces_vs_direct_plummer(rvmod):
+    p32, m32 = _inputs("plummer", 4096)
+    ctx = _ctx(rvmod, 4096, theta=0.5, eps_star=0.01)
+    gpu_tree(ctx, p32, m32)
+    ax, ay, az, _ = ctx.tree_forces()
+    a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)
+    ad, _ = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), float(np.float32(0.01)))
+    _, p99, _ = err_stats(a, ad)
+    assert p99 <= P99_DIRECT
+
+
+def test_small_theta_is_direct_sum(rvmod):
+    p32, m32 = _inputs("hernquist", 3000)
+    ctx = _ctx(rvmod, 3000, theta=1e-3, eps_star=0.005)
+    gpu_tree(ctx, p32, m32)
+    ax, ay, az, pot = ctx.tree_forces()
+    a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)
+    ad, pd = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), float(np.float32(0.005)))
+    _, _, mx = err_stats(a, ad)
+    assert mx <= 1e-5
+    np.testing.assert_allclose(pot.cpu().numpy(), pd, rtol=1e-5)
+    assert ctx.walk_stats()[1] == 0
+
+
+def test_coincident_unsoftened_is_finite(rvmod):
+    p32, m32 = _inputs("coincident", 100)
+    ctx = _ctx(rvmod, 100, eps_star=0.0)
+    gpu_tree(ctx, p32, m32)
+    out = ctx.tree_forces()
+    ctx.sync_status()
+    for t in out:
+        assert np.all(np.isfinite(t.cpu().numpy())) and np.all(t.cpu().numpy() == 0)
+
+
+def test_empty_input(rvmod):
+    import torch
+    ctx = _ctx(rvmod, 16)
+    e = torch.empty(0, dtype=torch.float32, device="cuda")
+    ctx.build_tree(e, e, e, e)
+    out = ctx.tree_forces()
+    ctx.sync_status()
+    assert all(t.numel() == 0 for t in out)
+
+
+def test_forces_before_build_rejected(rvmod):
+    ctx = _ctx(rvmod, 16)
+    with pytest.raises(rvmod.RvError) as ei:
+        ctx.tree_forces()
+    assert ei.value.status == rvmod.RV_E_NOTBUILT
+
+
+def test_deterministic(rvmod):
+    p32, m32 = _inputs("hernquist", 65659)
+    ctx = _ctx(rvmod, 65659)
+    gpu_tree(ctx, p32, m32)
+    a1 = [t.cpu().numpy().copy() for t in ctx.tree_forces()]
+    gpu_tree(ctx, p32, m32)
+    a2 = [t.cpu().numpy().copy() for t in ctx.tree_forces()]
+    for u, w in zip(a1, a2):
+        np.testing.assert_array_equal(u, w)
+
+
+def test_extra_particle_vs_oracle(rvmod):
+    """An unsoftened centre-of-mass particle outside the tree (Sect. 2/3)."""
+    p32, m32 = _inputs("hernquist", 65659)
+    xp = np.array([[0.05], [-0.02], [0.01]], dtype=np.float32)
+    xm = np.array([0.01])
+    ctx = _ctx(rvmod, 65659, eps_star=0.005)
+    gpu_tree(ctx, p32, m32)
+    xyzm = to_dev(np.array([[xp[0, 0], xp[1, 0], xp[2, 0], xm[0]]], dtype=np.float32))
+    xeps = to_dev(np.zeros(1, np.float32))
+    ax, ay, az, pot, xo = ctx.tree_forces(extra_xyzm=xyzm, extra_eps=xeps)
+    a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)
+    T = oracle.Tree(p32, m32, 16, 32)
+    ao, po, xa, xpot = T.forces(0.5, float(np.float32(0.005)), True, xp, np.float32(xm).astype(np.float64), [0.0])
+    med, _, mx = err_stats(a, ao)
+    assert med <= MED_TOL and mx <= MAX_TOL
+    xo = xo.cpu().numpy().astype(np.float64)
+    assert oracle.rel_err(xo[:, :3].T, xa).max() <= MAX_TOL
+    assert abs(xo[0, 3] / xpot[0] - 1) <= MAX_TOL
+
+
+def test_perturber_forces_vs_oracle(rvmod):
+    import torch
+    b = ics.central_binary()
+    g = ics.rng(31)
+    px = g.normal(0, 0.01, (256, 3))
+    pm = np.full(256, 1.0 / (1 << 20))
+    ctx = _ctx(rvmod, 16)
+    d = ctx.perturber_forces(to_dev(b.mass), to_dev(b.pos), to_dev(pm), to_dev(px))
+    torch.cuda.synchronize()
+    o = oracle.perturber(b.mass, b.pos, pm, px)
+    np.testing.assert_allclose(d["a_pert"].cpu().numpy(), o["a_pert"], rtol=1e-11, atol=1e-11 * np.abs(o["a_pert"]).max())
+    np.testing.assert_allclose(d["pot_pert"].cpu().numpy(), o["pot_pert"], rtol=1e-11, atol=1e-11 * np.abs(o["pot_pert"]).max())
+    np.testing.assert_allclose(d["a_chain"].cpu().numpy(), o["a_chain"], rtol=1e-12)
+    np.testing.assert_allclose(d["pot_chain"].cpu().numpy(), o["pot_chain"], rtol=1e-12)
+    out8 = d["out8"].cpu().numpy()
+    np.testing.assert_allclose(out8[0:3], o["corr"], rtol=1e-12)
+    np.testing.assert_allclose(out8[3:6], o["sub"], rtol=1e-12)
+    np.testing.assert_allclose(out8[6:8], [o["corr_pot"], o["sub_pot"]], rtol=1e-12)
+    np.testing.assert_allclose(out8[8:12], [*o["com"], o["M"]], rtol=1e-15, atol=1e-18)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_perturber_selection_exact(rvmod, mode):
+    p32, m32 = _inputs("hernquist", 65659)
+    c = np.array([0.01, -0.005, 0.002], dtype=np.float32)
+    ctx = _ctx(rvmod, 65659)
+    x, y, z = (to_dev(p32[a]) for a in range(3))
+    if mode == 1:
+        r = np.float32(0.05)
+        idx, cnt = ctx.select_perturbers(x, y, z, c, 1, radius=r)
+        ref = oracle.radius(p32, c, np.float32(r * r))
+    else:
+        idx, cnt = ctx.select_perturbers(x, y, z, c, 2, k=256)
+        ref = oracle.knn(p32, c, 256)
+    ctx.sync_status()
+    k = int(cnt.item())
+    assert k == len(ref) and k > 0
+    np.testing.assert_array_equal(idx[:k].cpu().numpy(), ref)
+
+
+def _system(rvmod, w, ctx_n, **kw):
+    ch = w.chain
+    kwargs = {}
+    if ch is not None:
+        kwargs = dict(chain_m=ch.mass, chain_x=ch.pos, chain_v=ch.vel)
+    return rvmod.System(w.stars.pos, w.stars.vel, w.stars.mass, **kwargs, **kw)
+
+
+def _oracle_system_forces(w, p32, m32, theta, eps, sub=None, pert=None):
+    """Oracle forces of a star + chain system, following the same steps:
+    tree over stars with the chain centre of mass as an unsoftened extra
+    particle, then the resolved-chain corrections of the perturbers (Sect. 2)."""
+    ch = w.chain
+    T = oracle.Tree(p32, m32, 16, 32)
+    com = ch.com
+    M = ch.total_mass
+    xp = com.astype(np.float32).reshape(3, 1)
+    xm = np.array([np.float32(M)], dtype=np.float64)
+    ao, po, xa, xpot = T.forces(theta, eps, True, xp, xm, [0.0], targets=sub)
+    o = oracle.perturber(ch.mass, ch.pos, m32[pert].astype(np.float64), p32[:, pert].T.astype(np.float64))
+    return ao, po, xa, xpot, o
+
+
+def test_system_forces_hernquist_bh(rvmod):
+    """Stars + one SMBH (a chain of one member), perturbers within r = 0.02."""
+    import torch
+    w = ics.hernquist_bh_workload(1 << 16, seed=12)
+    w.chain.pos[0] = [0.02, 0.0, 0.0]                       # put it in the dense core: several perturbers
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    eps = float(np.float32(w.eps_star))
+    ctx = _ctx(rvmod, p32.shape[1], theta=0.5, eps_star=eps)
+    S = _system(rvmod, w, p32.shape[1], pert_mode=1, pert_radius=0.02)
+    ctx.system_forces(S)
+    ctx.sync_status()
+    com32 = w.chain.com.astype(np.float32)
+    pert = oracle.radius(p32, com32, np.float32(np.float32(0.02) * np.float32(0.02)))
+    assert len(pert) > 3
+    ao, po, xa, xpot, o = _oracle_system_forces(w, p32, m32, 0.5, eps, pert=pert)
+    ao[:, pert] += o["a_pert"].T
+    a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
+    med, _, mx = err_stats(a, ao)
+    assert med <= MED_TOL and mx <= MAX_TOL
+    # chain member: tree force on the CoM - perturbers' direct terms + per-member perturber pull
+    a_bh = xa[:, 0] - o["sub"] + o["a_chain"][0]
+    got = S.chain_a.cpu().numpy()[:3]
+    assert np.linalg.norm(got - a_bh) / np.linalg.norm(a_bh) <= MAX_TOL
+    # vs the FP64 direct sum over everything (stars softened, SMBH pairs unsoftened)
+    allp = np.concatenate([p32.astype(np.float64), w.chain.pos.T], 1)
+    allm = np.concatenate([m32.astype(np.float64), w.chain.mass])
+    epsv = np.concatenate([np.full(p32.shape[1], eps), [0.0]])
+    tg = ics.subsample(p32.shape[1], 2048, seed=5)
+    ad, _ = oracle.direct(allp, allm, epsv, targets=tg)
+    _, p99, _ = err_stats(a[:, tg], ad)
+    assert p99 <= P99_DIRECT
+
+
+def test_energy_reduction_vs_oracle(rvmod):
+    import torch
+    w = ics.hernquist_binary_workload(1 << 14, seed=8)
+    ctx = _ctx(rvmod, w.stars.n, eps_star=0.005)
+    S = _system(rvmod, w, w.stars.n, pert_mode=2, pert_k=64)
+    ctx.system_forces(S)
+    E = ctx.energy(S).cpu().numpy()
+    ctx.sync_status()
+    pos = np.concatenate([np.stack([t.cpu().numpy() for t in (S.x, S.y, S.z)]).astype(np.float64),
+                          S.chain_x.cpu().numpy().reshape(-1, 3).T], 1)
+    vel = np.concatenate([np.stack([t.cpu().numpy() for t in (S.vx, S.vy, S.vz)]).astype(np.float64),
+                          S.chain_v.cpu().numpy().reshape(-1, 3).T], 1)
+    m = np.concatenate([S.m.cpu().numpy().astype(np.float64), S.chain_m.cpu().numpy()])
+    pot = np.concatenate([S.pot.cpu().numpy().astype(np.float64), S.chain_pot.cpu().numpy()])
+    ref = oracle.energy(pos, vel, m, pot)
+    np.testing.assert_allclose(E[0], ref["ekin"], rtol=1e-12)
+    np.testing.assert_allclose(E[1], ref["epot"], rtol=1e-12)
+    np.testing.assert_allclose(E[3:6], ref["P"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(E[6:9], ref["L"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(E[9], m.sum(), rtol=1e-12)
+
+
+@pytest.mark.slow
+def test_kdk_plummer_100_steps(rvmod):
+    """Plummer N=4096, eps=0.01, theta=0.5, 100 KDK steps of 1e-3: GPU and
+    oracle (FP64 tree forces) both conserve energy to 1e-5 and their final
+    positions agree to 1e-4 relative."""
+    import torch
+    w = ics.plummer_workload()
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    eps = float(np.float32(0.01))
+    ctx = _ctx(rvmod, 4096, theta=0.5, eps_star=eps)
+    S = rvmod.System(p32, w.stars.vel.astype(np.float32), m32)
+    ctx.system_forces(S)
+    E0 = ctx.energy(S).cpu().numpy()[2]
+    ctx.kdk_step(S, 1e-3, 100)
+    E1 = ctx.energy(S).cpu().numpy()[2]
+    ctx.sync_status()
+    assert abs(E1 / E0 - 1) <= 1e-5
+
+    def f(x):
+        x32 = x.astype(np.float32)
+        return oracle.Tree(x32, m32, 16, 32).forces(0.5, eps)[0]
+
+    x0 = p32.astype(np.float64)
+    v0 = w.stars.vel.astype(np.float32).astype(np.float64)
+    xo, vo, _ = oracle.kdk(x0, v0, f(x0), 1e-3, f, 100)
+    xg = np.stack([t.cpu().numpy() for t in (S.x, S.y, S.z)]).astype(np.float64)
+    rel = np.linalg.norm(xg - xo, axis=0) / np.linalg.norm(xo, axis=0)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-4
+
+
+@pytest.mark.slow
+def test_full_size_hernquist_bh_sampled(rvmod):
+    """The 2^20-star Hernquist + SMBH workload in the benchmark's launch
+    configuration: sampled stars against the oracle tree (same theta) and the
+    FP64 direct sum over all 2^20 + 1 bodies."""
+    w = ics.hernquist_bh_workload(1 << 20, seed=2)
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    eps = float(np.float32(w.eps_star))
+    ctx = _ctx(rvmod, p32.shape[1], theta=0.5, eps_star=eps)
+    S = _system(rvmod, w, p32.shape[1], pert_mode=1, pert_radius=0.02)
+    ctx.system_forces(S)
+    ctx.sync_status()
+    a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
+    tg = ics.subsample(p32.shape[1], 512, seed=9)
+    com32 = w.chain.com.astype(np.float32)
+    pert = oracle.radius(p32, com32, np.float32(np.float32(0.02) * np.float32(0.02)))
+    ao, _, _, _, o = _oracle_system_forces(w, p32, m32, 0.5, eps, sub=tg, pert=pert)
+    ao[:, pert] += o["a_pert"].T
+    med, _, mx = err_stats(a[:, tg], ao[:, tg])
+    assert med <= MED_TOL and mx <= MAX_TOL
+    allp = np.concatenate([p32.astype(np.float64), w.chain.pos.T], 1)
+    allm = np.concatenate([m32.astype(np.float64), w.chain.mass])
+    epsv = np.concatenate([np.full(p32.shape[1], eps), [0.0]])
+    ad, _ = oracle.direct(allp, allm, epsv, targets=tg)
+    _, p99, _ = err_stats(a[:, tg], ad)
+    assert p99 <= P99_DIRECT
