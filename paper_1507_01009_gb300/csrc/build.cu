@@ -532,8 +532,10 @@ __global__ void groups_k(const int *clink, const int *gofs, int G, int64_t cap, 
 // from its children in child order, so the result does not depend on timing.
 // FP32, accumulated relative to the cell's geometric centre.
 // ---------------------------------------------------------------------------
+// Moments are stored relative to the cell's geometric centre c0 (geo_centre):
+// (M, com - c0), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0).
 struct Mom {
-    float M, cx, cy, cz, q[6];  // q: xx, yy, zz, xy, xz, yz
+    float M, cx, cy, cz, q[6];  // cx..cz: centre of mass minus c0; q: xx, yy, zz, xy, xz, yz
 };
 
 __device__ __forceinline__ void store_mom(float4 *cmom, int c, const Mom &m) {
@@ -542,12 +544,7 @@ __device__ __forceinline__ void store_mom(float4 *cmom, int c, const Mom &m) {
     cmom[3 * c + 2] = make_float4(m.q[4], m.q[5], 0.f, 0.f);
 }
 
-__device__ __forceinline__ void geo_centre(const int4 b, const float lo[3], float unit, float g[3]) {
-    float half = 0.5f * (float)(1 << (kMaxLevel - b.w));
-    g[0] = lo[0] + ((float)b.x + half) * unit;
-    g[1] = lo[1] + ((float)b.y + half) * unit;
-    g[2] = lo[2] + ((float)b.z + half) * unit;
-}
+
 
 __device__ __forceinline__ void add_q(float q[6], float m, float dx, float dy, float dz) {
     float d2 = dx * dx + dy * dy + dz * dz;
@@ -580,13 +577,11 @@ __global__ void moments_k(int64_t n, const float4 *pos, const int4 *cbox, const 
             sz += p.w * (p.z - g[2]);
         }
         if (m.M > 0.f) {
-            m.cx = g[0] + sx / m.M; m.cy = g[1] + sy / m.M; m.cz = g[2] + sz / m.M;
+            m.cx = sx / m.M; m.cy = sy / m.M; m.cz = sz / m.M;
             for (int j = lk.z; j < lk.w; j++) {
                 float4 p = pos[j];
-                add_q(m.q, p.w, p.x - m.cx, p.y - m.cy, p.z - m.cz);
+                add_q(m.q, p.w, (p.x - g[0]) - m.cx, (p.y - g[1]) - m.cy, (p.z - g[2]) - m.cz);
             }
-        } else {
-            m.cx = g[0]; m.cy = g[1]; m.cz = g[2];
         }
         store_mom(cmom, c, m);
         // climb while this thread is the last child to arrive (at most 21 levels)
@@ -607,22 +602,25 @@ __global__ void moments_k(int64_t n, const float4 *pos, const int4 *cbox, const 
             float px = 0.f, py = 0.f, pz = 0.f;
             for (int ch = pl.x; ch < pl.y; ch++) {
                 float4 a = __ldcg(&cmom[3 * ch]);
+                float cg[3];
+                geo_centre(cbox[ch], lo, unit, cg);
                 P.M += a.x;
-                px += a.x * (a.y - pg[0]);
-                py += a.x * (a.z - pg[1]);
-                pz += a.x * (a.w - pg[2]);
+                px += a.x * ((cg[0] - pg[0]) + a.y);
+                py += a.x * ((cg[1] - pg[1]) + a.z);
+                pz += a.x * ((cg[2] - pg[2]) + a.w);
             }
             if (P.M > 0.f) {
-                P.cx = pg[0] + px / P.M; P.cy = pg[1] + py / P.M; P.cz = pg[2] + pz / P.M;
+                P.cx = px / P.M; P.cy = py / P.M; P.cz = pz / P.M;
                 for (int ch = pl.x; ch < pl.y; ch++) {
                     float4 a = __ldcg(&cmom[3 * ch]);
                     float4 b = __ldcg(&cmom[3 * ch + 1]);
                     float4 e = __ldcg(&cmom[3 * ch + 2]);
+                    float cg[3];
+                    geo_centre(cbox[ch], lo, unit, cg);
                     P.q[0] += b.x; P.q[1] += b.y; P.q[2] += b.z; P.q[3] += b.w; P.q[4] += e.x; P.q[5] += e.y;
-                    add_q(P.q, a.x, a.y - P.cx, a.z - P.cy, a.w - P.cz);
+                    add_q(P.q, a.x, ((cg[0] - pg[0]) + a.y) - P.cx, ((cg[1] - pg[1]) + a.z) - P.cy,
+                          ((cg[2] - pg[2]) + a.w) - P.cz);
                 }
-            } else {
-                P.cx = pg[0]; P.cy = pg[1]; P.cz = pg[2];
             }
             store_mom(cmom, p, P);
             cur = p;

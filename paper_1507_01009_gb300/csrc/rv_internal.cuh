@@ -141,4 +141,14 @@ __device__ __forceinline__ void nadd(float &s, float &c, float x) {
 
 __host__ __device__ __forceinline__ int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Geometric centre of the grid box b = (ox, oy, oz, level) in FP32:
+// lo + (o + side/2) * unit, every operation rounded once, so that the tree
+// build and the walk get the same value. (o + side/2 is exact in FP32.)
+__device__ __forceinline__ void geo_centre(const int4 b, const float lo[3], float unit, float g[3]) {
+    float half = __int_as_float((127 + kMaxLevel - 1 - b.w) << 23);  // 2^(20 - level)
+    g[0] = __fadd_rn(lo[0], __fmul_rn(__fadd_rn((float)b.x, half), unit));
+    g[1] = __fadd_rn(lo[1], __fmul_rn(__fadd_rn((float)b.y, half), unit));
+    g[2] = __fadd_rn(lo[2], __fmul_rn(__fadd_rn((float)b.z, half), unit));
+}
+
 }  // namespace rv

@@ -35,6 +35,7 @@ struct WalkArgs {
     DevState *st;
     int ncell;           // cells of the tree (bounded by the workspace)
     int cell_cap;
+    float lo[3], unit;   // bounding-cube corner and grid unit (FP32)
     int n;               // stars of the tree
     MacTable mac;
     float eps2;          // star-star and star-cell softening^2
@@ -122,9 +123,15 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 }
 
 // Walks the tree for one group; returns false if the stack overflowed.
+// Positions in the walk are relative to g, the geometric centre of the
+// group's box: targets and staged sources are shifted once, cell centres of
+// mass are (cell centre - g) + (centre of mass - cell centre). Differences of
+// nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
+// any distance from the origin.
 template <bool SOFT, bool QUAD>
-__device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3], float xi, float yi, float zi,
-                           float eps2, Acc &acc, unsigned long long &np2p, unsigned long long &nm2p) {
+__device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3], const float g[3], float xi,
+                           float yi, float zi, float eps2, Acc &acc, unsigned long long &np2p,
+                           unsigned long long &nm2p) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
     int *stack = reinterpret_cast<int *>(wsm);
@@ -168,8 +175,9 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
 
         bool accept = false, leaf = false, open = false;
         int4 lk = make_int4(0, 0, 0, 0);
+        int4 b = make_int4(0, 0, 0, 0);
         if (c >= 0) {
-            int4 b = __ldg(&A.cbox[c]);
+            b = __ldg(&A.cbox[c]);
             int side = 1 << (kMaxLevel - b.w);
             long long gx = gap1(blo[0], bhi[0], b.x, b.x + side);
             long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
@@ -199,7 +207,10 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
         unsigned am = __ballot_sync(0xffffffffu, accept);
         if (accept) {
             int p = nm + __popc(am & lt);
-            m2p[3 * p + 0] = __ldg(&A.cmom[3 * c + 0]);
+            float4 r0 = __ldg(&A.cmom[3 * c + 0]);
+            float c0[3];
+            geo_centre(b, A.lo, A.unit, c0);
+            m2p[3 * p + 0] = make_float4(r0.x, (c0[0] - g[0]) + r0.y, (c0[1] - g[1]) + r0.z, (c0[2] - g[2]) + r0.w);
             if (QUAD) {
                 m2p[3 * p + 1] = __ldg(&A.cmom[3 * c + 1]);
                 m2p[3 * p + 2] = __ldg(&A.cmom[3 * c + 2]);
@@ -216,7 +227,10 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
             int end = __shfl_sync(0xffffffffu, lk.w, src);
             for (int o = f; o < end; o += 32) {
                 int cc = min(32, end - o);
-                if (lane < cc) p2p[np + lane] = __ldg(&A.pos[o + lane]);
+                if (lane < cc) {
+                    float4 s = __ldg(&A.pos[o + lane]);
+                    p2p[np + lane] = make_float4(s.x - g[0], s.y - g[1], s.z - g[2], s.w);
+                }
                 np += cc;
                 np2p += cc;
                 if (np >= T) {
@@ -279,13 +293,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
     char *wsm = smem + wib * warp_smem_bytes(A.tile);
     const int ngroup = A.st->ngroup;
     A.ncell = min(A.st->ncell, A.cell_cap);
+    A.lo[0] = (float)A.st->bounds[0]; A.lo[1] = (float)A.st->bounds[1]; A.lo[2] = (float)A.st->bounds[2];
+    A.unit = (float)(A.st->bounds[3] / 2097152.0);
     unsigned long long np2p = 0, nm2p = 0;
     while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(&A.st->next_group, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= ngroup) break;
-        int4 grp = __ldg(&A.groups[g]);
+        int gi = 0;
+        if (lane == 0) gi = atomicAdd(&A.st->next_group, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= ngroup) break;
+        int4 grp = __ldg(&A.groups[gi]);
         if (grp.z < 0 || grp.z >= A.ncell || grp.x < 0 || grp.y < 1 || grp.y > 32 || grp.x + grp.y > A.n) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
@@ -293,12 +309,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
         int4 b = __ldg(&A.cbox[grp.z]);
         int side = 1 << (kMaxLevel - b.w);
         int blo[3] = {b.x, b.y, b.z}, bhi[3] = {b.x + side, b.y + side, b.z + side};
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        float g[3];
+        geo_centre(b, A.lo, A.unit, g);
+        float4 p = make_float4(g[0], g[1], g[2], 0.f);
         bool has = lane < grp.y;
         if (has) p = __ldg(&A.pos[grp.x + lane]);
         Acc acc = {};
         unsigned long long a2 = 0, a3 = 0;
-        bool ok = walk_group<SOFT, QUAD>(A, wsm, blo, bhi, p.x, p.y, p.z, A.eps2, acc, a2, a3);
+        bool ok = walk_group<SOFT, QUAD>(A, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], A.eps2, acc, a2,
+                                         a3);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
@@ -331,6 +350,8 @@ __global__ void __launch_bounds__(32) walk_extra_k(WalkArgs A) {
     const int k = blockIdx.x;
     float xi = A.xyzm[4 * k], yi = A.xyzm[4 * k + 1], zi = A.xyzm[4 * k + 2];
     A.ncell = min(A.st->ncell, A.cell_cap);
+    A.lo[0] = (float)A.st->bounds[0]; A.lo[1] = (float)A.st->bounds[1]; A.lo[2] = (float)A.st->bounds[2];
+    A.unit = (float)(A.st->bounds[3] / 2097152.0);
     float ek = A.xeps[k];
     float e = (ek == 0.f || A.eps_star == 0.f) ? 0.f : fmaxf(ek, A.eps_star);
     int blo[3], bhi[3];
@@ -344,7 +365,10 @@ __global__ void __launch_bounds__(32) walk_extra_k(WalkArgs A) {
     Acc acc = {};
     unsigned long long a2 = 0, a3 = 0;
     bool ok = true;
-    if (A.st->ncell > 0) ok = walk_group<false, QUAD>(A, smem, blo, bhi, xi, yi, zi, e * e, acc, a2, a3);
+    float g[3];
+    geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), A.lo, A.unit, g);
+    if (A.ncell > 0)
+        ok = walk_group<false, QUAD>(A, smem, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], e * e, acc, a2, a3);
     if (!ok) {
         if (lane == 0) latch_err(A.st, kErrStack);
         return;

@@ -51,3 +51,23 @@ def hernquist32(n, seed):
 def err_stats(a, ref):
     e = oracle.rel_err(a, ref)
     return oracle.percentile(e, 0.5), oracle.percentile(e, 0.99), float(e.max())
+
+
+def gpu_cell_centres(view):
+    """Geometric cell centres in FP32, computed as librv does:
+    lo + (o + side/2) * unit with each operation rounded once."""
+    b = view["bounds"].cpu().numpy()
+    cb = view["cbox"].cpu().numpy()
+    lo = b[:3].astype(np.float32)
+    unit = np.float32(b[3] / 2097152.0)
+    half = (2.0 ** (20 - cb[:, 3].astype(np.float64))).astype(np.float32)
+    out = np.empty((cb.shape[0], 3), dtype=np.float32)
+    for a in range(3):
+        out[:, a] = lo[a] + (cb[:, a].astype(np.float32) + half) * unit
+    return out
+
+
+def gpu_com(view):
+    """Absolute centres of mass (FP64) from the GPU's centre-relative records."""
+    g = view["cmom"].cpu().numpy().astype(np.float64)
+    return gpu_cell_centres(view).astype(np.float64) + g[:, 1:4]
