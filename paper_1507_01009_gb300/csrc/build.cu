@@ -150,15 +150,21 @@ __global__ void bounds_partial_k(int64_t n, const float *x, const float *y, cons
 }
 
 // min per axis; L = max_a (max_a - min_a) with FP64 differences; scale = 2^21 / L.
+// One warp: lanes stride over the block partials, then a shuffle reduction
+// (min and max are exact, so the order does not matter).
 __global__ void bounds_final_k(int nb, const float *part, DevState *st) {
-    if (threadIdx.x != 0) return;
-    float lo[3], hi[3];
-    for (int a = 0; a < 3; a++) { lo[a] = part[a]; hi[a] = part[3 + a]; }
-    for (int b = 1; b < nb; b++)
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nb; b += 32)
         for (int a = 0; a < 3; a++) {
             lo[a] = fminf(lo[a], part[6 * b + a]);
             hi[a] = fmaxf(hi[a], part[6 * b + 3 + a]);
         }
+    for (int a = 0; a < 3; a++)
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    if (threadIdx.x != 0) return;
     double L = 0.0;
     for (int a = 0; a < 3; a++) {
         double e = __dsub_rn((double)hi[a], (double)lo[a]);

@@ -370,19 +370,20 @@ rv_status kdk(rv_ctx *c, rv_system *sys, double dt, int nsteps, cudaStream_t s) 
 // FP64 totals: fixed grid, fixed per-thread striding, fixed tree reductions
 // ---------------------------------------------------------------------------
 constexpr int kRedBlocks = 256;
-constexpr int kRedQ = 8;  // ekin, epot, P(3), L(3)
+constexpr int kRedQ = 9;  // ekin, epot, P(3), L(3), mass
 
 __global__ void __launch_bounds__(256) energy_partial_k(int64_t n, const float *x, const float *y, const float *z,
                                                         const float *vx, const float *vy, const float *vz,
                                                         const float *m, const float *pot, double *part) {
     __shared__ double sm[kRedQ][256];
-    double q[kRedQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double q[kRedQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)kRedBlocks * 256) {
         double mi = m[i], X = x[i], Y = y[i], Z = z[i], U = vx[i], V = vy[i], W = vz[i];
         q[0] += 0.5 * mi * (U * U + V * V + W * W);
         q[1] += 0.5 * mi * (double)pot[i];
         q[2] += mi * U; q[3] += mi * V; q[4] += mi * W;
         q[5] += mi * (Y * W - Z * V); q[6] += mi * (Z * U - X * W); q[7] += mi * (X * V - Y * U);
+        q[8] += mi;
     }
     for (int a = 0; a < kRedQ; a++) sm[a][threadIdx.x] = q[a];
     __syncthreads();
@@ -398,22 +399,17 @@ __global__ void __launch_bounds__(256) energy_final_k(const double *part, int64_
                                                       const double *cm, const double *cx, const double *cv,
                                                       const double *cpot, double *out) {
     __shared__ double sm[kRedQ][256];
-    __shared__ double msum[256];
     for (int a = 0; a < kRedQ; a++) sm[a][threadIdx.x] = part[kRedQ * threadIdx.x + a];
-    double ms = 0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) ms += (double)m[i];
-    msum[threadIdx.x] = ms;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
+        if ((int)threadIdx.x < o)
             for (int a = 0; a < kRedQ; a++) sm[a][threadIdx.x] += sm[a][threadIdx.x + o];
-            msum[threadIdx.x] += msum[threadIdx.x + o];
-        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double q[kRedQ], M = msum[0];
+        double q[kRedQ];
         for (int a = 0; a < kRedQ; a++) q[a] = sm[a][0];
+        double M = q[8];
         for (int k = 0; k < n_ch; k++) {
             double mk = cm[k];
             const double *X = cx + 3 * k, *V = cv + 3 * k;

@@ -1,13 +1,17 @@
 // walk.cu -- Barnes-Hut tree walk and interaction evaluation (FP32).
 //
-// One warp walks the tree for one group of up to 32 consecutive stars (one
-// star per lane). Cells are tested 32 at a time, one per lane, under the
-// box-box opening test; accepted cells are staged in shared memory as
-// multipole records, opened leaves stage their stars, opened internal cells
-// push their child range on a per-warp stack. Whenever a staged list holds a
-// full tile, every lane evaluates the tile against its own star with
-// broadcast shared-memory reads, adds the tile's sum to its running total
-// with Neumaier compensation, and the walk continues.
+// One warp walks the tree for one group of up to 32 consecutive stars. Cells
+// are tested 32 at a time, one per lane, under the box-box opening test;
+// accepted cells are staged in shared memory as multipole records, opened
+// leaves stage their stars, opened internal cells push their child range on
+// a per-warp stack. Whenever a staged list holds a full tile, the warp
+// evaluates it: each star of the group is served by k = floor(32 / s) lanes
+// (s = stars in the group), lane t + i s taking list entries i, i + k, ...
+// with broadcast shared-memory reads; tile sums are added to running totals
+// with Neumaier compensation, and the k partial totals of a star are
+// combined in lane order at the end. Particles outside the tree (a chain's
+// centre of mass) are walked by the same kernel as one-star groups before the
+// tree's own groups.
 //
 // Interactions (G = 1, Sect. 3 Plummer softening; multipoles about the cell's
 // centre of mass, Sect. 1):
@@ -17,6 +21,8 @@
 //                      phi -= M / rho + (r.Q.r) / (2 rho^5).
 // Flops per interaction in this source (add/mul 1, FMA 2, rsqrt 1):
 //   star-star 20, cell (monopole + quadrupole) 54, cell (monopole) 18.
+#include <algorithm>
+
 #include "rv_internal.cuh"
 
 namespace rv {
@@ -29,13 +35,11 @@ struct WalkArgs {
     const float4 *pos;   // sorted (x, y, z, m)
     const int4 *cbox;
     const int4 *clink;   // (child first, child end, first star, end star)
-    const float4 *cmom;
+    const float4 *cmom;  // relative to the cell's geometric centre
     const int4 *groups;
     const int *perm;
     DevState *st;
-    int ncell;           // cells of the tree (bounded by the workspace)
     int cell_cap;
-    float lo[3], unit;   // bounding-cube corner and grid unit (FP32)
     int n;               // stars of the tree
     MacTable mac;
     float eps2;          // star-star and star-cell softening^2
@@ -53,17 +57,34 @@ __host__ __device__ inline size_t warp_smem_bytes(int tile) {
     return (size_t)kStackCap * 4 + 32 * 4 + (size_t)(tile + 32) * 48 + (size_t)(tile + 32) * 16;
 }
 
+// Values of the last build read from device state at kernel start.
+struct TreeGeo {
+    int ncell;           // cells of the tree (at most the workspace capacity)
+    float lo[3], unit;   // bounding-cube corner and grid unit in FP32
+};
+
+__device__ __forceinline__ TreeGeo tree_geo(const WalkArgs &A) {
+    TreeGeo t;
+    t.ncell = min(A.st->ncell, A.cell_cap);
+    t.lo[0] = (float)A.st->bounds[0];
+    t.lo[1] = (float)A.st->bounds[1];
+    t.lo[2] = (float)A.st->bounds[2];
+    t.unit = (float)(A.st->bounds[3] / 2097152.0);
+    return t;
+}
+
 struct Acc {
     float ax, ay, az, ph;      // running sums
     float cx, cy, cz, cp;      // Neumaier compensation
 };
 
+// This lane's share of a staged list: entries j0, j0 + k, ... below cnt.
 template <bool SOFT>
-__device__ __forceinline__ void eval_p2p(const float4 *src, int cnt, float xi, float yi, float zi, float eps2,
-                                         Acc &A) {
+__device__ __forceinline__ void eval_p2p(const float4 *src, int cnt, int j0, int k, float xi, float yi, float zi,
+                                         float eps2, Acc &A) {
     float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
 #pragma unroll 4
-    for (int j = 0; j < cnt; j++) {
+    for (int j = j0; j < cnt; j += k) {
         float4 s = src[j];
         float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
         float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
@@ -80,19 +101,18 @@ __device__ __forceinline__ void eval_p2p(const float4 *src, int cnt, float xi, f
 }
 
 template <bool QUAD>
-__device__ __forceinline__ void eval_m2p(const float4 *src, int cnt, float xi, float yi, float zi, float eps2,
-                                         Acc &A) {
+__device__ __forceinline__ void eval_m2p(const float4 *src, int cnt, int j0, int k, float xi, float yi, float zi,
+                                         float eps2, Acc &A) {
     float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
 #pragma unroll 2
-    for (int j = 0; j < cnt; j++) {
+    for (int j = j0; j < cnt; j += k) {
         float4 a = src[3 * j];
         float rx = xi - a.y, ry = yi - a.z, rz = zi - a.w;
         float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
         // r > 0: an accepted cell's box is separated from the group's box
         float rinv = rsqrtf(r2);
-        float rinv2 = rinv * rinv;
-        float mr = a.x * rinv;
-        float mr3 = mr * rinv2;
+        float u = rinv * rinv;
+        float rinv3 = rinv * u;
         if (QUAD) {
             float4 b = src[3 * j + 1];
             float4 e = src[3 * j + 2];
@@ -101,18 +121,19 @@ __device__ __forceinline__ void eval_m2p(const float4 *src, int cnt, float xi, f
             float qy = fmaf(b.w, rx, fmaf(b.y, ry, e.y * rz));
             float qz = fmaf(e.x, rx, fmaf(e.y, ry, b.z * rz));
             float rqr = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
-            float rinv5 = rinv * (rinv2 * rinv2);
-            float rinv7 = rinv5 * rinv2;
-            float A1 = fmaf(-2.5f * rqr, rinv7, -mr3);
-            tx = fmaf(A1, rx, fmaf(rinv5, qx, tx));
-            ty = fmaf(A1, ry, fmaf(rinv5, qy, ty));
-            tz = fmaf(A1, rz, fmaf(rinv5, qz, tz));
-            tp -= fmaf(0.5f * rqr, rinv5, mr);
+            float w = rqr * (u * u);                  // (r.Q.r) / rho^4
+            float rinv5 = rinv3 * u;
+            float B = -rinv3 * fmaf(2.5f, w, a.x);    // -(M + 5/2 w) / rho^3
+            tx = fmaf(B, rx, fmaf(rinv5, qx, tx));
+            ty = fmaf(B, ry, fmaf(rinv5, qy, ty));
+            tz = fmaf(B, rz, fmaf(rinv5, qz, tz));
+            tp = fmaf(-rinv, fmaf(0.5f, w, a.x), tp); // -(M + w/2) / rho
         } else {
+            float mr3 = a.x * rinv3;
             tx = fmaf(-mr3, rx, tx);
             ty = fmaf(-mr3, ry, ty);
             tz = fmaf(-mr3, rz, tz);
-            tp -= mr;
+            tp = fmaf(-a.x, rinv, tp);
         }
     }
     nadd(A.ax, A.cx, tx); nadd(A.ay, A.cy, ty); nadd(A.az, A.cz, tz); nadd(A.ph, A.cp, tp);
@@ -122,16 +143,17 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
     return (clo >= bhi) ? clo - bhi : ((blo >= chi) ? blo - chi : 0);
 }
 
-// Walks the tree for one group; returns false if the stack overflowed.
+// Walks the tree for one group; returns false if a bound was violated.
 // Positions in the walk are relative to g, the geometric centre of the
 // group's box: targets and staged sources are shifted once, cell centres of
 // mass are (cell centre - g) + (centre of mass - cell centre). Differences of
 // nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
 // any distance from the origin.
 template <bool SOFT, bool QUAD>
-__device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3], const float g[3], float xi,
-                           float yi, float zi, float eps2, Acc &acc, unsigned long long &np2p,
-                           unsigned long long &nm2p) {
+__device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, char *wsm, const int blo[3],
+                                           const int bhi[3], const float g[3], float xi, float yi, float zi, int j0,
+                                           int k, float eps2, Acc &acc, unsigned long long &np2p,
+                                           unsigned long long &nm2p) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
     int *stack = reinterpret_cast<int *>(wsm);
@@ -139,11 +161,11 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
     float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 32);
     float4 *p2p = m2p + 3 * (T + 32);
     const unsigned lt = lanemask_lt();
+    const int ncell = G.ncell;
 
     if (lane == 0) stack[0] = (0 << 4) | 1;  // root: a range of one cell starting at 0
     int top = 1, nm = 0, np = 0, hwm = 1;
     bool ok = true;
-    const int ncell = A.ncell;
     // every pass tests at least one new cell, so a walk ends within ncell passes
     int guard = ncell + 1;
     __syncwarp();
@@ -160,14 +182,14 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
             if (lane >= o) incl += y;
         }
         unsigned fit = __ballot_sync(0xffffffffu, lane < avail && incl <= 32);
-        int k = __popc(fit);
-        int total = __shfl_sync(0xffffffffu, incl, k - 1);
+        int kk = __popc(fit);
+        int total = __shfl_sync(0xffffffffu, incl, kk - 1);
         __syncwarp();
-        if (lane < k) {
+        if (lane < kk) {
             int b = incl - cnt, c0 = e >> 4;
             for (int t = 0; t < cnt; t++) lane_cell[b + t] = c0 + t;
         }
-        top -= k;
+        top -= kk;
         __syncwarp();
         int c = (lane < total) ? lane_cell[lane] : -1;
         __syncwarp();
@@ -203,13 +225,13 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
         top += __popc(om);
         hwm = max(hwm, top);
         if (top > kStackCap) { ok = false; break; }
-        // accepted cells: stage their multipole records
+        // accepted cells: stage their multipole records, centre of mass relative to g
         unsigned am = __ballot_sync(0xffffffffu, accept);
         if (accept) {
             int p = nm + __popc(am & lt);
             float4 r0 = __ldg(&A.cmom[3 * c + 0]);
             float c0[3];
-            geo_centre(b, A.lo, A.unit, c0);
+            geo_centre(b, G.lo, G.unit, c0);
             m2p[3 * p + 0] = make_float4(r0.x, (c0[0] - g[0]) + r0.y, (c0[1] - g[1]) + r0.z, (c0[2] - g[2]) + r0.w);
             if (QUAD) {
                 m2p[3 * p + 1] = __ldg(&A.cmom[3 * c + 1]);
@@ -218,7 +240,7 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
         }
         nm += __popc(am);
         nm2p += __popc(am);
-        // opened leaves: stage their stars
+        // opened leaves: stage their stars relative to g
         unsigned lm = __ballot_sync(0xffffffffu, leaf);
         while (lm) {
             int src = __ffs(lm) - 1;
@@ -235,7 +257,7 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
                 np2p += cc;
                 if (np >= T) {
                     __syncwarp();
-                    eval_p2p<SOFT>(p2p, T, xi, yi, zi, eps2, acc);
+                    eval_p2p<SOFT>(p2p, T, j0, k, xi, yi, zi, eps2, acc);
                     __syncwarp();
                     if (lane < np - T) p2p[lane] = p2p[T + lane];
                     np -= T;
@@ -245,7 +267,7 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
         }
         if (nm >= T) {
             __syncwarp();
-            eval_m2p<QUAD>(m2p, T, xi, yi, zi, eps2, acc);
+            eval_m2p<QUAD>(m2p, T, j0, k, xi, yi, zi, eps2, acc);
             __syncwarp();
             if (lane < nm - T) {
                 m2p[3 * lane] = m2p[3 * (T + lane)];
@@ -258,15 +280,35 @@ __device__ bool walk_group(const WalkArgs &A, char *wsm, int blo[3], int bhi[3],
     }
     __syncwarp();
     if (ok) {
-        if (np > 0) eval_p2p<SOFT>(p2p, np, xi, yi, zi, eps2, acc);
-        if (nm > 0) eval_m2p<QUAD>(m2p, nm, xi, yi, zi, eps2, acc);
+        if (np > 0) eval_p2p<SOFT>(p2p, np, j0, k, xi, yi, zi, eps2, acc);
+        if (nm > 0) eval_m2p<QUAD>(m2p, nm, j0, k, xi, yi, zi, eps2, acc);
     }
     __syncwarp();
     if (lane == 0) atomicMax(&A.st->stack_hwm, hwm);
     return ok;
 }
 
-// Unsoftened-or-softened direct terms of the extra particles on one target.
+// Adds the partial totals of the k lanes serving a star (lanes t, t+s, ...)
+// into lane t, in lane order.
+__device__ __forceinline__ void combine_lanes(Acc &a, int s, int k) {
+    const int lane = threadIdx.x & 31;
+    float sx = a.ax, sy = a.ay, sz = a.az, sp = a.ph;
+    float cx = a.cx, cy = a.cy, cz = a.cz, cp = a.cp;
+    for (int i = 1; i < k; i++) {
+        int src = min(lane + i * s, 31);
+        float ox = __shfl_sync(0xffffffffu, a.ax, src), oy = __shfl_sync(0xffffffffu, a.ay, src);
+        float oz = __shfl_sync(0xffffffffu, a.az, src), op = __shfl_sync(0xffffffffu, a.ph, src);
+        float qx = __shfl_sync(0xffffffffu, a.cx, src), qy = __shfl_sync(0xffffffffu, a.cy, src);
+        float qz = __shfl_sync(0xffffffffu, a.cz, src), qp = __shfl_sync(0xffffffffu, a.cp, src);
+        nadd(sx, cx, ox); nadd(sy, cy, oy); nadd(sz, cz, oz); nadd(sp, cp, op);
+        cx += qx; cy += qy; cz += qz; cp += qp;
+    }
+    a.ax = sx; a.ay = sy; a.az = sz; a.ph = sp;
+    a.cx = cx; a.cy = cy; a.cz = cz; a.cp = cp;
+}
+
+// Direct terms of the extra particles on one target (pair softening rule of
+// Sect. 3: max(eps_i, eps_j), none if either is unsoftened), absolute FP32.
 __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float yi, float zi, float ei, int skip,
                                             Acc &acc) {
     float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
@@ -286,23 +328,61 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
     nadd(acc.ax, acc.cx, tx); nadd(acc.ay, acc.cy, ty); nadd(acc.az, acc.cz, tz); nadd(acc.ph, acc.cp, tp);
 }
 
+// Work items 0 .. n_extra-1 are the extra particles (one-star groups whose box
+// is their own grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited
+// to +-2^23); the tree's groups follow.
 template <bool SOFT, bool QUAD>
 __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     char *wsm = smem + wib * warp_smem_bytes(A.tile);
-    const int ngroup = A.st->ngroup;
-    A.ncell = min(A.st->ncell, A.cell_cap);
-    A.lo[0] = (float)A.st->bounds[0]; A.lo[1] = (float)A.st->bounds[1]; A.lo[2] = (float)A.st->bounds[2];
-    A.unit = (float)(A.st->bounds[3] / 2097152.0);
+    const int nitem = A.n_extra + A.st->ngroup;
+    const TreeGeo G = tree_geo(A);
     unsigned long long np2p = 0, nm2p = 0;
     while (true) {
         int gi = 0;
         if (lane == 0) gi = atomicAdd(&A.st->next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= ngroup) break;
-        int4 grp = __ldg(&A.groups[gi]);
-        if (grp.z < 0 || grp.z >= A.ncell || grp.x < 0 || grp.y < 1 || grp.y > 32 || grp.x + grp.y > A.n) {
+        if (gi >= nitem) break;
+        Acc acc = {};
+        unsigned long long a2 = 0, a3 = 0;
+        if (gi < A.n_extra) {
+            // ---- a particle outside the tree: 32 lanes share its interaction list
+            const int kx = gi;
+            float xi = A.xyzm[4 * kx], yi = A.xyzm[4 * kx + 1], zi = A.xyzm[4 * kx + 2];
+            float ek = A.xeps[kx];
+            float e = (ek == 0.f || A.eps_star == 0.f) ? 0.f : fmaxf(ek, A.eps_star);
+            int blo[3], bhi[3];
+            const float pv[3] = {xi, yi, zi};
+            for (int a = 0; a < 3; a++) {
+                double q = floor(__dmul_rn(__dsub_rn((double)pv[a], A.st->bounds[a]), A.st->bounds[4]));
+                q = fmin(fmax(q, -8388608.0), 8388608.0);
+                blo[a] = (int)q;
+                bhi[a] = (int)q + 1;
+            }
+            float g[3];
+            geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), G.lo, G.unit, g);
+            bool ok = true;
+            if (G.ncell > 0)
+                ok = walk_group<false, QUAD>(A, G, wsm, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], lane, 32,
+                                             e * e, acc, a2, a3);
+            if (!ok) {
+                if (lane == 0) latch_err(A.st, kErrStack);
+                continue;
+            }
+            combine_lanes(acc, 1, 32);
+            if (lane == 0) {
+                extra_terms(A, xi, yi, zi, ek, kx, acc);
+                A.xout[4 * kx] = acc.ax + acc.cx;
+                A.xout[4 * kx + 1] = acc.ay + acc.cy;
+                A.xout[4 * kx + 2] = acc.az + acc.cz;
+                A.xout[4 * kx + 3] = acc.ph + acc.cp;
+            }
+            continue;
+        }
+        // ---- a group of the tree
+        int4 grp = __ldg(&A.groups[gi - A.n_extra]);
+        if (grp.z < 0 || grp.z >= G.ncell || grp.x < 0 || grp.y < 1 || grp.y > 32 || grp.x + grp.y > A.n) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
         }
@@ -310,21 +390,21 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
         int side = 1 << (kMaxLevel - b.w);
         int blo[3] = {b.x, b.y, b.z}, bhi[3] = {b.x + side, b.y + side, b.z + side};
         float g[3];
-        geo_centre(b, A.lo, A.unit, g);
-        float4 p = make_float4(g[0], g[1], g[2], 0.f);
-        bool has = lane < grp.y;
-        if (has) p = __ldg(&A.pos[grp.x + lane]);
-        Acc acc = {};
-        unsigned long long a2 = 0, a3 = 0;
-        bool ok = walk_group<SOFT, QUAD>(A, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], A.eps2, acc, a2,
-                                         a3);
+        geo_centre(b, G.lo, G.unit, g);
+        const int s = grp.y, k = 32 / s;      // k lanes per star
+        const int t = lane % s, sub = lane / s;
+        const int j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k s take no list entries
+        float4 p = __ldg(&A.pos[grp.x + t]);
+        bool ok = walk_group<SOFT, QUAD>(A, G, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], j0, k,
+                                         A.eps2, acc, a2, a3);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
         }
-        np2p += a2 * (unsigned long long)grp.y;
-        nm2p += a3 * (unsigned long long)grp.y;
-        if (has) {
+        np2p += a2 * (unsigned long long)s;
+        nm2p += a3 * (unsigned long long)s;
+        combine_lanes(acc, s, k);
+        if (lane < s) {
             // the star's own pair was evaluated at r = 0: remove its -m/eps
             if (SOFT) acc.ph += p.w * rsqrtf(A.eps2);
             if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, acc);
@@ -341,47 +421,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
     }
 }
 
-// One warp per extra particle (lane 0 holds it); its group box is its own
-// grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited to +-2^23.
-template <bool QUAD>
-__global__ void __launch_bounds__(32) walk_extra_k(WalkArgs A) {
-    extern __shared__ __align__(16) char smem[];
-    const int lane = threadIdx.x & 31;
-    const int k = blockIdx.x;
-    float xi = A.xyzm[4 * k], yi = A.xyzm[4 * k + 1], zi = A.xyzm[4 * k + 2];
-    A.ncell = min(A.st->ncell, A.cell_cap);
-    A.lo[0] = (float)A.st->bounds[0]; A.lo[1] = (float)A.st->bounds[1]; A.lo[2] = (float)A.st->bounds[2];
-    A.unit = (float)(A.st->bounds[3] / 2097152.0);
-    float ek = A.xeps[k];
-    float e = (ek == 0.f || A.eps_star == 0.f) ? 0.f : fmaxf(ek, A.eps_star);
-    int blo[3], bhi[3];
-    const float pv[3] = {xi, yi, zi};
-    for (int a = 0; a < 3; a++) {
-        double q = floor(__dmul_rn(__dsub_rn((double)pv[a], A.st->bounds[a]), A.st->bounds[4]));
-        q = fmin(fmax(q, -8388608.0), 8388608.0);
-        blo[a] = (int)q;
-        bhi[a] = (int)q + 1;
-    }
-    Acc acc = {};
-    unsigned long long a2 = 0, a3 = 0;
-    bool ok = true;
-    float g[3];
-    geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), A.lo, A.unit, g);
-    if (A.ncell > 0)
-        ok = walk_group<false, QUAD>(A, smem, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], e * e, acc, a2, a3);
-    if (!ok) {
-        if (lane == 0) latch_err(A.st, kErrStack);
-        return;
-    }
-    if (lane == 0) {
-        extra_terms(A, xi, yi, zi, ek, k, acc);
-        A.xout[4 * k] = acc.ax + acc.cx;
-        A.xout[4 * k + 1] = acc.ay + acc.cy;
-        A.xout[4 * k + 2] = acc.az + acc.cz;
-        A.xout[4 * k + 3] = acc.ph + acc.cp;
-    }
-}
-
 // MAC thresholds: the smallest integer D with fl(theta^2 * D) > s^2 (FP64,
 // theta^2 = theta * theta rounded once), so that "d^2 >= thr" is exactly the
 // FP64 test s^2 < theta^2 d^2 on integer grid distances.
@@ -391,8 +430,8 @@ static MacTable mac_table(float theta) {
     for (int l = 0; l < kLevels; l++) {
         double s2 = ldexp(1.0, 2 * (kMaxLevel - l));
         if (!(th2 > 0.0)) { t.thr[l] = ~0ull; continue; }
-        unsigned long long lo = 0, hi = 1ull << 53;  // th2 * 2^53 > s2 for th2 >= 2^-11
-        if (!(th2 * (double)hi > s2)) { t.thr[l] = ~0ull; continue; }
+        unsigned long long lo = 0, hi = 1ull << 53;
+        if (!(th2 * (double)hi > s2)) { t.thr[l] = ~0ull; continue; }  // no grid distance can pass
         while (lo < hi) {
             unsigned long long mid = lo + (hi - lo) / 2;
             if (th2 * (double)mid > s2) hi = mid; else lo = mid + 1;
@@ -411,7 +450,7 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkWarps * 32, smem);
     if (e != cudaSuccess) return e;
-    int grid = max(1, per_sm) * c->num_sms;
+    int grid = std::max(1, per_sm) * c->num_sms;
     kern<<<grid, kWalkWarps * 32, smem, s>>>(A);
     count_launch(c);
     return cudaGetLastError();
@@ -428,9 +467,8 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.groups = w.groups;
     A.perm = w.perm;
     A.st = w.st;
-    A.ncell = 0;         // set on the device side: see walk kernels
-    A.n = (int)c->n;
     A.cell_cap = (int)c->cell_cap;
+    A.n = (int)c->n;
     A.mac = mac_table(theta);
     A.eps2 = eps_star * eps_star;
     A.eps_star = eps_star;
@@ -444,23 +482,11 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     cudaError_t e = cudaMemsetAsync(&w.st->next_group, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&w.st->n_p2p, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_check(c, e, "walk reset");
+    if (c->n == 0 && n_extra == 0) return RV_OK;
     const bool quad = c->cfg.quadrupole != 0;
-    if (c->n > 0) {
-        if (eps_star > 0.f) e = quad ? launch_walk<true, true>(c, A, s) : launch_walk<true, false>(c, A, s);
-        else e = quad ? launch_walk<false, true>(c, A, s) : launch_walk<false, false>(c, A, s);
-        if (e != cudaSuccess) return cuda_check(c, e, "walk launch");
-    }
-    if (n_extra > 0) {
-        size_t smem = warp_smem_bytes(A.tile);
-        auto kern = quad ? walk_extra_k<true> : walk_extra_k<false>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) {
-            kern<<<n_extra, 32, smem, s>>>(A);
-            count_launch(c);
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) return cuda_check(c, e, "extra walk launch");
-    }
+    if (eps_star > 0.f) e = quad ? launch_walk<true, true>(c, A, s) : launch_walk<true, false>(c, A, s);
+    else e = quad ? launch_walk<false, true>(c, A, s) : launch_walk<false, false>(c, A, s);
+    if (e != cudaSuccess) return cuda_check(c, e, "walk launch");
     return RV_OK;
 }
 
