@@ -44,7 +44,8 @@ typedef enum {
     RV_E_WORKSPACE = 3, /* workspace missing, too small, or the tree outgrew it */
     RV_E_STACK = 4,     /* a walk's traversal stack filled up (results invalid) */
     RV_E_TIMEOUT = 5,   /* reserved: a bounded device wait gave up */
-    RV_E_NOTBUILT = 6   /* forces asked before rv_build_tree */
+    RV_E_NOTBUILT = 6,  /* forces asked before rv_build_tree */
+    RV_E_TOO_LARGE = 7  /* input larger than a fixed-size internal buffer allows */
 } rv_status;
 
 typedef struct rv_ctx rv_ctx; /* opaque; owned by librv */
@@ -176,6 +177,32 @@ rv_status rv_energy(rv_ctx *ctx, const rv_system *sys, double *out, void *stream
 rv_status rv_select_perturbers(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
                                const float centre[3], int32_t mode, float radius, int32_t k, int32_t cap,
                                int32_t *idx, int32_t *count, void *stream);
+
+/* Radius perturber search that allocates nothing and needs no context.
+ * (The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- e.g. a chain integrator that looks for
+ * perturbers from inside its own step or from a host callback, or a host
+ * application that forbids device allocation after start-up.)
+ *
+ * Same result as rv_select_perturbers(mode 1): the indices of the stars
+ * whose FP32 squared distance to centre, ((dx*dx + dy*dy) + dz*dz) with every
+ * operation rounded once, is below radius*radius (one FP32 product), in
+ * ascending order; at most cap indices are written to device idx[cap] and
+ * min(total, cap) to device count[1].
+ *
+ * Scratch: a fixed 32 KiB device array inside librv (one count per block of
+ * 2048 stars), held by every GPU that loads the library until the process
+ * exits. Limit: n <= 16,777,216 stars; larger n returns RV_E_TOO_LARGE
+ * without launching anything. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. Every call overwrites the
+ * part of the array it uses before reading it, so no clearing is needed, but
+ * all calls share the one array: calls whose GPU work overlaps (different
+ * streams, or other host threads) race and may return wrong results. x, y, z
+ * are device FP32 [n]; centre is a host FP32 point; stream as elsewhere. */
+rv_status rv_select_radius_static(int64_t n, const float *x, const float *y, const float *z,
+                                  const float centre[3], float radius, int32_t cap, int32_t *idx,
+                                  int32_t *count, void *stream);
 
 /* Read-only views of the last tree (device pointers into the workspace,
  * valid until the next build). Synchronises `stream` to read the sizes.

@@ -19,12 +19,13 @@ from . import build_lib
 _LOCK = threading.Lock()
 _LIB = None
 
-RV_OK, RV_E_INVAL, RV_E_CUDA, RV_E_WORKSPACE, RV_E_STACK, RV_E_TIMEOUT, RV_E_NOTBUILT = range(7)
-STATUS_NAMES = ["RV_OK", "RV_E_INVAL", "RV_E_CUDA", "RV_E_WORKSPACE", "RV_E_STACK", "RV_E_TIMEOUT", "RV_E_NOTBUILT"]
+RV_OK, RV_E_INVAL, RV_E_CUDA, RV_E_WORKSPACE, RV_E_STACK, RV_E_TIMEOUT, RV_E_NOTBUILT, RV_E_TOO_LARGE = range(8)
+STATUS_NAMES = ["RV_OK", "RV_E_INVAL", "RV_E_CUDA", "RV_E_WORKSPACE", "RV_E_STACK", "RV_E_TIMEOUT", "RV_E_NOTBUILT",
+                "RV_E_TOO_LARGE"]
 EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", "rv_set_workspace", "rv_build_tree",
            "rv_tree_forces", "rv_perturber_forces", "rv_system_forces", "rv_kdk_step", "rv_energy",
-           "rv_select_perturbers", "rv_get_tree", "rv_walk_stats", "rv_sync_status", "rv_launch_count",
-           "rv_last_error"]
+           "rv_select_perturbers", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
+           "rv_launch_count", "rv_last_error"]
 
 
 class RvError(RuntimeError):
@@ -91,6 +92,7 @@ def _declare(L):
     L.rv_kdk_step.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp]
     L.rv_energy.argtypes = [vp, C.POINTER(rv_system), vp, vp]
     L.rv_select_perturbers.argtypes = [vp, i64, vp, vp, vp, C.POINTER(C.c_float), i32, f32, i32, i32, vp, vp, vp]
+    L.rv_select_radius_static.argtypes = [i64, vp, vp, vp, C.POINTER(C.c_float), f32, i32, vp, vp, vp]
     L.rv_get_tree.argtypes = [vp, C.POINTER(rv_tree_view), vp]
     L.rv_walk_stats.argtypes = [vp, C.POINTER(C.c_int64), vp]
     L.rv_sync_status.argtypes = [vp, vp]
@@ -133,6 +135,26 @@ def _need_cuda(*ts):
     for t in ts:
         if t is not None and not t.is_cuda:
             raise ValueError("librv takes CUDA tensors only")
+
+
+def select_radius_static(x, y, z, centre, radius, cap=5000, idx=None, count=None, stream=None):
+    """rv_select_radius_static: radius perturber search with no context and no
+    device allocation inside librv (its scratch is a fixed array in the
+    library). ``idx`` (int32 [cap]) and ``count`` (int32 [1]) may be passed in
+    by a caller that must not allocate either; otherwise they are created here.
+    Returns (idx, count)."""
+    import torch
+    _need_cuda(x, y, z, idx, count)
+    if idx is None:
+        idx = torch.empty(max(cap, 1), dtype=torch.int32, device=x.device)
+    if count is None:
+        count = torch.zeros(1, dtype=torch.int32, device=x.device)
+    c3 = (C.c_float * 3)(*[float(v) for v in centre])
+    st = load().rv_select_radius_static(int(x.shape[0]), _ptr(x), _ptr(y), _ptr(z), c3, float(radius), int(cap),
+                                         _ptr(idx), _ptr(count), _stream(stream))
+    if st != RV_OK:
+        raise RvError(st, "rv_select_radius_static")
+    return idx, count
 
 
 class Context:
