@@ -97,6 +97,14 @@ rv_status rv_set_workspace(rv_ctx *ctx, void *dev, size_t bytes);
 rv_status rv_build_tree(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
                         const float *m, void *stream);
 
+/* rv_build_tree for n_members independent members stored one after another
+ * (host offsets[n_members + 1], offsets[0] = 0, non-decreasing,
+ * offsets[n_members] = n <= n_max; 1 <= n_members <= 512). Every member gets
+ * its own bounding cube, keys and tree, exactly as if built alone; they
+ * share the launches. */
+rv_status rv_build_tree_members(rv_ctx *ctx, int32_t n_members, const int64_t *offsets, const float *x,
+                                const float *y, const float *z, const float *m, void *stream);
+
 /* Tree forces on all stars of the last build (G = 1, Sect. 3):
  *   a_i = sum_j m_j r_ij / (r_ij^2 + eps^2)^{3/2},  phi_i = -sum_j m_j (r^2+eps^2)^{-1/2}
  * over the other stars, with distant cells replaced by their multipoles
@@ -113,6 +121,14 @@ rv_status rv_build_tree(rv_ctx *ctx, int64_t n, const float *x, const float *y, 
 rv_status rv_tree_forces(rv_ctx *ctx, float theta, float eps_star, int32_t n_extra,
                          const float *extra_xyzm, const float *extra_eps, float *ax, float *ay,
                          float *az, float *pot, float *extra_out, void *stream);
+
+/* rv_tree_forces after rv_build_tree_members: each star feels only its own
+ * member's tree and the extra particles of its member; extra k belongs to
+ * member extra_member[k] (device int32 [n_extra]; NULL = member 0) and walks
+ * that member's tree. */
+rv_status rv_tree_forces_members(rv_ctx *ctx, float theta, float eps_star, int32_t n_extra,
+                                 const float *extra_xyzm, const float *extra_eps, const int32_t *extra_member,
+                                 float *ax, float *ay, float *az, float *pot, float *extra_out, void *stream);
 
 /* Unsoftened FP64 chain/perturber coupling (Sect. 2, Eq. 3). Chain members k
  * (n_ch <= 250; device chain_m[n_ch], chain_x[3 n_ch]) with centre of mass
@@ -133,21 +149,32 @@ rv_status rv_perturber_forces(rv_ctx *ctx, int32_t n_ch, const double *chain_m, 
                               double *pot_pert, double *a_chain, double *pot_chain, double *out8,
                               void *stream);
 
-/* A system advanced by rv_kdk_step: n stars (device FP32, caller order) and
- * at most one chain of n_chain members (device FP64; 0 = no chain).
- * Perturbers of the chain: pert_mode 1 = stars with FP32 squared distance to
- * the chain centre below pert_radius^2 (ascending index), 2 = the pert_k
- * nearest stars (ties by lower index); at most 5000. */
+/* A system advanced by rv_kdk_step: n stars (device FP32, caller order),
+ * split into n_members independent members (galaxy realisations that never
+ * interact) stored one after another: member k owns stars
+ * [member_offsets[k], member_offsets[k+1]) (host int64 [n_members + 1],
+ * offsets[0] = 0, offsets[n_members] = n; n_members <= 1 with
+ * member_offsets = NULL means one member of all n stars; at most 512
+ * members). Each member has its own tree and, if n_chain > 0, its own chain
+ * of n_chain members (device FP64, member-major: chain_m[n_members n_chain],
+ * chain_x/v/a[3 n_members n_chain], chain_pot[n_members n_chain]; at most
+ * 2048 chain members in total). Perturbers of a chain (stars of its own
+ * member): pert_mode 1 = FP32 squared distance to the chain centre below
+ * pert_radius^2 (ascending index), 2 = the pert_k nearest (ties by lower
+ * index); at most min(5000, 65536 / n_members) per member (overflow of a
+ * radius search is reported by rv_sync_status as RV_E_WORKSPACE). */
 typedef struct {
     int64_t n;
     float *x, *y, *z, *vx, *vy, *vz;
     const float *m;
     float *ax, *ay, *az, *pot; /* forces at the current positions */
     int32_t n_chain;
-    double *chain_m, *chain_x, *chain_v, *chain_a, *chain_pot; /* [n], [3n], [3n], [3n], [n] */
+    double *chain_m, *chain_x, *chain_v, *chain_a, *chain_pot;
     int32_t pert_mode;
     float pert_radius;
     int32_t pert_k;
+    int32_t n_members;
+    const int64_t *member_offsets;
 } rv_system;
 
 /* One full force evaluation of a system: tree build, perturber selection,
@@ -164,10 +191,21 @@ rv_status rv_system_forces(rv_ctx *ctx, rv_system *sys, void *stream);
  * rv_system_forces once first). */
 rv_status rv_kdk_step(rv_ctx *ctx, rv_system *sys, double dt, int32_t nsteps, void *stream);
 
-/* FP64 totals of a system, written to device out[10]: E_kin, E_pot, E_tot,
- * P (3), L (3), M. Stars: sum m v^2/2, sum m phi/2, sum m v, sum m x cross v;
- * chain members added in FP64 with their potential chain_pot. Deterministic
- * (fixed reduction order). */
+/* Like rv_kdk_step, but the step (and, if energy_out is not NULL, the
+ * rv_energy reduction into device energy_out[10 n_members] after it) is
+ * captured once into a CUDA graph and replayed nsteps times: no host work
+ * per step. The graph is rebuilt when the system's pointers, offsets, dt or
+ * energy_out change; rebuilding first runs rv_system_forces once (forces at
+ * the current positions, as the step expects). `stream` must be a created
+ * stream (not the legacy or per-thread default stream): RV_E_INVAL
+ * otherwise. */
+rv_status rv_kdk_step_graph(rv_ctx *ctx, rv_system *sys, double dt, int32_t nsteps, double *energy_out,
+                            void *stream);
+
+/* FP64 totals of each member of a system, written to device out[10 k ..] for
+ * member k: E_kin, E_pot, E_tot, P (3), L (3), M. Stars: sum m v^2/2,
+ * sum m phi/2, sum m v, sum m x cross v; chain members added in FP64 with
+ * their potential chain_pot. Deterministic (fixed reduction order). */
 rv_status rv_energy(rv_ctx *ctx, const rv_system *sys, double *out, void *stream);
 
 /* Perturber selection on its own (see rv_system): writes ascending indices

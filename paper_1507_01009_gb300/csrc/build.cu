@@ -119,9 +119,13 @@ rv_status exclusive_scan(rv_ctx *c, int *data, int64_t nmax, const int *d_len, i
 // ---------------------------------------------------------------------------
 // bounding cube
 // ---------------------------------------------------------------------------
-__global__ void bounds_partial_k(int64_t n, const float *x, const float *y, const float *z, float *part) {
+// Blocks (bx, m): member m's stars, strided by bpm blocks.
+__global__ void bounds_partial_k(const int64_t *moff, int bpm, const float *x, const float *y, const float *z,
+                                 float *part) {
+    const int m = blockIdx.y;
+    const int64_t s = moff[m], e = moff[m + 1];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = s + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (int64_t)bpm * blockDim.x) {
         float v[3] = {x[i], y[i], z[i]};
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -136,28 +140,28 @@ __global__ void bounds_partial_k(int64_t n, const float *x, const float *y, cons
             hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
         }
     }
-    __shared__ float s[8][6];
+    __shared__ float sh[8][6];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0)
-        for (int a = 0; a < 3; a++) { s[wid][a] = lo[a]; s[wid][3 + a] = hi[a]; }
+        for (int a = 0; a < 3; a++) { sh[wid][a] = lo[a]; sh[wid][3 + a] = hi[a]; }
     __syncthreads();
     if (threadIdx.x < 6) {
-        float r = s[0][threadIdx.x];
+        float r = sh[0][threadIdx.x];
         for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-            r = (threadIdx.x < 3) ? fminf(r, s[w][threadIdx.x]) : fmaxf(r, s[w][threadIdx.x]);
-        part[6 * blockIdx.x + threadIdx.x] = r;
+            r = (threadIdx.x < 3) ? fminf(r, sh[w][threadIdx.x]) : fmaxf(r, sh[w][threadIdx.x]);
+        part[6 * ((int64_t)m * bpm + blockIdx.x) + threadIdx.x] = r;
     }
 }
 
-// min per axis; L = max_a (max_a - min_a) with FP64 differences; scale = 2^21 / L.
-// One warp: lanes stride over the block partials, then a shuffle reduction
-// (min and max are exact, so the order does not matter).
-__global__ void bounds_final_k(int nb, const float *part, DevState *st) {
+// One warp per member: min per axis; L = max_a (max_a - min_a) with FP64
+// differences; scale = 2^21 / L (min and max are exact, so order is free).
+__global__ void bounds_final_k(int bpm, const float *part, double *mbounds, DevState *st) {
+    const int m = blockIdx.x;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = threadIdx.x; b < nb; b += 32)
+    for (int b = threadIdx.x; b < bpm; b += 32)
         for (int a = 0; a < 3; a++) {
-            lo[a] = fminf(lo[a], part[6 * b + a]);
-            hi[a] = fmaxf(hi[a], part[6 * b + 3 + a]);
+            lo[a] = fminf(lo[a], part[6 * ((int64_t)m * bpm + b) + a]);
+            hi[a] = fmaxf(hi[a], part[6 * ((int64_t)m * bpm + b) + 3 + a]);
         }
     for (int a = 0; a < 3; a++)
         for (int o = 16; o > 0; o >>= 1) {
@@ -165,14 +169,20 @@ __global__ void bounds_final_k(int nb, const float *part, DevState *st) {
             hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
         }
     if (threadIdx.x != 0) return;
+    double out[5];
     double L = 0.0;
     for (int a = 0; a < 3; a++) {
-        double e = __dsub_rn((double)hi[a], (double)lo[a]);
+        bool empty = !(lo[a] <= hi[a]);
+        double e = empty ? 0.0 : __dsub_rn((double)hi[a], (double)lo[a]);
         if (e > L) L = e;
-        st->bounds[a] = (double)lo[a];
+        out[a] = empty ? 0.0 : (double)lo[a];
     }
-    st->bounds[3] = L;
-    st->bounds[4] = (L > 0.0) ? __ddiv_rn(2097152.0, L) : 0.0;
+    out[3] = L;
+    out[4] = (L > 0.0) ? __ddiv_rn(2097152.0, L) : 0.0;
+    for (int k = 0; k < 5; k++) {
+        mbounds[5 * m + k] = out[k];
+        if (m == 0) st->bounds[k] = out[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -207,10 +217,13 @@ __device__ __forceinline__ uint32_t grid_coord(float v, double lo, double scale)
     return (uint32_t)f;
 }
 
-__global__ void keys_k(int64_t n, const float *x, const float *y, const float *z, const DevState *st,
-                       uint64_t *key) {
-    const double lx = st->bounds[0], ly = st->bounds[1], lz = st->bounds[2], sc = st->bounds[4];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+// Blocks (bx, m): member m's stars with member m's bounding cube.
+__global__ void keys_k(const int64_t *moff, int bpm, const float *x, const float *y, const float *z,
+                       const double *mbounds, uint64_t *key) {
+    const int m = blockIdx.y;
+    const double lx = mbounds[5 * m], ly = mbounds[5 * m + 1], lz = mbounds[5 * m + 2], sc = mbounds[5 * m + 4];
+    const int64_t s = moff[m], e = moff[m + 1];
+    for (int64_t i = s + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (int64_t)bpm * blockDim.x) {
         uint64_t k = spread3(grid_coord(x[i], lx, sc)) | (spread3(grid_coord(y[i], ly, sc)) << 1) |
                      (spread3(grid_coord(z[i], lz, sc)) << 2);
         key[i] = k;
@@ -220,8 +233,17 @@ __global__ void keys_k(int64_t n, const float *x, const float *y, const float *z
 // ---------------------------------------------------------------------------
 // stable LSD radix sort of (key, index), 9-bit digits
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSortThreads) sort_upsweep_k(int64_t n, const uint64_t *key, int shift,
-                                                               int ntiles, int *hist) {
+// Digit of element j: 9 key bits from `shift`, or (member pass) the member of
+// its caller index, which groups the members while keeping each one's order.
+__device__ __forceinline__ int sort_digit(const uint64_t *key, const int *idx, int64_t j, int shift,
+                                          const int64_t *moff, int M) {
+    if (moff) return member_of(moff, M, (int64_t)idx[j]);
+    return (int)((key[j] >> shift) & (kSortBins - 1));
+}
+
+__global__ void __launch_bounds__(kSortThreads) sort_upsweep_k(int64_t n, const uint64_t *key, const int *idx,
+                                                               int shift, const int64_t *moff, int M, int ntiles,
+                                                               int *hist) {
     __shared__ int h[kSortBins];
     for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) h[b] = 0;
     __syncthreads();
@@ -229,7 +251,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_upsweep_k(int64_t n, const 
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         int64_t j = base + k * kSortThreads + threadIdx.x;
-        if (j < n) atomicAdd(&h[(int)((key[j] >> shift) & (kSortBins - 1))], 1);
+        if (j < n) atomicAdd(&h[sort_digit(key, idx, j, shift, moff, M)], 1);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) hist[(int64_t)b * ntiles + blockIdx.x] = h[b];
@@ -239,9 +261,9 @@ __global__ void __launch_bounds__(kSortThreads) sort_upsweep_k(int64_t n, const 
 // counters), so the in-tile order is (warp, round, lane) = input order and the
 // sort is stable.
 __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, const uint64_t *key_in,
-                                                                 const int *idx_in, int shift, int ntiles,
-                                                                 const int *hist, uint64_t *key_out,
-                                                                 int *idx_out) {
+                                                                 const int *idx_in, int shift, const int64_t *moff,
+                                                                 int M, int ntiles, const int *hist,
+                                                                 uint64_t *key_out, int *idx_out) {
     constexpr int NW = kSortThreads / 32;
     __shared__ unsigned short cnt[NW][kSortBins];
     __shared__ int gbase[kSortBins];
@@ -258,7 +280,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, cons
         int64_t j = base + r * 32 + lane;
         bool ok = j < n;
         kk[r] = ok ? key_in[j] : 0ull;
-        int d = ok ? (int)((kk[r] >> shift) & (kSortBins - 1)) : kSortBins;
+        int d = ok ? sort_digit(key_in, idx_in, j, shift, moff, M) : kSortBins;
         digit[r] = d;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int before = (d < kSortBins) ? cnt[wid][d] : 0;
@@ -290,18 +312,22 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, cons
 }
 
 rv_status radix_sort(rv_ctx *c, int64_t n, int passes, uint64_t **keys, int **idx, bool identity_idx,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool member_pass) {
     if (n <= 0) return RV_OK;
     int ntiles = ceil_div(n, kSortTile);
     uint64_t *kin = c->w.key_a, *kout = c->w.key_b;
     int *iin = identity_idx ? nullptr : c->w.idx_a, *iout = c->w.idx_b;
-    for (int p = 0; p < passes; p++) {
+    const int M = c->n_members;
+    const int total = passes + ((member_pass && M > 1) ? 1 : 0);
+    for (int p = 0; p < total; p++) {
         int shift = p * kSortBits;
-        sort_upsweep_k<<<ntiles, kSortThreads, 0, s>>>(n, kin, shift, ntiles, c->w.hist);
+        const int64_t *moff = (p == passes) ? c->w.moff : nullptr;  // last pass: members
+        sort_upsweep_k<<<ntiles, kSortThreads, 0, s>>>(n, kin, iin, shift, moff, M, ntiles, c->w.hist);
         count_launch(c);
         rv_status st = exclusive_scan(c, c->w.hist, (int64_t)kSortBins * ntiles, nullptr, nullptr, s);
         if (st != RV_OK) return st;
-        sort_downsweep_k<<<ntiles, kSortThreads, 0, s>>>(n, kin, iin, shift, ntiles, c->w.hist, kout, iout);
+        sort_downsweep_k<<<ntiles, kSortThreads, 0, s>>>(n, kin, iin, shift, moff, M, ntiles, c->w.hist, kout,
+                                                          iout);
         count_launch(c);
         // next pass reads what this one wrote
         uint64_t *tk = kin; kin = kout; kout = tk;
@@ -336,13 +362,16 @@ __device__ __forceinline__ int diff_level(uint64_t a, uint64_t b) {
 
 // Window of D values for one block: D(j) for j in [b0 - n_leaf + 1, b0 + NT + n_leaf].
 // Out-of-range positions are not boundaries (99); D(0) = D(n) = 0.
-__device__ void load_window(int64_t n, const uint64_t *key, int64_t b0, int n_leaf, unsigned char *win) {
+// A member's first star is a cut at every level, like position 0.
+__device__ void load_window(int64_t n, const uint64_t *key, int64_t b0, int n_leaf, const int64_t *moff, int M,
+                            unsigned char *win) {
     int wlen = kTopoBlock + 2 * n_leaf;
     for (int t = threadIdx.x; t < wlen; t += blockDim.x) {
         int64_t j = b0 - n_leaf + 1 + t;
         int d;
         if (j < 0 || j > n) d = 99;
         else if (j == 0 || j == n) d = 0;
+        else if (M > 1 && moff[member_of(moff, M, j)] == j) d = 0;
         else d = diff_level(key[j - 1], key[j]);
         win[t] = (unsigned char)d;
     }
@@ -374,12 +403,12 @@ __device__ __forceinline__ void topo_ballots(bool valid, int Di, int lam, TopoBa
 }
 
 __global__ void __launch_bounds__(kTopoBlock) topo_count_k(int64_t n, const uint64_t *key, int n_leaf,
-                                                           uint8_t *dlev, uint8_t *lam_out, int *lvcnt,
-                                                           int nblk) {
+                                                           const int64_t *moff, int M, uint8_t *dlev,
+                                                           uint8_t *lam_out, int *lvcnt, int nblk) {
     extern __shared__ unsigned char win[];
     __shared__ int wc[kLevels][kTopoBlock / 32];
     int64_t b0 = (int64_t)blockIdx.x * kTopoBlock;
-    load_window(n, key, b0, n_leaf, win);
+    load_window(n, key, b0, n_leaf, moff, M, win);
     __syncthreads();
     int64_t i = b0 + threadIdx.x;
     bool valid = i < n;
@@ -413,8 +442,9 @@ __device__ __forceinline__ int4 cell_box(uint64_t key, int l) {
 // that ends a cell, its end star and child end.
 __global__ void __launch_bounds__(kTopoBlock) topo_write_k(int64_t n, const uint64_t *key, const uint8_t *dlev,
                                                            const uint8_t *lamv, const int *lvscan, int nblk,
-                                                           int64_t cap, int4 *cbox, int *clink, int *cparent,
-                                                           int *carrive, DevState *st) {
+                                                           int64_t cap, const int64_t *moff, int M, int4 *cbox,
+                                                           int *clink, int *cparent, int *carrive, int *mroot,
+                                                           DevState *st) {
     __shared__ int wp[kLevels][kTopoBlock / 32];
     __shared__ int lvoff[kLevels + 1];
     __shared__ int bbase[kLevels + 1];
@@ -458,6 +488,7 @@ __global__ void __launch_bounds__(kTopoBlock) topo_write_k(int64_t n, const uint
         clink[4 * c + 2] = (int)i;
         cparent[c] = (l == 0) ? -1 : rank(l - 1) - ((Di == l) ? 1 : 0);
         carrive[c] = 0;
+        if (l == 0) mroot[member_of(moff, M, i)] = c;
     }
     // cells containing star i-1 that end at i: levels D(i)..lambda_{i-1}
     if (i > 0) {
@@ -488,8 +519,8 @@ __global__ void __launch_bounds__(kTopoBlock) topo_write_k(int64_t n, const uint
 // pack has one unit, else the parent's); a leaf with more than G stars is
 // cut into chunks of G (box: the leaf). The root, if small, is one group.
 template <bool WRITE>
-__global__ void groups_k(const int *clink, const int *gofs, int G, int64_t cap, DevState *st, int *gcnt,
-                         int4 *groups) {
+__global__ void groups_k(const int4 *cbox, const int *clink, const int *gofs, int G, int64_t cap, DevState *st,
+                         int *gcnt, int4 *groups) {
     int ncell = (int)min((int64_t)st->ncell, cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
         int4 lk = reinterpret_cast<const int4 *>(clink)[c];
@@ -500,8 +531,9 @@ __global__ void groups_k(const int *clink, const int *gofs, int G, int64_t cap, 
             if (WRITE) groups[out + ng] = make_int4(first, count, box, 0);
             ng++;
         };
-        if (c == 0 && cnt <= G) {
-            emit(lk.z, cnt, 0);
+        const bool root = cbox[c].w == 0;
+        if (root && cnt <= G) {
+            emit(lk.z, cnt, c);
         } else if (cnt > G) {
             if (lk.y == lk.x) {
                 for (int o = 0; o < cnt; o += G) emit(lk.z + o, min(G, cnt - o), c);
@@ -563,14 +595,16 @@ __device__ __forceinline__ void add_q(float q[6], float m, float dx, float dy, f
 }
 
 __global__ void moments_k(int64_t n, const float4 *pos, const int4 *cbox, const int *clink, const int *cparent,
-                          int *carrive, float4 *cmom, int64_t cap, DevState *st) {
+                          int *carrive, float4 *cmom, int64_t cap, const int64_t *moff, int M,
+                          const double *mbounds, DevState *st) {
     int ncell = (int)min((int64_t)st->ncell, cap);
-    float lo[3] = {(float)st->bounds[0], (float)st->bounds[1], (float)st->bounds[2]};
-    float unit = (float)(st->bounds[3] / 2097152.0);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
         int4 lk = reinterpret_cast<const int4 *>(clink)[c];
         if (lk.y != lk.x) continue;  // not a leaf
-        if (lk.z < 0 || lk.w > n || lk.z > lk.w) { latch_err(st, kErrCells); continue; }
+        if (lk.z < 0 || lk.w > n || lk.z >= lk.w) { latch_err(st, kErrCells); continue; }
+        const int mb = member_of(moff, M, lk.z);
+        const float lo[3] = {(float)mbounds[5 * mb], (float)mbounds[5 * mb + 1], (float)mbounds[5 * mb + 2]};
+        const float unit = (float)(mbounds[5 * mb + 3] / 2097152.0);
         float g[3];
         geo_centre(cbox[c], lo, unit, g);
         Mom m = {};
@@ -643,28 +677,54 @@ static int grid_for(rv_ctx *c, int64_t n, int per_block) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
-rv_status build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *m,
-                     cudaStream_t s) {
+// Copies the member offsets to the device only when they differ from the
+// last ones sent (a captured step must not copy from host memory).
+rv_status upload_offsets(rv_ctx *c, int M, const int64_t *offsets, cudaStream_t s) {
+    bool same = c->moff_on_device && c->n_members == M;
+    for (int k = 0; k <= M && same; k++) same = (c->moff_host[k] == offsets[k]);
+    if (same) return RV_OK;
+    for (int k = 0; k <= M; k++) c->moff_host[k] = offsets[k];
+    c->n_members = M;
+    rv_status r = cuda_check(c, cudaMemcpyAsync(c->w.moff, c->moff_host, sizeof(int64_t) * (M + 1),
+                                                cudaMemcpyHostToDevice, s), "member offsets");
+    if (r == RV_OK) r = cuda_check(c, cudaStreamSynchronize(s), "member offsets");
+    if (r == RV_OK) c->moff_on_device = true;
+    return r;
+}
+
+// Members are independent systems stored one after another (offsets on the
+// host, M >= 1). Each gets its own bounding cube, keys, tree and groups; all
+// of them share these launches, and the walk serves them together.
+rv_status build_tree(rv_ctx *c, int n_members, const int64_t *offsets, const float *x, const float *y,
+                     const float *z, const float *m, cudaStream_t s) {
     Workspace &w = c->w;
+    const int M = n_members;
+    const int64_t n = offsets[M];
     c->n = n;
     c->built = false;
-    rv_status r;
+    int64_t big = 0;
+    for (int k = 0; k < M; k++) big = std::max<int64_t>(big, offsets[k + 1] - offsets[k]);
+    c->max_member = big;
+    rv_status r = upload_offsets(c, M, offsets, s);
+    if (r != RV_OK) return r;
     if (n == 0) {
         r = cuda_check(c, cudaMemsetAsync(w.st, 0, sizeof(DevState), s), "state reset");
         if (r == RV_OK) c->built = true;
         return r;
     }
-    // bounds
-    int nb = (int)std::min<int64_t>(ceil_div(n, 2048), 1024);
-    bounds_partial_k<<<nb, 256, 0, s>>>(n, x, y, z, reinterpret_cast<float *>(w.partials));
+    if ((r = cuda_check(c, cudaMemsetAsync(w.mroot, 0xff, sizeof(int) * M, s), "roots")) != RV_OK) return r;
+    // bounds and keys: blocks per member sized by the largest member
+    const int bpm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(big, kBoundsChunk), 512 / M + 1));
+    bounds_partial_k<<<dim3(bpm, M), 256, 0, s>>>(w.moff, bpm, x, y, z, w.bpart);
     count_launch(c);
-    bounds_final_k<<<1, 32, 0, s>>>(nb, reinterpret_cast<float *>(w.partials), w.st);
+    bounds_final_k<<<M, 32, 0, s>>>(bpm, w.bpart, w.mbounds, w.st);
     count_launch(c);
-    keys_k<<<grid_for(c, n, 256), 256, 0, s>>>(n, x, y, z, w.st, w.key_a);
+    const int kpm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(big, 256), (int64_t)c->num_sms * 8 / M + 1));
+    keys_k<<<dim3(kpm, M), 256, 0, s>>>(w.moff, kpm, x, y, z, w.mbounds, w.key_a);
     count_launch(c);
     uint64_t *skey;
     int *perm;
-    if ((r = radix_sort(c, n, 7, &skey, &perm, true, s)) != RV_OK) return r;
+    if ((r = radix_sort(c, n, 7, &skey, &perm, true, s, true)) != RV_OK) return r;
     w.skey = skey;
     w.perm = perm;
     gather_k<<<grid_for(c, n, 256), 256, 0, s>>>(n, perm, x, y, z, m, w.pos);
@@ -672,21 +732,22 @@ rv_status build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, const
     // topology
     int nblk = ceil_div(n, kTopoBlock);
     size_t win = kTopoBlock + 2 * c->cfg.n_leaf;
-    topo_count_k<<<nblk, kTopoBlock, win, s>>>(n, skey, c->cfg.n_leaf, w.dlev, w.lam, w.lvcnt, nblk);
+    topo_count_k<<<nblk, kTopoBlock, win, s>>>(n, skey, c->cfg.n_leaf, w.moff, M, w.dlev, w.lam, w.lvcnt, nblk);
     count_launch(c);
     if ((r = exclusive_scan(c, w.lvcnt, (int64_t)kLevels * nblk, nullptr, &w.st->ncell, s)) != RV_OK) return r;
-    topo_write_k<<<nblk, kTopoBlock, 0, s>>>(n, skey, w.dlev, w.lam, w.lvcnt, nblk, c->cell_cap, w.cbox,
-                                             w.clink, w.cparent, w.carrive, w.st);
+    topo_write_k<<<nblk, kTopoBlock, 0, s>>>(n, skey, w.dlev, w.lam, w.lvcnt, nblk, c->cell_cap, w.moff, M, w.cbox,
+                                             w.clink, w.cparent, w.carrive, w.mroot, w.st);
     count_launch(c);
     // groups
     int gb = grid_for(c, c->cell_cap, 256);
-    groups_k<false><<<gb, 256, 0, s>>>(w.clink, nullptr, c->cfg.group, c->cell_cap, w.st, w.gcnt, nullptr);
+    groups_k<false><<<gb, 256, 0, s>>>(w.cbox, w.clink, nullptr, c->cfg.group, c->cell_cap, w.st, w.gcnt, nullptr);
     count_launch(c);
     if ((r = exclusive_scan(c, w.gcnt, c->cell_cap, &w.st->ncell, &w.st->ngroup, s)) != RV_OK) return r;
-    groups_k<true><<<gb, 256, 0, s>>>(w.clink, w.gcnt, c->cfg.group, c->cell_cap, w.st, nullptr, w.groups);
+    groups_k<true><<<gb, 256, 0, s>>>(w.cbox, w.clink, w.gcnt, c->cfg.group, c->cell_cap, w.st, nullptr, w.groups);
     count_launch(c);
     // multipoles
-    moments_k<<<gb, 128, 0, s>>>(n, w.pos, w.cbox, w.clink, w.cparent, w.carrive, w.cmom, c->cell_cap, w.st);
+    moments_k<<<gb, 128, 0, s>>>(n, w.pos, w.cbox, w.clink, w.cparent, w.carrive, w.cmom, c->cell_cap, w.moff, M,
+                                 w.mbounds, w.st);
     count_launch(c);
     r = cuda_check(c, cudaGetLastError(), "build_tree");
     if (r == RV_OK) c->built = true;

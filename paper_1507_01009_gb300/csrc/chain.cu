@@ -108,7 +108,51 @@ rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y
 }
 
 // ---------------------------------------------------------------------------
-// FP64 chain / perturber coupling
+// perturber selection per member (systems of several members): one stable
+// sort of (member, key) over all stars; member m's stars occupy the same
+// slots [moff[m], moff[m+1]) in sorted order, best first.
+//   k nearest: key = FP32 squared distance bits to the member's centre
+//   radius:    key = 0 inside, 1 outside (inside stars first, ascending index)
+// ---------------------------------------------------------------------------
+__global__ void sel_member_keys_k(const int64_t *moff, int bpm, const float *x, const float *y, const float *z,
+                                  const float *xyzm, int mode, float r2, uint64_t *key) {
+    const int m = blockIdx.y;
+    const float cx = xyzm[4 * m], cy = xyzm[4 * m + 1], cz = xyzm[4 * m + 2];
+    for (int64_t i = moff[m] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < moff[m + 1];
+         i += (int64_t)bpm * blockDim.x) {
+        float d2 = dist2_f32(x[i], y[i], z[i], cx, cy, cz);
+        key[i] = (mode == 2) ? (uint64_t)__float_as_uint(d2) : (d2 < r2 ? 0ull : 1ull);
+    }
+}
+
+// member m: its first min(k, n_m) sorted slots (k nearest), or its leading
+// "inside" slots (radius), written to idx[m cap ..], count to npert[m]
+__global__ void sel_member_write_k(const int64_t *moff, const uint64_t *skey, const int *sidx, int mode, int k,
+                                   int cap, int *idx, int *npert, DevState *st) {
+    const int m = blockIdx.x;
+    const int64_t s = moff[m], e = moff[m + 1];
+    int cnt;
+    if (mode == 2) {
+        cnt = (int)min((int64_t)k, e - s);
+    } else {
+        // first "outside" key in the member's slots
+        int64_t lo = s, hi = e;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (skey[mid] == 0ull) lo = mid + 1; else hi = mid;
+        }
+        cnt = (int)(lo - s);
+    }
+    if (cnt > cap && threadIdx.x == 0) latch_err(st, kErrPert);
+    cnt = min(cnt, cap);
+    for (int p = threadIdx.x; p < cnt; p += blockDim.x) idx[(int64_t)m * cap + p] = sidx[s + p];
+    if (threadIdx.x == 0) npert[m] = cnt;
+}
+
+static int member_cap(int M) { return std::min(kMaxPert, kPertTotal / std::max(1, M)); }
+
+// ---------------------------------------------------------------------------
+// FP64 chain / perturber coupling, one chain per member
 // ---------------------------------------------------------------------------
 // f = m r / |r|^3 and -m/|r| for r = to - from (zero separation: nothing).
 __device__ __forceinline__ void kep(double rx, double ry, double rz, double m, double &ax, double &ay, double &az,
@@ -121,36 +165,57 @@ __device__ __forceinline__ void kep(double rx, double ry, double rz, double m, d
     p -= m * rinv;
 }
 
-// out8 layout: [0..3) corr (Eq. 3), [3..6) sub, [6] sum_k m_k pot_chain[k] / M, [7] sub potential,
-// [8..11) centre of mass, [11] M.
-__global__ void chain_com_k(int n_ch, const double *cm, const double *cx, double *out8, float *xyzm, float *xeps) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double M = 0, c[3] = {0, 0, 0};
-    for (int k = 0; k < n_ch; k++) {
-        M += cm[k];
-        for (int a = 0; a < 3; a++) c[a] += cm[k] * cx[3 * k + a];
-    }
-    for (int a = 0; a < 3; a++) c[a] = (M > 0) ? c[a] / M : 0.0;
-    out8[8] = c[0]; out8[9] = c[1]; out8[10] = c[2]; out8[11] = M;
-    if (xyzm) {
-        xyzm[0] = (float)c[0]; xyzm[1] = (float)c[1]; xyzm[2] = (float)c[2]; xyzm[3] = (float)M;
-        xeps[0] = 0.f;
+// Per member m (out8 + 16 m): [0..3) corr (Eq. 3), [3..6) sub, [6] sum_k m_k
+// pot_chain[k] / M, [7] sub potential, [8..11) centre of mass, [11] M.
+// With xyzm, the centre of mass also becomes member m's extra particle m
+// (FP32, unsoftened).
+__global__ void chain_com_k(int M, int n_ch, const double *cm, const double *cx, double *out8, float *xyzm,
+                            float *xeps) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const double *mm = cm + (int64_t)m * n_ch, *xx = cx + 3 * (int64_t)m * n_ch;
+        double Mt = 0, c[3] = {0, 0, 0};
+        for (int k = 0; k < n_ch; k++) {
+            Mt += mm[k];
+            for (int a = 0; a < 3; a++) c[a] += mm[k] * xx[3 * k + a];
+        }
+        for (int a = 0; a < 3; a++) c[a] = (Mt > 0) ? c[a] / Mt : 0.0;
+        double *o = out8 + 16 * (int64_t)m;
+        o[8] = c[0]; o[9] = c[1]; o[10] = c[2]; o[11] = Mt;
+        if (xyzm) {
+            xyzm[4 * m] = (float)c[0]; xyzm[4 * m + 1] = (float)c[1]; xyzm[4 * m + 2] = (float)c[2];
+            xyzm[4 * m + 3] = (float)Mt;
+            xeps[m] = 0.f;
+        }
     }
 }
 
+// Member addressing shared by the coupling kernels (blockIdx.y = member).
+struct ChainView {
+    int n_ch;            // members of each chain
+    int cap;             // perturber slots per member
+    const double *cm, *cx;
+    const int *npert;    // perturbers per member (nullptr: cap)
+    const double *pm, *px;
+};
+
+__device__ __forceinline__ int npert_of(const ChainView &V, int m) { return V.npert ? min(V.npert[m], V.cap) : V.cap; }
+
 // perturbers: resolved members minus the centre-of-mass point mass
-__global__ void pert_on_stars_k(int n_ch, const double *cm, const double *cx, int n_max, const int *d_np,
-                                const double *px, const double *out8, double *a_pert, double *pot_pert) {
-    int np = d_np ? min(*d_np, n_max) : n_max;
-    double M = out8[11];
+__global__ void pert_on_stars_k(ChainView V, const double *out8, double *a_pert, double *pot_pert) {
+    const int m = blockIdx.y;
+    const int np = npert_of(V, m);
+    const double *cm = V.cm + (int64_t)m * V.n_ch, *cx = V.cx + 3 * (int64_t)m * V.n_ch;
+    const double *o = out8 + 16 * (int64_t)m;
+    const double M = o[11];
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-        double x = px[3 * p], y = px[3 * p + 1], z = px[3 * p + 2];
+        const int64_t q = (int64_t)m * V.cap + p;
+        double x = V.px[3 * q], y = V.px[3 * q + 1], z = V.px[3 * q + 2];
         double ax = 0, ay = 0, az = 0, ph = 0;
-        for (int k = 0; k < n_ch; k++) kep(cx[3 * k] - x, cx[3 * k + 1] - y, cx[3 * k + 2] - z, cm[k], ax, ay, az, ph);
+        for (int k = 0; k < V.n_ch; k++) kep(cx[3 * k] - x, cx[3 * k + 1] - y, cx[3 * k + 2] - z, cm[k], ax, ay, az, ph);
         double bx = 0, by = 0, bz = 0, bp = 0;
-        kep(out8[8] - x, out8[9] - y, out8[10] - z, M, bx, by, bz, bp);
-        a_pert[3 * p] = ax - bx; a_pert[3 * p + 1] = ay - by; a_pert[3 * p + 2] = az - bz;
-        pot_pert[p] = ph - bp;
+        kep(o[8] - x, o[9] - y, o[10] - z, M, bx, by, bz, bp);
+        a_pert[3 * q] = ax - bx; a_pert[3 * q + 1] = ay - by; a_pert[3 * q + 2] = az - bz;
+        pot_pert[q] = ph - bp;
     }
 }
 
@@ -167,147 +232,195 @@ __device__ void block_sum4(double v[4], double (*sm)[NT]) {
     __syncthreads();
 }
 
-// one block per member: perturbers on member k (fixed order: strided partials + tree)
-__global__ void __launch_bounds__(256) pert_on_members_k(int n_ch, const double *cx, int n_max, const int *d_np,
-                                                         const double *pm, const double *px, double *a_chain,
-                                                         double *pot_chain) {
+// block (k, m): perturbers of member m on its chain member k (fixed order)
+__global__ void __launch_bounds__(256) pert_on_members_k(ChainView V, double *a_chain, double *pot_chain) {
     __shared__ double sm[4][256];
-    int np = d_np ? min(*d_np, n_max) : n_max;
-    int k = blockIdx.x;
-    double x = cx[3 * k], y = cx[3 * k + 1], z = cx[3 * k + 2];
+    const int k = blockIdx.x, m = blockIdx.y;
+    const int np = npert_of(V, m);
+    const int64_t kk = (int64_t)m * V.n_ch + k;
+    double x = V.cx[3 * kk], y = V.cx[3 * kk + 1], z = V.cx[3 * kk + 2];
     double v[4] = {0, 0, 0, 0};
-    for (int p = threadIdx.x; p < np; p += 256)
-        kep(px[3 * p] - x, px[3 * p + 1] - y, px[3 * p + 2] - z, pm[p], v[0], v[1], v[2], v[3]);
+    for (int p = threadIdx.x; p < np; p += 256) {
+        const int64_t q = (int64_t)m * V.cap + p;
+        kep(V.px[3 * q] - x, V.px[3 * q + 1] - y, V.px[3 * q + 2] - z, V.pm[q], v[0], v[1], v[2], v[3]);
+    }
     block_sum4<256>(v, sm);
     if (threadIdx.x == 0) {
-        a_chain[3 * k] = v[0]; a_chain[3 * k + 1] = v[1]; a_chain[3 * k + 2] = v[2];
-        pot_chain[k] = v[3];
+        a_chain[3 * kk] = v[0]; a_chain[3 * kk + 1] = v[1]; a_chain[3 * kk + 2] = v[2];
+        pot_chain[kk] = v[3];
     }
 }
 
-// Eq. 3 correction, and the perturbers' direct terms on the centre of mass
-__global__ void __launch_bounds__(256) pert_totals_k(int n_ch, const double *cm, const double *a_chain,
-                                                     const double *pot_chain, int n_max, const int *d_np,
-                                                     const double *pm, const double *px, double *out8) {
+// block m: Eq. 3 correction, and the perturbers' direct terms on the centre of mass
+__global__ void __launch_bounds__(256) pert_totals_k(ChainView V, const double *a_chain, const double *pot_chain,
+                                                     double *out8) {
     __shared__ double sm[4][256];
-    int np = d_np ? min(*d_np, n_max) : n_max;
-    double M = out8[11];
+    const int m = blockIdx.x;
+    const int np = npert_of(V, m);
+    double *o = out8 + 16 * (int64_t)m;
+    const double M = o[11];
     double v[4] = {0, 0, 0, 0};
-    for (int k = threadIdx.x; k < n_ch; k += 256) {
-        v[0] += cm[k] * a_chain[3 * k]; v[1] += cm[k] * a_chain[3 * k + 1]; v[2] += cm[k] * a_chain[3 * k + 2];
-        v[3] += cm[k] * pot_chain[k];
+    for (int k = threadIdx.x; k < V.n_ch; k += 256) {
+        const int64_t kk = (int64_t)m * V.n_ch + k;
+        const double mk = V.cm[kk];
+        v[0] += mk * a_chain[3 * kk]; v[1] += mk * a_chain[3 * kk + 1]; v[2] += mk * a_chain[3 * kk + 2];
+        v[3] += mk * pot_chain[kk];
     }
     block_sum4<256>(v, sm);
     double u[4] = {0, 0, 0, 0};
-    for (int p = threadIdx.x; p < np; p += 256)
-        kep(px[3 * p] - out8[8], px[3 * p + 1] - out8[9], px[3 * p + 2] - out8[10], pm[p], u[0], u[1], u[2], u[3]);
+    for (int p = threadIdx.x; p < np; p += 256) {
+        const int64_t q = (int64_t)m * V.cap + p;
+        kep(V.px[3 * q] - o[8], V.px[3 * q + 1] - o[9], V.px[3 * q + 2] - o[10], V.pm[q], u[0], u[1], u[2], u[3]);
+    }
     block_sum4<256>(u, sm);
     if (threadIdx.x == 0) {
-        for (int a = 0; a < 3; a++) out8[a] = (M > 0) ? v[a] / M : 0.0;
-        for (int a = 0; a < 3; a++) out8[3 + a] = u[a];
-        out8[6] = (M > 0) ? v[3] / M : 0.0;
-        out8[7] = u[3];
+        for (int a = 0; a < 3; a++) o[a] = (M > 0) ? v[a] / M : 0.0;
+        for (int a = 0; a < 3; a++) o[3 + a] = u[a];
+        o[6] = (M > 0) ? v[3] / M : 0.0;
+        o[7] = u[3];
     }
+}
+
+static rv_status coupling(rv_ctx *c, int M, const ChainView &V, double *a_pert, double *pot_pert, double *a_chain,
+                          double *pot_chain, double *out8, cudaStream_t s) {
+    chain_com_k<<<ceil_div(M, 128), 128, 0, s>>>(M, V.n_ch, V.cm, V.cx, out8, nullptr, nullptr);
+    count_launch(c);
+    if (V.cap > 0) {
+        pert_on_stars_k<<<dim3(ceil_div(V.cap, 128), M), 128, 0, s>>>(V, out8, a_pert, pot_pert);
+        count_launch(c);
+    }
+    if (V.n_ch > 0) {
+        pert_on_members_k<<<dim3(V.n_ch, M), 256, 0, s>>>(V, a_chain, pot_chain);
+        count_launch(c);
+    }
+    pert_totals_k<<<M, 256, 0, s>>>(V, a_chain, pot_chain, out8);
+    count_launch(c);
+    return cuda_check(c, cudaGetLastError(), "perturber forces");
 }
 
 rv_status perturber_forces(rv_ctx *c, int n_ch, const double *cm, const double *cx, int n_pert_max,
                            const int *d_npert, const double *pm, const double *px, double *a_pert,
                            double *pot_pert, double *a_chain, double *pot_chain, double *out8, cudaStream_t s) {
-    chain_com_k<<<1, 32, 0, s>>>(n_ch, cm, cx, out8, nullptr, nullptr);
-    count_launch(c);
-    if (n_pert_max > 0) {
-        pert_on_stars_k<<<ceil_div(n_pert_max, 128), 128, 0, s>>>(n_ch, cm, cx, n_pert_max, d_npert, px, out8, a_pert,
-                                                                  pot_pert);
-        count_launch(c);
-    }
-    if (n_ch > 0) {
-        pert_on_members_k<<<n_ch, 256, 0, s>>>(n_ch, cx, n_pert_max, d_npert, pm, px, a_chain, pot_chain);
-        count_launch(c);
-    }
-    pert_totals_k<<<1, 256, 0, s>>>(n_ch, cm, a_chain, pot_chain, n_pert_max, d_npert, pm, px, out8);
-    count_launch(c);
-    return cuda_check(c, cudaGetLastError(), "perturber forces");
+    ChainView V{n_ch, n_pert_max, cm, cx, d_npert, pm, px};
+    return coupling(c, 1, V, a_pert, pot_pert, a_chain, pot_chain, out8, s);
 }
 
 // ---------------------------------------------------------------------------
 // system force evaluation
 // ---------------------------------------------------------------------------
-__global__ void gather_pert_k(const int *idx, const int *d_np, const float *x, const float *y, const float *z,
-                              const float *m, double *pm, double *px) {
-    int np = min(*d_np, kMaxPert);
+__global__ void gather_pert_k(int cap, const int *idx, const int *npert, const float *x, const float *y,
+                              const float *z, const float *m, double *pm, double *px) {
+    const int mb = blockIdx.y;
+    const int np = min(npert[mb], cap);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-        int i = idx[p];
-        pm[p] = (double)m[i];
-        px[3 * p] = (double)x[i]; px[3 * p + 1] = (double)y[i]; px[3 * p + 2] = (double)z[i];
+        const int64_t q = (int64_t)mb * cap + p;
+        const int i = idx[q];
+        pm[q] = (double)m[i];
+        px[3 * q] = (double)x[i]; px[3 * q + 1] = (double)y[i]; px[3 * q + 2] = (double)z[i];
     }
 }
 
 // stars that are perturbers: add the FP64 correction (resolved chain - centre-of-mass point mass)
-__global__ void apply_pert_k(const int *idx, const int *d_np, const double *a_pert, const double *pot_pert, float *ax,
-                             float *ay, float *az, float *pot) {
-    int np = min(*d_np, kMaxPert);
+__global__ void apply_pert_k(int cap, const int *idx, const int *npert, const double *a_pert, const double *pot_pert,
+                             float *ax, float *ay, float *az, float *pot) {
+    const int mb = blockIdx.y;
+    const int np = min(npert[mb], cap);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-        int i = idx[p];
-        ax[i] = (float)((double)ax[i] + a_pert[3 * p]);
-        ay[i] = (float)((double)ay[i] + a_pert[3 * p + 1]);
-        az[i] = (float)((double)az[i] + a_pert[3 * p + 2]);
-        pot[i] = (float)((double)pot[i] + pot_pert[p]);
+        const int64_t q = (int64_t)mb * cap + p;
+        const int i = idx[q];
+        ax[i] = (float)((double)ax[i] + a_pert[3 * q]);
+        ay[i] = (float)((double)ay[i] + a_pert[3 * q + 1]);
+        az[i] = (float)((double)az[i] + a_pert[3 * q + 2]);
+        pot[i] = (float)((double)pot[i] + pot_pert[q]);
     }
 }
 
-// Member k: mutual unsoftened FP64 pull of the other members, plus the
-// perturbers on k, plus the tree's force on the centre of mass without the
-// perturbers' direct terms (those are now resolved per member).
-__global__ void chain_accel_k(int n_ch, const double *cm, const double *cx, const double *a_ext,
-                              const double *pot_ext, const float *xout, const double *out8, double *ca,
-                              double *cpot) {
-    double tx = (double)xout[0] - out8[3], ty = (double)xout[1] - out8[4], tz = (double)xout[2] - out8[5];
-    double tp = (double)xout[3] - out8[7];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_ch; k += gridDim.x * blockDim.x) {
+// Chain member k of member m: mutual unsoftened FP64 pull of the other chain
+// members, plus the perturbers on k, plus the tree's force on the centre of
+// mass without the perturbers' direct terms (those are resolved per member).
+__global__ void chain_accel_k(int M, int n_ch, const double *cm, const double *cx, const double *a_ext,
+                              const double *pot_ext, const float *xout, const double *out8, double *ca, double *cpot) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M * n_ch; t += gridDim.x * blockDim.x) {
+        const int m = t / n_ch, k = t % n_ch;
+        const double *o = out8 + 16 * (int64_t)m;
+        const double *mm = cm + (int64_t)m * n_ch, *xx = cx + 3 * (int64_t)m * n_ch;
+        double tx = (double)xout[4 * m] - o[3], ty = (double)xout[4 * m + 1] - o[4], tz = (double)xout[4 * m + 2] - o[5];
+        double tp = (double)xout[4 * m + 3] - o[7];
         double ax = 0, ay = 0, az = 0, ph = 0;
         for (int j = 0; j < n_ch; j++) {
             if (j == k) continue;
-            kep(cx[3 * j] - cx[3 * k], cx[3 * j + 1] - cx[3 * k + 1], cx[3 * j + 2] - cx[3 * k + 2], cm[j], ax, ay, az,
+            kep(xx[3 * j] - xx[3 * k], xx[3 * j + 1] - xx[3 * k + 1], xx[3 * j + 2] - xx[3 * k + 2], mm[j], ax, ay, az,
                 ph);
         }
-        ca[3 * k] = ax + a_ext[3 * k] + tx;
-        ca[3 * k + 1] = ay + a_ext[3 * k + 1] + ty;
-        ca[3 * k + 2] = az + a_ext[3 * k + 2] + tz;
-        cpot[k] = ph + pot_ext[k] + tp;
+        ca[3 * (int64_t)t] = ax + a_ext[3 * (int64_t)t] + tx;
+        ca[3 * (int64_t)t + 1] = ay + a_ext[3 * (int64_t)t + 1] + ty;
+        ca[3 * (int64_t)t + 2] = az + a_ext[3 * (int64_t)t + 2] + tz;
+        cpot[t] = ph + pot_ext[t] + tp;
     }
 }
+
+static const int64_t *system_offsets(const rv_system *sys, int64_t tmp[2]) {
+    if (sys->n_members > 1 || sys->member_offsets) return sys->member_offsets;
+    tmp[0] = 0;
+    tmp[1] = sys->n;
+    return tmp;
+}
+
+static int system_members(const rv_system *sys) { return std::max(1, (int)sys->n_members); }
 
 rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s) {
     Workspace &w = c->w;
     rv_status r;
     const bool chain = sys->n_chain > 0;
+    const int M = system_members(sys);
+    int64_t tmp[2];
+    const int64_t *off = system_offsets(sys, tmp);
+    const int cap = member_cap(M);
     if (chain) {
-        chain_com_k<<<1, 32, 0, s>>>(sys->n_chain, sys->chain_m, sys->chain_x, w.out8, w.extra_xyzm, w.extra_eps);
+        chain_com_k<<<ceil_div(M, 128), 128, 0, s>>>(M, sys->n_chain, sys->chain_m, sys->chain_x, w.out8, w.extra_xyzm,
+                                                     w.extra_eps);
         count_launch(c);
-        if (sys->pert_mode == 1 || sys->pert_mode == 2) {
+    }
+    if ((r = upload_offsets(c, M, off, s)) != RV_OK) return r;
+    if (chain && (sys->pert_mode == 1 || sys->pert_mode == 2)) {
+        if (M == 1) {
             r = select_perturbers(c, sys->n, sys->x, sys->y, sys->z, w.extra_xyzm, nullptr, sys->pert_mode,
-                                  sys->pert_radius, sys->pert_k, kMaxPert, w.pert_idx, &w.st->n_pert, s);
+                                  sys->pert_radius, sys->pert_k, cap, w.pert_idx, w.npert, s);
             if (r != RV_OK) return r;
         } else {
-            cudaMemsetAsync(&w.st->n_pert, 0, sizeof(int), s);
+            // the sort buffers are shared with the tree build, which comes next
+            const int bpm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c->max_member, 256), 64));
+            const float r2 = sys->pert_radius * sys->pert_radius;
+            sel_member_keys_k<<<dim3(bpm, M), 256, 0, s>>>(w.moff, bpm, sys->x, sys->y, sys->z, w.extra_xyzm,
+                                                           sys->pert_mode, r2, w.key_a);
+            count_launch(c);
+            uint64_t *sk;
+            int *si;
+            if ((r = radix_sort(c, sys->n, sys->pert_mode == 2 ? 4 : 1, &sk, &si, true, s, true)) != RV_OK) return r;
+            sel_member_write_k<<<M, 256, 0, s>>>(w.moff, sk, si, sys->pert_mode, sys->pert_k, cap, w.pert_idx,
+                                                 w.npert, w.st);
+            count_launch(c);
         }
+    } else if (chain) {
+        cudaMemsetAsync(w.npert, 0, sizeof(int) * M, s);
     }
-    if ((r = build_tree(c, sys->n, sys->x, sys->y, sys->z, sys->m, s)) != RV_OK) return r;
-    if ((r = tree_walk(c, c->cfg.theta, c->cfg.eps_star, chain ? 1 : 0, w.extra_xyzm, w.extra_eps, sys->ax, sys->ay,
-                       sys->az, sys->pot, w.extra_out, s)) != RV_OK)
+    if ((r = build_tree(c, M, off, sys->x, sys->y, sys->z, sys->m, s)) != RV_OK) return r;
+    if ((r = tree_walk(c, c->cfg.theta, c->cfg.eps_star, chain ? M : 0, w.extra_xyzm, w.extra_eps, nullptr, true,
+                       sys->ax, sys->ay, sys->az, sys->pot, w.extra_out, s)) != RV_OK)
         return r;
     if (chain) {
-        gather_pert_k<<<ceil_div(kMaxPert, 128), 128, 0, s>>>(w.pert_idx, &w.st->n_pert, sys->x, sys->y, sys->z,
-                                                              sys->m, w.pert_m, w.pert_x);
+        gather_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, sys->x, sys->y, sys->z,
+                                                                  sys->m, w.pert_m, w.pert_x);
         count_launch(c);
-        r = perturber_forces(c, sys->n_chain, sys->chain_m, sys->chain_x, kMaxPert, &w.st->n_pert, w.pert_m, w.pert_x,
-                             w.pert_a, w.pert_pot, w.chain_ext_a, w.chain_ext_pot, w.out8, s);
+        ChainView V{sys->n_chain, cap, sys->chain_m, sys->chain_x, w.npert, w.pert_m, w.pert_x};
+        r = coupling(c, M, V, w.pert_a, w.pert_pot, w.chain_ext_a, w.chain_ext_pot, w.out8, s);
         if (r != RV_OK) return r;
-        apply_pert_k<<<ceil_div(kMaxPert, 128), 128, 0, s>>>(w.pert_idx, &w.st->n_pert, w.pert_a, w.pert_pot, sys->ax,
-                                                             sys->ay, sys->az, sys->pot);
+        apply_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, w.pert_a, w.pert_pot,
+                                                                 sys->ax, sys->ay, sys->az, sys->pot);
         count_launch(c);
-        chain_accel_k<<<1, 256, 0, s>>>(sys->n_chain, sys->chain_m, sys->chain_x, w.chain_ext_a, w.chain_ext_pot,
-                                        w.extra_out, w.out8, sys->chain_a, sys->chain_pot);
+        chain_accel_k<<<ceil_div(M * sys->n_chain, 128), 128, 0, s>>>(M, sys->n_chain, sys->chain_m, sys->chain_x,
+                                                                      w.chain_ext_a, w.chain_ext_pot, w.extra_out,
+                                                                      w.out8, sys->chain_a, sys->chain_pot);
         count_launch(c);
     }
     return cuda_check(c, cudaGetLastError(), "system forces");
@@ -327,57 +440,55 @@ __global__ void kick_drift_k(int64_t n, float *x, float *y, float *z, float *vx,
     }
 }
 
-__global__ void chain_kick_drift_k(int n_ch, double *cx, double *cv, const double *ca, double hdt, double dt,
-                                   int drift) {
-    for (int k = threadIdx.x; k < n_ch; k += blockDim.x)
+__global__ void chain_kick_drift_k(int n, double *cx, double *cv, const double *ca, double hdt, double dt, int drift) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
         for (int a = 0; a < 3; a++) {
             cv[3 * k + a] += ca[3 * k + a] * hdt;
             if (drift) cx[3 * k + a] += cv[3 * k + a] * dt;
         }
 }
 
+static void kick(rv_ctx *c, rv_system *sys, double dt, int drift, cudaStream_t s) {
+    const int M = system_members(sys);
+    if (sys->n > 0) {
+        kick_drift_k<<<grid_n(c, sys->n), 256, 0, s>>>(sys->n, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz,
+                                                      sys->ax, sys->ay, sys->az, (float)(0.5 * dt), (float)dt, drift);
+        count_launch(c);
+    }
+    if (sys->n_chain > 0) {
+        const int nc = M * sys->n_chain;
+        chain_kick_drift_k<<<ceil_div(nc, 128), 128, 0, s>>>(nc, sys->chain_x, sys->chain_v, sys->chain_a, 0.5 * dt, dt,
+                                                             drift);
+        count_launch(c);
+    }
+}
+
 rv_status kdk(rv_ctx *c, rv_system *sys, double dt, int nsteps, cudaStream_t s) {
-    const float hdt = (float)(0.5 * dt), fdt = (float)dt;
-    const int g = grid_n(c, sys->n);
     for (int step = 0; step < nsteps; step++) {
-        if (sys->n > 0) {
-            kick_drift_k<<<g, 256, 0, s>>>(sys->n, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->ax, sys->ay,
-                                          sys->az, hdt, fdt, 1);
-            count_launch(c);
-        }
-        if (sys->n_chain > 0) {
-            chain_kick_drift_k<<<1, 256, 0, s>>>(sys->n_chain, sys->chain_x, sys->chain_v, sys->chain_a, 0.5 * dt, dt,
-                                                 1);
-            count_launch(c);
-        }
+        kick(c, sys, dt, 1, s);
         rv_status r = system_forces(c, sys, s);
         if (r != RV_OK) return r;
-        if (sys->n > 0) {
-            kick_drift_k<<<g, 256, 0, s>>>(sys->n, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->ax, sys->ay,
-                                          sys->az, hdt, fdt, 0);
-            count_launch(c);
-        }
-        if (sys->n_chain > 0) {
-            chain_kick_drift_k<<<1, 256, 0, s>>>(sys->n_chain, sys->chain_x, sys->chain_v, sys->chain_a, 0.5 * dt, dt,
-                                                 0);
-            count_launch(c);
-        }
+        kick(c, sys, dt, 0, s);
     }
     return cuda_check(c, cudaGetLastError(), "kdk");
 }
 
 // ---------------------------------------------------------------------------
-// FP64 totals: fixed grid, fixed per-thread striding, fixed tree reductions
+// FP64 totals per member: fixed grid, fixed per-thread striding, fixed tree
+// reductions, so the result does not depend on scheduling
 // ---------------------------------------------------------------------------
-constexpr int kRedBlocks = 256;
 constexpr int kRedQ = 9;  // ekin, epot, P(3), L(3), mass
 
-__global__ void __launch_bounds__(256) energy_partial_k(int64_t n, const float *x, const float *y, const float *z,
-                                                        const float *vx, const float *vy, const float *vz,
-                                                        const float *m, const float *pot, double *part) {
+static int energy_bpm(int M) { return std::max(1, std::min(256, kRedSlots / M)); }
+
+__global__ void __launch_bounds__(256) energy_partial_k(const int64_t *moff, int bpm, const float *x, const float *y,
+                                                        const float *z, const float *vx, const float *vy,
+                                                        const float *vz, const float *m, const float *pot,
+                                                        double *part) {
     __shared__ double sm[kRedQ][256];
+    const int mb = blockIdx.y;
     double q[kRedQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)kRedBlocks * 256) {
+    for (int64_t i = moff[mb] + (int64_t)blockIdx.x * 256 + threadIdx.x; i < moff[mb + 1]; i += (int64_t)bpm * 256) {
         double mi = m[i], X = x[i], Y = y[i], Z = z[i], U = vx[i], V = vy[i], W = vz[i];
         q[0] += 0.5 * mi * (U * U + V * V + W * W);
         q[1] += 0.5 * mi * (double)pot[i];
@@ -392,14 +503,16 @@ __global__ void __launch_bounds__(256) energy_partial_k(int64_t n, const float *
             for (int a = 0; a < kRedQ; a++) sm[a][threadIdx.x] += sm[a][threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x < kRedQ) part[kRedQ * blockIdx.x + threadIdx.x] = sm[threadIdx.x][0];
+    if (threadIdx.x < kRedQ) part[kRedQ * ((int64_t)mb * bpm + blockIdx.x) + threadIdx.x] = sm[threadIdx.x][0];
 }
 
-__global__ void __launch_bounds__(256) energy_final_k(const double *part, int64_t n, const float *m, int n_ch,
-                                                      const double *cm, const double *cx, const double *cv,
-                                                      const double *cpot, double *out) {
+__global__ void __launch_bounds__(256) energy_final_k(const double *part, int bpm, int n_ch, const double *cm,
+                                                      const double *cx, const double *cv, const double *cpot,
+                                                      double *out) {
     __shared__ double sm[kRedQ][256];
-    for (int a = 0; a < kRedQ; a++) sm[a][threadIdx.x] = part[kRedQ * threadIdx.x + a];
+    const int mb = blockIdx.x;
+    for (int a = 0; a < kRedQ; a++)
+        sm[a][threadIdx.x] = ((int)threadIdx.x < bpm) ? part[kRedQ * ((int64_t)mb * bpm + threadIdx.x) + a] : 0.0;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o)
@@ -409,32 +522,97 @@ __global__ void __launch_bounds__(256) energy_final_k(const double *part, int64_
     if (threadIdx.x == 0) {
         double q[kRedQ];
         for (int a = 0; a < kRedQ; a++) q[a] = sm[a][0];
-        double M = q[8];
         for (int k = 0; k < n_ch; k++) {
-            double mk = cm[k];
-            const double *X = cx + 3 * k, *V = cv + 3 * k;
+            const int64_t kk = (int64_t)mb * n_ch + k;
+            double mk = cm[kk];
+            const double *X = cx + 3 * kk, *V = cv + 3 * kk;
             q[0] += 0.5 * mk * (V[0] * V[0] + V[1] * V[1] + V[2] * V[2]);
-            q[1] += 0.5 * mk * cpot[k];
+            q[1] += 0.5 * mk * cpot[kk];
             q[2] += mk * V[0]; q[3] += mk * V[1]; q[4] += mk * V[2];
             q[5] += mk * (X[1] * V[2] - X[2] * V[1]);
             q[6] += mk * (X[2] * V[0] - X[0] * V[2]);
             q[7] += mk * (X[0] * V[1] - X[1] * V[0]);
-            M += mk;
+            q[8] += mk;
         }
-        out[0] = q[0]; out[1] = q[1]; out[2] = q[0] + q[1];
-        for (int a = 0; a < 6; a++) out[3 + a] = q[2 + a];
-        out[9] = M;
+        double *o = out + 10 * (int64_t)mb;
+        o[0] = q[0]; o[1] = q[1]; o[2] = q[0] + q[1];
+        for (int a = 0; a < 6; a++) o[3 + a] = q[2 + a];
+        o[9] = q[8];
     }
 }
 
 rv_status energy(rv_ctx *c, const rv_system *sys, double *out, cudaStream_t s) {
-    energy_partial_k<<<kRedBlocks, 256, 0, s>>>(sys->n, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz, sys->m,
-                                                sys->pot, c->w.red);
+    const int M = system_members(sys);
+    int64_t tmp[2];
+    rv_status r = upload_offsets(c, M, system_offsets(sys, tmp), s);
+    if (r != RV_OK) return r;
+    const int bpm = energy_bpm(M);
+    energy_partial_k<<<dim3(bpm, M), 256, 0, s>>>(c->w.moff, bpm, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz,
+                                                  sys->m, sys->pot, c->w.red);
     count_launch(c);
-    energy_final_k<<<1, 256, 0, s>>>(c->w.red, sys->n, sys->m, sys->n_chain, sys->chain_m, sys->chain_x, sys->chain_v,
+    energy_final_k<<<M, 256, 0, s>>>(c->w.red, bpm, sys->n_chain, sys->chain_m, sys->chain_x, sys->chain_v,
                                      sys->chain_pot, out);
     count_launch(c);
     return cuda_check(c, cudaGetLastError(), "energy");
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graph of one step (kick-drift-kick [+ energy]), captured once per
+// (system, dt, energy output) and replayed
+// ---------------------------------------------------------------------------
+static unsigned long long graph_key(const rv_system *sys, double dt, const double *eout) {
+    unsigned long long h = 1469598103934665603ull;
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(sys);
+    for (size_t i = 0; i < sizeof(rv_system); i++) h = (h ^ p[i]) * 1099511628211ull;
+    const int M = system_members(sys);
+    if (sys->member_offsets)
+        for (int k = 0; k <= M; k++) h = (h ^ (unsigned long long)sys->member_offsets[k]) * 1099511628211ull;
+    unsigned long long d;
+    memcpy(&d, &dt, sizeof d);
+    h = (h ^ d) * 1099511628211ull;
+    h = (h ^ (unsigned long long)(uintptr_t)eout) * 1099511628211ull;
+    return h;
+}
+
+rv_status kdk_graph(rv_ctx *c, rv_system *sys, double dt, int nsteps, double *eout, cudaStream_t s) {
+    const unsigned long long key = graph_key(sys, dt, eout);
+    if (!c->graph || c->graph_key != key) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        // settle everything a capture must not do (offset upload, kernel attributes) with an uncaptured
+        // force evaluation at the current positions, which the step's first kick already expects
+        rv_status r = system_forces(c, sys, s);
+        if (r != RV_OK) return r;
+        if ((r = cuda_check(c, cudaStreamSynchronize(s), "graph prepare")) != RV_OK) return r;
+        cudaGraph_t g = nullptr;
+        if ((r = cuda_check(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture")) != RV_OK)
+            return r;
+        const long long l0 = c->launches;
+        r = kdk(c, sys, dt, 1, s);
+        if (r == RV_OK && eout) r = energy(c, sys, eout, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (r != RV_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_check(c, e, "end capture");
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+        c->graph = ge;
+        c->graph_key = key;
+        c->graph_launches = c->launches - l0;
+        c->launches = l0;
+    }
+    for (int k = 0; k < nsteps; k++) {
+        cudaError_t e = cudaGraphLaunch(c->graph, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "graph launch");
+        c->launches += c->graph_launches;
+    }
+    return RV_OK;
 }
 
 }  // namespace rv

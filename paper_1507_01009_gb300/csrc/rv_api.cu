@@ -71,19 +71,25 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.gcnt = (int *)take(4 * cap);
     t.groups = (int4 *)take(16 * (n + 1));
     t.partials = (int *)take(4 * nparts);
-    t.pert_idx = (int *)take(4 * kMaxPert);
-    t.pert_m = (double *)take(8 * kMaxPert);
-    t.pert_x = (double *)take(24 * kMaxPert);
-    t.pert_a = (double *)take(24 * kMaxPert);
-    t.pert_pot = (double *)take(8 * kMaxPert);
-    t.chain_ext_a = (double *)take(24 * kMaxChain);
-    t.chain_ext_pot = (double *)take(8 * kMaxChain);
-    t.out8 = (double *)take(8 * 16);
-    t.extra_xyzm = (float *)take(16 * kMaxExtra);
-    t.extra_eps = (float *)take(4 * kMaxExtra);
-    t.extra_out = (float *)take(16 * kMaxExtra);
-    t.red = (double *)take(8 * 8 * 1024);
+    t.pert_idx = (int *)take(4 * kPertTotal);
+    t.pert_m = (double *)take(8 * kPertTotal);
+    t.pert_x = (double *)take(24 * kPertTotal);
+    t.pert_a = (double *)take(24 * kPertTotal);
+    t.pert_pot = (double *)take(8 * kPertTotal);
+    t.chain_ext_a = (double *)take(24 * kChainTotal);
+    t.chain_ext_pot = (double *)take(8 * kChainTotal);
+    t.out8 = (double *)take(8 * 16 * kMaxMembers);
+    t.extra_xyzm = (float *)take(16 * kExtraTotal);
+    t.extra_eps = (float *)take(4 * kExtraTotal);
+    t.extra_out = (float *)take(16 * kExtraTotal);
+    t.red = (double *)take(8 * 9 * kRedSlots);
     t.sel_flag = (int *)take(4 * n);
+    t.moff = (int64_t *)take(8 * (kMaxMembers + 1));
+    t.mbounds = (double *)take(8 * 5 * kMaxMembers);
+    t.mroot = (int *)take(4 * kMaxMembers);
+    t.bpart = (float *)take(4 * 6 * 2048);
+    t.xmem = (int *)take(4 * kExtraTotal);
+    t.npert = (int *)take(4 * kMaxMembers);
     t.st = (DevState *)take(sizeof(DevState));
     if (w) *w = t;
     return off;
@@ -127,6 +133,7 @@ rv_status rv_create(rv_ctx **out, int64_t n_max, const rv_config *cfg) {
     rv_ctx *c = (rv_ctx *)calloc(1, sizeof(rv_ctx));
     if (!c) return RV_E_INVAL;
     c->cfg = *cfg;
+    c->n_members = 1;
     c->n_max = n_max;
     c->cell_cap = cap;
     cudaError_t e = cudaGetDevice(&c->device);
@@ -139,7 +146,11 @@ rv_status rv_create(rv_ctx **out, int64_t n_max, const rv_config *cfg) {
     return RV_OK;
 }
 
-void rv_destroy(rv_ctx *c) { free(c); }
+void rv_destroy(rv_ctx *c) {
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    free(c);
+}
 
 rv_status rv_set_workspace(rv_ctx *c, void *dev, size_t bytes) {
     if (!c || !dev) return RV_E_INVAL;
@@ -150,6 +161,11 @@ rv_status rv_set_workspace(rv_ctx *c, void *dev, size_t bytes) {
     c->ws_bytes = bytes;
     layout(c->n_max, c->cfg, c->ws, &c->w, &c->cell_cap);
     c->built = false;
+    c->moff_on_device = false;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
     cudaError_t e = cudaMemset(c->w.st, 0, sizeof(DevState));
     return cuda_check(c, e, "workspace init");
 }
@@ -160,7 +176,29 @@ rv_status rv_build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, co
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (n < 0 || n > c->n_max) return set_err(c, RV_E_INVAL, "n = %lld outside [0, %lld]", (long long)n, (long long)c->n_max);
     if (n > 0 && (!x || !y || !z || !m)) return set_err(c, RV_E_INVAL, "null star array");
-    return build_tree(c, n, x, y, z, m, (cudaStream_t)stream);
+    const int64_t off[2] = {0, n};
+    return build_tree(c, 1, off, x, y, z, m, (cudaStream_t)stream);
+}
+
+static rv_status check_offsets(rv_ctx *c, int M, const int64_t *off, int64_t n) {
+    if (M < 1 || M > kMaxMembers || !off) return set_err(c, RV_E_INVAL, "need 1 <= n_members <= %d and offsets", kMaxMembers);
+    if (off[0] != 0 || off[M] != n) return set_err(c, RV_E_INVAL, "offsets must run from 0 to n");
+    for (int k = 0; k < M; k++)
+        if (off[k + 1] < off[k]) return set_err(c, RV_E_INVAL, "offsets must not decrease");
+    return RV_OK;
+}
+
+rv_status rv_build_tree_members(rv_ctx *c, int32_t n_members, const int64_t *offsets, const float *x,
+                                const float *y, const float *z, const float *m, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (!offsets || n_members < 1) return set_err(c, RV_E_INVAL, "bad members");
+    const int64_t n = offsets[n_members > kMaxMembers ? 0 : n_members];
+    rv_status r = check_offsets(c, n_members, offsets, n);
+    if (r != RV_OK) return r;
+    if (n > c->n_max) return set_err(c, RV_E_INVAL, "n = %lld above n_max %lld", (long long)n, (long long)c->n_max);
+    if (n > 0 && (!x || !y || !z || !m)) return set_err(c, RV_E_INVAL, "null star array");
+    return build_tree(c, n_members, offsets, x, y, z, m, (cudaStream_t)stream);
 }
 
 rv_status rv_tree_forces(rv_ctx *c, float theta, float eps_star, int32_t n_extra, const float *extra_xyzm,
@@ -173,8 +211,22 @@ rv_status rv_tree_forces(rv_ctx *c, float theta, float eps_star, int32_t n_extra
     if (n_extra < 0 || n_extra > kMaxExtra) return set_err(c, RV_E_INVAL, "n_extra must be in [0, %d]", kMaxExtra);
     if (n_extra > 0 && (!extra_xyzm || !extra_eps || !extra_out)) return set_err(c, RV_E_INVAL, "null extra array");
     if (c->n > 0 && (!ax || !ay || !az || !pot)) return set_err(c, RV_E_INVAL, "null output array");
-    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, ax, ay, az, pot, extra_out,
+    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, nullptr, false, ax, ay, az, pot, extra_out,
                      (cudaStream_t)stream);
+}
+
+rv_status rv_tree_forces_members(rv_ctx *c, float theta, float eps_star, int32_t n_extra, const float *extra_xyzm,
+                                 const float *extra_eps, const int32_t *extra_member, float *ax, float *ay, float *az,
+                                 float *pot, float *extra_out, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces_members before a build");
+    if (!(theta >= 0.f && theta < 2.f) || !(eps_star >= 0.f)) return set_err(c, RV_E_INVAL, "bad theta/eps");
+    if (n_extra < 0 || n_extra > kMaxExtra) return set_err(c, RV_E_INVAL, "n_extra must be in [0, %d]", kMaxExtra);
+    if (n_extra > 0 && (!extra_xyzm || !extra_eps || !extra_out)) return set_err(c, RV_E_INVAL, "null extra array");
+    if (c->n > 0 && (!ax || !ay || !az || !pot)) return set_err(c, RV_E_INVAL, "null output array");
+    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, extra_member, false, ax, ay, az, pot,
+                     extra_out, (cudaStream_t)stream);
 }
 
 rv_status rv_perturber_forces(rv_ctx *c, int32_t n_ch, const double *chain_m, const double *chain_x,
@@ -193,6 +245,12 @@ rv_status rv_perturber_forces(rv_ctx *c, int32_t n_ch, const double *chain_m, co
 static rv_status check_system(rv_ctx *c, const rv_system *s) {
     if (!s) return set_err(c, RV_E_INVAL, "null system");
     if (s->n < 0 || s->n > c->n_max) return set_err(c, RV_E_INVAL, "system n outside [0, n_max]");
+    const int M = std::max(1, (int)s->n_members);
+    if (s->n_members > 1 || s->member_offsets) {
+        rv_status r = check_offsets(c, M, s->member_offsets, s->n);
+        if (r != RV_OK) return r;
+    }
+    if ((int64_t)M * s->n_chain > kChainTotal) return set_err(c, RV_E_INVAL, "more than %d chain members", kChainTotal);
     if (s->n > 0 && (!s->x || !s->y || !s->z || !s->vx || !s->vy || !s->vz || !s->m || !s->ax || !s->ay || !s->az ||
                      !s->pot))
         return set_err(c, RV_E_INVAL, "null star array in system");
@@ -219,6 +277,19 @@ rv_status rv_kdk_step(rv_ctx *c, rv_system *sys, double dt, int32_t nsteps, void
     if (r != RV_OK) return r;
     if (nsteps < 0 || !(dt == dt)) return set_err(c, RV_E_INVAL, "bad dt/nsteps");
     return kdk(c, sys, dt, nsteps, (cudaStream_t)stream);
+}
+
+rv_status rv_kdk_step_graph(rv_ctx *c, rv_system *sys, double dt, int32_t nsteps, double *energy_out,
+                            void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    rv_status r = check_system(c, sys);
+    if (r != RV_OK) return r;
+    if (nsteps < 0 || !(dt == dt)) return set_err(c, RV_E_INVAL, "bad dt/nsteps");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+        return set_err(c, RV_E_INVAL, "graph capture needs a created stream");
+    return kdk_graph(c, sys, dt, nsteps, energy_out, s);
 }
 
 rv_status rv_energy(rv_ctx *c, const rv_system *sys, double *out, void *stream) {

@@ -20,7 +20,13 @@ constexpr int kTopoBlock = 256;
 constexpr int kScanChunk = 2048;        // elements per scan block
 constexpr int kWalkWarps = 4;           // warps per walk block
 constexpr int kStackCap = 768;          // walk traversal stack entries per warp
-constexpr int kMaxExtra = 8;
+constexpr int kMaxExtra = 8;            // extra particles through rv_tree_forces
+constexpr int kMaxMembers = 512;        // independent systems built and walked together (9-bit sort digit)
+constexpr int kBoundsChunk = 2048;      // stars per bounds/keys block within a member
+constexpr int kPertTotal = 65536;       // perturber slots over all members
+constexpr int kChainTotal = 2048;       // chain members over all members
+constexpr int kExtraTotal = kMaxMembers;  // extra particles (chain centres) over all members
+constexpr int kRedSlots = 1024;         // energy partial-sum blocks over all members
 constexpr int kMaxChain = 250;
 constexpr int kMaxPert = 5000;
 
@@ -67,6 +73,13 @@ struct Workspace {
     float *extra_xyzm, *extra_eps, *extra_out;  // [4 kMaxExtra], [kMaxExtra], [4 kMaxExtra]
     double *red;          // energy partial sums
     int *sel_flag;        // perturber selection flags (n)
+    // members (independent systems sharing one build and one walk)
+    int64_t *moff;        // member star offsets [kMaxMembers + 1]
+    double *mbounds;      // per member: min x, y, z, L, 2^21 / L
+    int *mroot;           // root cell of each member (-1 if empty)
+    float *bpart;         // bounds partials
+    int *xmem;            // member of each extra particle
+    int *npert;           // perturbers selected per member
     DevState *st;
 };
 
@@ -84,6 +97,14 @@ struct rv_ctx {
     char *ws;
     size_t ws_bytes;
     rv::Workspace w;
+    int n_members;                          // members of the last build (>= 1)
+    int64_t moff_host[rv::kMaxMembers + 1]; // their star offsets
+    int64_t max_member;                     // largest member
+    bool moff_on_device;                    // moff_host[0..n_members] already uploaded
+    // captured kick-drift-kick step (rv_kdk_step_graph)
+    cudaGraphExec_t graph;
+    long long graph_launches;
+    unsigned long long graph_key;
     char err[512];
 };
 
@@ -97,15 +118,19 @@ rv_status set_err(rv_ctx *c, rv_status s, const char *fmt, ...);
 rv_status cuda_check(rv_ctx *c, cudaError_t e, const char *what);
 
 // build.cu
-rv_status build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *m,
-                     cudaStream_t s);
+rv_status build_tree(rv_ctx *c, int n_members, const int64_t *offsets, const float *x, const float *y,
+                     const float *z, const float *m, cudaStream_t s);
+rv_status upload_offsets(rv_ctx *c, int M, const int64_t *offsets, cudaStream_t s);
 rv_status radix_sort(rv_ctx *c, int64_t n, int passes, uint64_t **keys, int **idx, bool identity_idx,
-                     cudaStream_t s);
+                     cudaStream_t s, bool member_pass = false);
 rv_status exclusive_scan(rv_ctx *c, int *data, int64_t nmax, const int *d_len, int *d_total, cudaStream_t s);
 
 // walk.cu
+// extra particles: xmem[k] = member of extra k (device), or nullptr when
+// extra k belongs to member k (one chain per member) -- see walk.cu.
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
-                    float *ax, float *ay, float *az, float *pot, float *xout, cudaStream_t s);
+                    const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
+                    float *xout, cudaStream_t s);
 
 // chain.cu
 rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
@@ -117,8 +142,20 @@ rv_status perturber_forces(rv_ctx *c, int n_ch, const double *cm, const double *
 rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s);
 rv_status kdk(rv_ctx *c, rv_system *sys, double dt, int nsteps, cudaStream_t s);
 rv_status energy(rv_ctx *c, const rv_system *sys, double *out, cudaStream_t s);
+rv_status kdk_graph(rv_ctx *c, rv_system *sys, double dt, int nsteps, double *eout, cudaStream_t s);
 
 inline void count_launch(rv_ctx *c) { c->launches++; }
+
+// Member holding star i: the largest m < M with moff[m] <= i (empty members
+// are skipped because their successor has the same offset).
+__device__ __forceinline__ int member_of(const int64_t *moff, int M, int64_t i) {
+    int lo = 0, hi = M - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (moff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // ---- device helpers ----
 __device__ __forceinline__ void latch_err(DevState *st, int code) { atomicCAS(&st->err, 0, code); }

@@ -41,6 +41,12 @@ struct WalkArgs {
     DevState *st;
     int cell_cap;
     int n;               // stars of the tree
+    const int64_t *moff; // member star offsets [M + 1]
+    int M;               // members (independent systems)
+    const double *mbounds;  // per member: min x, y, z, L, 2^21 / L
+    const int *mroot;    // root cell of each member
+    const int *xmem;     // member of each extra particle (nullptr: member 0)
+    int extra_per_member;  // extra k belongs to member k (one chain per member)
     MacTable mac;
     float eps2;          // star-star and star-cell softening^2
     float eps_star;
@@ -57,19 +63,22 @@ __host__ __device__ inline size_t warp_smem_bytes(int tile) {
     return (size_t)kStackCap * 4 + 32 * 4 + (size_t)(tile + 32) * 48 + (size_t)(tile + 32) * 16;
 }
 
-// Values of the last build read from device state at kernel start.
+// The tree of one member as the walk sees it.
 struct TreeGeo {
-    int ncell;           // cells of the tree (at most the workspace capacity)
-    float lo[3], unit;   // bounding-cube corner and grid unit in FP32
+    int ncell;           // cells of all trees (at most the workspace capacity)
+    int root;            // the member's root cell (-1: empty member)
+    float lo[3], unit;   // the member's bounding-cube corner and grid unit in FP32
 };
 
-__device__ __forceinline__ TreeGeo tree_geo(const WalkArgs &A) {
+__device__ __forceinline__ TreeGeo tree_geo(const WalkArgs &A, int member) {
     TreeGeo t;
     t.ncell = min(A.st->ncell, A.cell_cap);
-    t.lo[0] = (float)A.st->bounds[0];
-    t.lo[1] = (float)A.st->bounds[1];
-    t.lo[2] = (float)A.st->bounds[2];
-    t.unit = (float)(A.st->bounds[3] / 2097152.0);
+    t.root = A.mroot[member];
+    const double *b = A.mbounds + 5 * member;
+    t.lo[0] = (float)b[0];
+    t.lo[1] = (float)b[1];
+    t.lo[2] = (float)b[2];
+    t.unit = (float)(b[3] / 2097152.0);
     return t;
 }
 
@@ -163,7 +172,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
     const unsigned lt = lanemask_lt();
     const int ncell = G.ncell;
 
-    if (lane == 0) stack[0] = (0 << 4) | 1;  // root: a range of one cell starting at 0
+    if (lane == 0) stack[0] = (G.root << 4) | 1;  // the member's root: a range of one cell
     int top = 1, nm = 0, np = 0, hwm = 1;
     bool ok = true;
     // every pass tests at least one new cell, so a walk ends within ncell passes
@@ -307,13 +316,17 @@ __device__ __forceinline__ void combine_lanes(Acc &a, int s, int k) {
     a.cx = cx; a.cy = cy; a.cz = cz; a.cp = cp;
 }
 
-// Direct terms of the extra particles on one target (pair softening rule of
-// Sect. 3: max(eps_i, eps_j), none if either is unsoftened), absolute FP32.
+// Direct terms of the extra particles of `member` on one target (pair
+// softening rule of Sect. 3: max(eps_i, eps_j), none if either is
+// unsoftened), absolute FP32.
 __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float yi, float zi, float ei, int skip,
-                                            Acc &acc) {
+                                            int member, Acc &acc) {
     float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-    for (int k = 0; k < A.n_extra; k++) {
+    const int k0 = A.extra_per_member ? member : 0;
+    const int k1 = A.extra_per_member ? min(member + 1, A.n_extra) : A.n_extra;
+    for (int k = k0; k < k1; k++) {
         if (k == skip) continue;
+        if (!A.extra_per_member && (A.xmem ? A.xmem[k] : 0) != member) continue;
         float ek = A.xeps[k];
         float e = (ei == 0.f || ek == 0.f) ? 0.f : fmaxf(ei, ek);
         float dx = A.xyzm[4 * k] - xi, dy = A.xyzm[4 * k + 1] - yi, dz = A.xyzm[4 * k + 2] - zi;
@@ -337,7 +350,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     char *wsm = smem + wib * warp_smem_bytes(A.tile);
     const int nitem = A.n_extra + A.st->ngroup;
-    const TreeGeo G = tree_geo(A);
     unsigned long long np2p = 0, nm2p = 0;
     while (true) {
         int gi = 0;
@@ -349,13 +361,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
         if (gi < A.n_extra) {
             // ---- a particle outside the tree: 32 lanes share its interaction list
             const int kx = gi;
+            const int mk = A.extra_per_member ? kx : (A.xmem ? A.xmem[kx] : 0);
+            const TreeGeo G = tree_geo(A, mk);
+            const double *mb = A.mbounds + 5 * mk;
             float xi = A.xyzm[4 * kx], yi = A.xyzm[4 * kx + 1], zi = A.xyzm[4 * kx + 2];
             float ek = A.xeps[kx];
             float e = (ek == 0.f || A.eps_star == 0.f) ? 0.f : fmaxf(ek, A.eps_star);
             int blo[3], bhi[3];
             const float pv[3] = {xi, yi, zi};
             for (int a = 0; a < 3; a++) {
-                double q = floor(__dmul_rn(__dsub_rn((double)pv[a], A.st->bounds[a]), A.st->bounds[4]));
+                double q = floor(__dmul_rn(__dsub_rn((double)pv[a], mb[a]), mb[4]));
                 q = fmin(fmax(q, -8388608.0), 8388608.0);
                 blo[a] = (int)q;
                 bhi[a] = (int)q + 1;
@@ -363,7 +378,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
             float g[3];
             geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), G.lo, G.unit, g);
             bool ok = true;
-            if (G.ncell > 0)
+            if (G.ncell > 0 && G.root >= 0)
                 ok = walk_group<false, QUAD>(A, G, wsm, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], lane, 32,
                                              e * e, acc, a2, a3);
             if (!ok) {
@@ -372,7 +387,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
             }
             combine_lanes(acc, 1, 32);
             if (lane == 0) {
-                extra_terms(A, xi, yi, zi, ek, kx, acc);
+                extra_terms(A, xi, yi, zi, ek, kx, mk, acc);
                 A.xout[4 * kx] = acc.ax + acc.cx;
                 A.xout[4 * kx + 1] = acc.ay + acc.cy;
                 A.xout[4 * kx + 2] = acc.az + acc.cz;
@@ -382,7 +397,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
         }
         // ---- a group of the tree
         int4 grp = __ldg(&A.groups[gi - A.n_extra]);
-        if (grp.z < 0 || grp.z >= G.ncell || grp.x < 0 || grp.y < 1 || grp.y > 32 || grp.x + grp.y > A.n) {
+        const int mg = member_of(A.moff, A.M, grp.x);
+        const TreeGeo G = tree_geo(A, mg);
+        if (grp.z < 0 || grp.z >= G.ncell || G.root < 0 || grp.x < 0 || grp.y < 1 || grp.y > 32 ||
+            grp.x + grp.y > A.n) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
         }
@@ -407,7 +425,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
         if (lane < s) {
             // the star's own pair was evaluated at r = 0: remove its -m/eps
             if (SOFT) acc.ph += p.w * rsqrtf(A.eps2);
-            if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, acc);
+            if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, mg, acc);
             int o = A.perm[grp.x + lane];
             A.ax[o] = acc.ax + acc.cx;
             A.ay[o] = acc.ay + acc.cy;
@@ -457,7 +475,8 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
 }
 
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
-                    float *ax, float *ay, float *az, float *pot, float *xout, cudaStream_t s) {
+                    const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
+                    float *xout, cudaStream_t s) {
     Workspace &w = c->w;
     WalkArgs A;
     A.pos = w.pos;
@@ -469,6 +488,12 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.st = w.st;
     A.cell_cap = (int)c->cell_cap;
     A.n = (int)c->n;
+    A.moff = w.moff;
+    A.M = c->n_members;
+    A.mbounds = w.mbounds;
+    A.mroot = w.mroot;
+    A.xmem = xmem;
+    A.extra_per_member = extra_per_member ? 1 : 0;
     A.mac = mac_table(theta);
     A.eps2 = eps_star * eps_star;
     A.eps_star = eps_star;

@@ -23,7 +23,8 @@ RV_OK, RV_E_INVAL, RV_E_CUDA, RV_E_WORKSPACE, RV_E_STACK, RV_E_TIMEOUT, RV_E_NOT
 STATUS_NAMES = ["RV_OK", "RV_E_INVAL", "RV_E_CUDA", "RV_E_WORKSPACE", "RV_E_STACK", "RV_E_TIMEOUT", "RV_E_NOTBUILT",
                 "RV_E_TOO_LARGE"]
 EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", "rv_set_workspace", "rv_build_tree",
-           "rv_tree_forces", "rv_perturber_forces", "rv_system_forces", "rv_kdk_step", "rv_energy",
+           "rv_build_tree_members", "rv_tree_forces", "rv_tree_forces_members", "rv_perturber_forces",
+           "rv_system_forces", "rv_kdk_step", "rv_kdk_step_graph", "rv_energy",
            "rv_select_perturbers", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
            "rv_launch_count", "rv_last_error"]
 
@@ -52,7 +53,7 @@ class rv_system(C.Structure):
                 ("az", C.c_void_p), ("pot", C.c_void_p), ("n_chain", C.c_int32), ("chain_m", C.c_void_p),
                 ("chain_x", C.c_void_p), ("chain_v", C.c_void_p), ("chain_a", C.c_void_p),
                 ("chain_pot", C.c_void_p), ("pert_mode", C.c_int32), ("pert_radius", C.c_float),
-                ("pert_k", C.c_int32)]
+                ("pert_k", C.c_int32), ("n_members", C.c_int32), ("member_offsets", C.c_void_p)]
 
 
 def lib_path() -> str:
@@ -86,7 +87,10 @@ def _declare(L):
     L.rv_destroy.restype = None
     L.rv_set_workspace.argtypes = [vp, vp, C.c_size_t]
     L.rv_build_tree.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.rv_build_tree_members.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
     L.rv_tree_forces.argtypes = [vp, f32, f32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rv_tree_forces_members.argtypes = [vp, f32, f32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rv_kdk_step_graph.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp, vp]
     L.rv_perturber_forces.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rv_system_forces.argtypes = [vp, C.POINTER(rv_system), vp]
     L.rv_kdk_step.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp]
@@ -202,6 +206,30 @@ class Context:
         self._check(self.L.rv_build_tree(self.h, n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _stream(stream)))
         self.n = n
 
+    def build_tree_members(self, offsets, x, y, z, m, stream=None):
+        """Independent members stored one after another; offsets: host ints [n_members + 1]."""
+        import numpy as np
+        _need_cuda(x, y, z, m)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._check(self.L.rv_build_tree_members(self.h, len(off) - 1, off.ctypes.data_as(C.c_void_p), _ptr(x),
+                                                 _ptr(y), _ptr(z), _ptr(m), _stream(stream)))
+        self.n = int(off[-1])
+
+    def tree_forces_members(self, theta=None, eps_star=None, extra_xyzm=None, extra_eps=None, extra_member=None,
+                            out=None, stream=None):
+        import torch
+        theta = self.cfg.theta if theta is None else theta
+        eps_star = self.cfg.eps_star if eps_star is None else eps_star
+        if out is None:
+            out = [torch.empty(self.n, dtype=torch.float32, device="cuda") for _ in range(4)]
+        k = 0 if extra_xyzm is None else int(extra_xyzm.shape[0])
+        xout = torch.empty((max(k, 1), 4), dtype=torch.float32, device="cuda") if k else None
+        _need_cuda(*out, extra_xyzm, extra_eps, extra_member)
+        self._check(self.L.rv_tree_forces_members(self.h, float(theta), float(eps_star), k, _ptr(extra_xyzm),
+                                                  _ptr(extra_eps), _ptr(extra_member), *[_ptr(o) for o in out],
+                                                  _ptr(xout), _stream(stream)))
+        return tuple(out) + ((xout[:k],) if k else ())
+
     def tree_forces(self, theta=None, eps_star=None, extra_xyzm=None, extra_eps=None, out=None, stream=None):
         """Returns (ax, ay, az, pot[, extra_out (k,4)]) as new or given CUDA tensors."""
         import torch
@@ -287,9 +315,15 @@ class Context:
     def kdk_step(self, sysobj, dt, nsteps=1, stream=None):
         self._check(self.L.rv_kdk_step(self.h, C.byref(sysobj.c()), float(dt), int(nsteps), _stream(stream)))
 
+    def kdk_step_graph(self, sysobj, dt, nsteps=1, energy_out=None, stream=None):
+        """Graph-captured KDK steps; `stream` must be a torch.cuda.Stream (not the default stream)."""
+        self._check(self.L.rv_kdk_step_graph(self.h, C.byref(sysobj.c()), float(dt), int(nsteps),
+                                             _ptr(energy_out), _stream(stream)))
+
     def energy(self, sysobj, out=None, stream=None):
         import torch
-        out = torch.zeros(10, dtype=torch.float64, device="cuda") if out is None else out
+        if out is None:
+            out = torch.zeros(10 * max(1, sysobj.n_members), dtype=torch.float64, device="cuda")
         self._check(self.L.rv_energy(self.h, C.byref(sysobj.c()), _ptr(out), _stream(stream)))
         return out
 
@@ -298,7 +332,11 @@ class System:
     """Device state of stars (FP32, caller order) and an optional chain (FP64)."""
 
     def __init__(self, pos, vel, mass, chain_m=None, chain_x=None, chain_v=None, pert_mode=0, pert_radius=0.0,
-                 pert_k=0):
+                 pert_k=0, member_offsets=None):
+        """pos/vel (3, n); mass (n,). member_offsets: host ints [M + 1] for M
+        independent members stored one after another (None: one member).
+        chain_* are member-major: chain_m (M n_ch,) or (n_ch,), chain_x/v
+        (M n_ch, 3)."""
         import torch
         f32 = dict(dtype=torch.float32, device="cuda")
         f64 = dict(dtype=torch.float64, device="cuda")
@@ -319,6 +357,14 @@ class System:
         else:
             self.chain_m = self.chain_x = self.chain_v = self.chain_a = self.chain_pot = None
         self.pert_mode, self.pert_radius, self.pert_k = int(pert_mode), float(pert_radius), int(pert_k)
+        import numpy as np
+        if member_offsets is None:
+            self.n_members, self.member_offsets = 1, None
+        else:
+            self.member_offsets = np.ascontiguousarray(member_offsets, dtype=np.int64)
+            self.n_members = int(len(self.member_offsets) - 1)
+        if self.n_chain:
+            self.n_chain //= self.n_members          # chain members per member
         self._c = None
 
     def c(self) -> rv_system:
@@ -331,5 +377,7 @@ class System:
             t = getattr(self, f)
             setattr(s, f, t.data_ptr() if t is not None else None)
         s.pert_mode, s.pert_radius, s.pert_k = self.pert_mode, self.pert_radius, self.pert_k
+        s.n_members = self.n_members
+        s.member_offsets = None if self.member_offsets is None else self.member_offsets.ctypes.data
         self._c = s
         return s
