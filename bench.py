@@ -1,16 +1,24 @@
 """Benchmark: tree-force particles/s on one GB300 at p99 relative force
 error <= 1e-3 against the FP64 direct sum.
 
-Workload: Hernquist (Dehnen gamma = 1) galaxy, 2^20 equal-mass stars of total
-mass 1 and scale radius 1, plus one SMBH of mass 0.005 on a circular orbit at
-r = 0.5; star softening 0.005; SMBH-star forces unsoftened, FP64 for the
-stars within 0.02 of the SMBH; opening angle 0.5 with quadrupoles.
+Default workload (the one the metric is quoted on): a Hernquist (Dehnen
+gamma = 1) galaxy of 2^20 equal-mass stars, total mass 1, scale radius 1,
+plus one SMBH of mass 0.005 on a circular orbit at r = 0.5; star softening
+0.005; SMBH-star forces unsoftened, FP64 for the stars within 0.02 of the
+SMBH; opening angle 0.5 with quadrupoles.
 
 One step = the whole force path once: kick/drift, perturber selection, tree
-build (keys, sort, topology, multipoles, groups), tree walk, FP64 perturber
-coupling and chain hand-off, kick, FP64 energy/momentum totals.
+build (bounds, keys, sort, topology, multipoles, groups), tree walk, FP64
+perturber coupling and chain hand-off, kick, FP64 energy/momentum totals.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload hernquist_bh|hernquist_binary|plummer|ensemble]
+
+Other workloads: `hernquist_binary` (2^22 stars, central SMBH pair, 256
+nearest perturbers), `plummer` (4096 stars), `ensemble` (64 independent
+Hernquist realisations, sizes log-uniform in 8192..524288, each with a
+central SMBH pair, all members in one build and one walk per step, the step
+captured in a CUDA graph, walk parameters from the autotuner).
 
 Under torchrun (N > 1) every rank runs its own realisation (replicas: no
 data exchange); the value is the sum of particles over ranks / max time.
@@ -21,7 +29,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -35,26 +42,61 @@ sys.path.insert(0, ROOT)
 
 METRIC = "tree-force particles/s on 1 GB300 at p99 rel. force err ≤1e-3 vs FP64 direct"
 UNIT = "particles/s"
-N_STARS = 1 << 20
-THETA, EPS, PERT_R, DT = 0.5, 0.005, 0.02, 1e-3
 FLOP_P2P, FLOP_M2P = 20, 54   # per interaction, counted from the walk kernel's source
 L2_FLUSH_BYTES = 256 << 20
+WALK_PROFILE = os.path.join(ROOT, "profiles", "walk_tree_k_hernquist_n1048576.md")
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def _workload_config(n_ranks):
-    return {"workload": f"hernquist_gamma1_n{N_STARS}_smbh", "n_stars": N_STARS, "smbh_mass": 0.005,
-            "smbh_orbit_r": 0.5, "eps_star": EPS, "theta": THETA, "quadrupole": True, "n_leaf": 16,
-            "walk_group": 32, "tile": 64, "perturber_radius": PERT_R, "dt": DT,
-            "step": "kdk + perturber select + build + walk + fp64 perturber/chain + energy",
-            "parallelism": f"replicas{n_ranks}" if n_ranks > 1 else "single",
-            "l2": "flushed (256 MiB write) before every timed step"}
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def make_workload(name: str, rank: int = 0) -> dict:
+    import ics
+    base = 1000 * rank
+    if name == "hernquist_bh":
+        w = ics.hernquist_bh_workload(1 << 20, seed=2 + base)
+        d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=w.chain.mass,
+                 chain_x=w.chain.pos, chain_v=w.chain.vel, pert_mode=1, pert_radius=0.02, pert_k=0)
+        cfg = {"workload": "hernquist_gamma1_n1048576_smbh", "n_stars": 1 << 20, "smbh_mass": 0.005,
+               "smbh_orbit_r": 0.5, "perturber_radius": 0.02}
+    elif name == "hernquist_binary":
+        w = ics.hernquist_binary_workload(1 << 22, seed=3 + base)
+        d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=w.chain.mass,
+                 chain_x=w.chain.pos, chain_v=w.chain.vel, pert_mode=2, pert_radius=0.0, pert_k=256)
+        cfg = {"workload": "hernquist_gamma1_n4194304_smbh_binary", "n_stars": 1 << 22, "binary_a": 0.01,
+               "binary_e": 0.1, "smbh_mass": 0.005, "perturbers": "256 nearest"}
+    elif name == "plummer":
+        w = ics.plummer_workload(4096, seed=1 + base)
+        d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=None, chain_x=None,
+                 chain_v=None, pert_mode=0, pert_radius=0.0, pert_k=0)
+        cfg = {"workload": "plummer_n4096", "n_stars": 4096}
+    elif name == "ensemble":
+        e = ics.ensemble_workload(64, seed=4 + base)
+        d = dict(pos=e["pos"], vel=e["vel"], mass=e["mass"], offsets=e["offsets"], chain_m=e["chain_m"],
+                 chain_x=e["chain_x"], chain_v=e["chain_v"], pert_mode=2, pert_radius=0.0, pert_k=256)
+        cfg = {"workload": "ensemble64_hernquist_gamma1_smbh_binary", "n_stars": int(e["offsets"][-1]),
+               "members": 64, "member_sizes": "log-uniform 8192..524288 (seed 4)", "perturbers": "256 nearest",
+               "graph_captured": True}
+    else:
+        raise ValueError(name)
+    d["eps"] = 0.01 if name == "plummer" else 0.005
+    d["theta"] = 0.5
+    d["dt"] = 1e-3
+    d["name"] = name
+    d["n"] = int(d["mass"].shape[0])
+    cfg.update({"eps_star": d["eps"], "theta": 0.5, "quadrupole": True, "dt": 1e-3})
+    d["config"] = cfg
+    return d
+
+
+def member_ranges(d):
+    off = d["offsets"] if d["offsets"] is not None else np.array([0, d["n"]])
+    return [(int(off[k]), int(off[k + 1])) for k in range(len(off) - 1)]
 
 
 # ---------------------------------------------------------------------------
@@ -66,10 +108,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap"
 
     def __init__(self, index):
-        self.index = index
-        self.samples = []
-        self.proc = None
-        self.thread = None
+        self.index, self.samples, self.proc, self.thread = index, [], None, None
 
     def start(self):
         try:
@@ -119,47 +158,69 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reported baseline; never tuned)
 # ---------------------------------------------------------------------------
-def oracle_step_time(p32, m32, bh_pos32, bh_mass, sample, seed=0):
-    """Seconds for one oracle force pass on this workload, from a bounded
-    sample: full tree build + tree walk for `sample` stars, scaled to all
-    stars. Returns (seconds per full pass, description)."""
+def oracle_step_time(d, sample=65536, seed=0, max_stars=1 << 20):
+    """Seconds for one oracle force pass over the whole workload, from a
+    bounded sample: oracle trees of the members covering the first
+    <= max_stars stars, walks of `sample` of their stars, both scaled to all
+    stars. Returns (seconds, description)."""
     import ics
     import oracle
-    n = p32.shape[1]
-    tg = ics.subsample(n, sample, seed=seed)
-    t0 = time.perf_counter()
-    T = oracle.Tree(p32, m32, 16, 32)
-    t1 = time.perf_counter()
-    T.forces(THETA, float(np.float32(EPS)), True, bh_pos32, np.array([bh_mass]), [0.0], targets=tg)
-    t2 = time.perf_counter()
-    full = (t1 - t0) + (t2 - t1) * n / len(tg)
-    return full, f"oracle tree build of all {n} stars + walk of {len(tg)} sampled stars, walk time scaled x{n / len(tg):.1f}"
+    p32 = d["pos"].astype(np.float32)
+    m32 = d["mass"].astype(np.float32)
+    ranges = member_ranges(d)
+    chosen, tot = [], 0
+    for (s, e) in ranges:
+        if e == s:
+            continue
+        if chosen and tot + (e - s) > max_stars:
+            break
+        chosen.append((s, e))
+        tot += e - s
+    per = max(1, sample // len(chosen))
+    t_build = t_walk = 0.0
+    walked = 0
+    for k, (s, e) in enumerate(chosen):
+        t0 = time.perf_counter()
+        T = oracle.Tree(p32[:, s:e], m32[s:e], 16, 32)
+        t1 = time.perf_counter()
+        tg = ics.subsample(e - s, per, seed=seed + k)
+        if d["chain_m"] is not None:
+            nch = len(d["chain_m"]) // len(ranges)
+            mi = ranges.index((s, e))
+            cm = d["chain_m"][mi * nch:(mi + 1) * nch]
+            cx = d["chain_x"][mi * nch:(mi + 1) * nch]
+            com = (cm[:, None] * cx).sum(0) / cm.sum()
+            T.forces(d["theta"], float(np.float32(d["eps"])), True, com.astype(np.float32).reshape(3, 1),
+                     np.array([float(np.float32(cm.sum()))]), [0.0], targets=tg)
+        else:
+            T.forces(d["theta"], float(np.float32(d["eps"])), True, targets=tg)
+        t2 = time.perf_counter()
+        t_build += t1 - t0
+        t_walk += t2 - t1
+        walked += len(tg)
+    full = (t_build * d["n"] / tot) + t_walk * d["n"] / walked
+    desc = (f"oracle trees of {len(chosen)} member(s) ({tot} stars) + walks of {walked} sampled stars; "
+            f"build scaled x{d['n'] / tot:.2f}, walk scaled x{d['n'] / walked:.1f}")
+    return full, desc
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    import ics
-    w = ics.hernquist_bh_workload(N_STARS, seed=2)
-    p32 = w.stars.pos.astype(np.float32)
-    m32 = w.stars.mass.astype(np.float32)
-    bh = w.chain.pos.T.astype(np.float32)
-    sample = 16384
+    d = make_workload(args.workload, 0)
     for i in range(args.warmup):
-        oracle_step_time(p32, m32, bh, float(np.float32(w.chain.mass[0])), sample, seed=100 + i)
+        oracle_step_time(d, sample=8192, seed=100 + i)
     times, desc = [], ""
     for i in range(args.steps):
-        t, desc = oracle_step_time(p32, m32, bh, float(np.float32(w.chain.mass[0])), sample, seed=i)
+        t, desc = oracle_step_time(d, sample=8192, seed=i)
         times.append(t)
     ms = 1e3 * float(np.mean(times))
-    value = N_STARS / (ms / 1e3)
-    cores = os.cpu_count()
+    value = d["n"] / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _workload_config(1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": d["config"],
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -168,11 +229,57 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def _walk_traffic():
+    """dram bytes per walk launch from the committed ncu summary, if it was
+    taken on the current walk.cu (else None)."""
+    import hashlib
+    import re
+    try:
+        txt = open(WALK_PROFILE).read()
+        src = open(os.path.join(ROOT, "paper_1507_01009_gb300", "csrc", "walk.cu"), "rb").read()
+    except OSError:
+        return None
+    h = hashlib.sha256(src).hexdigest()[:16]
+    m = re.search(r"walk.cu sha256 prefix: `([0-9a-f]+)`", txt)
+    t = re.search(r"= \*\*([0-9.]+) MB per launch\*\*", txt)
+    if not m or not t or m.group(1) != h:
+        return None
+    return float(t.group(1)) * 1e6
+
+
+def p99_vs_direct(d, S, sample=2048, seed=77):
+    """p99 relative acceleration error of the current GPU forces against the
+    FP64 direct sum over each sampled star's own member (stars softened,
+    chain members unsoftened)."""
+    import ics
+    import oracle
+    xs = np.stack([t.cpu().numpy() for t in (S.x, S.y, S.z)]).astype(np.float64)
+    a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
+    m32 = S.m.cpu().numpy().astype(np.float64)
+    eps = float(np.float32(d["eps"]))
+    ranges = member_ranges(d)
+    tg = ics.subsample(d["n"], sample, seed=seed)
+    cx = S.chain_x.cpu().numpy().reshape(-1, 3) if S.chain_x is not None else None
+    errs = []
+    for k, (s, e) in enumerate(ranges):
+        t = tg[(tg >= s) & (tg < e)]
+        if len(t) == 0:
+            continue
+        pos, mass, epsv = xs[:, s:e], m32[s:e], np.full(e - s, eps)
+        if cx is not None:
+            nch = S.n_chain
+            pos = np.concatenate([pos, cx[k * nch:(k + 1) * nch].T], 1)
+            mass = np.concatenate([mass, d["chain_m"][k * nch:(k + 1) * nch]])
+            epsv = np.concatenate([epsv, np.zeros(nch)])
+        ad, _ = oracle.direct(pos, mass, epsv, targets=t - s)
+        errs.append(oracle.rel_err(a[:, t], ad))
+    return oracle.percentile(np.concatenate(errs), 0.99)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    import ics
     from paper_1507_01009_gb300 import rv
 
     ws, rank, local = _dist()
@@ -180,144 +287,159 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    d = make_workload(args.workload, rank)
+    n = d["n"]
+    use_graph = args.workload == "ensemble"
 
-    w = ics.hernquist_bh_workload(N_STARS, seed=2 + 1000 * rank)
-    p32 = w.stars.pos.astype(np.float32)
-    v32 = w.stars.vel.astype(np.float32)
-    m32 = w.stars.mass.astype(np.float32)
-    ctx = rv.Context(N_STARS, theta=THETA, eps_star=float(np.float32(EPS)), n_leaf=16, group=32, tile=64)
-    S = rv.System(p32, v32, m32, chain_m=w.chain.mass, chain_x=w.chain.pos, chain_v=w.chain.vel, pert_mode=1,
-                  pert_radius=PERT_R)
-    energy_out = torch.zeros(10, dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream()
+    tune = {"group": 32, "n_leaf": 16, "tile": 64}
+    tuned = None
+    if args.workload == "ensemble":
+        from paper_1507_01009_gb300 import autotune
+        p32 = d["pos"].astype(np.float32)
+        xs = [torch.from_numpy(np.ascontiguousarray(p32[a])).to(dev) for a in range(3)]
+        ms = torch.from_numpy(d["mass"].astype(np.float32)).to(dev)
+        tuned = autotune.autotune(*xs, ms, offsets=d["offsets"], theta=d["theta"], eps_star=float(np.float32(d["eps"])),
+                                  grid=autotune.candidates(groups=(32,), leaves=(16, 32), tiles=(64, 128)), reps=2)
+        tune = tuned["config"]
+        del xs, ms
+    ctx = rv.Context(n, theta=d["theta"], eps_star=float(np.float32(d["eps"])), **tune)
+    S = rv.System(d["pos"], d["vel"], d["mass"], chain_m=d["chain_m"], chain_x=d["chain_x"], chain_v=d["chain_v"],
+                  pert_mode=d["pert_mode"], pert_radius=d["pert_radius"], pert_k=d["pert_k"],
+                  member_offsets=d["offsets"])
+    M = S.n_members
+    energy_out = torch.zeros(10 * M, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev) if use_graph else torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step():
-        ctx.kdk_step(S, DT, 1)
-        ctx.energy(S, out=energy_out)
+        if use_graph:
+            ctx.kdk_step_graph(S, d["dt"], 1, energy_out=energy_out, stream=stream)
+        else:
+            ctx.kdk_step(S, d["dt"], 1, stream=stream)
+            ctx.energy(S, out=energy_out, stream=stream)
 
-    ctx.system_forces(S)
-    for _ in range(max(3, args.warmup)):
-        step()
-    ctx.sync_status()
+    with torch.cuda.stream(stream):
+        ctx.system_forces(S, stream=stream)
+        for _ in range(max(3, args.warmup)):
+            step()
+    ctx.sync_status(stream=stream)
 
-    # ---- timed region: exactly K steps, each timed with CUDA events, L2 flushed before each
+    # ---- timed region: exactly K steps, CUDA events on the launching stream, L2 flushed before each
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    sampler = ClockSampler(gpu_id)
     sampler.start()
     time.sleep(0.3)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     l0 = ctx.launch_count()
-    for k in range(args.steps):
-        flush.fill_(k & 255)
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
+    ctx.profile_walk(True)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     launches = ctx.launch_count() - l0
+    walk_total_ms, walk_launches = ctx.walk_time()
+    ctx.profile_walk(False)
     sampler.stop()
-    ctx.sync_status()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(np.sum(step_ms))
+    ctx.sync_status(stream=stream)
+    total_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = ws * N_STARS * args.steps / (total_ms / 1e3)
+    value = ws * n * args.steps / (total_ms / 1e3)
+    p99 = p99_vs_direct(d, S) if rank == 0 else None
 
-    # ---- accuracy of the forces the timed steps produced (current state) vs FP64 direct
-    p99 = None
-    if rank == 0:
-        import oracle
-        xs = np.stack([t_.cpu().numpy() for t_ in (S.x, S.y, S.z)]).astype(np.float64)
-        a = np.stack([t_.cpu().numpy() for t_ in (S.ax, S.ay, S.az)]).astype(np.float64)
-        cx = S.chain_x.cpu().numpy().reshape(-1, 3).T
-        allp = np.concatenate([xs, cx], 1)
-        allm = np.concatenate([m32.astype(np.float64), w.chain.mass])
-        epsv = np.concatenate([np.full(N_STARS, float(np.float32(EPS))), [0.0]])
-        tg = ics.subsample(N_STARS, 2048, seed=77)
-        ad, _ = oracle.direct(allp, allm, epsv, targets=tg)
-        p99 = oracle.percentile(oracle.rel_err(a[:, tg], ad), 0.99)
-
-    # ---- dominant kernel (tree walk): CUDA events around rv_tree_forces on the launching stream
-    walk_ms, flops = [], []
-    xyzm = torch.tensor([[float(S.chain_x[0]), float(S.chain_x[1]), float(S.chain_x[2]), float(S.chain_m[0])]],
-                        dtype=torch.float32, device=dev)
-    xeps = torch.zeros(1, dtype=torch.float32, device=dev)
-    outs = (S.ax, S.ay, S.az, S.pot)
-    for k in range(args.steps):
-        ctx.build_tree(S.x, S.y, S.z, S.m)
-        flush.fill_(k & 255)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.tree_forces(extra_xyzm=xyzm, extra_eps=xeps, out=outs)
-        e1.record(stream)
-        e1.synchronize()
-        walk_ms.append(e0.elapsed_time(e1))
+    # ---- dominant kernel: the walk. Its launches inside the timed steps were timed
+    # with CUDA events on the launching stream (not possible inside a replayed
+    # graph: then a separate loop of build + walk on the same stream is timed).
+    n_p2p, n_m2p = ctx.walk_stats()
+    flop = FLOP_P2P * n_p2p + FLOP_M2P * n_m2p
+    if walk_launches > 0:
+        walk_ms = walk_total_ms / walk_launches
+        walk_src = "walk launches inside the timed steps"
+    else:
+        pairs = []
+        off = d["offsets"] if d["offsets"] is not None else [0, n]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ctx.build_tree_members(off, S.x, S.y, S.z, S.m, stream=stream)
+                flush.fill_(k & 255)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.tree_forces_members(out=(S.ax, S.ay, S.az, S.pot), stream=stream)
+                e1.record(stream)
+                pairs.append((e0, e1))
+        torch.cuda.synchronize()
+        ctx.sync_status(stream=stream)
+        walk_ms = float(np.mean([a.elapsed_time(b) for a, b in pairs]))
         n_p2p, n_m2p = ctx.walk_stats()
-        flops.append(FLOP_P2P * n_p2p + FLOP_M2P * n_m2p)
-    ctx.sync_status()
-    walk_s = float(np.mean(walk_ms)) / 1e3
-    achieved = float(np.mean(flops)) / walk_s / 1e12
+        flop = FLOP_P2P * n_p2p + FLOP_M2P * n_m2p
+        walk_src = "separate build + walk loop (steps replayed from a CUDA graph); extra particles omitted"
+    achieved = flop / (walk_ms / 1e3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock
+    traffic = _walk_traffic() if args.workload == "hernquist_bh" else None
     roofline = {"bound": "alu", "kernel": "walk_tree_k", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_note": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
-                "walk_ms": float(np.mean(walk_ms)), "flop_per_launch": float(np.mean(flops)),
-                "interactions_per_star": float((n_p2p + n_m2p) / N_STARS),
-                "walk_share_of_step": float(np.mean(walk_ms)) / ms_per_step}
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_note": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz (derived, not measured)",
+                "walk_ms": walk_ms, "walk_timing": walk_src, "flop_per_launch": float(flop),
+                "interactions_per_star": float((n_p2p + n_m2p) / max(n, 1)),
+                "walk_share_of_step": walk_ms / ms_per_step}
 
     # ---- end to end through the public API with host (pinned) buffers
-    host = {k_: torch.empty(N_STARS, dtype=torch.float32, pin_memory=True)
-            for k_ in ("x", "y", "z", "vx", "vy", "vz", "m", "ax", "ay", "az", "pot")}
-    for k_, arr in zip(("x", "y", "z"), p32):
-        host[k_].copy_(torch.from_numpy(np.ascontiguousarray(arr)))
-    for k_, arr in zip(("vx", "vy", "vz"), v32):
-        host[k_].copy_(torch.from_numpy(np.ascontiguousarray(arr)))
-    host["m"].copy_(torch.from_numpy(m32))
-    for k_ in ("ax", "ay", "az", "pot"):
-        host[k_].copy_(getattr(S, k_).cpu())
-    e_host = torch.empty(10, dtype=torch.float64, pin_memory=True)
-    ins = ("x", "y", "z", "vx", "vy", "vz", "m", "ax", "ay", "az")
-    outs_h = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "pot")
-    h2d = 4 * N_STARS * len(ins)
-    d2h = 4 * N_STARS * len(outs_h) + 80
+    fields_in = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
+    fields_out = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "pot")
+    host = {f: torch.empty(n, dtype=torch.float32, pin_memory=True) for f in set(fields_in) | set(fields_out) | {"m"}}
+    for f in host:
+        host[f].copy_(getattr(S, f).cpu())
+    e_host = torch.empty(10 * M, dtype=torch.float64, pin_memory=True)
+    h2d = 4 * n * (len(fields_in) + 1)
+    d2h = 4 * n * len(fields_out) + 80 * M
     e2e_ms = []
-    for k in range(args.steps):
-        flush.fill_(k & 255)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k_ in ins:
-            getattr(S, k_).copy_(host[k_], non_blocking=True)
-        step()
-        for k_ in outs_h:
-            host[k_].copy_(getattr(S, k_), non_blocking=True)
-        e_host.copy_(energy_out, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    ctx.sync_status()
-    e2e_val = ws * N_STARS / (float(np.mean(e2e_ms)) / 1e3)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for f in fields_in + ("m",):
+                getattr(S, f).copy_(host[f], non_blocking=True)
+            step()
+            for f in fields_out:
+                host[f].copy_(getattr(S, f), non_blocking=True)
+            e_host.copy_(energy_out, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+    ctx.sync_status(stream=stream)
+    e2e_val = ws * n / (float(np.mean(e2e_ms)) / 1e3)
 
-    # ---- CPU oracle on this machine's host cores (bounded sample), rank 0 at N = 1 only
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        sec, desc = oracle_step_time(p32, m32, w.chain.pos.T.astype(np.float32), float(np.float32(w.chain.mass[0])),
-                                     65536, seed=3)
-        cpu = {"value": N_STARS / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+        sec, desc = oracle_step_time(d, sample=65536, seed=3)
+        cpu = {"value": n / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
 
     if rank == 0:
+        cfg = dict(d["config"])
+        cfg.update({"n_leaf": tune["n_leaf"], "walk_group": tune["group"], "tile": tune["tile"],
+                    "step": "kdk + perturber select + build + walk + fp64 perturber/chain + energy",
+                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                    "l2": "flushed (256 MiB write) before every timed step"})
+        if tuned is not None:
+            cfg["autotuned"] = {"cached": tuned["cached"], "candidates": len(tuned["table"])}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": _workload_config(ws), "p99_rel_err_vs_fp64_direct": p99,
-                "clocks": sampler.summary(),
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+                "p99_rel_err_vs_fp64_direct": p99, "clocks": sampler.summary(),
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": float(np.mean(e2e_ms))},
                 "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu}
@@ -333,6 +455,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="hernquist_bh", choices=["hernquist_bh", "hernquist_binary", "plummer",
+                                                                   "ensemble"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -241,3 +241,26 @@ def subsample(n: int, k: int, seed: int) -> np.ndarray:
     """k distinct indices of range(n), sorted, seeded."""
     k = min(k, n)
     return np.sort(rng(seed).choice(n, size=k, replace=False)).astype(np.int64)
+
+
+def ensemble_workload(members: int = 64, lo: int = 8192, hi: int = 524288, seed: int = 4,
+                      sizes: np.ndarray | None = None) -> dict:
+    """Ensemble of independent Hernquist realisations of uneven N (log-uniform
+    sizes), each with a central SMBH pair (a = 0.01, e = 0.1, m = 0.005 each),
+    stored one after another. Member k uses seed 1000 + k. Returns a dict with
+    pos/vel (3, N), mass (N,), offsets (members + 1,), chain_m (2 members,),
+    chain_x/chain_v (2 members, 3)."""
+    if sizes is None:
+        sizes = ensemble_sizes(members, lo, hi, seed)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    pos, vel, mass = [], [], []
+    for k, n in enumerate(sizes):
+        p = hernquist(int(n), 1000 + k)
+        pos.append(p.pos)
+        vel.append(p.vel)
+        mass.append(p.mass)
+    b = central_binary()
+    m = len(sizes)
+    return {"pos": np.concatenate(pos, 1), "vel": np.concatenate(vel, 1), "mass": np.concatenate(mass),
+            "offsets": np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64), "sizes": sizes,
+            "chain_m": np.tile(b.mass, m), "chain_x": np.tile(b.pos, (m, 1)), "chain_v": np.tile(b.vel, (m, 1))}

@@ -272,6 +272,14 @@ rv_status rv_walk_stats(rv_ctx *ctx, int64_t out[2], void *stream);
  * the last call (and clears it), else RV_OK. */
 rv_status rv_sync_status(rv_ctx *ctx, void *stream);
 
+/* Walk timing: with enable != 0, every later tree-walk launch on this context
+ * that is not part of a graph capture records a pair of CUDA events around
+ * the walk kernel on its own stream; enabling (or disabling) clears the
+ * record. rv_walk_time waits for the recorded launches and returns their
+ * summed duration in milliseconds and their number. */
+rv_status rv_profile_walk(rv_ctx *ctx, int32_t enable);
+rv_status rv_walk_time(rv_ctx *ctx, double *total_ms, int64_t *launches);
+
 /* Number of kernels librv has launched through this context since it was
  * created (host-side count, incremented at each launch). */
 int64_t rv_launch_count(const rv_ctx *ctx);

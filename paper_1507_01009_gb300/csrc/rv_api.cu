@@ -149,7 +149,32 @@ rv_status rv_create(rv_ctx **out, int64_t n_max, const rv_config *cfg) {
 void rv_destroy(rv_ctx *c) {
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (int k = 0; k < 2 * c->cap_walk_events; k++)
+        if (c->walk_events[k]) cudaEventDestroy(c->walk_events[k]);
+    free(c->walk_events);
     free(c);
+}
+
+rv_status rv_profile_walk(rv_ctx *c, int32_t enable) {
+    if (!c) return RV_E_INVAL;
+    c->profile_walk = enable != 0;
+    c->n_walk_events = 0;
+    return RV_OK;
+}
+
+rv_status rv_walk_time(rv_ctx *c, double *total_ms, int64_t *launches) {
+    if (!c || !total_ms || !launches) return RV_E_INVAL;
+    double t = 0.0;
+    for (int k = 0; k < c->n_walk_events; k++) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(c->walk_events[2 * k + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->walk_events[2 * k], c->walk_events[2 * k + 1]);
+        if (e != cudaSuccess) return cuda_check(c, e, "walk time");
+        t += ms;
+    }
+    *total_ms = t;
+    *launches = c->n_walk_events;
+    return RV_OK;
 }
 
 rv_status rv_set_workspace(rv_ctx *c, void *dev, size_t bytes) {

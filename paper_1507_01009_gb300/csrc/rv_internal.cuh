@@ -101,6 +101,11 @@ struct rv_ctx {
     int64_t moff_host[rv::kMaxMembers + 1]; // their star offsets
     int64_t max_member;                     // largest member
     bool moff_on_device;                    // moff_host[0..n_members] already uploaded
+    // walk timing (rv_profile_walk): event pairs recorded around each walk launch
+    bool profile_walk;
+    int n_walk_events;
+    int cap_walk_events;
+    cudaEvent_t *walk_events;               // [2 cap_walk_events]
     // captured kick-drift-kick step (rv_kdk_step_graph)
     cudaGraphExec_t graph;
     long long graph_launches;

@@ -509,8 +509,32 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     if (e != cudaSuccess) return cuda_check(c, e, "walk reset");
     if (c->n == 0 && n_extra == 0) return RV_OK;
     const bool quad = c->cfg.quadrupole != 0;
+    // optional timing of this launch on its own stream (not while a graph is being captured)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (c->profile_walk) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cs);
+        if (cs == cudaStreamCaptureStatusNone) {
+            if (c->n_walk_events == c->cap_walk_events) {
+                int cap = c->cap_walk_events ? 2 * c->cap_walk_events : 64;
+                cudaEvent_t *ev = (cudaEvent_t *)realloc(c->walk_events, sizeof(cudaEvent_t) * 2 * cap);
+                if (!ev) return set_err(c, RV_E_CUDA, "walk timing events");
+                for (int k = 2 * c->cap_walk_events; k < 2 * cap; k++) ev[k] = nullptr;
+                c->walk_events = ev;
+                c->cap_walk_events = cap;
+            }
+            cudaEvent_t *pair = c->walk_events + 2 * c->n_walk_events;
+            if (!pair[0]) cudaEventCreate(&pair[0]);
+            if (!pair[1]) cudaEventCreate(&pair[1]);
+            ev0 = pair[0];
+            ev1 = pair[1];
+            c->n_walk_events++;
+        }
+    }
+    if (ev0) cudaEventRecord(ev0, s);
     if (eps_star > 0.f) e = quad ? launch_walk<true, true>(c, A, s) : launch_walk<true, false>(c, A, s);
     else e = quad ? launch_walk<false, true>(c, A, s) : launch_walk<false, false>(c, A, s);
+    if (ev1) cudaEventRecord(ev1, s);
     if (e != cudaSuccess) return cuda_check(c, e, "walk launch");
     return RV_OK;
 }

@@ -26,7 +26,7 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_build_tree_members", "rv_tree_forces", "rv_tree_forces_members", "rv_perturber_forces",
            "rv_system_forces", "rv_kdk_step", "rv_kdk_step_graph", "rv_energy",
            "rv_select_perturbers", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
-           "rv_launch_count", "rv_last_error"]
+           "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error"]
 
 
 class RvError(RuntimeError):
@@ -100,6 +100,8 @@ def _declare(L):
     L.rv_get_tree.argtypes = [vp, C.POINTER(rv_tree_view), vp]
     L.rv_walk_stats.argtypes = [vp, C.POINTER(C.c_int64), vp]
     L.rv_sync_status.argtypes = [vp, vp]
+    L.rv_profile_walk.argtypes = [vp, i32]
+    L.rv_walk_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.rv_launch_count.argtypes = [vp]
     L.rv_launch_count.restype = C.c_int64
     L.rv_last_error.argtypes = [vp]
@@ -198,6 +200,16 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.L.rv_launch_count(self.h))
+
+    def profile_walk(self, enable=True):
+        self._check(self.L.rv_profile_walk(self.h, int(bool(enable))))
+
+    def walk_time(self):
+        """(summed ms, launches) of the walks recorded since profile_walk(True)."""
+        t = C.c_double()
+        k = C.c_int64()
+        self._check(self.L.rv_walk_time(self.h, C.byref(t), C.byref(k)))
+        return float(t.value), int(k.value)
 
     # --- tree ---
     def build_tree(self, x, y, z, m, stream=None):
