@@ -265,8 +265,10 @@ typedef struct {
 rv_status rv_get_tree(rv_ctx *ctx, rv_tree_view *out, void *stream);
 
 /* Interaction counts of the last rv_tree_forces (synchronises `stream`):
- * out[0] = P2P pairs, out[1] = multipole (M2P) pairs, over all targets. */
-rv_status rv_walk_stats(rv_ctx *ctx, int64_t out[2], void *stream);
+ * out[0] = P2P pairs, out[1] = multipole (M2P) pairs, over all targets;
+ * out[2] = deepest walk stack (pending child ranges) seen since the context
+ * got its workspace. */
+rv_status rv_walk_stats(rv_ctx *ctx, int64_t out[3], void *stream);
 
 /* Synchronises `stream` and returns the first error latched by a kernel since
  * the last call (and clears it), else RV_OK. */

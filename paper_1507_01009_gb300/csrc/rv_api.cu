@@ -362,16 +362,19 @@ rv_status rv_get_tree(rv_ctx *c, rv_tree_view *out, void *stream) {
     return RV_OK;
 }
 
-rv_status rv_walk_stats(rv_ctx *c, int64_t out[2], void *stream) {
+rv_status rv_walk_stats(rv_ctx *c, int64_t out[3], void *stream) {
     if (!c || !out) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long v[2];
+    int hwm = 0;
     cudaError_t e = cudaMemcpyAsync(v, &c->w.st->n_p2p, sizeof(v), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hwm, &c->w.st->stack_hwm, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_check(c, e, "walk stats");
     out[0] = (int64_t)v[0];
     out[1] = (int64_t)v[1];
+    out[2] = hwm;
     return RV_OK;
 }
 

@@ -25,6 +25,11 @@
 
 #include "rv_internal.cuh"
 
+// Resident blocks per SM the walk kernel is compiled for (register budget).
+#ifndef RV_WALK_MIN_BLOCKS
+#define RV_WALK_MIN_BLOCKS 6
+#endif
+
 namespace rv {
 
 struct MacTable {
@@ -159,7 +164,8 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 // nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
 // any distance from the origin.
 template <bool SOFT, bool QUAD>
-__device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, char *wsm, const int blo[3],
+__device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
+                                           char *wsm, const int blo[3],
                                            const int bhi[3], const float g[3], float xi, float yi, float zi, int j0,
                                            int k, float eps2, Acc &acc, unsigned long long &np2p,
                                            unsigned long long &nm2p) {
@@ -214,7 +220,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
             long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
             long long gz = gap1(blo[2], bhi[2], b.z, b.z + side);
             unsigned long long d2 = (unsigned long long)(gx * gx + gy * gy + gz * gz);
-            accept = d2 >= A.mac.thr[b.w];
+            accept = d2 >= thr[b.w];
             if (!accept) {
                 lk = __ldg(&A.clink[c]);
                 leaf = (lk.x == lk.y);
@@ -345,9 +351,14 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
 // is their own grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited
 // to +-2^23); the tree's groups follow.
 template <bool SOFT, bool QUAD>
-__global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
+__global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree_k(WalkArgs A) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    // per-level opening thresholds in shared memory: lanes of a warp test cells
+    // of different levels, which a constant-bank read would serialise
+    __shared__ unsigned long long mac_thr[kLevels];
+    if (threadIdx.x < kLevels) mac_thr[threadIdx.x] = A.mac.thr[threadIdx.x];
+    __syncthreads();
     char *wsm = smem + wib * warp_smem_bytes(A.tile);
     const int nitem = A.n_extra + A.st->ngroup;
     unsigned long long np2p = 0, nm2p = 0;
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
             geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), G.lo, G.unit, g);
             bool ok = true;
             if (G.ncell > 0 && G.root >= 0)
-                ok = walk_group<false, QUAD>(A, G, wsm, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], lane, 32,
+                ok = walk_group<false, QUAD>(A, G, mac_thr, wsm, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], lane, 32,
                                              e * e, acc, a2, a3);
             if (!ok) {
                 if (lane == 0) latch_err(A.st, kErrStack);
@@ -413,7 +424,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_tree_k(WalkArgs A) {
         const int t = lane % s, sub = lane / s;
         const int j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k s take no list entries
         float4 p = __ldg(&A.pos[grp.x + t]);
-        bool ok = walk_group<SOFT, QUAD>(A, G, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], j0, k,
+        bool ok = walk_group<SOFT, QUAD>(A, G, mac_thr, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], j0, k,
                                          A.eps2, acc, a2, a3);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);

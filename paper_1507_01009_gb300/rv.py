@@ -285,9 +285,14 @@ class Context:
         }
 
     def walk_stats(self, stream=None):
-        out = (C.c_int64 * 2)()
+        """(P2P pairs, M2P pairs) of the last walk."""
+        return self.walk_stats3(stream)[:2]
+
+    def walk_stats3(self, stream=None):
+        """(P2P pairs, M2P pairs, deepest walk stack so far)."""
+        out = (C.c_int64 * 3)()
         self._check(self.L.rv_walk_stats(self.h, out, _stream(stream)))
-        return int(out[0]), int(out[1])
+        return int(out[0]), int(out[1]), int(out[2])
 
     def sync_status(self, stream=None):
         self._check(self.L.rv_sync_status(self.h, _stream(stream)))
