@@ -174,6 +174,11 @@ class Tree:
         lib().orc_tree_moments(self._h, _p(self.moments, _d))
         self.groups = np.zeros((self.ngroup, 3), dtype=np.int64)
         lib().orc_tree_groups(self._h, _p(self.groups, _i64))
+        # FP64 copies of the stars in key order
+        self.x_sorted = self.x[self.perm].astype(np.float64)
+        self.y_sorted = self.y[self.perm].astype(np.float64)
+        self.z_sorted = self.z[self.perm].astype(np.float64)
+        self.m_sorted = self.m[self.perm].astype(np.float64)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -304,3 +309,122 @@ def percentile(e, p):
     if s.size == 0:
         return float("nan")
     return float(s[max(0, math.ceil(p * s.size) - 1)])
+
+
+# ---------------------------------------------------------------------------
+# Learned cell-force correction (not in the paper): features, targets, MLP
+# ---------------------------------------------------------------------------
+MLP_IN, MLP_IN_PAD, MLP_HID, MLP_OUT, MLP_OUT_PAD = 11, 16, 64, 3, 8
+
+
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64:
+    the float32 value's low 16 bits are rounded away."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def cell_features(tree, cell, x, eps):
+    """Features of one (target at x, accepted cell) pair: r/|r| (3), s/|r|,
+    eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz), with r = x - com and s the
+    cell side; and the normalisation M/|r|^2 of the output."""
+    mo = tree.moments[cell]
+    M, com, Q = mo[0], mo[1:4], mo[4:10]
+    lev = tree.cells[cell, 0]
+    s = tree.L / 2.0 ** lev
+    r = np.asarray(x, dtype=np.float64) - com
+    d = np.linalg.norm(r)
+    f = np.concatenate([r / d, [s / d, eps / d], Q / (M * s * s)])
+    return f, M / (d * d)
+
+
+def cell_residual(tree, cell, x, eps):
+    """Exact softened force of the cell's stars on x minus the cell's softened
+    monopole + quadrupole force (the quantity the network learns)."""
+    c = tree.cells[cell]
+    first, count = c[1], c[2]
+    xs = np.stack([tree.x_sorted[first:first + count], tree.y_sorted[first:first + count],
+                   tree.z_sorted[first:first + count]])
+    ms = tree.m_sorted[first:first + count]
+    dx = xs - np.asarray(x, dtype=np.float64)[:, None]
+    r2 = (dx * dx).sum(0) + eps * eps
+    exact = (ms * r2 ** -1.5 * dx).sum(1)
+    mo = tree.moments[cell]
+    M, com = mo[0], mo[1:4]
+    q = mo[4:10]
+    Q = np.array([[q[0], q[3], q[4]], [q[3], q[1], q[5]], [q[4], q[5], q[2]]])
+    r = np.asarray(x, dtype=np.float64) - com
+    rho2 = r @ r + eps * eps
+    rinv = rho2 ** -0.5
+    Qr = Q @ r
+    rqr = r @ Qr
+    quad = -M * r * rinv ** 3 + Qr * rinv ** 5 - 2.5 * rqr * r * rinv ** 7
+    return exact - quad
+
+
+def silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+def silu_grad(z):
+    s = 1.0 / (1.0 + np.exp(-z))
+    return s * (1.0 + z * (1.0 - s))
+
+
+def mlp_forward(params, X, rounding=True):
+    """Forward pass in FP64 with the rounding points of the BF16 tensor-core
+    path: inputs, weights and hidden activations rounded to bfloat16, biases
+    and sums exact (rounding=False: plain FP64 everywhere). params: W1 (16,64),
+    b1 (64,), W2 (64,64), b2, W3 (64,8), b3 (8,) (padded rows/columns zero).
+    Returns (Y (n,3), cache)."""
+    rnd = bf16_round if rounding else (lambda a: np.asarray(a, np.float64))
+    W1, W2, W3 = (rnd(params[k]) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = (np.asarray(params[k], np.float64) for k in ("b1", "b2", "b3"))
+    X0 = rnd(X)
+    Z1 = X0 @ W1 + b1
+    H1 = rnd(silu(Z1))
+    Z2 = H1 @ W2 + b2
+    H2 = rnd(silu(Z2))
+    Y = H2 @ W3 + b3
+    return Y[:, :MLP_OUT], dict(X0=X0, Z1=Z1, H1=H1, Z2=Z2, H2=H2, W2=W2, W3=W3)
+
+
+def mlp_loss_grad(params, X, T, rounding=True):
+    """Mean squared error over the batch and the 3 outputs, and its analytic
+    gradient with respect to every parameter (straight-through the bfloat16
+    roundings)."""
+    Y, c = mlp_forward(params, X, rounding)
+    n = X.shape[0]
+    D = Y - T
+    loss = float((D * D).sum() / (n * MLP_OUT))
+    dY = np.zeros((n, MLP_OUT_PAD))
+    dY[:, :MLP_OUT] = 2.0 * D / (n * MLP_OUT)
+    g = {}
+    g["W3"] = c["H2"].T @ dY
+    g["b3"] = dY.sum(0)
+    dZ2 = (dY @ c["W3"].T) * silu_grad(c["Z2"])
+    g["W2"] = c["H1"].T @ dZ2
+    g["b2"] = dZ2.sum(0)
+    dZ1 = (dZ2 @ c["W2"].T) * silu_grad(c["Z1"])
+    g["W1"] = c["X0"].T @ dZ1
+    g["b1"] = dZ1.sum(0)
+    return loss, g
+
+
+def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) of FP64 master parameters in place;
+    state holds m, v and the step count t."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for k in params:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k], dtype=np.float64))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k], dtype=np.float64))
+        g = grads[k]
+        m[...] = b1 * m + (1 - b1) * g
+        v[...] = b2 * v + (1 - b2) * g * g
+        mh = m / (1 - b1 ** t)
+        vh = v / (1 - b2 ** t)
+        params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+    return params
