@@ -216,6 +216,48 @@ rv_status rv_select_perturbers(rv_ctx *ctx, int64_t n, const float *x, const flo
                                const float centre[3], int32_t mode, float radius, int32_t k, int32_t cap,
                                int32_t *idx, int32_t *count, void *stream);
 
+/* ---- Learned cell-force correction (not in the paper, whose tree uses the
+ * multipoles alone). A network of 11 features -> 64 -> 64 -> 3 (SiLU;
+ * bfloat16 weights and activations, FP32 accumulation on the tensor cores)
+ * predicts, for a point at r = x - com from an accepted cell of side s and
+ * mass M, (exact softened force of the cell's stars - its monopole +
+ * quadrupole force) * |r|^2 / M. Features (16 floats per row, 11 used):
+ * r/|r| (3), s/|r|, eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz).
+ * The parameter block (rv_mlp_param_bytes, device, caller-owned) holds FP32
+ * master weights, Adam moments and bfloat16 copies. */
+size_t rv_mlp_param_bytes(void);
+/* Device scratch rv_mlp_gradient needs for a batch of `batch` rows. */
+size_t rv_mlp_scratch_bytes(int64_t batch);
+/* Glorot-uniform weights from a SplitMix64 stream of `seed`, zero biases. */
+rv_status rv_mlp_init(void *params, uint64_t seed, void *stream);
+/* y[n][3] = network(x[n][16]) (device FP32). */
+rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y, void *stream);
+/* Mean squared error of network(x) against t[n][3] and its gradient with
+ * respect to the FP32 parameter vector (grad: device FP32 [5768], ordered W1
+ * 16x64, b1, W2 64x64, b2, W3 64x8, b3, row-major; loss: device FP32 [1] or
+ * NULL). Sums run in a fixed order. */
+rv_status rv_mlp_gradient(const void *params, int64_t n, const float *x, const float *t, float *grad, float *loss,
+                          void *scratch, size_t scratch_bytes, void *stream);
+/* One Adam step (step >= 1) on the master weights; refreshes the copies. */
+rv_status rv_mlp_adam(void *params, const float *grad, int32_t step, float lr, float beta1, float beta2,
+                      float adam_eps, void *stream);
+/* Training samples from the last tree: n_samples random stars (SplitMix64 of
+ * seed), each paired with a cell chosen uniformly among the cells its own
+ * walk accepts at theta (its box: its grid cell). Writes features x[n][16],
+ * targets t[n][3] (exact residual, FP32) and pairs[2n] = (sorted star slot,
+ * cell index; cell -1 if none accepted, then x, t are zero). */
+rv_status rv_mlp_samples(rv_ctx *ctx, float theta, float eps_star, int64_t n_samples, uint64_t seed, float *x,
+                         float *t, int32_t *pairs, void *stream);
+/* Tree forces at theta (as rv_tree_forces, no extra particles) plus the
+ * learned correction: the walk records every (group, cell) pair accepted at
+ * theta that a walk at theta_rec (< theta) would open, into device pairs[2
+ * pair_cap] with the count in npairs[1]; the network evaluates each pair at
+ * the group's geometric centre and adds the correction (device scratch
+ * gcorr[3 n]) to every star of the group. Synchronises `stream` once. */
+rv_status rv_tree_forces_mlp(rv_ctx *ctx, const void *params, float theta, float theta_rec, float eps_star,
+                             float *ax, float *ay, float *az, float *pot, int32_t *pairs, int32_t pair_cap,
+                             int32_t *npairs, float *gcorr, void *stream);
+
 /* Radius perturber search that allocates nothing and needs no context.
  * (The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- e.g. a chain integrator that looks for

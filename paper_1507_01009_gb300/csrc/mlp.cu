@@ -1,0 +1,696 @@
+// mlp.cu -- learned correction of cell forces (not in the paper).
+//
+// A small network (11 features -> 64 -> 64 -> 3, SiLU, bfloat16 weights and
+// activations, FP32 accumulation on the tensor cores with mma.sync m16n8k16)
+// predicts, for a star (or a walk group's centre) at r from an accepted
+// cell, the difference between the cell's exact softened force and its
+// monopole + quadrupole force, scaled by |r|^2 / M. Features: r/|r| (3),
+// s/|r|, eps/|r|, Q/(M s^2) (6), s the cell side.
+//
+// Training (per minibatch): tensor-core forward, FP32 backward (exact
+// gradients of the same rounded forward), per-block gradient partials summed
+// in a fixed order, Adam on FP32 master weights, bfloat16 copies refreshed.
+// Samples: random stars, a random cell among those each star's walk accepts
+// at a given angle (reservoir choice), features and exact residual target.
+// Inference in the tree force: the walk records the (group, cell) pairs
+// accepted at theta that a walk at theta_rec < theta would open; the network
+// evaluates each pair at the group's centre and the correction is added to
+// every star of the group.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "rv_internal.cuh"
+
+namespace rv {
+
+constexpr int kIn = 11, kInPad = 16, kHid = 64, kOut = 3, kOutPad = 8;
+// FP32 parameter vector (master weights, Adam moments and gradients share it):
+constexpr int oW1 = 0;                  // W1[k][n], 16 x 64 (rows 11..15 zero)
+constexpr int ob1 = oW1 + kInPad * kHid;
+constexpr int oW2 = ob1 + kHid;         // W2[k][n], 64 x 64
+constexpr int ob2 = oW2 + kHid * kHid;
+constexpr int oW3 = ob2 + kHid;         // W3[k][n], 64 x 8 (columns 3..7 zero)
+constexpr int ob3 = oW3 + kHid * kOutPad;
+constexpr int kParams = ob3 + kOutPad;  // 5768
+// bfloat16 copies, n-major (B operand of mma: element (k, n) at [n][k])
+constexpr int oW1t = 0;                 // [64][16]
+constexpr int oW2t = oW1t + kHid * kInPad;   // [64][64]
+constexpr int oW3t = oW2t + kHid * kHid;     // [8][64]
+constexpr int kBf16 = oW3t + kOutPad * kHid;  // 5632
+constexpr size_t kBlockBytes = sizeof(float) * 3 * kParams + sizeof(__nv_bfloat16) * kBf16;
+
+struct MlpBlock {
+    float *w, *m, *v;      // master weights, Adam moments
+    __nv_bfloat16 *wb;     // bfloat16 copies
+};
+
+__host__ __device__ inline MlpBlock mlp_block(void *p) {
+    MlpBlock b;
+    b.w = reinterpret_cast<float *>(p);
+    b.m = b.w + kParams;
+    b.v = b.m + kParams;
+    b.wb = reinterpret_cast<__nv_bfloat16 *>(b.v + kParams);
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// counter-based random numbers: SplitMix64 (Steele, Lea & Flood 2014)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+    float s = 1.f / (1.f + expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Weights and biases staged in shared memory by a block.
+struct MlpSmem {
+    __nv_bfloat16 wb[kBf16];
+    float b1[kHid], b2[kHid], b3[kOutPad];
+};
+
+__device__ void load_mlp_smem(const MlpBlock &P, MlpSmem &S) {
+    for (int i = threadIdx.x; i < kBf16; i += blockDim.x) S.wb[i] = P.wb[i];
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+        S.b1[i] = P.w[ob1 + i];
+        S.b2[i] = P.w[ob2 + i];
+    }
+    if (threadIdx.x < kOutPad) S.b3[threadIdx.x] = P.w[ob3 + threadIdx.x];
+}
+
+__device__ __forceinline__ unsigned ldb(const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned *>(p); }
+
+// Forward pass of one warp over 16 rows. Input fragment a (rows g, g+8 of the
+// warp's 16, columns 2t.. / 2t+8..) in bfloat16; outputs y[4] (rows g, g+8,
+// columns 2t, 2t+1). If z1/z2 are given, the pre-activations are kept
+// ([8][4] fragments: tile j holds columns 8j + 2t, +1).
+__device__ __forceinline__ void mlp_warp_forward(const MlpSmem &S, const unsigned a[4], float y[4],
+                                                 float (*z1)[4], float (*z2)[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float h[8][4];
+    // layer 1: 16 -> 64
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        const __nv_bfloat16 *bn = S.wb + oW1t + (8 * j + g) * kInPad;
+        mma_bf16(c, a, ldb(bn + 2 * t), ldb(bn + 2 * t + 8));
+        const float bb0 = S.b1[8 * j + 2 * t], bb1 = S.b1[8 * j + 2 * t + 1];
+        c[0] += bb0; c[1] += bb1; c[2] += bb0; c[3] += bb1;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (z1) z1[j][q] = c[q];
+            h[j][q] = silu(c[q]);
+        }
+    }
+    unsigned A2[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        A2[k][0] = pack_bf16(h[2 * k][0], h[2 * k][1]);
+        A2[k][1] = pack_bf16(h[2 * k][2], h[2 * k][3]);
+        A2[k][2] = pack_bf16(h[2 * k + 1][0], h[2 * k + 1][1]);
+        A2[k][3] = pack_bf16(h[2 * k + 1][2], h[2 * k + 1][3]);
+    }
+    // layer 2: 64 -> 64
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        const __nv_bfloat16 *bn = S.wb + oW2t + (8 * j + g) * kHid;
+#pragma unroll
+        for (int k = 0; k < 4; k++) mma_bf16(c, A2[k], ldb(bn + 16 * k + 2 * t), ldb(bn + 16 * k + 8 + 2 * t));
+        const float bb0 = S.b2[8 * j + 2 * t], bb1 = S.b2[8 * j + 2 * t + 1];
+        c[0] += bb0; c[1] += bb1; c[2] += bb0; c[3] += bb1;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (z2) z2[j][q] = c[q];
+            h[j][q] = silu(c[q]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        A2[k][0] = pack_bf16(h[2 * k][0], h[2 * k][1]);
+        A2[k][1] = pack_bf16(h[2 * k][2], h[2 * k][3]);
+        A2[k][2] = pack_bf16(h[2 * k + 1][0], h[2 * k + 1][1]);
+        A2[k][3] = pack_bf16(h[2 * k + 1][2], h[2 * k + 1][3]);
+    }
+    // layer 3: 64 -> 8 (3 used)
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const __nv_bfloat16 *bn = S.wb + oW3t + g * kHid;
+#pragma unroll
+    for (int k = 0; k < 4; k++) mma_bf16(c, A2[k], ldb(bn + 16 * k + 2 * t), ldb(bn + 16 * k + 8 + 2 * t));
+    y[0] = c[0] + S.b3[2 * t];
+    y[1] = c[1] + S.b3[2 * t + 1];
+    y[2] = c[2] + S.b3[2 * t];
+    y[3] = c[3] + S.b3[2 * t + 1];
+}
+
+// A fragment of 16 rows of FP32 features x[row][16] (rows >= n are zero).
+__device__ __forceinline__ void load_a(const float *x, int64_t r0, int64_t n, unsigned a[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t ra = r0 + g, rb = r0 + g + 8;
+    float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (ra < n) {
+        v[0] = x[ra * kInPad + 2 * t]; v[1] = x[ra * kInPad + 2 * t + 1];
+        v[4] = x[ra * kInPad + 2 * t + 8]; v[5] = x[ra * kInPad + 2 * t + 9];
+    }
+    if (rb < n) {
+        v[2] = x[rb * kInPad + 2 * t]; v[3] = x[rb * kInPad + 2 * t + 1];
+        v[6] = x[rb * kInPad + 2 * t + 8]; v[7] = x[rb * kInPad + 2 * t + 9];
+    }
+    a[0] = pack_bf16(v[0], v[1]);
+    a[1] = pack_bf16(v[2], v[3]);
+    a[2] = pack_bf16(v[4], v[5]);
+    a[3] = pack_bf16(v[6], v[7]);
+}
+
+// ---------------------------------------------------------------------------
+// init, bfloat16 refresh, forward
+// ---------------------------------------------------------------------------
+// Glorot-uniform weights from SplitMix64(seed, index), zero biases, zero padding.
+__global__ void mlp_init_k(MlpBlock P, unsigned long long seed) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
+        float a = 0.f;
+        bool use = false;
+        if (i < ob1) { int k = (i - oW1) / kHid; use = k < kIn; a = sqrtf(6.f / (kIn + kHid)); }
+        else if (i >= oW2 && i < ob2) { use = true; a = sqrtf(6.f / (2 * kHid)); }
+        else if (i >= oW3 && i < ob3) { int n = (i - oW3) % kOutPad; use = n < kOut; a = sqrtf(6.f / (kHid + kOut)); }
+        float u = (float)((splitmix64(seed ^ (0xA5A5A5A5ull + (unsigned long long)i)) >> 40) * (1.0 / 16777216.0));
+        P.w[i] = use ? a * (2.f * u - 1.f) : 0.f;
+        P.m[i] = 0.f;
+        P.v[i] = 0.f;
+    }
+}
+
+__global__ void mlp_sync_k(MlpBlock P) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kBf16; i += gridDim.x * blockDim.x) {
+        float v;
+        if (i < oW2t) { int n = i / kInPad, k = i % kInPad; v = P.w[oW1 + k * kHid + n]; }
+        else if (i < oW3t) { int j = i - oW2t, n = j / kHid, k = j % kHid; v = P.w[oW2 + k * kHid + n]; }
+        else { int j = i - oW3t, n = j / kHid, k = j % kHid; v = P.w[oW3 + k * kOutPad + n]; }
+        P.wb[i] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void __launch_bounds__(128) mlp_forward_k(MlpBlock P, int64_t n, const float *x, float *y) {
+    __shared__ MlpSmem S;
+    load_mlp_smem(P, S);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    for (int64_t r0 = ((int64_t)blockIdx.x * 4 + wid) * 16; r0 < n; r0 += (int64_t)gridDim.x * 64) {
+        unsigned a[4];
+        load_a(x, r0, n, a);
+        float o[4];
+        mlp_warp_forward(S, a, o, nullptr, nullptr);
+        const int64_t ra = r0 + g, rb = r0 + g + 8;
+        for (int q = 0; q < 2; q++) {
+            int col = 2 * t + q;
+            if (col < kOut) {
+                if (ra < n) y[ra * kOut + col] = o[q];
+                if (rb < n) y[rb * kOut + col] = o[2 + q];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gradients: one block = 64 rows; FP32 backward through the rounded forward
+// ---------------------------------------------------------------------------
+struct GradSmem {
+    MlpSmem W;
+    float x0[64][kInPad];
+    float z1[64][kHid], h1[64][kHid], z2[64][kHid], h2[64][kHid];
+    float dy[64][kOutPad];
+    float red[128];
+};
+
+__global__ void __launch_bounds__(128) mlp_grad_k(MlpBlock P, int64_t n, const float *x, const float *tgt,
+                                                  float *partial, float *loss_partial) {
+    extern __shared__ __align__(16) char smem_raw[];
+    GradSmem &S = *reinterpret_cast<GradSmem *>(smem_raw);
+    load_mlp_smem(P, S.W);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int64_t r0 = (int64_t)blockIdx.x * 64 + wid * 16;
+    const float inv = 2.f / (float)(n * kOut);
+    // forward of this warp's 16 rows, keeping what the backward needs
+    {
+        unsigned a[4];
+        load_a(x, r0, n, a);
+        float z1[8][4], z2[8][4], y[4];
+        mlp_warp_forward(S.W, a, y, z1, z2);
+        const int ra = wid * 16 + g, rb = ra + 8;
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int col = 8 * j + 2 * t + q;
+                S.z1[ra][col] = z1[j][q];
+                S.z1[rb][col] = z1[j][2 + q];
+                S.z2[ra][col] = z2[j][q];
+                S.z2[rb][col] = z2[j][2 + q];
+                S.h1[ra][col] = __bfloat162float(__float2bfloat16_rn(silu(z1[j][q])));
+                S.h1[rb][col] = __bfloat162float(__float2bfloat16_rn(silu(z1[j][2 + q])));
+                S.h2[ra][col] = __bfloat162float(__float2bfloat16_rn(silu(z2[j][q])));
+                S.h2[rb][col] = __bfloat162float(__float2bfloat16_rn(silu(z2[j][2 + q])));
+            }
+        float lsum = 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int col = 2 * t + q;
+            const int64_t gra = r0 + g, grb = r0 + g + 8;
+            float da = 0.f, db = 0.f;
+            if (col < kOut && gra < n) { float e = y[q] - tgt[gra * kOut + col]; da = inv * e; lsum += e * e; }
+            if (col < kOut && grb < n) { float e = y[2 + q] - tgt[grb * kOut + col]; db = inv * e; lsum += e * e; }
+            S.dy[ra][col] = da;
+            S.dy[rb][col] = db;
+        }
+        for (int c = 0; c < kInPad; c++) {
+            // rounded inputs, row by row (two rows per lane group)
+            if (lane < 16) {
+                const int64_t r = r0 + lane;
+                S.x0[wid * 16 + lane][c] = (r < n) ? __bfloat162float(__float2bfloat16_rn(x[r * kInPad + c])) : 0.f;
+            }
+        }
+        S.red[threadIdx.x] = lsum;
+    }
+    __syncthreads();
+    // dZ2 = (dY W3b^T) . silu'(Z2), in place of z2
+    for (int e = threadIdx.x; e < 64 * kHid; e += 128) {
+        const int r = e / kHid, i = e % kHid;
+        float s = 0.f;
+        for (int o = 0; o < kOut; o++) s += S.dy[r][o] * __bfloat162float(S.W.wb[oW3t + o * kHid + i]);
+        S.z2[r][i] = s * silu_grad(S.z2[r][i]);
+    }
+    __syncthreads();
+    // dZ1 = (dZ2 W2b^T) . silu'(Z1), in place of z1
+    for (int e = threadIdx.x; e < 64 * kHid; e += 128) {
+        const int r = e / kHid, i = e % kHid;
+        float s = 0.f;
+        for (int j = 0; j < kHid; j++) s += S.z2[r][j] * __bfloat162float(S.W.wb[oW2t + j * kHid + i]);
+        S.z1[r][i] = s * silu_grad(S.z1[r][i]);
+    }
+    __syncthreads();
+    // this block's share of every gradient entry (sums over its 64 rows)
+    float *out = partial + (int64_t)blockIdx.x * kParams;
+    for (int p = threadIdx.x; p < kParams; p += 128) {
+        float s = 0.f;
+        if (p < ob1) { int k = p / kHid, j = p % kHid; for (int r = 0; r < 64; r++) s += S.x0[r][k] * S.z1[r][j]; }
+        else if (p < oW2) { int j = p - ob1; for (int r = 0; r < 64; r++) s += S.z1[r][j]; }
+        else if (p < ob2) { int k = (p - oW2) / kHid, j = (p - oW2) % kHid; for (int r = 0; r < 64; r++) s += S.h1[r][k] * S.z2[r][j]; }
+        else if (p < oW3) { int j = p - ob2; for (int r = 0; r < 64; r++) s += S.z2[r][j]; }
+        else if (p < ob3) { int k = (p - oW3) / kOutPad, o = (p - oW3) % kOutPad; for (int r = 0; r < 64; r++) s += S.h2[r][k] * S.dy[r][o]; }
+        else { int o = p - ob3; for (int r = 0; r < 64; r++) s += S.dy[r][o]; }
+        out[p] = s;
+    }
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; i < 128; i++) s += S.red[i];
+        loss_partial[blockIdx.x] = s;
+    }
+}
+
+// grad[p] = sum over blocks in block order; loss = mean squared error
+__global__ void mlp_reduce_k(int nblk, const float *partial, const float *loss_partial, float *grad, float *loss,
+                             int64_t n) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < kParams; p += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * kParams + p];
+        grad[p] = s;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && loss) {
+        float s = 0.f;
+        for (int b = 0; b < nblk; b++) s += loss_partial[b];
+        *loss = s / (float)(n * kOut);
+    }
+}
+
+// Adam (Kingma & Ba 2015), step t >= 1, on the FP32 master weights
+__global__ void mlp_adam_k(MlpBlock P, const float *grad, int t, float lr, float b1, float b2, float eps) {
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kParams; i += gridDim.x * blockDim.x) {
+        const float gr = grad[i];
+        const float m = b1 * P.m[i] + (1.f - b1) * gr;
+        const float v = b2 * P.v[i] + (1.f - b2) * gr * gr;
+        P.m[i] = m;
+        P.v[i] = v;
+        P.w[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// features of a (point, cell) pair; residual of the cell's multipole force
+// ---------------------------------------------------------------------------
+struct CellGeo {
+    const float4 *pos;
+    const int4 *cbox;
+    const int4 *clink;
+    const float4 *cmom;
+    const int64_t *moff;
+    int M;
+    const double *mbounds;
+    const int *mroot;
+    int ncell;
+};
+
+__device__ __forceinline__ void member_geo(const CellGeo &T, int m, float lo[3], float &unit) {
+    const double *b = T.mbounds + 5 * m;
+    lo[0] = (float)b[0]; lo[1] = (float)b[1]; lo[2] = (float)b[2];
+    unit = (float)(b[3] / 2097152.0);
+}
+
+// r = x - com with x given relative to the point g (xr = x - g), gc = cell
+// centre - g: com - g = gc + (com - c0). Writes 16 features (11 used) and
+// returns M / |r|^2.
+__device__ float pair_features(const float4 r0, const float4 q0, const float4 q1, float side, float eps,
+                               const float r[3], float f[kInPad]) {
+    const float d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    if (!(r0.x > 0.f) || !(d2 > 0.f)) {  // massless (ghost) cell: no correction
+        for (int k = 0; k < kInPad; k++) f[k] = 0.f;
+        return 0.f;
+    }
+    const float d = sqrtf(d2), id = 1.f / d;
+    f[0] = r[0] * id; f[1] = r[1] * id; f[2] = r[2] * id;
+    f[3] = side * id;
+    f[4] = eps * id;
+    const float qs = 1.f / (r0.x * side * side);
+    f[5] = q0.x * qs; f[6] = q0.y * qs; f[7] = q0.z * qs; f[8] = q0.w * qs; f[9] = q1.x * qs; f[10] = q1.y * qs;
+    for (int k = kIn; k < kInPad; k++) f[k] = 0.f;
+    return r0.x / d2;
+}
+
+// Sample s: star i = SplitMix64 pick; walk of that star alone at theta
+// (box: its grid cell) choosing uniformly among accepted cells (reservoir);
+// features, residual target and the pair (i, cell).
+__global__ void mlp_samples_k(CellGeo T, MacTable mac, int64_t n, float eps, unsigned long long seed, int64_t ns,
+                              float *xo, float *to, int2 *pairs, DevState *st) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long h = splitmix64(seed + 2 * (unsigned long long)s);
+        const int i = (int)(h % (unsigned long long)n);
+        const float4 p = T.pos[i];
+        const int m = member_of(T.moff, T.M, i);
+        const double *mb = T.mbounds + 5 * m;
+        int blo[3], bhi[3];
+        const float pv[3] = {p.x, p.y, p.z};
+        for (int a = 0; a < 3; a++) {
+            double q = floor(__dmul_rn(__dsub_rn((double)pv[a], mb[a]), mb[4]));
+            q = fmin(fmax(q, -8388608.0), 8388608.0);
+            blo[a] = (int)q;
+            bhi[a] = (int)q + 1;
+        }
+        int stack[192];
+        int top = 0, chosen = -1;
+        long long nacc = 0;
+        stack[top++] = T.mroot[m];
+        int guard = T.ncell + 1;
+        while (top > 0) {
+            if (--guard < 0) { latch_err(st, kErrStack); break; }
+            const int c = stack[--top];
+            if (c < 0 || c >= T.ncell) { latch_err(st, kErrCells); break; }
+            const int4 b = T.cbox[c];
+            const int side = 1 << (kMaxLevel - b.w);
+            long long gx = (b.x >= bhi[0]) ? b.x - bhi[0] : ((blo[0] >= b.x + side) ? blo[0] - (b.x + side) : 0);
+            long long gy = (b.y >= bhi[1]) ? b.y - bhi[1] : ((blo[1] >= b.y + side) ? blo[1] - (b.y + side) : 0);
+            long long gz = (b.z >= bhi[2]) ? b.z - bhi[2] : ((blo[2] >= b.z + side) ? blo[2] - (b.z + side) : 0);
+            const unsigned long long d2 = (unsigned long long)(gx * gx + gy * gy + gz * gz);
+            if (d2 >= mac.thr[b.w]) {
+                nacc++;
+                const unsigned long long u = splitmix64(seed + 2 * (unsigned long long)s + 1 + 0x51ED27ull * nacc);
+                if (u % (unsigned long long)nacc == 0) chosen = c;
+                continue;
+            }
+            const int4 lk = T.clink[c];
+            if (lk.x == lk.y) continue;
+            if (top + (lk.y - lk.x) > 192) { latch_err(st, kErrStack); break; }
+            for (int ch = lk.y - 1; ch >= lk.x; ch--) stack[top++] = ch;
+        }
+        float f[kInPad], tr[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < kInPad; k++) f[k] = 0.f;
+        if (chosen >= 0) {
+            float lo[3], unit;
+            member_geo(T, m, lo, unit);
+            const int4 b = T.cbox[chosen];
+            float c0[3];
+            geo_centre(b, lo, unit, c0);
+            const float4 r0 = T.cmom[3 * chosen], q0 = T.cmom[3 * chosen + 1], q1 = T.cmom[3 * chosen + 2];
+            // r = x - com = (x - c0) - (com - c0)
+            const float r[3] = {(p.x - c0[0]) - r0.y, (p.y - c0[1]) - r0.z, (p.z - c0[2]) - r0.w};
+            const float side = unit * (float)(1 << (kMaxLevel - b.w));
+            const float norm = pair_features(r0, q0, q1, side, eps, r, f);
+            // exact softened force of the cell's stars
+            const int4 lk = T.clink[chosen];
+            float ex[3] = {0.f, 0.f, 0.f};
+            for (int j = lk.z; j < lk.w; j++) {
+                const float4 sj = T.pos[j];
+                const float dx = sj.x - p.x, dy = sj.y - p.y, dz = sj.z - p.z;
+                const float q2 = dx * dx + dy * dy + dz * dz + eps * eps;
+                const float ri = rsqrtf(q2);
+                const float w = sj.w * ri * ri * ri;
+                ex[0] += w * dx; ex[1] += w * dy; ex[2] += w * dz;
+            }
+            // its monopole + quadrupole force
+            const float rho2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + eps * eps;
+            const float ri = rsqrtf(rho2), ri2 = ri * ri, ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
+            const float qx = q0.x * r[0] + q0.w * r[1] + q1.x * r[2];
+            const float qy = q0.w * r[0] + q0.y * r[1] + q1.y * r[2];
+            const float qz = q1.x * r[0] + q1.y * r[1] + q0.z * r[2];
+            const float rqr = r[0] * qx + r[1] * qy + r[2] * qz;
+            const float qd[3] = {qx, qy, qz};
+            for (int a = 0; a < 3; a++) {
+                const float quad = -r0.x * r[a] * ri3 + qd[a] * ri5 - 2.5f * rqr * r[a] * ri7;
+                tr[a] = (norm > 0.f) ? (ex[a] - quad) / norm : 0.f;
+            }
+        }
+        for (int k = 0; k < kInPad; k++) xo[s * kInPad + k] = f[k];
+        for (int a = 0; a < 3; a++) to[s * kOut + a] = tr[a];
+        if (pairs) pairs[s] = make_int2(i, chosen);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// correction of recorded (group, cell) pairs, evaluated at the group centre
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) mlp_pairs_k(MlpBlock P, CellGeo T, const int4 *groups, const int2 *pairs,
+                                                   const int *npairs, int cap, float eps, float *gcorr) {
+    __shared__ MlpSmem S;
+    __shared__ float feat[4][16][kInPad];
+    __shared__ float nrm[4][16];
+    __shared__ int gid[4][16];
+    load_mlp_smem(P, S);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int np = min(*npairs, cap);
+    for (int r0 = (blockIdx.x * 4 + wid) * 16; r0 < np; r0 += gridDim.x * 64) {
+        if (lane < 16) {
+            const int r = r0 + lane;
+            float f[kInPad];
+            float norm = 0.f;
+            int gg = -1;
+            if (r < np) {
+                const int2 pr = pairs[r];
+                gg = pr.x;
+                const int4 grp = groups[pr.x];
+                const int m = member_of(T.moff, T.M, grp.x);
+                float lo[3], unit;
+                member_geo(T, m, lo, unit);
+                float gcen[3], c0[3];
+                geo_centre(T.cbox[grp.z], lo, unit, gcen);
+                const int4 b = T.cbox[pr.y];
+                geo_centre(b, lo, unit, c0);
+                const float4 q = T.cmom[3 * pr.y], q0 = T.cmom[3 * pr.y + 1], q1 = T.cmom[3 * pr.y + 2];
+                // r = g - com = -((c0 - g) + (com - c0))
+                const float rr[3] = {-((c0[0] - gcen[0]) + q.y), -((c0[1] - gcen[1]) + q.z),
+                                     -((c0[2] - gcen[2]) + q.w)};
+                const float side = unit * (float)(1 << (kMaxLevel - b.w));
+                norm = pair_features(q, q0, q1, side, eps, rr, f);
+            } else {
+                for (int k = 0; k < kInPad; k++) f[k] = 0.f;
+            }
+            for (int k = 0; k < kInPad; k++) feat[wid][lane][k] = f[k];
+            nrm[wid][lane] = norm;
+            gid[wid][lane] = gg;
+        }
+        __syncwarp();
+        unsigned a[4];
+        a[0] = pack_bf16(feat[wid][g][2 * t], feat[wid][g][2 * t + 1]);
+        a[1] = pack_bf16(feat[wid][g + 8][2 * t], feat[wid][g + 8][2 * t + 1]);
+        a[2] = pack_bf16(feat[wid][g][2 * t + 8], feat[wid][g][2 * t + 9]);
+        a[3] = pack_bf16(feat[wid][g + 8][2 * t + 8], feat[wid][g + 8][2 * t + 9]);
+        float y[4];
+        mlp_warp_forward(S, a, y, nullptr, nullptr);
+        for (int q = 0; q < 2; q++) {
+            const int col = 2 * t + q;
+            if (col < kOut) {
+                if (gid[wid][g] >= 0) atomicAdd(&gcorr[3 * gid[wid][g] + col], y[q] * nrm[wid][g]);
+                if (gid[wid][g + 8] >= 0) atomicAdd(&gcorr[3 * gid[wid][g + 8] + col], y[2 + q] * nrm[wid][g + 8]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// every star of group k gets the group's correction
+__global__ void mlp_apply_k(const int4 *groups, const int *ngroup, const int *perm, const float *gcorr, float *ax,
+                            float *ay, float *az) {
+    const int ng = *ngroup;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
+        const int4 grp = groups[k];
+        const float cx = gcorr[3 * k], cy = gcorr[3 * k + 1], cz = gcorr[3 * k + 2];
+        for (int i = grp.x; i < grp.x + grp.y; i++) {
+            const int o = perm[i];
+            ax[o] += cx; ay[o] += cy; az[o] += cz;
+        }
+    }
+}
+
+static CellGeo cell_geo(rv_ctx *c, int ncell_host) {
+    CellGeo T;
+    T.pos = c->w.pos;
+    T.cbox = c->w.cbox;
+    T.clink = reinterpret_cast<const int4 *>(c->w.clink);
+    T.cmom = c->w.cmom;
+    T.moff = c->w.moff;
+    T.M = c->n_members;
+    T.mbounds = c->w.mbounds;
+    T.mroot = c->w.mroot;
+    T.ncell = ncell_host;
+    return T;
+}
+
+static rv_status read_ncell(rv_ctx *c, cudaStream_t s, int *ncell, int *ngroup) {
+    int v[2];
+    cudaError_t e = cudaMemcpyAsync(v, &c->w.st->ncell, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(c, e, "tree size");
+    *ncell = (int)std::min<int64_t>(v[0], c->cell_cap);
+    *ngroup = v[1];
+    return RV_OK;
+}
+
+}  // namespace rv
+
+using namespace rv;
+
+extern "C" {
+
+size_t rv_mlp_param_bytes(void) { return kBlockBytes; }
+
+size_t rv_mlp_scratch_bytes(int64_t batch) {
+    if (batch < 0) return 0;
+    const int64_t nblk = (batch + 63) / 64;
+    return sizeof(float) * (size_t)((nblk + 1) * kParams + nblk + 1);
+}
+
+rv_status rv_mlp_init(void *params, uint64_t seed, void *stream) {
+    if (!params) return RV_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpBlock P = mlp_block(params);
+    mlp_init_k<<<ceil_div(kParams, 256), 256, 0, s>>>(P, seed);
+    mlp_sync_k<<<ceil_div(kBf16, 256), 256, 0, s>>>(P);
+    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y, void *stream) {
+    if (!params || n < 0 || (n > 0 && (!x || !y))) return RV_E_INVAL;
+    if (n == 0) return RV_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpBlock P = mlp_block(const_cast<void *>(params));
+    const int grid = (int)std::min<int64_t>((n + 63) / 64, 65535);
+    mlp_forward_k<<<grid, 128, 0, s>>>(P, n, x, y);
+    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_mlp_gradient(const void *params, int64_t n, const float *x, const float *t, float *grad, float *loss,
+                          void *scratch, size_t scratch_bytes, void *stream) {
+    if (!params || n <= 0 || !x || !t || !grad || !scratch) return RV_E_INVAL;
+    if (scratch_bytes < rv_mlp_scratch_bytes(n)) return RV_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpBlock P = mlp_block(const_cast<void *>(params));
+    const int nblk = (int)((n + 63) / 64);
+    float *partial = reinterpret_cast<float *>(scratch);
+    float *lpart = partial + (int64_t)nblk * kParams;
+    const size_t smem = sizeof(GradSmem);
+    cudaError_t e = cudaFuncSetAttribute(mlp_grad_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return RV_E_CUDA;
+    mlp_grad_k<<<nblk, 128, smem, s>>>(P, n, x, t, partial, lpart);
+    mlp_reduce_k<<<ceil_div(kParams, 256), 256, 0, s>>>(nblk, partial, lpart, grad, loss, n);
+    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_mlp_adam(void *params, const float *grad, int32_t step, float lr, float beta1, float beta2,
+                      float adam_eps, void *stream) {
+    if (!params || !grad || step < 1) return RV_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpBlock P = mlp_block(params);
+    mlp_adam_k<<<ceil_div(kParams, 256), 256, 0, s>>>(P, grad, step, lr, beta1, beta2, adam_eps);
+    mlp_sync_k<<<ceil_div(kBf16, 256), 256, 0, s>>>(P);
+    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_mlp_samples(rv_ctx *c, float theta, float eps_star, int64_t n_samples, uint64_t seed, float *x,
+                         float *t, int32_t *pairs, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!c->ws) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (!c->built || c->n == 0) return set_err(c, RV_E_NOTBUILT, "samples need a built, non-empty tree");
+    if (n_samples < 0 || (n_samples > 0 && (!x || !t)) || !(theta > 0.f && theta < 2.f))
+        return set_err(c, RV_E_INVAL, "bad sample arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    int ncell, ngroup;
+    rv_status r = read_ncell(c, s, &ncell, &ngroup);
+    if (r != RV_OK || n_samples == 0) return r;
+    const int grid = (int)std::min<int64_t>((n_samples + 127) / 128, (int64_t)c->num_sms * 16);
+    mlp_samples_k<<<grid, 128, 0, s>>>(cell_geo(c, ncell), mac_table(theta), c->n, eps_star, seed, n_samples, x, t,
+                                        reinterpret_cast<int2 *>(pairs), c->w.st);
+    count_launch(c);
+    return cuda_check(c, cudaGetLastError(), "mlp samples");
+}
+
+rv_status rv_tree_forces_mlp(rv_ctx *c, const void *params, float theta, float theta_rec, float eps_star, float *ax,
+                             float *ay, float *az, float *pot, int32_t *pairs, int32_t pair_cap, int32_t *npairs,
+                             float *gcorr, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!c->ws) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces_mlp before a build");
+    if (!params || !pairs || !npairs || !gcorr || pair_cap < 0 || !(theta_rec > 0.f && theta_rec <= theta) ||
+        !(theta < 2.f) || !(eps_star > 0.f) || (c->n > 0 && (!ax || !ay || !az || !pot)))
+        return set_err(c, RV_E_INVAL, "bad arguments");
+    if (c->cfg.quadrupole == 0) return set_err(c, RV_E_INVAL, "the correction is learned on quadrupole cells");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(npairs, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gcorr, 0, sizeof(float) * 3 * std::max<int64_t>(c->n, 1), s);
+    if (e != cudaSuccess) return cuda_check(c, e, "mlp reset");
+    PairRecord rec{theta_rec, reinterpret_cast<int2 *>(pairs), npairs, pair_cap};
+    rv_status r = tree_walk(c, theta, eps_star, 0, nullptr, nullptr, nullptr, false, ax, ay, az, pot, nullptr, s, &rec);
+    if (r != RV_OK || c->n == 0) return r;
+    int ncell, ngroup;
+    if ((r = read_ncell(c, s, &ncell, &ngroup)) != RV_OK) return r;
+    MlpBlock P = mlp_block(const_cast<void *>(params));
+    const int grid = std::max(1, std::min(ceil_div(pair_cap, 64), c->num_sms * 8));
+    mlp_pairs_k<<<grid, 128, 0, s>>>(P, cell_geo(c, ncell), c->w.groups, reinterpret_cast<const int2 *>(pairs),
+                                     npairs, pair_cap, eps_star, gcorr);
+    count_launch(c);
+    mlp_apply_k<<<std::max(1, ceil_div(ngroup, 256)), 256, 0, s>>>(c->w.groups, &c->w.st->ngroup, c->w.perm, gcorr, ax,
+                                                                 ay, az);
+    count_launch(c);
+    return cuda_check(c, cudaGetLastError(), "mlp forces");
+}
+
+}  // extern "C"

@@ -31,7 +31,7 @@ constexpr int kMaxChain = 250;
 constexpr int kMaxPert = 5000;
 
 // Error codes latched by kernels (first one wins).
-enum DevErr : int { kErrNone = 0, kErrStack = 1, kErrCells = 2, kErrPert = 3 };
+enum DevErr : int { kErrNone = 0, kErrStack = 1, kErrCells = 2, kErrPert = 3, kErrPairs = 4 };
 
 // Device-resident scalars (one small block in the workspace).
 struct DevState {
@@ -130,12 +130,26 @@ rv_status radix_sort(rv_ctx *c, int64_t n, int passes, uint64_t **keys, int **id
                      cudaStream_t s, bool member_pass = false);
 rv_status exclusive_scan(rv_ctx *c, int *data, int64_t nmax, const int *d_len, int *d_total, cudaStream_t s);
 
+// Opening test on integer grid distances: accept iff d^2 >= thr[level].
+struct MacTable {
+    unsigned long long thr[kLevels];
+};
+MacTable mac_table(float theta);
+
 // walk.cu
+// Record of (group, cell) pairs accepted at theta but opened at theta_rec.
+struct PairRecord {
+    float theta_rec;
+    int2 *pairs;
+    int *npairs;
+    int cap;
+};
+
 // extra particles: xmem[k] = member of extra k (device), or nullptr when
 // extra k belongs to member k (one chain per member) -- see walk.cu.
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
-                    float *xout, cudaStream_t s);
+                    float *xout, cudaStream_t s, const PairRecord *rec = nullptr);
 
 // chain.cu
 rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,

@@ -32,10 +32,6 @@
 
 namespace rv {
 
-struct MacTable {
-    unsigned long long thr[kLevels];  // accept iff d^2 >= thr[level]
-};
-
 struct WalkArgs {
     const float4 *pos;   // sorted (x, y, z, m)
     const int4 *cbox;
@@ -61,6 +57,12 @@ struct WalkArgs {
     const float *xeps;
     float *ax, *ay, *az, *pot;
     float *xout;
+    // optional record of accepted (group, cell) pairs that a walk at the
+    // smaller angle theta_rec would have opened (the learned correction's input)
+    MacTable rec;
+    int2 *pairs;
+    int *npairs;
+    int pair_cap;
 };
 
 // Per-warp shared memory: stack | lane_cell[32] | m2p staging (tile+32) x 3 float4 | p2p staging (tile+32) float4
@@ -163,9 +165,9 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 // mass are (cell centre - g) + (centre of mass - cell centre). Differences of
 // nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
 // any distance from the origin.
-template <bool SOFT, bool QUAD>
+template <bool SOFT, bool QUAD, bool REC>
 __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
-                                           char *wsm, const int blo[3],
+                                           const unsigned long long *thr_rec, int gid, char *wsm, const int blo[3],
                                            const int bhi[3], const float g[3], float xi, float yi, float zi, int j0,
                                            int k, float eps2, Acc &acc, unsigned long long &np2p,
                                            unsigned long long &nm2p) {
@@ -210,7 +212,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         __syncwarp();
         if (__any_sync(0xffffffffu, c >= ncell)) { ok = false; break; }
 
-        bool accept = false, leaf = false, open = false;
+        bool accept = false, leaf = false, open = false, band = false;
         int4 lk = make_int4(0, 0, 0, 0);
         int4 b = make_int4(0, 0, 0, 0);
         if (c >= 0) {
@@ -221,6 +223,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
             long long gz = gap1(blo[2], bhi[2], b.z, b.z + side);
             unsigned long long d2 = (unsigned long long)(gx * gx + gy * gy + gz * gz);
             accept = d2 >= thr[b.w];
+            if (REC) band = accept && d2 < thr_rec[b.w];
             if (!accept) {
                 lk = __ldg(&A.clink[c]);
                 leaf = (lk.x == lk.y);
@@ -255,6 +258,19 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         }
         nm += __popc(am);
         nm2p += __popc(am);
+        if (REC) {
+            unsigned bm = __ballot_sync(0xffffffffu, band);
+            if (bm) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(A.npairs, __popc(bm));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (band) {
+                    int p = base + __popc(bm & lt);
+                    if (p < A.pair_cap) A.pairs[p] = make_int2(gid, c);
+                    else latch_err(A.st, kErrPairs);
+                }
+            }
+        }
         // opened leaves: stage their stars relative to g
         unsigned lm = __ballot_sync(0xffffffffu, leaf);
         while (lm) {
@@ -350,14 +366,16 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
 // Work items 0 .. n_extra-1 are the extra particles (one-star groups whose box
 // is their own grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited
 // to +-2^23); the tree's groups follow.
-template <bool SOFT, bool QUAD>
+template <bool SOFT, bool QUAD, bool REC>
 __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree_k(WalkArgs A) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // per-level opening thresholds in shared memory: lanes of a warp test cells
     // of different levels, which a constant-bank read would serialise
     __shared__ unsigned long long mac_thr[kLevels];
+    __shared__ unsigned long long rec_thr[REC ? kLevels : 1];
     if (threadIdx.x < kLevels) mac_thr[threadIdx.x] = A.mac.thr[threadIdx.x];
+    if (REC && threadIdx.x < kLevels) rec_thr[threadIdx.x] = A.rec.thr[threadIdx.x];
     __syncthreads();
     char *wsm = smem + wib * warp_smem_bytes(A.tile);
     const int nitem = A.n_extra + A.st->ngroup;
@@ -390,7 +408,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), G.lo, G.unit, g);
             bool ok = true;
             if (G.ncell > 0 && G.root >= 0)
-                ok = walk_group<false, QUAD>(A, G, mac_thr, wsm, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], lane, 32,
+                ok = walk_group<false, QUAD, false>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], lane, 32,
                                              e * e, acc, a2, a3);
             if (!ok) {
                 if (lane == 0) latch_err(A.st, kErrStack);
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         const int t = lane % s, sub = lane / s;
         const int j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k s take no list entries
         float4 p = __ldg(&A.pos[grp.x + t]);
-        bool ok = walk_group<SOFT, QUAD>(A, G, mac_thr, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], j0, k,
+        bool ok = walk_group<SOFT, QUAD, REC>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], j0, k,
                                          A.eps2, acc, a2, a3);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
@@ -453,7 +471,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
 // MAC thresholds: the smallest integer D with fl(theta^2 * D) > s^2 (FP64,
 // theta^2 = theta * theta rounded once), so that "d^2 >= thr" is exactly the
 // FP64 test s^2 < theta^2 d^2 on integer grid distances.
-static MacTable mac_table(float theta) {
+MacTable mac_table(float theta) {
     MacTable t;
     double th2 = (double)theta * (double)theta;
     for (int l = 0; l < kLevels; l++) {
@@ -470,10 +488,10 @@ static MacTable mac_table(float theta) {
     return t;
 }
 
-template <bool SOFT, bool QUAD>
+template <bool SOFT, bool QUAD, bool REC>
 static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
     size_t smem = warp_smem_bytes(A.tile) * kWalkWarps;
-    auto kern = walk_tree_k<SOFT, QUAD>;
+    auto kern = walk_tree_k<SOFT, QUAD, REC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -487,7 +505,7 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
 
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
-                    float *xout, cudaStream_t s) {
+                    float *xout, cudaStream_t s, const PairRecord *rec) {
     Workspace &w = c->w;
     WalkArgs A;
     A.pos = w.pos;
@@ -514,6 +532,10 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.xeps = xeps;
     A.ax = ax; A.ay = ay; A.az = az; A.pot = pot;
     A.xout = xout;
+    A.pairs = rec ? rec->pairs : nullptr;
+    A.npairs = rec ? rec->npairs : nullptr;
+    A.pair_cap = rec ? rec->cap : 0;
+    if (rec) A.rec = mac_table(rec->theta_rec);
     // reset the work counter and statistics (next_group, n_p2p, n_m2p)
     cudaError_t e = cudaMemsetAsync(&w.st->next_group, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&w.st->n_p2p, 0, 2 * sizeof(unsigned long long), s);
@@ -543,8 +565,14 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
         }
     }
     if (ev0) cudaEventRecord(ev0, s);
-    if (eps_star > 0.f) e = quad ? launch_walk<true, true>(c, A, s) : launch_walk<true, false>(c, A, s);
-    else e = quad ? launch_walk<false, true>(c, A, s) : launch_walk<false, false>(c, A, s);
+    if (rec) {
+        if (!(eps_star > 0.f) || !quad) return set_err(c, RV_E_INVAL, "pair record needs softening and quadrupoles");
+        e = launch_walk<true, true, true>(c, A, s);
+    } else if (eps_star > 0.f) {
+        e = quad ? launch_walk<true, true, false>(c, A, s) : launch_walk<true, false, false>(c, A, s);
+    } else {
+        e = quad ? launch_walk<false, true, false>(c, A, s) : launch_walk<false, false, false>(c, A, s);
+    }
     if (ev1) cudaEventRecord(ev1, s);
     if (e != cudaSuccess) return cuda_check(c, e, "walk launch");
     return RV_OK;

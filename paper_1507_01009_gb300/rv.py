@@ -26,7 +26,9 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_build_tree_members", "rv_tree_forces", "rv_tree_forces_members", "rv_perturber_forces",
            "rv_system_forces", "rv_kdk_step", "rv_kdk_step_graph", "rv_energy",
            "rv_select_perturbers", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
-           "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error"]
+           "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
+           "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
+           "rv_mlp_samples", "rv_tree_forces_mlp"]
 
 
 class RvError(RuntimeError):
@@ -102,13 +104,24 @@ def _declare(L):
     L.rv_sync_status.argtypes = [vp, vp]
     L.rv_profile_walk.argtypes = [vp, i32]
     L.rv_walk_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.rv_mlp_param_bytes.argtypes = []
+    L.rv_mlp_param_bytes.restype = C.c_size_t
+    L.rv_mlp_scratch_bytes.argtypes = [i64]
+    L.rv_mlp_scratch_bytes.restype = C.c_size_t
+    L.rv_mlp_init.argtypes = [vp, C.c_uint64, vp]
+    L.rv_mlp_forward.argtypes = [vp, i64, vp, vp, vp]
+    L.rv_mlp_gradient.argtypes = [vp, i64, vp, vp, vp, vp, vp, C.c_size_t, vp]
+    L.rv_mlp_adam.argtypes = [vp, vp, i32, f32, f32, f32, f32, vp]
+    L.rv_mlp_samples.argtypes = [vp, f32, f32, i64, C.c_uint64, vp, vp, vp, vp]
+    L.rv_tree_forces_mlp.argtypes = [vp, vp, f32, f32, f32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
     L.rv_launch_count.argtypes = [vp]
     L.rv_launch_count.restype = C.c_int64
     L.rv_last_error.argtypes = [vp]
     L.rv_last_error.restype = C.c_char_p
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("rv_default_config", "rv_workspace_size", "rv_destroy", "rv_last_error", "rv_launch_count"):
+        if name not in ("rv_default_config", "rv_workspace_size", "rv_destroy", "rv_last_error", "rv_launch_count",
+                        "rv_mlp_param_bytes", "rv_mlp_scratch_bytes"):
             f.restype = C.c_int
 
 
@@ -398,3 +411,107 @@ class System:
         s.member_offsets = None if self.member_offsets is None else self.member_offsets.ctypes.data
         self._c = s
         return s
+
+
+# --------------------------------------------------------------------------
+# learned cell-force correction
+# --------------------------------------------------------------------------
+MLP_PARAMS = 5768
+MLP_LAYOUT = (("W1", (16, 64)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (64, 8)), ("b3", (8,)))
+
+
+class Mlp:
+    """Parameter block of the correction network on the current device."""
+
+    def __init__(self, seed=1, stream=None):
+        import torch
+        self.L = load()
+        self.block = torch.zeros(int(self.L.rv_mlp_param_bytes()), dtype=torch.uint8, device="cuda")
+        self._scratch = None
+        st = self.L.rv_mlp_init(_ptr(self.block), int(seed), _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_init")
+        self.step = 0
+
+    def master(self):
+        """FP32 master parameters as a dict of CUDA tensors (views)."""
+        w = self.block[:4 * MLP_PARAMS].view(torch_float32())
+        out, o = {}, 0
+        for k, shp in MLP_LAYOUT:
+            sz = 1
+            for s in shp:
+                sz *= s
+            out[k] = w[o:o + sz].view(*shp)
+            o += sz
+        return out
+
+    def forward(self, x, stream=None):
+        import torch
+        y = torch.empty((x.shape[0], 3), dtype=torch.float32, device=x.device)
+        st = self.L.rv_mlp_forward(_ptr(self.block), int(x.shape[0]), _ptr(x), _ptr(y), _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_forward")
+        return y
+
+    def gradient(self, x, t, stream=None):
+        import torch
+        n = int(x.shape[0])
+        need = int(self.L.rv_mlp_scratch_bytes(n))
+        if self._scratch is None or self._scratch.numel() < need:
+            self._scratch = torch.empty(need, dtype=torch.uint8, device=x.device)
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        st = self.L.rv_mlp_gradient(_ptr(self.block), n, _ptr(x), _ptr(t), _ptr(grad), _ptr(loss),
+                                    _ptr(self._scratch), self._scratch.numel(), _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_gradient")
+        return grad, loss
+
+    def adam(self, grad, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        self.step += 1
+        st = self.L.rv_mlp_adam(_ptr(self.block), _ptr(grad), self.step, lr, b1, b2, eps, _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_adam")
+
+    def train(self, x, t, steps, batch=4096, lr=1e-3, seed=0, stream=None):
+        """Adam on minibatches drawn in a seeded order; returns the losses."""
+        import torch
+        g = torch.Generator(device="cpu").manual_seed(int(seed))
+        n = int(x.shape[0])
+        losses = []
+        for k in range(steps):
+            idx = torch.randint(0, n, (batch,), generator=g).to(x.device)
+            grad, loss = self.gradient(x[idx].contiguous(), t[idx].contiguous(), stream)
+            self.adam(grad, lr=lr, stream=stream)
+            losses.append(loss)
+        return [float(l.item()) for l in losses]
+
+
+def torch_float32():
+    import torch
+    return torch.float32
+
+
+def mlp_samples(ctx, theta, eps_star, n, seed, stream=None):
+    """Training samples from ctx's last tree: (x [n,16], t [n,3], pairs [n,2])."""
+    import torch
+    x = torch.empty((n, 16), dtype=torch.float32, device="cuda")
+    t = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    p = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+    ctx._check(ctx.L.rv_mlp_samples(ctx.h, float(theta), float(eps_star), int(n), int(seed), _ptr(x), _ptr(t),
+                                    _ptr(p), _stream(stream)))
+    return x, t, p
+
+
+def tree_forces_mlp(ctx, mlp, theta, theta_rec, eps_star, pair_cap=1 << 24, stream=None):
+    """(ax, ay, az, pot, pairs, npairs) with the learned correction."""
+    import torch
+    n = ctx.n
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(4)]
+    pairs = torch.empty((pair_cap, 2), dtype=torch.int32, device="cuda")
+    npairs = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gcorr = torch.empty(3 * max(n, 1), dtype=torch.float32, device="cuda")
+    ctx._check(ctx.L.rv_tree_forces_mlp(ctx.h, _ptr(mlp.block), float(theta), float(theta_rec), float(eps_star),
+                                        *[_ptr(o) for o in out], _ptr(pairs), int(pair_cap), _ptr(npairs),
+                                        _ptr(gcorr), _stream(stream)))
+    return (*out, pairs, npairs)
