@@ -449,6 +449,114 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# learned cell-force correction: tree at theta 0.8 + network, 2^24 stars
+# ---------------------------------------------------------------------------
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_learned(args):
+    """One step = tree build + walk at theta = 0.8 with the (group, cell) pair
+    record + network correction. The network is trained first (untimed) on
+    2^20 samples the code generates at theta = 0.8. Reported beside: the plain
+    tree at 0.8 and at 0.5 (p99 vs FP64 direct on a 2048-star sample)."""
+    import torch
+    import ics
+    import oracle
+    from paper_1507_01009_gb300 import rv
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    n = 1 << 24
+    th, trec = 0.8, 0.5
+    eps = float(np.float32(0.005))
+    w = ics.hernquist(n, 5)
+    p32 = w.pos.astype(np.float32)
+    m32 = w.mass.astype(np.float32)
+    x, y, z = (torch.from_numpy(np.ascontiguousarray(p32[a])).cuda() for a in range(3))
+    m = torch.from_numpy(m32).cuda()
+    ctx = rv.Context(n, theta=th, eps_star=eps, n_leaf=32)
+    ctx.build_tree(x, y, z, m)
+    xs, ts, _ = rv.mlp_samples(ctx, th, eps, 1 << 20, seed=7)
+    net = rv.Mlp(seed=8)
+    losses = net.train(xs, ts, steps=400, batch=8192, lr=2e-3, seed=2)
+    pair_cap = 1 << 28
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ctx.build_tree(x, y, z, m)
+        return rv.tree_forces_mlp(ctx, net, th, trec, eps, pair_cap=pair_cap)
+
+    for _ in range(max(3, args.warmup)):
+        out = step()
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = step()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ctx.sync_status()
+    npairs = int(out[5].item())
+    ms_step = float(np.mean(ms))
+    # the network kernel alone, on the recorded pairs
+    t_mlp = []
+    for k in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        feats = torch.zeros((npairs, 16), dtype=torch.float32, device="cuda")
+        e0.record()
+        net.forward(feats)
+        e1.record()
+        e1.synchronize()
+        t_mlp.append(e0.elapsed_time(e1))
+    flop_pair = 2 * (16 * 64 + 64 * 64 + 64 * 8)
+    mlp_tflops = npairs * flop_pair / (np.median(t_mlp) / 1e3) / 1e12
+    peaks = _measured_peaks()
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    tg = ics.subsample(n, 2048, seed=17)
+    ad, _ = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), eps, targets=tg)
+
+    def p99(a):
+        return oracle.percentile(oracle.rel_err(np.stack([u.cpu().numpy() for u in a[:3]])[:, tg].astype(
+            np.float64), ad), 0.99)
+
+    def plain(theta):
+        ctx.build_tree(x, y, z, m)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        o = ctx.tree_forces(theta=theta, eps_star=eps)
+        e1.record()
+        e1.synchronize()
+        return o, e0.elapsed_time(e1)
+
+    o8, t8 = plain(th)
+    o5, t5 = plain(0.5)
+    line = {"metric": METRIC, "value": n / (ms_step / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": "hernquist_gamma1_n16777216_learned_correction", "n_stars": n, "theta": th,
+                       "theta_rec": trec, "eps_star": eps, "mlp": "11-64-64-3 SiLU, bf16 weights, fp32 accumulate",
+                       "training": "2^20 samples at theta 0.8, 400 Adam steps of 8192",
+                       "step": "build + walk with pair record + network correction"},
+            "p99_rel_err_vs_fp64_direct": p99(out), "train_loss_first_last": [losses[0], losses[-1]],
+            "pairs": npairs,
+            "plain_tree": {"theta_0.8": {"walk_ms": t8, "p99": p99(o8)}, "theta_0.5": {"walk_ms": t5, "p99": p99(o5)}},
+            "roofline": {"bound": "tensor", "kernel": "mlp_forward_k (mma.sync bf16, on the recorded pairs)",
+                         "achieved": mlp_tflops, "peak": bf16, "unit": "TFLOP/s", "frac": mlp_tflops / bf16,
+                         "traffic": None, "peak_note": "bf16_tflops of MEASURED_PEAKS.json (burst)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,11 +564,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="hernquist_bh", choices=["hernquist_bh", "hernquist_binary", "plummer",
-                                                                   "ensemble"])
+                                                                   "ensemble", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_gpu(args)
 
 
