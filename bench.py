@@ -291,17 +291,15 @@ def run_gpu(args):
     n = d["n"]
     use_graph = args.workload == "ensemble"
 
-    tune = {"group": 32, "n_leaf": 16, "tile": 64}
-    tuned = None
-    if args.workload == "ensemble":
-        from paper_1507_01009_gb300 import autotune
-        p32 = d["pos"].astype(np.float32)
-        xs = [torch.from_numpy(np.ascontiguousarray(p32[a])).to(dev) for a in range(3)]
-        ms = torch.from_numpy(d["mass"].astype(np.float32)).to(dev)
-        tuned = autotune.autotune(*xs, ms, offsets=d["offsets"], theta=d["theta"], eps_star=float(np.float32(d["eps"])),
-                                  grid=autotune.candidates(groups=(32,), leaves=(16, 32), tiles=(64, 128)), reps=2)
-        tune = tuned["config"]
-        del xs, ms
+    # walk parameters (not part of the workload): the autotuner's pick over a small grid, untimed
+    from paper_1507_01009_gb300 import autotune
+    p32 = d["pos"].astype(np.float32)
+    xs = [torch.from_numpy(np.ascontiguousarray(p32[a])).to(dev) for a in range(3)]
+    ms = torch.from_numpy(d["mass"].astype(np.float32)).to(dev)
+    tuned = autotune.autotune(*xs, ms, offsets=d["offsets"], theta=d["theta"], eps_star=float(np.float32(d["eps"])),
+                              grid=autotune.candidates(groups=(32,), leaves=(16, 32, 64), tiles=(64,)), reps=2)
+    tune = tuned["config"]
+    del xs, ms
     ctx = rv.Context(n, theta=d["theta"], eps_star=float(np.float32(d["eps"])), **tune)
     S = rv.System(d["pos"], d["vel"], d["mass"], chain_m=d["chain_m"], chain_x=d["chain_x"], chain_v=d["chain_v"],
                   pert_mode=d["pert_mode"], pert_radius=d["pert_radius"], pert_k=d["pert_k"],
@@ -434,8 +432,8 @@ def run_gpu(args):
                     "step": "kdk + perturber select + build + walk + fp64 perturber/chain + energy",
                     "parallelism": f"replicas{ws}" if ws > 1 else "single",
                     "l2": "flushed (256 MiB write) before every timed step"})
-        if tuned is not None:
-            cfg["autotuned"] = {"cached": tuned["cached"], "candidates": len(tuned["table"])}
+        cfg["autotuned"] = {"cached": tuned["cached"], "candidates": len(tuned["table"]),
+                            "walk_ms_by_n_leaf": {str(r["n_leaf"]): round(r["walk_ms"], 3) for r in tuned["table"]}}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
@@ -473,7 +471,7 @@ def run_learned(args):
         return 0
     torch.cuda.set_device(local)
     n = 1 << 24
-    th, trec = 0.8, 0.5
+    th, trec = 0.8, 0.7
     eps = float(np.float32(0.005))
     w = ics.hernquist(n, 5)
     p32 = w.pos.astype(np.float32)
@@ -485,7 +483,7 @@ def run_learned(args):
     xs, ts, _ = rv.mlp_samples(ctx, th, eps, 1 << 20, seed=7)
     net = rv.Mlp(seed=8)
     losses = net.train(xs, ts, steps=400, batch=8192, lr=2e-3, seed=2)
-    pair_cap = 1 << 28
+    pair_cap = 1 << 29
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def step():

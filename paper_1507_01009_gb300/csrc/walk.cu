@@ -29,6 +29,13 @@
 #ifndef RV_WALK_MIN_BLOCKS
 #define RV_WALK_MIN_BLOCKS 6
 #endif
+// (target, list share) slots per lane: 2 would let a group of s stars use
+// floor(64 / s) shares per star instead of floor(32 / s); on GB300 the
+// predicated two-slot loop measured slower (17.0 vs 14.2 ms on 2^20 stars),
+// so one slot is the default.
+#ifndef RV_WALK_SLOTS
+#define RV_WALK_SLOTS 1
+#endif
 
 namespace rv {
 
@@ -94,65 +101,112 @@ struct Acc {
     float cx, cy, cz, cp;      // Neumaier compensation
 };
 
-// This lane's share of a staged list: entries j0, j0 + k, ... below cnt.
+// A lane serves NS (target, list share) slots: slot q evaluates its target
+// against list entries j0[q], j0[q] + k, ... (positions relative to the
+// group's centre; j0 >= 2^20 marks an idle slot).
+template <int NS>
+struct Slots {
+    float x[NS], y[NS], z[NS];
+    int j0[NS];
+    int k;
+};
+
+struct Part {
+    float x, y, z, p;
+};
+
 template <bool SOFT>
-__device__ __forceinline__ void eval_p2p(const float4 *src, int cnt, int j0, int k, float xi, float yi, float zi,
-                                         float eps2, Acc &A) {
-    float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-#pragma unroll 4
-    for (int j = j0; j < cnt; j += k) {
-        float4 s = src[j];
-        float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        float rinv = rsqrtf(r2);
-        if (!SOFT) rinv = (r2 > 0.f) ? rinv : 0.f;
-        float mr = s.w * rinv;
-        float mr3 = mr * (rinv * rinv);
-        tx = fmaf(mr3, dx, tx);
-        ty = fmaf(mr3, dy, ty);
-        tz = fmaf(mr3, dz, tz);
-        tp -= mr;
-    }
-    nadd(A.ax, A.cx, tx); nadd(A.ay, A.cy, ty); nadd(A.az, A.cz, tz); nadd(A.ph, A.cp, tp);
+__device__ __forceinline__ void p2p_pair(const float4 s, float xi, float yi, float zi, float eps2, Part &t) {
+    float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    float rinv = rsqrtf(r2);
+    if (!SOFT) rinv = (r2 > 0.f) ? rinv : 0.f;
+    float mr = s.w * rinv;
+    float mr3 = mr * (rinv * rinv);
+    t.x = fmaf(mr3, dx, t.x);
+    t.y = fmaf(mr3, dy, t.y);
+    t.z = fmaf(mr3, dz, t.z);
+    t.p -= mr;
 }
 
 template <bool QUAD>
-__device__ __forceinline__ void eval_m2p(const float4 *src, int cnt, int j0, int k, float xi, float yi, float zi,
-                                         float eps2, Acc &A) {
-    float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+__device__ __forceinline__ void m2p_pair(const float4 *src, int j, float xi, float yi, float zi, float eps2,
+                                         Part &t) {
+    float4 a = src[3 * j];
+    float rx = xi - a.y, ry = yi - a.z, rz = zi - a.w;
+    float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
+    // r > 0: an accepted cell's box is separated from the group's box
+    float rinv = rsqrtf(r2);
+    float u = rinv * rinv;
+    float rinv3 = rinv * u;
+    if (QUAD) {
+        float4 b = src[3 * j + 1];
+        float4 e = src[3 * j + 2];
+        // Q r with Q = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
+        float qx = fmaf(b.x, rx, fmaf(b.w, ry, e.x * rz));
+        float qy = fmaf(b.w, rx, fmaf(b.y, ry, e.y * rz));
+        float qz = fmaf(e.x, rx, fmaf(e.y, ry, b.z * rz));
+        float rqr = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
+        float w = rqr * (u * u);                  // (r.Q.r) / rho^4
+        float rinv5 = rinv3 * u;
+        float B = -rinv3 * fmaf(2.5f, w, a.x);    // -(M + 5/2 w) / rho^3
+        t.x = fmaf(B, rx, fmaf(rinv5, qx, t.x));
+        t.y = fmaf(B, ry, fmaf(rinv5, qy, t.y));
+        t.z = fmaf(B, rz, fmaf(rinv5, qz, t.z));
+        t.p = fmaf(-rinv, fmaf(0.5f, w, a.x), t.p); // -(M + w/2) / rho
+    } else {
+        float mr3 = a.x * rinv3;
+        t.x = fmaf(-mr3, rx, t.x);
+        t.y = fmaf(-mr3, ry, t.y);
+        t.z = fmaf(-mr3, rz, t.z);
+        t.p = fmaf(-a.x, rinv, t.p);
+    }
+}
+
+template <int NS>
+__device__ __forceinline__ void add_tile(Acc *A, const Part *t) {
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+        nadd(A[q].ax, A[q].cx, t[q].x); nadd(A[q].ay, A[q].cy, t[q].y);
+        nadd(A[q].az, A[q].cz, t[q].z); nadd(A[q].ph, A[q].cp, t[q].p);
+    }
+}
+
+// This lane's shares of a staged star list (cnt entries).
+template <bool SOFT, int NS>
+__device__ __forceinline__ void eval_p2p(const float4 *src, int cnt, const Slots<NS> &S, float eps2, Acc *A) {
+    Part t[NS];
+#pragma unroll
+    for (int q = 0; q < NS; q++) t[q] = Part{0.f, 0.f, 0.f, 0.f};
+    if (NS == 1) {
+#pragma unroll 4
+        for (int j = S.j0[0]; j < cnt; j += S.k) p2p_pair<SOFT>(src[j], S.x[0], S.y[0], S.z[0], eps2, t[0]);
+    } else {
 #pragma unroll 2
-    for (int j = j0; j < cnt; j += k) {
-        float4 a = src[3 * j];
-        float rx = xi - a.y, ry = yi - a.z, rz = zi - a.w;
-        float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
-        // r > 0: an accepted cell's box is separated from the group's box
-        float rinv = rsqrtf(r2);
-        float u = rinv * rinv;
-        float rinv3 = rinv * u;
-        if (QUAD) {
-            float4 b = src[3 * j + 1];
-            float4 e = src[3 * j + 2];
-            // Q r with Q = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
-            float qx = fmaf(b.x, rx, fmaf(b.w, ry, e.x * rz));
-            float qy = fmaf(b.w, rx, fmaf(b.y, ry, e.y * rz));
-            float qz = fmaf(e.x, rx, fmaf(e.y, ry, b.z * rz));
-            float rqr = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
-            float w = rqr * (u * u);                  // (r.Q.r) / rho^4
-            float rinv5 = rinv3 * u;
-            float B = -rinv3 * fmaf(2.5f, w, a.x);    // -(M + 5/2 w) / rho^3
-            tx = fmaf(B, rx, fmaf(rinv5, qx, tx));
-            ty = fmaf(B, ry, fmaf(rinv5, qy, ty));
-            tz = fmaf(B, rz, fmaf(rinv5, qz, tz));
-            tp = fmaf(-rinv, fmaf(0.5f, w, a.x), tp); // -(M + w/2) / rho
-        } else {
-            float mr3 = a.x * rinv3;
-            tx = fmaf(-mr3, rx, tx);
-            ty = fmaf(-mr3, ry, ty);
-            tz = fmaf(-mr3, rz, tz);
-            tp = fmaf(-a.x, rinv, tp);
+        for (int ja = S.j0[0], jb = S.j0[NS - 1]; ja < cnt || jb < cnt; ja += S.k, jb += S.k) {
+            if (ja < cnt) p2p_pair<SOFT>(src[ja], S.x[0], S.y[0], S.z[0], eps2, t[0]);
+            if (jb < cnt) p2p_pair<SOFT>(src[jb], S.x[NS - 1], S.y[NS - 1], S.z[NS - 1], eps2, t[NS - 1]);
         }
     }
-    nadd(A.ax, A.cx, tx); nadd(A.ay, A.cy, ty); nadd(A.az, A.cz, tz); nadd(A.ph, A.cp, tp);
+    add_tile<NS>(A, t);
+}
+
+// This lane's shares of a staged cell list (cnt multipole records).
+template <bool QUAD, int NS>
+__device__ __forceinline__ void eval_m2p(const float4 *src, int cnt, const Slots<NS> &S, float eps2, Acc *A) {
+    Part t[NS];
+#pragma unroll
+    for (int q = 0; q < NS; q++) t[q] = Part{0.f, 0.f, 0.f, 0.f};
+    if (NS == 1) {
+#pragma unroll 2
+        for (int j = S.j0[0]; j < cnt; j += S.k) m2p_pair<QUAD>(src, j, S.x[0], S.y[0], S.z[0], eps2, t[0]);
+    } else {
+        for (int ja = S.j0[0], jb = S.j0[NS - 1]; ja < cnt || jb < cnt; ja += S.k, jb += S.k) {
+            if (ja < cnt) m2p_pair<QUAD>(src, ja, S.x[0], S.y[0], S.z[0], eps2, t[0]);
+            if (jb < cnt) m2p_pair<QUAD>(src, jb, S.x[NS - 1], S.y[NS - 1], S.z[NS - 1], eps2, t[NS - 1]);
+        }
+    }
+    add_tile<NS>(A, t);
 }
 
 __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
@@ -165,12 +219,11 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 // mass are (cell centre - g) + (centre of mass - cell centre). Differences of
 // nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
 // any distance from the origin.
-template <bool SOFT, bool QUAD, bool REC>
+template <bool SOFT, bool QUAD, bool REC, int NS>
 __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
                                            const unsigned long long *thr_rec, int gid, char *wsm, const int blo[3],
-                                           const int bhi[3], const float g[3], float xi, float yi, float zi, int j0,
-                                           int k, float eps2, Acc &acc, unsigned long long &np2p,
-                                           unsigned long long &nm2p) {
+                                           const int bhi[3], const float g[3], const Slots<NS> &sl, float eps2,
+                                           Acc *acc, unsigned long long &np2p, unsigned long long &nm2p) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
     int *stack = reinterpret_cast<int *>(wsm);
@@ -288,7 +341,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                 np2p += cc;
                 if (np >= T) {
                     __syncwarp();
-                    eval_p2p<SOFT>(p2p, T, j0, k, xi, yi, zi, eps2, acc);
+                    eval_p2p<SOFT, NS>(p2p, T, sl, eps2, acc);
                     __syncwarp();
                     if (lane < np - T) p2p[lane] = p2p[T + lane];
                     np -= T;
@@ -298,7 +351,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         }
         if (nm >= T) {
             __syncwarp();
-            eval_m2p<QUAD>(m2p, T, j0, k, xi, yi, zi, eps2, acc);
+            eval_m2p<QUAD, NS>(m2p, T, sl, eps2, acc);
             __syncwarp();
             if (lane < nm - T) {
                 m2p[3 * lane] = m2p[3 * (T + lane)];
@@ -311,31 +364,38 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
     }
     __syncwarp();
     if (ok) {
-        if (np > 0) eval_p2p<SOFT>(p2p, np, j0, k, xi, yi, zi, eps2, acc);
-        if (nm > 0) eval_m2p<QUAD>(m2p, nm, j0, k, xi, yi, zi, eps2, acc);
+        if (np > 0) eval_p2p<SOFT, NS>(p2p, np, sl, eps2, acc);
+        if (nm > 0) eval_m2p<QUAD, NS>(m2p, nm, sl, eps2, acc);
     }
     __syncwarp();
     if (lane == 0) atomicMax(&A.st->stack_hwm, hwm);
     return ok;
 }
 
-// Adds the partial totals of the k lanes serving a star (lanes t, t+s, ...)
-// into lane t, in lane order.
-__device__ __forceinline__ void combine_lanes(Acc &a, int s, int k) {
+// Virtual lane v = lane + 32 q holds a lane's slot q. Star t is served by the
+// virtual lanes t, t + s, ..., t + (k - 1) s; their partial totals are added
+// into lane t in that order through the warp's (now free) staging memory.
+template <int NS>
+__device__ __forceinline__ Acc combine_slots(const Acc *acc, int s, int k, float *scr) {
     const int lane = threadIdx.x & 31;
-    float sx = a.ax, sy = a.ay, sz = a.az, sp = a.ph;
-    float cx = a.cx, cy = a.cy, cz = a.cz, cp = a.cp;
-    for (int i = 1; i < k; i++) {
-        int src = min(lane + i * s, 31);
-        float ox = __shfl_sync(0xffffffffu, a.ax, src), oy = __shfl_sync(0xffffffffu, a.ay, src);
-        float oz = __shfl_sync(0xffffffffu, a.az, src), op = __shfl_sync(0xffffffffu, a.ph, src);
-        float qx = __shfl_sync(0xffffffffu, a.cx, src), qy = __shfl_sync(0xffffffffu, a.cy, src);
-        float qz = __shfl_sync(0xffffffffu, a.cz, src), qp = __shfl_sync(0xffffffffu, a.cp, src);
-        nadd(sx, cx, ox); nadd(sy, cy, oy); nadd(sz, cz, oz); nadd(sp, cp, op);
-        cx += qx; cy += qy; cz += qz; cp += qp;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+        float *d = scr + 8 * (lane + 32 * q);
+        d[0] = acc[q].ax; d[1] = acc[q].ay; d[2] = acc[q].az; d[3] = acc[q].ph;
+        d[4] = acc[q].cx; d[5] = acc[q].cy; d[6] = acc[q].cz; d[7] = acc[q].cp;
     }
-    a.ax = sx; a.ay = sy; a.az = sz; a.ph = sp;
-    a.cx = cx; a.cy = cy; a.cz = cz; a.cp = cp;
+    __syncwarp();
+    Acc out = {};
+    if (lane < s)
+        for (int i = 0; i < k; i++) {
+            const float *d = scr + 8 * (lane + i * s);
+            nadd(out.ax, out.cx, d[0]); nadd(out.ay, out.cy, d[1]);
+            nadd(out.az, out.cz, d[2]); nadd(out.ph, out.cp, d[3]);
+            out.cx += d[4]; out.cy += d[5]; out.cz += d[6]; out.cp += d[7];
+        }
+    __syncwarp();
+    return out;
 }
 
 // Direct terms of the extra particles of `member` on one target (pair
@@ -368,6 +428,7 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
 // to +-2^23); the tree's groups follow.
 template <bool SOFT, bool QUAD, bool REC>
 __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree_k(WalkArgs A) {
+    constexpr int NS = RV_WALK_SLOTS;
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // per-level opening thresholds in shared memory: lanes of a warp test cells
@@ -385,10 +446,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         if (lane == 0) gi = atomicAdd(&A.st->next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= nitem) break;
-        Acc acc = {};
+        Acc acc[NS];
+#pragma unroll
+        for (int q = 0; q < NS; q++) acc[q] = Acc{};
         unsigned long long a2 = 0, a3 = 0;
+        float *scr = reinterpret_cast<float *>(wsm + kStackCap * 4 + 32 * 4);  // m2p staging, free after a walk
         if (gi < A.n_extra) {
-            // ---- a particle outside the tree: 32 lanes share its interaction list
+            // ---- a particle outside the tree: all 32 NS virtual lanes share its interaction list
             const int kx = gi;
             const int mk = A.extra_per_member ? kx : (A.xmem ? A.xmem[kx] : 0);
             const TreeGeo G = tree_geo(A, mk);
@@ -406,21 +470,28 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             }
             float g[3];
             geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), G.lo, G.unit, g);
+            Slots<NS> sl;
+            sl.k = 32 * NS;
+#pragma unroll
+            for (int q = 0; q < NS; q++) {
+                sl.x[q] = xi - g[0]; sl.y[q] = yi - g[1]; sl.z[q] = zi - g[2];
+                sl.j0[q] = lane + 32 * q;
+            }
             bool ok = true;
             if (G.ncell > 0 && G.root >= 0)
-                ok = walk_group<false, QUAD, false>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, xi - g[0], yi - g[1], zi - g[2], lane, 32,
-                                             e * e, acc, a2, a3);
+                ok = walk_group<false, QUAD, false, NS>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, sl, e * e, acc,
+                                                        a2, a3);
             if (!ok) {
                 if (lane == 0) latch_err(A.st, kErrStack);
                 continue;
             }
-            combine_lanes(acc, 1, 32);
+            Acc tot = combine_slots<NS>(acc, 1, 32 * NS, scr);
             if (lane == 0) {
-                extra_terms(A, xi, yi, zi, ek, kx, mk, acc);
-                A.xout[4 * kx] = acc.ax + acc.cx;
-                A.xout[4 * kx + 1] = acc.ay + acc.cy;
-                A.xout[4 * kx + 2] = acc.az + acc.cz;
-                A.xout[4 * kx + 3] = acc.ph + acc.cp;
+                extra_terms(A, xi, yi, zi, ek, kx, mk, tot);
+                A.xout[4 * kx] = tot.ax + tot.cx;
+                A.xout[4 * kx + 1] = tot.ay + tot.cy;
+                A.xout[4 * kx + 2] = tot.az + tot.cz;
+                A.xout[4 * kx + 3] = tot.ph + tot.cp;
             }
             continue;
         }
@@ -438,28 +509,35 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         int blo[3] = {b.x, b.y, b.z}, bhi[3] = {b.x + side, b.y + side, b.z + side};
         float g[3];
         geo_centre(b, G.lo, G.unit, g);
-        const int s = grp.y, k = 32 / s;      // k lanes per star
-        const int t = lane % s, sub = lane / s;
-        const int j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k s take no list entries
-        float4 p = __ldg(&A.pos[grp.x + t]);
-        bool ok = walk_group<SOFT, QUAD, REC>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, p.x - g[0], p.y - g[1], p.z - g[2], j0, k,
-                                         A.eps2, acc, a2, a3);
+        const int s = grp.y, k = (32 * NS) / s;  // k virtual lanes per star
+        Slots<NS> sl;
+        sl.k = k;
+#pragma unroll
+        for (int q = 0; q < NS; q++) {
+            const int v = lane + 32 * q, t = v % s, sub = v / s;
+            const float4 pq = __ldg(&A.pos[grp.x + t]);
+            sl.x[q] = pq.x - g[0]; sl.y[q] = pq.y - g[1]; sl.z[q] = pq.z - g[2];
+            sl.j0[q] = (sub < k) ? sub : (1 << 20);  // virtual lanes beyond k s take no list entries
+        }
+        bool ok = walk_group<SOFT, QUAD, REC, NS>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, sl,
+                                                  A.eps2, acc, a2, a3);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
         }
         np2p += a2 * (unsigned long long)s;
         nm2p += a3 * (unsigned long long)s;
-        combine_lanes(acc, s, k);
+        Acc tot = combine_slots<NS>(acc, s, k, scr);
         if (lane < s) {
+            const float4 p = __ldg(&A.pos[grp.x + lane]);
             // the star's own pair was evaluated at r = 0: remove its -m/eps
-            if (SOFT) acc.ph += p.w * rsqrtf(A.eps2);
-            if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, mg, acc);
+            if (SOFT) tot.ph += p.w * rsqrtf(A.eps2);
+            if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, mg, tot);
             int o = A.perm[grp.x + lane];
-            A.ax[o] = acc.ax + acc.cx;
-            A.ay[o] = acc.ay + acc.cy;
-            A.az[o] = acc.az + acc.cz;
-            A.pot[o] = acc.ph + acc.cp;
+            A.ax[o] = tot.ax + tot.cx;
+            A.ay[o] = tot.ay + tot.cy;
+            A.az[o] = tot.az + tot.cz;
+            A.pot[o] = tot.ph + tot.cp;
         }
     }
     if (lane == 0) {
