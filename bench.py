@@ -247,6 +247,22 @@ def _walk_traffic():
     return float(t.group(1)) * 1e6
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """Largest timed-region duration over all ranks (the job's time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, stars_per_rank: int, steps: int, total_ms: float) -> float:
+    """Whole-job particles/s: every rank advances its own realisation (replicas)."""
+    return world * stars_per_rank * steps / (total_ms / 1e3)
+
+
 def p99_vs_direct(d, S, sample=2048, seed=77):
     """p99 relative acceleration error of the current GPU forces against the
     FP64 direct sum over each sampled star's own member (stars softened,
@@ -348,13 +364,9 @@ def run_gpu(args):
     ctx.profile_walk(False)
     sampler.stop()
     ctx.sync_status(stream=stream)
-    total_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev])), dev)
     ms_per_step = total_ms / args.steps
-    value = ws * n * args.steps / (total_ms / 1e3)
+    value = job_throughput(ws, n, args.steps, total_ms)
     p99 = p99_vs_direct(d, S) if rank == 0 else None
 
     # ---- dominant kernel: the walk. Its launches inside the timed steps were timed

@@ -58,3 +58,20 @@ def test_create_rejects_bad_arguments(lib):
     assert lib.rv_create(C.byref(h), -1, C.byref(cfg)) == rv.RV_E_INVAL
     assert lib.rv_build_tree(None, 0, None, None, None, None, None) == rv.RV_E_INVAL
     assert lib.rv_last_error(None) == b"null context"
+
+
+@pytest.mark.gpu
+def test_workspace_too_small_rejected(lib):
+    """rv_set_workspace checks size and alignment before touching the device."""
+    from paper_1507_01009_gb300 import rv
+    cfg = rv.default_config()
+    h = C.c_void_p()
+    st = lib.rv_create(C.byref(h), 1000, C.byref(cfg))
+    if st == rv.RV_E_CUDA:
+        pytest.skip("no CUDA device to create a context on")
+    assert st == rv.RV_OK
+    need = rv.workspace_size(1000, cfg)
+    assert lib.rv_set_workspace(h, C.c_void_p(1 << 20), need - 256) == rv.RV_E_WORKSPACE
+    assert lib.rv_set_workspace(h, C.c_void_p((1 << 20) + 8), need) == rv.RV_E_WORKSPACE
+    assert b"need" in lib.rv_last_error(h)
+    lib.rv_destroy(h)

@@ -398,3 +398,31 @@ def test_full_size_hernquist_bh_sampled(rvmod):
     ad, _ = oracle.direct(allp, allm, epsv, targets=tg)
     _, p99, _ = err_stats(a[:, tg], ad)
     assert p99 <= P99_DIRECT
+
+
+def test_radius_overflow_reported(rvmod):
+    """More stars inside the radius than the output holds: the first `cap`
+    ascending indices are written and rv_sync_status reports RV_E_WORKSPACE."""
+    p32, m32 = _inputs("hernquist", 20000)
+    ctx = _ctx(rvmod, 20000)
+    x, y, z = (to_dev(p32[a]) for a in range(3))
+    idx, cnt = ctx.select_perturbers(x, y, z, (0.0, 0.0, 0.0), 1, radius=1.0, cap=100)
+    with pytest.raises(rvmod.RvError) as ei:
+        ctx.sync_status()
+    assert ei.value.status == rvmod.RV_E_WORKSPACE
+    ref = oracle.radius(p32, np.zeros(3, np.float32), np.float32(1.0))
+    assert int(cnt.item()) == 100
+    np.testing.assert_array_equal(idx[:100].cpu().numpy(), ref[:100])
+    ctx.sync_status()                      # the latched error was cleared
+
+
+def test_pair_record_overflow_reported(rvmod):
+    p32, m32 = _inputs("hernquist", 20000)
+    eps = float(np.float32(0.005))
+    ctx = _ctx(rvmod, 20000, theta=0.9, eps_star=eps)
+    gpu_tree(ctx, p32, m32)
+    mlp = rvmod.Mlp(seed=1)
+    rvmod.tree_forces_mlp(ctx, mlp, 0.9, 0.5, eps, pair_cap=16)
+    with pytest.raises(rvmod.RvError) as ei:
+        ctx.sync_status()
+    assert ei.value.status == rvmod.RV_E_WORKSPACE
