@@ -6,12 +6,20 @@
 // leaves stage their stars, opened internal cells push their child range on
 // a per-warp stack. Whenever a staged list holds a full tile, the warp
 // evaluates it: each star of the group is served by k = floor(32 / s) lanes
-// (s = stars in the group), lane t + i s taking list entries i, i + k, ...
+// (s = stars in the group), lane t + i s taking list pairs i, i + k, ...
 // with broadcast shared-memory reads; tile sums are added to running totals
 // with Neumaier compensation, and the k partial totals of a star are
 // combined in lane order at the end. Particles outside the tree (a chain's
 // centre of mass) are walked by the same kernel as one-star groups before the
 // tree's own groups.
+//
+// Staged lists hold list entries in pairs, each field of the two entries
+// side by side, so that one lane evaluates two interactions with the packed
+// two-wide FP32 instructions (add/mul/fma .f32x2): the walk is bound by
+// instruction issue, and a packed instruction does two lanes' worth of FP32
+// work in one issue slot. Each interaction is still computed element by
+// element in FP32 round-to-nearest; only the order of the running sums
+// differs from one entry per instruction.
 //
 // Interactions (G = 1, Sect. 3 Plummer softening; multipoles about the cell's
 // centre of mass, Sect. 1):
@@ -25,16 +33,18 @@
 
 #include "rv_internal.cuh"
 
-// Resident blocks per SM the walk kernel is compiled for (register budget).
-#ifndef RV_WALK_MIN_BLOCKS
-#define RV_WALK_MIN_BLOCKS 6
+// Unrolling of the evaluation loops (list pairs in flight per lane) and the
+// resident blocks per SM the walk kernel is compiled for (register budget:
+// 5 blocks of 128 threads leave 96 registers a thread, enough for two cell
+// pairs in flight without spills).
+#ifndef RV_P2P_UNROLL
+#define RV_P2P_UNROLL 2
 #endif
-// (target, list share) slots per lane: 2 would let a group of s stars use
-// floor(64 / s) shares per star instead of floor(32 / s); on GB300 the
-// predicated two-slot loop measured slower (17.0 vs 14.2 ms on 2^20 stars),
-// so one slot is the default.
-#ifndef RV_WALK_SLOTS
-#define RV_WALK_SLOTS 1
+#ifndef RV_M2P_UNROLL
+#define RV_M2P_UNROLL 2
+#endif
+#ifndef RV_WALK_MIN_BLOCKS
+#define RV_WALK_MIN_BLOCKS 5
 #endif
 
 namespace rv {
@@ -72,9 +82,15 @@ struct WalkArgs {
     int pair_cap;
 };
 
-// Per-warp shared memory: stack | lane_cell[32] | m2p staging (tile+32) x 3 float4 | p2p staging (tile+32) float4
+// Per-warp shared memory: stack | lane_cell[32] | cell staging | star staging.
+// Cell staging: (tile + 32) / 2 pairs of multipole records, 5 float4 per pair
+// holding (M, cx), (cy, cz), (-Qxx, -Qyy), (-Qzz, -Qxy), (-Qxz, -Qyz) of both
+// entries side by side (cx.. = centre of mass relative to the group centre).
+// Star staging: (tile + 32) / 2 pairs, 2 float4 per pair: (x, y), (z, m).
+constexpr int kCellPairF4 = 5, kStarPairF4 = 2;
+constexpr int kP2PUnroll = RV_P2P_UNROLL, kM2PUnroll = RV_M2P_UNROLL;
 __host__ __device__ inline size_t warp_smem_bytes(int tile) {
-    return (size_t)kStackCap * 4 + 32 * 4 + (size_t)(tile + 32) * 48 + (size_t)(tile + 32) * 16;
+    return (size_t)kStackCap * 4 + 32 * 4 + (size_t)(tile + 32) / 2 * 16 * (kCellPairF4 + kStarPairF4);
 }
 
 // The tree of one member as the walk sees it.
@@ -101,112 +117,150 @@ struct Acc {
     float cx, cy, cz, cp;      // Neumaier compensation
 };
 
-// A lane serves NS (target, list share) slots: slot q evaluates its target
-// against list entries j0[q], j0[q] + k, ... (positions relative to the
-// group's centre; j0 >= 2^20 marks an idle slot).
-template <int NS>
-struct Slots {
-    float x[NS], y[NS], z[NS];
-    int j0[NS];
-    int k;
+// Two FP32 values in one 64-bit register (low half: the even list entry).
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ float f2_sum(f2 v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo + hi;
+}
+__device__ __forceinline__ f2 f2_rsqrt(f2 v, bool guard_zero) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    float a = rsqrtf(lo), b = rsqrtf(hi);
+    if (guard_zero) {
+        a = (lo > 0.f) ? a : 0.f;
+        b = (hi > 0.f) ? b : 0.f;
+    }
+    return f2_pack(a, b);
+}
+constexpr f2 kF2MinusHalf = 0xBF000000BF000000ull;     // (-0.5f, -0.5f)
+constexpr f2 kF2MinusFiveHalf = 0xC0200000C0200000ull; // (-2.5f, -2.5f)
+
+// A lane's target (minus its position relative to the group's centre, in both
+// halves) and its share of a staged list: pairs j0, j0 + k, ... (j0 >= 2^20:
+// the lane takes no share).
+struct Tgt {
+    f2 nx, ny, nz;
+    int j0, k;
 };
 
-struct Part {
-    float x, y, z, p;
-};
+__device__ __forceinline__ void add_tile(Acc &A, f2 tx, f2 ty, f2 tz, f2 tp) {
+    nadd(A.ax, A.cx, f2_sum(tx));
+    nadd(A.ay, A.cy, f2_sum(ty));
+    nadd(A.az, A.cz, f2_sum(tz));
+    nadd(A.ph, A.cp, -f2_sum(tp));
+}
 
+// Star pairs 0 .. npair-1 of a staged star list on this lane's target:
+//   d = x_j - x_i, a += m_j d / (d.d + e^2)^{3/2}, phi -= m_j / (d.d + e^2)^{1/2}.
 template <bool SOFT>
-__device__ __forceinline__ void p2p_pair(const float4 s, float xi, float yi, float zi, float eps2, Part &t) {
-    float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    float rinv = rsqrtf(r2);
-    if (!SOFT) rinv = (r2 > 0.f) ? rinv : 0.f;
-    float mr = s.w * rinv;
-    float mr3 = mr * (rinv * rinv);
-    t.x = fmaf(mr3, dx, t.x);
-    t.y = fmaf(mr3, dy, t.y);
-    t.z = fmaf(mr3, dz, t.z);
-    t.p -= mr;
+__device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc &A) {
+    f2 tx = 0, ty = 0, tz = 0, tp = 0;   // tp sums +m/r
+#pragma unroll kP2PUnroll
+    for (int j = t.j0; j < npair; j += t.k) {
+        const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(src)[2 * j];      // x, y
+        const ulonglong2 b = reinterpret_cast<const ulonglong2 *>(src)[2 * j + 1];  // z, m
+        f2 dx = f2_add(a.x, t.nx), dy = f2_add(a.y, t.ny), dz = f2_add(b.x, t.nz);
+        f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
+        f2 rinv = f2_rsqrt(r2, !SOFT);
+        f2 mr = f2_mul(b.y, rinv);
+        f2 mr3 = f2_mul(mr, f2_mul(rinv, rinv));
+        tx = f2_fma(mr3, dx, tx);
+        ty = f2_fma(mr3, dy, ty);
+        tz = f2_fma(mr3, dz, tz);
+        tp = f2_add(tp, mr);
+    }
+    add_tile(A, tx, ty, tz, tp);
 }
 
+// Cell pairs 0 .. npair-1 of a staged cell list on this lane's target. With
+// d = com - x_i = -r, rho^2 = d.d + e^2, the staged -Q gives q = -Q d = Q r
+// and s = d.q / rho^4 = -(r.Q.r) / rho^4, so that
+//   a += (M - 5/2 s) d / rho^3 + q / rho^5,  phi -= (M - s/2) / rho,
+// which is the monopole + quadrupole expansion of the file header.
 template <bool QUAD>
-__device__ __forceinline__ void m2p_pair(const float4 *src, int j, float xi, float yi, float zi, float eps2,
-                                         Part &t) {
-    float4 a = src[3 * j];
-    float rx = xi - a.y, ry = yi - a.z, rz = zi - a.w;
-    float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2)));
-    // r > 0: an accepted cell's box is separated from the group's box
-    float rinv = rsqrtf(r2);
-    float u = rinv * rinv;
-    float rinv3 = rinv * u;
-    if (QUAD) {
-        float4 b = src[3 * j + 1];
-        float4 e = src[3 * j + 2];
-        // Q r with Q = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
-        float qx = fmaf(b.x, rx, fmaf(b.w, ry, e.x * rz));
-        float qy = fmaf(b.w, rx, fmaf(b.y, ry, e.y * rz));
-        float qz = fmaf(e.x, rx, fmaf(e.y, ry, b.z * rz));
-        float rqr = fmaf(rx, qx, fmaf(ry, qy, rz * qz));
-        float w = rqr * (u * u);                  // (r.Q.r) / rho^4
-        float rinv5 = rinv3 * u;
-        float B = -rinv3 * fmaf(2.5f, w, a.x);    // -(M + 5/2 w) / rho^3
-        t.x = fmaf(B, rx, fmaf(rinv5, qx, t.x));
-        t.y = fmaf(B, ry, fmaf(rinv5, qy, t.y));
-        t.z = fmaf(B, rz, fmaf(rinv5, qz, t.z));
-        t.p = fmaf(-rinv, fmaf(0.5f, w, a.x), t.p); // -(M + w/2) / rho
-    } else {
-        float mr3 = a.x * rinv3;
-        t.x = fmaf(-mr3, rx, t.x);
-        t.y = fmaf(-mr3, ry, t.y);
-        t.z = fmaf(-mr3, rz, t.z);
-        t.p = fmaf(-a.x, rinv, t.p);
-    }
-}
-
-template <int NS>
-__device__ __forceinline__ void add_tile(Acc *A, const Part *t) {
-#pragma unroll
-    for (int q = 0; q < NS; q++) {
-        nadd(A[q].ax, A[q].cx, t[q].x); nadd(A[q].ay, A[q].cy, t[q].y);
-        nadd(A[q].az, A[q].cz, t[q].z); nadd(A[q].ph, A[q].cp, t[q].p);
-    }
-}
-
-// This lane's shares of a staged star list (cnt entries).
-template <bool SOFT, int NS>
-__device__ __forceinline__ void eval_p2p(const float4 *src, int cnt, const Slots<NS> &S, float eps2, Acc *A) {
-    Part t[NS];
-#pragma unroll
-    for (int q = 0; q < NS; q++) t[q] = Part{0.f, 0.f, 0.f, 0.f};
-    if (NS == 1) {
-#pragma unroll 4
-        for (int j = S.j0[0]; j < cnt; j += S.k) p2p_pair<SOFT>(src[j], S.x[0], S.y[0], S.z[0], eps2, t[0]);
-    } else {
-#pragma unroll 2
-        for (int ja = S.j0[0], jb = S.j0[NS - 1]; ja < cnt || jb < cnt; ja += S.k, jb += S.k) {
-            if (ja < cnt) p2p_pair<SOFT>(src[ja], S.x[0], S.y[0], S.z[0], eps2, t[0]);
-            if (jb < cnt) p2p_pair<SOFT>(src[jb], S.x[NS - 1], S.y[NS - 1], S.z[NS - 1], eps2, t[NS - 1]);
+__device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc &A) {
+    f2 tx = 0, ty = 0, tz = 0, tp = 0;   // tp sums +(M - s/2)/rho
+#pragma unroll kM2PUnroll
+    for (int j = t.j0; j < npair; j += t.k) {
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(src) + kCellPairF4 * j;
+        const ulonglong2 a = p[0];   // M, cx
+        const ulonglong2 b = p[1];   // cy, cz
+        f2 dx = f2_add(a.y, t.nx), dy = f2_add(b.x, t.ny), dz = f2_add(b.y, t.nz);
+        f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
+        // r > 0: an accepted cell's box is separated from the group's box
+        f2 rinv = f2_rsqrt(r2, false);
+        f2 u = f2_mul(rinv, rinv);
+        f2 rinv3 = f2_mul(rinv, u);
+        if (QUAD) {
+            const ulonglong2 c = p[2];   // -Qxx, -Qyy
+            const ulonglong2 e = p[3];   // -Qzz, -Qxy
+            const ulonglong2 f = p[4];   // -Qxz, -Qyz
+            f2 qx = f2_fma(c.x, dx, f2_fma(e.y, dy, f2_mul(f.x, dz)));
+            f2 qy = f2_fma(e.y, dx, f2_fma(c.y, dy, f2_mul(f.y, dz)));
+            f2 qz = f2_fma(f.x, dx, f2_fma(f.y, dy, f2_mul(e.x, dz)));
+            f2 dq = f2_fma(dx, qx, f2_fma(dy, qy, f2_mul(dz, qz)));
+            f2 sw = f2_mul(dq, f2_mul(u, u));
+            f2 rinv5 = f2_mul(rinv3, u);
+            f2 B = f2_mul(rinv3, f2_fma(kF2MinusFiveHalf, sw, a.x));
+            tx = f2_fma(B, dx, f2_fma(rinv5, qx, tx));
+            ty = f2_fma(B, dy, f2_fma(rinv5, qy, ty));
+            tz = f2_fma(B, dz, f2_fma(rinv5, qz, tz));
+            tp = f2_fma(rinv, f2_fma(kF2MinusHalf, sw, a.x), tp);
+        } else {
+            f2 mr3 = f2_mul(a.x, rinv3);
+            tx = f2_fma(mr3, dx, tx);
+            ty = f2_fma(mr3, dy, ty);
+            tz = f2_fma(mr3, dz, tz);
+            tp = f2_fma(a.x, rinv, tp);
         }
     }
-    add_tile<NS>(A, t);
+    add_tile(A, tx, ty, tz, tp);
 }
 
-// This lane's shares of a staged cell list (cnt multipole records).
-template <bool QUAD, int NS>
-__device__ __forceinline__ void eval_m2p(const float4 *src, int cnt, const Slots<NS> &S, float eps2, Acc *A) {
-    Part t[NS];
-#pragma unroll
-    for (int q = 0; q < NS; q++) t[q] = Part{0.f, 0.f, 0.f, 0.f};
-    if (NS == 1) {
-#pragma unroll 2
-        for (int j = S.j0[0]; j < cnt; j += S.k) m2p_pair<QUAD>(src, j, S.x[0], S.y[0], S.z[0], eps2, t[0]);
-    } else {
-        for (int ja = S.j0[0], jb = S.j0[NS - 1]; ja < cnt || jb < cnt; ja += S.k, jb += S.k) {
-            if (ja < cnt) m2p_pair<QUAD>(src, ja, S.x[0], S.y[0], S.z[0], eps2, t[0]);
-            if (jb < cnt) m2p_pair<QUAD>(src, jb, S.x[NS - 1], S.y[NS - 1], S.z[NS - 1], eps2, t[NS - 1]);
-        }
+// Field f of staged entry e in a pair-interleaved list whose pairs are
+// `pair_f4` float4 long.
+__device__ __forceinline__ float *staged(float4 *base, int pair_f4, int e, int f) {
+    return reinterpret_cast<float *>(base + pair_f4 * (e >> 1)) + 2 * f + (e & 1);
+}
+
+// An odd list gets a massless partner in its last pair at the position of
+// the entry beside it (finite, nonzero distance; contributes exactly 0).
+__device__ __forceinline__ void pad_cells(float4 *m2p, int cnt) {
+    if ((cnt & 1) && (threadIdx.x & 31) == 0) {
+        float *d = reinterpret_cast<float *>(m2p + kCellPairF4 * (cnt >> 1));
+        d[1] = 0.f;
+        d[3] = d[2]; d[5] = d[4]; d[7] = d[6];
+        for (int f = 4; f < 10; f++) d[2 * f + 1] = 0.f;
     }
-    add_tile<NS>(A, t);
+}
+__device__ __forceinline__ void pad_stars(float4 *p2p, int cnt) {
+    if ((cnt & 1) && (threadIdx.x & 31) == 0) {
+        float *d = reinterpret_cast<float *>(p2p + kStarPairF4 * (cnt >> 1));
+        d[1] = d[0]; d[3] = d[2]; d[5] = d[4];
+        d[7] = 0.f;
+    }
 }
 
 __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
@@ -219,17 +273,17 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 // mass are (cell centre - g) + (centre of mass - cell centre). Differences of
 // nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
 // any distance from the origin.
-template <bool SOFT, bool QUAD, bool REC, int NS>
+template <bool SOFT, bool QUAD, bool REC>
 __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
                                            const unsigned long long *thr_rec, int gid, char *wsm, const int blo[3],
-                                           const int bhi[3], const float g[3], const Slots<NS> &sl, float eps2,
-                                           Acc *acc, unsigned long long &np2p, unsigned long long &nm2p) {
+                                           const int bhi[3], const float g[3], const Tgt &tg, f2 eps2, Acc &acc,
+                                           unsigned long long &np2p, unsigned long long &nm2p) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
     int *stack = reinterpret_cast<int *>(wsm);
     int *lane_cell = stack + kStackCap;
     float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 32);
-    float4 *p2p = m2p + 3 * (T + 32);
+    float4 *p2p = m2p + kCellPairF4 * ((T + 32) / 2);
     const unsigned lt = lanemask_lt();
     const int ncell = G.ncell;
 
@@ -296,17 +350,26 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         top += __popc(om);
         hwm = max(hwm, top);
         if (top > kStackCap) { ok = false; break; }
-        // accepted cells: stage their multipole records, centre of mass relative to g
+        // accepted cells: stage their multipole records, centre of mass relative to g, -Q
         unsigned am = __ballot_sync(0xffffffffu, accept);
         if (accept) {
             int p = nm + __popc(am & lt);
             float4 r0 = __ldg(&A.cmom[3 * c + 0]);
             float c0[3];
             geo_centre(b, G.lo, G.unit, c0);
-            m2p[3 * p + 0] = make_float4(r0.x, (c0[0] - g[0]) + r0.y, (c0[1] - g[1]) + r0.z, (c0[2] - g[2]) + r0.w);
+            *staged(m2p, kCellPairF4, p, 0) = r0.x;
+            *staged(m2p, kCellPairF4, p, 1) = (c0[0] - g[0]) + r0.y;
+            *staged(m2p, kCellPairF4, p, 2) = (c0[1] - g[1]) + r0.z;
+            *staged(m2p, kCellPairF4, p, 3) = (c0[2] - g[2]) + r0.w;
             if (QUAD) {
-                m2p[3 * p + 1] = __ldg(&A.cmom[3 * c + 1]);
-                m2p[3 * p + 2] = __ldg(&A.cmom[3 * c + 2]);
+                float4 q1 = __ldg(&A.cmom[3 * c + 1]);   // Qxx, Qyy, Qzz, Qxy
+                float4 q2 = __ldg(&A.cmom[3 * c + 2]);   // Qxz, Qyz
+                *staged(m2p, kCellPairF4, p, 4) = -q1.x;
+                *staged(m2p, kCellPairF4, p, 5) = -q1.y;
+                *staged(m2p, kCellPairF4, p, 6) = -q1.z;
+                *staged(m2p, kCellPairF4, p, 7) = -q1.w;
+                *staged(m2p, kCellPairF4, p, 8) = -q2.x;
+                *staged(m2p, kCellPairF4, p, 9) = -q2.y;
             }
         }
         nm += __popc(am);
@@ -335,15 +398,23 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                 int cc = min(32, end - o);
                 if (lane < cc) {
                     float4 s = __ldg(&A.pos[o + lane]);
-                    p2p[np + lane] = make_float4(s.x - g[0], s.y - g[1], s.z - g[2], s.w);
+                    const int e = np + lane;
+                    *staged(p2p, kStarPairF4, e, 0) = s.x - g[0];
+                    *staged(p2p, kStarPairF4, e, 1) = s.y - g[1];
+                    *staged(p2p, kStarPairF4, e, 2) = s.z - g[2];
+                    *staged(p2p, kStarPairF4, e, 3) = s.w;
                 }
                 np += cc;
                 np2p += cc;
                 if (np >= T) {
                     __syncwarp();
-                    eval_p2p<SOFT, NS>(p2p, T, sl, eps2, acc);
+                    eval_p2p<SOFT>(p2p, T / 2, tg, eps2, acc);
                     __syncwarp();
-                    if (lane < np - T) p2p[lane] = p2p[T + lane];
+                    // T is even: the leftover entries move pair by pair
+                    if (lane < (np - T + 1) / 2) {
+                        p2p[kStarPairF4 * lane] = p2p[kStarPairF4 * (T / 2 + lane)];
+                        p2p[kStarPairF4 * lane + 1] = p2p[kStarPairF4 * (T / 2 + lane) + 1];
+                    }
                     np -= T;
                     __syncwarp();
                 }
@@ -351,12 +422,12 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         }
         if (nm >= T) {
             __syncwarp();
-            eval_m2p<QUAD, NS>(m2p, T, sl, eps2, acc);
+            eval_m2p<QUAD>(m2p, T / 2, tg, eps2, acc);
             __syncwarp();
-            if (lane < nm - T) {
-                m2p[3 * lane] = m2p[3 * (T + lane)];
-                m2p[3 * lane + 1] = m2p[3 * (T + lane) + 1];
-                m2p[3 * lane + 2] = m2p[3 * (T + lane) + 2];
+            if (lane < (nm - T + 1) / 2) {
+#pragma unroll
+                for (int f = 0; f < kCellPairF4; f++)
+                    m2p[kCellPairF4 * lane + f] = m2p[kCellPairF4 * (T / 2 + lane) + f];
             }
             nm -= T;
         }
@@ -364,35 +435,34 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
     }
     __syncwarp();
     if (ok) {
-        if (np > 0) eval_p2p<SOFT, NS>(p2p, np, sl, eps2, acc);
-        if (nm > 0) eval_m2p<QUAD, NS>(m2p, nm, sl, eps2, acc);
+        pad_stars(p2p, np);
+        pad_cells(m2p, nm);
+        __syncwarp();
+        if (np > 0) eval_p2p<SOFT>(p2p, (np + 1) / 2, tg, eps2, acc);
+        if (nm > 0) eval_m2p<QUAD>(m2p, (nm + 1) / 2, tg, eps2, acc);
     }
     __syncwarp();
     if (lane == 0) atomicMax(&A.st->stack_hwm, hwm);
     return ok;
 }
 
-// Virtual lane v = lane + 32 q holds a lane's slot q. Star t is served by the
-// virtual lanes t, t + s, ..., t + (k - 1) s; their partial totals are added
-// into lane t in that order through the warp's (now free) staging memory.
-template <int NS>
-__device__ __forceinline__ Acc combine_slots(const Acc *acc, int s, int k, float *scr) {
+// Star t is served by lanes t, t + s, ..., t + (k - 1) s; their partial
+// totals are added into lane t in that order through the warp's (now free)
+// staging memory.
+__device__ __forceinline__ Acc combine_shares(const Acc &acc, int s, int k, float *scr) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-#pragma unroll
-    for (int q = 0; q < NS; q++) {
-        float *d = scr + 8 * (lane + 32 * q);
-        d[0] = acc[q].ax; d[1] = acc[q].ay; d[2] = acc[q].az; d[3] = acc[q].ph;
-        d[4] = acc[q].cx; d[5] = acc[q].cy; d[6] = acc[q].cz; d[7] = acc[q].cp;
-    }
+    float *d = scr + 8 * lane;
+    d[0] = acc.ax; d[1] = acc.ay; d[2] = acc.az; d[3] = acc.ph;
+    d[4] = acc.cx; d[5] = acc.cy; d[6] = acc.cz; d[7] = acc.cp;
     __syncwarp();
     Acc out = {};
     if (lane < s)
         for (int i = 0; i < k; i++) {
-            const float *d = scr + 8 * (lane + i * s);
-            nadd(out.ax, out.cx, d[0]); nadd(out.ay, out.cy, d[1]);
-            nadd(out.az, out.cz, d[2]); nadd(out.ph, out.cp, d[3]);
-            out.cx += d[4]; out.cy += d[5]; out.cz += d[6]; out.cp += d[7];
+            const float *e = scr + 8 * (lane + i * s);
+            nadd(out.ax, out.cx, e[0]); nadd(out.ay, out.cy, e[1]);
+            nadd(out.az, out.cz, e[2]); nadd(out.ph, out.cp, e[3]);
+            out.cx += e[4]; out.cy += e[5]; out.cz += e[6]; out.cp += e[7];
         }
     __syncwarp();
     return out;
@@ -428,7 +498,6 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
 // to +-2^23); the tree's groups follow.
 template <bool SOFT, bool QUAD, bool REC>
 __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree_k(WalkArgs A) {
-    constexpr int NS = RV_WALK_SLOTS;
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // per-level opening thresholds in shared memory: lanes of a warp test cells
@@ -446,13 +515,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         if (lane == 0) gi = atomicAdd(&A.st->next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= nitem) break;
-        Acc acc[NS];
-#pragma unroll
-        for (int q = 0; q < NS; q++) acc[q] = Acc{};
+        Acc acc = {};
         unsigned long long a2 = 0, a3 = 0;
         float *scr = reinterpret_cast<float *>(wsm + kStackCap * 4 + 32 * 4);  // m2p staging, free after a walk
         if (gi < A.n_extra) {
-            // ---- a particle outside the tree: all 32 NS virtual lanes share its interaction list
+            // ---- a particle outside the tree: all 32 lanes share its interaction list
             const int kx = gi;
             const int mk = A.extra_per_member ? kx : (A.xmem ? A.xmem[kx] : 0);
             const TreeGeo G = tree_geo(A, mk);
@@ -470,22 +537,21 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             }
             float g[3];
             geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), G.lo, G.unit, g);
-            Slots<NS> sl;
-            sl.k = 32 * NS;
-#pragma unroll
-            for (int q = 0; q < NS; q++) {
-                sl.x[q] = xi - g[0]; sl.y[q] = yi - g[1]; sl.z[q] = zi - g[2];
-                sl.j0[q] = lane + 32 * q;
-            }
+            Tgt tg;
+            tg.nx = f2_pack(g[0] - xi, g[0] - xi);
+            tg.ny = f2_pack(g[1] - yi, g[1] - yi);
+            tg.nz = f2_pack(g[2] - zi, g[2] - zi);
+            tg.j0 = lane;
+            tg.k = 32;
             bool ok = true;
             if (G.ncell > 0 && G.root >= 0)
-                ok = walk_group<false, QUAD, false, NS>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, sl, e * e, acc,
-                                                        a2, a3);
+                ok = walk_group<false, QUAD, false>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, tg,
+                                                    f2_pack(e * e, e * e), acc, a2, a3);
             if (!ok) {
                 if (lane == 0) latch_err(A.st, kErrStack);
                 continue;
             }
-            Acc tot = combine_slots<NS>(acc, 1, 32 * NS, scr);
+            Acc tot = combine_shares(acc, 1, 32, scr);
             if (lane == 0) {
                 extra_terms(A, xi, yi, zi, ek, kx, mk, tot);
                 A.xout[4 * kx] = tot.ax + tot.cx;
@@ -509,25 +575,28 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         int blo[3] = {b.x, b.y, b.z}, bhi[3] = {b.x + side, b.y + side, b.z + side};
         float g[3];
         geo_centre(b, G.lo, G.unit, g);
-        const int s = grp.y, k = (32 * NS) / s;  // k virtual lanes per star
-        Slots<NS> sl;
-        sl.k = k;
-#pragma unroll
-        for (int q = 0; q < NS; q++) {
-            const int v = lane + 32 * q, t = v % s, sub = v / s;
+        const int s = grp.y, k = 32 / s;  // k lanes per star
+        Tgt tg;
+        {
+            const int t = lane % s, sub = lane / s;
             const float4 pq = __ldg(&A.pos[grp.x + t]);
-            sl.x[q] = pq.x - g[0]; sl.y[q] = pq.y - g[1]; sl.z[q] = pq.z - g[2];
-            sl.j0[q] = (sub < k) ? sub : (1 << 20);  // virtual lanes beyond k s take no list entries
+            // minus the star's position relative to g (exact: FP32 negation)
+            const float nx = -(pq.x - g[0]), ny = -(pq.y - g[1]), nz = -(pq.z - g[2]);
+            tg.nx = f2_pack(nx, nx);
+            tg.ny = f2_pack(ny, ny);
+            tg.nz = f2_pack(nz, nz);
+            tg.j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k s take no list pairs
+            tg.k = k;
         }
-        bool ok = walk_group<SOFT, QUAD, REC, NS>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, sl,
-                                                  A.eps2, acc, a2, a3);
+        bool ok = walk_group<SOFT, QUAD, REC>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, tg,
+                                              f2_pack(A.eps2, A.eps2), acc, a2, a3);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
         }
         np2p += a2 * (unsigned long long)s;
         nm2p += a3 * (unsigned long long)s;
-        Acc tot = combine_slots<NS>(acc, s, k, scr);
+        Acc tot = combine_shares(acc, s, k, scr);
         if (lane < s) {
             const float4 p = __ldg(&A.pos[grp.x + lane]);
             // the star's own pair was evaluated at r = 0: remove its -m/eps
