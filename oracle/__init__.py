@@ -148,7 +148,7 @@ class Tree:
       key, perm         sorted keys and sorted slot -> caller index
       cells [ncell, 9]  level, first, count, child, nchild, parent, ox, oy, oz
       moments [ncell,10] M, com x/y/z, Q xx, yy, zz, xy, xz, yz (FP64)
-      groups [ngroup,3] first, count, box cell
+      groups [ngroup,8] first, count, box lo x/y/z, box hi x/y/z (grid units)
       lo, L, scale      bounding cube
     """
 
@@ -172,7 +172,7 @@ class Tree:
         lib().orc_tree_cells(self._h, _p(self.cells, _i64))
         self.moments = np.zeros((self.ncell, 10))
         lib().orc_tree_moments(self._h, _p(self.moments, _d))
-        self.groups = np.zeros((self.ngroup, 3), dtype=np.int64)
+        self.groups = np.zeros((self.ngroup, 8), dtype=np.int64)
         lib().orc_tree_groups(self._h, _p(self.groups, _i64))
         # FP64 copies of the stars in key order
         self.x_sorted = self.x[self.perm].astype(np.float64)

@@ -181,8 +181,8 @@ typedef struct {
     int64_t *first, *count, *child, *nchild, *parent;
     int64_t *ox, *oy, *oz;          /* integer-grid origin of the cell box */
     double *cm, *cx, *cy, *cz, *cq; /* mass, centre of mass, Q (xx,yy,zz,xy,xz,yz) */
-    /* walk groups */
-    int64_t *gfirst, *gcount, *gcell; /* gcell: cell whose box is the group box */
+    /* walk groups: first star, count, integer-grid box [glo, ghi) per axis */
+    int64_t *gfirst, *gcount, *glo, *ghi;
 } orc_tree;
 
 static void tree_push_cell(orc_tree *t, int32_t lev, int64_t first, int64_t count, int64_t parent) {
@@ -275,55 +275,40 @@ static void build_moments(orc_tree *t) {
     }
 }
 
-static void push_group(orc_tree *t, int64_t first, int64_t count, int64_t boxcell) {
+static void push_group(orc_tree *t, int64_t first, int64_t count, const int64_t lo[3], const int64_t hi[3]) {
     if (t->ngroup == t->gcap) {
         t->gcap = t->gcap ? 2 * t->gcap : 64;
         t->gfirst = (int64_t *)realloc(t->gfirst, sizeof(int64_t) * (size_t)t->gcap);
         t->gcount = (int64_t *)realloc(t->gcount, sizeof(int64_t) * (size_t)t->gcap);
-        t->gcell = (int64_t *)realloc(t->gcell, sizeof(int64_t) * (size_t)t->gcap);
+        t->glo = (int64_t *)realloc(t->glo, sizeof(int64_t) * 3 * (size_t)t->gcap);
+        t->ghi = (int64_t *)realloc(t->ghi, sizeof(int64_t) * 3 * (size_t)t->gcap);
     }
-    t->gfirst[t->ngroup] = first; t->gcount[t->ngroup] = count; t->gcell[t->ngroup] = boxcell;
-    t->ngroup++;
+    int64_t g = t->ngroup++;
+    t->gfirst[g] = first; t->gcount[g] = count;
+    for (int a = 0; a < 3; a++) { t->glo[3 * g + a] = lo[a]; t->ghi[3 * g + a] = hi[a]; }
 }
 
-static void chunk_cell(orc_tree *t, int64_t c) {
-    for (int64_t o = 0; o < t->count[c]; o += t->group_max) {
-        int64_t k = t->count[c] - o;
-        push_group(t, t->first[c] + o, k < t->group_max ? k : t->group_max, c);
-    }
-}
-
-/* Walk groups (reading): a "unit" is a cell with at most G particles whose
- * parent has more; consecutive unit siblings are packed greedily while the
- * total stays <= G. A pack of one unit uses that unit's box, a pack of
- * several uses the parent's box. A leaf with more than G particles is cut
- * into chunks of G that use the leaf's box. */
-static void visit_groups(orc_tree *t, int64_t p) {
-    int64_t pk_first = -1, pk_count = 0, pk_units = 0, pk_cell = -1;
-    for (int64_t k = 0; k < t->nchild[p]; k++) {
-        int64_t c = t->child[p] + k;
-        if (t->count[c] <= t->group_max) {
-            if (pk_units > 0 && pk_count + t->count[c] > t->group_max) {
-                push_group(t, pk_first, pk_count, pk_units == 1 ? pk_cell : p);
-                pk_units = 0;
-            }
-            if (pk_units == 0) { pk_first = t->first[c]; pk_count = 0; pk_cell = c; }
-            pk_count += t->count[c];
-            pk_units++;
-        } else {
-            if (pk_units > 0) { push_group(t, pk_first, pk_count, pk_units == 1 ? pk_cell : p); pk_units = 0; }
-            if (cell_is_leaf(t, c)) chunk_cell(t, c);
-            else visit_groups(t, c);
-        }
-    }
-    if (pk_units > 0) push_group(t, pk_first, pk_count, pk_units == 1 ? pk_cell : p);
-}
-
+/* Walk groups (reading; the paper does not group targets):
+ * runs of G consecutive stars in key order, the last one possibly shorter.
+ * A group's box is the smallest box on the integer grid that holds its stars'
+ * grid cells: per axis lo = min q, hi = max q + 1, with q the star's grid
+ * coordinate (its key de-interleaved). Every star of a group lies in the
+ * group's box, so a cell the box-box test accepts for the group satisfies the
+ * opening-angle test for each of its stars. */
 static void build_groups(orc_tree *t) {
-    if (t->ncell == 0) return;
-    if (t->count[0] <= t->group_max) push_group(t, 0, t->count[0], 0);
-    else if (cell_is_leaf(t, 0)) chunk_cell(t, 0);
-    else visit_groups(t, 0);
+    for (int64_t f = 0; f < t->n; f += t->group_max) {
+        int64_t cnt = t->n - f < t->group_max ? t->n - f : t->group_max;
+        int64_t lo[3], hi[3];
+        for (int64_t i = f; i < f + cnt; i++) {
+            int64_t q[3];
+            deinterleave(t->key[i], &q[0], &q[1], &q[2]);
+            for (int a = 0; a < 3; a++) {
+                if (i == f || q[a] < lo[a]) lo[a] = q[a];
+                if (i == f || q[a] + 1 > hi[a]) hi[a] = q[a] + 1;
+            }
+        }
+        push_group(t, f, cnt, lo, hi);
+    }
 }
 
 orc_tree *orc_tree_build(int64_t n, const float *x, const float *y, const float *z, const float *m,
@@ -355,7 +340,7 @@ void orc_tree_free(orc_tree *t) {
     free(t->key); free(t->perm); free(t->x); free(t->y); free(t->z); free(t->m);
     free(t->level); free(t->first); free(t->count); free(t->child); free(t->nchild); free(t->parent);
     free(t->ox); free(t->oy); free(t->oz); free(t->cm); free(t->cx); free(t->cy); free(t->cz); free(t->cq);
-    free(t->gfirst); free(t->gcount); free(t->gcell);
+    free(t->gfirst); free(t->gcount); free(t->glo); free(t->ghi);
     free(t);
 }
 
@@ -383,10 +368,12 @@ void orc_tree_moments(const orc_tree *t, double *out) {
         for (int k = 0; k < 6; k++) o[4 + k] = t->cq[6 * c + k];
     }
 }
-/* groups: [ngroup][3] = first, count, box cell */
+/* groups: [ngroup][8] = first, count, box lo x, y, z, box hi x, y, z */
 void orc_tree_groups(const orc_tree *t, int64_t *out) {
     for (int64_t g = 0; g < t->ngroup; g++) {
-        out[3 * g] = t->gfirst[g]; out[3 * g + 1] = t->gcount[g]; out[3 * g + 2] = t->gcell[g];
+        int64_t *o = out + 8 * g;
+        o[0] = t->gfirst[g]; o[1] = t->gcount[g];
+        for (int a = 0; a < 3; a++) { o[2 + a] = t->glo[3 * g + a]; o[5 + a] = t->ghi[3 * g + a]; }
     }
 }
 
@@ -471,12 +458,6 @@ static void walk_cell(walk_state *w, int64_t c) {
     for (int64_t k = 0; k < t->nchild[c]; k++) walk_cell(w, t->child[c] + k);
 }
 
-static void box_of_cell(const orc_tree *t, int64_t c, int64_t lo[3], int64_t hi[3]) {
-    int64_t s = (int64_t)1 << (ORC_MAXLEVEL - t->level[c]);
-    lo[0] = t->ox[c]; lo[1] = t->oy[c]; lo[2] = t->oz[c];
-    hi[0] = lo[0] + s; hi[1] = lo[1] + s; hi[2] = lo[2] + s;
-}
-
 /* Tree forces on every tree particle, written in caller order.
  * eps_star softens every tree pair (all tree particles are stars).
  * Extra particles (chain centres of mass, unsoftened when xeps = 0) are not in
@@ -502,7 +483,7 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t g = 0; g < t->ngroup; g++) {
         int64_t blo[3], bhi[3];
-        box_of_cell(t, t->gcell[g], blo, bhi);
+        for (int a = 0; a < 3; a++) { blo[a] = t->glo[3 * g + a]; bhi[a] = t->ghi[3 * g + a]; }
         for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
             if (want && !want[t->perm[i]]) continue;
             walk_state w;

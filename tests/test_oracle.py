@@ -228,12 +228,15 @@ def _check_tree_invariants(T, n_leaf, G):
                 o = cells[c, 6 + a]
                 assert np.all((q[a][sl] >= o) & (q[a][sl] < o + s))
     assert np.all(leaf_cover == 1)
-    # groups partition the particles, each <= G
-    gs = T.groups[np.argsort(T.groups[:, 0])]
-    assert gs[0, 0] == 0 and np.all(gs[1:, 0] == gs[:-1, 0] + gs[:-1, 1]) and gs[-1, 0] + gs[-1, 1] == n
-    assert gs[:, 1].max() <= G
-    for f, k, c in gs:
-        assert first[c] <= f and f + k <= first[c] + cnt[c]
+    # groups: consecutive runs of G (the last one shorter) partitioning the
+    # particles, each box the tightest one holding its particles' grid cells
+    gs = T.groups
+    assert np.all(gs[:, 0] == np.arange(len(gs)) * G)
+    assert np.all(gs[:-1, 1] == G) and 1 <= gs[-1, 1] <= G and gs[-1, 0] + gs[-1, 1] == n
+    if q is not None:
+        for f, k, *box in gs:
+            for a in range(3):
+                assert box[a] == q[a][f:f + k].min() and box[3 + a] == q[a][f:f + k].max() + 1
 
 
 @pytest.mark.parametrize("n,n_leaf,G", [(1, 16, 32), (2, 1, 1), (33, 16, 32), (1000, 8, 32), (3000, 16, 64)])
@@ -245,11 +248,12 @@ def test_tree_invariants(n, n_leaf, G):
 
 def test_tree_coincident_particles():
     """All particles at one point: one chain of single-child cells down to an
-    overflow leaf at level 21, cut into groups of G."""
+    overflow leaf at level 21; groups of G share one grid cell as their box."""
     pos = np.full((3, 100), 0.25, dtype=np.float32)
     T = oracle.Tree(pos, np.ones(100, np.float32), 16, 32)
     assert T.ncell == 22 and T.cells[-1, 0] == 21 and T.cells[-1, 2] == 100
     assert list(T.groups[:, 1]) == [32, 32, 32, 4]
+    assert np.all(T.groups[:, 5:] - T.groups[:, 2:5] == 1)
 
 
 def test_moments_two_point_closed_form():
