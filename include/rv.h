@@ -56,7 +56,9 @@ typedef struct rv_ctx rv_ctx; /* opaque; owned by librv */
  *              group's box and the cell's box (0 <= theta < 2).
  *   eps_star   Plummer softening length of the stars (>= 0).
  *   n_leaf     a cell with more than n_leaf stars is split (1..64).
- *   group      stars per walk group, at most 32 (one warp lane each).
+ *   group      stars per walk group, at most 32: runs of `group` consecutive
+ *              stars in key order, each walked with the tightest integer-grid
+ *              box of its stars as the group's box.
  *   quadrupole 1: monopole + traceless quadrupole; 0: monopole only.
  *   tile       interaction-list tile, a multiple of 32 in [32, 256]. */
 typedef struct {
@@ -93,7 +95,7 @@ rv_status rv_set_workspace(rv_ctx *ctx, void *dev, size_t bytes);
  * gather of (x, y, z, m) in key order; cells = key prefixes split while they
  * hold more than n_leaf stars (down to level 21), breadth-first; per cell the
  * mass, centre of mass and traceless quadrupole about it (Sect. 1); walk
- * groups. Inputs are read during the call's stream work only. */
+ * groups (runs of `group` stars and their boxes). Inputs are read during the call's stream work only. */
 rv_status rv_build_tree(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
                         const float *m, void *stream);
 
@@ -292,7 +294,8 @@ rv_status rv_select_radius_static(int64_t n, const float *x, const float *y, con
  *   clink   int4 [ncell] (child first, n children, first star, star count)
  *   cmom    float4 [3 ncell] (M, com x, y, z), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0)
  *   cparent int32 [ncell]
- *   groups  int4 [ngroup] (first star, count, box cell, 0)
+ *   groups  int32 [ngroup][8] (first star, count, box lo x, y, z, box hi x, y, z): runs of
+ *           `group` consecutive stars per member, box = tightest integer-grid box of their cells
  *   bounds  double [5] (min x, y, z, L, 2^21/L) */
 typedef struct {
     int64_t n, ncell, ngroup;

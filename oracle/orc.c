@@ -288,16 +288,19 @@ static void push_group(orc_tree *t, int64_t first, int64_t count, const int64_t 
     for (int a = 0; a < 3; a++) { t->glo[3 * g + a] = lo[a]; t->ghi[3 * g + a] = hi[a]; }
 }
 
-/* Walk groups (reading; the paper does not group targets):
- * runs of G consecutive stars in key order, the last one possibly shorter.
- * A group's box is the smallest box on the integer grid that holds its stars'
- * grid cells: per axis lo = min q, hi = max q + 1, with q the star's grid
- * coordinate (its key de-interleaved). Every star of a group lies in the
- * group's box, so a cell the box-box test accepts for the group satisfies the
- * opening-angle test for each of its stars. */
-static void build_groups(orc_tree *t) {
-    for (int64_t f = 0; f < t->n; f += t->group_max) {
-        int64_t cnt = t->n - f < t->group_max ? t->n - f : t->group_max;
+/* Walk groups (reading; the paper does not group targets). A unit is a
+ * maximal cell with at most U = 16 G stars (a cell with <= U stars whose
+ * parent has more, or the root), or a leaf with more than U stars. Each unit
+ * is cut into runs of G consecutive stars in key order, the last run possibly
+ * shorter; each run is a group. A group's box is the smallest box on the
+ * integer grid that holds its stars' grid cells: per axis lo = min q,
+ * hi = max q + 1, with q the star's grid coordinate (its key de-interleaved).
+ * Every star of a group lies in the group's box, so a cell the box-box test
+ * accepts for the group satisfies the opening-angle test for each of its
+ * stars. */
+static void push_runs(orc_tree *t, int64_t first, int64_t count) {
+    for (int64_t f = first; f < first + count; f += t->group_max) {
+        int64_t cnt = first + count - f < t->group_max ? first + count - f : t->group_max;
         int64_t lo[3], hi[3];
         for (int64_t i = f; i < f + cnt; i++) {
             int64_t q[3];
@@ -309,6 +312,19 @@ static void build_groups(orc_tree *t) {
         }
         push_group(t, f, cnt, lo, hi);
     }
+}
+
+static void visit_units(orc_tree *t, int64_t c, int64_t U) {
+    if (t->count[c] <= U || cell_is_leaf(t, c)) {
+        push_runs(t, t->first[c], t->count[c]);
+        return;
+    }
+    for (int64_t k = 0; k < t->nchild[c]; k++) visit_units(t, t->child[c] + k, U);
+}
+
+static void build_groups(orc_tree *t) {
+    if (t->ncell == 0) return;
+    visit_units(t, 0, 16 * (int64_t)t->group_max);
 }
 
 orc_tree *orc_tree_build(int64_t n, const float *x, const float *y, const float *z, const float *m,

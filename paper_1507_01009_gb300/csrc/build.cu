@@ -514,53 +514,74 @@ __global__ void __launch_bounds__(kTopoBlock) topo_write_k(int64_t n, const uint
 // ---------------------------------------------------------------------------
 // walk groups
 // ---------------------------------------------------------------------------
-// A unit is a cell with <= G stars whose parent has more; consecutive unit
-// siblings are packed while the total stays <= G (box: the unit's own if the
-// pack has one unit, else the parent's); a leaf with more than G stars is
-// cut into chunks of G (box: the leaf). The root, if small, is one group.
-template <bool WRITE>
-__global__ void groups_k(const int4 *cbox, const int *clink, const int *gofs, int G, int64_t cap, DevState *st,
-                         int *gcnt, int4 *groups) {
-    int ncell = (int)min((int64_t)st->ncell, cap);
+// A unit is a maximal cell with at most U = 16 G stars (one with <= U stars
+// whose parent has more, or a member's root) or a leaf with more than U stars.
+// Each unit is cut into runs of G consecutive stars in key order, the last run
+// possibly shorter; each run is a group. A group's box is the tightest box on
+// the member's integer grid that holds its stars' grid cells: per axis
+// [min q, max q + 1), q the star's de-interleaved key. Every star lies in its
+// group's box, so a cell the box-box test accepts passes the opening test for
+// each star of the group.
+// gcnt[c] = groups of cell c (0 unless c is a unit).
+__global__ void groups_count_k(const int4 *cbox, const int4 *clink, const int *cparent, int G, int U, int64_t cap,
+                               const DevState *st, int *gcnt) {
+    const int ncell = (int)min((int64_t)st->ncell, cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
-        int4 lk = reinterpret_cast<const int4 *>(clink)[c];
-        int cnt = lk.w - lk.z;
-        int ng = 0;
-        int out = WRITE ? gofs[c] : 0;
-        auto emit = [&](int first, int count, int box) {
-            if (WRITE) groups[out + ng] = make_int4(first, count, box, 0);
-            ng++;
-        };
-        const bool root = cbox[c].w == 0;
-        if (root && cnt <= G) {
-            emit(lk.z, cnt, c);
-        } else if (cnt > G) {
-            if (lk.y == lk.x) {
-                for (int o = 0; o < cnt; o += G) emit(lk.z + o, min(G, cnt - o), c);
-            } else if (lk.x <= c || lk.y > ncell || lk.y - lk.x > 8) {
-                latch_err(st, kErrCells);
-            } else {
-                int pk_first = 0, pk_count = 0, pk_units = 0, pk_cell = 0;
-                for (int ch = lk.x; ch < lk.y; ch++) {
-                    int4 q = reinterpret_cast<const int4 *>(clink)[ch];
-                    int qc = q.w - q.z;
-                    if (qc <= G) {
-                        if (pk_units > 0 && pk_count + qc > G) {
-                            emit(pk_first, pk_count, pk_units == 1 ? pk_cell : c);
-                            pk_units = 0;
-                        }
-                        if (pk_units == 0) { pk_first = q.z; pk_count = 0; pk_cell = ch; }
-                        pk_count += qc;
-                        pk_units++;
-                    } else if (pk_units > 0) {
-                        emit(pk_first, pk_count, pk_units == 1 ? pk_cell : c);
-                        pk_units = 0;
-                    }
-                }
-                if (pk_units > 0) emit(pk_first, pk_count, pk_units == 1 ? pk_cell : c);
+        const int4 lk = clink[c];
+        const int cnt = lk.w - lk.z;
+        bool unit;
+        if (cnt > U) {
+            unit = (lk.x == lk.y);   // an overfull leaf
+        } else if (cbox[c].w == 0) {
+            unit = true;             // a member's root
+        } else {
+            const int p = cparent[c];
+            unit = false;
+            if (p >= 0 && p < ncell) {
+                const int4 pl = clink[p];
+                unit = (pl.w - pl.z) > U;
             }
         }
-        if (!WRITE) gcnt[c] = ng;
+        gcnt[c] = unit ? (cnt + G - 1) / G : 0;
+    }
+}
+
+// One warp per unit cell: writes its runs with their boxes from the scanned
+// offsets gofs (exclusive prefix of gcnt).
+__global__ void groups_write_k(const uint64_t *skey, const int4 *clink, const int *gofs, const int *gcnt_total,
+                               int G, int64_t cap, const DevState *st, int4 *groups) {
+    const int lane = threadIdx.x & 31;
+    const int ncell = (int)min((int64_t)st->ncell, cap);
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < ncell; c += nw) {
+        const int g0 = gofs[c];
+        const int g1 = (c + 1 < ncell) ? gofs[c + 1] : *gcnt_total;
+        if (g1 <= g0) continue;
+        const int4 lk = clink[c];
+        for (int r = 0; r < g1 - g0; r++) {
+            const int first = lk.z + r * G;
+            const int cnt = min(G, lk.w - first);
+            unsigned qlo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, qhi[3] = {0u, 0u, 0u};
+            if (lane < cnt) {
+                const uint64_t key = skey[first + lane];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    qlo[a] = compact3(key >> a);
+                    qhi[a] = qlo[a] + 1;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                for (int o = 16; o > 0; o >>= 1) {
+                    qlo[a] = min(qlo[a], __shfl_xor_sync(0xffffffffu, qlo[a], o));
+                    qhi[a] = max(qhi[a], __shfl_xor_sync(0xffffffffu, qhi[a], o));
+                }
+            if (lane == 0) {
+                const int g = g0 + r;
+                groups[2 * g] = make_int4(first, cnt, (int)qlo[0], (int)qlo[1]);
+                groups[2 * g + 1] = make_int4((int)qlo[2], (int)qhi[0], (int)qhi[1], (int)qhi[2]);
+            }
+        }
     }
 }
 
@@ -739,11 +760,14 @@ rv_status build_tree(rv_ctx *c, int n_members, const int64_t *offsets, const flo
                                              w.clink, w.cparent, w.carrive, w.mroot, w.st);
     count_launch(c);
     // groups
+    const int G = c->cfg.group, U = 16 * c->cfg.group;
+    const int4 *clink4 = reinterpret_cast<const int4 *>(w.clink);
     int gb = grid_for(c, c->cell_cap, 256);
-    groups_k<false><<<gb, 256, 0, s>>>(w.cbox, w.clink, nullptr, c->cfg.group, c->cell_cap, w.st, w.gcnt, nullptr);
+    groups_count_k<<<gb, 256, 0, s>>>(w.cbox, clink4, w.cparent, G, U, c->cell_cap, w.st, w.gcnt);
     count_launch(c);
     if ((r = exclusive_scan(c, w.gcnt, c->cell_cap, &w.st->ncell, &w.st->ngroup, s)) != RV_OK) return r;
-    groups_k<true><<<gb, 256, 0, s>>>(w.cbox, w.clink, w.gcnt, c->cfg.group, c->cell_cap, w.st, nullptr, w.groups);
+    groups_write_k<<<grid_for(c, c->cell_cap, 8), 256, 0, s>>>(skey, clink4, w.gcnt, &w.st->ngroup, G, c->cell_cap,
+                                                                w.st, w.groups);
     count_launch(c);
     // multipoles
     moments_k<<<gb, 128, 0, s>>>(n, w.pos, w.cbox, w.clink, w.cparent, w.carrive, w.cmom, c->cell_cap, w.moff, M,

@@ -507,12 +507,12 @@ __global__ void __launch_bounds__(128) mlp_pairs_k(MlpBlock P, CellGeo T, const 
             if (r < np) {
                 const int2 pr = pairs[r];
                 gg = pr.x;
-                const int4 grp = groups[pr.x];
-                const int m = member_of(T.moff, T.M, grp.x);
+                const GroupRec grp = load_group(groups, pr.x);
+                const int m = member_of(T.moff, T.M, grp.first);
                 float lo[3], unit;
                 member_geo(T, m, lo, unit);
                 float gcen[3], c0[3];
-                geo_centre(T.cbox[grp.z], lo, unit, gcen);
+                box_centre(grp.lo, grp.hi, lo, unit, gcen);
                 const int4 b = T.cbox[pr.y];
                 geo_centre(b, lo, unit, c0);
                 const float4 q = T.cmom[3 * pr.y], q0 = T.cmom[3 * pr.y + 1], q1 = T.cmom[3 * pr.y + 2];
@@ -552,7 +552,7 @@ __global__ void mlp_apply_k(const int4 *groups, const int *ngroup, const int *pe
                             float *ay, float *az) {
     const int ng = *ngroup;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
-        const int4 grp = groups[k];
+        const int4 grp = groups[2 * k];   // (first, count, ...)
         const float cx = gcorr[3 * k], cy = gcorr[3 * k + 1], cz = gcorr[3 * k + 2];
         for (int i = grp.x; i < grp.x + grp.y; i++) {
             const int o = perm[i];

@@ -69,7 +69,7 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.cparent = (int *)take(4 * cap);
     t.carrive = (int *)take(4 * cap);
     t.gcnt = (int *)take(4 * cap);
-    t.groups = (int4 *)take(16 * (n + 1));
+    t.groups = (int4 *)take(32 * (n + 1));   // every group holds a star
     t.partials = (int *)take(4 * nparts);
     t.pert_idx = (int *)take(4 * kPertTotal);
     t.pert_m = (double *)take(8 * kPertTotal);

@@ -61,8 +61,8 @@ struct Workspace {
     int *clink;           // [4 ncell] child first, child end, first star, end star
     float4 *cmom;         // [3 ncell]
     int *cparent, *carrive;
-    int *gcnt;            // groups started by each cell, scanned in place
-    int4 *groups;
+    int *gcnt;            // groups of each cell, scanned in place to each cell's first group
+    int4 *groups;         // 2 int4 per group: (first, count, lo x, lo y), (lo z, hi x, hi y, hi z)
     int *partials;        // scan block sums
     // perturbers and chain hand-off
     int *pert_idx;        // [kMaxPert]
@@ -205,6 +205,30 @@ __device__ __forceinline__ void geo_centre(const int4 b, const float lo[3], floa
     g[0] = __fadd_rn(lo[0], __fmul_rn(__fadd_rn((float)b.x, half), unit));
     g[1] = __fadd_rn(lo[1], __fmul_rn(__fadd_rn((float)b.y, half), unit));
     g[2] = __fadd_rn(lo[2], __fmul_rn(__fadd_rn((float)b.z, half), unit));
+}
+
+// Centre of the grid box [blo, bhi) in FP32: lo + (blo + bhi) * (unit / 2),
+// each operation rounded once (blo + bhi is exact in FP32 for boxes inside
+// the grid, unit / 2 is exact).
+__device__ __forceinline__ void box_centre(const int blo[3], const int bhi[3], const float lo[3], float unit,
+                                           float g[3]) {
+    const float hu = 0.5f * unit;
+#pragma unroll
+    for (int a = 0; a < 3; a++) g[a] = __fadd_rn(lo[a], __fmul_rn((float)(blo[a] + bhi[a]), hu));
+}
+
+// A walk group: stars [first, first + count) in key order and its box [lo, hi)
+// on the member's integer grid.
+struct GroupRec {
+    int first, count, lo[3], hi[3];
+};
+__device__ __forceinline__ GroupRec load_group(const int4 *groups, int g) {
+    const int4 a = groups[2 * g], b = groups[2 * g + 1];
+    GroupRec r;
+    r.first = a.x; r.count = a.y;
+    r.lo[0] = a.z; r.lo[1] = a.w; r.lo[2] = b.x;
+    r.hi[0] = b.y; r.hi[1] = b.z; r.hi[2] = b.w;
+    return r;
 }
 
 }  // namespace rv

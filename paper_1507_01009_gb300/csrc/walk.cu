@@ -562,24 +562,25 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             continue;
         }
         // ---- a group of the tree
-        int4 grp = __ldg(&A.groups[gi - A.n_extra]);
-        const int mg = member_of(A.moff, A.M, grp.x);
-        const TreeGeo G = tree_geo(A, mg);
-        if (grp.z < 0 || grp.z >= G.ncell || G.root < 0 || grp.x < 0 || grp.y < 1 || grp.y > 32 ||
-            grp.x + grp.y > A.n) {
+        const GroupRec grp = load_group(A.groups, gi - A.n_extra);
+        if (grp.first < 0 || grp.count < 1 || grp.count > 32 || grp.first + grp.count > A.n) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
         }
-        int4 b = __ldg(&A.cbox[grp.z]);
-        int side = 1 << (kMaxLevel - b.w);
-        int blo[3] = {b.x, b.y, b.z}, bhi[3] = {b.x + side, b.y + side, b.z + side};
+        const int mg = member_of(A.moff, A.M, grp.first);
+        const TreeGeo G = tree_geo(A, mg);
+        if (G.root < 0) {
+            if (lane == 0) latch_err(A.st, kErrStack);
+            continue;
+        }
+        const int *blo = grp.lo, *bhi = grp.hi;
         float g[3];
-        geo_centre(b, G.lo, G.unit, g);
-        const int s = grp.y, k = 32 / s;  // k lanes per star
+        box_centre(blo, bhi, G.lo, G.unit, g);
+        const int s = grp.count, k = 32 / s;  // k lanes per star
         Tgt tg;
         {
             const int t = lane % s, sub = lane / s;
-            const float4 pq = __ldg(&A.pos[grp.x + t]);
+            const float4 pq = __ldg(&A.pos[grp.first + t]);
             // minus the star's position relative to g (exact: FP32 negation)
             const float nx = -(pq.x - g[0]), ny = -(pq.y - g[1]), nz = -(pq.z - g[2]);
             tg.nx = f2_pack(nx, nx);
@@ -598,11 +599,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         nm2p += a3 * (unsigned long long)s;
         Acc tot = combine_shares(acc, s, k, scr);
         if (lane < s) {
-            const float4 p = __ldg(&A.pos[grp.x + lane]);
+            const float4 p = __ldg(&A.pos[grp.first + lane]);
             // the star's own pair was evaluated at r = 0: remove its -m/eps
             if (SOFT) tot.ph += p.w * rsqrtf(A.eps2);
             if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, mg, tot);
-            int o = A.perm[grp.x + lane];
+            int o = A.perm[grp.first + lane];
             A.ax[o] = tot.ax + tot.cx;
             A.ay[o] = tot.ay + tot.cy;
             A.az[o] = tot.az + tot.cz;

@@ -293,7 +293,7 @@ class Context:
             "clink": view(v.clink, nc, torch.int32, 4),
             "cmom": view(v.cmom, 3 * nc, torch.float32, 4).reshape(nc, 12),
             "cparent": view(v.cparent, nc, torch.int32),
-            "groups": view(v.groups, ng, torch.int32, 4),
+            "groups": view(v.groups, ng, torch.int32, 8),
             "bounds": view(v.bounds, 5, torch.float64),
         }
 

@@ -39,7 +39,8 @@ def gpu_cells_as_oracle(view):
 
 
 def sorted_groups(g):
-    g = np.asarray(g, dtype=np.int64)[:, :3]
+    """Groups [ngroup, 8] (first, count, box lo x/y/z, box hi x/y/z) ordered by first star."""
+    g = np.asarray(g, dtype=np.int64).reshape(-1, 8)
     return g[np.argsort(g[:, 0], kind="stable")]
 
 

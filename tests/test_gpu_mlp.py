@@ -157,15 +157,13 @@ def test_correction_applied_as_the_oracle_says(rvmod):
     params = _params_np(mlp)
     feats, norms = [], []
     for gid, c in pr:
-        gcell = groups[gid, 2]
-        glev = T.cells[gcell, 0]
-        go = T.cells[gcell, 6:9].astype(np.float64)
-        gside = 2.0 ** (21 - glev)
-        centre = T.lo + (go + 0.5 * gside) * (T.L / 2 ** 21)
+        glo = groups[gid, 2:5].astype(np.float64)
+        ghi = groups[gid, 5:8].astype(np.float64)
+        centre = T.lo + 0.5 * (glo + ghi) * (T.L / 2 ** 21)
         lev = T.cells[c, 0]
         side = 2 ** (21 - lev)
         o = T.cells[c, 6:9]
-        gap = np.maximum(0, np.maximum(o - (go + gside), go - (o + side)))
+        gap = np.maximum(0, np.maximum(o - ghi, glo - (o + side)))
         d2 = float((gap * gap).sum())
         assert float(side * side) < th2 * d2 and not (float(side * side) < tr2 * d2)   # in the band
         f, nm = oracle.cell_features(T, c, centre, eps)
@@ -176,7 +174,7 @@ def test_correction_applied_as_the_oracle_says(rvmod):
     np.add.at(corr, pr[:, 0], y * np.array(norms)[:, None])
     got = np.stack([ax.cpu().numpy() - plain[0], ay.cpu().numpy() - plain[1], az.cpu().numpy() - plain[2]])
     want = np.zeros((3, p32.shape[1]))
-    for gi, (first, cnt, _, _) in enumerate(groups):
+    for gi, (first, cnt, *_) in enumerate(groups):
         want[:, perm[first:first + cnt]] += corr[gi][:, None]
     scale = np.abs(want).max()
     assert np.abs(got - want).max() <= 2e-3 * scale + 1e-6 * np.abs(plain[0]).max()

@@ -154,8 +154,10 @@ def test_forces_vs_direct_plummer(rvmod):
 
 
 def test_small_theta_is_direct_sum(rvmod):
+    """At theta = 1e-7 no cell can pass the opening test (theta^2 d^2 < 1 for
+    every grid distance d < 2^21 sqrt 3), so the walk is the direct sum."""
     p32, m32 = _inputs("hernquist", 3000)
-    ctx = _ctx(rvmod, 3000, theta=1e-3, eps_star=0.005)
+    ctx = _ctx(rvmod, 3000, theta=1e-7, eps_star=0.005)
     gpu_tree(ctx, p32, m32)
     ax, ay, az, pot = ctx.tree_forces()
     a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)

@@ -228,18 +228,25 @@ def _check_tree_invariants(T, n_leaf, G):
                 o = cells[c, 6 + a]
                 assert np.all((q[a][sl] >= o) & (q[a][sl] < o + s))
     assert np.all(leaf_cover == 1)
-    # groups: consecutive runs of G (the last one shorter) partitioning the
-    # particles, each box the tightest one holding its particles' grid cells
+    # groups: each unit (a maximal cell with <= 16 G particles, or a leaf with
+    # more) cut into runs of G, the last one shorter; together they partition
+    # the particles; each box is the tightest one holding its particles' cells
+    U = 16 * G
+    unit = [c for c in range(T.ncell) if (cnt[c] <= U and (par[c] < 0 or cnt[par[c]] > U)) or
+            (nch[c] == 0 and cnt[c] > U)]
+    want = [(f, min(G, first[c] + cnt[c] - f)) for c in sorted(unit, key=lambda c: first[c])
+            for f in range(first[c], first[c] + cnt[c], G)]
     gs = T.groups
-    assert np.all(gs[:, 0] == np.arange(len(gs)) * G)
-    assert np.all(gs[:-1, 1] == G) and 1 <= gs[-1, 1] <= G and gs[-1, 0] + gs[-1, 1] == n
+    np.testing.assert_array_equal(gs[:, :2], np.array(want).reshape(-1, 2))
+    assert gs[:, 1].sum() == n
     if q is not None:
         for f, k, *box in gs:
             for a in range(3):
                 assert box[a] == q[a][f:f + k].min() and box[3 + a] == q[a][f:f + k].max() + 1
 
 
-@pytest.mark.parametrize("n,n_leaf,G", [(1, 16, 32), (2, 1, 1), (33, 16, 32), (1000, 8, 32), (3000, 16, 64)])
+@pytest.mark.parametrize("n,n_leaf,G", [(1, 16, 32), (2, 1, 1), (33, 16, 32), (1000, 8, 32), (3000, 16, 64),
+                                        (4000, 8, 4), (5000, 64, 2)])
 def test_tree_invariants(n, n_leaf, G):
     w = ics.hernquist(n, seed=n)
     T = oracle.Tree(w.pos.astype(np.float32), w.mass.astype(np.float32), n_leaf, G)
