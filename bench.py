@@ -334,7 +334,7 @@ def run_gpu(args):
     xs = [torch.from_numpy(np.ascontiguousarray(p32[a])).to(dev) for a in range(3)]
     ms = torch.from_numpy(d["mass"].astype(np.float32)).to(dev)
     tuned = autotune.autotune(*xs, ms, offsets=d["offsets"], theta=d["theta"], eps_star=float(np.float32(d["eps"])),
-                              grid=autotune.candidates(groups=(32,), leaves=(16, 32, 64), tiles=(64,)), reps=2)
+                              grid=autotune.candidates(groups=(32, 64), leaves=(16, 32), tiles=(64, 128)), reps=2)
     tune = tuned["config"]
     del xs, ms
     ctx = rv.Context(n, theta=d["theta"], eps_star=float(np.float32(d["eps"])), **tune)
@@ -467,7 +467,8 @@ def run_gpu(args):
                     "parallelism": f"replicas{ws}" if ws > 1 else "single",
                     "l2": "flushed (256 MiB write) before every timed step"})
         cfg["autotuned"] = {"cached": tuned["cached"], "candidates": len(tuned["table"]),
-                            "walk_ms_by_n_leaf": {str(r["n_leaf"]): round(r["walk_ms"], 3) for r in tuned["table"]}}
+                            "walk_ms_by_group_leaf_tile": {f'{r["group"]}/{r["n_leaf"]}/{r["tile"]}': round(r["walk_ms"], 3)
+                                                           for r in tuned["table"]}}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
@@ -513,7 +514,7 @@ def run_learned(args):
     m32 = w.mass.astype(np.float32)
     x, y, z = (torch.from_numpy(np.ascontiguousarray(p32[a])).cuda() for a in range(3))
     m = torch.from_numpy(m32).cuda()
-    ctx = rv.Context(n, theta=th, eps_star=eps, n_leaf=32)
+    ctx = rv.Context(n, theta=th, eps_star=eps, n_leaf=32, group=64)
     ctx.build_tree(x, y, z, m)
     xs, ts, _ = rv.mlp_samples(ctx, th, eps, 1 << 20, seed=7)
     net = rv.Mlp(seed=8)

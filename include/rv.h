@@ -56,7 +56,7 @@ typedef struct rv_ctx rv_ctx; /* opaque; owned by librv */
  *              group's box and the cell's box (0 <= theta < 2).
  *   eps_star   Plummer softening length of the stars (>= 0).
  *   n_leaf     a cell with more than n_leaf stars is split (1..64).
- *   group      stars per walk group, at most 32: runs of `group` consecutive
+ *   group      stars per walk group, at most 64 (two per warp lane): runs of `group` consecutive
  *              stars in key order, each walked with the tightest integer-grid
  *              box of its stars as the group's box.
  *   quadrupole 1: monopole + traceless quadrupole; 0: monopole only.

@@ -21,7 +21,7 @@ import threading
 
 from . import rv
 
-GRID_GROUP = (32, 16)
+GRID_GROUP = (64, 32, 16)
 GRID_LEAF = (8, 16, 32, 64)
 GRID_TILE = (32, 64, 128)
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")

@@ -562,12 +562,13 @@ __global__ void groups_write_k(const uint64_t *skey, const int4 *clink, const in
             const int first = lk.z + r * G;
             const int cnt = min(G, lk.w - first);
             unsigned qlo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, qhi[3] = {0u, 0u, 0u};
-            if (lane < cnt) {
-                const uint64_t key = skey[first + lane];
+            for (int i = lane; i < cnt; i += 32) {   // a run may hold up to 64 stars
+                const uint64_t key = skey[first + i];
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    qlo[a] = compact3(key >> a);
-                    qhi[a] = qlo[a] + 1;
+                    const unsigned q = compact3(key >> a);
+                    qlo[a] = min(qlo[a], q);
+                    qhi[a] = max(qhi[a], q + 1);
                 }
             }
 #pragma unroll

@@ -97,7 +97,7 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
 
 static bool config_ok(const rv_config *cfg) {
     return cfg && cfg->theta >= 0.f && cfg->theta < 2.f && cfg->eps_star >= 0.f && cfg->n_leaf >= 1 &&
-           cfg->n_leaf <= 64 && cfg->group >= 1 && cfg->group <= 32 && (cfg->quadrupole == 0 || cfg->quadrupole == 1) &&
+           cfg->n_leaf <= 64 && cfg->group >= 1 && cfg->group <= kMaxGroup && (cfg->quadrupole == 0 || cfg->quadrupole == 1) &&
            cfg->tile >= 32 && cfg->tile <= 256 && cfg->tile % 32 == 0;
 }
 

@@ -19,6 +19,7 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per tile
 constexpr int kTopoBlock = 256;
 constexpr int kScanChunk = 2048;        // elements per scan block
 constexpr int kWalkWarps = 4;           // warps per walk block
+constexpr int kMaxGroup = 64;           // stars per walk group (two per lane)
 constexpr int kStackCap = 768;          // walk traversal stack entries per warp
 constexpr int kMaxExtra = 8;            // extra particles through rv_tree_forces
 constexpr int kMaxMembers = 512;        // independent systems built and walked together (9-bit sort digit)

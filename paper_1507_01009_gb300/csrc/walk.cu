@@ -1,15 +1,16 @@
 // walk.cu -- Barnes-Hut tree walk and interaction evaluation (FP32).
 //
-// One warp walks the tree for one group of up to 32 consecutive stars. Cells
+// One warp walks the tree for one group of up to 64 consecutive stars. Cells
 // are tested 32 at a time, one per lane, under the box-box opening test;
 // accepted cells are staged in shared memory as multipole records, opened
 // leaves stage their stars, opened internal cells push their child range on
 // a per-warp stack. Whenever a staged list holds a full tile, the warp
-// evaluates it: each star of the group is served by k = floor(32 / s) lanes
-// (s = stars in the group), lane t + i s taking list pairs i, i + k, ...
-// with broadcast shared-memory reads; tile sums are added to running totals
-// with Neumaier compensation, and the k partial totals of a star are
-// combined in lane order at the end. Particles outside the tree (a chain's
+// evaluates it: a lane holds two stars of the group (a target pair), each of
+// the p = ceil(s / 2) pairs is served by k = floor(32 / p) lanes, lane t + i p
+// taking list pairs i, i + k, ... with broadcast shared-memory reads and
+// evaluating every loaded source pair on both its stars; tile sums are added
+// to running totals with Neumaier compensation, and the k partial totals of a
+// star are combined in lane order at the end. Particles outside the tree (a chain's
 // centre of mass) are walked by the same kernel as one-star groups before the
 // tree's own groups.
 //
@@ -33,10 +34,10 @@
 
 #include "rv_internal.cuh"
 
-// Unrolling of the evaluation loops (list pairs in flight per lane) and the
-// resident blocks per SM the walk kernel is compiled for (register budget:
-// 5 blocks of 128 threads leave 96 registers a thread, enough for two cell
-// pairs in flight without spills).
+// Unrolling of the evaluation loops (list pairs in flight per lane, each on
+// two targets) and the resident blocks per SM the walk kernel is compiled for
+// (register budget: 4 blocks of 128 threads leave 128 registers a thread,
+// enough for two targets' sums and two cell pairs in flight without spills).
 #ifndef RV_P2P_UNROLL
 #define RV_P2P_UNROLL 2
 #endif
@@ -44,7 +45,11 @@
 #define RV_M2P_UNROLL 2
 #endif
 #ifndef RV_WALK_MIN_BLOCKS
-#define RV_WALK_MIN_BLOCKS 5
+#define RV_WALK_MIN_BLOCKS 4
+#endif
+// 1: load a tested cell's box, links and multipole record together
+#ifndef RV_WALK_PREFETCH
+#define RV_WALK_PREFETCH 0
 #endif
 
 namespace rv {
@@ -157,11 +162,12 @@ __device__ __forceinline__ f2 f2_rsqrt(f2 v, bool guard_zero) {
 constexpr f2 kF2MinusHalf = 0xBF000000BF000000ull;     // (-0.5f, -0.5f)
 constexpr f2 kF2MinusFiveHalf = 0xC0200000C0200000ull; // (-2.5f, -2.5f)
 
-// A lane's target (minus its position relative to the group's centre, in both
-// halves) and its share of a staged list: pairs j0, j0 + k, ... (j0 >= 2^20:
-// the lane takes no share).
+// A lane's two targets (minus their positions relative to the group's
+// centre, each in both halves) and its share of a staged list: pairs j0,
+// j0 + k, ... (j0 >= 2^20: the lane takes no share). Both targets use every
+// source pair the lane loads.
 struct Tgt {
-    f2 nx, ny, nz;
+    f2 nx[2], ny[2], nz[2];
     int j0, k;
 };
 
@@ -172,71 +178,82 @@ __device__ __forceinline__ void add_tile(Acc &A, f2 tx, f2 ty, f2 tz, f2 tp) {
     nadd(A.ph, A.cp, -f2_sum(tp));
 }
 
-// Star pairs 0 .. npair-1 of a staged star list on this lane's target:
+// Star pairs 0 .. npair-1 of a staged star list on this lane's targets:
 //   d = x_j - x_i, a += m_j d / (d.d + e^2)^{3/2}, phi -= m_j / (d.d + e^2)^{1/2}.
 template <bool SOFT>
-__device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc &A) {
-    f2 tx = 0, ty = 0, tz = 0, tp = 0;   // tp sums +m/r
+__device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc *A) {
+    f2 tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0}, tp[2] = {0, 0};   // tp sums +m/r
 #pragma unroll kP2PUnroll
     for (int j = t.j0; j < npair; j += t.k) {
         const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(src)[2 * j];      // x, y
         const ulonglong2 b = reinterpret_cast<const ulonglong2 *>(src)[2 * j + 1];  // z, m
-        f2 dx = f2_add(a.x, t.nx), dy = f2_add(a.y, t.ny), dz = f2_add(b.x, t.nz);
-        f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
-        f2 rinv = f2_rsqrt(r2, !SOFT);
-        f2 mr = f2_mul(b.y, rinv);
-        f2 mr3 = f2_mul(mr, f2_mul(rinv, rinv));
-        tx = f2_fma(mr3, dx, tx);
-        ty = f2_fma(mr3, dy, ty);
-        tz = f2_fma(mr3, dz, tz);
-        tp = f2_add(tp, mr);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            f2 dx = f2_add(a.x, t.nx[q]), dy = f2_add(a.y, t.ny[q]), dz = f2_add(b.x, t.nz[q]);
+            f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
+            f2 rinv = f2_rsqrt(r2, !SOFT);
+            f2 mr = f2_mul(b.y, rinv);
+            f2 mr3 = f2_mul(mr, f2_mul(rinv, rinv));
+            tx[q] = f2_fma(mr3, dx, tx[q]);
+            ty[q] = f2_fma(mr3, dy, ty[q]);
+            tz[q] = f2_fma(mr3, dz, tz[q]);
+            tp[q] = f2_add(tp[q], mr);
+        }
     }
-    add_tile(A, tx, ty, tz, tp);
+    add_tile(A[0], tx[0], ty[0], tz[0], tp[0]);
+    add_tile(A[1], tx[1], ty[1], tz[1], tp[1]);
 }
 
-// Cell pairs 0 .. npair-1 of a staged cell list on this lane's target. With
+// Cell pairs 0 .. npair-1 of a staged cell list on this lane's targets. With
 // d = com - x_i = -r, rho^2 = d.d + e^2, the staged -Q gives q = -Q d = Q r
 // and s = d.q / rho^4 = -(r.Q.r) / rho^4, so that
 //   a += (M - 5/2 s) d / rho^3 + q / rho^5,  phi -= (M - s/2) / rho,
 // which is the monopole + quadrupole expansion of the file header.
 template <bool QUAD>
-__device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc &A) {
-    f2 tx = 0, ty = 0, tz = 0, tp = 0;   // tp sums +(M - s/2)/rho
+__device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc *A) {
+    f2 tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0}, tp[2] = {0, 0};   // tp sums +(M - s/2)/rho
 #pragma unroll kM2PUnroll
     for (int j = t.j0; j < npair; j += t.k) {
         const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(src) + kCellPairF4 * j;
         const ulonglong2 a = p[0];   // M, cx
         const ulonglong2 b = p[1];   // cy, cz
-        f2 dx = f2_add(a.y, t.nx), dy = f2_add(b.x, t.ny), dz = f2_add(b.y, t.nz);
-        f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
-        // r > 0: an accepted cell's box is separated from the group's box
-        f2 rinv = f2_rsqrt(r2, false);
-        f2 u = f2_mul(rinv, rinv);
-        f2 rinv3 = f2_mul(rinv, u);
+        ulonglong2 c = make_ulonglong2(0, 0), e = c, f = c;
         if (QUAD) {
-            const ulonglong2 c = p[2];   // -Qxx, -Qyy
-            const ulonglong2 e = p[3];   // -Qzz, -Qxy
-            const ulonglong2 f = p[4];   // -Qxz, -Qyz
-            f2 qx = f2_fma(c.x, dx, f2_fma(e.y, dy, f2_mul(f.x, dz)));
-            f2 qy = f2_fma(e.y, dx, f2_fma(c.y, dy, f2_mul(f.y, dz)));
-            f2 qz = f2_fma(f.x, dx, f2_fma(f.y, dy, f2_mul(e.x, dz)));
-            f2 dq = f2_fma(dx, qx, f2_fma(dy, qy, f2_mul(dz, qz)));
-            f2 sw = f2_mul(dq, f2_mul(u, u));
-            f2 rinv5 = f2_mul(rinv3, u);
-            f2 B = f2_mul(rinv3, f2_fma(kF2MinusFiveHalf, sw, a.x));
-            tx = f2_fma(B, dx, f2_fma(rinv5, qx, tx));
-            ty = f2_fma(B, dy, f2_fma(rinv5, qy, ty));
-            tz = f2_fma(B, dz, f2_fma(rinv5, qz, tz));
-            tp = f2_fma(rinv, f2_fma(kF2MinusHalf, sw, a.x), tp);
-        } else {
-            f2 mr3 = f2_mul(a.x, rinv3);
-            tx = f2_fma(mr3, dx, tx);
-            ty = f2_fma(mr3, dy, ty);
-            tz = f2_fma(mr3, dz, tz);
-            tp = f2_fma(a.x, rinv, tp);
+            c = p[2];   // -Qxx, -Qyy
+            e = p[3];   // -Qzz, -Qxy
+            f = p[4];   // -Qxz, -Qyz
+        }
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            f2 dx = f2_add(a.y, t.nx[q]), dy = f2_add(b.x, t.ny[q]), dz = f2_add(b.y, t.nz[q]);
+            f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
+            // r > 0: an accepted cell's box is separated from the group's box
+            f2 rinv = f2_rsqrt(r2, false);
+            f2 u = f2_mul(rinv, rinv);
+            f2 rinv3 = f2_mul(rinv, u);
+            if (QUAD) {
+                f2 qx = f2_fma(c.x, dx, f2_fma(e.y, dy, f2_mul(f.x, dz)));
+                f2 qy = f2_fma(e.y, dx, f2_fma(c.y, dy, f2_mul(f.y, dz)));
+                f2 qz = f2_fma(f.x, dx, f2_fma(f.y, dy, f2_mul(e.x, dz)));
+                f2 dq = f2_fma(dx, qx, f2_fma(dy, qy, f2_mul(dz, qz)));
+                f2 sw = f2_mul(dq, f2_mul(u, u));
+                f2 rinv5 = f2_mul(rinv3, u);
+                f2 B = f2_mul(rinv3, f2_fma(kF2MinusFiveHalf, sw, a.x));
+                tx[q] = f2_fma(B, dx, f2_fma(rinv5, qx, tx[q]));
+                ty[q] = f2_fma(B, dy, f2_fma(rinv5, qy, ty[q]));
+                tz[q] = f2_fma(B, dz, f2_fma(rinv5, qz, tz[q]));
+                tp[q] = f2_fma(rinv, f2_fma(kF2MinusHalf, sw, a.x), tp[q]);
+            } else {
+                f2 mr3 = f2_mul(a.x, rinv3);
+                tx[q] = f2_fma(mr3, dx, tx[q]);
+                ty[q] = f2_fma(mr3, dy, ty[q]);
+                tz[q] = f2_fma(mr3, dz, tz[q]);
+                tp[q] = f2_fma(a.x, rinv, tp[q]);
+            }
         }
     }
-    add_tile(A, tx, ty, tz, tp);
+    add_tile(A[0], tx[0], ty[0], tz[0], tp[0]);
+    add_tile(A[1], tx[1], ty[1], tz[1], tp[1]);
 }
 
 // Field f of staged entry e in a pair-interleaved list whose pairs are
@@ -276,7 +293,7 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 template <bool SOFT, bool QUAD, bool REC>
 __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
                                            const unsigned long long *thr_rec, int gid, char *wsm, const int blo[3],
-                                           const int bhi[3], const float g[3], const Tgt &tg, f2 eps2, Acc &acc,
+                                           const int bhi[3], const float g[3], const Tgt &tg, f2 eps2, Acc *acc,
                                            unsigned long long &np2p, unsigned long long &nm2p) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
@@ -322,8 +339,18 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         bool accept = false, leaf = false, open = false, band = false;
         int4 lk = make_int4(0, 0, 0, 0);
         int4 b = make_int4(0, 0, 0, 0);
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = r0, q2 = r0;
         if (c >= 0) {
             b = __ldg(&A.cbox[c]);
+#if RV_WALK_PREFETCH
+            // every record of the cell at once: one L2 round trip per pass
+            lk = __ldg(&A.clink[c]);
+            r0 = __ldg(&A.cmom[3 * c + 0]);
+            if (QUAD) {
+                q1 = __ldg(&A.cmom[3 * c + 1]);
+                q2 = __ldg(&A.cmom[3 * c + 2]);
+            }
+#endif
             int side = 1 << (kMaxLevel - b.w);
             long long gx = gap1(blo[0], bhi[0], b.x, b.x + side);
             long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
@@ -332,7 +359,9 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
             accept = d2 >= thr[b.w];
             if (REC) band = accept && d2 < thr_rec[b.w];
             if (!accept) {
+#if !RV_WALK_PREFETCH
                 lk = __ldg(&A.clink[c]);
+#endif
                 leaf = (lk.x == lk.y);
                 open = !leaf;
             }
@@ -354,16 +383,20 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         unsigned am = __ballot_sync(0xffffffffu, accept);
         if (accept) {
             int p = nm + __popc(am & lt);
-            float4 r0 = __ldg(&A.cmom[3 * c + 0]);
+#if !RV_WALK_PREFETCH
+            r0 = __ldg(&A.cmom[3 * c + 0]);
+            if (QUAD) {
+                q1 = __ldg(&A.cmom[3 * c + 1]);
+                q2 = __ldg(&A.cmom[3 * c + 2]);
+            }
+#endif
             float c0[3];
             geo_centre(b, G.lo, G.unit, c0);
             *staged(m2p, kCellPairF4, p, 0) = r0.x;
             *staged(m2p, kCellPairF4, p, 1) = (c0[0] - g[0]) + r0.y;
             *staged(m2p, kCellPairF4, p, 2) = (c0[1] - g[1]) + r0.z;
             *staged(m2p, kCellPairF4, p, 3) = (c0[2] - g[2]) + r0.w;
-            if (QUAD) {
-                float4 q1 = __ldg(&A.cmom[3 * c + 1]);   // Qxx, Qyy, Qzz, Qxy
-                float4 q2 = __ldg(&A.cmom[3 * c + 2]);   // Qxz, Qyz
+            if (QUAD) {   // q1 = (Qxx, Qyy, Qzz, Qxy), q2 = (Qxz, Qyz, 0, 0)
                 *staged(m2p, kCellPairF4, p, 4) = -q1.x;
                 *staged(m2p, kCellPairF4, p, 5) = -q1.y;
                 *staged(m2p, kCellPairF4, p, 6) = -q1.z;
@@ -446,26 +479,34 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
     return ok;
 }
 
-// Star t is served by lanes t, t + s, ..., t + (k - 1) s; their partial
-// totals are added into lane t in that order through the warp's (now free)
-// staging memory.
-__device__ __forceinline__ Acc combine_shares(const Acc &acc, int s, int k, float *scr) {
+// Lane l serves target pair t = l % p (stars 2t and 2t + 1) with share
+// l / p; the k lanes t, t + p, ..., t + (k - 1) p of a pair add their partial
+// totals in that order through the warp's (now free) staging memory. Returns
+// the totals of stars `lane` and `lane + 32`.
+__device__ __forceinline__ void combine_shares(const Acc *acc, int s, int p, int k, float *scr, Acc out[2]) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
-    float *d = scr + 8 * lane;
-    d[0] = acc.ax; d[1] = acc.ay; d[2] = acc.az; d[3] = acc.ph;
-    d[4] = acc.cx; d[5] = acc.cy; d[6] = acc.cz; d[7] = acc.cp;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        float *d = scr + 8 * (2 * lane + q);
+        d[0] = acc[q].ax; d[1] = acc[q].ay; d[2] = acc[q].az; d[3] = acc[q].ph;
+        d[4] = acc[q].cx; d[5] = acc[q].cy; d[6] = acc[q].cz; d[7] = acc[q].cp;
+    }
     __syncwarp();
-    Acc out = {};
-    if (lane < s)
-        for (int i = 0; i < k; i++) {
-            const float *e = scr + 8 * (lane + i * s);
-            nadd(out.ax, out.cx, e[0]); nadd(out.ay, out.cy, e[1]);
-            nadd(out.az, out.cz, e[2]); nadd(out.ph, out.cp, e[3]);
-            out.cx += e[4]; out.cy += e[5]; out.cz += e[6]; out.cp += e[7];
-        }
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int i = lane + 32 * h;   // star of the group
+        Acc o = {};
+        if (i < s)
+            for (int m = 0; m < k; m++) {
+                const float *e = scr + 8 * (2 * ((i >> 1) + m * p) + (i & 1));
+                nadd(o.ax, o.cx, e[0]); nadd(o.ay, o.cy, e[1]);
+                nadd(o.az, o.cz, e[2]); nadd(o.ph, o.cp, e[3]);
+                o.cx += e[4]; o.cy += e[5]; o.cz += e[6]; o.cp += e[7];
+            }
+        out[h] = o;
+    }
     __syncwarp();
-    return out;
 }
 
 // Direct terms of the extra particles of `member` on one target (pair
@@ -515,11 +556,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         if (lane == 0) gi = atomicAdd(&A.st->next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= nitem) break;
-        Acc acc = {};
+        Acc acc[2] = {};
         unsigned long long a2 = 0, a3 = 0;
         float *scr = reinterpret_cast<float *>(wsm + kStackCap * 4 + 32 * 4);  // m2p staging, free after a walk
         if (gi < A.n_extra) {
             // ---- a particle outside the tree: all 32 lanes share its interaction list
+            // (both target slots hold it; the second slot's sums are not used)
             const int kx = gi;
             const int mk = A.extra_per_member ? kx : (A.xmem ? A.xmem[kx] : 0);
             const TreeGeo G = tree_geo(A, mk);
@@ -538,9 +580,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             float g[3];
             geo_centre(make_int4(blo[0], blo[1], blo[2], kMaxLevel), G.lo, G.unit, g);
             Tgt tg;
-            tg.nx = f2_pack(g[0] - xi, g[0] - xi);
-            tg.ny = f2_pack(g[1] - yi, g[1] - yi);
-            tg.nz = f2_pack(g[2] - zi, g[2] - zi);
+            tg.nx[0] = tg.nx[1] = f2_pack(g[0] - xi, g[0] - xi);
+            tg.ny[0] = tg.ny[1] = f2_pack(g[1] - yi, g[1] - yi);
+            tg.nz[0] = tg.nz[1] = f2_pack(g[2] - zi, g[2] - zi);
             tg.j0 = lane;
             tg.k = 32;
             bool ok = true;
@@ -551,7 +593,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
                 if (lane == 0) latch_err(A.st, kErrStack);
                 continue;
             }
-            Acc tot = combine_shares(acc, 1, 32, scr);
+            Acc tots[2];
+            combine_shares(acc, 1, 1, 32, scr, tots);
+            Acc &tot = tots[0];
             if (lane == 0) {
                 extra_terms(A, xi, yi, zi, ek, kx, mk, tot);
                 A.xout[4 * kx] = tot.ax + tot.cx;
@@ -563,7 +607,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         }
         // ---- a group of the tree
         const GroupRec grp = load_group(A.groups, gi - A.n_extra);
-        if (grp.first < 0 || grp.count < 1 || grp.count > 32 || grp.first + grp.count > A.n) {
+        if (grp.first < 0 || grp.count < 1 || grp.count > kMaxGroup || grp.first + grp.count > A.n) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
         }
@@ -576,17 +620,22 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         const int *blo = grp.lo, *bhi = grp.hi;
         float g[3];
         box_centre(blo, bhi, G.lo, G.unit, g);
-        const int s = grp.count, k = 32 / s;  // k lanes per star
+        // p target pairs (stars 2t, 2t + 1), k lanes per pair
+        const int s = grp.count, p = (s + 1) >> 1, k = 32 / p;
         Tgt tg;
         {
-            const int t = lane % s, sub = lane / s;
-            const float4 pq = __ldg(&A.pos[grp.first + t]);
-            // minus the star's position relative to g (exact: FP32 negation)
-            const float nx = -(pq.x - g[0]), ny = -(pq.y - g[1]), nz = -(pq.z - g[2]);
-            tg.nx = f2_pack(nx, nx);
-            tg.ny = f2_pack(ny, ny);
-            tg.nz = f2_pack(nz, nz);
-            tg.j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k s take no list pairs
+            const int t = lane % p, sub = lane / p;
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                // an odd group's last pair repeats its star; those sums are not used
+                const float4 pq = __ldg(&A.pos[grp.first + min(2 * t + q, s - 1)]);
+                // minus the star's position relative to g (exact: FP32 negation)
+                const float nx = -(pq.x - g[0]), ny = -(pq.y - g[1]), nz = -(pq.z - g[2]);
+                tg.nx[q] = f2_pack(nx, nx);
+                tg.ny[q] = f2_pack(ny, ny);
+                tg.nz[q] = f2_pack(nz, nz);
+            }
+            tg.j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k p take no list pairs
             tg.k = k;
         }
         bool ok = walk_group<SOFT, QUAD, REC>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, tg,
@@ -597,13 +646,18 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         }
         np2p += a2 * (unsigned long long)s;
         nm2p += a3 * (unsigned long long)s;
-        Acc tot = combine_shares(acc, s, k, scr);
-        if (lane < s) {
-            const float4 p = __ldg(&A.pos[grp.first + lane]);
+        Acc tots[2];
+        combine_shares(acc, s, p, k, scr, tots);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int i = lane + 32 * h;
+            if (i >= s) continue;
+            Acc &tot = tots[h];
+            const float4 ps = __ldg(&A.pos[grp.first + i]);
             // the star's own pair was evaluated at r = 0: remove its -m/eps
-            if (SOFT) tot.ph += p.w * rsqrtf(A.eps2);
-            if (A.n_extra > 0) extra_terms(A, p.x, p.y, p.z, A.eps_star, -1, mg, tot);
-            int o = A.perm[grp.first + lane];
+            if (SOFT) tot.ph += ps.w * rsqrtf(A.eps2);
+            if (A.n_extra > 0) extra_terms(A, ps.x, ps.y, ps.z, A.eps_star, -1, mg, tot);
+            int o = A.perm[grp.first + i];
             A.ax[o] = tot.ax + tot.cx;
             A.ay[o] = tot.ay + tot.cy;
             A.az[o] = tot.az + tot.cz;

@@ -45,7 +45,7 @@ def test_config_and_workspace_size(lib):
     assert 0 < s1 < s2 < 2 * s1 + (1 << 20)
     bad = rv.default_config(tile=48)
     assert rv.workspace_size(1000, bad) == 0
-    bad = rv.default_config(group=33)
+    bad = rv.default_config(group=65)
     assert rv.workspace_size(1000, bad) == 0
 
 

@@ -17,7 +17,7 @@ def test_cache_key_and_grid():
     assert k1 == k2 and k1 != at.cache_key("GB300", 1 << 20, 64, 0.5, True)
     grid = at.candidates()
     assert len(grid) == len(at.GRID_GROUP) * len(at.GRID_LEAF) * len(at.GRID_TILE)
-    assert all(c["tile"] % 32 == 0 and c["group"] <= 32 for c in grid)
+    assert all(c["tile"] % 32 == 0 and c["group"] <= 64 for c in grid)
 
 
 def test_cache_roundtrip(tmp_path):

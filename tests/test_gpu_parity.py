@@ -54,7 +54,8 @@ TREE_CASES = [("hernquist", 1, 16, 32), ("hernquist", 2, 16, 32), ("hernquist", 
               ("hernquist", 33, 16, 32), ("hernquist", 1000, 8, 32), ("hernquist", 4097, 16, 32),
               ("hernquist", 65659, 16, 32), ("plummer", 4096, 16, 32), ("coincident", 100, 16, 32),
               ("two_clusters", 3000, 16, 32), ("ghosts", 5000, 16, 32), ("hernquist", 20000, 32, 32),
-              ("hernquist", 20000, 4, 8)]
+              ("hernquist", 20000, 4, 8), ("hernquist", 20000, 16, 64), ("hernquist", 4097, 8, 48),
+              ("coincident", 100, 16, 64)]
 
 
 @pytest.mark.parametrize("kind,n,n_leaf,G", TREE_CASES)
@@ -117,7 +118,9 @@ def test_moments(rvmod, kind, n):
 FORCE_CASES = [("plummer", 4096, 0.5, 0.01, 16, 32, 64, True), ("hernquist", 65659, 0.5, 0.005, 16, 32, 64, True),
                ("hernquist", 65659, 0.7, 0.005, 8, 16, 32, True), ("hernquist", 30000, 0.5, 0.005, 16, 32, 128, False),
                ("ghosts", 5000, 0.5, 0.005, 16, 32, 64, True), ("two_clusters", 3000, 0.6, 0.001, 4, 8, 64, True),
-               ("hernquist", 1000, 0.5, 0.0, 16, 32, 64, True)]
+               ("hernquist", 1000, 0.5, 0.0, 16, 32, 64, True), ("hernquist", 65659, 0.5, 0.005, 32, 64, 128, True),
+               ("plummer", 4096, 0.6, 0.01, 16, 64, 64, True), ("two_clusters", 3000, 0.5, 0.001, 8, 47, 32, True),
+               ("ghosts", 5000, 0.5, 0.005, 16, 64, 64, False)]
 
 
 @pytest.mark.parametrize("kind,n,theta,eps,n_leaf,G,tile,quad", FORCE_CASES)
@@ -274,12 +277,12 @@ def _system(rvmod, w, ctx_n, **kw):
     return rvmod.System(w.stars.pos, w.stars.vel, w.stars.mass, **kwargs, **kw)
 
 
-def _oracle_system_forces(w, p32, m32, theta, eps, sub=None, pert=None):
+def _oracle_system_forces(w, p32, m32, theta, eps, sub=None, pert=None, n_leaf=16, G=32):
     """Oracle forces of a star + chain system, following the same steps:
     tree over stars with the chain centre of mass as an unsoftened extra
     particle, then the resolved-chain corrections of the perturbers (Sect. 2)."""
     ch = w.chain
-    T = oracle.Tree(p32, m32, 16, 32)
+    T = oracle.Tree(p32, m32, n_leaf, G)
     com = ch.com
     M = ch.total_mass
     xp = com.astype(np.float32).reshape(3, 1)
@@ -375,14 +378,15 @@ def test_kdk_plummer_100_steps(rvmod):
 
 
 @pytest.mark.slow
-def test_full_size_hernquist_bh_sampled(rvmod):
-    """The 2^20-star Hernquist + SMBH workload in the benchmark's launch
-    configuration: sampled stars against the oracle tree (same theta) and the
-    FP64 direct sum over all 2^20 + 1 bodies."""
+@pytest.mark.parametrize("G,n_leaf,tile", [(32, 16, 64), (64, 32, 128), (64, 16, 128)])
+def test_full_size_hernquist_bh_sampled(rvmod, G, n_leaf, tile):
+    """The 2^20-star Hernquist + SMBH workload in the launch configurations the
+    benchmark's autotuner picks from: sampled stars against the oracle tree
+    (same theta and groups) and the FP64 direct sum over all 2^20 + 1 bodies."""
     w = ics.hernquist_bh_workload(1 << 20, seed=2)
     p32, m32 = stars32(w.stars.pos, w.stars.mass)
     eps = float(np.float32(w.eps_star))
-    ctx = _ctx(rvmod, p32.shape[1], theta=0.5, eps_star=eps)
+    ctx = _ctx(rvmod, p32.shape[1], theta=0.5, eps_star=eps, group=G, n_leaf=n_leaf, tile=tile)
     S = _system(rvmod, w, p32.shape[1], pert_mode=1, pert_radius=0.02)
     ctx.system_forces(S)
     ctx.sync_status()
@@ -390,7 +394,7 @@ def test_full_size_hernquist_bh_sampled(rvmod):
     tg = ics.subsample(p32.shape[1], 512, seed=9)
     com32 = w.chain.com.astype(np.float32)
     pert = oracle.radius(p32, com32, np.float32(np.float32(0.02) * np.float32(0.02)))
-    ao, _, _, _, o = _oracle_system_forces(w, p32, m32, 0.5, eps, sub=tg, pert=pert)
+    ao, _, _, _, o = _oracle_system_forces(w, p32, m32, 0.5, eps, sub=tg, pert=pert, n_leaf=n_leaf, G=G)
     ao[:, pert] += o["a_pert"].T
     med, _, mx = err_stats(a[:, tg], ao[:, tg])
     assert med <= MED_TOL and mx <= MAX_TOL
