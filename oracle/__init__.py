@@ -70,6 +70,8 @@ def _declare(L):
     L.orc_tree_groups.argtypes = [C.c_void_p, _i64]
     L.orc_tree_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32,
                                   _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64, C.c_int64, _i64]
+    L.orc_tree_forces_rel.argtypes = [C.c_void_p, C.c_float, C.c_double, C.c_int32, _f, _d, _d, _d, _d, _i64,
+                                      C.c_int64, _i64]
     L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d, _d]
     L.orc_knn.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_int64, _i64]
     L.orc_knn.restype = C.c_int64
@@ -216,6 +218,26 @@ class Tree:
                               -1 if targets is None else len(targets),
                               None if targets is None else _p(_c(targets, np.int64), _i64))
         res = (np.stack(out[:3]), out[3], np.stack(xout[:3])[:, :k], xout[3][:k])
+        return res + (cnt,) if counts else res
+
+
+    def forces_rel(self, alpha: float, eps_star: float, aref, quadrupole: bool = True, counts: bool = False,
+                   targets=None):
+        """Tree acceleration/potential (caller order, FP64) under the relative
+        opening criterion (Sect. 3's "Gadget" criterion, Gadget-2 reading):
+        a cell of mass M and side s at box distance d is used when
+        M s^2 <= alpha |a| d^4, |a| the smallest ``aref`` (FP32 reference
+        acceleration magnitudes, caller order) of the group, and the group
+        lies outside the cell's box grown by s/10 per side. Returns
+        (acc (3,n), pot (n,)[, counts (n,2)])."""
+        aref = _c(np.asarray(aref, dtype=np.float32), np.float32)
+        out = [np.zeros(self.n) for _ in range(4)]
+        cnt = np.zeros((self.n, 2), dtype=np.int64) if counts else None
+        lib().orc_tree_forces_rel(self._h, float(np.float32(alpha)), float(eps_star), int(quadrupole), _p(aref, _f),
+                                  *[_p(o, _d) for o in out], _p(cnt, _i64) if counts else None,
+                                  -1 if targets is None else len(targets),
+                                  None if targets is None else _p(_c(targets, np.int64), _i64))
+        res = (np.stack(out[:3]), out[3])
         return res + (cnt,) if counts else res
 
 

@@ -454,11 +454,47 @@ typedef struct {
     int64_t self; /* sorted slot of the target, or -1 */
     nsum ax, ay, az, ph;
     int64_t n_p2p, n_m2p;
+    int rel;      /* 1: relative criterion with constant K below */
+    float K;
 } walk_state;
+
+/* Relative opening criterion (Sect. 3: the runs use a "Gadget" criterion with
+ * an error tolerance; reading: the relative criterion of the Gadget-2 code).
+ * A cell of mass M and side s at distance d is used as a multipole for a
+ * target whose reference acceleration has magnitude |a| when
+ *     M s^2 <= alpha |a| d^4        (G = 1),
+ * and only when the target lies outside the cell's box grown by a tenth of its
+ * side on every side (a safeguard against a massive cell close to the target).
+ * For a group: |a| is the smallest reference magnitude among its stars, d the
+ * box-box distance, and the safeguard asks the group's box to lie outside the
+ * grown box. The decision is taken in FP32, one rounding per operation, as the
+ * CUDA walk takes it: with u the grid unit rounded to FP32,
+ * K = (alpha * amin) * (u * u) per group and d2 = d^2 in grid units rounded
+ * once to FP32, accept iff M32 * s^2 <= (K * d2) * d2 (M32 = M rounded to
+ * FP32). */
+static int mac_accept_rel(const orc_tree *t, const int64_t blo[3], const int64_t bhi[3], int64_t c, float K) {
+    int64_t s = (int64_t)1 << (ORC_MAXLEVEL - t->level[c]);
+    const int64_t o[3] = {t->ox[c], t->oy[c], t->oz[c]};
+    int outside = 0;
+    for (int a = 0; a < 3; a++)
+        if (10 * bhi[a] <= 10 * o[a] - s || 10 * blo[a] >= 10 * (o[a] + s) + s) outside = 1;
+    if (!outside) return 0;
+    int64_t d2 = 0;
+    for (int a = 0; a < 3; a++) {
+        int64_t g = gap1(blo[a], bhi[a], o[a], o[a] + s);
+        d2 += g * g;
+    }
+    float d2f = (float)d2;
+    float m32 = (float)t->cm[c];
+    float s2 = (float)((double)s * (double)s);
+    float lhs = m32 * s2;
+    float rhs = (K * d2f) * d2f;
+    return lhs <= rhs;
+}
 
 static void walk_cell(walk_state *w, int64_t c) {
     const orc_tree *t = w->t;
-    if (mac_accept(t, w->blo, w->bhi, c, w->theta2)) {
+    if (w->rel ? mac_accept_rel(t, w->blo, w->bhi, c, w->K) : mac_accept(t, w->blo, w->bhi, c, w->theta2)) {
         m2p(t, c, w->px, w->py, w->pz, w->e, w->quad, &w->ax, &w->ay, &w->az, &w->ph);
         w->n_m2p++;
         return;
@@ -536,6 +572,45 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
         }
         xax[k] = nval(&w.ax); xay[k] = nval(&w.ay); xaz[k] = nval(&w.az); xpot[k] = nval(&w.ph);
     }
+}
+
+/* Tree forces on every tree particle (caller order) under the relative
+ * criterion above: alpha the tolerance, aref[i] the reference acceleration
+ * magnitude of particle i (caller order, FP32). counts / nsub / sub as in
+ * orc_tree_forces. */
+void orc_tree_forces_rel(const orc_tree *t, float alpha, double eps_star, int32_t quad, const float *aref,
+                         double *ax, double *ay, double *az, double *pot, int64_t *counts,
+                         int64_t nsub, const int64_t *sub) {
+    char *want = NULL;
+    if (nsub >= 0) {
+        want = (char *)calloc((size_t)(t->n > 0 ? t->n : 1), 1);
+        for (int64_t s = 0; s < nsub; s++) want[sub[s]] = 1;
+    }
+    const float u = (float)(t->L / ORC_GRID);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t g = 0; g < t->ngroup; g++) {
+        int64_t blo[3], bhi[3];
+        for (int a = 0; a < 3; a++) { blo[a] = t->glo[3 * g + a]; bhi[a] = t->ghi[3 * g + a]; }
+        float amin = 0.0f;
+        for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
+            float v = aref[t->perm[i]];
+            if (i == t->gfirst[g] || v < amin) amin = v;
+        }
+        const float K = (alpha * amin) * (u * u);
+        for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
+            if (want && !want[t->perm[i]]) continue;
+            walk_state w;
+            memset(&w, 0, sizeof w);
+            w.t = t; w.quad = quad; w.e = eps_star; w.self = i; w.rel = 1; w.K = K;
+            memcpy(w.blo, blo, sizeof blo); memcpy(w.bhi, bhi, sizeof bhi);
+            w.px = t->x[i]; w.py = t->y[i]; w.pz = t->z[i];
+            if (t->ncell > 0) walk_cell(&w, 0);
+            int64_t o = t->perm[i];
+            ax[o] = nval(&w.ax); ay[o] = nval(&w.ay); az[o] = nval(&w.az); pot[o] = nval(&w.ph);
+            if (counts) { counts[2 * o] = w.n_p2p; counts[2 * o + 1] = w.n_m2p; }
+        }
+    }
+    free(want);
 }
 
 /* ------------------------------------------------------------------ */

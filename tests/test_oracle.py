@@ -341,6 +341,78 @@ def test_walk_accuracy_ordering(plummer_case):
         assert p99[(th, True)] < p99[(th, False)]
 
 
+def test_relative_mac_zero_tolerance_is_direct(plummer_case):
+    """alpha = 0: no massive cell passes M s^2 <= 0, so the walk is the direct sum."""
+    p32, m32, ad, pd = plummer_case
+    T = oracle.Tree(p32, m32, 16, 32)
+    aref = np.linalg.norm(ad, axis=0).astype(np.float32)
+    a, p, cnt = T.forces_rel(0.0, 0.01, aref, counts=True)
+    assert cnt[:, 1].sum() == 0
+    assert oracle.rel_err(a, ad).max() < 1e-12
+    np.testing.assert_allclose(p, pd, rtol=1e-12)
+
+
+def test_relative_mac_error_follows_tolerance(plummer_case):
+    """The error grows with the tolerance alpha and stays below it (the
+    criterion bounds the monopole truncation term by alpha |a|; the quadrupole
+    term makes the actual error smaller), and fewer interactions are needed."""
+    p32, m32, ad, _ = plummer_case
+    T = oracle.Tree(p32, m32, 16, 32)
+    aref = np.linalg.norm(ad, axis=0).astype(np.float32)
+    p99, work = {}, {}
+    for al in (1e-4, 1e-3, 1e-2):
+        a, _, cnt = T.forces_rel(al, 0.01, aref, counts=True)
+        p99[al] = oracle.percentile(oracle.rel_err(a, ad), 0.99)
+        work[al] = cnt.sum()
+        assert p99[al] < al
+    assert p99[1e-4] < p99[1e-3] < p99[1e-2]
+    assert work[1e-4] > work[1e-3] > work[1e-2]
+
+
+def test_relative_mac_scale_invariance(plummer_case):
+    """The criterion is dimensionally consistent: M s^2 <= alpha |a| d^4 is
+    unchanged when masses and |a| are scaled by c, and when lengths are doubled
+    (|a| / 4, softening x 2): same opening decisions, forces scaled exactly."""
+    p32, m32, ad, _ = plummer_case
+    aref = np.linalg.norm(ad, axis=0).astype(np.float32)
+    T = oracle.Tree(p32, m32, 16, 32)
+    a0, _, c0 = T.forces_rel(1e-3, 0.01, aref, counts=True)
+    T2 = oracle.Tree(p32, (m32 * np.float32(8.0)).astype(np.float32), 16, 32)
+    a2, _, c2 = T2.forces_rel(1e-3, 0.01, (aref * np.float32(8.0)).astype(np.float32), counts=True)
+    np.testing.assert_array_equal(c2, c0)
+    np.testing.assert_allclose(a2, 8.0 * a0, rtol=1e-12)
+    T3 = oracle.Tree((p32 * np.float32(2.0)).astype(np.float32), m32, 16, 32)
+    a3, _, c3 = T3.forces_rel(1e-3, 0.02, (aref / np.float32(4.0)).astype(np.float32), counts=True)
+    np.testing.assert_array_equal(c3, c0)
+    np.testing.assert_allclose(a3, a0 / 4.0, rtol=1e-12)
+
+
+def test_relative_mac_safeguard():
+    """A cluster of 1000 stars inside the cell [0.5, 0.625)^3 (side s = 1/8)
+    and a group of 8 stars at distance delta beside its +x face. With a huge
+    tolerance every separated cell passes M s^2 <= alpha |a| d^4, so only the
+    safeguard decides: within s/10 = 0.0125 the group must open the cluster's
+    cell (more, smaller multipoles); beyond it the cell is one multipole, as
+    far away; touching the face, leaves are opened down to single stars."""
+    g = ics.rng(31)
+    A = g.uniform(0.51, 0.615, (3, 1000))
+    corners = np.array([[0.0, 1.0], [0.0, 1.0], [0.0, 1.0]])   # bounding cube [0, 1]^3
+    cnt = {}
+    for delta in (0.0003, 0.011, 0.014, 0.1):
+        B = np.array([0.625 + delta, 0.56, 0.56])[:, None] + g.uniform(-1e-4, 1e-4, (3, 8))
+        pos = np.concatenate([A, B, corners], 1).astype(np.float32)
+        m = np.full(pos.shape[1], 1.0 / pos.shape[1], dtype=np.float32)
+        T = oracle.Tree(pos, m, 16, 8)
+        assert T.L == 1.0
+        _, _, c = T.forces_rel(1e30, 0.001, np.ones(pos.shape[1], np.float32), counts=True)
+        cnt[delta] = c[1000:1008]
+    far = cnt[0.1]
+    np.testing.assert_array_equal(cnt[0.014], far)            # beyond s/10: as far away
+    assert np.all(cnt[0.011][:, 1] > far[:, 1] + 6)           # within s/10: the cell is opened
+    assert np.all(far[:, 0] == 7)                             # only the group's own stars directly
+    assert np.all(cnt[0.0003][:, 0] > 7)                      # touching: leaves of the cluster opened
+
+
 def test_walk_extra_particles_match_direct(plummer_case):
     """An unsoftened centre-of-mass particle outside the tree: at small theta
     the stars' forces and its own equal the direct sum with eps = 0 pairs."""
