@@ -12,9 +12,11 @@ build (bounds, keys, sort, topology, multipoles, groups), tree walk, FP64
 perturber coupling and chain hand-off, kick, FP64 energy/momentum totals.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload hernquist_bh|hernquist_binary|plummer|ensemble]
+                  [--workload hernquist_bh|hernquist_bh_relmac|hernquist_binary|plummer|ensemble|learned]
 
-Other workloads: `hernquist_binary` (2^22 stars, central SMBH pair, 256
+Other workloads: `hernquist_bh_relmac` (the default workload with the
+relative opening criterion the paper's runs use, tolerance 1e-3, the previous
+step's accelerations as references), `hernquist_binary` (2^22 stars, central SMBH pair, 256
 nearest perturbers), `plummer` (4096 stars), `ensemble` (64 independent
 Hernquist realisations, sizes log-uniform in 8192..524288, each with a
 central SMBH pair, all members in one build and one walk per step, the step
@@ -58,7 +60,7 @@ def _dist():
 def make_workload(name: str, rank: int = 0) -> dict:
     import ics
     base = 1000 * rank
-    if name == "hernquist_bh":
+    if name in ("hernquist_bh", "hernquist_bh_relmac"):
         w = ics.hernquist_bh_workload(1 << 20, seed=2 + base)
         d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=w.chain.mass,
                  chain_x=w.chain.pos, chain_v=w.chain.vel, pert_mode=1, pert_radius=0.02, pert_k=0)
@@ -89,7 +91,12 @@ def make_workload(name: str, rank: int = 0) -> dict:
     d["dt"] = 1e-3
     d["name"] = name
     d["n"] = int(d["mass"].shape[0])
+    # the paper's runs open cells by a relative ("Gadget") criterion with tolerance 1e-3 (Sect. 3)
+    d["mac"], d["alpha"] = (1, 1e-3) if name.endswith("_relmac") else (0, 1e-3)
     cfg.update({"eps_star": d["eps"], "theta": 0.5, "quadrupole": True, "dt": 1e-3})
+    if d["mac"] == 1:
+        cfg.update({"workload": cfg["workload"] + "_relative_mac", "mac": "relative (M s^2 <= alpha |a| d^4)",
+                    "alpha": d["alpha"], "theta_for_first_pass_and_smbh": 0.5})
     d["config"] = cfg
     return d
 
@@ -184,6 +191,12 @@ def oracle_step_time(d, sample=65536, seed=0, max_stars=1 << 20):
         T = oracle.Tree(p32[:, s:e], m32[s:e], 16, 32)
         t1 = time.perf_counter()
         tg = ics.subsample(e - s, per, seed=seed + k)
+        rel = None
+        if d.get("mac") == 1:
+            # references for the relative criterion: the Hernquist field -x / (r (r + 1)^2) (G = M = a = 1)
+            x = p32[:, s:e].astype(np.float64)
+            r = np.maximum(np.linalg.norm(x, axis=0), 1e-12)
+            rel = (d["alpha"], (-x / (r * (r + 1.0) ** 2)).astype(np.float32))
         if d["chain_m"] is not None:
             nch = len(d["chain_m"]) // len(ranges)
             mi = ranges.index((s, e))
@@ -191,9 +204,9 @@ def oracle_step_time(d, sample=65536, seed=0, max_stars=1 << 20):
             cx = d["chain_x"][mi * nch:(mi + 1) * nch]
             com = (cm[:, None] * cx).sum(0) / cm.sum()
             T.forces(d["theta"], float(np.float32(d["eps"])), True, com.astype(np.float32).reshape(3, 1),
-                     np.array([float(np.float32(cm.sum()))]), [0.0], targets=tg)
+                     np.array([float(np.float32(cm.sum()))]), [0.0], targets=tg, rel=rel)
         else:
-            T.forces(d["theta"], float(np.float32(d["eps"])), True, targets=tg)
+            T.forces(d["theta"], float(np.float32(d["eps"])), True, targets=tg, rel=rel)
         t2 = time.perf_counter()
         t_build += t1 - t0
         t_walk += t2 - t1
@@ -337,7 +350,8 @@ def run_gpu(args):
                               grid=autotune.candidates(groups=(32, 64), leaves=(16, 32), tiles=(64, 128)), reps=2)
     tune = tuned["config"]
     del xs, ms
-    ctx = rv.Context(n, theta=d["theta"], eps_star=float(np.float32(d["eps"])), **tune)
+    ctx = rv.Context(n, theta=d["theta"], eps_star=float(np.float32(d["eps"])), mac=d["mac"], alpha=d["alpha"],
+                     **tune)
     S = rv.System(d["pos"], d["vel"], d["mass"], chain_m=d["chain_m"], chain_x=d["chain_x"], chain_v=d["chain_v"],
                   pert_mode=d["pert_mode"], pert_radius=d["pert_radius"], pert_k=d["pert_k"],
                   member_offsets=d["offsets"])
@@ -597,8 +611,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="hernquist_bh", choices=["hernquist_bh", "hernquist_binary", "plummer",
-                                                                   "ensemble", "learned"])
+    ap.add_argument("--workload", default="hernquist_bh",
+                    choices=["hernquist_bh", "hernquist_bh_relmac", "hernquist_binary", "plummer", "ensemble", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -60,7 +60,14 @@ typedef struct rv_ctx rv_ctx; /* opaque; owned by librv */
  *              stars in key order, each walked with the tightest integer-grid
  *              box of its stars as the group's box.
  *   quadrupole 1: monopole + traceless quadrupole; 0: monopole only.
- *   tile       interaction-list tile, a multiple of 32 in [32, 256]. */
+ *   tile       interaction-list tile, a multiple of 32 in [32, 256].
+ *   mac        opening criterion of rv_system_forces / rv_kdk_step(_graph):
+ *              0 = opening angle theta; 1 = the relative criterion of
+ *              rv_tree_forces_rel with tolerance `alpha`, the system's current
+ *              accelerations (the previous pass's) as references; groups
+ *              without a reference yet (|a| = 0) and the chain's
+ *              centre-of-mass particles use theta.
+ *   alpha      tolerance of the relative criterion (>= 0). */
 typedef struct {
     float theta;
     float eps_star;
@@ -68,10 +75,12 @@ typedef struct {
     int32_t group;
     int32_t quadrupole;
     int32_t tile;
+    int32_t mac;
+    float alpha;
 } rv_config;
 
 /* Fills *cfg with the defaults: theta 0.5, eps 0.01, n_leaf 16, group 32,
- * quadrupole 1, tile 64. */
+ * quadrupole 1, tile 64, mac 0, alpha 1e-3. */
 void rv_default_config(rv_config *cfg);
 
 /* Bytes of device workspace a context needs for up to n_max stars (0 if the
@@ -123,6 +132,25 @@ rv_status rv_build_tree_members(rv_ctx *ctx, int32_t n_members, const int64_t *o
 rv_status rv_tree_forces(rv_ctx *ctx, float theta, float eps_star, int32_t n_extra,
                          const float *extra_xyzm, const float *extra_eps, float *ax, float *ay,
                          float *az, float *pot, float *extra_out, void *stream);
+
+/* Tree forces on all stars of the last build (members included) under the
+ * relative opening criterion the paper's runs use (Sect. 3: a "Gadget"
+ * criterion with an error tolerance; read as the Gadget-2 relative
+ * criterion). A cell of mass M and side s is used as a multipole for a walk
+ * group when
+ *   M s^2 <= alpha |a| d^4   and the group's box lies outside the cell's box
+ *                            grown by s/10 on every side,
+ * d the box-box distance and |a| the smallest reference magnitude among the
+ * group's stars: ref_ax, ref_ay, ref_az (device FP32 [n], caller order) hold
+ * reference accelerations, normally the previous step's, and |a| =
+ * sqrt((x x + y y) + z z). Every test runs in FP32 with one rounding per
+ * operation: K = (alpha |a|min) (u u), u the grid unit, accept iff
+ * M s^2 <= (K d^2) d^2 with d^2 in grid units. alpha = 0 gives the direct
+ * sum. Outputs as rv_tree_forces (no extra particles); the reference arrays
+ * may be the output arrays themselves (each group reads its own stars'
+ * references before it writes their forces). */
+rv_status rv_tree_forces_rel(rv_ctx *ctx, float alpha, float eps_star, const float *ref_ax, const float *ref_ay,
+                             const float *ref_az, float *ax, float *ay, float *az, float *pot, void *stream);
 
 /* rv_tree_forces after rv_build_tree_members: each star feels only its own
  * member's tree and the extra particles of its member; extra k belongs to

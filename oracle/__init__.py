@@ -69,9 +69,8 @@ def _declare(L):
     L.orc_tree_moments.argtypes = [C.c_void_p, _d]
     L.orc_tree_groups.argtypes = [C.c_void_p, _i64]
     L.orc_tree_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32,
-                                  _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64, C.c_int64, _i64]
-    L.orc_tree_forces_rel.argtypes = [C.c_void_p, C.c_float, C.c_double, C.c_int32, _f, _d, _d, _d, _d, _i64,
-                                      C.c_int64, _i64]
+                                  _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64, C.c_int64, _i64,
+                                  C.c_float, _f, _f, _f]
     L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d, _d]
     L.orc_knn.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_int64, _i64]
     L.orc_knn.restype = C.c_int64
@@ -189,7 +188,7 @@ class Tree:
             self._h = None
 
     def forces(self, theta: float, eps_star: float, quadrupole: bool = True,
-               extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False, targets=None):
+               extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False, targets=None, rel=None):
         """Tree acceleration/potential on every star (caller order), FP64.
 
         Walk under the box-box opening-angle test at ``theta``; ``extra_*``
@@ -198,7 +197,9 @@ class Tree:
         tree through their own walk. Returns (acc (3,n), pot (n,), xacc (3,k),
         xpot (k,)[, counts (n,2) = P2P, M2P interactions]). With ``targets``
         (caller indices) only those stars are computed; the rest of the
-        returned arrays is zero."""
+        returned arrays is zero. With ``rel = (alpha, aref)`` the stars' groups
+        use the relative opening criterion (see ``forces_rel``); groups whose
+        smallest reference |a| is 0 and the extra particles use theta."""
         k = 0 if extra_mass is None else int(np.asarray(extra_mass).shape[0])
         ex = np.zeros((3, max(k, 1)), dtype=np.float32)
         xm = np.zeros(max(k, 1))
@@ -208,6 +209,7 @@ class Tree:
             xm[:k] = np.asarray(extra_mass, dtype=np.float64)
             xe[:k] = np.asarray(extra_eps, dtype=np.float64)
         exx, exy, exz = (_c(ex[a], np.float32) for a in range(3))
+        ar = [_c(np.asarray(rel[1][a], dtype=np.float32), np.float32) for a in range(3)] if rel is not None else None
         out = [np.zeros(self.n) for _ in range(4)]
         xout = [np.zeros(max(k, 1)) for _ in range(4)]
         cnt = np.zeros((self.n, 2), dtype=np.int64) if counts else None
@@ -216,29 +218,25 @@ class Tree:
                               *[_p(o, _d) for o in out], *[_p(o, _d) for o in xout],
                               _p(cnt, _i64) if counts else None,
                               -1 if targets is None else len(targets),
-                              None if targets is None else _p(_c(targets, np.int64), _i64))
+                              None if targets is None else _p(_c(targets, np.int64), _i64),
+                              float(np.float32(rel[0])) if rel is not None else 0.0,
+                              *([_p(v, _f) for v in ar] if rel is not None else [None, None, None]))
         res = (np.stack(out[:3]), out[3], np.stack(xout[:3])[:, :k], xout[3][:k])
         return res + (cnt,) if counts else res
 
 
     def forces_rel(self, alpha: float, eps_star: float, aref, quadrupole: bool = True, counts: bool = False,
-                   targets=None):
+                   targets=None, theta: float = 0.5):
         """Tree acceleration/potential (caller order, FP64) under the relative
         opening criterion (Sect. 3's "Gadget" criterion, Gadget-2 reading):
         a cell of mass M and side s at box distance d is used when
-        M s^2 <= alpha |a| d^4, |a| the smallest ``aref`` (FP32 reference
-        acceleration magnitudes, caller order) of the group, and the group
-        lies outside the cell's box grown by s/10 per side. Returns
-        (acc (3,n), pot (n,)[, counts (n,2)])."""
-        aref = _c(np.asarray(aref, dtype=np.float32), np.float32)
-        out = [np.zeros(self.n) for _ in range(4)]
-        cnt = np.zeros((self.n, 2), dtype=np.int64) if counts else None
-        lib().orc_tree_forces_rel(self._h, float(np.float32(alpha)), float(eps_star), int(quadrupole), _p(aref, _f),
-                                  *[_p(o, _d) for o in out], _p(cnt, _i64) if counts else None,
-                                  -1 if targets is None else len(targets),
-                                  None if targets is None else _p(_c(targets, np.int64), _i64))
-        res = (np.stack(out[:3]), out[3])
-        return res + (cnt,) if counts else res
+        M s^2 <= alpha |a| d^4, |a| the smallest reference magnitude of the
+        group (``aref``: FP32 reference accelerations (3, n), caller order;
+        magnitudes taken in FP32), and the group lies outside the cell's box
+        grown by s/10 per side; a group whose smallest |a| is 0 uses theta.
+        Returns (acc (3,n), pot (n,)[, counts (n,2)])."""
+        r = self.forces(theta, eps_star, quadrupole, counts=counts, targets=targets, rel=(alpha, aref))
+        return (r[0], r[1], r[4]) if counts else (r[0], r[1])
 
 
 # ---------------------------------------------------------------------------

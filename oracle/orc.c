@@ -492,6 +492,15 @@ static int mac_accept_rel(const orc_tree *t, const int64_t blo[3], const int64_t
     return lhs <= rhs;
 }
 
+/* Reference magnitude |a| of a reference acceleration (FP32 components), in
+ * FP32 with one rounding per operation: sqrt((x x + y y) + z z). */
+static float ref_mag(float x, float y, float z) {
+    float s = x * x;
+    s = s + y * y;
+    s = s + z * z;
+    return sqrtf(s);
+}
+
 static void walk_cell(walk_state *w, int64_t c) {
     const orc_tree *t = w->t;
     if (w->rel ? mac_accept_rel(t, w->blo, w->bhi, c, w->K) : mac_accept(t, w->blo, w->bhi, c, w->theta2)) {
@@ -518,14 +527,19 @@ static void walk_cell(walk_state *w, int64_t c) {
  * the grid cell [q, q+1)^3 of its position (q unclamped, limited to
  * +-2^23). counts (optional, [n][2]) receives the P2P and M2P interaction
  * counts per tree particle. With nsub >= 0 only the stars whose caller
- * indices are listed in sub[0..nsub) are computed (others untouched). */
+ * indices are listed in sub[0..nsub) are computed (others untouched).
+ * With rx != NULL the stars' groups use the relative criterion above with
+ * tolerance alpha and reference accelerations (rx, ry, rz)[i] (caller order,
+ * FP32); the extra particles always use the opening angle. */
 void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t quad,
                      int32_t nx, const float *xx, const float *xy, const float *xz, const double *xm,
                      const double *xeps,
                      double *ax, double *ay, double *az, double *pot,
                      double *xax, double *xay, double *xaz, double *xpot, int64_t *counts,
-                     int64_t nsub, const int64_t *sub) {
+                     int64_t nsub, const int64_t *sub,
+                     float alpha, const float *rx, const float *ry, const float *rz) {
     double theta2 = theta * theta;
+    const float u = (float)(t->L / ORC_GRID);
     /* optional subset: only sorted slots whose caller index is flagged */
     char *want = NULL;
     if (nsub >= 0) {
@@ -536,11 +550,24 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
     for (int64_t g = 0; g < t->ngroup; g++) {
         int64_t blo[3], bhi[3];
         for (int a = 0; a < 3; a++) { blo[a] = t->glo[3 * g + a]; bhi[a] = t->ghi[3 * g + a]; }
+        /* relative criterion: K of the group; a group without a reference
+         * (smallest |a| = 0, e.g. before any force pass) uses the opening angle */
+        int rel = 0;
+        float K = 0.0f;
+        if (rx) {
+            float amin = 0.0f;
+            for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
+                const int64_t j = t->perm[i];
+                float v = ref_mag(rx[j], ry[j], rz[j]);
+                if (i == t->gfirst[g] || v < amin) amin = v;
+            }
+            if (amin > 0.0f) { rel = 1; K = (alpha * amin) * (u * u); }
+        }
         for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
             if (want && !want[t->perm[i]]) continue;
             walk_state w;
             memset(&w, 0, sizeof w);
-            w.t = t; w.theta2 = theta2; w.quad = quad; w.e = eps_star; w.self = i;
+            w.t = t; w.theta2 = theta2; w.quad = quad; w.e = eps_star; w.self = i; w.rel = rel; w.K = K;
             memcpy(w.blo, blo, sizeof blo); memcpy(w.bhi, bhi, sizeof bhi);
             w.px = t->x[i]; w.py = t->y[i]; w.pz = t->z[i];
             if (t->ncell > 0) walk_cell(&w, 0);
@@ -572,45 +599,6 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
         }
         xax[k] = nval(&w.ax); xay[k] = nval(&w.ay); xaz[k] = nval(&w.az); xpot[k] = nval(&w.ph);
     }
-}
-
-/* Tree forces on every tree particle (caller order) under the relative
- * criterion above: alpha the tolerance, aref[i] the reference acceleration
- * magnitude of particle i (caller order, FP32). counts / nsub / sub as in
- * orc_tree_forces. */
-void orc_tree_forces_rel(const orc_tree *t, float alpha, double eps_star, int32_t quad, const float *aref,
-                         double *ax, double *ay, double *az, double *pot, int64_t *counts,
-                         int64_t nsub, const int64_t *sub) {
-    char *want = NULL;
-    if (nsub >= 0) {
-        want = (char *)calloc((size_t)(t->n > 0 ? t->n : 1), 1);
-        for (int64_t s = 0; s < nsub; s++) want[sub[s]] = 1;
-    }
-    const float u = (float)(t->L / ORC_GRID);
-#pragma omp parallel for schedule(dynamic, 4)
-    for (int64_t g = 0; g < t->ngroup; g++) {
-        int64_t blo[3], bhi[3];
-        for (int a = 0; a < 3; a++) { blo[a] = t->glo[3 * g + a]; bhi[a] = t->ghi[3 * g + a]; }
-        float amin = 0.0f;
-        for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
-            float v = aref[t->perm[i]];
-            if (i == t->gfirst[g] || v < amin) amin = v;
-        }
-        const float K = (alpha * amin) * (u * u);
-        for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
-            if (want && !want[t->perm[i]]) continue;
-            walk_state w;
-            memset(&w, 0, sizeof w);
-            w.t = t; w.quad = quad; w.e = eps_star; w.self = i; w.rel = 1; w.K = K;
-            memcpy(w.blo, blo, sizeof blo); memcpy(w.bhi, bhi, sizeof bhi);
-            w.px = t->x[i]; w.py = t->y[i]; w.pz = t->z[i];
-            if (t->ncell > 0) walk_cell(&w, 0);
-            int64_t o = t->perm[i];
-            ax[o] = nval(&w.ax); ay[o] = nval(&w.ay); az[o] = nval(&w.az); pot[o] = nval(&w.ph);
-            if (counts) { counts[2 * o] = w.n_p2p; counts[2 * o + 1] = w.n_m2p; }
-        }
-    }
-    free(want);
 }
 
 /* ------------------------------------------------------------------ */

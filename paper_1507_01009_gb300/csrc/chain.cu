@@ -405,8 +405,12 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s) {
         cudaMemsetAsync(w.npert, 0, sizeof(int) * M, s);
     }
     if ((r = build_tree(c, M, off, sys->x, sys->y, sys->z, sys->m, s)) != RV_OK) return r;
+    // relative criterion (cfg.mac = 1): the accelerations in the system arrays (the previous
+    // pass's, zero before the first one) are the references, read before they are overwritten
+    const RelMac rel{c->cfg.alpha, sys->ax, sys->ay, sys->az};
     if ((r = tree_walk(c, c->cfg.theta, c->cfg.eps_star, chain ? M : 0, w.extra_xyzm, w.extra_eps, nullptr, true,
-                       sys->ax, sys->ay, sys->az, sys->pot, w.extra_out, s)) != RV_OK)
+                       sys->ax, sys->ay, sys->az, sys->pot, w.extra_out, s, nullptr,
+                       c->cfg.mac == 1 ? &rel : nullptr)) != RV_OK)
         return r;
     if (chain) {
         gather_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, sys->x, sys->y, sys->z,

@@ -98,7 +98,8 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
 static bool config_ok(const rv_config *cfg) {
     return cfg && cfg->theta >= 0.f && cfg->theta < 2.f && cfg->eps_star >= 0.f && cfg->n_leaf >= 1 &&
            cfg->n_leaf <= 64 && cfg->group >= 1 && cfg->group <= kMaxGroup && (cfg->quadrupole == 0 || cfg->quadrupole == 1) &&
-           cfg->tile >= 32 && cfg->tile <= 256 && cfg->tile % 32 == 0;
+           cfg->tile >= 32 && cfg->tile <= 256 && cfg->tile % 32 == 0 && (cfg->mac == 0 || cfg->mac == 1) &&
+           cfg->alpha >= 0.f && cfg->alpha < 3e38f;
 }
 
 static bool ready(rv_ctx *c) { return c && c->ws; }
@@ -117,6 +118,8 @@ void rv_default_config(rv_config *cfg) {
     cfg->group = 32;
     cfg->quadrupole = 1;
     cfg->tile = 64;
+    cfg->mac = 0;
+    cfg->alpha = 1e-3f;
 }
 
 size_t rv_workspace_size(int64_t n_max, const rv_config *cfg) {
@@ -238,6 +241,19 @@ rv_status rv_tree_forces(rv_ctx *c, float theta, float eps_star, int32_t n_extra
     if (c->n > 0 && (!ax || !ay || !az || !pot)) return set_err(c, RV_E_INVAL, "null output array");
     return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, nullptr, false, ax, ay, az, pot, extra_out,
                      (cudaStream_t)stream);
+}
+
+rv_status rv_tree_forces_rel(rv_ctx *c, float alpha, float eps_star, const float *ref_ax, const float *ref_ay,
+                             const float *ref_az, float *ax, float *ay, float *az, float *pot, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces_rel before rv_build_tree");
+    if (!(alpha >= 0.f) || !(alpha < 3e38f) || !(eps_star >= 0.f)) return set_err(c, RV_E_INVAL, "bad alpha/eps");
+    if (c->n > 0 && (!ax || !ay || !az || !pot || !ref_ax || !ref_ay || !ref_az))
+        return set_err(c, RV_E_INVAL, "null array");
+    RelMac rel{alpha, ref_ax, ref_ay, ref_az};
+    return tree_walk(c, 0.f, eps_star, 0, nullptr, nullptr, nullptr, false, ax, ay, az, pot, nullptr,
+                     (cudaStream_t)stream, nullptr, &rel);
 }
 
 rv_status rv_tree_forces_members(rv_ctx *c, float theta, float eps_star, int32_t n_extra, const float *extra_xyzm,

@@ -146,11 +146,18 @@ struct PairRecord {
     int cap;
 };
 
+// Relative opening criterion of a walk (see walk.cu): tolerance alpha and the
+// stars' reference accelerations (device FP32 [n] each, caller order).
+struct RelMac {
+    float alpha;
+    const float *rx, *ry, *rz;
+};
+
 // extra particles: xmem[k] = member of extra k (device), or nullptr when
 // extra k belongs to member k (one chain per member) -- see walk.cu.
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
-                    float *xout, cudaStream_t s, const PairRecord *rec = nullptr);
+                    float *xout, cudaStream_t s, const PairRecord *rec = nullptr, const RelMac *rel = nullptr);
 
 // chain.cu
 rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,

@@ -85,6 +85,9 @@ struct WalkArgs {
     int2 *pairs;
     int *npairs;
     int pair_cap;
+    // relative opening criterion: tolerance and reference acceleration per star (caller order)
+    float rel_alpha;
+    const float *arx, *ary, *arz;
 };
 
 // Per-warp shared memory: stack | lane_cell[32] | cell staging | star staging.
@@ -290,11 +293,11 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 // mass are (cell centre - g) + (centre of mass - cell centre). Differences of
 // nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
 // any distance from the origin.
-template <bool SOFT, bool QUAD, bool REC>
+template <bool SOFT, bool QUAD, bool REC, bool REL>
 __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
                                            const unsigned long long *thr_rec, int gid, char *wsm, const int blo[3],
                                            const int bhi[3], const float g[3], const Tgt &tg, f2 eps2, Acc *acc,
-                                           unsigned long long &np2p, unsigned long long &nm2p) {
+                                           unsigned long long &np2p, unsigned long long &nm2p, float K) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
     int *stack = reinterpret_cast<int *>(wsm);
@@ -342,7 +345,9 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = r0, q2 = r0;
         if (c >= 0) {
             b = __ldg(&A.cbox[c]);
-#if RV_WALK_PREFETCH
+#if !RV_WALK_PREFETCH
+            if (REL) r0 = __ldg(&A.cmom[3 * c + 0]);   // the relative test needs the cell's mass
+#else
             // every record of the cell at once: one L2 round trip per pass
             lk = __ldg(&A.clink[c]);
             r0 = __ldg(&A.cmom[3 * c + 0]);
@@ -356,7 +361,20 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
             long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
             long long gz = gap1(blo[2], bhi[2], b.z, b.z + side);
             unsigned long long d2 = (unsigned long long)(gx * gx + gy * gy + gz * gz);
-            accept = d2 >= thr[b.w];
+            if (REL && K >= 0.f) {
+                // relative criterion: the group's box outside the cell's box grown by
+                // side/10 per side (integers x 10), and M s^2 <= (K d^2) d^2 in FP32
+                const int bo[3] = {b.x, b.y, b.z};
+                bool outside = false;
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    outside |= (10 * bhi[a] <= 10 * bo[a] - side) || (10 * blo[a] >= 10 * (bo[a] + side) + side);
+                const float d2f = __ull2float_rn(d2);
+                const float s2 = __fmul_rn((float)side, (float)side);
+                accept = outside && (__fmul_rn(r0.x, s2) <= __fmul_rn(__fmul_rn(K, d2f), d2f));
+            } else {
+                accept = d2 >= thr[b.w];
+            }
             if (REC) band = accept && d2 < thr_rec[b.w];
             if (!accept) {
 #if !RV_WALK_PREFETCH
@@ -384,7 +402,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         if (accept) {
             int p = nm + __popc(am & lt);
 #if !RV_WALK_PREFETCH
-            r0 = __ldg(&A.cmom[3 * c + 0]);
+            if (!REL) r0 = __ldg(&A.cmom[3 * c + 0]);
             if (QUAD) {
                 q1 = __ldg(&A.cmom[3 * c + 1]);
                 q2 = __ldg(&A.cmom[3 * c + 2]);
@@ -537,7 +555,7 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
 // Work items 0 .. n_extra-1 are the extra particles (one-star groups whose box
 // is their own grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited
 // to +-2^23); the tree's groups follow.
-template <bool SOFT, bool QUAD, bool REC>
+template <bool SOFT, bool QUAD, bool REC, bool REL>
 __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree_k(WalkArgs A) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -587,8 +605,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             tg.k = 32;
             bool ok = true;
             if (G.ncell > 0 && G.root >= 0)
-                ok = walk_group<false, QUAD, false>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, tg,
-                                                    f2_pack(e * e, e * e), acc, a2, a3);
+                ok = walk_group<false, QUAD, false, false>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, tg,
+                                                           f2_pack(e * e, e * e), acc, a2, a3, -1.f);
             if (!ok) {
                 if (lane == 0) latch_err(A.st, kErrStack);
                 continue;
@@ -638,8 +656,22 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             tg.j0 = (sub < k) ? sub : (1 << 20);  // lanes beyond k p take no list pairs
             tg.k = k;
         }
-        bool ok = walk_group<SOFT, QUAD, REC>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, tg,
-                                              f2_pack(A.eps2, A.eps2), acc, a2, a3);
+        // relative criterion: K = (alpha |a|min) u^2 of the group, as in the oracle;
+        // a group without a reference (|a|min = 0, no force pass yet) walks at theta (K < 0)
+        float K = -1.f;
+        if (REL) {
+            float am = __int_as_float(0x7f800000);
+            for (int i = lane; i < s; i += 32) {
+                // |a| = sqrt((x x + y y) + z z) in FP32, one rounding per operation, as the oracle takes it
+                const int j = A.perm[grp.first + i];
+                const float x = A.arx[j], y = A.ary[j], z = A.arz[j];
+                am = fminf(am, sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z))));
+            }
+            for (int o = 16; o > 0; o >>= 1) am = fminf(am, __shfl_xor_sync(0xffffffffu, am, o));
+            if (am > 0.f) K = __fmul_rn(__fmul_rn(A.rel_alpha, am), __fmul_rn(G.unit, G.unit));
+        }
+        bool ok = walk_group<SOFT, QUAD, REC, REL>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, tg,
+                                                   f2_pack(A.eps2, A.eps2), acc, a2, a3, K);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
@@ -690,10 +722,10 @@ MacTable mac_table(float theta) {
     return t;
 }
 
-template <bool SOFT, bool QUAD, bool REC>
+template <bool SOFT, bool QUAD, bool REC, bool REL = false>
 static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
     size_t smem = warp_smem_bytes(A.tile) * kWalkWarps;
-    auto kern = walk_tree_k<SOFT, QUAD, REC>;
+    auto kern = walk_tree_k<SOFT, QUAD, REC, REL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -707,7 +739,7 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
 
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
-                    float *xout, cudaStream_t s, const PairRecord *rec) {
+                    float *xout, cudaStream_t s, const PairRecord *rec, const RelMac *rel) {
     Workspace &w = c->w;
     WalkArgs A;
     A.pos = w.pos;
@@ -738,6 +770,11 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.npairs = rec ? rec->npairs : nullptr;
     A.pair_cap = rec ? rec->cap : 0;
     if (rec) A.rec = mac_table(rec->theta_rec);
+    A.rel_alpha = rel ? rel->alpha : 0.f;
+    A.arx = rel ? rel->rx : nullptr;
+    A.ary = rel ? rel->ry : nullptr;
+    A.arz = rel ? rel->rz : nullptr;
+    if (rel && rec) return set_err(c, RV_E_INVAL, "no pair record under the relative criterion");
     // reset the work counter and statistics (next_group, n_p2p, n_m2p)
     cudaError_t e = cudaMemsetAsync(&w.st->next_group, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&w.st->n_p2p, 0, 2 * sizeof(unsigned long long), s);
@@ -767,7 +804,12 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
         }
     }
     if (ev0) cudaEventRecord(ev0, s);
-    if (rec) {
+    if (rel) {
+        if (eps_star > 0.f)
+            e = quad ? launch_walk<true, true, false, true>(c, A, s) : launch_walk<true, false, false, true>(c, A, s);
+        else
+            e = quad ? launch_walk<false, true, false, true>(c, A, s) : launch_walk<false, false, false, true>(c, A, s);
+    } else if (rec) {
         if (!(eps_star > 0.f) || !quad) return set_err(c, RV_E_INVAL, "pair record needs softening and quadrupoles");
         e = launch_walk<true, true, true>(c, A, s);
     } else if (eps_star > 0.f) {

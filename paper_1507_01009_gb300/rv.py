@@ -23,7 +23,8 @@ RV_OK, RV_E_INVAL, RV_E_CUDA, RV_E_WORKSPACE, RV_E_STACK, RV_E_TIMEOUT, RV_E_NOT
 STATUS_NAMES = ["RV_OK", "RV_E_INVAL", "RV_E_CUDA", "RV_E_WORKSPACE", "RV_E_STACK", "RV_E_TIMEOUT", "RV_E_NOTBUILT",
                 "RV_E_TOO_LARGE"]
 EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", "rv_set_workspace", "rv_build_tree",
-           "rv_build_tree_members", "rv_tree_forces", "rv_tree_forces_members", "rv_perturber_forces",
+           "rv_build_tree_members", "rv_tree_forces", "rv_tree_forces_rel", "rv_tree_forces_members",
+           "rv_perturber_forces",
            "rv_system_forces", "rv_kdk_step", "rv_kdk_step_graph", "rv_energy",
            "rv_select_perturbers", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
            "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
@@ -40,7 +41,7 @@ class RvError(RuntimeError):
 
 class rv_config(C.Structure):
     _fields_ = [("theta", C.c_float), ("eps_star", C.c_float), ("n_leaf", C.c_int32), ("group", C.c_int32),
-                ("quadrupole", C.c_int32), ("tile", C.c_int32)]
+                ("quadrupole", C.c_int32), ("tile", C.c_int32), ("mac", C.c_int32), ("alpha", C.c_float)]
 
 
 class rv_tree_view(C.Structure):
@@ -91,6 +92,7 @@ def _declare(L):
     L.rv_build_tree.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.rv_build_tree_members.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
     L.rv_tree_forces.argtypes = [vp, f32, f32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rv_tree_forces_rel.argtypes = [vp, f32, f32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rv_tree_forces_members.argtypes = [vp, f32, f32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rv_kdk_step_graph.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp, vp]
     L.rv_perturber_forces.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -180,11 +182,11 @@ class Context:
     """An rv_ctx with a torch-allocated workspace on the current device."""
 
     def __init__(self, n_max: int, theta: float = 0.5, eps_star: float = 0.01, n_leaf: int = 16,
-                 group: int = 32, quadrupole: bool = True, tile: int = 64):
+                 group: int = 32, quadrupole: bool = True, tile: int = 64, mac: int = 0, alpha: float = 1e-3):
         import torch
         self.L = load()
         self.cfg = default_config(theta=theta, eps_star=eps_star, n_leaf=n_leaf, group=group,
-                                  quadrupole=int(bool(quadrupole)), tile=tile)
+                                  quadrupole=int(bool(quadrupole)), tile=tile, mac=int(mac), alpha=float(alpha))
         self.n_max = int(n_max)
         h = C.c_void_p()
         st = self.L.rv_create(C.byref(h), self.n_max, C.byref(self.cfg))
@@ -268,6 +270,20 @@ class Context:
         self._check(self.L.rv_tree_forces(self.h, float(theta), float(eps_star), k, _ptr(extra_xyzm),
                                           _ptr(extra_eps), *[_ptr(o) for o in out], _ptr(xout), _stream(stream)))
         return tuple(out) + ((xout[:k],) if k else ())
+
+    def tree_forces_rel(self, alpha, ref, eps_star=None, out=None, stream=None):
+        """Tree forces under the relative opening criterion with tolerance
+        alpha and reference accelerations ref = (ax, ay, az) (CUDA FP32 [n]
+        each, caller order; may be the output tensors themselves).
+        Returns (ax, ay, az, pot)."""
+        import torch
+        eps_star = self.cfg.eps_star if eps_star is None else eps_star
+        if out is None:
+            out = [torch.empty(self.n, dtype=torch.float32, device="cuda") for _ in range(4)]
+        _need_cuda(*out, *ref)
+        self._check(self.L.rv_tree_forces_rel(self.h, float(alpha), float(eps_star), *[_ptr(r) for r in ref],
+                                              *[_ptr(o) for o in out], _stream(stream)))
+        return tuple(out)
 
     def tree_view(self, stream=None) -> dict:
         """Copies of the last tree's arrays (as CUDA tensors)."""

@@ -47,6 +47,9 @@ def test_config_and_workspace_size(lib):
     assert rv.workspace_size(1000, bad) == 0
     bad = rv.default_config(group=65)
     assert rv.workspace_size(1000, bad) == 0
+    assert (cfg.mac, abs(cfg.alpha - 1e-3) < 1e-9) == (0, True)
+    assert rv.workspace_size(1000, rv.default_config(mac=2)) == 0
+    assert rv.workspace_size(1000, rv.default_config(mac=1, alpha=-1.0)) == 0
 
 
 def test_create_rejects_bad_arguments(lib):

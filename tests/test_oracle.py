@@ -345,7 +345,7 @@ def test_relative_mac_zero_tolerance_is_direct(plummer_case):
     """alpha = 0: no massive cell passes M s^2 <= 0, so the walk is the direct sum."""
     p32, m32, ad, pd = plummer_case
     T = oracle.Tree(p32, m32, 16, 32)
-    aref = np.linalg.norm(ad, axis=0).astype(np.float32)
+    aref = ad.astype(np.float32)
     a, p, cnt = T.forces_rel(0.0, 0.01, aref, counts=True)
     assert cnt[:, 1].sum() == 0
     assert oracle.rel_err(a, ad).max() < 1e-12
@@ -358,7 +358,7 @@ def test_relative_mac_error_follows_tolerance(plummer_case):
     term makes the actual error smaller), and fewer interactions are needed."""
     p32, m32, ad, _ = plummer_case
     T = oracle.Tree(p32, m32, 16, 32)
-    aref = np.linalg.norm(ad, axis=0).astype(np.float32)
+    aref = ad.astype(np.float32)
     p99, work = {}, {}
     for al in (1e-4, 1e-3, 1e-2):
         a, _, cnt = T.forces_rel(al, 0.01, aref, counts=True)
@@ -374,7 +374,7 @@ def test_relative_mac_scale_invariance(plummer_case):
     unchanged when masses and |a| are scaled by c, and when lengths are doubled
     (|a| / 4, softening x 2): same opening decisions, forces scaled exactly."""
     p32, m32, ad, _ = plummer_case
-    aref = np.linalg.norm(ad, axis=0).astype(np.float32)
+    aref = ad.astype(np.float32)
     T = oracle.Tree(p32, m32, 16, 32)
     a0, _, c0 = T.forces_rel(1e-3, 0.01, aref, counts=True)
     T2 = oracle.Tree(p32, (m32 * np.float32(8.0)).astype(np.float32), 16, 32)
@@ -385,6 +385,19 @@ def test_relative_mac_scale_invariance(plummer_case):
     a3, _, c3 = T3.forces_rel(1e-3, 0.02, (aref / np.float32(4.0)).astype(np.float32), counts=True)
     np.testing.assert_array_equal(c3, c0)
     np.testing.assert_allclose(a3, a0 / 4.0, rtol=1e-12)
+
+
+def test_relative_mac_without_reference_uses_theta(plummer_case):
+    """Groups whose smallest reference |a| is 0 (before any force pass) fall
+    back to the opening-angle test: all-zero references reproduce the walk at
+    theta exactly."""
+    p32, m32, _, _ = plummer_case
+    T = oracle.Tree(p32, m32, 16, 32)
+    a0, p0, _, _, c0 = T.forces(0.6, 0.01, True, counts=True)
+    a1, p1, c1 = T.forces_rel(1e-3, 0.01, np.zeros((3, p32.shape[1]), np.float32), counts=True, theta=0.6)
+    np.testing.assert_array_equal(c1, c0)
+    np.testing.assert_array_equal(a1, a0)
+    np.testing.assert_array_equal(p1, p0)
 
 
 def test_relative_mac_safeguard():
@@ -404,7 +417,7 @@ def test_relative_mac_safeguard():
         m = np.full(pos.shape[1], 1.0 / pos.shape[1], dtype=np.float32)
         T = oracle.Tree(pos, m, 16, 8)
         assert T.L == 1.0
-        _, _, c = T.forces_rel(1e30, 0.001, np.ones(pos.shape[1], np.float32), counts=True)
+        _, _, c = T.forces_rel(1e30, 0.001, np.ones((3, pos.shape[1]), np.float32), counts=True)
         cnt[delta] = c[1000:1008]
     far = cnt[0.1]
     np.testing.assert_array_equal(cnt[0.014], far)            # beyond s/10: as far away
