@@ -191,8 +191,10 @@ rv_status rv_perturber_forces(rv_ctx *ctx, int32_t n_ch, const double *chain_m, 
  * 2048 chain members in total). Perturbers of a chain (stars of its own
  * member): pert_mode 1 = FP32 squared distance to the chain centre below
  * pert_radius^2 (ascending index), 2 = the pert_k nearest (ties by lower
- * index); at most min(5000, 65536 / n_members) per member (overflow of a
- * radius search is reported by rv_sync_status as RV_E_WORKSPACE). */
+ * index), 3 = the tidal criterion of Eq. 2 with r_crit = pert_radius and
+ * gamma_crit = pert_gamma (see rv_select_perturbers_tidal); at most
+ * min(5000, 65536 / n_members) per member (overflow of a radius or tidal
+ * search is reported by rv_sync_status as RV_E_WORKSPACE). */
 typedef struct {
     int64_t n;
     float *x, *y, *z, *vx, *vy, *vz;
@@ -205,6 +207,7 @@ typedef struct {
     int32_t pert_k;
     int32_t n_members;
     const int64_t *member_offsets;
+    float pert_gamma;
 } rv_system;
 
 /* One full force evaluation of a system: tree build, perturber selection,
@@ -232,6 +235,21 @@ rv_status rv_kdk_step(rv_ctx *ctx, rv_system *sys, double dt, int32_t nsteps, vo
 rv_status rv_kdk_step_graph(rv_ctx *ctx, rv_system *sys, double dt, int32_t nsteps, double *energy_out,
                             void *stream);
 
+/* Perturber pull on the chain members for the chain integrator's own force
+ * evaluations (Sect. 2: inside its substeps the chain integrator needs the
+ * perturbers' forces many times, with the perturbers' positions predicted to
+ * first order). Uses the perturber sets of the last rv_system_forces on this
+ * system and the stars' current positions and velocities:
+ *   x_p(dt) = x_p + v_p dt   (FP64, one rounding per operation),
+ *   a_k = sum_p m_p (x_p(dt) - x_k) / |x_p(dt) - x_k|^3,  pot_k = -sum_p m_p / |..|
+ * (unsoftened FP64, a fixed summation order) for the chain members at
+ * chain_x (device FP64, member-major [3 n_members n_chain], the same frame as
+ * the stars). Writes device a_chain[3 n_members n_chain] and, if not NULL,
+ * pot_chain[n_members n_chain]. RV_E_NOTBUILT before a force pass of the
+ * system. */
+rv_status rv_chain_perturber_forces(rv_ctx *ctx, const rv_system *sys, double dt, const double *chain_x,
+                                    double *a_chain, double *pot_chain, void *stream);
+
 /* FP64 totals of each member of a system, written to device out[10 k ..] for
  * member k: E_kin, E_pot, E_tot, P (3), L (3), M. Stars: sum m v^2/2,
  * sum m phi/2, sum m v, sum m x cross v; chain members added in FP64 with
@@ -245,6 +263,19 @@ rv_status rv_energy(rv_ctx *ctx, const rv_system *sys, double *out, void *stream
 rv_status rv_select_perturbers(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
                                const float centre[3], int32_t mode, float radius, int32_t k, int32_t cap,
                                int32_t *idx, int32_t *count, void *stream);
+
+/* Tidal perturber search (Eq. 2): star j (device FP32 x, y, z, m [n]) perturbs
+ * a chain of total mass m_chain centred at `centre` (host FP32) when
+ *   r_j < (2 m_j / (gamma_crit m_chain))^(1/3) r_crit.
+ * Decided without a cube root, in FP64 with one rounding per operation on the
+ * FP32 squared distance d2 (as in the radius search):
+ *   (d2 d2) d2 < (q q) rc6,  q = (2 m_j) / (gamma_crit m_chain),
+ *   rc6 = (rc2 rc2) rc2,  rc2 = r_crit r_crit.
+ * Ascending indices to device idx[cap], count to device count[1]; more than
+ * cap is truncated and reported as RV_E_WORKSPACE by rv_sync_status. */
+rv_status rv_select_perturbers_tidal(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
+                                     const float *m, const float centre[3], float m_chain, float gamma_crit,
+                                     float r_crit, int32_t cap, int32_t *idx, int32_t *count, void *stream);
 
 /* ---- Learned cell-force correction (not in the paper, whose tree uses the
  * multipoles alone). A network of 11 features -> 64 -> 64 -> 3 (SiLU;

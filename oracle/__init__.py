@@ -76,6 +76,8 @@ def _declare(L):
     L.orc_knn.restype = C.c_int64
     L.orc_radius.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_float, C.c_int64, _i64]
     L.orc_radius.restype = C.c_int64
+    L.orc_tidal.argtypes = [C.c_int64, _f, _f, _f, _f, _f, C.c_float, C.c_float, C.c_float, C.c_int64, _i64]
+    L.orc_tidal.restype = C.c_int64
 
 
 def _p(a, ty):
@@ -282,6 +284,20 @@ def radius(pos32, centre32, r2_32):
     n = x.shape[0]
     out = np.zeros(max(n, 1), dtype=np.int64)
     got = lib().orc_radius(n, _p(x, _f), _p(y, _f), _p(z, _f), _p(c, _f), np.float32(r2_32), n, _p(out, _i64))
+    return out[:got]
+
+
+def tidal(pos32, mass32, centre32, mchain32, gamma, rcrit):
+    """Indices (ascending) of the stars that pass the tidal perturber
+    criterion of Eq. 2, r_j < (2 m_j / (gamma M))^(1/3) r_crit, decided in FP64
+    without a cube root on the FP32 squared distances."""
+    x, y, z = (_c(pos32[a], np.float32) for a in range(3))
+    m = _c(mass32, np.float32)
+    c = _c(centre32, np.float32)
+    n = x.shape[0]
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    got = lib().orc_tidal(n, _p(x, _f), _p(y, _f), _p(z, _f), _p(m, _f), _p(c, _f), np.float32(mchain32),
+                          np.float32(gamma), np.float32(rcrit), n, _p(out, _i64))
     return out[:got]
 
 

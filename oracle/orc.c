@@ -702,6 +702,27 @@ int64_t orc_knn(int64_t n, const float *x, const float *y, const float *z, const
     return k;
 }
 
+/* Tidal perturber criterion (Eq. 2): particle j perturbs a chain of total
+ * mass M when r_j < (2 m_j / (gamma M))^(1/3) r_crit, r_j its distance to the
+ * chain's centre. Taken without a cube root, in FP64 with one rounding per
+ * operation on the FP32 squared distance d2 (computed as for the radius
+ * search): (d2 d2) d2 < (q q) rc6 with q = (2 m_j) / (gamma M) and
+ * rc6 = (rc2 rc2) rc2, rc2 = r_crit r_crit. Ascending index; returns the
+ * count (at most cap are written). */
+int64_t orc_tidal(int64_t n, const float *x, const float *y, const float *z, const float *m, const float c[3],
+                  float mchain, float gamma, float rcrit, int64_t cap, int64_t *out) {
+    const double rc2 = (double)rcrit * (double)rcrit;
+    const double rc6 = (rc2 * rc2) * rc2;
+    const double den = (double)gamma * (double)mchain;
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const double d2 = (double)dist2_f32(x[i], y[i], z[i], c[0], c[1], c[2]);
+        const double q = (2.0 * (double)m[i]) / den;
+        if ((d2 * d2) * d2 < (q * q) * rc6) { if (k < cap) out[k] = i; k++; }
+    }
+    return k;
+}
+
 /* All particles with d2 < r2 (FP32), ascending index; returns the count
  * (at most cap are written). */
 int64_t orc_radius(int64_t n, const float *x, const float *y, const float *z, const float c[3], float r2,

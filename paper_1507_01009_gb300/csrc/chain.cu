@@ -26,19 +26,53 @@ __device__ __forceinline__ float3 centre_of(const float *cdev, float3 chost) {
     return cdev ? make_float3(cdev[0], cdev[1], cdev[2]) : chost;
 }
 
+// Membership test of a sphere-like selection around a chain centre:
+//   mode 1 (radius): d2 < r2 (FP32);
+//   mode 3 (tidal criterion of Eq. 2): r < (2 m_j / (gamma M))^(1/3) r_crit,
+//   taken without a cube root in FP64, one rounding per operation:
+//   (d2 d2) d2 < (q q) rc6, q = (2 m_j) / (gamma M), rc6 = (rc2 rc2) rc2.
+// M is the chain's FP32 total mass (the 4th value of its centre record).
+struct SelRule {
+    int mode;
+    float r2;         // mode 1
+    const float *m;   // mode 3: star masses
+    float gamma;      // mode 3
+    double rc6;       // mode 3
+};
+
+__device__ __forceinline__ bool sel_inside(const SelRule &R, float d2, int64_t i, float mchain) {
+    if (R.mode != 3) return d2 < R.r2;
+    const double dd = (double)d2;
+    const double q = __ddiv_rn(__dmul_rn(2.0, (double)R.m[i]), __dmul_rn((double)R.gamma, (double)mchain));
+    return __dmul_rn(__dmul_rn(dd, dd), dd) < __dmul_rn(__dmul_rn(q, q), R.rc6);
+}
+
+static SelRule sel_rule(int mode, float radius, const float *m, float gamma) {
+    SelRule R;
+    R.mode = mode;
+    R.r2 = radius * radius;   // one FP32 product
+    R.m = m;
+    R.gamma = gamma;
+    const double rc2 = (double)radius * (double)radius;
+    R.rc6 = (rc2 * rc2) * rc2;
+    return R;
+}
+
 __global__ void sel_radius_flag_k(int64_t n, const float *x, const float *y, const float *z, const float *cdev,
-                                  float3 chost, float r2, int *flag) {
-    float3 c = centre_of(cdev, chost);
+                                  float4 chost, SelRule R, int *flag) {
+    const float3 c = centre_of(cdev, make_float3(chost.x, chost.y, chost.z));
+    const float mc = cdev ? cdev[3] : chost.w;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        flag[i] = dist2_f32(x[i], y[i], z[i], c.x, c.y, c.z) < r2 ? 1 : 0;
+        flag[i] = sel_inside(R, dist2_f32(x[i], y[i], z[i], c.x, c.y, c.z), i, mc) ? 1 : 0;
 }
 
 __global__ void sel_radius_write_k(int64_t n, const float *x, const float *y, const float *z, const float *cdev,
-                                   float3 chost, float r2, const int *ofs, const int *total, int cap, int *idx,
+                                   float4 chost, SelRule R, const int *ofs, const int *total, int cap, int *idx,
                                    int *count, DevState *st) {
-    float3 c = centre_of(cdev, chost);
+    const float3 c = centre_of(cdev, make_float3(chost.x, chost.y, chost.z));
+    const float mc = cdev ? cdev[3] : chost.w;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (dist2_f32(x[i], y[i], z[i], c.x, c.y, c.z) < r2) {
+        if (sel_inside(R, dist2_f32(x[i], y[i], z[i], c.x, c.y, c.z), i, mc)) {
             int p = ofs[i];
             if (p < cap) idx[p] = (int)i;
         }
@@ -74,18 +108,20 @@ static int grid_n(rv_ctx *c, int64_t n) {
 
 rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
                             const float *centre_dev, const float *centre_host, int mode, float radius, int k,
-                            int cap, int *idx, int *count, cudaStream_t s) {
-    float3 ch = centre_host ? make_float3(centre_host[0], centre_host[1], centre_host[2]) : make_float3(0, 0, 0);
+                            int cap, int *idx, int *count, cudaStream_t s, const float *m, float gamma) {
+    // centre_host: (x, y, z, chain mass) -- the mass is read by the tidal rule only
+    float4 ch = centre_host ? make_float4(centre_host[0], centre_host[1], centre_host[2], centre_host[3])
+                            : make_float4(0, 0, 0, 0);
     Workspace &w = c->w;
-    if (mode == 1) {
-        float r2 = radius * radius;  // one FP32 product
+    if (mode == 1 || mode == 3) {
+        const SelRule R = sel_rule(mode, radius, m, gamma);
         if (n == 0) return cuda_check(c, cudaMemsetAsync(count, 0, sizeof(int), s), "select");
-        sel_radius_flag_k<<<grid_n(c, n), 256, 0, s>>>(n, x, y, z, centre_dev, ch, r2, w.sel_flag);
+        sel_radius_flag_k<<<grid_n(c, n), 256, 0, s>>>(n, x, y, z, centre_dev, ch, R, w.sel_flag);
         count_launch(c);
         int *total = &w.st->n_pert;  // scratch for the total; overwritten by the clamped count
         rv_status r = exclusive_scan(c, w.sel_flag, n, nullptr, total, s);
         if (r != RV_OK) return r;
-        sel_radius_write_k<<<grid_n(c, n), 256, 0, s>>>(n, x, y, z, centre_dev, ch, r2, w.sel_flag, total, cap, idx,
+        sel_radius_write_k<<<grid_n(c, n), 256, 0, s>>>(n, x, y, z, centre_dev, ch, R, w.sel_flag, total, cap, idx,
                                                         count, w.st);
         count_launch(c);
     } else {
@@ -95,7 +131,7 @@ rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y
         }
         // the sort buffers are shared with the tree build: the tree is invalid afterwards
         c->built = false;
-        sel_knn_keys_k<<<grid_n(c, n), 256, 0, s>>>(n, x, y, z, centre_dev, ch, w.key_a);
+        sel_knn_keys_k<<<grid_n(c, n), 256, 0, s>>>(n, x, y, z, centre_dev, make_float3(ch.x, ch.y, ch.z), w.key_a);
         count_launch(c);
         uint64_t *sk;
         int *si;
@@ -115,13 +151,13 @@ rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y
 //   radius:    key = 0 inside, 1 outside (inside stars first, ascending index)
 // ---------------------------------------------------------------------------
 __global__ void sel_member_keys_k(const int64_t *moff, int bpm, const float *x, const float *y, const float *z,
-                                  const float *xyzm, int mode, float r2, uint64_t *key) {
+                                  const float *xyzm, SelRule R, uint64_t *key) {
     const int m = blockIdx.y;
-    const float cx = xyzm[4 * m], cy = xyzm[4 * m + 1], cz = xyzm[4 * m + 2];
+    const float cx = xyzm[4 * m], cy = xyzm[4 * m + 1], cz = xyzm[4 * m + 2], mc = xyzm[4 * m + 3];
     for (int64_t i = moff[m] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < moff[m + 1];
          i += (int64_t)bpm * blockDim.x) {
         float d2 = dist2_f32(x[i], y[i], z[i], cx, cy, cz);
-        key[i] = (mode == 2) ? (uint64_t)__float_as_uint(d2) : (d2 < r2 ? 0ull : 1ull);
+        key[i] = (R.mode == 2) ? (uint64_t)__float_as_uint(d2) : (sel_inside(R, d2, i, mc) ? 0ull : 1ull);
     }
 }
 
@@ -320,6 +356,24 @@ __global__ void gather_pert_k(int cap, const int *idx, const int *npert, const f
     }
 }
 
+// perturbers of the last selection predicted to first order, dt after the force pass
+// (Sect. 2: the chain integrator predicts them at each of its force evaluations):
+// x_p(dt) = x_p + v_p dt in FP64, one rounding per operation
+__global__ void predict_pert_k(int cap, const int *idx, const int *npert, const float *x, const float *y,
+                               const float *z, const float *vx, const float *vy, const float *vz, const float *m,
+                               double dt, double *pm, double *px) {
+    const int mb = blockIdx.y;
+    const int np = min(npert[mb], cap);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        const int64_t q = (int64_t)mb * cap + p;
+        const int i = idx[q];
+        pm[q] = (double)m[i];
+        px[3 * q] = __dadd_rn((double)x[i], __dmul_rn((double)vx[i], dt));
+        px[3 * q + 1] = __dadd_rn((double)y[i], __dmul_rn((double)vy[i], dt));
+        px[3 * q + 2] = __dadd_rn((double)z[i], __dmul_rn((double)vz[i], dt));
+    }
+}
+
 // stars that are perturbers: add the FP64 correction (resolved chain - centre-of-mass point mass)
 __global__ void apply_pert_k(int cap, const int *idx, const int *npert, const double *a_pert, const double *pot_pert,
                              float *ax, float *ay, float *az, float *pot) {
@@ -359,6 +413,26 @@ __global__ void chain_accel_k(int M, int n_ch, const double *cm, const double *c
     }
 }
 
+static const int64_t *system_offsets(const rv_system *sys, int64_t tmp[2]);
+static int system_members(const rv_system *sys);
+
+// Perturber pull on the chain members at chain positions chain_x (member-major
+// FP64), the perturbers of the last force pass predicted dt ahead.
+rv_status chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, const double *chain_x, double *a_chain,
+                                 double *pot_chain, cudaStream_t s) {
+    Workspace &w = c->w;
+    const int M = system_members(sys);
+    const int cap = member_cap(M);
+    predict_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, sys->x, sys->y, sys->z,
+                                                               sys->vx, sys->vy, sys->vz, sys->m, dt, w.pert_m,
+                                                               w.pert_x);
+    count_launch(c);
+    ChainView V{sys->n_chain, cap, sys->chain_m, chain_x, w.npert, w.pert_m, w.pert_x};
+    pert_on_members_k<<<dim3(sys->n_chain, M), 256, 0, s>>>(V, a_chain, pot_chain ? pot_chain : w.chain_ext_pot);
+    count_launch(c);
+    return cuda_check(c, cudaGetLastError(), "chain perturber forces");
+}
+
 static const int64_t *system_offsets(const rv_system *sys, int64_t tmp[2]) {
     if (sys->n_members > 1 || sys->member_offsets) return sys->member_offsets;
     tmp[0] = 0;
@@ -382,17 +456,18 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s) {
         count_launch(c);
     }
     if ((r = upload_offsets(c, M, off, s)) != RV_OK) return r;
-    if (chain && (sys->pert_mode == 1 || sys->pert_mode == 2)) {
+    if (chain && (sys->pert_mode == 1 || sys->pert_mode == 2 || sys->pert_mode == 3)) {
         if (M == 1) {
             r = select_perturbers(c, sys->n, sys->x, sys->y, sys->z, w.extra_xyzm, nullptr, sys->pert_mode,
-                                  sys->pert_radius, sys->pert_k, cap, w.pert_idx, w.npert, s);
+                                  sys->pert_radius, sys->pert_k, cap, w.pert_idx, w.npert, s, sys->m,
+                                  sys->pert_gamma);
             if (r != RV_OK) return r;
         } else {
             // the sort buffers are shared with the tree build, which comes next
             const int bpm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c->max_member, 256), 64));
-            const float r2 = sys->pert_radius * sys->pert_radius;
+            const SelRule R = sel_rule(sys->pert_mode, sys->pert_radius, sys->m, sys->pert_gamma);
             sel_member_keys_k<<<dim3(bpm, M), 256, 0, s>>>(w.moff, bpm, sys->x, sys->y, sys->z, w.extra_xyzm,
-                                                           sys->pert_mode, r2, w.key_a);
+                                                           R, w.key_a);
             count_launch(c);
             uint64_t *sk;
             int *si;
@@ -412,6 +487,7 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s) {
                        sys->ax, sys->ay, sys->az, sys->pot, w.extra_out, s, nullptr,
                        c->cfg.mac == 1 ? &rel : nullptr)) != RV_OK)
         return r;
+    c->pert_members = chain ? M : 0;
     if (chain) {
         gather_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, sys->x, sys->y, sys->z,
                                                                   sys->m, w.pert_m, w.pert_x);

@@ -298,7 +298,9 @@ static rv_status check_system(rv_ctx *c, const rv_system *s) {
     if (s->n_chain < 0 || s->n_chain > kMaxChain) return set_err(c, RV_E_INVAL, "n_chain outside [0, %d]", kMaxChain);
     if (s->n_chain > 0 && (!s->chain_m || !s->chain_x || !s->chain_v || !s->chain_a || !s->chain_pot))
         return set_err(c, RV_E_INVAL, "null chain array in system");
-    if (s->n_chain > 0 && (s->pert_mode < 0 || s->pert_mode > 2)) return set_err(c, RV_E_INVAL, "bad pert_mode");
+    if (s->n_chain > 0 && (s->pert_mode < 0 || s->pert_mode > 3)) return set_err(c, RV_E_INVAL, "bad pert_mode");
+    if (s->n_chain > 0 && s->pert_mode == 3 && (!(s->pert_gamma > 0.f) || !(s->pert_radius >= 0.f)))
+        return set_err(c, RV_E_INVAL, "tidal selection needs pert_gamma > 0 and pert_radius >= 0");
     if (s->pert_mode == 2 && (s->pert_k < 0 || s->pert_k > kMaxPert)) return set_err(c, RV_E_INVAL, "bad pert_k");
     return RV_OK;
 }
@@ -351,7 +353,34 @@ rv_status rv_select_perturbers(rv_ctx *c, int64_t n, const float *x, const float
         return set_err(c, RV_E_INVAL, "bad selection arguments");
     if (n > 0 && (!x || !y || !z)) return set_err(c, RV_E_INVAL, "null star array");
     if (mode == 1 && !(radius >= 0.f)) return set_err(c, RV_E_INVAL, "bad radius");
-    return select_perturbers(c, n, x, y, z, nullptr, centre, mode, radius, k, cap, idx, count, (cudaStream_t)stream);
+    const float c4[4] = {centre[0], centre[1], centre[2], 0.f};
+    return select_perturbers(c, n, x, y, z, nullptr, c4, mode, radius, k, cap, idx, count, (cudaStream_t)stream);
+}
+
+rv_status rv_chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, const double *chain_x,
+                                    double *a_chain, double *pot_chain, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    rv_status r = check_system(c, sys);
+    if (r != RV_OK) return r;
+    if (sys->n_chain <= 0 || !chain_x || !a_chain) return set_err(c, RV_E_INVAL, "needs a chain and its arrays");
+    if (c->pert_members != std::max(1, (int)sys->n_members))
+        return set_err(c, RV_E_NOTBUILT, "rv_chain_perturber_forces before rv_system_forces of this system");
+    if (!(dt == dt)) return set_err(c, RV_E_INVAL, "bad dt");
+    return chain_perturber_forces(c, sys, dt, chain_x, a_chain, pot_chain, (cudaStream_t)stream);
+}
+
+rv_status rv_select_perturbers_tidal(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
+                                     const float *m, const float centre[3], float m_chain, float gamma_crit,
+                                     float r_crit, int32_t cap, int32_t *idx, int32_t *count, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (n < 0 || n > c->n_max || !centre || !idx || !count || cap < 0) return set_err(c, RV_E_INVAL, "bad selection arguments");
+    if (n > 0 && (!x || !y || !z || !m)) return set_err(c, RV_E_INVAL, "null star array");
+    if (!(m_chain > 0.f) || !(gamma_crit > 0.f) || !(r_crit >= 0.f)) return set_err(c, RV_E_INVAL, "bad tidal parameters");
+    const float c4[4] = {centre[0], centre[1], centre[2], m_chain};
+    return select_perturbers(c, n, x, y, z, nullptr, c4, 3, r_crit, 0, cap, idx, count, (cudaStream_t)stream, m,
+                             gamma_crit);
 }
 
 rv_status rv_get_tree(rv_ctx *c, rv_tree_view *out, void *stream) {

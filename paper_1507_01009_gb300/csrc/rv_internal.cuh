@@ -102,6 +102,7 @@ struct rv_ctx {
     int64_t moff_host[rv::kMaxMembers + 1]; // their star offsets
     int64_t max_member;                     // largest member
     bool moff_on_device;                    // moff_host[0..n_members] already uploaded
+    int pert_members;                       // members whose perturber sets the last force pass chose (0: none)
     // walk timing (rv_profile_walk): event pairs recorded around each walk launch
     bool profile_walk;
     int n_walk_events;
@@ -160,9 +161,14 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
                     float *xout, cudaStream_t s, const PairRecord *rec = nullptr, const RelMac *rel = nullptr);
 
 // chain.cu
+// mode 1 radius, 2 k nearest, 3 tidal (Eq. 2: radius = r_crit, star masses m, gamma);
+// centre_dev / centre_host hold (x, y, z, chain mass)
 rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
                             const float *centre_dev, const float *centre_host, int mode, float radius, int k,
-                            int cap, int *idx, int *count, cudaStream_t s);
+                            int cap, int *idx, int *count, cudaStream_t s, const float *m = nullptr,
+                            float gamma = 0.f);
+rv_status chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, const double *chain_x, double *a_chain,
+                                 double *pot_chain, cudaStream_t s);
 rv_status perturber_forces(rv_ctx *c, int n_ch, const double *cm, const double *cx, int n_pert_max,
                            const int *d_npert, const double *pm, const double *px, double *a_pert,
                            double *pot_pert, double *a_chain, double *pot_chain, double *out8, cudaStream_t s);

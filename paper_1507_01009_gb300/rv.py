@@ -26,7 +26,7 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_build_tree_members", "rv_tree_forces", "rv_tree_forces_rel", "rv_tree_forces_members",
            "rv_perturber_forces",
            "rv_system_forces", "rv_kdk_step", "rv_kdk_step_graph", "rv_energy",
-           "rv_select_perturbers", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
+           "rv_select_perturbers", "rv_select_perturbers_tidal", "rv_chain_perturber_forces", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
            "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
            "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
            "rv_mlp_samples", "rv_tree_forces_mlp"]
@@ -56,7 +56,8 @@ class rv_system(C.Structure):
                 ("az", C.c_void_p), ("pot", C.c_void_p), ("n_chain", C.c_int32), ("chain_m", C.c_void_p),
                 ("chain_x", C.c_void_p), ("chain_v", C.c_void_p), ("chain_a", C.c_void_p),
                 ("chain_pot", C.c_void_p), ("pert_mode", C.c_int32), ("pert_radius", C.c_float),
-                ("pert_k", C.c_int32), ("n_members", C.c_int32), ("member_offsets", C.c_void_p)]
+                ("pert_k", C.c_int32), ("n_members", C.c_int32), ("member_offsets", C.c_void_p),
+                ("pert_gamma", C.c_float)]
 
 
 def lib_path() -> str:
@@ -100,6 +101,9 @@ def _declare(L):
     L.rv_kdk_step.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp]
     L.rv_energy.argtypes = [vp, C.POINTER(rv_system), vp, vp]
     L.rv_select_perturbers.argtypes = [vp, i64, vp, vp, vp, C.POINTER(C.c_float), i32, f32, i32, i32, vp, vp, vp]
+    L.rv_chain_perturber_forces.argtypes = [vp, C.POINTER(rv_system), C.c_double, vp, vp, vp, vp]
+    L.rv_select_perturbers_tidal.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(C.c_float), f32, f32, f32, i32, vp,
+                                             vp, vp]
     L.rv_select_radius_static.argtypes = [i64, vp, vp, vp, C.POINTER(C.c_float), f32, i32, vp, vp, vp]
     L.rv_get_tree.argtypes = [vp, C.POINTER(rv_tree_view), vp]
     L.rv_walk_stats.argtypes = [vp, C.POINTER(C.c_int64), vp]
@@ -355,6 +359,30 @@ class Context:
                                                 _stream(stream)))
         return idx, cnt
 
+    def select_perturbers_tidal(self, x, y, z, m, centre, m_chain, gamma_crit, r_crit, cap=5000, stream=None):
+        """Eq. 2 tidal perturber search; returns (idx, count) CUDA int32 tensors."""
+        import torch
+        _need_cuda(x, y, z, m)
+        idx = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        c3 = (C.c_float * 3)(*[float(v) for v in centre])
+        self._check(self.L.rv_select_perturbers_tidal(self.h, int(x.shape[0]), _ptr(x), _ptr(y), _ptr(z), _ptr(m), c3,
+                                                      float(m_chain), float(gamma_crit), float(r_crit), int(cap),
+                                                      _ptr(idx), _ptr(cnt), _stream(stream)))
+        return idx, cnt
+
+    def chain_perturber_forces(self, sysobj, dt, chain_x, a_chain=None, pot_chain=None, stream=None):
+        """Perturber pull on the chain members at chain_x (CUDA FP64 (M n_ch, 3)),
+        the last force pass's perturbers predicted dt ahead. Returns (a_chain, pot_chain)."""
+        import torch
+        nk = sysobj.n_members * sysobj.n_chain
+        a_chain = torch.empty(3 * nk, dtype=torch.float64, device="cuda") if a_chain is None else a_chain
+        pot_chain = torch.empty(nk, dtype=torch.float64, device="cuda") if pot_chain is None else pot_chain
+        _need_cuda(chain_x, a_chain, pot_chain)
+        self._check(self.L.rv_chain_perturber_forces(self.h, C.byref(sysobj.c()), float(dt), _ptr(chain_x),
+                                                     _ptr(a_chain), _ptr(pot_chain), _stream(stream)))
+        return a_chain, pot_chain
+
     def system_forces(self, sysobj, stream=None):
         self._check(self.L.rv_system_forces(self.h, C.byref(sysobj.c()), _stream(stream)))
 
@@ -378,11 +406,12 @@ class System:
     """Device state of stars (FP32, caller order) and an optional chain (FP64)."""
 
     def __init__(self, pos, vel, mass, chain_m=None, chain_x=None, chain_v=None, pert_mode=0, pert_radius=0.0,
-                 pert_k=0, member_offsets=None):
+                 pert_k=0, member_offsets=None, pert_gamma=0.0):
         """pos/vel (3, n); mass (n,). member_offsets: host ints [M + 1] for M
         independent members stored one after another (None: one member).
         chain_* are member-major: chain_m (M n_ch,) or (n_ch,), chain_x/v
-        (M n_ch, 3)."""
+        (M n_ch, 3). pert_mode 1 radius, 2 k nearest, 3 tidal (Eq. 2,
+        r_crit = pert_radius, gamma_crit = pert_gamma)."""
         import torch
         f32 = dict(dtype=torch.float32, device="cuda")
         f64 = dict(dtype=torch.float64, device="cuda")
@@ -403,6 +432,7 @@ class System:
         else:
             self.chain_m = self.chain_x = self.chain_v = self.chain_a = self.chain_pot = None
         self.pert_mode, self.pert_radius, self.pert_k = int(pert_mode), float(pert_radius), int(pert_k)
+        self.pert_gamma = float(pert_gamma)
         import numpy as np
         if member_offsets is None:
             self.n_members, self.member_offsets = 1, None
@@ -423,6 +453,7 @@ class System:
             t = getattr(self, f)
             setattr(s, f, t.data_ptr() if t is not None else None)
         s.pert_mode, s.pert_radius, s.pert_k = self.pert_mode, self.pert_radius, self.pert_k
+        s.pert_gamma = self.pert_gamma
         s.n_members = self.n_members
         s.member_offsets = None if self.member_offsets is None else self.member_offsets.ctypes.data
         self._c = s

@@ -432,3 +432,81 @@ def test_pair_record_overflow_reported(rvmod):
     with pytest.raises(rvmod.RvError) as ei:
         ctx.sync_status()
     assert ei.value.status == rvmod.RV_E_WORKSPACE
+
+
+def test_tidal_selection_matches_oracle(rvmod):
+    """Eq. 2 on the GPU and in the oracle: the same FP64 decision without a
+    cube root, so the index sets are identical; unequal masses (heavier stars
+    reach farther) and a tiny cap (truncation reported)."""
+    g = ics.rng(43)
+    n = 200000
+    p32, _ = hernquist32(n, 44)
+    m32 = (g.uniform(0.5, 8.0, n) / n).astype(np.float32)
+    centre = np.array([0.01, -0.02, 0.0], np.float32)
+    ctx = _ctx(rvmod, n)
+    x, y, z = (to_dev(p32[a]) for a in range(3))
+    m = to_dev(m32)
+    for gam, rc in ((1e-3, 0.05), (1e-2, 0.2)):
+        idx, cnt = ctx.select_perturbers_tidal(x, y, z, m, centre, 0.01, gam, rc, cap=20000)
+        ctx.sync_status()
+        ref = oracle.tidal(p32, m32, centre, np.float32(0.01), np.float32(gam), np.float32(rc))
+        assert len(ref) > 20
+        k = int(cnt.item())
+        np.testing.assert_array_equal(idx[:k].cpu().numpy(), ref)
+    idx, cnt = ctx.select_perturbers_tidal(x, y, z, m, centre, 0.01, 1e-2, 0.2, cap=10)
+    with pytest.raises(rvmod.RvError):
+        ctx.sync_status()
+    np.testing.assert_array_equal(idx[:10].cpu().numpy(), ref[:10])
+    ctx.sync_status()
+
+
+def test_system_forces_with_tidal_perturbers(rvmod):
+    """pert_mode 3 in the full force pass: the perturbers are the Eq. 2 set and
+    the forces match the oracle following the same steps."""
+    w = ics.hernquist_bh_workload(1 << 16, seed=12)
+    w.chain.pos[0] = [0.02, 0.0, 0.0]
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    eps = float(np.float32(w.eps_star))
+    ctx = _ctx(rvmod, p32.shape[1], theta=0.5, eps_star=eps)
+    S = _system(rvmod, w, p32.shape[1], pert_mode=3, pert_radius=0.03, pert_gamma=1e-4)
+    ctx.system_forces(S)
+    ctx.sync_status()
+    com32 = w.chain.com.astype(np.float32)
+    pert = oracle.tidal(p32, m32, com32, np.float32(w.chain.total_mass), np.float32(1e-4), np.float32(0.03))
+    assert len(pert) > 3
+    ao, po, xa, xpot, o = _oracle_system_forces(w, p32, m32, 0.5, eps, pert=pert)
+    ao[:, pert] += o["a_pert"].T
+    a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
+    med, _, mx = err_stats(a, ao)
+    assert med <= MED_TOL and mx <= MAX_TOL
+    a_bh = xa[:, 0] - o["sub"] + o["a_chain"][0]
+    got = S.chain_a.cpu().numpy()[:3]
+    assert np.linalg.norm(got - a_bh) / np.linalg.norm(a_bh) <= MAX_TOL
+
+
+def test_chain_perturber_forces_predicted(rvmod):
+    """The chain integrator's perturber pull: the last force pass's perturbers
+    predicted to first order, x + v dt, acting on chain members at positions
+    the caller gives, against the oracle's FP64 perturber sum on the same
+    predicted positions (only the summation order differs)."""
+    import torch
+    w = ics.hernquist_binary_workload(1 << 16, seed=13)
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    v32 = np.ascontiguousarray(w.stars.vel, dtype=np.float32)
+    eps = float(np.float32(w.eps_star))
+    ctx = _ctx(rvmod, p32.shape[1], theta=0.5, eps_star=eps)
+    S = _system(rvmod, w, p32.shape[1], pert_mode=2, pert_k=256)
+    with pytest.raises(rvmod.RvError):                      # no force pass yet: no perturber set
+        ctx.chain_perturber_forces(S, 0.0, S.chain_x)
+    ctx.system_forces(S)
+    ctx.sync_status()
+    com32 = w.chain.com.astype(np.float32)
+    pert = oracle.knn(p32, com32, 256)
+    for dt in (0.0, 3e-4, -2e-4):
+        cx = w.chain.pos + np.array([[1e-4, -2e-4, 5e-5], [-1e-4, 2e-4, -5e-5]]) * (dt * 1e3)
+        a, pot = ctx.chain_perturber_forces(S, dt, torch.from_numpy(cx.reshape(-1)).cuda())
+        xp = p32[:, pert].astype(np.float64) + v32[:, pert].astype(np.float64) * dt
+        o = oracle.perturber(w.chain.mass, cx, m32[pert].astype(np.float64), xp.T)
+        got = a.cpu().numpy().reshape(-1, 3)
+        assert np.abs(got - o["a_chain"]).max() <= 1e-12 * np.abs(o["a_chain"]).max()
+        np.testing.assert_allclose(pot.cpu().numpy(), o["pot_chain"], rtol=1e-12)

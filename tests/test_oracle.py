@@ -479,6 +479,33 @@ def test_perturber_binary_newton_third_law():
     np.testing.assert_allclose(M * r["corr"], f_members, rtol=1e-13)
 
 
+def test_tidal_selection_closed_form():
+    """Eq. 2: with equal masses the criterion is a sphere of radius
+    R = (2 m / (gamma M))^(1/3) r_crit; a star 8 times heavier reaches twice as
+    far (the cube root of its mass ratio)."""
+    g = ics.rng(41)
+    n = 20000
+    pos = g.uniform(-1, 1, (3, n)).astype(np.float32)
+    m = np.full(n, 1e-4, np.float32)
+    c = np.zeros(3, np.float32)
+    M, gam, rc = np.float32(0.01), np.float32(1e-3), np.float32(0.1)
+    R = (2 * 1e-4 / (float(gam) * float(M))) ** (1 / 3) * float(rc)
+    r = np.linalg.norm(pos.astype(np.float64), axis=0)
+    clear = np.abs(r - R) > 1e-6 * R                      # no star on the boundary within rounding
+    sel = oracle.tidal(pos, m, c, M, gam, rc)
+    want = np.nonzero(r < R)[0]
+    assert len(want) > 50
+    np.testing.assert_array_equal(sel[np.isin(sel, np.nonzero(clear)[0])], want[clear[want]])
+    # eight times the mass: twice the radius
+    m8 = m.copy()
+    heavy = np.array([0, 1])
+    pos[:, heavy] = np.array([[1.9 * R, 2.1 * R], [0, 0], [0, 0]], np.float32)
+    m8[heavy] = np.float32(8e-4)
+    sel8 = oracle.tidal(pos, m8, c, M, gam, rc)
+    assert 0 in sel8 and 1 not in sel8
+    assert np.all(np.diff(sel8) > 0)
+
+
 def test_knn_and_radius_selection():
     w = ics.hernquist(3000, seed=21)
     p32 = w.pos.astype(np.float32)
