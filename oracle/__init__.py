@@ -13,6 +13,7 @@ points the paper leaves open are documented in ``orc.c``.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -330,6 +331,77 @@ def kdk(pos, vel, acc, dt, force_fn, nsteps=1):
         acc = force_fn(pos)
         vel = vel + 0.5 * dt * acc
     return pos, vel, acc
+
+
+def block_levels(acc32, vel32, level, n, max_level, dt_max, tau_acc, tau_vel, eps, start=False):
+    """New time-step levels (block time steps, Sect. 2; criteria of Sect. 3)
+    of the stars active at substep n: dt = min(tau_acc sqrt(eps / |a|),
+    tau_vel eps / |v|) in FP64 from the FP32 components (sums in the order
+    (x x + y y) + z z), level = the smallest l in [0, L] with dt_max 2^-l <= dt;
+    unless start, a coarser level only where its step boundary is at n (else
+    the coarsest such level between). Inactive stars keep theirs."""
+    a = np.asarray(acc32, dtype=np.float32).astype(np.float64)
+    v = np.asarray(vel32, dtype=np.float32).astype(np.float64)
+    tau_acc, tau_vel, eps = (float(np.float32(t)) for t in (tau_acc, tau_vel, eps))
+    L = int(max_level)
+    level = np.asarray(level, dtype=np.int64).copy()
+    out = level.copy()
+    for i in range(level.shape[0]):
+        if not start and n % (1 << (L - level[i])) != 0:
+            continue
+        a2 = (a[0, i] * a[0, i] + a[1, i] * a[1, i]) + a[2, i] * a[2, i]
+        v2 = (v[0, i] * v[0, i] + v[1, i] * v[1, i]) + v[2, i] * v[2, i]
+        dt = math.inf
+        if a2 > 0:
+            dt = tau_acc * math.sqrt(eps / math.sqrt(a2))
+        if v2 > 0:
+            dt = min(dt, (tau_vel * eps) / math.sqrt(v2))
+        lv, step = 0, float(dt_max)
+        while lv < L and step > dt:
+            step *= 0.5
+            lv += 1
+        if not start:
+            while lv < level[i] and n % (1 << (L - lv)) != 0:
+                lv += 1
+        out[i] = lv
+    return out
+
+
+def block_kdk(pos, vel, force_fn, level, max_level, dt_max, nsub, adapt=None):
+    """Block time steps in kick-drift-kick form (Sect. 2: stars on a hierarchy
+    of step levels), FP64. Star i has step dt_max / 2^level[i]; a substep of
+    dt_min = dt_max / 2^L drifts every star; the stars whose step ends then
+    (substep count a multiple of 2^(L - level)) take the force of the new
+    positions (force_fn(pos, active) -> acc (3, n), only the active columns
+    are used), their closing half kick, a new level (adapt = (tau_acc,
+    tau_vel, eps): block_levels on the FP32-rounded acc and velocity; None:
+    fixed) and the opening half kick. Starts with forces on every star, levels
+    and opening kicks. Returns (pos, vel, acc, level, active updates)."""
+    pos, vel = np.array(pos, dtype=np.float64), np.array(vel, dtype=np.float64)
+    level = np.asarray(level, dtype=np.int64).copy()
+    L = int(max_level)
+    n_all = pos.shape[1]
+    acc = np.asarray(force_fn(pos, np.ones(n_all, bool)), dtype=np.float64)
+
+    def new_levels(lv, n, start):
+        if adapt is None:
+            return lv
+        return block_levels(acc.astype(np.float32), vel.astype(np.float32), lv, n, L, dt_max, *adapt, start=start)
+
+    level = new_levels(level, 0, True)
+    vel = vel + acc * (0.5 * dt_max * 2.0 ** -level)
+    updates = 0
+    dt_min = dt_max * 2.0 ** -L
+    for n in range(1, nsub + 1):
+        pos = pos + vel * dt_min
+        active = (n % (1 << (L - level))) == 0
+        updates += int(active.sum())
+        a_new = np.asarray(force_fn(pos, active), dtype=np.float64)
+        acc[:, active] = a_new[:, active]
+        vel[:, active] += acc[:, active] * (0.5 * dt_max * 2.0 ** -level[active])
+        level = new_levels(level, n, False)
+        vel[:, active] += acc[:, active] * (0.5 * dt_max * 2.0 ** -level[active])
+    return pos, vel, acc, level, updates
 
 
 def rel_err(a, ref):

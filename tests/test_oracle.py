@@ -519,3 +519,70 @@ def test_knn_and_radius_selection():
     r2 = np.float32(0.3 * 0.3)
     rs = oracle.radius(p32, c, r2)
     np.testing.assert_array_equal(rs, np.nonzero(d2 < r2)[0])
+
+
+# ---------------------------------------------------------------------------
+# block time steps
+# ---------------------------------------------------------------------------
+def test_block_steps_single_level_is_kdk(plummer_case):
+    """Every star on level 0 with L = 0: the block scheme is the global KDK
+    leapfrog, operation for operation (same positions bit for bit)."""
+    p32, m32, _, _ = plummer_case
+    x0 = p32[:, :512].astype(np.float64)
+    v0 = np.zeros_like(x0)
+    m = m32[:512].astype(np.float64)
+
+    def f(x, active=None):
+        return oracle.direct(x, m, 0.01)[0]
+
+    xk, vk, ak = oracle.kdk(x0, v0, f(x0), 1e-2, f, 5)
+    xb, vb, ab, lv, upd = oracle.block_kdk(x0, v0, f, np.zeros(512, int), 0, 1e-2, 5)
+    np.testing.assert_array_equal(xb, xk)
+    np.testing.assert_array_equal(ab, ak)
+    np.testing.assert_allclose(vb, vk + 0.5 * 1e-2 * ak, rtol=1e-15, atol=1e-18)   # plus the next opening kick
+    assert upd == 5 * 512
+
+
+def test_block_steps_constant_field_closed_form():
+    """In a uniform field g each star's leapfrog is exact: at the end of each of
+    its own steps x = x0 + v0 t + g t^2 / 2 and v (before the next opening
+    kick) = v0 + g t. Stars on levels 0..3 over 16 substeps of L = 3; each
+    level l takes 2^l forces per dt_max."""
+    g = np.array([0.3, -0.2, 0.1])
+    n = 8
+    lv = np.array([0, 1, 2, 3, 0, 1, 2, 3])
+    x0 = np.arange(3 * n, dtype=np.float64).reshape(3, n) * 0.1
+    v0 = np.ones((3, n)) * np.array([1.0, -0.5, 0.25])[:, None]
+
+    def f(x, active):
+        return np.repeat(g[:, None], x.shape[1], 1)
+
+    dt_max, L, nsub = 0.25, 3, 16
+    xb, vb, _, _, upd = oracle.block_kdk(x0, v0, f, lv, L, dt_max, nsub)
+    t = nsub * dt_max / 2 ** L
+    np.testing.assert_allclose(xb, x0 + v0 * t + 0.5 * g[:, None] * t * t, rtol=1e-14, atol=1e-14)
+    vt = v0 + g[:, None] * t + g[:, None] * (0.5 * dt_max * 2.0 ** -lv)      # + the next opening kick
+    np.testing.assert_allclose(vb, vt, rtol=1e-14, atol=1e-14)
+    assert upd == int(sum(nsub // 2 ** (L - l) for l in lv))
+
+
+def test_block_level_rule_examples():
+    """dt = min(tau_acc sqrt(eps/|a|), tau_vel eps/|v|); level = the smallest l
+    with dt_max 2^-l <= dt (capped at L); coarser only on a step boundary."""
+    tau, eps, dt_max, L = 0.5, 0.01, 1.0, 4
+    # |a| = 1: dt_acc = 0.5 sqrt(0.01) = 0.05 < 1/16 -> level 5, capped at 4
+    # |a| = 0.01: dt_acc = 0.5 sqrt(1) = 0.5 -> level 1 (dt_max / 2 <= 0.5)
+    # |a| = 1e-4: dt_acc = 5; |v| = 0.02: dt_vel = 0.5 * 0.01 / 0.02 = 0.25 -> level 2
+    # a = 0, v = 0: no limit -> level 0
+    a = np.array([[1.0, 0.01, 1e-4, 0.0], [0, 0, 0, 0], [0, 0, 0, 0]], np.float32)
+    v = np.array([[0.0, 0.0, 0.02, 0.0], [0, 0, 0, 0], [0, 0, 0, 0]], np.float32)
+    lv = oracle.block_levels(a, v, np.zeros(4, int), 0, L, dt_max, tau, tau, eps, start=True)
+    np.testing.assert_array_equal(lv, [4, 1, 2, 0])
+    # star on level 4 wanting level 1 at substep 2 (L = 4): levels 1..3 end every 8, 4, 2 substeps -> level 3
+    lv = oracle.block_levels(a[:, 1:2], v[:, 1:2], np.array([4]), 2, L, dt_max, tau, tau, eps)
+    np.testing.assert_array_equal(lv, [3])
+    lv = oracle.block_levels(a[:, 1:2], v[:, 1:2], np.array([4]), 8, L, dt_max, tau, tau, eps)
+    np.testing.assert_array_equal(lv, [1])
+    # an inactive star keeps its level
+    lv = oracle.block_levels(a[:, 1:2], v[:, 1:2], np.array([2]), 3, L, dt_max, tau, tau, eps)
+    np.testing.assert_array_equal(lv, [2])
