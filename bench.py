@@ -14,7 +14,10 @@ perturber coupling and chain hand-off, kick, FP64 energy/momentum totals.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload hernquist_bh|hernquist_bh_relmac|hernquist_binary|plummer|ensemble|learned]
 
-Other workloads: `hernquist_bh_relmac` (the default workload with the
+Other workloads: `hernquist_bh_block` (the default workload on block time
+steps: levels 0..4 below dt_max = 1/64 from tau_acc = tau_vel = 0.3, walks of
+the groups holding an active star; particles = active star updates),
+`hernquist_bh_relmac` (the default workload with the
 relative opening criterion the paper's runs use, tolerance 1e-3, the previous
 step's accelerations as references), `hernquist_binary` (2^22 stars, central SMBH pair, 256
 nearest perturbers), `plummer` (4096 stars), `ensemble` (64 independent
@@ -60,7 +63,7 @@ def _dist():
 def make_workload(name: str, rank: int = 0) -> dict:
     import ics
     base = 1000 * rank
-    if name in ("hernquist_bh", "hernquist_bh_relmac"):
+    if name in ("hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block"):
         w = ics.hernquist_bh_workload(1 << 20, seed=2 + base)
         d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=w.chain.mass,
                  chain_x=w.chain.pos, chain_v=w.chain.vel, pert_mode=1, pert_radius=0.02, pert_k=0)
@@ -97,6 +100,13 @@ def make_workload(name: str, rank: int = 0) -> dict:
     if d["mac"] == 1:
         cfg.update({"workload": cfg["workload"] + "_relative_mac", "mac": "relative (M s^2 <= alpha |a| d^4)",
                     "alpha": d["alpha"], "theta_for_first_pass_and_smbh": 0.5})
+    # block time steps (Sect. 2 hierarchy; tau 0.3 as the paper's stars, Sect. 3)
+    d["block"] = dict(dt_max=1.0 / 64, L=4, tau=0.3) if name.endswith("_block") else None
+    if d["block"]:
+        cfg.update({"workload": cfg["workload"] + "_block_steps", "dt_max": 1.0 / 64, "max_level": 4,
+                    "tau_acc": 0.3, "tau_vel": 0.3,
+                    "metric_note": "particles = active star force updates; one step = dt_max = 16 substeps"})
+        cfg.pop("dt", None)
     d["config"] = cfg
     return d
 
@@ -340,6 +350,7 @@ def run_gpu(args):
     d = make_workload(args.workload, rank)
     n = d["n"]
     use_graph = args.workload == "ensemble"
+    blk = d["block"]
 
     # walk parameters (not part of the workload): the autotuner's pick over a small grid, untimed
     from paper_1507_01009_gb300 import autotune
@@ -360,15 +371,24 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev) if use_graph else torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    B = rv.Blocks(n, blk["dt_max"], blk["L"], tau_acc=blk["tau"], tau_vel=blk["tau"],
+                  eps=float(np.float32(d["eps"]))) if blk else None
+
     def step():
         if use_graph:
             ctx.kdk_step_graph(S, d["dt"], 1, energy_out=energy_out, stream=stream)
+        elif blk:
+            ctx.block_steps(S, B, 2 ** blk["L"], stream=stream)      # one dt_max: ends at a sync point
+            ctx.energy(S, out=energy_out, stream=stream)
         else:
             ctx.kdk_step(S, d["dt"], 1, stream=stream)
             ctx.energy(S, out=energy_out, stream=stream)
 
     with torch.cuda.stream(stream):
-        ctx.system_forces(S, stream=stream)
+        if blk:
+            ctx.block_start(S, B, stream=stream)
+        else:
+            ctx.system_forces(S, stream=stream)
         for _ in range(max(3, args.warmup)):
             step()
     ctx.sync_status(stream=stream)
@@ -384,7 +404,8 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     l0 = ctx.launch_count()
-    ctx.profile_walk(True)
+    b0 = ctx.block_count() if blk else 0
+    ctx.profile_walk(not blk)   # block steps: walks of varying size, timed as full walks below
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.fill_(k & 255)
@@ -401,7 +422,11 @@ def run_gpu(args):
     ctx.sync_status(stream=stream)
     total_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev])), dev)
     ms_per_step = total_ms / args.steps
-    value = job_throughput(ws, n, args.steps, total_ms)
+    if blk:   # particles = active star force updates
+        upd = ctx.block_count() - b0
+        value = job_throughput(ws, upd / args.steps, args.steps, total_ms)
+    else:
+        value = job_throughput(ws, n, args.steps, total_ms)
     p99 = p99_vs_direct(d, S) if rank == 0 else None
     p99_model = p99_vs_direct(d, S, model=True) if rank == 0 and S.n_chain > 0 else p99
 
@@ -430,7 +455,9 @@ def run_gpu(args):
         walk_ms = float(np.mean([a.elapsed_time(b) for a, b in pairs]))
         n_p2p, n_m2p = ctx.walk_stats()
         flop = FLOP_P2P * n_p2p + FLOP_M2P * n_m2p
-        walk_src = "separate build + walk loop (steps replayed from a CUDA graph); extra particles omitted"
+        walk_src = ("separate build + full walk loop (block steps walk only the active groups); extra particles "
+                    "omitted" if blk else
+                    "separate build + walk loop (steps replayed from a CUDA graph); extra particles omitted")
     achieved = flop / (walk_ms / 1e3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock
@@ -451,6 +478,12 @@ def run_gpu(args):
     e_host = torch.empty(10 * M, dtype=torch.float64, pin_memory=True)
     h2d = 4 * n * (len(fields_in) + 1)
     d2h = 4 * n * len(fields_out) + 80 * M
+    lv_host = None
+    if blk:   # the levels are state of the block scheme too
+        lv_host = torch.empty(n, dtype=torch.int8, pin_memory=True)
+        lv_host.copy_(B.level.cpu())
+        h2d += n
+        d2h += n
     e2e_ms = []
     with torch.cuda.stream(stream):
         for k in range(args.steps):
@@ -459,15 +492,19 @@ def run_gpu(args):
             e0.record(stream)
             for f in fields_in + ("m",):
                 getattr(S, f).copy_(host[f], non_blocking=True)
+            if blk:
+                B.level.copy_(lv_host, non_blocking=True)
             step()
             for f in fields_out:
                 host[f].copy_(getattr(S, f), non_blocking=True)
+            if blk:
+                lv_host.copy_(B.level, non_blocking=True)
             e_host.copy_(energy_out, non_blocking=True)
             e1.record(stream)
             e1.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))
     ctx.sync_status(stream=stream)
-    e2e_val = ws * n / (float(np.mean(e2e_ms)) / 1e3)
+    e2e_val = ws * (upd / args.steps if blk else n) / (float(np.mean(e2e_ms)) / 1e3)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -477,7 +514,9 @@ def run_gpu(args):
     if rank == 0:
         cfg = dict(d["config"])
         cfg.update({"n_leaf": tune["n_leaf"], "walk_group": tune["group"], "tile": tune["tile"],
-                    "step": "kdk + perturber select + build + walk + fp64 perturber/chain + energy",
+                    "step": ("16 block substeps (drift, perturber select, build, walk of active groups, fp64 "
+                             "perturber/chain, kicks and levels of active stars) + energy" if blk else
+                             "kdk + perturber select + build + walk + fp64 perturber/chain + energy"),
                     "parallelism": f"replicas{ws}" if ws > 1 else "single",
                     "l2": "flushed (256 MiB write) before every timed step"})
         cfg["autotuned"] = {"cached": tuned["cached"], "candidates": len(tuned["table"]),
@@ -612,7 +651,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="hernquist_bh",
-                    choices=["hernquist_bh", "hernquist_bh_relmac", "hernquist_binary", "plummer", "ensemble", "learned"])
+                    choices=["hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block", "hernquist_binary", "plummer",
+                             "ensemble", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -250,6 +250,42 @@ rv_status rv_kdk_step_graph(rv_ctx *ctx, rv_system *sys, double dt, int32_t nste
 rv_status rv_chain_perturber_forces(rv_ctx *ctx, const rv_system *sys, double dt, const double *chain_x,
                                     double *a_chain, double *pot_chain, void *stream);
 
+/* Individual hierarchical block time steps (Sect. 2: the tree code advances
+ * its particles on a hierarchy of time-step levels), kick-drift-kick form.
+ * Star i is on level level[i] (device int8 [n], 0..max_level), step
+ * dt_max / 2^level; the substep is dt_min = dt_max / 2^max_level. A substep
+ * drifts all stars and the chain by dt_min; the stars whose step ends then are
+ * active: the tree is rebuilt from all stars and only the walk groups holding
+ * an active star are walked; active stars get their closing half kick, a new
+ * level when adapt = 1 (dt = min(tau_acc sqrt(eps / |a|), tau_vel eps / |v|),
+ * level = the smallest l with dt_max 2^-l <= dt, capped at max_level, in FP64;
+ * a coarser level only where its step boundary falls on this substep), and the
+ * opening half kick of their next step. Chain members move on the finest
+ * level (a kick of dt_min per substep). With every level 0 and max_level 0 this
+ * is rv_kdk_step. The system's ax..pot hold each star's force of its last
+ * active substep. */
+typedef struct {
+    double dt_max;      /* step of level 0 */
+    int32_t max_level;  /* finest level L, 0..20 */
+    float tau_acc, tau_vel, eps;  /* step criteria (Sect. 3 uses 0.3 for stars) */
+    int32_t adapt;      /* 1: levels follow the criteria; 0: levels stay as given */
+    int8_t *level;      /* device int8 [n], in/out */
+    int64_t substep;    /* substeps done since rv_block_start (out) */
+} rv_blocks;
+/* Forces on every star, levels (adapt = 1) and the opening half kicks; substep = 0. */
+rv_status rv_block_start(rv_ctx *ctx, rv_system *sys, rv_blocks *b, void *stream);
+/* nsub substeps of dt_min (rv_block_start first). */
+rv_status rv_block_steps(rv_ctx *ctx, rv_system *sys, rv_blocks *b, int32_t nsub, void *stream);
+/* The level rule alone on n stars (device FP32 a and v, caller order) for a
+ * host integrator: the stars active at b->substep (all when start != 0, then
+ * unconstrained) get the level of the criteria, a coarser one only where its
+ * step boundary is at b->substep. Writes b->level. */
+rv_status rv_block_levels(rv_ctx *ctx, int64_t n, const float *ax, const float *ay, const float *az,
+                          const float *vx, const float *vy, const float *vz, rv_blocks *b, int32_t start,
+                          void *stream);
+/* Active star updates (forces used by a kick) since rv_block_start; synchronises `stream`. */
+rv_status rv_block_count(rv_ctx *ctx, int64_t *active_updates, void *stream);
+
 /* FP64 totals of each member of a system, written to device out[10 k ..] for
  * member k: E_kin, E_pot, E_tot, P (3), L (3), M. Stars: sum m v^2/2,
  * sum m phi/2, sum m v, sum m x cross v; chain members added in FP64 with

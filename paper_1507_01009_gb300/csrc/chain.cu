@@ -375,13 +375,15 @@ __global__ void predict_pert_k(int cap, const int *idx, const int *npert, const 
 }
 
 // stars that are perturbers: add the FP64 correction (resolved chain - centre-of-mass point mass)
+// (block time steps: only the stars active now, whose forces this pass wrote)
 __global__ void apply_pert_k(int cap, const int *idx, const int *npert, const double *a_pert, const double *pot_pert,
-                             float *ax, float *ay, float *az, float *pot) {
+                             float *ax, float *ay, float *az, float *pot, const int8_t *level, long long n, int L) {
     const int mb = blockIdx.y;
     const int np = min(npert[mb], cap);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         const int64_t q = (int64_t)mb * cap + p;
         const int i = idx[q];
+        if (level && (n & ((1ll << (L - level[i])) - 1)) != 0) continue;
         ax[i] = (float)((double)ax[i] + a_pert[3 * q]);
         ay[i] = (float)((double)ay[i] + a_pert[3 * q + 1]);
         az[i] = (float)((double)az[i] + a_pert[3 * q + 2]);
@@ -414,7 +416,6 @@ __global__ void chain_accel_k(int M, int n_ch, const double *cm, const double *c
 }
 
 static const int64_t *system_offsets(const rv_system *sys, int64_t tmp[2]);
-static int system_members(const rv_system *sys);
 
 // Perturber pull on the chain members at chain positions chain_x (member-major
 // FP64), the perturbers of the last force pass predicted dt ahead.
@@ -440,9 +441,9 @@ static const int64_t *system_offsets(const rv_system *sys, int64_t tmp[2]) {
     return tmp;
 }
 
-static int system_members(const rv_system *sys) { return std::max(1, (int)sys->n_members); }
+int system_members(const rv_system *sys) { return std::max(1, (int)sys->n_members); }
 
-rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s) {
+rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s, const BlockSel *blk) {
     Workspace &w = c->w;
     rv_status r;
     const bool chain = sys->n_chain > 0;
@@ -480,12 +481,17 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s) {
         cudaMemsetAsync(w.npert, 0, sizeof(int) * M, s);
     }
     if ((r = build_tree(c, M, off, sys->x, sys->y, sys->z, sys->m, s)) != RV_OK) return r;
+    const uint8_t *gact = nullptr;
+    if (blk) {
+        launch_block_groups(c, *blk, s);
+        gact = w.gact;
+    }
     // relative criterion (cfg.mac = 1): the accelerations in the system arrays (the previous
     // pass's, zero before the first one) are the references, read before they are overwritten
     const RelMac rel{c->cfg.alpha, sys->ax, sys->ay, sys->az};
     if ((r = tree_walk(c, c->cfg.theta, c->cfg.eps_star, chain ? M : 0, w.extra_xyzm, w.extra_eps, nullptr, true,
                        sys->ax, sys->ay, sys->az, sys->pot, w.extra_out, s, nullptr,
-                       c->cfg.mac == 1 ? &rel : nullptr)) != RV_OK)
+                       c->cfg.mac == 1 ? &rel : nullptr, gact)) != RV_OK)
         return r;
     c->pert_members = chain ? M : 0;
     if (chain) {
@@ -496,7 +502,9 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s) {
         r = coupling(c, M, V, w.pert_a, w.pert_pot, w.chain_ext_a, w.chain_ext_pot, w.out8, s);
         if (r != RV_OK) return r;
         apply_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, w.pert_a, w.pert_pot,
-                                                                 sys->ax, sys->ay, sys->az, sys->pot);
+                                                                 sys->ax, sys->ay, sys->az, sys->pot,
+                                                                 blk ? blk->level : nullptr, blk ? blk->n : 0,
+                                                                 blk ? blk->L : 0);
         count_launch(c);
         chain_accel_k<<<ceil_div(M * sys->n_chain, 128), 128, 0, s>>>(M, sys->n_chain, sys->chain_m, sys->chain_x,
                                                                       w.chain_ext_a, w.chain_ext_pot, w.extra_out,
@@ -528,7 +536,7 @@ __global__ void chain_kick_drift_k(int n, double *cx, double *cv, const double *
         }
 }
 
-static void kick(rv_ctx *c, rv_system *sys, double dt, int drift, cudaStream_t s) {
+void kick(rv_ctx *c, rv_system *sys, double dt, int drift, cudaStream_t s) {
     const int M = system_members(sys);
     if (sys->n > 0) {
         kick_drift_k<<<grid_n(c, sys->n), 256, 0, s>>>(sys->n, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz,

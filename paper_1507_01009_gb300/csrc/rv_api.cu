@@ -70,6 +70,8 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.carrive = (int *)take(4 * cap);
     t.gcnt = (int *)take(4 * cap);
     t.groups = (int4 *)take(32 * (n + 1));   // every group holds a star
+    t.gact = (uint8_t *)take(n + 1);
+    t.block_count = (unsigned long long *)take(16);
     t.partials = (int *)take(4 * nparts);
     t.pert_idx = (int *)take(4 * kPertTotal);
     t.pert_m = (double *)take(8 * kPertTotal);
@@ -368,6 +370,56 @@ rv_status rv_chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, 
         return set_err(c, RV_E_NOTBUILT, "rv_chain_perturber_forces before rv_system_forces of this system");
     if (!(dt == dt)) return set_err(c, RV_E_INVAL, "bad dt");
     return chain_perturber_forces(c, sys, dt, chain_x, a_chain, pot_chain, (cudaStream_t)stream);
+}
+
+static rv_status check_blocks(rv_ctx *c, const rv_system *sys, const rv_blocks *b) {
+    if (!b) return set_err(c, RV_E_INVAL, "null block parameters");
+    if (!(b->dt_max > 0.0) || b->max_level < 0 || b->max_level > 20 || (sys->n > 0 && !b->level))
+        return set_err(c, RV_E_INVAL, "bad block parameters (dt_max > 0, max_level 0..20, level array)");
+    if (b->adapt && !(b->tau_acc > 0.f && b->tau_vel > 0.f && b->eps > 0.f))
+        return set_err(c, RV_E_INVAL, "adaptive levels need tau_acc, tau_vel, eps > 0");
+    return RV_OK;
+}
+
+rv_status rv_block_start(rv_ctx *c, rv_system *sys, rv_blocks *b, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    rv_status r = check_system(c, sys);
+    if (r == RV_OK) r = check_blocks(c, sys, b);
+    if (r != RV_OK) return r;
+    return block_start(c, sys, b, (cudaStream_t)stream);
+}
+
+rv_status rv_block_steps(rv_ctx *c, rv_system *sys, rv_blocks *b, int32_t nsub, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    rv_status r = check_system(c, sys);
+    if (r == RV_OK) r = check_blocks(c, sys, b);
+    if (r != RV_OK) return r;
+    if (nsub < 0) return set_err(c, RV_E_INVAL, "nsub < 0");
+    return block_steps(c, sys, b, nsub, (cudaStream_t)stream);
+}
+
+rv_status rv_block_levels(rv_ctx *c, int64_t n, const float *ax, const float *ay, const float *az, const float *vx,
+                          const float *vy, const float *vz, rv_blocks *b, int32_t start, void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (n < 0 || (n > 0 && (!ax || !ay || !az || !vx || !vy || !vz))) return set_err(c, RV_E_INVAL, "bad arrays");
+    if (!b || !(b->dt_max > 0.0) || b->max_level < 0 || b->max_level > 20 || (n > 0 && !b->level) ||
+        !(b->tau_acc > 0.f && b->tau_vel > 0.f && b->eps > 0.f))
+        return set_err(c, RV_E_INVAL, "bad block parameters");
+    return block_levels(c, n, ax, ay, az, vx, vy, vz, b, start ? 1 : 0, (cudaStream_t)stream);
+}
+
+rv_status rv_block_count(rv_ctx *c, int64_t *active_updates, void *stream) {
+    if (!c || !active_updates) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    unsigned long long v = 0;
+    rv_status r = cuda_check(c, cudaMemcpyAsync(&v, c->w.block_count, sizeof v, cudaMemcpyDeviceToHost,
+                                                (cudaStream_t)stream), "block count");
+    if (r == RV_OK) r = cuda_check(c, cudaStreamSynchronize((cudaStream_t)stream), "block count");
+    *active_updates = (int64_t)v;
+    return r;
 }
 
 rv_status rv_select_perturbers_tidal(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,

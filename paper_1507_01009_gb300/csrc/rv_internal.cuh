@@ -64,6 +64,8 @@ struct Workspace {
     int *cparent, *carrive;
     int *gcnt;            // groups of each cell, scanned in place to each cell's first group
     int4 *groups;         // 2 int4 per group: (first, count, lo x, lo y), (lo z, hi x, hi y, hi z)
+    uint8_t *gact;        // block time steps: groups holding an active star
+    unsigned long long *block_count;  // block time steps: active star updates so far
     int *partials;        // scan block sums
     // perturbers and chain hand-off
     int *pert_idx;        // [kMaxPert]
@@ -158,7 +160,8 @@ struct RelMac {
 // extra k belongs to member k (one chain per member) -- see walk.cu.
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
-                    float *xout, cudaStream_t s, const PairRecord *rec = nullptr, const RelMac *rel = nullptr);
+                    float *xout, cudaStream_t s, const PairRecord *rec = nullptr, const RelMac *rel = nullptr,
+                    const uint8_t *gact = nullptr);
 
 // chain.cu
 // mode 1 radius, 2 k nearest, 3 tidal (Eq. 2: radius = r_crit, star masses m, gamma);
@@ -172,8 +175,23 @@ rv_status chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, con
 rv_status perturber_forces(rv_ctx *c, int n_ch, const double *cm, const double *cx, int n_pert_max,
                            const int *d_npert, const double *pm, const double *px, double *a_pert,
                            double *pot_pert, double *a_chain, double *pot_chain, double *out8, cudaStream_t s);
-rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s);
+// Block time steps: the stars' levels, the substep n that ends now, the finest level L.
+struct BlockSel {
+    const int8_t *level;
+    long long n;
+    int L;
+};
+// blk (optional): after the build, walk only the groups holding a star active at blk->n
+rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s, const BlockSel *blk = nullptr);
+// blocks.cu
+void launch_block_groups(rv_ctx *c, const BlockSel &b, cudaStream_t s);
+rv_status block_start(rv_ctx *c, rv_system *sys, rv_blocks *b, cudaStream_t s);
+rv_status block_steps(rv_ctx *c, rv_system *sys, rv_blocks *b, int nsub, cudaStream_t s);
+rv_status block_levels(rv_ctx *c, int64_t n_st, const float *ax, const float *ay, const float *az, const float *vx,
+                       const float *vy, const float *vz, const rv_blocks *b, int start, cudaStream_t s);
 rv_status kdk(rv_ctx *c, rv_system *sys, double dt, int nsteps, cudaStream_t s);
+void kick(rv_ctx *c, rv_system *sys, double dt, int drift, cudaStream_t s);
+int system_members(const rv_system *sys);
 rv_status energy(rv_ctx *c, const rv_system *sys, double *out, cudaStream_t s);
 rv_status kdk_graph(rv_ctx *c, rv_system *sys, double dt, int nsteps, double *eout, cudaStream_t s);
 

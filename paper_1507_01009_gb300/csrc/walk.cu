@@ -88,6 +88,8 @@ struct WalkArgs {
     // relative opening criterion: tolerance and reference acceleration per star (caller order)
     float rel_alpha;
     const float *arx, *ary, *arz;
+    // optional group mask (block time steps): only groups with gact[g] != 0 are walked
+    const uint8_t *gact;
 };
 
 // Per-warp shared memory: stack | lane_cell[32] | cell staging | star staging.
@@ -623,7 +625,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             }
             continue;
         }
-        // ---- a group of the tree
+        // ---- a group of the tree (skipped when the mask says none of its stars is active)
+        if (A.gact && !A.gact[gi - A.n_extra]) continue;
         const GroupRec grp = load_group(A.groups, gi - A.n_extra);
         if (grp.first < 0 || grp.count < 1 || grp.count > kMaxGroup || grp.first + grp.count > A.n) {
             if (lane == 0) latch_err(A.st, kErrStack);
@@ -739,7 +742,7 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
 
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
-                    float *xout, cudaStream_t s, const PairRecord *rec, const RelMac *rel) {
+                    float *xout, cudaStream_t s, const PairRecord *rec, const RelMac *rel, const uint8_t *gact) {
     Workspace &w = c->w;
     WalkArgs A;
     A.pos = w.pos;
@@ -770,6 +773,7 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.npairs = rec ? rec->npairs : nullptr;
     A.pair_cap = rec ? rec->cap : 0;
     if (rec) A.rec = mac_table(rec->theta_rec);
+    A.gact = gact;
     A.rel_alpha = rel ? rel->alpha : 0.f;
     A.arx = rel ? rel->rx : nullptr;
     A.ary = rel ? rel->ry : nullptr;

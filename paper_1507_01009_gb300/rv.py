@@ -26,7 +26,8 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_build_tree_members", "rv_tree_forces", "rv_tree_forces_rel", "rv_tree_forces_members",
            "rv_perturber_forces",
            "rv_system_forces", "rv_kdk_step", "rv_kdk_step_graph", "rv_energy",
-           "rv_select_perturbers", "rv_select_perturbers_tidal", "rv_chain_perturber_forces", "rv_select_radius_static", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
+           "rv_select_perturbers", "rv_select_perturbers_tidal", "rv_chain_perturber_forces", "rv_select_radius_static",
+           "rv_block_start", "rv_block_steps", "rv_block_levels", "rv_block_count", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
            "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
            "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
            "rv_mlp_samples", "rv_tree_forces_mlp"]
@@ -42,6 +43,11 @@ class RvError(RuntimeError):
 class rv_config(C.Structure):
     _fields_ = [("theta", C.c_float), ("eps_star", C.c_float), ("n_leaf", C.c_int32), ("group", C.c_int32),
                 ("quadrupole", C.c_int32), ("tile", C.c_int32), ("mac", C.c_int32), ("alpha", C.c_float)]
+
+
+class rv_blocks(C.Structure):
+    _fields_ = [("dt_max", C.c_double), ("max_level", C.c_int32), ("tau_acc", C.c_float), ("tau_vel", C.c_float),
+                ("eps", C.c_float), ("adapt", C.c_int32), ("level", C.c_void_p), ("substep", C.c_int64)]
 
 
 class rv_tree_view(C.Structure):
@@ -101,6 +107,10 @@ def _declare(L):
     L.rv_kdk_step.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp]
     L.rv_energy.argtypes = [vp, C.POINTER(rv_system), vp, vp]
     L.rv_select_perturbers.argtypes = [vp, i64, vp, vp, vp, C.POINTER(C.c_float), i32, f32, i32, i32, vp, vp, vp]
+    L.rv_block_start.argtypes = [vp, C.POINTER(rv_system), C.POINTER(rv_blocks), vp]
+    L.rv_block_steps.argtypes = [vp, C.POINTER(rv_system), C.POINTER(rv_blocks), i32, vp]
+    L.rv_block_levels.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, C.POINTER(rv_blocks), i32, vp]
+    L.rv_block_count.argtypes = [vp, C.POINTER(C.c_int64), vp]
     L.rv_chain_perturber_forces.argtypes = [vp, C.POINTER(rv_system), C.c_double, vp, vp, vp, vp]
     L.rv_select_perturbers_tidal.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(C.c_float), f32, f32, f32, i32, vp,
                                              vp, vp]
@@ -383,6 +393,28 @@ class Context:
                                                      _ptr(a_chain), _ptr(pot_chain), _stream(stream)))
         return a_chain, pot_chain
 
+    def block_start(self, sysobj, blocks, stream=None):
+        b = blocks.c()
+        self._check(self.L.rv_block_start(self.h, C.byref(sysobj.c()), C.byref(b), _stream(stream)))
+        blocks.substep = int(b.substep)
+
+    def block_steps(self, sysobj, blocks, nsub, stream=None):
+        b = blocks.c()
+        self._check(self.L.rv_block_steps(self.h, C.byref(sysobj.c()), C.byref(b), int(nsub), _stream(stream)))
+        blocks.substep = int(b.substep)
+
+    def block_levels(self, blocks, acc, vel, start=False, stream=None):
+        """The level rule on device FP32 acc = (ax, ay, az), vel = (vx, vy, vz)."""
+        _need_cuda(*acc, *vel)
+        b = blocks.c()
+        self._check(self.L.rv_block_levels(self.h, int(acc[0].shape[0]), *[_ptr(t) for t in acc],
+                                           *[_ptr(t) for t in vel], C.byref(b), int(bool(start)), _stream(stream)))
+
+    def block_count(self, stream=None) -> int:
+        v = C.c_int64(0)
+        self._check(self.L.rv_block_count(self.h, C.byref(v), _stream(stream)))
+        return int(v.value)
+
     def system_forces(self, sysobj, stream=None):
         self._check(self.L.rv_system_forces(self.h, C.byref(sysobj.c()), _stream(stream)))
 
@@ -458,6 +490,27 @@ class System:
         s.member_offsets = None if self.member_offsets is None else self.member_offsets.ctypes.data
         self._c = s
         return s
+
+
+class Blocks:
+    """Block time-step state: levels (CUDA int8 [n]) and parameters (see rv_blocks)."""
+
+    def __init__(self, n, dt_max, max_level, tau_acc=0.3, tau_vel=0.3, eps=0.01, adapt=True, level=None):
+        import torch
+        self.level = (torch.zeros(n, dtype=torch.int8, device="cuda") if level is None else
+                      torch.as_tensor(level).to(dtype=torch.int8, device="cuda").contiguous())
+        self.dt_max, self.max_level = float(dt_max), int(max_level)
+        self.tau_acc, self.tau_vel, self.eps, self.adapt = float(tau_acc), float(tau_vel), float(eps), bool(adapt)
+        self.substep = 0
+
+    def c(self) -> rv_blocks:
+        b = rv_blocks()
+        b.dt_max, b.max_level = self.dt_max, self.max_level
+        b.tau_acc, b.tau_vel, b.eps, b.adapt = self.tau_acc, self.tau_vel, self.eps, int(self.adapt)
+        b.level = self.level.data_ptr()
+        b.substep = self.substep
+        self._c = b
+        return b
 
 
 # --------------------------------------------------------------------------
