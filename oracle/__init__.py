@@ -56,7 +56,7 @@ _u64 = C.POINTER(C.c_uint64)
 
 
 def _declare(L):
-    L.orc_direct.argtypes = [C.c_int64, _d, _d, _d, _d, _d, C.c_int64, _i64, _d, _d, _d, _d]
+    L.orc_direct.argtypes = [C.c_int64, _d, _d, _d, _d, _d, C.c_int64, _i64, _d, _d, _d, _d, C.c_int32]
     L.orc_bounds.argtypes = [C.c_int64, _f, _f, _f, _d, _d, _d]
     L.orc_keys.argtypes = [C.c_int64, _f, _f, _f, _d, C.c_double, _u64]
     L.orc_sort.argtypes = [C.c_int64, _u64, _u64, _i64]
@@ -71,7 +71,7 @@ def _declare(L):
     L.orc_tree_groups.argtypes = [C.c_void_p, _i64]
     L.orc_tree_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32,
                                   _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64, C.c_int64, _i64,
-                                  C.c_float, _f, _f, _f]
+                                  C.c_float, _f, _f, _f, C.c_int32]
     L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d, _d]
     L.orc_knn.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_int64, _i64]
     L.orc_knn.restype = C.c_int64
@@ -92,9 +92,11 @@ def _c(a, dt):
 # ---------------------------------------------------------------------------
 # Direct sum
 # ---------------------------------------------------------------------------
-def direct(pos, mass, eps, targets=None):
+def direct(pos, mass, eps, targets=None, kind=0):
     """Direct-summation acceleration and potential (G = 1, Plummer softening,
-    Sect. 3) on ``targets`` (indices; default all) from all particles.
+    Sect. 3; kind = 1: spline softening of Plummer-equivalent length eps, the
+    cubic-spline field with h = 2.8 eps) on ``targets`` (indices; default all)
+    from all particles.
 
     ``pos`` (3, n) float64, ``mass`` (n,), ``eps`` scalar or (n,) where 0 marks
     an unsoftened particle (the chain centre of mass, Sect. 2/3). Pair
@@ -107,7 +109,7 @@ def direct(pos, mass, eps, targets=None):
     x, y, z = (_c(pos[a], np.float64) for a in range(3))
     out = [np.zeros(t.shape[0]) for _ in range(4)]
     lib().orc_direct(n, _p(x, _d), _p(y, _d), _p(z, _d), _p(m, _d), _p(e, _d), t.shape[0], _p(t, _i64),
-                     *[_p(o, _d) for o in out])
+                     *[_p(o, _d) for o in out], int(kind))
     return np.stack(out[:3]), out[3]
 
 
@@ -191,7 +193,8 @@ class Tree:
             self._h = None
 
     def forces(self, theta: float, eps_star: float, quadrupole: bool = True,
-               extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False, targets=None, rel=None):
+               extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False, targets=None, rel=None,
+               kind: int = 0):
         """Tree acceleration/potential on every star (caller order), FP64.
 
         Walk under the box-box opening-angle test at ``theta``; ``extra_*``
@@ -202,7 +205,9 @@ class Tree:
         (caller indices) only those stars are computed; the rest of the
         returned arrays is zero. With ``rel = (alpha, aref)`` the stars' groups
         use the relative opening criterion (see ``forces_rel``); groups whose
-        smallest reference |a| is 0 and the extra particles use theta."""
+        smallest reference |a| is 0 and the extra particles use theta. ``kind``
+        1: spline softening of the stars (see ``direct``; accepted cells closer
+        than h = 2.8 eps act as softened monopoles)."""
         k = 0 if extra_mass is None else int(np.asarray(extra_mass).shape[0])
         ex = np.zeros((3, max(k, 1)), dtype=np.float32)
         xm = np.zeros(max(k, 1))
@@ -223,7 +228,7 @@ class Tree:
                               -1 if targets is None else len(targets),
                               None if targets is None else _p(_c(targets, np.int64), _i64),
                               float(np.float32(rel[0])) if rel is not None else 0.0,
-                              *([_p(v, _f) for v in ar] if rel is not None else [None, None, None]))
+                              *([_p(v, _f) for v in ar] if rel is not None else [None, None, None]), int(kind))
         res = (np.stack(out[:3]), out[3], np.stack(xout[:3])[:, :k], xout[3][:k])
         return res + (cnt,) if counts else res
 

@@ -51,12 +51,48 @@ static double pair_eps(double ei, double ej) {
     return ei > ej ? ei : ej;
 }
 
-/* Softened point-mass acceleration on i from j and potential (G = 1):
- * a = m_j r / (r^2+e^2)^{3/2}, phi = -m_j / (r^2+e^2)^{1/2}, r = x_j - x_i.
- * A pair at zero softened distance contributes nothing. */
-static void p2p(double xi, double yi, double zi, double xj, double yj, double zj,
-                double mj, double e, nsum *ax, nsum *ay, nsum *az, nsum *ph) {
+/* Spline softening (the "spline" option of Sect. 2; reading: the point mass
+ * smoothed by the cubic spline kernel of compact support h, W(r) = 8/(pi h^3)
+ * (1 - 6u^2 + 6u^3) for u = r/h < 1/2, 16/(pi h^3) (1 - u)^3 for 1/2 <= u < 1,
+ * 0 beyond, with h = 2.8 e, so that the potential at r = 0 is -m/e as for
+ * Plummer softening of length e). Integrating the kernel's enclosed mass
+ * gives a = m r f(u) / h^3 toward the mass and phi = (m/h) P(u):
+ *   u < 1/2:      f = 32/3 - 192/5 u^2 + 32 u^3,
+ *                 P = -14/5 + 16/3 u^2 - 48/5 u^4 + 32/5 u^5,
+ *   1/2 <= u < 1: f = 64/3 - 48 u + 192/5 u^2 - 32/3 u^3 - 1/(15 u^3),
+ *                 P = -16/5 + 1/(15 u) + 32/3 u^2 - 16 u^3 + 48/5 u^4 - 32/15 u^5,
+ *   u >= 1:       f = 1/u^3, P = -1/u (Newton). */
+#define ORC_SPLINE_H 2.8
+static void spline_fp(double u, double *f, double *p) {
+    if (u < 0.5) {
+        *f = 32.0 / 3.0 + u * u * (-192.0 / 5.0 + 32.0 * u);
+        *p = -14.0 / 5.0 + u * u * (16.0 / 3.0 + u * u * (-48.0 / 5.0 + 32.0 / 5.0 * u));
+    } else {
+        *f = 64.0 / 3.0 - 48.0 * u + u * u * (192.0 / 5.0 - 32.0 / 3.0 * u) - 1.0 / (15.0 * u * u * u);
+        *p = -16.0 / 5.0 + 1.0 / (15.0 * u) + u * u * (32.0 / 3.0 + u * (-16.0 + u * (48.0 / 5.0 - 32.0 / 15.0 * u)));
+    }
+}
+
+/* Softened point-mass acceleration on i from j and potential (G = 1),
+ * r = x_j - x_i. kind 0 (Plummer, Sect. 3): a = m_j r / (r^2+e^2)^{3/2},
+ * phi = -m_j / (r^2+e^2)^{1/2}; a pair at zero softened distance contributes
+ * nothing. kind 1: the spline field above with h = 2.8 e (Newton for e = 0). */
+static void p2p_k(int kind, double xi, double yi, double zi, double xj, double yj, double zj,
+                  double mj, double e, nsum *ax, nsum *ay, nsum *az, nsum *ph) {
     double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    if (kind == 1 && e > 0.0) {
+        const double h = ORC_SPLINE_H * e;
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r < h) {
+            double f, p;
+            spline_fp(r / h, &f, &p);
+            const double s = mj * f / (h * h * h);
+            nadd(ax, s * dx); nadd(ay, s * dy); nadd(az, s * dz);
+            nadd(ph, mj * p / h);
+            return;
+        }
+        e = 0.0;
+    }
     double r2 = dx * dx + dy * dy + dz * dz + e * e;
     if (r2 <= 0.0) return;
     double rinv = 1.0 / sqrt(r2);
@@ -64,22 +100,27 @@ static void p2p(double xi, double yi, double zi, double xj, double yj, double zj
     nadd(ax, mr3 * dx); nadd(ay, mr3 * dy); nadd(az, mr3 * dz);
     nadd(ph, -mj * rinv);
 }
+static void p2p(double xi, double yi, double zi, double xj, double yj, double zj,
+                double mj, double e, nsum *ax, nsum *ay, nsum *az, nsum *ph) {
+    p2p_k(0, xi, yi, zi, xj, yj, zj, mj, e, ax, ay, az, ph);
+}
 
 /* ------------------------------------------------------------------ */
 /* 1. Direct sum                                                        */
 /* ------------------------------------------------------------------ */
 /* Acceleration and potential on targets tidx[0..nt) from all n particles,
- * skipping j == i. eps[j] = 0 marks an unsoftened particle. */
+ * skipping j == i. eps[j] = 0 marks an unsoftened particle; kind 0 Plummer,
+ * 1 spline softening (see p2p_k). */
 void orc_direct(int64_t n, const double *x, const double *y, const double *z,
                 const double *m, const double *eps, int64_t nt, const int64_t *tidx,
-                double *ax, double *ay, double *az, double *pot) {
+                double *ax, double *ay, double *az, double *pot, int32_t kind) {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; t++) {
         int64_t i = tidx[t];
         nsum sx = {0, 0}, sy = {0, 0}, sz = {0, 0}, sp = {0, 0};
         for (int64_t j = 0; j < n; j++) {
             if (j == i) continue;
-            p2p(x[i], y[i], z[i], x[j], y[j], z[j], m[j], pair_eps(eps[i], eps[j]), &sx, &sy, &sz, &sp);
+            p2p_k(kind, x[i], y[i], z[i], x[j], y[j], z[j], m[j], pair_eps(eps[i], eps[j]), &sx, &sy, &sz, &sp);
         }
         ax[t] = nval(&sx); ay[t] = nval(&sy); az[t] = nval(&sz); pot[t] = nval(&sp);
     }
@@ -422,10 +463,24 @@ static int mac_accept(const orc_tree *t, const int64_t blo[3], const int64_t bhi
  * a = -M r/rho^3 + Q r/rho^5 - 5 (r.Q.r) r/(2 rho^7); for e = 0 this is the
  * exact two-term multipole expansion about the centre of mass. */
 static void m2p(const orc_tree *t, int64_t c, double px, double py, double pz, double e, int quad,
-                nsum *ax, nsum *ay, nsum *az, nsum *ph) {
+                nsum *ax, nsum *ay, nsum *az, nsum *ph, int kind) {
     double M = t->cm[c];
     if (M == 0.0) return;
     double rx = px - t->cx[c], ry = py - t->cy[c], rz = pz - t->cz[c];
+    if (kind == 1 && e > 0.0) {
+        /* spline softening (reading): beyond h = 2.8 e the field is Newton's, so
+         * the unsoftened expansion; inside, the cell acts as a softened monopole */
+        const double h = ORC_SPLINE_H * e;
+        const double r = sqrt(rx * rx + ry * ry + rz * rz);
+        if (r < h) {
+            double f, p;
+            spline_fp(r / h, &f, &p);
+            const double s = -M * f / (h * h * h);
+            nadd(ax, s * rx); nadd(ay, s * ry); nadd(az, s * rz); nadd(ph, M * p / h);
+            return;
+        }
+        e = 0.0;
+    }
     double r2 = rx * rx + ry * ry + rz * rz + e * e;
     if (r2 <= 0.0) return;
     double rinv = 1.0 / sqrt(r2), rinv2 = rinv * rinv, rinv3 = rinv * rinv2;
@@ -456,6 +511,7 @@ typedef struct {
     int64_t n_p2p, n_m2p;
     int rel;      /* 1: relative criterion with constant K below */
     float K;
+    int kind;     /* softening: 0 Plummer, 1 spline */
 } walk_state;
 
 /* Relative opening criterion (Sect. 3: the runs use a "Gadget" criterion with
@@ -504,14 +560,15 @@ static float ref_mag(float x, float y, float z) {
 static void walk_cell(walk_state *w, int64_t c) {
     const orc_tree *t = w->t;
     if (w->rel ? mac_accept_rel(t, w->blo, w->bhi, c, w->K) : mac_accept(t, w->blo, w->bhi, c, w->theta2)) {
-        m2p(t, c, w->px, w->py, w->pz, w->e, w->quad, &w->ax, &w->ay, &w->az, &w->ph);
+        m2p(t, c, w->px, w->py, w->pz, w->e, w->quad, &w->ax, &w->ay, &w->az, &w->ph, w->kind);
         w->n_m2p++;
         return;
     }
     if (cell_is_leaf(t, c)) {
         for (int64_t j = t->first[c]; j < t->first[c] + t->count[c]; j++) {
             if (j == w->self) continue;
-            p2p(w->px, w->py, w->pz, t->x[j], t->y[j], t->z[j], t->m[j], w->e, &w->ax, &w->ay, &w->az, &w->ph);
+            p2p_k(w->kind, w->px, w->py, w->pz, t->x[j], t->y[j], t->z[j], t->m[j], w->e, &w->ax, &w->ay, &w->az,
+                  &w->ph);
             w->n_p2p++;
         }
         return;
@@ -530,14 +587,16 @@ static void walk_cell(walk_state *w, int64_t c) {
  * indices are listed in sub[0..nsub) are computed (others untouched).
  * With rx != NULL the stars' groups use the relative criterion above with
  * tolerance alpha and reference accelerations (rx, ry, rz)[i] (caller order,
- * FP32); the extra particles always use the opening angle. */
+ * FP32); the extra particles always use the opening angle. kind selects the
+ * stars' softening: 0 Plummer, 1 spline (see p2p_k; the extra particles'
+ * pairs use Plummer's rule with their own lengths). */
 void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t quad,
                      int32_t nx, const float *xx, const float *xy, const float *xz, const double *xm,
                      const double *xeps,
                      double *ax, double *ay, double *az, double *pot,
                      double *xax, double *xay, double *xaz, double *xpot, int64_t *counts,
                      int64_t nsub, const int64_t *sub,
-                     float alpha, const float *rx, const float *ry, const float *rz) {
+                     float alpha, const float *rx, const float *ry, const float *rz, int32_t kind) {
     double theta2 = theta * theta;
     const float u = (float)(t->L / ORC_GRID);
     /* optional subset: only sorted slots whose caller index is flagged */
@@ -568,6 +627,7 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
             walk_state w;
             memset(&w, 0, sizeof w);
             w.t = t; w.theta2 = theta2; w.quad = quad; w.e = eps_star; w.self = i; w.rel = rel; w.K = K;
+            w.kind = kind;
             memcpy(w.blo, blo, sizeof blo); memcpy(w.bhi, bhi, sizeof bhi);
             w.px = t->x[i]; w.py = t->y[i]; w.pz = t->z[i];
             if (t->ncell > 0) walk_cell(&w, 0);

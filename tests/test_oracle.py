@@ -586,3 +586,60 @@ def test_block_level_rule_examples():
     # an inactive star keeps its level
     lv = oracle.block_levels(a[:, 1:2], v[:, 1:2], np.array([2]), 3, L, dt_max, tau, tau, eps)
     np.testing.assert_array_equal(lv, [2])
+
+
+# ---------------------------------------------------------------------------
+# spline softening
+# ---------------------------------------------------------------------------
+def _pair(r, e, kind=1):
+    pos = np.array([[0.0, r], [0.0, 0.0], [0.0, 0.0]])
+    a, p = oracle.direct(pos, np.array([1.0, 1.0]), e, targets=[0], kind=kind)
+    return a[0, 0], p[0]
+
+
+def test_spline_newton_beyond_support():
+    """At r >= h = 2.8 eps the spline field is Newton's exactly."""
+    e = 0.01
+    for r in (0.028, 0.03, 0.5, 7.0):
+        a, p = _pair(r, e)
+        assert abs(a - 1.0 / r ** 2) <= 1e-14 / r ** 2 and abs(p + 1.0 / r) <= 1e-14 / r
+
+
+def test_spline_centre_and_continuity():
+    """phi(0) = -m/eps (the Plummer-equivalent length: -2.8 m / h); a(0) = 0;
+    force and potential are continuous at u = 1/2 and u = 1."""
+    e = 0.01
+    h = 2.8 * e
+    a0, p0 = _pair(0.0, e)
+    assert a0 == 0.0 and abs(p0 + 1.0 / e) <= 1e-12 / e
+    for u in (0.5, 1.0):
+        lo = _pair(u * h * (1 - 1e-10), e)
+        hi = _pair(u * h * (1 + 1e-10), e)
+        assert abs(lo[0] - hi[0]) <= 1e-8 * abs(hi[0]) and abs(lo[1] - hi[1]) <= 1e-8 * abs(hi[1])
+
+
+def test_spline_force_is_minus_gradient_and_mass_is_enclosed():
+    """a(r) = -dphi/dr (central differences), and r^2 a(r) -- the kernel's
+    enclosed mass -- grows from 0 to m at r = h."""
+    e = 0.01
+    h = 2.8 * e
+    for u in (0.1, 0.3, 0.45, 0.55, 0.7, 0.95):
+        r, d = u * h, 1e-6 * h
+        a, _ = _pair(r, e)
+        dp = (_pair(r + d, e)[1] - _pair(r - d, e)[1]) / (2 * d)
+        assert abs(a - dp) <= 1e-6 * abs(a), (u, a, dp)
+    enc = [(_pair(u * h, e)[0]) * (u * h) ** 2 for u in np.linspace(0.05, 1.0, 20)]
+    assert np.all(np.diff(enc) > 0) and abs(enc[-1] - 1.0) < 1e-12
+
+
+def test_spline_tree_matches_direct(plummer_case):
+    """The tree with spline softening at small theta equals the spline direct
+    sum; at theta 0.5 it stays within 1e-3 at p99."""
+    p32, m32, _, _ = plummer_case
+    ad, pd = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), 0.01, kind=1)
+    T = oracle.Tree(p32, m32, 16, 32)
+    a, p, _, _ = T.forces(1e-6, 0.01, kind=1)
+    assert oracle.rel_err(a, ad).max() < 1e-12
+    np.testing.assert_allclose(p, pd, rtol=1e-12)
+    a, _, _, _ = T.forces(0.5, 0.01, kind=1)
+    assert oracle.percentile(oracle.rel_err(a, ad), 0.99) <= 1e-3
