@@ -67,7 +67,11 @@ typedef struct rv_ctx rv_ctx; /* opaque; owned by librv */
  *              accelerations (the previous pass's) as references; groups
  *              without a reference yet (|a| = 0) and the chain's
  *              centre-of-mass particles use theta.
- *   alpha      tolerance of the relative criterion (>= 0). */
+ *   alpha      tolerance of the relative criterion (>= 0).
+ *   softening  0 = Plummer (Sect. 3); 1 = spline (the "spline" option of
+ *              Sect. 2): the cubic-spline field of support h = 2.8 eps_star
+ *              (phi(0) = -m/eps_star as for Plummer), Newton beyond h; cells
+ *              closer than h act as spline monopoles. */
 typedef struct {
     float theta;
     float eps_star;
@@ -77,10 +81,11 @@ typedef struct {
     int32_t tile;
     int32_t mac;
     float alpha;
+    int32_t softening;
 } rv_config;
 
 /* Fills *cfg with the defaults: theta 0.5, eps 0.01, n_leaf 16, group 32,
- * quadrupole 1, tile 64, mac 0, alpha 1e-3. */
+ * quadrupole 1, tile 64, mac 0, alpha 1e-3, softening 0. */
 void rv_default_config(rv_config *cfg);
 
 /* Bytes of device workspace a context needs for up to n_max stars (0 if the

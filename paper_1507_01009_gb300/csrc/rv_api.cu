@@ -101,7 +101,7 @@ static bool config_ok(const rv_config *cfg) {
     return cfg && cfg->theta >= 0.f && cfg->theta < 2.f && cfg->eps_star >= 0.f && cfg->n_leaf >= 1 &&
            cfg->n_leaf <= 64 && cfg->group >= 1 && cfg->group <= kMaxGroup && (cfg->quadrupole == 0 || cfg->quadrupole == 1) &&
            cfg->tile >= 32 && cfg->tile <= 256 && cfg->tile % 32 == 0 && (cfg->mac == 0 || cfg->mac == 1) &&
-           cfg->alpha >= 0.f && cfg->alpha < 3e38f;
+           cfg->alpha >= 0.f && cfg->alpha < 3e38f && (cfg->softening == 0 || cfg->softening == 1);
 }
 
 static bool ready(rv_ctx *c) { return c && c->ws; }
@@ -122,6 +122,7 @@ void rv_default_config(rv_config *cfg) {
     cfg->tile = 64;
     cfg->mac = 0;
     cfg->alpha = 1e-3f;
+    cfg->softening = 0;
 }
 
 size_t rv_workspace_size(int64_t n_max, const rv_config *cfg) {

@@ -54,6 +54,11 @@
 
 namespace rv {
 
+// spline softening lengths (h = 2.8 eps): h^2, 1/h, 1/h^3
+struct Spline {
+    float h2, hinv, hinv3;
+};
+
 struct WalkArgs {
     const float4 *pos;   // sorted (x, y, z, m)
     const int4 *cbox;
@@ -90,6 +95,8 @@ struct WalkArgs {
     const float *arx, *ary, *arz;
     // optional group mask (block time steps): only groups with gact[g] != 0 are walked
     const uint8_t *gact;
+    // spline softening of the stars (h = 2.8 eps)
+    Spline spl;
 };
 
 // Per-warp shared memory: stack | lane_cell[32] | cell staging | star staging.
@@ -183,10 +190,62 @@ __device__ __forceinline__ void add_tile(Acc &A, f2 tx, f2 ty, f2 tz, f2 tp) {
     nadd(A.ph, A.cp, -f2_sum(tp));
 }
 
+// Spline softening (the "spline" option of Sect. 2): the point mass smoothed
+// by the cubic spline kernel of support h = 2.8 eps, so that phi(0) = -m/eps
+// as for Plummer softening of length eps. From the kernel's enclosed mass,
+// a = m d f(u) / h^3 and phi = (m/h) P(u) with u = |d| / h:
+//   u < 1/2:  f = 32/3 - 192/5 u^2 + 32 u^3,  P = -14/5 + 16/3 u^2 - 48/5 u^4 + 32/5 u^5
+//   u < 1:    f = 64/3 - 48 u + 192/5 u^2 - 32/3 u^3 - 1/(15 u^3),
+//             P = -16/5 + 1/(15 u) + 32/3 u^2 - 16 u^3 + 48/5 u^4 - 32/15 u^5
+//   u >= 1:   Newton.
+
+
+// m f / h^3 and -m P / h (the walk sums -phi) for one pair at squared distance r2 < h^2
+__device__ __forceinline__ void spline_terms(float r2, float m, const Spline &S, float &mr3, float &mr) {
+    const float u = sqrtf(r2) * S.hinv;
+    const float u2 = u * u;
+    float f, P;
+    if (u < 0.5f) {
+        f = fmaf(u2, fmaf(32.f, u, -192.f / 5.f), 32.f / 3.f);
+        P = fmaf(u2, fmaf(u2, fmaf(32.f / 5.f, u, -48.f / 5.f), 16.f / 3.f), -14.f / 5.f);
+    } else {
+        const float iu = 1.f / u;
+        f = fmaf(u2, fmaf(-32.f / 3.f, u, 192.f / 5.f), fmaf(-48.f, u, 64.f / 3.f)) - (1.f / 15.f) * (iu * iu * iu);
+        P = fmaf(u2, fmaf(u, fmaf(u, fmaf(-32.f / 15.f, u, 48.f / 5.f), -16.f), 32.f / 3.f),
+                 fmaf(1.f / 15.f, iu, -16.f / 5.f));
+    }
+    mr3 = m * f * S.hinv3;
+    mr = -m * P * S.hinv;
+}
+
+// One packed pair of star-star terms under spline softening: Newton beyond h,
+// the kernel's field inside (per element).
+__device__ __forceinline__ void spline_pair(f2 r2, f2 m2, const Spline &S, f2 &mr, f2 &mr3) {
+    float ra, rb, ma, mb;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(ra), "=f"(rb) : "l"(r2));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(ma), "=f"(mb) : "l"(m2));
+    float o3[2], o1[2];
+    const float rr[2] = {ra, rb}, mm[2] = {ma, mb};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        if (rr[h] >= S.h2) {
+            const float ri = rsqrtf(rr[h]);
+            o1[h] = mm[h] * ri;
+            o3[h] = o1[h] * (ri * ri);
+        } else {
+            spline_terms(rr[h], mm[h], S, o3[h], o1[h]);
+        }
+    }
+    mr = f2_pack(o1[0], o1[1]);
+    mr3 = f2_pack(o3[0], o3[1]);
+}
+
 // Star pairs 0 .. npair-1 of a staged star list on this lane's targets:
-//   d = x_j - x_i, a += m_j d / (d.d + e^2)^{3/2}, phi -= m_j / (d.d + e^2)^{1/2}.
-template <bool SOFT>
-__device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc *A) {
+//   d = x_j - x_i, a += m_j d / (d.d + e^2)^{3/2}, phi -= m_j / (d.d + e^2)^{1/2}
+// (SPL: the spline field instead).
+template <bool SOFT, bool SPL>
+__device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt &t, f2 eps2, const Spline &S,
+                                         Acc *A) {
     f2 tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0}, tp[2] = {0, 0};   // tp sums +m/r
 #pragma unroll kP2PUnroll
     for (int j = t.j0; j < npair; j += t.k) {
@@ -195,10 +254,16 @@ __device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             f2 dx = f2_add(a.x, t.nx[q]), dy = f2_add(a.y, t.ny[q]), dz = f2_add(b.x, t.nz[q]);
-            f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
-            f2 rinv = f2_rsqrt(r2, !SOFT);
-            f2 mr = f2_mul(b.y, rinv);
-            f2 mr3 = f2_mul(mr, f2_mul(rinv, rinv));
+            f2 mr, mr3;
+            if (SPL) {
+                f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+                spline_pair(r2, b.y, S, mr, mr3);
+            } else {
+                f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
+                f2 rinv = f2_rsqrt(r2, !SOFT);
+                mr = f2_mul(b.y, rinv);
+                mr3 = f2_mul(mr, f2_mul(rinv, rinv));
+            }
             tx[q] = f2_fma(mr3, dx, tx[q]);
             ty[q] = f2_fma(mr3, dy, ty[q]);
             tz[q] = f2_fma(mr3, dz, tz[q]);
@@ -213,10 +278,14 @@ __device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt
 // d = com - x_i = -r, rho^2 = d.d + e^2, the staged -Q gives q = -Q d = Q r
 // and s = d.q / rho^4 = -(r.Q.r) / rho^4, so that
 //   a += (M - 5/2 s) d / rho^3 + q / rho^5,  phi -= (M - s/2) / rho,
-// which is the monopole + quadrupole expansion of the file header.
-template <bool QUAD>
-__device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt &t, f2 eps2, Acc *A) {
+// which is the monopole + quadrupole expansion of the file header. SPL: the
+// unsoftened expansion (e = 0), and a cell closer than h acts as the spline
+// monopole.
+template <bool QUAD, bool SPL>
+__device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt &t, f2 eps2, const Spline &S,
+                                         Acc *A) {
     f2 tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0}, tp[2] = {0, 0};   // tp sums +(M - s/2)/rho
+    if (SPL) eps2 = 0;
 #pragma unroll kM2PUnroll
     for (int j = t.j0; j < npair; j += t.k) {
         const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(src) + kCellPairF4 * j;
@@ -236,6 +305,7 @@ __device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt
             f2 rinv = f2_rsqrt(r2, false);
             f2 u = f2_mul(rinv, rinv);
             f2 rinv3 = f2_mul(rinv, u);
+            f2 ix, iy, iz, ip;   // this pair's terms
             if (QUAD) {
                 f2 qx = f2_fma(c.x, dx, f2_fma(e.y, dy, f2_mul(f.x, dz)));
                 f2 qy = f2_fma(e.y, dx, f2_fma(c.y, dy, f2_mul(f.y, dz)));
@@ -244,16 +314,67 @@ __device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt
                 f2 sw = f2_mul(dq, f2_mul(u, u));
                 f2 rinv5 = f2_mul(rinv3, u);
                 f2 B = f2_mul(rinv3, f2_fma(kF2MinusFiveHalf, sw, a.x));
-                tx[q] = f2_fma(B, dx, f2_fma(rinv5, qx, tx[q]));
-                ty[q] = f2_fma(B, dy, f2_fma(rinv5, qy, ty[q]));
-                tz[q] = f2_fma(B, dz, f2_fma(rinv5, qz, tz[q]));
-                tp[q] = f2_fma(rinv, f2_fma(kF2MinusHalf, sw, a.x), tp[q]);
+                if (!SPL) {
+                    tx[q] = f2_fma(B, dx, f2_fma(rinv5, qx, tx[q]));
+                    ty[q] = f2_fma(B, dy, f2_fma(rinv5, qy, ty[q]));
+                    tz[q] = f2_fma(B, dz, f2_fma(rinv5, qz, tz[q]));
+                    tp[q] = f2_fma(rinv, f2_fma(kF2MinusHalf, sw, a.x), tp[q]);
+                    continue;
+                }
+                ix = f2_fma(B, dx, f2_mul(rinv5, qx));
+                iy = f2_fma(B, dy, f2_mul(rinv5, qy));
+                iz = f2_fma(B, dz, f2_mul(rinv5, qz));
+                ip = f2_mul(rinv, f2_fma(kF2MinusHalf, sw, a.x));
             } else {
                 f2 mr3 = f2_mul(a.x, rinv3);
-                tx[q] = f2_fma(mr3, dx, tx[q]);
-                ty[q] = f2_fma(mr3, dy, ty[q]);
-                tz[q] = f2_fma(mr3, dz, tz[q]);
-                tp[q] = f2_fma(a.x, rinv, tp[q]);
+                if (!SPL) {
+                    tx[q] = f2_fma(mr3, dx, tx[q]);
+                    ty[q] = f2_fma(mr3, dy, ty[q]);
+                    tz[q] = f2_fma(mr3, dz, tz[q]);
+                    tp[q] = f2_fma(a.x, rinv, tp[q]);
+                    continue;
+                }
+                ix = f2_mul(mr3, dx);
+                iy = f2_mul(mr3, dy);
+                iz = f2_mul(mr3, dz);
+                ip = f2_mul(a.x, rinv);
+            }
+            if (SPL) {
+                float ra, rb;
+                asm("mov.b64 {%0, %1}, %2;" : "=f"(ra), "=f"(rb) : "l"(r2));
+                if (ra < S.h2 || rb < S.h2) {   // a cell closer than h: the spline monopole
+                    float m0, m1, o3, o1;
+                    asm("mov.b64 {%0, %1}, %2;" : "=f"(m0), "=f"(m1) : "l"(a.x));
+                    float v[4][2];
+                    const f2 in4[4] = {ix, iy, iz, ip};
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(v[k][0]), "=f"(v[k][1]) : "l"(in4[k]));
+                    float dd[3][2];
+                    const f2 d3[3] = {dx, dy, dz};
+#pragma unroll
+                    for (int k = 0; k < 3; k++)
+                        asm("mov.b64 {%0, %1}, %2;" : "=f"(dd[k][0]), "=f"(dd[k][1]) : "l"(d3[k]));
+                    const float rr[2] = {ra, rb}, mm[2] = {m0, m1};
+#pragma unroll
+                    for (int hh = 0; hh < 2; hh++) {
+                        if (rr[hh] < S.h2) {
+                            spline_terms(rr[hh], mm[hh], S, o3, o1);
+                            v[0][hh] = o3 * dd[0][hh];
+                            v[1][hh] = o3 * dd[1][hh];
+                            v[2][hh] = o3 * dd[2][hh];
+                            v[3][hh] = o1;
+                        }
+                    }
+                    ix = f2_pack(v[0][0], v[0][1]);
+                    iy = f2_pack(v[1][0], v[1][1]);
+                    iz = f2_pack(v[2][0], v[2][1]);
+                    ip = f2_pack(v[3][0], v[3][1]);
+                }
+                tx[q] = f2_add(tx[q], ix);
+                ty[q] = f2_add(ty[q], iy);
+                tz[q] = f2_add(tz[q], iz);
+                tp[q] = f2_add(tp[q], ip);
             }
         }
     }
@@ -295,7 +416,7 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 // mass are (cell centre - g) + (centre of mass - cell centre). Differences of
 // nearby FP32 coordinates are exact, so FP32 keeps its relative precision at
 // any distance from the origin.
-template <bool SOFT, bool QUAD, bool REC, bool REL>
+template <bool SOFT, bool QUAD, bool REC, bool REL, bool SPL>
 __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
                                            const unsigned long long *thr_rec, int gid, char *wsm, const int blo[3],
                                            const int bhi[3], const float g[3], const Tgt &tg, f2 eps2, Acc *acc,
@@ -461,7 +582,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                 np2p += cc;
                 if (np >= T) {
                     __syncwarp();
-                    eval_p2p<SOFT>(p2p, T / 2, tg, eps2, acc);
+                    eval_p2p<SOFT, SPL>(p2p, T / 2, tg, eps2, A.spl, acc);
                     __syncwarp();
                     // T is even: the leftover entries move pair by pair
                     if (lane < (np - T + 1) / 2) {
@@ -475,7 +596,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         }
         if (nm >= T) {
             __syncwarp();
-            eval_m2p<QUAD>(m2p, T / 2, tg, eps2, acc);
+            eval_m2p<QUAD, SPL>(m2p, T / 2, tg, eps2, A.spl, acc);
             __syncwarp();
             if (lane < (nm - T + 1) / 2) {
 #pragma unroll
@@ -491,8 +612,8 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         pad_stars(p2p, np);
         pad_cells(m2p, nm);
         __syncwarp();
-        if (np > 0) eval_p2p<SOFT>(p2p, (np + 1) / 2, tg, eps2, acc);
-        if (nm > 0) eval_m2p<QUAD>(m2p, (nm + 1) / 2, tg, eps2, acc);
+        if (np > 0) eval_p2p<SOFT, SPL>(p2p, (np + 1) / 2, tg, eps2, A.spl, acc);
+        if (nm > 0) eval_m2p<QUAD, SPL>(m2p, (nm + 1) / 2, tg, eps2, A.spl, acc);
     }
     __syncwarp();
     if (lane == 0) atomicMax(&A.st->stack_hwm, hwm);
@@ -557,7 +678,7 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
 // Work items 0 .. n_extra-1 are the extra particles (one-star groups whose box
 // is their own grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited
 // to +-2^23); the tree's groups follow.
-template <bool SOFT, bool QUAD, bool REC, bool REL>
+template <bool SOFT, bool QUAD, bool REC, bool REL, bool SPL>
 __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree_k(WalkArgs A) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -607,7 +728,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             tg.k = 32;
             bool ok = true;
             if (G.ncell > 0 && G.root >= 0)
-                ok = walk_group<false, QUAD, false, false>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, tg,
+                ok = walk_group<false, QUAD, false, false, false>(A, G, mac_thr, rec_thr, -1, wsm, blo, bhi, g, tg,
                                                            f2_pack(e * e, e * e), acc, a2, a3, -1.f);
             if (!ok) {
                 if (lane == 0) latch_err(A.st, kErrStack);
@@ -673,7 +794,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             for (int o = 16; o > 0; o >>= 1) am = fminf(am, __shfl_xor_sync(0xffffffffu, am, o));
             if (am > 0.f) K = __fmul_rn(__fmul_rn(A.rel_alpha, am), __fmul_rn(G.unit, G.unit));
         }
-        bool ok = walk_group<SOFT, QUAD, REC, REL>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, tg,
+        bool ok = walk_group<SOFT, QUAD, REC, REL, SPL>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, tg,
                                                    f2_pack(A.eps2, A.eps2), acc, a2, a3, K);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
@@ -725,10 +846,10 @@ MacTable mac_table(float theta) {
     return t;
 }
 
-template <bool SOFT, bool QUAD, bool REC, bool REL = false>
+template <bool SOFT, bool QUAD, bool REC, bool REL = false, bool SPL = false>
 static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
     size_t smem = warp_smem_bytes(A.tile) * kWalkWarps;
-    auto kern = walk_tree_k<SOFT, QUAD, REC, REL>;
+    auto kern = walk_tree_k<SOFT, QUAD, REC, REL, SPL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -774,6 +895,13 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.pair_cap = rec ? rec->cap : 0;
     if (rec) A.rec = mac_table(rec->theta_rec);
     A.gact = gact;
+    const bool spline = c->cfg.softening == 1 && eps_star > 0.f;
+    {
+        const float h = 2.8f * eps_star;
+        A.spl.h2 = h * h;
+        A.spl.hinv = spline ? 1.f / h : 0.f;
+        A.spl.hinv3 = A.spl.hinv * A.spl.hinv * A.spl.hinv;
+    }
     A.rel_alpha = rel ? rel->alpha : 0.f;
     A.arx = rel ? rel->rx : nullptr;
     A.ary = rel ? rel->ry : nullptr;
@@ -808,7 +936,15 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
         }
     }
     if (ev0) cudaEventRecord(ev0, s);
-    if (rel) {
+    if (spline) {
+        if (rec) return set_err(c, RV_E_INVAL, "no pair record with spline softening");
+        if (rel)
+            e = quad ? launch_walk<true, true, false, true, true>(c, A, s)
+                     : launch_walk<true, false, false, true, true>(c, A, s);
+        else
+            e = quad ? launch_walk<true, true, false, false, true>(c, A, s)
+                     : launch_walk<true, false, false, false, true>(c, A, s);
+    } else if (rel) {
         if (eps_star > 0.f)
             e = quad ? launch_walk<true, true, false, true>(c, A, s) : launch_walk<true, false, false, true>(c, A, s);
         else

@@ -42,7 +42,8 @@ class RvError(RuntimeError):
 
 class rv_config(C.Structure):
     _fields_ = [("theta", C.c_float), ("eps_star", C.c_float), ("n_leaf", C.c_int32), ("group", C.c_int32),
-                ("quadrupole", C.c_int32), ("tile", C.c_int32), ("mac", C.c_int32), ("alpha", C.c_float)]
+                ("quadrupole", C.c_int32), ("tile", C.c_int32), ("mac", C.c_int32), ("alpha", C.c_float),
+                ("softening", C.c_int32)]
 
 
 class rv_blocks(C.Structure):
@@ -196,11 +197,13 @@ class Context:
     """An rv_ctx with a torch-allocated workspace on the current device."""
 
     def __init__(self, n_max: int, theta: float = 0.5, eps_star: float = 0.01, n_leaf: int = 16,
-                 group: int = 32, quadrupole: bool = True, tile: int = 64, mac: int = 0, alpha: float = 1e-3):
+                 group: int = 32, quadrupole: bool = True, tile: int = 64, mac: int = 0, alpha: float = 1e-3,
+                 softening: int = 0):
         import torch
         self.L = load()
         self.cfg = default_config(theta=theta, eps_star=eps_star, n_leaf=n_leaf, group=group,
-                                  quadrupole=int(bool(quadrupole)), tile=tile, mac=int(mac), alpha=float(alpha))
+                                  quadrupole=int(bool(quadrupole)), tile=tile, mac=int(mac), alpha=float(alpha),
+                                  softening=int(softening))
         self.n_max = int(n_max)
         h = C.c_void_p()
         st = self.L.rv_create(C.byref(h), self.n_max, C.byref(self.cfg))

@@ -510,3 +510,38 @@ def test_chain_perturber_forces_predicted(rvmod):
         got = a.cpu().numpy().reshape(-1, 3)
         assert np.abs(got - o["a_chain"]).max() <= 1e-12 * np.abs(o["a_chain"]).max()
         np.testing.assert_allclose(pot.cpu().numpy(), o["pot_chain"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind,n,theta,n_leaf,G,tile,quad,rel", [("plummer", 4096, 0.5, 16, 32, 64, True, False),
+                                                                  ("hernquist", 65536, 0.5, 16, 64, 128, True, False),
+                                                                  ("two_clusters", 3000, 0.6, 8, 47, 32, False, False),
+                                                                  ("hernquist", 65536, 1e-3, 32, 64, 128, True, True)])
+def test_spline_softening_vs_oracle(rvmod, kind, n, theta, n_leaf, G, tile, quad, rel):
+    """Spline softening (h = 2.8 eps) on the GPU against the oracle tree with the
+    same softening (same opening decisions: identical interaction counts), and
+    against the spline direct sum."""
+    p32, m32 = _inputs(kind, n)
+    eps = float(np.float32(0.005 if kind != "plummer" else 0.01))
+    ctx = _ctx(rvmod, n, theta=theta if not rel else 0.5, eps_star=eps, n_leaf=n_leaf, group=G, tile=tile,
+               quadrupole=quad, softening=1)
+    gpu_tree(ctx, p32, m32)
+    ad, pd = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), eps, kind=1)
+    T = oracle.Tree(p32, m32, n_leaf, G)
+    if rel:
+        aref = ad.astype(np.float32)
+        ax, ay, az, pot = ctx.tree_forces_rel(theta, tuple(to_dev(np.ascontiguousarray(aref[k])) for k in range(3)))
+        ao, po, _, _, cnt = T.forces(0.5, eps, quad, counts=True, rel=(theta, aref), kind=1)
+    else:
+        ax, ay, az, pot = ctx.tree_forces(theta=theta, eps_star=eps)
+        ao, po, _, _, cnt = T.forces(theta, eps, quad, counts=True, kind=1)
+    ctx.sync_status()
+    a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)
+    p = pot.cpu().numpy().astype(np.float64)
+    med, p99, mx = err_stats(a, ao)
+    assert med <= MED_TOL and mx <= MAX_TOL, (med, p99, mx)
+    ep = np.abs(p - po) / np.abs(po)
+    assert np.median(ep) <= MED_TOL and ep.max() <= MAX_TOL
+    n_p2p, n_m2p = ctx.walk_stats()
+    assert n_p2p == int(cnt[:, 0].sum()) + n and n_m2p == int(cnt[:, 1].sum())
+    if quad:
+        assert err_stats(a, ad)[1] <= P99_DIRECT
