@@ -305,6 +305,21 @@ rv_status rv_select_perturbers(rv_ctx *ctx, int64_t n, const float *x, const flo
                                const float centre[3], int32_t mode, float radius, int32_t k, int32_t cap,
                                int32_t *idx, int32_t *count, void *stream);
 
+/* The chain's start radius (Eq. 1): r_chain,0 = max(alpha r_infl, beta eps)
+ * with r_infl = min(r(<2 M_bh), G M_bh / sigma^2) around `centre` (host
+ * FP32, the SMBH), sigma the velocity dispersion of the n_sigma (Sect. 2: 50)
+ * nearest stars. Stars (device FP32, caller order) in ascending FP32 squared
+ * distance, ties by index; r(<2 M_bh) = the distance of the star at which
+ * the FP64 running mass in that order first reaches 2 m_bh (infinity if
+ * never); sigma = sqrt(sum |v - <v>|^2 / (3 k)) over the k = min(n_sigma, n)
+ * nearest, FP64 sums in distance order. Writes host out[5] = r(<2 M_bh),
+ * sigma, G M_bh / sigma^2, r_infl, r_chain,0. Synchronises `stream`; the tree
+ * must be rebuilt afterwards (shared sort buffers). */
+rv_status rv_chain_start_radius(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z,
+                                const float *vx, const float *vy, const float *vz, const float *m,
+                                const float centre[3], double m_bh, int32_t n_sigma, double alpha, double beta,
+                                double eps, double out[5], void *stream);
+
 /* Tidal perturber search (Eq. 2): star j (device FP32 x, y, z, m [n]) perturbs
  * a chain of total mass m_chain centred at `centre` (host FP32) when
  *   r_j < (2 m_j / (gamma_crit m_chain))^(1/3) r_crit.

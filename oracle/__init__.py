@@ -77,6 +77,7 @@ def _declare(L):
     L.orc_knn.restype = C.c_int64
     L.orc_radius.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_float, C.c_int64, _i64]
     L.orc_radius.restype = C.c_int64
+    L.orc_influence.argtypes = [C.c_int64, _f, _f, _f, _f, _f, _f, _f, _f, C.c_double, C.c_int64, _d]
     L.orc_tidal.argtypes = [C.c_int64, _f, _f, _f, _f, _f, C.c_float, C.c_float, C.c_float, C.c_int64, _i64]
     L.orc_tidal.restype = C.c_int64
 
@@ -291,6 +292,23 @@ def radius(pos32, centre32, r2_32):
     out = np.zeros(max(n, 1), dtype=np.int64)
     got = lib().orc_radius(n, _p(x, _f), _p(y, _f), _p(z, _f), _p(c, _f), np.float32(r2_32), n, _p(out, _i64))
     return out[:got]
+
+
+def chain_start_radius(pos32, vel32, mass32, centre32, m_bh, alpha, beta, eps, n_sigma=50):
+    """The chain's start radius of Eq. 1, r_chain,0 = max(alpha r_infl, beta eps),
+    r_infl = min(r(<2 M_bh), G M_bh / sigma^2), sigma the velocity dispersion
+    of the n_sigma nearest stars (see orc_influence for the exact rule).
+    Returns dict r2m, sigma, r_sigma, r_infl, r_chain0."""
+    x, y, z = (_c(pos32[a], np.float32) for a in range(3))
+    vx, vy, vz = (_c(vel32[a], np.float32) for a in range(3))
+    m = _c(mass32, np.float32)
+    c = _c(centre32, np.float32)
+    out = np.zeros(3)
+    lib().orc_influence(x.shape[0], *[_p(a, _f) for a in (x, y, z, vx, vy, vz, m, c)], float(m_bh), int(n_sigma),
+                        _p(out, _d))
+    r_infl = min(out[0], out[2])
+    return {"r2m": out[0], "sigma": out[1], "r_sigma": out[2], "r_infl": r_infl,
+            "r_chain0": max(alpha * r_infl, beta * eps)}
 
 
 def tidal(pos32, mass32, centre32, mchain32, gamma, rcrit):

@@ -762,6 +762,47 @@ int64_t orc_knn(int64_t n, const float *x, const float *y, const float *z, const
     return k;
 }
 
+/* Ingredients of the chain's start radius (Eq. 1) around a centre c (FP32):
+ * stars in ascending FP32 squared distance (ties by index, as orc_knn);
+ * out[0] = r(<2 M_bh): the distance (sqrt of the FP64 value of the FP32 d2)
+ *          of the star at which the running FP64 sum of masses, taken in that
+ *          order, first reaches 2 m_bh (infinity if it never does);
+ * out[1] = sigma: the 1D velocity dispersion of the n_sigma nearest stars,
+ *          sqrt(sum |v - <v>|^2 / (3 k)), k = min(n_sigma, n), all sums in
+ *          FP64 in distance order (<v> their mean velocity);
+ * out[2] = G m_bh / sigma^2 (G = 1). */
+void orc_influence(int64_t n, const float *x, const float *y, const float *z, const float *vx, const float *vy,
+                   const float *vz, const float *m, const float c[3], double m_bh, int64_t n_sigma, double out[3]) {
+    fd *t = (fd *)malloc(sizeof(fd) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) { t[i].d2 = dist2_f32(x[i], y[i], z[i], c[0], c[1], c[2]); t[i].idx = i; }
+    qsort(t, (size_t)n, sizeof(fd), fd_cmp);
+    double cum = 0.0;
+    out[0] = INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        cum += (double)m[t[i].idx];
+        if (cum >= 2.0 * m_bh) { out[0] = sqrt((double)t[i].d2); break; }
+    }
+    int64_t k = n_sigma < n ? n_sigma : n;
+    double mx = 0.0, my = 0.0, mz = 0.0;
+    for (int64_t i = 0; i < k; i++) {
+        int64_t j = t[i].idx;
+        mx += (double)vx[j]; my += (double)vy[j]; mz += (double)vz[j];
+    }
+    mx /= (double)k; my /= (double)k; mz /= (double)k;
+    double s = 0.0;
+    for (int64_t i = 0; i < k; i++) {
+        int64_t j = t[i].idx;
+        double dx = (double)vx[j] - mx, dy = (double)vy[j] - my, dz = (double)vz[j] - mz;
+        s += dx * dx;
+        s += dy * dy;
+        s += dz * dz;
+    }
+    double s2 = s / (3.0 * (double)k);
+    out[1] = sqrt(s2);
+    out[2] = m_bh / s2;
+    free(t);
+}
+
 /* Tidal perturber criterion (Eq. 2): particle j perturbs a chain of total
  * mass M when r_j < (2 m_j / (gamma M))^(1/3) r_crit, r_j its distance to the
  * chain's centre. Taken without a cube root, in FP64 with one rounding per

@@ -102,6 +102,41 @@ __global__ void sel_knn_write_k(const int *sorted_idx, int64_t n, int k, int *id
     }
 }
 
+// Eq. 1 ingredients from the stars sorted by FP32 squared distance (keys =
+// the d2 bits, ties by index): r(<2 M_bh), sigma of the k nearest, M_bh / sigma^2.
+// One thread, sums in distance order in FP64, exactly as the rule reads.
+__global__ void influence_k(int64_t n, const uint64_t *skey, const int *sidx, const float *vx, const float *vy,
+                            const float *vz, const float *m, double m_bh, int64_t k, double *out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double cum = 0.0, r2m = __longlong_as_double(0x7ff0000000000000ll);
+    for (int64_t i = 0; i < n; i++) {
+        cum = __dadd_rn(cum, (double)m[sidx[i]]);
+        if (cum >= 2.0 * m_bh) {
+            r2m = __dsqrt_rn((double)__uint_as_float((unsigned)skey[i]));
+            break;
+        }
+    }
+    double mx = 0.0, my = 0.0, mz = 0.0;
+    for (int64_t i = 0; i < k; i++) {
+        const int j = sidx[i];
+        mx = __dadd_rn(mx, (double)vx[j]); my = __dadd_rn(my, (double)vy[j]); mz = __dadd_rn(mz, (double)vz[j]);
+    }
+    mx = __ddiv_rn(mx, (double)k); my = __ddiv_rn(my, (double)k); mz = __ddiv_rn(mz, (double)k);
+    double s = 0.0;
+    for (int64_t i = 0; i < k; i++) {
+        const int j = sidx[i];
+        const double dx = __dsub_rn((double)vx[j], mx), dy = __dsub_rn((double)vy[j], my),
+                     dz = __dsub_rn((double)vz[j], mz);
+        s = __dadd_rn(s, __dmul_rn(dx, dx));
+        s = __dadd_rn(s, __dmul_rn(dy, dy));
+        s = __dadd_rn(s, __dmul_rn(dz, dz));
+    }
+    const double s2 = __ddiv_rn(s, __dmul_rn(3.0, (double)k));
+    out[0] = r2m;
+    out[1] = __dsqrt_rn(s2);
+    out[2] = __ddiv_rn(m_bh, s2);
+}
+
 static int grid_n(rv_ctx *c, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8));
 }
@@ -141,6 +176,25 @@ rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y
         count_launch(c);
     }
     return cuda_check(c, cudaGetLastError(), "select perturbers");
+}
+
+rv_status influence_radius(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *vx,
+                           const float *vy, const float *vz, const float *m, const float centre[3], double m_bh,
+                           int64_t n_sigma, double out[3], cudaStream_t s) {
+    Workspace &w = c->w;
+    c->built = false;   // the sort buffers are shared with the tree build
+    sel_knn_keys_k<<<grid_n(c, n), 256, 0, s>>>(n, x, y, z, nullptr, make_float3(centre[0], centre[1], centre[2]),
+                                                w.key_a);
+    count_launch(c);
+    uint64_t *sk;
+    int *si;
+    rv_status r = radix_sort(c, n, 4, &sk, &si, true, s);
+    if (r != RV_OK) return r;
+    influence_k<<<1, 32, 0, s>>>(n, sk, si, vx, vy, vz, m, m_bh, std::min<int64_t>(n_sigma, n), w.out8);
+    count_launch(c);
+    r = cuda_check(c, cudaMemcpyAsync(out, w.out8, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "influence");
+    if (r == RV_OK) r = cuda_check(c, cudaStreamSynchronize(s), "influence");
+    return r;
 }
 
 // ---------------------------------------------------------------------------

@@ -423,6 +423,26 @@ rv_status rv_block_count(rv_ctx *c, int64_t *active_updates, void *stream) {
     return r;
 }
 
+rv_status rv_chain_start_radius(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *vx,
+                                const float *vy, const float *vz, const float *m, const float centre[3], double m_bh,
+                                int32_t n_sigma, double alpha, double beta, double eps, double out[5], void *stream) {
+    if (!c) return RV_E_INVAL;
+    if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
+    if (n < 1 || n > c->n_max || !x || !y || !z || !vx || !vy || !vz || !m || !centre || !out || n_sigma < 1 ||
+        !(m_bh > 0.0))
+        return set_err(c, RV_E_INVAL, "bad chain start radius arguments");
+    double o3[3];
+    rv_status r = influence_radius(c, n, x, y, z, vx, vy, vz, m, centre, m_bh, n_sigma, o3, (cudaStream_t)stream);
+    if (r != RV_OK) return r;
+    const double r_infl = std::min(o3[0], o3[2]);
+    out[0] = o3[0];
+    out[1] = o3[1];
+    out[2] = o3[2];
+    out[3] = r_infl;
+    out[4] = std::max(alpha * r_infl, beta * eps);
+    return RV_OK;
+}
+
 rv_status rv_select_perturbers_tidal(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
                                      const float *m, const float centre[3], float m_chain, float gamma_crit,
                                      float r_crit, int32_t cap, int32_t *idx, int32_t *count, void *stream) {

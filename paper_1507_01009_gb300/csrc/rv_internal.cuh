@@ -170,6 +170,9 @@ rv_status select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y
                             const float *centre_dev, const float *centre_host, int mode, float radius, int k,
                             int cap, int *idx, int *count, cudaStream_t s, const float *m = nullptr,
                             float gamma = 0.f);
+rv_status influence_radius(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *vx,
+                           const float *vy, const float *vz, const float *m, const float centre[3], double m_bh,
+                           int64_t n_sigma, double out[3], cudaStream_t s);
 rv_status chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, const double *chain_x, double *a_chain,
                                  double *pot_chain, cudaStream_t s);
 rv_status perturber_forces(rv_ctx *c, int n_ch, const double *cm, const double *cx, int n_pert_max,

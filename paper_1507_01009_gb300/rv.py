@@ -27,7 +27,7 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_perturber_forces",
            "rv_system_forces", "rv_kdk_step", "rv_kdk_step_graph", "rv_energy",
            "rv_select_perturbers", "rv_select_perturbers_tidal", "rv_chain_perturber_forces", "rv_select_radius_static",
-           "rv_block_start", "rv_block_steps", "rv_block_levels", "rv_block_count", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
+           "rv_block_start", "rv_block_steps", "rv_block_levels", "rv_block_count", "rv_chain_start_radius", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
            "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
            "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
            "rv_mlp_samples", "rv_tree_forces_mlp"]
@@ -108,6 +108,8 @@ def _declare(L):
     L.rv_kdk_step.argtypes = [vp, C.POINTER(rv_system), f64, i32, vp]
     L.rv_energy.argtypes = [vp, C.POINTER(rv_system), vp, vp]
     L.rv_select_perturbers.argtypes = [vp, i64, vp, vp, vp, C.POINTER(C.c_float), i32, f32, i32, i32, vp, vp, vp]
+    L.rv_chain_start_radius.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_float), C.c_double,
+                                        i32, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double), vp]
     L.rv_block_start.argtypes = [vp, C.POINTER(rv_system), C.POINTER(rv_blocks), vp]
     L.rv_block_steps.argtypes = [vp, C.POINTER(rv_system), C.POINTER(rv_blocks), i32, vp]
     L.rv_block_levels.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, C.POINTER(rv_blocks), i32, vp]
@@ -395,6 +397,16 @@ class Context:
         self._check(self.L.rv_chain_perturber_forces(self.h, C.byref(sysobj.c()), float(dt), _ptr(chain_x),
                                                      _ptr(a_chain), _ptr(pot_chain), _stream(stream)))
         return a_chain, pot_chain
+
+    def chain_start_radius(self, pos, vel, m, centre, m_bh, alpha, beta, eps, n_sigma=50, stream=None) -> dict:
+        """Eq. 1: returns r2m, sigma, r_sigma, r_infl, r_chain0 (pos/vel: CUDA (x, y, z) tuples)."""
+        _need_cuda(*pos, *vel, m)
+        c3 = (C.c_float * 3)(*[float(v) for v in centre])
+        out = (C.c_double * 5)()
+        self._check(self.L.rv_chain_start_radius(self.h, int(m.shape[0]), *[_ptr(t) for t in pos],
+                                                 *[_ptr(t) for t in vel], _ptr(m), c3, float(m_bh), int(n_sigma),
+                                                 float(alpha), float(beta), float(eps), out, _stream(stream)))
+        return dict(zip(("r2m", "sigma", "r_sigma", "r_infl", "r_chain0"), list(out)))
 
     def block_start(self, sysobj, blocks, stream=None):
         b = blocks.c()

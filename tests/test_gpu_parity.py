@@ -545,3 +545,22 @@ def test_spline_softening_vs_oracle(rvmod, kind, n, theta, n_leaf, G, tile, quad
     assert n_p2p == int(cnt[:, 0].sum()) + n and n_m2p == int(cnt[:, 1].sum())
     if quad:
         assert err_stats(a, ad)[1] <= P99_DIRECT
+
+
+def test_chain_start_radius_matches_oracle(rvmod):
+    """Eq. 1 on the GPU and in the oracle: the same distance order (FP32 d2,
+    ties by index) and the same FP64 sums in that order, so r(<2 M_bh), sigma
+    and the derived radii agree to the last bit; and around an off-centre
+    SMBH of a Hernquist galaxy r_infl is the smaller of the two proxies."""
+    w = ics.hernquist_bh_workload(1 << 16, seed=14)
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    v32 = np.ascontiguousarray(w.stars.vel, dtype=np.float32)
+    ctx = _ctx(rvmod, p32.shape[1])
+    pos = tuple(to_dev(p32[a]) for a in range(3))
+    vel = tuple(to_dev(v32[a]) for a in range(3))
+    for centre in (np.zeros(3, np.float32), w.chain.pos[0].astype(np.float32)):
+        got = ctx.chain_start_radius(pos, vel, to_dev(m32), centre, 0.005, 1.2, 1.5, 0.005)
+        ref = oracle.chain_start_radius(p32, v32, m32, centre, 0.005, 1.2, 1.5, 0.005)
+        for k in ("r2m", "sigma", "r_sigma", "r_infl", "r_chain0"):
+            assert got[k] == ref[k], (k, got[k], ref[k])
+        assert got["r_infl"] == min(got["r2m"], got["r_sigma"]) and np.isfinite(got["r2m"])

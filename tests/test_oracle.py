@@ -506,6 +506,31 @@ def test_tidal_selection_closed_form():
     assert np.all(np.diff(sel8) > 0)
 
 
+def test_chain_start_radius_closed_form():
+    """Eq. 1 ingredients on a constructed cluster: stars of mass 0.001 on
+    shells at radius 0.01 k (k = 1, 2, ...), so the running mass reaches
+    2 M_bh = 0.01 at the 10th star; the 50 nearest stars move with velocities
+    +-0.3 along x (mean 0): sigma^2 = 0.09 / 3 = 0.03."""
+    n = 200
+    g = ics.rng(61)
+    dirs = g.normal(size=(3, n))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    r = 0.01 * np.arange(1, n + 1)
+    pos = (dirs * r).astype(np.float32)
+    vel = np.zeros((3, n), np.float32)
+    vel[0, :50] = np.where(np.arange(50) % 2 == 0, 0.3, -0.3)
+    m = np.full(n, 0.001, np.float32)
+    out = oracle.chain_start_radius(pos, vel, m, np.zeros(3, np.float32), 0.005, 1.2, 1.5, 0.01)
+    assert abs(out["r2m"] - 0.10) < 1e-7
+    assert abs(out["sigma"] ** 2 - float(np.float32(0.3)) ** 2 / 3) < 1e-12
+    assert abs(out["r_sigma"] - 0.005 / out["sigma"] ** 2) < 1e-12
+    assert out["r_infl"] == min(out["r2m"], out["r_sigma"])
+    assert abs(out["r_chain0"] - max(1.2 * out["r_infl"], 0.015)) < 1e-15
+    # not enough mass: infinite r(<2M)
+    assert oracle.chain_start_radius(pos[:, :5], vel[:, :5], m[:5], np.zeros(3, np.float32), 0.005, 1, 1,
+                                     0.01)["r2m"] == np.inf
+
+
 def test_knn_and_radius_selection():
     w = ics.hernquist(3000, seed=21)
     p32 = w.pos.astype(np.float32)
