@@ -190,10 +190,13 @@ rv_status rv_perturber_forces(rv_ctx *ctx, int32_t n_ch, const double *chain_m, 
  * [member_offsets[k], member_offsets[k+1]) (host int64 [n_members + 1],
  * offsets[0] = 0, offsets[n_members] = n; n_members <= 1 with
  * member_offsets = NULL means one member of all n stars; at most 512
- * members). Each member has its own tree and, if n_chain > 0, its own chain
- * of n_chain members (device FP64, member-major: chain_m[n_members n_chain],
- * chain_x/v/a[3 n_members n_chain], chain_pot[n_members n_chain]; at most
- * 2048 chain members in total). Perturbers of a chain (stars of its own
+ * members). Each member has its own tree and, if n_chain > 0, n_chains
+ * chains (several distant SMBHs: the paper's outlook, Sect. 7) of n_chain
+ * members each (device FP64, chain-major and member by member:
+ * chain_m[n_members n_chains n_chain], chain_x/v/a[3 ...], chain_pot[...];
+ * at most 2048 chain members and 512 chains in total). Every chain's centre
+ * of mass is an unsoftened particle of its member's tree; the chains of one
+ * member feel each other through these. Perturbers of a chain (stars of its own
  * member): pert_mode 1 = FP32 squared distance to the chain centre below
  * pert_radius^2 (ascending index), 2 = the pert_k nearest (ties by lower
  * index), 3 = the tidal criterion of Eq. 2 with r_crit = pert_radius and
@@ -213,6 +216,7 @@ typedef struct {
     int32_t n_members;
     const int64_t *member_offsets;
     float pert_gamma;
+    int32_t n_chains;  /* chains per member (0 or 1: one); chain c belongs to member c / n_chains */
 } rv_system;
 
 /* One full force evaluation of a system: tree build, perturber selection,

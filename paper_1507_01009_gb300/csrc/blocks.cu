@@ -146,7 +146,7 @@ static int grid_of(rv_ctx *c, int64_t n) {
 
 static void chain_kick(rv_ctx *c, rv_system *sys, double hdt, cudaStream_t s) {
     if (sys->n_chain <= 0) return;
-    const int nc = system_members(sys) * sys->n_chain;
+    const int nc = system_chains(sys) * sys->n_chain;
     chain_kick_k<<<ceil_div(3 * nc, 128), 128, 0, s>>>(nc, sys->chain_v, sys->chain_a, hdt);
     count_launch(c);
 }
@@ -178,7 +178,7 @@ rv_status block_steps(rv_ctx *c, rv_system *sys, rv_blocks *b, int nsub, cudaStr
             count_launch(c);
         }
         if (sys->n_chain > 0) {
-            const int nc = system_members(sys) * sys->n_chain;
+            const int nc = system_chains(sys) * sys->n_chain;
             chain_drift_k<<<ceil_div(3 * nc, 128), 128, 0, s>>>(nc, sys->chain_x, sys->chain_v, dt_min);
             count_launch(c);
         }

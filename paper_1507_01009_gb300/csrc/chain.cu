@@ -205,9 +205,10 @@ rv_status influence_radius(rv_ctx *c, int64_t n, const float *x, const float *y,
 //   radius:    key = 0 inside, 1 outside (inside stars first, ascending index)
 // ---------------------------------------------------------------------------
 __global__ void sel_member_keys_k(const int64_t *moff, int bpm, const float *x, const float *y, const float *z,
-                                  const float *xyzm, SelRule R, uint64_t *key) {
+                                  const float *xyzm, int C, int j, SelRule R, uint64_t *key) {
     const int m = blockIdx.y;
-    const float cx = xyzm[4 * m], cy = xyzm[4 * m + 1], cz = xyzm[4 * m + 2], mc = xyzm[4 * m + 3];
+    const float *q = xyzm + 4 * ((int64_t)m * C + j);   // chain j of member m
+    const float cx = q[0], cy = q[1], cz = q[2], mc = q[3];
     for (int64_t i = moff[m] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < moff[m + 1];
          i += (int64_t)bpm * blockDim.x) {
         float d2 = dist2_f32(x[i], y[i], z[i], cx, cy, cz);
@@ -218,7 +219,7 @@ __global__ void sel_member_keys_k(const int64_t *moff, int bpm, const float *x, 
 // member m: its first min(k, n_m) sorted slots (k nearest), or its leading
 // "inside" slots (radius), written to idx[m cap ..], count to npert[m]
 __global__ void sel_member_write_k(const int64_t *moff, const uint64_t *skey, const int *sidx, int mode, int k,
-                                   int cap, int *idx, int *npert, DevState *st) {
+                                   int cap, int C, int j, int *idx, int *npert, DevState *st) {
     const int m = blockIdx.x;
     const int64_t s = moff[m], e = moff[m + 1];
     int cnt;
@@ -235,8 +236,9 @@ __global__ void sel_member_write_k(const int64_t *moff, const uint64_t *skey, co
     }
     if (cnt > cap && threadIdx.x == 0) latch_err(st, kErrPert);
     cnt = min(cnt, cap);
-    for (int p = threadIdx.x; p < cnt; p += blockDim.x) idx[(int64_t)m * cap + p] = sidx[s + p];
-    if (threadIdx.x == 0) npert[m] = cnt;
+    const int64_t ch = (int64_t)m * C + j;   // chain j of member m
+    for (int p = threadIdx.x; p < cnt; p += blockDim.x) idx[ch * cap + p] = sidx[s + p];
+    if (threadIdx.x == 0) npert[ch] = cnt;
 }
 
 static int member_cap(int M) { return std::min(kMaxPert, kPertTotal / std::max(1, M)); }
@@ -476,7 +478,7 @@ static const int64_t *system_offsets(const rv_system *sys, int64_t tmp[2]);
 rv_status chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, const double *chain_x, double *a_chain,
                                  double *pot_chain, cudaStream_t s) {
     Workspace &w = c->w;
-    const int M = system_members(sys);
+    const int M = system_chains(sys);   // the coupling kernels treat each chain as a unit
     const int cap = member_cap(M);
     predict_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, sys->x, sys->y, sys->z,
                                                                sys->vx, sys->vy, sys->vz, sys->m, dt, w.pert_m,
@@ -496,43 +498,53 @@ static const int64_t *system_offsets(const rv_system *sys, int64_t tmp[2]) {
 }
 
 int system_members(const rv_system *sys) { return std::max(1, (int)sys->n_members); }
+int chains_per_member(const rv_system *sys) { return std::max(1, (int)sys->n_chains); }
+int system_chains(const rv_system *sys) {
+    return sys->n_chain > 0 ? system_members(sys) * chains_per_member(sys) : 0;
+}
 
 rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s, const BlockSel *blk) {
     Workspace &w = c->w;
     rv_status r;
     const bool chain = sys->n_chain > 0;
     const int M = system_members(sys);
+    const int C = chains_per_member(sys);
+    const int NC = system_chains(sys);   // chains: the unit of every chain kernel below
     int64_t tmp[2];
     const int64_t *off = system_offsets(sys, tmp);
-    const int cap = member_cap(M);
+    const int cap = member_cap(std::max(1, NC));
     if (chain) {
-        chain_com_k<<<ceil_div(M, 128), 128, 0, s>>>(M, sys->n_chain, sys->chain_m, sys->chain_x, w.out8, w.extra_xyzm,
-                                                     w.extra_eps);
+        chain_com_k<<<ceil_div(NC, 128), 128, 0, s>>>(NC, sys->n_chain, sys->chain_m, sys->chain_x, w.out8,
+                                                      w.extra_xyzm, w.extra_eps);
         count_launch(c);
     }
     if ((r = upload_offsets(c, M, off, s)) != RV_OK) return r;
     if (chain && (sys->pert_mode == 1 || sys->pert_mode == 2 || sys->pert_mode == 3)) {
-        if (M == 1) {
-            r = select_perturbers(c, sys->n, sys->x, sys->y, sys->z, w.extra_xyzm, nullptr, sys->pert_mode,
-                                  sys->pert_radius, sys->pert_k, cap, w.pert_idx, w.npert, s, sys->m,
-                                  sys->pert_gamma);
-            if (r != RV_OK) return r;
-        } else {
-            // the sort buffers are shared with the tree build, which comes next
-            const int bpm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c->max_member, 256), 64));
-            const SelRule R = sel_rule(sys->pert_mode, sys->pert_radius, sys->m, sys->pert_gamma);
-            sel_member_keys_k<<<dim3(bpm, M), 256, 0, s>>>(w.moff, bpm, sys->x, sys->y, sys->z, w.extra_xyzm,
-                                                           R, w.key_a);
-            count_launch(c);
-            uint64_t *sk;
-            int *si;
-            if ((r = radix_sort(c, sys->n, sys->pert_mode == 2 ? 4 : 1, &sk, &si, true, s, true)) != RV_OK) return r;
-            sel_member_write_k<<<M, 256, 0, s>>>(w.moff, sk, si, sys->pert_mode, sys->pert_k, cap, w.pert_idx,
-                                                 w.npert, w.st);
-            count_launch(c);
+        // one selection per chain j of every member (perturber slots of chain m C + j)
+        for (int j = 0; j < C; j++) {
+            if (M == 1) {
+                r = select_perturbers(c, sys->n, sys->x, sys->y, sys->z, w.extra_xyzm + 4 * j, nullptr,
+                                      sys->pert_mode, sys->pert_radius, sys->pert_k, cap, w.pert_idx + (int64_t)j * cap,
+                                      w.npert + j, s, sys->m, sys->pert_gamma);
+                if (r != RV_OK) return r;
+            } else {
+                // the sort buffers are shared with the tree build, which comes next
+                const int bpm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(c->max_member, 256), 64));
+                const SelRule R = sel_rule(sys->pert_mode, sys->pert_radius, sys->m, sys->pert_gamma);
+                sel_member_keys_k<<<dim3(bpm, M), 256, 0, s>>>(w.moff, bpm, sys->x, sys->y, sys->z, w.extra_xyzm, C,
+                                                               j, R, w.key_a);
+                count_launch(c);
+                uint64_t *sk;
+                int *si;
+                if ((r = radix_sort(c, sys->n, sys->pert_mode == 2 ? 4 : 1, &sk, &si, true, s, true)) != RV_OK)
+                    return r;
+                sel_member_write_k<<<M, 256, 0, s>>>(w.moff, sk, si, sys->pert_mode, sys->pert_k, cap, C, j,
+                                                     w.pert_idx, w.npert, w.st);
+                count_launch(c);
+            }
         }
     } else if (chain) {
-        cudaMemsetAsync(w.npert, 0, sizeof(int) * M, s);
+        cudaMemsetAsync(w.npert, 0, sizeof(int) * NC, s);
     }
     if ((r = build_tree(c, M, off, sys->x, sys->y, sys->z, sys->m, s)) != RV_OK) return r;
     const uint8_t *gact = nullptr;
@@ -543,24 +555,24 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s, const BlockSe
     // relative criterion (cfg.mac = 1): the accelerations in the system arrays (the previous
     // pass's, zero before the first one) are the references, read before they are overwritten
     const RelMac rel{c->cfg.alpha, sys->ax, sys->ay, sys->az};
-    if ((r = tree_walk(c, c->cfg.theta, c->cfg.eps_star, chain ? M : 0, w.extra_xyzm, w.extra_eps, nullptr, true,
+    if ((r = tree_walk(c, c->cfg.theta, c->cfg.eps_star, NC, w.extra_xyzm, w.extra_eps, nullptr, C,
                        sys->ax, sys->ay, sys->az, sys->pot, w.extra_out, s, nullptr,
                        c->cfg.mac == 1 ? &rel : nullptr, gact)) != RV_OK)
         return r;
-    c->pert_members = chain ? M : 0;
+    c->pert_members = NC;
     if (chain) {
-        gather_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, sys->x, sys->y, sys->z,
+        gather_pert_k<<<dim3(ceil_div(cap, 128), NC), 128, 0, s>>>(cap, w.pert_idx, w.npert, sys->x, sys->y, sys->z,
                                                                   sys->m, w.pert_m, w.pert_x);
         count_launch(c);
         ChainView V{sys->n_chain, cap, sys->chain_m, sys->chain_x, w.npert, w.pert_m, w.pert_x};
-        r = coupling(c, M, V, w.pert_a, w.pert_pot, w.chain_ext_a, w.chain_ext_pot, w.out8, s);
+        r = coupling(c, NC, V, w.pert_a, w.pert_pot, w.chain_ext_a, w.chain_ext_pot, w.out8, s);
         if (r != RV_OK) return r;
-        apply_pert_k<<<dim3(ceil_div(cap, 128), M), 128, 0, s>>>(cap, w.pert_idx, w.npert, w.pert_a, w.pert_pot,
+        apply_pert_k<<<dim3(ceil_div(cap, 128), NC), 128, 0, s>>>(cap, w.pert_idx, w.npert, w.pert_a, w.pert_pot,
                                                                  sys->ax, sys->ay, sys->az, sys->pot,
                                                                  blk ? blk->level : nullptr, blk ? blk->n : 0,
                                                                  blk ? blk->L : 0);
         count_launch(c);
-        chain_accel_k<<<ceil_div(M * sys->n_chain, 128), 128, 0, s>>>(M, sys->n_chain, sys->chain_m, sys->chain_x,
+        chain_accel_k<<<ceil_div(NC * sys->n_chain, 128), 128, 0, s>>>(NC, sys->n_chain, sys->chain_m, sys->chain_x,
                                                                       w.chain_ext_a, w.chain_ext_pot, w.extra_out,
                                                                       w.out8, sys->chain_a, sys->chain_pot);
         count_launch(c);
@@ -591,14 +603,13 @@ __global__ void chain_kick_drift_k(int n, double *cx, double *cv, const double *
 }
 
 void kick(rv_ctx *c, rv_system *sys, double dt, int drift, cudaStream_t s) {
-    const int M = system_members(sys);
     if (sys->n > 0) {
         kick_drift_k<<<grid_n(c, sys->n), 256, 0, s>>>(sys->n, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz,
                                                       sys->ax, sys->ay, sys->az, (float)(0.5 * dt), (float)dt, drift);
         count_launch(c);
     }
     if (sys->n_chain > 0) {
-        const int nc = M * sys->n_chain;
+        const int nc = system_chains(sys) * sys->n_chain;
         chain_kick_drift_k<<<ceil_div(nc, 128), 128, 0, s>>>(nc, sys->chain_x, sys->chain_v, sys->chain_a, 0.5 * dt, dt,
                                                              drift);
         count_launch(c);
@@ -692,8 +703,9 @@ rv_status energy(rv_ctx *c, const rv_system *sys, double *out, cudaStream_t s) {
     energy_partial_k<<<dim3(bpm, M), 256, 0, s>>>(c->w.moff, bpm, sys->x, sys->y, sys->z, sys->vx, sys->vy, sys->vz,
                                                   sys->m, sys->pot, c->w.red);
     count_launch(c);
-    energy_final_k<<<M, 256, 0, s>>>(c->w.red, bpm, sys->n_chain, sys->chain_m, sys->chain_x, sys->chain_v,
-                                     sys->chain_pot, out);
+    // chain members of member m: the n_chains chains of that member, one after another
+    energy_final_k<<<M, 256, 0, s>>>(c->w.red, bpm, sys->n_chain > 0 ? chains_per_member(sys) * sys->n_chain : 0,
+                                     sys->chain_m, sys->chain_x, sys->chain_v, sys->chain_pot, out);
     count_launch(c);
     return cuda_check(c, cudaGetLastError(), "energy");
 }

@@ -678,7 +678,7 @@ rv_status rv_tree_forces_mlp(rv_ctx *c, const void *params, float theta, float t
     if (e == cudaSuccess) e = cudaMemsetAsync(gcorr, 0, sizeof(float) * 3 * std::max<int64_t>(c->n, 1), s);
     if (e != cudaSuccess) return cuda_check(c, e, "mlp reset");
     PairRecord rec{theta_rec, reinterpret_cast<int2 *>(pairs), npairs, pair_cap};
-    rv_status r = tree_walk(c, theta, eps_star, 0, nullptr, nullptr, nullptr, false, ax, ay, az, pot, nullptr, s, &rec);
+    rv_status r = tree_walk(c, theta, eps_star, 0, nullptr, nullptr, nullptr, 0, ax, ay, az, pot, nullptr, s, &rec);
     if (r != RV_OK || c->n == 0) return r;
     int ncell, ngroup;
     if ((r = read_ncell(c, s, &ncell, &ngroup)) != RV_OK) return r;

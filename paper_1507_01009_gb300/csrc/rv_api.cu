@@ -242,7 +242,7 @@ rv_status rv_tree_forces(rv_ctx *c, float theta, float eps_star, int32_t n_extra
     if (n_extra < 0 || n_extra > kMaxExtra) return set_err(c, RV_E_INVAL, "n_extra must be in [0, %d]", kMaxExtra);
     if (n_extra > 0 && (!extra_xyzm || !extra_eps || !extra_out)) return set_err(c, RV_E_INVAL, "null extra array");
     if (c->n > 0 && (!ax || !ay || !az || !pot)) return set_err(c, RV_E_INVAL, "null output array");
-    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, nullptr, false, ax, ay, az, pot, extra_out,
+    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, nullptr, 0, ax, ay, az, pot, extra_out,
                      (cudaStream_t)stream);
 }
 
@@ -255,7 +255,7 @@ rv_status rv_tree_forces_rel(rv_ctx *c, float alpha, float eps_star, const float
     if (c->n > 0 && (!ax || !ay || !az || !pot || !ref_ax || !ref_ay || !ref_az))
         return set_err(c, RV_E_INVAL, "null array");
     RelMac rel{alpha, ref_ax, ref_ay, ref_az};
-    return tree_walk(c, 0.f, eps_star, 0, nullptr, nullptr, nullptr, false, ax, ay, az, pot, nullptr,
+    return tree_walk(c, 0.f, eps_star, 0, nullptr, nullptr, nullptr, 0, ax, ay, az, pot, nullptr,
                      (cudaStream_t)stream, nullptr, &rel);
 }
 
@@ -269,7 +269,7 @@ rv_status rv_tree_forces_members(rv_ctx *c, float theta, float eps_star, int32_t
     if (n_extra < 0 || n_extra > kMaxExtra) return set_err(c, RV_E_INVAL, "n_extra must be in [0, %d]", kMaxExtra);
     if (n_extra > 0 && (!extra_xyzm || !extra_eps || !extra_out)) return set_err(c, RV_E_INVAL, "null extra array");
     if (c->n > 0 && (!ax || !ay || !az || !pot)) return set_err(c, RV_E_INVAL, "null output array");
-    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, extra_member, false, ax, ay, az, pot,
+    return tree_walk(c, theta, eps_star, n_extra, extra_xyzm, extra_eps, extra_member, 0, ax, ay, az, pot,
                      extra_out, (cudaStream_t)stream);
 }
 
@@ -294,7 +294,10 @@ static rv_status check_system(rv_ctx *c, const rv_system *s) {
         rv_status r = check_offsets(c, M, s->member_offsets, s->n);
         if (r != RV_OK) return r;
     }
-    if ((int64_t)M * s->n_chain > kChainTotal) return set_err(c, RV_E_INVAL, "more than %d chain members", kChainTotal);
+    if (s->n_chains < 0 || (int64_t)M * std::max(1, (int)s->n_chains) > kExtraTotal)
+        return set_err(c, RV_E_INVAL, "more than %d chains", kExtraTotal);
+    if ((int64_t)M * std::max(1, (int)s->n_chains) * s->n_chain > kChainTotal)
+        return set_err(c, RV_E_INVAL, "more than %d chain members", kChainTotal);
     if (s->n > 0 && (!s->x || !s->y || !s->z || !s->vx || !s->vy || !s->vz || !s->m || !s->ax || !s->ay || !s->az ||
                      !s->pot))
         return set_err(c, RV_E_INVAL, "null star array in system");
@@ -367,7 +370,7 @@ rv_status rv_chain_perturber_forces(rv_ctx *c, const rv_system *sys, double dt, 
     rv_status r = check_system(c, sys);
     if (r != RV_OK) return r;
     if (sys->n_chain <= 0 || !chain_x || !a_chain) return set_err(c, RV_E_INVAL, "needs a chain and its arrays");
-    if (c->pert_members != std::max(1, (int)sys->n_members))
+    if (c->pert_members != system_chains(sys))
         return set_err(c, RV_E_NOTBUILT, "rv_chain_perturber_forces before rv_system_forces of this system");
     if (!(dt == dt)) return set_err(c, RV_E_INVAL, "bad dt");
     return chain_perturber_forces(c, sys, dt, chain_x, a_chain, pot_chain, (cudaStream_t)stream);

@@ -159,7 +159,7 @@ struct RelMac {
 // extra particles: xmem[k] = member of extra k (device), or nullptr when
 // extra k belongs to member k (one chain per member) -- see walk.cu.
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
-                    const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
+                    const int *xmem, int extras_per_member, float *ax, float *ay, float *az, float *pot,
                     float *xout, cudaStream_t s, const PairRecord *rec = nullptr, const RelMac *rel = nullptr,
                     const uint8_t *gact = nullptr);
 
@@ -195,6 +195,8 @@ rv_status block_levels(rv_ctx *c, int64_t n_st, const float *ax, const float *ay
 rv_status kdk(rv_ctx *c, rv_system *sys, double dt, int nsteps, cudaStream_t s);
 void kick(rv_ctx *c, rv_system *sys, double dt, int drift, cudaStream_t s);
 int system_members(const rv_system *sys);
+int system_chains(const rv_system *sys);   // chains over all members (0 without a chain)
+int chains_per_member(const rv_system *sys);
 rv_status energy(rv_ctx *c, const rv_system *sys, double *out, cudaStream_t s);
 rv_status kdk_graph(rv_ctx *c, rv_system *sys, double dt, int nsteps, double *eout, cudaStream_t s);
 

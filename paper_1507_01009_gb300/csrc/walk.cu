@@ -74,7 +74,7 @@ struct WalkArgs {
     const double *mbounds;  // per member: min x, y, z, L, 2^21 / L
     const int *mroot;    // root cell of each member
     const int *xmem;     // member of each extra particle (nullptr: member 0)
-    int extra_per_member;  // extra k belongs to member k (one chain per member)
+    int extra_per_member;  // > 0: extras [m e, (m + 1) e) belong to member m (e chains per member)
     MacTable mac;
     float eps2;          // star-star and star-cell softening^2
     float eps_star;
@@ -656,8 +656,8 @@ __device__ __forceinline__ void combine_shares(const Acc *acc, int s, int p, int
 __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float yi, float zi, float ei, int skip,
                                             int member, Acc &acc) {
     float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-    const int k0 = A.extra_per_member ? member : 0;
-    const int k1 = A.extra_per_member ? min(member + 1, A.n_extra) : A.n_extra;
+    const int k0 = A.extra_per_member ? member * A.extra_per_member : 0;
+    const int k1 = A.extra_per_member ? min(k0 + A.extra_per_member, A.n_extra) : A.n_extra;
     for (int k = k0; k < k1; k++) {
         if (k == skip) continue;
         if (!A.extra_per_member && (A.xmem ? A.xmem[k] : 0) != member) continue;
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             // ---- a particle outside the tree: all 32 lanes share its interaction list
             // (both target slots hold it; the second slot's sums are not used)
             const int kx = gi;
-            const int mk = A.extra_per_member ? kx : (A.xmem ? A.xmem[kx] : 0);
+            const int mk = A.extra_per_member ? kx / A.extra_per_member : (A.xmem ? A.xmem[kx] : 0);
             const TreeGeo G = tree_geo(A, mk);
             const double *mb = A.mbounds + 5 * mk;
             float xi = A.xyzm[4 * kx], yi = A.xyzm[4 * kx + 1], zi = A.xyzm[4 * kx + 2];
@@ -862,7 +862,7 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
 }
 
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
-                    const int *xmem, bool extra_per_member, float *ax, float *ay, float *az, float *pot,
+                    const int *xmem, int extras_per_member, float *ax, float *ay, float *az, float *pot,
                     float *xout, cudaStream_t s, const PairRecord *rec, const RelMac *rel, const uint8_t *gact) {
     Workspace &w = c->w;
     WalkArgs A;
@@ -880,7 +880,7 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.mbounds = w.mbounds;
     A.mroot = w.mroot;
     A.xmem = xmem;
-    A.extra_per_member = extra_per_member ? 1 : 0;
+    A.extra_per_member = extras_per_member;
     A.mac = mac_table(theta);
     A.eps2 = eps_star * eps_star;
     A.eps_star = eps_star;

@@ -64,7 +64,7 @@ class rv_system(C.Structure):
                 ("chain_x", C.c_void_p), ("chain_v", C.c_void_p), ("chain_a", C.c_void_p),
                 ("chain_pot", C.c_void_p), ("pert_mode", C.c_int32), ("pert_radius", C.c_float),
                 ("pert_k", C.c_int32), ("n_members", C.c_int32), ("member_offsets", C.c_void_p),
-                ("pert_gamma", C.c_float)]
+                ("pert_gamma", C.c_float), ("n_chains", C.c_int32)]
 
 
 def lib_path() -> str:
@@ -390,7 +390,7 @@ class Context:
         """Perturber pull on the chain members at chain_x (CUDA FP64 (M n_ch, 3)),
         the last force pass's perturbers predicted dt ahead. Returns (a_chain, pot_chain)."""
         import torch
-        nk = sysobj.n_members * sysobj.n_chain
+        nk = sysobj.n_members * sysobj.chains_per_member * sysobj.n_chain
         a_chain = torch.empty(3 * nk, dtype=torch.float64, device="cuda") if a_chain is None else a_chain
         pot_chain = torch.empty(nk, dtype=torch.float64, device="cuda") if pot_chain is None else pot_chain
         _need_cuda(chain_x, a_chain, pot_chain)
@@ -453,12 +453,14 @@ class System:
     """Device state of stars (FP32, caller order) and an optional chain (FP64)."""
 
     def __init__(self, pos, vel, mass, chain_m=None, chain_x=None, chain_v=None, pert_mode=0, pert_radius=0.0,
-                 pert_k=0, member_offsets=None, pert_gamma=0.0):
+                 pert_k=0, member_offsets=None, pert_gamma=0.0, chains_per_member=1):
         """pos/vel (3, n); mass (n,). member_offsets: host ints [M + 1] for M
         independent members stored one after another (None: one member).
         chain_* are member-major: chain_m (M n_ch,) or (n_ch,), chain_x/v
         (M n_ch, 3). pert_mode 1 radius, 2 k nearest, 3 tidal (Eq. 2,
-        r_crit = pert_radius, gamma_crit = pert_gamma)."""
+        r_crit = pert_radius, gamma_crit = pert_gamma). chains_per_member: C
+        chains in every member (chain arrays hold M C chains of n_ch members,
+        member by member)."""
         import torch
         f32 = dict(dtype=torch.float32, device="cuda")
         f64 = dict(dtype=torch.float64, device="cuda")
@@ -486,8 +488,9 @@ class System:
         else:
             self.member_offsets = np.ascontiguousarray(member_offsets, dtype=np.int64)
             self.n_members = int(len(self.member_offsets) - 1)
+        self.chains_per_member = int(chains_per_member)
         if self.n_chain:
-            self.n_chain //= self.n_members          # chain members per member
+            self.n_chain //= self.n_members * self.chains_per_member   # members of each chain
         self._c = None
 
     def c(self) -> rv_system:
@@ -501,6 +504,7 @@ class System:
             setattr(s, f, t.data_ptr() if t is not None else None)
         s.pert_mode, s.pert_radius, s.pert_k = self.pert_mode, self.pert_radius, self.pert_k
         s.pert_gamma = self.pert_gamma
+        s.n_chains = self.chains_per_member
         s.n_members = self.n_members
         s.member_offsets = None if self.member_offsets is None else self.member_offsets.ctypes.data
         self._c = s

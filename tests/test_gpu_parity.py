@@ -564,3 +564,46 @@ def test_chain_start_radius_matches_oracle(rvmod):
         for k in ("r2m", "sigma", "r_sigma", "r_infl", "r_chain0"):
             assert got[k] == ref[k], (k, got[k], ref[k])
         assert got["r_infl"] == min(got["r2m"], got["r_sigma"]) and np.isfinite(got["r2m"])
+
+
+def test_system_forces_two_chains(rvmod):
+    """Two SMBHs far apart in one galaxy, each its own chain with its own
+    perturbers (several distant SMBHs: the paper's outlook, Sect. 7): both
+    centres of mass are unsoftened particles of the tree, each chain's
+    perturbers get its resolved-minus-centre correction, each chain member
+    feels the tree (with the other chain as a point mass) and its perturbers.
+    Against the oracle following the same steps."""
+    w = ics.hernquist_bh_workload(1 << 16, seed=15)
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    eps = float(np.float32(w.eps_star))
+    cm = np.array([0.005, 0.003])
+    cx = np.array([[0.02, 0.0, 0.0], [-0.3, 0.1, 0.0]])
+    cv = np.array([[0.0, 0.4, 0.0], [0.0, -0.3, 0.1]])
+    ctx = _ctx(rvmod, p32.shape[1], theta=0.5, eps_star=eps)
+    S = rvmod.System(w.stars.pos, w.stars.vel, w.stars.mass, chain_m=cm, chain_x=cx, chain_v=cv, pert_mode=1,
+                     pert_radius=0.06, chains_per_member=2)
+    assert S.n_chain == 1
+    ctx.system_forces(S)
+    ctx.sync_status()
+    T = oracle.Tree(p32, m32, 16, 32)
+    xp = cx.astype(np.float32).T
+    xm = np.array([np.float32(v) for v in cm], dtype=np.float64)
+    ao, _, xa, _ = T.forces(0.5, eps, True, xp, xm, [0.0, 0.0])
+    a_bh = []
+    for j in range(2):
+        pert = oracle.radius(p32, cx[j].astype(np.float32), np.float32(np.float32(0.06) * np.float32(0.06)))
+        assert len(pert) > 3
+        o = oracle.perturber(cm[j:j + 1], cx[j:j + 1], m32[pert].astype(np.float64), p32[:, pert].T.astype(np.float64))
+        ao[:, pert] += o["a_pert"].T
+        a_bh.append(xa[:, j] - o["sub"] + o["a_chain"][0])
+    a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
+    med, _, mx = err_stats(a, ao)
+    assert med <= MED_TOL and mx <= MAX_TOL, (med, mx)
+    got = S.chain_a.cpu().numpy().reshape(2, 3)
+    for j in range(2):
+        assert np.linalg.norm(got[j] - a_bh[j]) / np.linalg.norm(a_bh[j]) <= MAX_TOL
+    # a step runs with both chains and the energy totals include both members
+    ctx.kdk_step(S, 1e-3, 2)
+    e = ctx.energy(S).cpu().numpy()
+    ctx.sync_status()
+    assert abs(e[9] - (m32.astype(np.float64).sum() + cm.sum())) < 1e-6
