@@ -22,8 +22,10 @@ relative opening criterion the paper's runs use, tolerance 1e-3, the previous
 step's accelerations as references), `hernquist_binary` (2^22 stars, central SMBH pair, 256
 nearest perturbers), `plummer` (4096 stars), `ensemble` (64 independent
 Hernquist realisations, sizes log-uniform in 8192..524288, each with a
-central SMBH pair, all members in one build and one walk per step, the step
-captured in a CUDA graph, walk parameters from the autotuner).
+central SMBH pair, all members in one build and one walk per step). Every
+step except the block scheme's is captured once as a CUDA graph and
+replayed (--no-graph launches its kernels one by one); walk parameters come
+from the autotuner.
 
 Under torchrun (N > 1) every rank runs its own realisation (replicas: no
 data exchange); the value is the sum of particles over ranks / max time.
@@ -85,8 +87,7 @@ def make_workload(name: str, rank: int = 0) -> dict:
         d = dict(pos=e["pos"], vel=e["vel"], mass=e["mass"], offsets=e["offsets"], chain_m=e["chain_m"],
                  chain_x=e["chain_x"], chain_v=e["chain_v"], pert_mode=2, pert_radius=0.0, pert_k=256)
         cfg = {"workload": "ensemble64_hernquist_gamma1_smbh_binary", "n_stars": int(e["offsets"][-1]),
-               "members": 64, "member_sizes": "log-uniform 8192..524288 (seed 4)", "perturbers": "256 nearest",
-               "graph_captured": True}
+               "members": 64, "member_sizes": "log-uniform 8192..524288 (seed 4)", "perturbers": "256 nearest"}
     else:
         raise ValueError(name)
     d["eps"] = 0.01 if name == "plummer" else 0.005
@@ -349,7 +350,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     d = make_workload(args.workload, rank)
     n = d["n"]
-    use_graph = args.workload == "ensemble"
+    # every step but the block scheme's is captured once as a CUDA graph and replayed
+    use_graph = args.workload not in ("hernquist_bh_block",) and not args.no_graph
     blk = d["block"]
 
     # walk parameters (not part of the workload): the autotuner's pick over a small grid, untimed
@@ -441,13 +443,17 @@ def run_gpu(args):
     else:
         pairs = []
         off = d["offsets"] if d["offsets"] is not None else [0, n]
+        ref = tuple(t.clone() for t in (S.ax, S.ay, S.az))   # relative criterion: the step's references
         with torch.cuda.stream(stream):
             for k in range(args.steps):
                 ctx.build_tree_members(off, S.x, S.y, S.z, S.m, stream=stream)
                 flush.fill_(k & 255)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                ctx.tree_forces_members(out=(S.ax, S.ay, S.az, S.pot), stream=stream)
+                if d["mac"] == 1:
+                    ctx.tree_forces_rel(d["alpha"], ref, out=(S.ax, S.ay, S.az, S.pot), stream=stream)
+                else:
+                    ctx.tree_forces_members(out=(S.ax, S.ay, S.az, S.pot), stream=stream)
                 e1.record(stream)
                 pairs.append((e0, e1))
         torch.cuda.synchronize()
@@ -457,7 +463,8 @@ def run_gpu(args):
         flop = FLOP_P2P * n_p2p + FLOP_M2P * n_m2p
         walk_src = ("separate build + full walk loop (block steps walk only the active groups); extra particles "
                     "omitted" if blk else
-                    "separate build + walk loop (steps replayed from a CUDA graph); extra particles omitted")
+                    "separate build + walk loop, same criterion (steps replayed from a CUDA graph); extra particles "
+                    "omitted")
     achieved = flop / (walk_ms / 1e3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock
@@ -517,7 +524,7 @@ def run_gpu(args):
                     "step": ("16 block substeps (drift, perturber select, build, walk of active groups, fp64 "
                              "perturber/chain, kicks and levels of active stars) + energy" if blk else
                              "kdk + perturber select + build + walk + fp64 perturber/chain + energy"),
-                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                    "parallelism": f"replicas{ws}" if ws > 1 else "single", "graph_captured": bool(use_graph),
                     "l2": "flushed (256 MiB write) before every timed step"})
         cfg["autotuned"] = {"cached": tuned["cached"], "candidates": len(tuned["table"]),
                             "walk_ms_by_group_leaf_tile": {f'{r["group"]}/{r["n_leaf"]}/{r["tile"]}': round(r["walk_ms"], 3)
@@ -654,6 +661,7 @@ def main():
                     choices=["hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block", "hernquist_binary", "plummer",
                              "ensemble", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch every kernel of a step (no CUDA graph)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -49,7 +49,7 @@
 #endif
 // 1: load a tested cell's box, links and multipole record together
 #ifndef RV_WALK_PREFETCH
-#define RV_WALK_PREFETCH 0
+#define RV_WALK_PREFETCH 1
 #endif
 
 namespace rv {

@@ -130,6 +130,35 @@ def test_graph_step_equals_plain_step(rvmod):
         np.testing.assert_array_equal(a, g)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_graph_step_equals_plain_step_one_member(rvmod, mode):
+    """A single system with an SMBH (radius or k-nearest perturbers): the
+    replayed graph step equals the plain step bit for bit."""
+    import torch
+    w = ics.hernquist_bh_workload(1 << 14, seed=16)
+    eps = float(np.float32(w.eps_star))
+    out = []
+    for graph in (False, True):
+        ctx = rvmod.Context(1 << 14, theta=0.5, eps_star=eps, group=64, n_leaf=32, tile=128)
+        S = rvmod.System(w.stars.pos, w.stars.vel, w.stars.mass, chain_m=w.chain.mass, chain_x=w.chain.pos,
+                         chain_v=w.chain.vel, pert_mode=mode, pert_radius=0.05, pert_k=64)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            ctx.system_forces(S, stream=st)
+            if graph:
+                eo = torch.zeros(10, dtype=torch.float64, device="cuda")
+                ctx.kdk_step_graph(S, 1e-3, 4, energy_out=eo, stream=st)
+            else:
+                ctx.kdk_step(S, 1e-3, 4, stream=st)
+                eo = ctx.energy(S, stream=st)
+        st.synchronize()
+        ctx.sync_status(stream=st)
+        out.append([getattr(S, f).cpu().numpy().copy() for f in ("x", "vx", "ax", "pot", "chain_x")] +
+                   [eo.cpu().numpy().copy()])
+    for a, g in zip(*out):
+        np.testing.assert_array_equal(a, g)
+
+
 def test_graph_step_rejects_default_stream(rvmod):
     ctx = rvmod.Context(100)
     w = ics.plummer(100, 3)
