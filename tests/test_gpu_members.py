@@ -166,3 +166,65 @@ def test_graph_step_rejects_default_stream(rvmod):
     import ctypes as C
     st = ctx.L.rv_kdk_step_graph(ctx.h, C.byref(S.c()), 1e-3, 1, None, None)
     assert st == rvmod.RV_E_INVAL
+
+
+@pytest.mark.parametrize("softening,mac", [(0, 1), (1, 0), (1, 1)])
+def test_members_match_single_builds_relmac_and_spline(rvmod, softening, mac):
+    """Members under the relative criterion and/or spline softening: each member
+    gives bit for bit what it gives alone (references: each star's own |a|
+    from a first theta pass of its own member)."""
+    pos, _, mass, off = _members(SIZES, 41)
+    p32, m32 = stars32(pos, mass)
+    eps = float(np.float32(0.005))
+    ctx = rvmod.Context(int(off[-1]), theta=0.5, eps_star=eps, softening=softening, group=64, n_leaf=16, tile=128)
+    x, y, z, m = _dev(p32[0]), _dev(p32[1]), _dev(p32[2]), _dev(m32)
+    ctx.build_tree_members(off, x, y, z, m)
+    ref = ctx.tree_forces_members()[:3]
+    ens = ctx.tree_forces_rel(1e-3, ref) if mac else ctx.tree_forces_members()
+    ens = [t.cpu().numpy() for t in ens[:4]]
+    ctx.sync_status()
+    for k in range(len(SIZES)):
+        s, e = int(off[k]), int(off[k + 1])
+        if e == s:
+            continue
+        single = rvmod.Context(e - s, theta=0.5, eps_star=eps, softening=softening, group=64, n_leaf=16, tile=128)
+        single.build_tree(x[s:e].contiguous(), y[s:e].contiguous(), z[s:e].contiguous(), m[s:e].contiguous())
+        r1 = single.tree_forces()[:3]
+        one = single.tree_forces_rel(1e-3, r1) if mac else single.tree_forces()
+        one = [t.cpu().numpy() for t in one[:4]]
+        single.sync_status()
+        for a, b in zip(ens, one):
+            np.testing.assert_array_equal(a[s:e], b)
+
+
+def test_members_block_steps_match_single_systems(rvmod):
+    """Block time steps over members with a chain each: every member evolves
+    as it does alone (same levels, positions and velocities bit for bit)."""
+    sizes = [4096, 10000]
+    pos, vel, mass, off = _members(sizes, 62)
+    b = ics.central_binary()
+    M = len(sizes)
+    cm = np.tile(b.mass, M)
+    cx = np.concatenate([b.pos + 3.0 * k for k in range(M)])
+    cv = np.tile(b.vel, (M, 1))
+    eps = float(np.float32(0.005))
+    ctx = rvmod.Context(int(off[-1]), theta=0.5, eps_star=eps)
+    S = rvmod.System(pos, vel, mass, chain_m=cm, chain_x=cx, chain_v=cv, pert_mode=2, pert_k=32,
+                     member_offsets=off)
+    B = rvmod.Blocks(int(off[-1]), 1.0 / 64, 3, tau_acc=0.3, tau_vel=0.3, eps=eps)
+    ctx.block_start(S, B)
+    ctx.block_steps(S, B, 8)
+    ctx.sync_status()
+    for k in range(M):
+        s, e = int(off[k]), int(off[k + 1])
+        one = rvmod.Context(e - s, theta=0.5, eps_star=eps)
+        S1 = rvmod.System(pos[:, s:e], vel[:, s:e], mass[s:e], chain_m=b.mass, chain_x=cx[2 * k:2 * k + 2],
+                          chain_v=b.vel, pert_mode=2, pert_k=32)
+        B1 = rvmod.Blocks(e - s, 1.0 / 64, 3, tau_acc=0.3, tau_vel=0.3, eps=eps)
+        one.block_start(S1, B1)
+        one.block_steps(S1, B1, 8)
+        one.sync_status()
+        np.testing.assert_array_equal(B.level[s:e].cpu().numpy(), B1.level.cpu().numpy())
+        for f in ("x", "vx", "ax"):
+            np.testing.assert_array_equal(getattr(S, f)[s:e].cpu().numpy(), getattr(S1, f).cpu().numpy())
+        np.testing.assert_array_equal(S.chain_x.cpu().numpy()[6 * k:6 * k + 6], S1.chain_x.cpu().numpy())
