@@ -151,7 +151,9 @@ rv_status rv_tree_forces(rv_ctx *ctx, float theta, float eps_star, int32_t n_ext
  * sqrt((x x + y y) + z z). Every test runs in FP32 with one rounding per
  * operation: K = (alpha |a|min) (u u), u the grid unit, accept iff
  * M s^2 <= (K d^2) d^2 with d^2 in grid units. alpha = 0 gives the direct
- * sum. Outputs as rv_tree_forces (no extra particles); the reference arrays
+ * sum. A group whose smallest reference magnitude is 0 (no force pass yet)
+ * uses the opening angle of the context's configuration (theta).
+ * Outputs as rv_tree_forces (no extra particles); the reference arrays
  * may be the output arrays themselves (each group reads its own stars'
  * references before it writes their forces). */
 rv_status rv_tree_forces_rel(rv_ctx *ctx, float alpha, float eps_star, const float *ref_ax, const float *ref_ay,

@@ -22,7 +22,9 @@
 
 namespace rv {
 
+// (a level outside [0, L] is read as the nearest bound)
 __device__ __forceinline__ bool is_active(int lvl, long long n, int L) {
+    lvl = min(max(lvl, 0), L);
     const long long mask = (1ll << (L - lvl)) - 1;
     return (n & mask) == 0;
 }
@@ -79,7 +81,7 @@ __global__ void block_kick_k(int64_t n_st, float *vx, float *vy, float *vz, cons
                              double tau_vel, double eps, int adapt, int start) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_st;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int lvl = level[i];
+        int lvl = min(max((int)level[i], 0), L);
         if (!start && !is_active(lvl, n, L)) continue;
         float u = vx[i], v = vy[i], w = vz[i];
         if (!start) {
@@ -105,7 +107,7 @@ __global__ void block_levels_k(int64_t n_st, const float *ax, const float *ay, c
                                double tau_acc, double tau_vel, double eps, int start) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_st;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int lvl = level[i];
+        const int lvl = min(max((int)level[i], 0), L);
         if (!start && !is_active(lvl, n, L)) continue;
         int nl = level_of(ax[i], ay[i], az[i], vx[i], vy[i], vz[i], dt_max, L, tau_acc, tau_vel, eps);
         if (!start)

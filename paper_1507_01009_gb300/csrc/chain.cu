@@ -439,7 +439,7 @@ __global__ void apply_pert_k(int cap, const int *idx, const int *npert, const do
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         const int64_t q = (int64_t)mb * cap + p;
         const int i = idx[q];
-        if (level && (n & ((1ll << (L - level[i])) - 1)) != 0) continue;
+        if (level && (n & ((1ll << (L - min(max((int)level[i], 0), L))) - 1)) != 0) continue;
         ax[i] = (float)((double)ax[i] + a_pert[3 * q]);
         ay[i] = (float)((double)ay[i] + a_pert[3 * q + 1]);
         az[i] = (float)((double)az[i] + a_pert[3 * q + 2]);

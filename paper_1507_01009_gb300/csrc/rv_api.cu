@@ -255,7 +255,8 @@ rv_status rv_tree_forces_rel(rv_ctx *c, float alpha, float eps_star, const float
     if (c->n > 0 && (!ax || !ay || !az || !pot || !ref_ax || !ref_ay || !ref_az))
         return set_err(c, RV_E_INVAL, "null array");
     RelMac rel{alpha, ref_ax, ref_ay, ref_az};
-    return tree_walk(c, 0.f, eps_star, 0, nullptr, nullptr, nullptr, 0, ax, ay, az, pot, nullptr,
+    // groups without a reference yet use the context's opening angle
+    return tree_walk(c, c->cfg.theta, eps_star, 0, nullptr, nullptr, nullptr, 0, ax, ay, az, pot, nullptr,
                      (cudaStream_t)stream, nullptr, &rel);
 }
 

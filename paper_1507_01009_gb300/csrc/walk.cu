@@ -810,8 +810,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             if (i >= s) continue;
             Acc &tot = tots[h];
             const float4 ps = __ldg(&A.pos[grp.first + i]);
-            // the star's own pair was evaluated at r = 0: remove its -m/eps
-            if (SOFT) tot.ph += ps.w * rsqrtf(A.eps2);
+            // the star's own pair was evaluated at r = 0: remove its -m/eps (the product
+            // rounded on its own, as in the pair, so that the two cancel exactly)
+            if (SOFT) tot.ph += __fmul_rn(ps.w, rsqrtf(A.eps2));
             if (A.n_extra > 0) extra_terms(A, ps.x, ps.y, ps.z, A.eps_star, -1, mg, tot);
             int o = A.perm[grp.first + i];
             A.ax[o] = tot.ax + tot.cx;

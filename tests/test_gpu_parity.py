@@ -607,3 +607,78 @@ def test_system_forces_two_chains(rvmod):
     e = ctx.energy(S).cpu().numpy()
     ctx.sync_status()
     assert abs(e[9] - (m32.astype(np.float64).sum() + cm.sum())) < 1e-6
+
+
+def test_new_paths_on_empty_and_tiny_inputs(rvmod):
+    """Degenerate inputs on the relative criterion, tidal search, block steps
+    and chain start radius: no stars, one star, all stars at one point."""
+    import torch
+    e = torch.empty(0, dtype=torch.float32, device="cuda")
+    ctx = _ctx(rvmod, 16)
+    ctx.build_tree(e, e, e, e)
+    ctx.tree_forces_rel(1e-3, (e, e, e), out=(e, e, e, e))
+    idx, cnt = ctx.select_perturbers_tidal(e, e, e, e, (0, 0, 0), 0.01, 1e-3, 0.1)
+    ctx.sync_status()
+    assert int(cnt.item()) == 0
+    with pytest.raises(rvmod.RvError):
+        ctx.chain_start_radius((e, e, e), (e, e, e), e, (0, 0, 0), 0.005, 1, 1, 0.01)
+    S0 = rvmod.System(np.zeros((3, 0)), np.zeros((3, 0)), np.zeros(0))
+    B0 = rvmod.Blocks(0, 1e-2, 2)
+    ctx.block_start(S0, B0)
+    ctx.block_steps(S0, B0, 4)
+    ctx.sync_status()
+    # one star: no force; at one point (softened): finite, zero force, phi = -(n-1) m / eps
+    for n in (1, 100):
+        p32 = np.full((3, n), 0.25, np.float32)
+        m32 = np.full(n, 1.0 / n, np.float32)
+        c = _ctx(rvmod, n, eps_star=0.01)
+        gpu_tree(c, p32, m32)
+        z = tuple(to_dev(np.zeros(n, np.float32)) for _ in range(3))
+        ax, ay, az, pot = c.tree_forces_rel(1e-3, z)
+        c.sync_status()
+        assert np.all(ax.cpu().numpy() == 0) and np.all(np.isfinite(pot.cpu().numpy()))
+        np.testing.assert_allclose(pot.cpu().numpy(), -(n - 1) / n / float(np.float32(0.01)), rtol=1e-5)
+
+
+def test_relmac_mixed_references_vs_oracle(rvmod):
+    """References that are zero for some stars: their groups fall back to theta,
+    the others use the relative criterion -- the same split on both sides."""
+    p32, m32 = _inputs("hernquist", 65536)
+    eps = float(np.float32(0.005))
+    ad, _ = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), eps)
+    aref = ad.astype(np.float32)
+    r = np.linalg.norm(p32.astype(np.float64), axis=0)
+    aref[:, r > 1.0] = 0.0                             # outer stars: no reference yet
+    ctx = _ctx(rvmod, 65536, theta=0.6, eps_star=eps, group=64, n_leaf=32, tile=128)
+    gpu_tree(ctx, p32, m32)
+    ax, ay, az, _ = ctx.tree_forces_rel(1e-3, tuple(to_dev(np.ascontiguousarray(aref[k])) for k in range(3)))
+    ctx.sync_status()
+    a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)
+    T = oracle.Tree(p32, m32, 32, 64)
+    ao, _, cnt = T.forces_rel(1e-3, eps, aref, counts=True, theta=0.6)
+    med, _, mx = err_stats(a, ao)
+    assert med <= MED_TOL and mx <= MAX_TOL
+    n_p2p, n_m2p = ctx.walk_stats()
+    assert n_p2p == int(cnt[:, 0].sum()) + 65536 and n_m2p == int(cnt[:, 1].sum())
+
+
+def test_max_members_tiny(rvmod):
+    """512 members (the maximum) of one to three stars each: every member is its
+    own tree; each star feels only its own member (closed-form pairs)."""
+    g = ics.rng(71)
+    sizes = g.integers(1, 4, 512)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    p32 = g.uniform(-1, 1, (3, n)).astype(np.float32)
+    m32 = g.uniform(0.5, 1.5, n).astype(np.float32)
+    eps = float(np.float32(0.01))
+    ctx = _ctx(rvmod, n, eps_star=eps)
+    ctx.build_tree_members(off, *(to_dev(p32[a]) for a in range(3)), to_dev(m32))
+    ax, ay, az, pot = ctx.tree_forces_members()
+    ctx.sync_status()
+    a = np.stack([t.cpu().numpy() for t in (ax, ay, az)]).astype(np.float64)
+    for k in range(512):
+        s, e = int(off[k]), int(off[k + 1])
+        ad, pd = oracle.direct(p32[:, s:e].astype(np.float64), m32[s:e].astype(np.float64), eps)
+        np.testing.assert_allclose(a[:, s:e], ad, rtol=2e-5, atol=1e-6)
+        np.testing.assert_allclose(pot.cpu().numpy()[s:e], pd, rtol=2e-5, atol=1e-6)
