@@ -43,7 +43,7 @@ typedef enum {
     RV_E_CUDA = 2,      /* a CUDA runtime call failed; rv_last_error() has the text */
     RV_E_WORKSPACE = 3, /* workspace missing, too small, or the tree outgrew it */
     RV_E_STACK = 4,     /* a walk's traversal stack filled up (results invalid) */
-    RV_E_TIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    RV_E_TIMEOUT = 5,   /* a bounded device wait gave up */
     RV_E_NOTBUILT = 6,  /* forces asked before rv_build_tree */
     RV_E_TOO_LARGE = 7  /* input larger than a fixed-size internal buffer allows */
 } rv_status;
@@ -353,7 +353,10 @@ size_t rv_mlp_param_bytes(void);
 size_t rv_mlp_scratch_bytes(int64_t batch);
 /* Glorot-uniform weights from a SplitMix64 stream of `seed`, zero biases. */
 rv_status rv_mlp_init(void *params, uint64_t seed, void *stream);
-/* y[n][3] = network(x[n][16]) (device FP32). */
+/* y[n][3] = network(x[n][16]) (device FP32), on the tcgen05 tensor cores in
+ * tiles of 128 rows (x need not be 16-byte aligned; aligned rows load as
+ * float4). A completion wait that times out (after ~1 s) leaves NaN in the
+ * rows of that tile. */
 rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y, void *stream);
 /* Mean squared error of network(x) against t[n][3] and its gradient with
  * respect to the FP32 parameter vector (grad: device FP32 [5768], ordered W1
@@ -376,7 +379,9 @@ rv_status rv_mlp_samples(rv_ctx *ctx, float theta, float eps_star, int64_t n_sam
  * theta that a walk at theta_rec (< theta) would open, into device pairs[2
  * pair_cap] with the count in npairs[1]; the network evaluates each pair at
  * the group's geometric centre and adds the correction (device scratch
- * gcorr[3 n]) to every star of the group. Synchronises `stream` once. */
+ * gcorr[3 n]) to every star of the group. Synchronises `stream` once. The
+ * network runs as rv_mlp_forward does; a timed-out completion wait is
+ * reported as RV_E_TIMEOUT by rv_sync_status. */
 rv_status rv_tree_forces_mlp(rv_ctx *ctx, const void *params, float theta, float theta_rec, float eps_star,
                              float *ax, float *ay, float *az, float *pot, int32_t *pairs, int32_t pair_cap,
                              int32_t *npairs, float *gcorr, void *stream);

@@ -1,13 +1,15 @@
 // mlp.cu -- learned correction of cell forces (not in the paper).
 //
 // A small network (11 features -> 64 -> 64 -> 3, SiLU, bfloat16 weights and
-// activations, FP32 accumulation on the tensor cores with mma.sync m16n8k16)
+// activations, FP32 accumulation on the tensor cores)
 // predicts, for a star (or a walk group's centre) at r from an accepted
 // cell, the difference between the cell's exact softened force and its
 // monopole + quadrupole force, scaled by |r|^2 / M. Features: r/|r| (3),
 // s/|r|, eps/|r|, Q/(M s^2) (6), s the cell side.
 //
-// Training (per minibatch): tensor-core forward, FP32 backward (exact
+// Inference (rv_mlp_forward and the correction in the walk) runs on tcgen05:
+// operands in shared memory, accumulators in tensor memory, 128 rows per tile.
+// Training (per minibatch): warp-level mma.sync forward, FP32 backward (exact
 // gradients of the same rounded forward), per-block gradient partials summed
 // in a fixed order, Adam on FP32 master weights, bfloat16 copies refreshed.
 // Samples: random stars, a random cell among those each star's walk accepts
@@ -207,27 +209,6 @@ __global__ void mlp_sync_k(MlpBlock P) {
         else if (i < oW3t) { int j = i - oW2t, n = j / kHid, k = j % kHid; v = P.w[oW2 + k * kHid + n]; }
         else { int j = i - oW3t, n = j / kHid, k = j % kHid; v = P.w[oW3 + k * kOutPad + n]; }
         P.wb[i] = __float2bfloat16_rn(v);
-    }
-}
-
-__global__ void __launch_bounds__(128) mlp_forward_k(MlpBlock P, int64_t n, const float *x, float *y) {
-    __shared__ MlpSmem S;
-    load_mlp_smem(P, S);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    for (int64_t r0 = ((int64_t)blockIdx.x * 4 + wid) * 16; r0 < n; r0 += (int64_t)gridDim.x * 64) {
-        unsigned a[4];
-        load_a(x, r0, n, a);
-        float o[4];
-        mlp_warp_forward(S, a, o, nullptr, nullptr);
-        const int64_t ra = r0 + g, rb = r0 + g + 8;
-        for (int q = 0; q < 2; q++) {
-            int col = 2 * t + q;
-            if (col < kOut) {
-                if (ra < n) y[ra * kOut + col] = o[q];
-                if (rb < n) y[rb * kOut + col] = o[2 + q];
-            }
-        }
     }
 }
 
@@ -486,65 +467,341 @@ __global__ void mlp_samples_k(CellGeo T, MacTable mac, int64_t n, float eps, uns
 }
 
 // ---------------------------------------------------------------------------
+// inference on the 5th-generation tensor cores (tcgen05)
+// ---------------------------------------------------------------------------
+// One CTA of 128 threads evaluates the network on tiles of 128 rows; thread i
+// owns row i of a tile, which is lane i of the accumulator in tensor memory
+// (warp w reads lanes 32w .. 32w + 31). Per tile: the features (bfloat16) go
+// to shared memory, one thread issues the MMAs of a layer (M = 128, bfloat16
+// operands from shared memory, FP32 accumulator in 64 TMEM columns) and
+// commits them to an mbarrier; every thread then reads its row back, adds the
+// bias, applies SiLU and writes the next layer's operand. Operands use the
+// no-swizzle K-major layout of the tcgen05 matrix descriptors: 8 rows x 16
+// bytes per core matrix (rows 16 bytes apart), core matrices adjacent in K 128
+// bytes apart (leading byte offset), 8-row groups K x 16 bytes apart (stride
+// byte offset).
+constexpr int kTcRows = 128;   // rows per tile (the MMA's M)
+constexpr int kTcCols = 64;    // TMEM columns of a CTA (all three layers' accumulators)
+constexpr int kTcOutN = 16;    // layer 3's N (3 outputs, padded)
+constexpr int kTcCtas = 6;     // resident CTAs per SM (shared memory ~35 KB, 6 x 64 of 512 TMEM columns)
+
+struct TcSmem {
+    alignas(128) __nv_bfloat16 a1[kTcRows * kInPad];   // features: K = 16
+    alignas(128) __nv_bfloat16 a2[kTcRows * kHid];     // hidden activations: K = 64
+    alignas(128) __nv_bfloat16 w1[kHid * kInPad];      // W1^T: N = 64 rows, K = 16
+    alignas(128) __nv_bfloat16 w2[kHid * kHid];        // W2^T: 64 x 64
+    alignas(128) __nv_bfloat16 w3[kTcOutN * kHid];     // W3^T: 16 x 64 (rows 8 .. 15 zero)
+    float b1[kHid], b2[kHid], b3[kOutPad];
+    float red[4][32][3];                               // pair rows: per-warp terms for the group sums
+    unsigned long long bar;                            // MMA completion
+    unsigned tmem;                                     // TMEM base address from tcgen05.alloc
+};
+
+// element offset of (row r, column k) in a K-wide operand tile
+__device__ __forceinline__ int tc_off(int r, int k, int K) {
+    return (r >> 3) * (8 * K) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor of a K-wide tile (no swizzle, K-major)
+__device__ __forceinline__ unsigned long long tc_desc(const void *tile, int K) {
+    const unsigned a = smem_u32(tile);
+    return (unsigned long long)((a & 0x3FFFFu) >> 4) | ((unsigned long long)(128 >> 4) << 16) |
+           ((unsigned long long)((16 * K) >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, bfloat16 A and B,
+// both K-major, M x N
+__host__ __device__ constexpr unsigned tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       unsigned accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :
+                 : "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// shared-memory writes of this thread become visible to the tensor cores' reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Waits for the phase of parity `ph` of the barrier; false after about 2^31
+// clock cycles (~1 s) without completion.
+__device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned ph) {
+    const unsigned a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(ph)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane, starting at taddr
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float v[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    // the registers are read only after the load completed
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+// SiLU with the fast exponential and division (a few ulp; the result is
+// rounded to bfloat16 next). z < -88: exp overflows and the quotient is -0.
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+
+// Weights (bfloat16, n-major as stored: element (k, n) at [n][k]) and biases
+// into the operand layout.
+__device__ void tc_load_weights(const MlpBlock &P, TcSmem &S) {
+    for (int i = threadIdx.x; i < kHid * kInPad; i += blockDim.x)
+        S.w1[tc_off(i / kInPad, i % kInPad, kInPad)] = P.wb[oW1t + i];
+    for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x)
+        S.w2[tc_off(i / kHid, i % kHid, kHid)] = P.wb[oW2t + i];
+    for (int i = threadIdx.x; i < kTcOutN * kHid; i += blockDim.x) {
+        const int nn = i / kHid, k = i % kHid;
+        S.w3[tc_off(nn, k, kHid)] = nn < kOutPad ? P.wb[oW3t + i] : __float2bfloat16_rn(0.f);
+    }
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+        S.b1[i] = P.w[ob1 + i];
+        S.b2[i] = P.w[ob2 + i];
+    }
+    if (threadIdx.x < kOutPad) S.b3[threadIdx.x] = P.w[ob3 + threadIdx.x];
+}
+
+// This thread's 16 features into row r of the layer-1 operand.
+__device__ __forceinline__ void tc_put_features(TcSmem &S, int r, const float f[kInPad]) {
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        uint4 u;
+        u.x = pack_bf16(f[8 * c + 0], f[8 * c + 1]);
+        u.y = pack_bf16(f[8 * c + 2], f[8 * c + 3]);
+        u.z = pack_bf16(f[8 * c + 4], f[8 * c + 5]);
+        u.w = pack_bf16(f[8 * c + 6], f[8 * c + 7]);
+        *reinterpret_cast<uint4 *>(S.a1 + tc_off(r, 8 * c, kInPad)) = u;
+    }
+}
+
+// Accumulator columns 0 .. 63 of row r + bias -> SiLU -> bfloat16 row r of a2.
+__device__ __forceinline__ void tc_hidden(TcSmem &S, unsigned tlane, int r, const float *bias) {
+#pragma unroll
+    for (int c0 = 0; c0 < kHid; c0 += 16) {
+        float v[16];
+        tc_ld16(tlane + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = silu_fast(v[j] + bias[c0 + j]);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            uint4 u;
+            u.x = pack_bf16(v[8 * c + 0], v[8 * c + 1]);
+            u.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+            u.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+            u.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+            *reinterpret_cast<uint4 *>(S.a2 + tc_off(r, c0 + 8 * c, kHid)) = u;
+        }
+    }
+}
+
+// Issues layer `layer` (1, 2, 3) of the tile by one thread and waits for it
+// with every thread. The operands were written by all threads before.
+__device__ __forceinline__ bool tc_layer(TcSmem &S, int layer, unsigned tmem, unsigned &phase) {
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc_after_sync();
+        if (layer == 1) {
+            tc_mma(tmem, tc_desc(S.a1, kInPad), tc_desc(S.w1, kInPad), tc_idesc(kTcRows, kHid), 0u);
+        } else {
+            const unsigned long long da = tc_desc(S.a2, kHid);
+            const unsigned long long db = layer == 2 ? tc_desc(S.w2, kHid) : tc_desc(S.w3, kHid);
+            const unsigned id = layer == 2 ? tc_idesc(kTcRows, kHid) : tc_idesc(kTcRows, kTcOutN);
+            // K = 64 in four steps of 16: 2 core matrices (256 bytes) further each
+#pragma unroll
+            for (int s = 0; s < kHid / 16; s++) tc_mma(tmem, da + 16ull * s, db + 16ull * s, id, s > 0 ? 1u : 0u);
+        }
+        tc_commit(&S.bar);
+    }
+    const bool ok = bar_wait(&S.bar, phase);
+    phase ^= 1u;
+    tc_after_sync();
+    return !__syncthreads_or(!ok);   // the same answer in every thread
+}
+
+__device__ __forceinline__ void tc_setup(TcSmem &S, const MlpBlock &P) {
+    tc_load_weights(P, S);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&S.tmem)), "r"(kTcCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+}
+
+// A wait that timed out: wait once more (bounded) for the MMAs in flight, then
+// free the tensor memory. Every thread calls it.
+__device__ __forceinline__ void tc_teardown(TcSmem &S, bool ok, unsigned phase) {
+    if (!ok) bar_wait(&S.bar, phase ^ 1u);
+    tc_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(kTcCols) : "memory");
+    }
+}
+
+// One tile after its features are in a1: the three layers; returns the three
+// outputs of this thread's row (false, in every thread: a wait timed out).
+__device__ __forceinline__ bool tc_tile(TcSmem &S, unsigned tmem, unsigned tlane, int r, unsigned &phase,
+                                        float out[kOut]) {
+    if (!tc_layer(S, 1, tmem, phase)) return false;
+    tc_hidden(S, tlane, r, S.b1);
+    if (!tc_layer(S, 2, tmem, phase)) return false;
+    tc_hidden(S, tlane, r, S.b2);
+    if (!tc_layer(S, 3, tmem, phase)) return false;
+    float v[16];
+    tc_ld16(tlane, v);
+#pragma unroll
+    for (int q = 0; q < kOut; q++) out[q] = v[q] + S.b3[q];
+    return true;
+}
+
+// rows of x (n x 16 FP32) -> y (n x 3); a timed-out wait leaves NaN in the tile's rows
+__global__ void __launch_bounds__(kTcRows) mlp_forward_tc_k(MlpBlock P, int64_t n, const float *x, float *y) {
+    __shared__ TcSmem S;
+    tc_setup(S, P);
+    const int r = threadIdx.x;
+    const unsigned tmem = S.tmem, tlane = tmem + ((unsigned)(32 * (r >> 5)) << 16);
+    unsigned phase = 0;
+    bool ok = true;
+    const int64_t ntile = (n + kTcRows - 1) / kTcRows;
+    const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+        const int64_t row = t * kTcRows + r;
+        float f[kInPad];
+        if (row < n && vec) {
+            const float4 *s = reinterpret_cast<const float4 *>(x + row * kInPad);
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float4 u = __ldg(s + c);
+                f[4 * c] = u.x; f[4 * c + 1] = u.y; f[4 * c + 2] = u.z; f[4 * c + 3] = u.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kInPad; k++) f[k] = row < n ? x[row * kInPad + k] : 0.f;
+        }
+        tc_put_features(S, r, f);
+        float o[kOut];
+        ok = tc_tile(S, tmem, tlane, r, phase, o);
+        if (row < n)
+            for (int q = 0; q < kOut; q++) y[row * kOut + q] = ok ? o[q] : __int_as_float(0x7fc00000);
+    }
+    tc_teardown(S, ok, phase);
+}
+
+// ---------------------------------------------------------------------------
 // correction of recorded (group, cell) pairs, evaluated at the group centre
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) mlp_pairs_k(MlpBlock P, CellGeo T, const int4 *groups, const int2 *pairs,
-                                                   const int *npairs, int cap, float eps, float *gcorr) {
-    __shared__ MlpSmem S;
-    __shared__ float feat[4][16][kInPad];
-    __shared__ float nrm[4][16];
-    __shared__ int gid[4][16];
-    load_mlp_smem(P, S);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+// One row per recorded pair: features of the cell seen from the group's
+// centre, the network on the tensor cores, and the output scaled by M / |r|^2
+// summed into the group's correction (rows of one group within a warp are
+// summed first: one atomic per group, warp and component).
+__global__ void __launch_bounds__(kTcRows) mlp_pairs_tc_k(MlpBlock P, CellGeo T, const int4 *groups,
+                                                          const int2 *pairs, const int *npairs, int cap, float eps,
+                                                          float *gcorr, DevState *st) {
+    __shared__ TcSmem S;
+    tc_setup(S, P);
+    const int r = threadIdx.x, lane = r & 31, wid = r >> 5;
+    const unsigned tmem = S.tmem, tlane = tmem + ((unsigned)(32 * wid) << 16);
+    unsigned phase = 0;
+    bool ok = true;
     const int np = min(*npairs, cap);
-    for (int r0 = (blockIdx.x * 4 + wid) * 16; r0 < np; r0 += gridDim.x * 64) {
-        if (lane < 16) {
-            const int r = r0 + lane;
-            float f[kInPad];
-            float norm = 0.f;
-            int gg = -1;
-            if (r < np) {
-                const int2 pr = pairs[r];
-                gg = pr.x;
-                const GroupRec grp = load_group(groups, pr.x);
-                const int m = member_of(T.moff, T.M, grp.first);
-                float lo[3], unit;
-                member_geo(T, m, lo, unit);
-                float gcen[3], c0[3];
-                box_centre(grp.lo, grp.hi, lo, unit, gcen);
-                const int4 b = T.cbox[pr.y];
-                geo_centre(b, lo, unit, c0);
-                const float4 q = T.cmom[3 * pr.y], q0 = T.cmom[3 * pr.y + 1], q1 = T.cmom[3 * pr.y + 2];
-                // r = g - com = -((c0 - g) + (com - c0))
-                const float rr[3] = {-((c0[0] - gcen[0]) + q.y), -((c0[1] - gcen[1]) + q.z),
-                                     -((c0[2] - gcen[2]) + q.w)};
-                const float side = unit * (float)(1 << (kMaxLevel - b.w));
-                norm = pair_features(q, q0, q1, side, eps, rr, f);
-            } else {
-                for (int k = 0; k < kInPad; k++) f[k] = 0.f;
-            }
-            for (int k = 0; k < kInPad; k++) feat[wid][lane][k] = f[k];
-            nrm[wid][lane] = norm;
-            gid[wid][lane] = gg;
+    const int ntile = (np + kTcRows - 1) / kTcRows;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int p = t * kTcRows + r;
+        float f[kInPad];
+        float norm = 0.f;
+        int gg = -1;
+        if (p < np) {
+            const int2 pr = pairs[p];
+            gg = pr.x;
+            const GroupRec grp = load_group(groups, pr.x);
+            const int m = member_of(T.moff, T.M, grp.first);
+            float lo[3], unit;
+            member_geo(T, m, lo, unit);
+            float gcen[3], c0[3];
+            box_centre(grp.lo, grp.hi, lo, unit, gcen);
+            const int4 b = T.cbox[pr.y];
+            geo_centre(b, lo, unit, c0);
+            const float4 q = T.cmom[3 * pr.y], q0 = T.cmom[3 * pr.y + 1], q1 = T.cmom[3 * pr.y + 2];
+            // r = g - com = -((c0 - g) + (com - c0))
+            const float rr[3] = {-((c0[0] - gcen[0]) + q.y), -((c0[1] - gcen[1]) + q.z),
+                                 -((c0[2] - gcen[2]) + q.w)};
+            const float side = unit * (float)(1 << (kMaxLevel - b.w));
+            norm = pair_features(q, q0, q1, side, eps, rr, f);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kInPad; k++) f[k] = 0.f;
         }
+        tc_put_features(S, r, f);
+        float o[kOut];
+        ok = tc_tile(S, tmem, tlane, r, phase, o);
+        if (!ok) {
+            if (r == 0) latch_err(st, kErrTimeout);
+            break;
+        }
+#pragma unroll
+        for (int q = 0; q < kOut; q++) S.red[wid][lane][q] = o[q] * norm;
+        const unsigned peers = __match_any_sync(0xffffffffu, gg);
         __syncwarp();
-        unsigned a[4];
-        a[0] = pack_bf16(feat[wid][g][2 * t], feat[wid][g][2 * t + 1]);
-        a[1] = pack_bf16(feat[wid][g + 8][2 * t], feat[wid][g + 8][2 * t + 1]);
-        a[2] = pack_bf16(feat[wid][g][2 * t + 8], feat[wid][g][2 * t + 9]);
-        a[3] = pack_bf16(feat[wid][g + 8][2 * t + 8], feat[wid][g + 8][2 * t + 9]);
-        float y[4];
-        mlp_warp_forward(S, a, y, nullptr, nullptr);
-        for (int q = 0; q < 2; q++) {
-            const int col = 2 * t + q;
-            if (col < kOut) {
-                if (gid[wid][g] >= 0) atomicAdd(&gcorr[3 * gid[wid][g] + col], y[q] * nrm[wid][g]);
-                if (gid[wid][g + 8] >= 0) atomicAdd(&gcorr[3 * gid[wid][g + 8] + col], y[2 + q] * nrm[wid][g + 8]);
+        if (gg >= 0 && lane == __ffs(peers) - 1) {
+            float sum[kOut] = {0.f, 0.f, 0.f};
+            for (unsigned mm = peers; mm; mm &= mm - 1) {
+                const int l = __ffs(mm) - 1;
+#pragma unroll
+                for (int q = 0; q < kOut; q++) sum[q] += S.red[wid][l][q];
             }
+#pragma unroll
+            for (int q = 0; q < kOut; q++) atomicAdd(&gcorr[3 * gg + q], sum[q]);
         }
         __syncwarp();
     }
+    tc_teardown(S, ok, phase);
 }
 
 // every star of group k gets the group's correction
@@ -613,8 +870,12 @@ rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y
     if (n == 0) return RV_OK;
     cudaStream_t s = (cudaStream_t)stream;
     MlpBlock P = mlp_block(const_cast<void *>(params));
-    const int grid = (int)std::min<int64_t>((n + 63) / 64, 65535);
-    mlp_forward_k<<<grid, 128, 0, s>>>(P, n, x, y);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return RV_E_CUDA;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kTcRows - 1) / kTcRows, (int64_t)sms * kTcCtas));
+    mlp_forward_tc_k<<<grid, kTcRows, 0, s>>>(P, n, x, y);
     return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
 }
 
@@ -683,9 +944,9 @@ rv_status rv_tree_forces_mlp(rv_ctx *c, const void *params, float theta, float t
     int ncell, ngroup;
     if ((r = read_ncell(c, s, &ncell, &ngroup)) != RV_OK) return r;
     MlpBlock P = mlp_block(const_cast<void *>(params));
-    const int grid = std::max(1, std::min(ceil_div(pair_cap, 64), c->num_sms * 8));
-    mlp_pairs_k<<<grid, 128, 0, s>>>(P, cell_geo(c, ncell), c->w.groups, reinterpret_cast<const int2 *>(pairs),
-                                     npairs, pair_cap, eps_star, gcorr);
+    const int grid = std::max(1, std::min(ceil_div(pair_cap, kTcRows), c->num_sms * kTcCtas));
+    mlp_pairs_tc_k<<<grid, kTcRows, 0, s>>>(P, cell_geo(c, ncell), c->w.groups, reinterpret_cast<const int2 *>(pairs),
+                                            npairs, pair_cap, eps_star, gcorr, c->w.st);
     count_launch(c);
     mlp_apply_k<<<std::max(1, ceil_div(ngroup, 256)), 256, 0, s>>>(c->w.groups, &c->w.st->ngroup, c->w.perm, gcorr, ax,
                                                                  ay, az);

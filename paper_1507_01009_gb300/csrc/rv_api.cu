@@ -515,6 +515,7 @@ rv_status rv_sync_status(rv_ctx *c, void *stream) {
         case kErrCells: return set_err(c, RV_E_WORKSPACE, "tree has more cells than the workspace holds (%lld)", (long long)c->cell_cap);
         case kErrPert: return set_err(c, RV_E_WORKSPACE, "more perturbers inside the radius than the output holds");
         case kErrPairs: return set_err(c, RV_E_WORKSPACE, "more recorded (group, cell) pairs than the buffer holds");
+        case kErrTimeout: return set_err(c, RV_E_TIMEOUT, "a tensor-core completion wait timed out");
         default: return set_err(c, RV_E_CUDA, "unknown device error %d", err);
     }
 }

@@ -32,7 +32,7 @@ constexpr int kMaxChain = 250;
 constexpr int kMaxPert = 5000;
 
 // Error codes latched by kernels (first one wins).
-enum DevErr : int { kErrNone = 0, kErrStack = 1, kErrCells = 2, kErrPert = 3, kErrPairs = 4 };
+enum DevErr : int { kErrNone = 0, kErrStack = 1, kErrCells = 2, kErrPert = 3, kErrPairs = 4, kErrTimeout = 5 };
 
 // Device-resident scalars (one small block in the workspace).
 struct DevState {

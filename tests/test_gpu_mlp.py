@@ -47,6 +47,43 @@ def test_forward_matches_oracle(rvmod):
     assert err.max() <= 2e-2 * scale
 
 
+def test_forward_many_tiles_ragged_and_unaligned(rvmod):
+    """The tensor-core forward over more tiles of 128 rows than resident CTAs
+    (each CTA loops), a ragged last tile, and rows read from a buffer that is
+    not 16-byte aligned (scalar loads): identical results either way."""
+    import torch
+    mlp = rvmod.Mlp(seed=6)
+    n = 300_000 + 77
+    X = _features(n, 2)
+    xa = torch.from_numpy(X).cuda()
+    y = mlp.forward(xa).cpu().numpy()
+    buf = torch.zeros(n * 16 + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = xa.reshape(-1)
+    xu = buf[1:].view(n, 16)
+    assert xu.data_ptr() % 16 != 0
+    yu = mlp.forward(xu).cpu().numpy()
+    assert np.array_equal(y, yu)
+    assert np.array_equal(y, mlp.forward(xa).cpu().numpy())          # deterministic
+    yo, _ = oracle.mlp_forward(_params_np(mlp), X.astype(np.float64))
+    err = np.abs(y.astype(np.float64) - yo)
+    scale = np.sqrt((yo ** 2).mean())
+    assert np.sqrt((err ** 2).mean()) <= 1e-3 * scale
+    assert err.max() <= 2e-2 * scale
+    assert np.all(np.isfinite(y))
+
+
+def test_forward_tiny_inputs(rvmod):
+    """One row, a partial tile, and zero rows."""
+    import torch
+    mlp = rvmod.Mlp(seed=9)
+    for n in (1, 127, 128, 129):
+        X = _features(n, 10 + n)
+        y = mlp.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+        yo, _ = oracle.mlp_forward(_params_np(mlp), X.astype(np.float64))
+        assert np.abs(y - yo).max() <= 2e-2 * max(np.sqrt((yo ** 2).mean()), 1e-6), n
+    assert mlp.forward(torch.zeros((0, 16), dtype=torch.float32, device="cuda")).shape == (0, 3)
+
+
 def test_gradient_matches_oracle(rvmod):
     import torch
     mlp = rvmod.Mlp(seed=6)
