@@ -71,6 +71,8 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.gcnt = (int *)take(4 * cap);
     t.groups = (int4 *)take(32 * (n + 1));   // every group holds a star
     t.gact = (uint8_t *)take(n + 1);
+    t.scost = (float *)take(4 * n);
+    t.gorder = (int *)take(4 * (n + 1));
     t.block_count = (unsigned long long *)take(16);
     t.partials = (int *)take(4 * nparts);
     t.pert_idx = (int *)take(4 * kPertTotal);

@@ -42,7 +42,8 @@ struct DevState {
     int err;          // latched DevErr
     int n_pert;       // perturbers selected by the last selection
     int stack_hwm;    // deepest walk stack seen
-    int pad[2];
+    int cost_n;       // stars whose walk costs scost holds (0: none)
+    int pad;
     unsigned long long n_p2p, n_m2p;  // interaction counts of the last walk
     double bounds[5];                 // min x, y, z, L, 2^21 / L
     int lvoff[kLevels + 1];           // first cell of each level, then ncell
@@ -65,6 +66,8 @@ struct Workspace {
     int *gcnt;            // groups of each cell, scanned in place to each cell's first group
     int4 *groups;         // 2 int4 per group: (first, count, lo x, lo y), (lo z, hi x, hi y, hi z)
     uint8_t *gact;        // block time steps: groups holding an active star
+    float *scost;         // per caller star: list cost of its group in the last walk (scheduling only)
+    int *gorder;          // the walk's queue order of the groups
     unsigned long long *block_count;  // block time steps: active star updates so far
     int *partials;        // scan block sums
     // perturbers and chain hand-off

@@ -95,6 +95,9 @@ struct WalkArgs {
     const float *arx, *ary, *arz;
     // optional group mask (block time steps): only groups with gact[g] != 0 are walked
     const uint8_t *gact;
+    // queue order of the groups, and the per-star list cost written for the next walk's order
+    const int *order;
+    float *scost;
     // spline softening of the stars (h = 2.8 eps)
     Spline spl;
 };
@@ -746,9 +749,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             }
             continue;
         }
-        // ---- a group of the tree (skipped when the mask says none of its stars is active)
-        if (A.gact && !A.gact[gi - A.n_extra]) continue;
-        const GroupRec grp = load_group(A.groups, gi - A.n_extra);
+        // ---- a group of the tree, in queue order (skipped when the mask says none of its stars is active)
+        const int gk = A.order[gi - A.n_extra];
+        if (A.gact && !A.gact[gk]) continue;
+        const GroupRec grp = load_group(A.groups, gk);
         if (grp.first < 0 || grp.count < 1 || grp.count > kMaxGroup || grp.first + grp.count > A.n) {
             if (lane == 0) latch_err(A.st, kErrStack);
             continue;
@@ -794,7 +798,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             for (int o = 16; o > 0; o >>= 1) am = fminf(am, __shfl_xor_sync(0xffffffffu, am, o));
             if (am > 0.f) K = __fmul_rn(__fmul_rn(A.rel_alpha, am), __fmul_rn(G.unit, G.unit));
         }
-        bool ok = walk_group<SOFT, QUAD, REC, REL, SPL>(A, G, mac_thr, rec_thr, gi - A.n_extra, wsm, blo, bhi, g, tg,
+        bool ok = walk_group<SOFT, QUAD, REC, REL, SPL>(A, G, mac_thr, rec_thr, gk, wsm, blo, bhi, g, tg,
                                                    f2_pack(A.eps2, A.eps2), acc, a2, a3, K);
         if (!ok) {
             if (lane == 0) latch_err(A.st, kErrStack);
@@ -804,6 +808,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         nm2p += a3 * (unsigned long long)s;
         Acc tots[2];
         combine_shares(acc, s, p, k, scr, tots);
+        const float cost = (float)a2 + 2.5f * (float)a3;   // list pairs, a cell costing ~2.5 stars
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int i = lane + 32 * h;
@@ -819,12 +824,78 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             A.ay[o] = tot.ay + tot.cy;
             A.az[o] = tot.az + tot.cz;
             A.pot[o] = tot.ph + tot.cp;
+            A.scost[o] = cost;
         }
     }
     if (lane == 0) {
         atomicAdd(&A.st->n_p2p, np2p);
         atomicAdd(&A.st->n_m2p, nm2p);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Queue order of the groups: most expensive first (longest-processing-time
+// first: the walk's tail then holds the cheapest groups). The estimate is the
+// list cost the last walk recorded for the group's first star, if that walk
+// covered the same number of stars (st->cost_n); otherwise the volume of the
+// group's box, smallest first (small boxes sit in dense regions with long
+// lists). Groups are bucketed by log2 of the estimate (1/16 steps); the
+// order within a bucket is unspecified. The forces do not depend on it.
+constexpr int kOrderBins = 1024;
+
+__device__ __forceinline__ int order_bin(const int4 *groups, const int *perm, const float *scost, int n, bool hist,
+                                         int g) {
+    const GroupRec r = load_group(groups, g);
+    float lv;
+    if (hist) {
+        const int first = min(max(r.first, 0), n - 1);
+        // any stored value is a finite estimate >= 1 here (NaN -> 1)
+        const float c = fminf(fmaxf(scost[perm[first]], 1.f), 1e30f);
+        lv = 64.f - log2f(c);   // descending cost (a cost above 2^64 shares the first bin)
+    } else {
+        lv = log2f((float)max(r.hi[0] - r.lo[0], 1)) + log2f((float)max(r.hi[1] - r.lo[1], 1)) +
+             log2f((float)max(r.hi[2] - r.lo[2], 1));
+    }
+    return min(max((int)(16.f * lv), 0), kOrderBins - 1);
+}
+
+__global__ void __launch_bounds__(kOrderBins) group_order_k(const int4 *groups, DevState *st, const int *perm,
+                                                            const float *scost, int n, int *order) {
+    __shared__ int bins[kOrderBins];
+    __shared__ int wsum[kOrderBins / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int ng = st->ngroup;
+    const bool hist = st->cost_n == n;
+    bins[t] = 0;
+    __syncthreads();
+    for (int g = t; g < ng; g += kOrderBins) atomicAdd(&bins[order_bin(groups, perm, scost, n, hist, g)], 1);
+    __syncthreads();
+    // exclusive scan of the bins, one per thread
+    const int v = bins[t];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int x = wsum[lane];
+        int sx = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, sx, o);
+            if (lane >= o) sx += y;
+        }
+        wsum[lane] = sx - x;
+    }
+    __syncthreads();
+    bins[t] = incl - v + wsum[w];
+    __syncthreads();
+    for (int g = t; g < ng; g += kOrderBins) order[atomicAdd(&bins[order_bin(groups, perm, scost, n, hist, g)], 1)] = g;
+    // this walk records the costs of its stars
+    if (t == 0) st->cost_n = n;
 }
 
 // MAC thresholds: the smallest integer D with fl(theta^2 * D) > s^2 (FP64,
@@ -896,6 +967,8 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.pair_cap = rec ? rec->cap : 0;
     if (rec) A.rec = mac_table(rec->theta_rec);
     A.gact = gact;
+    A.order = w.gorder;
+    A.scost = w.scost;
     const bool spline = c->cfg.softening == 1 && eps_star > 0.f;
     {
         const float h = 2.8f * eps_star;
@@ -937,6 +1010,10 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
         }
     }
     if (ev0) cudaEventRecord(ev0, s);
+    if (c->n > 0) {
+        group_order_k<<<1, kOrderBins, 0, s>>>(w.groups, w.st, w.perm, w.scost, (int)c->n, w.gorder);
+        count_launch(c);
+    }
     if (spline) {
         if (rec) return set_err(c, RV_E_INVAL, "no pair record with spline softening");
         if (rel)
