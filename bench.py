@@ -360,7 +360,7 @@ def run_gpu(args):
     xs = [torch.from_numpy(np.ascontiguousarray(p32[a])).to(dev) for a in range(3)]
     ms = torch.from_numpy(d["mass"].astype(np.float32)).to(dev)
     tuned = autotune.autotune(*xs, ms, offsets=d["offsets"], theta=d["theta"], eps_star=float(np.float32(d["eps"])),
-                              grid=autotune.candidates(groups=(32, 64), leaves=(16, 32), tiles=(64, 128)), reps=2)
+                              grid=autotune.candidates(groups=(32, 64), leaves=(16, 24, 32), tiles=(64, 128)), reps=2)
     tune = tuned["config"]
     del xs, ms
     ctx = rv.Context(n, theta=d["theta"], eps_star=float(np.float32(d["eps"])), mac=d["mac"], alpha=d["alpha"],

@@ -73,6 +73,8 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.gact = (uint8_t *)take(n + 1);
     t.scost = (float *)take(4 * n);
     t.gorder = (int *)take(4 * (n + 1));
+    t.gbin = (int *)take(4 * (n + 1));
+    t.obins = (int *)take(4 * 1024);
     t.block_count = (unsigned long long *)take(16);
     t.partials = (int *)take(4 * nparts);
     t.pert_idx = (int *)take(4 * kPertTotal);

@@ -68,6 +68,8 @@ struct Workspace {
     uint8_t *gact;        // block time steps: groups holding an active star
     float *scost;         // per caller star: list cost of its group in the last walk (scheduling only)
     int *gorder;          // the walk's queue order of the groups
+    int *gbin;            // each group's cost bin (queue order scratch)
+    int *obins;           // bin counts, then next free slots (queue order scratch, 1024)
     unsigned long long *block_count;  // block time steps: active star updates so far
     int *partials;        // scan block sums
     // perturbers and chain hand-off

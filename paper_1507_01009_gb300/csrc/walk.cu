@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
 // group's box, smallest first (small boxes sit in dense regions with long
 // lists). Groups are bucketed by log2 of the estimate (1/16 steps); the
 // order within a bucket is unspecified. The forces do not depend on it.
-constexpr int kOrderBins = 1024;
+constexpr int kOrderBins = 1024;   // the workspace's obins holds this many
 
 __device__ __forceinline__ int order_bin(const int4 *groups, const int *perm, const float *scost, int n, bool hist,
                                          int g) {
@@ -859,18 +859,23 @@ __device__ __forceinline__ int order_bin(const int4 *groups, const int *perm, co
     return min(max((int)(16.f * lv), 0), kOrderBins - 1);
 }
 
-__global__ void __launch_bounds__(kOrderBins) group_order_k(const int4 *groups, DevState *st, const int *perm,
-                                                            const float *scost, int n, int *order) {
-    __shared__ int bins[kOrderBins];
-    __shared__ int wsum[kOrderBins / 32];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+// (A) each group's bin, and the bin counts (bins zeroed before)
+__global__ void group_bins_k(const int4 *groups, DevState *st, const int *perm, const float *scost, int n, int *gbin,
+                             int *bins) {
     const int ng = st->ngroup;
     const bool hist = st->cost_n == n;
-    bins[t] = 0;
-    __syncthreads();
-    for (int g = t; g < ng; g += kOrderBins) atomicAdd(&bins[order_bin(groups, perm, scost, n, hist, g)], 1);
-    __syncthreads();
-    // exclusive scan of the bins, one per thread
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const int b = order_bin(groups, perm, scost, n, hist, g);
+        gbin[g] = b;
+        atomicAdd(&bins[b], 1);
+    }
+}
+
+// (B) exclusive scan of the bin counts, one bin per thread; the walk that
+// follows records the costs of its stars
+__global__ void __launch_bounds__(kOrderBins) group_bins_scan_k(DevState *st, int n, int *bins) {
+    __shared__ int wsum[kOrderBins / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int v = bins[t];
     int incl = v;
 #pragma unroll
@@ -892,10 +897,14 @@ __global__ void __launch_bounds__(kOrderBins) group_order_k(const int4 *groups, 
     }
     __syncthreads();
     bins[t] = incl - v + wsum[w];
-    __syncthreads();
-    for (int g = t; g < ng; g += kOrderBins) order[atomicAdd(&bins[order_bin(groups, perm, scost, n, hist, g)], 1)] = g;
-    // this walk records the costs of its stars
     if (t == 0) st->cost_n = n;
+}
+
+// (C) each group to its place: order[next free slot of its bin] = g
+__global__ void group_scatter_k(const DevState *st, const int *gbin, int *bins, int *order) {
+    const int ng = st->ngroup;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        order[atomicAdd(&bins[gbin[g]], 1)] = g;
 }
 
 // MAC thresholds: the smallest integer D with fl(theta^2 * D) > s^2 (FP64,
@@ -1011,8 +1020,14 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     }
     if (ev0) cudaEventRecord(ev0, s);
     if (c->n > 0) {
-        group_order_k<<<1, kOrderBins, 0, s>>>(w.groups, w.st, w.perm, w.scost, (int)c->n, w.gorder);
-        count_launch(c);
+        int *bins = w.obins, *gbin = w.gbin;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 255) / 256, (int64_t)c->num_sms * 4));
+        e = cudaMemsetAsync(bins, 0, sizeof(int) * kOrderBins, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "walk order");
+        group_bins_k<<<grid, 256, 0, s>>>(w.groups, w.st, w.perm, w.scost, (int)c->n, gbin, bins);
+        group_bins_scan_k<<<1, kOrderBins, 0, s>>>(w.st, (int)c->n, bins);
+        group_scatter_k<<<grid, 256, 0, s>>>(w.st, gbin, bins, w.gorder);
+        c->launches += 3;
     }
     if (spline) {
         if (rec) return set_err(c, RV_E_INVAL, "no pair record with spline softening");
