@@ -358,6 +358,14 @@ rv_status rv_mlp_init(void *params, uint64_t seed, void *stream);
  * float4). A completion wait that times out (after ~1 s) leaves NaN in the
  * rows of that tile. */
 rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y, void *stream);
+/* Self-test of the bounded completion wait that guards every tensor-core
+ * (tcgen05) kernel here (the paper has no counterpart: this checks the failure
+ * path without faulting the GPU). One CTA allocates 32 TMEM columns, waits up
+ * to limit_cycles (0 .. 2^32) SM clock cycles on an mbarrier that gets its one
+ * arrival (arrive = 1) or none (arrive = 0), frees the TMEM and writes
+ * gave_up[0] (device int32) = 1 if the wait ran out, else 0. Asynchronous on
+ * `stream`; RV_E_INVAL on bad arguments. */
+rv_status rv_wait_selftest(int64_t limit_cycles, int32_t arrive, int32_t *gave_up, void *stream);
 /* Mean squared error of network(x) against t[n][3] and its gradient with
  * respect to the FP32 parameter vector (grad: device FP32 [5768], ordered W1
  * 16x64, b1, W2 64x64, b2, W3 64x8, b3, row-major; loss: device FP32 [1] or

@@ -539,9 +539,9 @@ __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::a
 // shared-memory writes of this thread become visible to the tensor cores' reads
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Waits for the phase of parity `ph` of the barrier; false after about 2^31
-// clock cycles (~1 s) without completion.
-__device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned ph) {
+// Waits for the phase of parity `ph` of the barrier; false after `limit`
+// clock cycles (default 2^31, ~1 s) without completion.
+__device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned ph, long long limit = 1ll << 31) {
     const unsigned a = smem_u32(bar);
     const long long t0 = clock64();
     while (true) {
@@ -553,7 +553,7 @@ __device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned ph) {
             : "r"(a), "r"(ph)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -699,6 +699,40 @@ __device__ __forceinline__ bool tc_tile(TcSmem &S, unsigned tmem, unsigned tlane
 #pragma unroll
     for (int q = 0; q < kOut; q++) out[q] = v[q] + S.b3[q];
     return true;
+}
+
+// The bounded completion wait on its own: TMEM allocated as the inference
+// kernels do, then a wait of `limit` cycles on an mbarrier that receives its
+// one arrival (arrive = 1) or none (arrive = 0: the wait must give up), then
+// TMEM freed. gave_up[0] = 1 if the wait gave up in any thread.
+__global__ void __launch_bounds__(kTcRows) wait_selftest_k(long long limit, int arrive, int *gave_up) {
+    __shared__ unsigned long long bar;
+    __shared__ unsigned tmem;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem)), "r"(32) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (arrive && threadIdx.x == 0) {
+        unsigned long long state;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(&bar)) : "memory");
+    }
+    const bool ok = bar_wait(&bar, 0u, limit);
+    const bool all_ok = !__syncthreads_or(!ok);
+    tc_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
+    }
+    if (threadIdx.x == 0) gave_up[0] = all_ok ? 0 : 1;
 }
 
 // rows of x (n x 16 FP32) -> y (n x 3); a timed-out wait leaves NaN in the tile's rows
@@ -876,6 +910,12 @@ rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y
         return RV_E_CUDA;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kTcRows - 1) / kTcRows, (int64_t)sms * kTcCtas));
     mlp_forward_tc_k<<<grid, kTcRows, 0, s>>>(P, n, x, y);
+    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_wait_selftest(int64_t limit_cycles, int32_t arrive, int32_t *gave_up, void *stream) {
+    if (!gave_up || limit_cycles < 0 || limit_cycles > (1ll << 32) || (arrive != 0 && arrive != 1)) return RV_E_INVAL;
+    wait_selftest_k<<<1, kTcRows, 0, (cudaStream_t)stream>>>((long long)limit_cycles, arrive, gave_up);
     return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
 }
 

@@ -95,7 +95,8 @@ struct WalkArgs {
     const float *arx, *ary, *arz;
     // optional group mask (block time steps): only groups with gact[g] != 0 are walked
     const uint8_t *gact;
-    // queue order of the groups, and the per-star list cost written for the next walk's order
+    // queue order of the groups (null: build order), and the per-star list cost
+    // written for the next walk's order
     const int *order;
     float *scost;
     // spline softening of the stars (h = 2.8 eps)
@@ -750,7 +751,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             continue;
         }
         // ---- a group of the tree, in queue order (skipped when the mask says none of its stars is active)
-        const int gk = A.order[gi - A.n_extra];
+        const int gk = A.order ? A.order[gi - A.n_extra] : gi - A.n_extra;
         if (A.gact && !A.gact[gk]) continue;
         const GroupRec grp = load_group(A.groups, gk);
         if (grp.first < 0 || grp.count < 1 || grp.count > kMaxGroup || grp.first + grp.count > A.n) {
@@ -842,6 +843,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
 // lists). Groups are bucketed by log2 of the estimate (1/16 steps); the
 // order within a bucket is unspecified. The forces do not depend on it.
 constexpr int kOrderBins = 1024;   // the workspace's obins holds this many
+constexpr int kOrderMinStars = 1 << 17;   // smaller systems walk their groups in build order
 
 __device__ __forceinline__ int order_bin(const int4 *groups, const int *perm, const float *scost, int n, bool hist,
                                          int g) {
@@ -976,7 +978,8 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.pair_cap = rec ? rec->cap : 0;
     if (rec) A.rec = mac_table(rec->theta_rec);
     A.gact = gact;
-    A.order = w.gorder;
+    // systems with fewer groups than resident walk warps gain nothing from an order
+    A.order = c->n >= kOrderMinStars ? w.gorder : nullptr;
     A.scost = w.scost;
     const bool spline = c->cfg.softening == 1 && eps_star > 0.f;
     {
@@ -1019,7 +1022,7 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
         }
     }
     if (ev0) cudaEventRecord(ev0, s);
-    if (c->n > 0) {
+    if (A.order) {
         int *bins = w.obins, *gbin = w.gbin;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 255) / 256, (int64_t)c->num_sms * 4));
         e = cudaMemsetAsync(bins, 0, sizeof(int) * kOrderBins, s);

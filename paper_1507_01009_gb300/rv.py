@@ -30,7 +30,7 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_block_start", "rv_block_steps", "rv_block_levels", "rv_block_count", "rv_chain_start_radius", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
            "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
            "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
-           "rv_mlp_samples", "rv_tree_forces_mlp"]
+           "rv_mlp_samples", "rv_tree_forces_mlp", "rv_wait_selftest"]
 
 
 class RvError(RuntimeError):
@@ -133,6 +133,7 @@ def _declare(L):
     L.rv_mlp_adam.argtypes = [vp, vp, i32, f32, f32, f32, f32, vp]
     L.rv_mlp_samples.argtypes = [vp, f32, f32, i64, C.c_uint64, vp, vp, vp, vp]
     L.rv_tree_forces_mlp.argtypes = [vp, vp, f32, f32, f32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
+    L.rv_wait_selftest.argtypes = [i64, i32, vp, vp]
     L.rv_launch_count.argtypes = [vp]
     L.rv_launch_count.restype = C.c_int64
     L.rv_last_error.argtypes = [vp]
@@ -609,6 +610,17 @@ class Mlp:
 def torch_float32():
     import torch
     return torch.float32
+
+
+def wait_selftest(limit_cycles, arrive, stream=None):
+    """Runs the bounded tensor-core completion wait once (see rv_wait_selftest):
+    returns 1 if it ran out after limit_cycles, else 0."""
+    import torch
+    flag = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    st = load().rv_wait_selftest(int(limit_cycles), int(bool(arrive)), _ptr(flag), _stream(stream))
+    if st != RV_OK:
+        raise RvError(st, "rv_wait_selftest")
+    return int(flag.item())
 
 
 def mlp_samples(ctx, theta, eps_star, n, seed, stream=None):

@@ -84,6 +84,26 @@ def test_forward_tiny_inputs(rvmod):
     assert mlp.forward(torch.zeros((0, 16), dtype=torch.float32, device="cuda")).shape == (0, 3)
 
 
+def test_bounded_wait_gives_up_and_context_stays_usable(rvmod):
+    """The completion wait that guards the tensor-core kernels gives up after
+    its limit when nothing arrives (no fault, no hang), succeeds when the
+    arrival comes, frees its tensor memory either way, and the network runs
+    normally afterwards."""
+    import time
+    import torch
+    mlp = rvmod.Mlp(seed=11)
+    X = torch.from_numpy(_features(5000, 12)).cuda()
+    y0 = mlp.forward(X).cpu().numpy()
+    t = time.time()
+    assert rvmod.wait_selftest(1 << 20, arrive=False) == 1          # ~0.5 ms at 2 GHz
+    assert time.time() - t < 10.0
+    assert rvmod.wait_selftest(1 << 31, arrive=True) == 0
+    assert rvmod.wait_selftest(1 << 20, arrive=False) == 1
+    assert np.array_equal(mlp.forward(X).cpu().numpy(), y0)
+    with pytest.raises(rvmod.RvError):
+        rvmod.wait_selftest(-1, arrive=False)
+
+
 def test_gradient_matches_oracle(rvmod):
     import torch
     mlp = rvmod.Mlp(seed=6)

@@ -209,31 +209,31 @@ def test_deterministic(rvmod):
         np.testing.assert_array_equal(u, w)
 
 
-def test_every_star_written_in_both_queue_orders(rvmod):
-    """The walk takes its groups in an order estimated from costs (box volume
-    on the first walk of a context, the recorded list costs on later ones;
-    a different star count falls back to the volume): every star is written
-    under each order, and the results do not depend on it."""
+def test_every_star_written_in_every_queue_order(rvmod):
+    """The walk takes its groups in an order estimated from costs: box volume
+    on the first walk of a context or after the star count changed, the
+    recorded list costs on later walks, build order below 2^17 stars. Every
+    star is written under each order, and the results do not depend on it."""
     import torch
-    n = 1 << 17
+    n = 1 << 18
     p32, m32 = hernquist32(n, 31)
     ctx = rvmod.Context(n, theta=0.5, eps_star=0.005, n_leaf=32, group=64, tile=128)
-    gpu_tree(ctx, p32, m32)
-    runs = []
-    for _ in range(3):
-        out = [torch.full((n,), float("nan"), dtype=torch.float32, device="cuda") for _ in range(4)]
+
+    def walk(k):
+        gpu_tree(ctx, p32[:, :k].copy(), m32[:k].copy())
+        out = [torch.full((k,), float("nan"), dtype=torch.float32, device="cuda") for _ in range(4)]
         ctx.tree_forces(out=out)
         ctx.sync_status()
-        runs.append(np.stack([o.cpu().numpy() for o in out]))
-        assert np.all(np.isfinite(runs[-1]))
+        a = np.stack([o.cpu().numpy() for o in out])
+        assert np.all(np.isfinite(a)), k
+        return a
+
+    runs = [walk(n) for _ in range(3)]        # volume order, then recorded costs twice
     assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[1], runs[2])
-    # fewer stars in the same context: the recorded costs no longer apply
-    k = n - 1000
-    gpu_tree(ctx, p32[:, :k].copy(), m32[:k].copy())
-    out = [torch.full((k,), float("nan"), dtype=torch.float32, device="cuda") for _ in range(4)]
-    ctx.tree_forces(out=out)
-    ctx.sync_status()
-    assert np.all(np.isfinite(np.stack([o.cpu().numpy() for o in out])))
+    k = n - 1000                                # another star count: volume order again
+    a1, a2 = walk(k), walk(k)
+    assert np.array_equal(a1, a2)
+    walk(5000)                                  # build order
 
 
 def test_extra_particle_vs_oracle(rvmod):
