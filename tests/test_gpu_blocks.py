@@ -85,6 +85,37 @@ def test_block_fixed_levels_vs_oracle(rvmod):
     assert upd < 24 * 4096
 
 
+def test_masked_walk_equals_full_walk_for_active_stars(rvmod):
+    """2^18 Hernquist stars (large enough for the cost-ordered walk queue),
+    levels by radius, L = 2: after one substep the active stars' new
+    accelerations equal, bit for bit, those of a full force pass at the same
+    positions (the masked walk skips whole groups and changes no list)."""
+    import torch
+    n = 1 << 18
+    w = ics.hernquist(n, 41)
+    p32, m32 = stars32(w.pos, w.mass)
+    v32 = np.ascontiguousarray(w.vel, dtype=np.float32)
+    eps = float(np.float32(0.005))
+    r = np.linalg.norm(p32.astype(np.float64), axis=0)
+    lv = np.select([r < 0.3, r < 1.0], [2, 1], 0).astype(np.int8)
+    ctx = rvmod.Context(n, theta=0.5, eps_star=eps, n_leaf=24, group=64, tile=128)
+    S = rvmod.System(p32, v32, m32)
+    B = rvmod.Blocks(n, 4e-3, 2, adapt=False, level=lv)
+    ctx.block_start(S, B)
+    ctx.block_steps(S, B, 1)                                    # substep 1: level-2 stars active
+    ctx.sync_status()
+    active = lv == 2
+    assert 0 < active.sum() < n and ctx.block_count() == int(active.sum())
+    xs = np.stack([t.cpu().numpy() for t in (S.x, S.y, S.z)])
+    a_blk = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)])
+    full = rvmod.Context(n, theta=0.5, eps_star=eps, n_leaf=24, group=64, tile=128)
+    S2 = rvmod.System(xs, v32, m32)
+    full.system_forces(S2)
+    full.sync_status()
+    a_full = np.stack([t.cpu().numpy() for t in (S2.ax, S2.ay, S2.az)])
+    np.testing.assert_array_equal(a_blk[:, active], a_full[:, active])
+
+
 def test_block_levels_match_oracle(rvmod):
     """The level rule on identical FP32 inputs: bit-identical levels, at the
     start and at substeps with and without step boundaries."""
