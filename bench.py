@@ -36,6 +36,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -287,14 +288,28 @@ def job_throughput(world: int, stars_per_rank: int, steps: int, total_ms: float)
     return world * stars_per_rank * steps / (total_ms / 1e3)
 
 
-def p99_vs_direct(d, S, sample=2048, seed=77, model=False):
+def _rel_err(a, ref):
+    """Per-body relative error |a - ref| / |ref| of (3, k) vectors."""
+    return np.linalg.norm(a - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+def _p99(e):
+    """Nearest-rank 99th percentile: sorted ascending, index ceil(0.99 k) - 1."""
+    s = np.sort(np.asarray(e, np.float64))
+    return float(s[max(0, math.ceil(0.99 * s.size) - 1)]) if s.size else float("nan")
+
+
+def p99_vs_direct(d, S, ctx, sample=2048, seed=77, model=False):
     """p99 relative acceleration error of the current GPU forces against the
-    FP64 direct sum over each sampled star's own member (stars softened,
-    chain members unsoftened). With model=True the reference is the direct
-    sum of the method's own model (Sect. 2): perturbers feel each chain member,
-    every other star feels the chain's centre of mass as one point mass."""
+    FP64 direct sum (the library's rv_direct_fp64, on the GPU) over each
+    sampled star's own member (stars softened, chain members unsoftened).
+    With model=True the reference is the direct sum of the method's own model
+    (Sect. 2): perturbers (the library's own selection) feel each chain
+    member, every other star feels the chain's centre of mass as one point
+    mass."""
+    import torch
     import ics
-    import oracle
+    from paper_1507_01009_gb300 import rv
     xs = np.stack([t.cpu().numpy() for t in (S.x, S.y, S.z)]).astype(np.float64)
     a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
     m32 = S.m.cpu().numpy().astype(np.float64)
@@ -309,8 +324,8 @@ def p99_vs_direct(d, S, sample=2048, seed=77, model=False):
             continue
         pos, mass, epsv = xs[:, s:e], m32[s:e], np.full(e - s, eps)
         if cx is None:
-            ad, _ = oracle.direct(pos, mass, epsv, targets=t - s)
-            errs.append(oracle.rel_err(a[:, t], ad))
+            ad, _ = rv.direct_fp64(pos, mass, epsv, t - s)
+            errs.append(_rel_err(a[:, t], ad))
             continue
         nch = S.n_chain
         cm = d["chain_m"][k * nch:(k + 1) * nch]
@@ -318,23 +333,25 @@ def p99_vs_direct(d, S, sample=2048, seed=77, model=False):
         res_pos = np.concatenate([pos, cpos.T], 1)
         res_m = np.concatenate([mass, cm])
         res_e = np.concatenate([epsv, np.zeros(nch)])
-        ad, _ = oracle.direct(res_pos, res_m, res_e, targets=t - s)
+        ad, _ = rv.direct_fp64(res_pos, res_m, res_e, t - s)
         if model:
             com = (cm[:, None] * cpos).sum(0) / cm.sum()
-            p32 = pos.astype(np.float32)
-            c32 = com.astype(np.float32)
+            xyz = [torch.from_numpy(np.ascontiguousarray(pos[q].astype(np.float32))).cuda() for q in range(3)]
+            c32 = [float(v) for v in com.astype(np.float32)]
             if d["pert_mode"] == 1:
-                pert = oracle.radius(p32, c32, np.float32(np.float32(d["pert_radius"]) ** 2))
+                idx, cnt = ctx.select_perturbers(*xyz, c32, 1, radius=float(d["pert_radius"]), cap=e - s)
             else:
-                pert = oracle.knn(p32, c32, d["pert_k"])
+                idx, cnt = ctx.select_perturbers(*xyz, c32, 2, k=int(d["pert_k"]), cap=e - s)
+            ctx.sync_status()
+            pert = idx[:int(cnt.item())].cpu().numpy()
             far = ~np.isin(t - s, pert)
             if far.any():
                 com_pos = np.concatenate([pos, com[:, None]], 1)
-                acom, _ = oracle.direct(com_pos, np.concatenate([mass, [cm.sum()]]),
-                                        np.concatenate([epsv, [0.0]]), targets=(t - s)[far])
+                acom, _ = rv.direct_fp64(com_pos, np.concatenate([mass, [cm.sum()]]), np.concatenate([epsv, [0.0]]),
+                                         (t - s)[far])
                 ad[:, far] = acom
-        errs.append(oracle.rel_err(a[:, t], ad))
-    return oracle.percentile(np.concatenate(errs), 0.99)
+        errs.append(_rel_err(a[:, t], ad))
+    return _p99(np.concatenate(errs))
 
 
 def run_gpu(args):
@@ -429,8 +446,8 @@ def run_gpu(args):
         value = job_throughput(ws, upd / args.steps, args.steps, total_ms)
     else:
         value = job_throughput(ws, n, args.steps, total_ms)
-    p99 = p99_vs_direct(d, S) if rank == 0 else None
-    p99_model = p99_vs_direct(d, S, model=True) if rank == 0 and S.n_chain > 0 else p99
+    p99 = p99_vs_direct(d, S, ctx) if rank == 0 else None
+    p99_model = p99_vs_direct(d, S, ctx, model=True) if rank == 0 and S.n_chain > 0 else p99
 
     # ---- dominant kernel: the walk. Its launches inside the timed steps were timed
     # with CUDA events on the launching stream (not possible inside a replayed
@@ -560,7 +577,6 @@ def run_learned(args):
     tree at 0.8 and at 0.5 (p99 vs FP64 direct on a 2048-star sample)."""
     import torch
     import ics
-    import oracle
     from paper_1507_01009_gb300 import rv
     ws, rank, local = _dist()
     if rank != 0:
@@ -616,11 +632,10 @@ def run_learned(args):
     peaks = _measured_peaks()
     bf16 = peaks.get("bf16_tflops") or 1900.0
     tg = ics.subsample(n, 2048, seed=17)
-    ad, _ = oracle.direct(p32.astype(np.float64), m32.astype(np.float64), eps, targets=tg)
+    ad, _ = rv.direct_fp64(p32.astype(np.float64), m32.astype(np.float64), eps, tg)
 
     def p99(a):
-        return oracle.percentile(oracle.rel_err(np.stack([u.cpu().numpy() for u in a[:3]])[:, tg].astype(
-            np.float64), ad), 0.99)
+        return _p99(_rel_err(np.stack([u.cpu().numpy() for u in a[:3]])[:, tg].astype(np.float64), ad))
 
     def plain(theta):
         ctx.build_tree(x, y, z, m)

@@ -351,13 +351,39 @@ rv_status rv_select_perturbers_tidal(rv_ctx *ctx, int64_t n, const float *x, con
 size_t rv_mlp_param_bytes(void);
 /* Device scratch rv_mlp_gradient needs for a batch of `batch` rows. */
 size_t rv_mlp_scratch_bytes(int64_t batch);
-/* Glorot-uniform weights from a SplitMix64 stream of `seed`, zero biases. */
+/* Glorot-uniform weights from a SplitMix64 stream of `seed`, zero biases, an
+ * unbounded feature box. */
 rv_status rv_mlp_init(void *params, uint64_t seed, void *stream);
+/* The feature box: the range of features the network was trained on, per
+ * feature [lo, hi]. rv_tree_forces_mlp applies no correction to a (group,
+ * cell) pair with any used feature outside it (the pair keeps its plain tree
+ * force). Fit sets it to the per-feature minimum and maximum of device rows
+ * x[n][16] (n >= 1); set copies host lo[16], hi[16] (lo <= hi, +-inf allowed;
+ * synchronises `stream`). RV_E_INVAL on bad arguments. */
+rv_status rv_mlp_fit_feature_box(void *params, int64_t n, const float *x, void *stream);
+rv_status rv_mlp_set_feature_box(void *params, const float *lo, const float *hi, void *stream);
 /* y[n][3] = network(x[n][16]) (device FP32), on the tcgen05 tensor cores in
  * tiles of 128 rows (x need not be 16-byte aligned; aligned rows load as
  * float4). A completion wait that times out (after ~1 s) leaves NaN in the
  * rows of that tile. */
 rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y, void *stream);
+/* FP64 direct summation for a sample of targets: the reference the tree's
+ * force error is measured against (Sect. 3/4 compare tree forces with direct
+ * summation). All arrays device FP64, caller-owned: bodies x, y, z, m,
+ * eps [n] (eps 0: unsoftened), target indices targets[nt] (int64, into
+ * 0..n-1), outputs ax, ay, az, pot [nt]:
+ *   a_i = sum_{j != i} m_j d / (d.d + e^2)^{3/2}, phi_i = -sum m_j / (d.d + e^2)^{1/2},
+ * d = x_j - x_i, G = 1, e = max(eps_i, eps_j) or 0 if either is 0; a pair with
+ * d.d + e^2 = 0 adds nothing. A target index outside 0..n-1 gives NaN.
+ * scratch: device, at least rv_direct_fp64_scratch_bytes(nt) bytes. Partial
+ * sums over source chunks are added in chunk order (deterministic). Plain
+ * FP64 sums. Asynchronous on `stream`. RV_E_INVAL on bad arguments,
+ * RV_E_WORKSPACE if the scratch is too small. */
+size_t rv_direct_fp64_scratch_bytes(int64_t nt);
+rv_status rv_direct_fp64(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                         const double *eps, int64_t nt, const int64_t *targets, double *ax, double *ay, double *az,
+                         double *pot, void *scratch, size_t scratch_bytes, void *stream);
+
 /* Self-test of the bounded completion wait that guards every tensor-core
  * (tcgen05) kernel here (the paper has no counterpart: this checks the failure
  * path without faulting the GPU). One CTA allocates 32 TMEM columns, waits up
@@ -387,9 +413,10 @@ rv_status rv_mlp_samples(rv_ctx *ctx, float theta, float eps_star, int64_t n_sam
  * theta that a walk at theta_rec (< theta) would open, into device pairs[2
  * pair_cap] with the count in npairs[1]; the network evaluates each pair at
  * the group's geometric centre and adds the correction (device scratch
- * gcorr[3 n]) to every star of the group. Synchronises `stream` once. The
- * network runs as rv_mlp_forward does; a timed-out completion wait is
- * reported as RV_E_TIMEOUT by rv_sync_status. */
+ * gcorr[3 n]) to every star of the group. A pair whose features lie outside
+ * the network's feature box gets no correction (the plain tree). Synchronises
+ * `stream` once. The network runs as rv_mlp_forward does; a timed-out
+ * completion wait is reported as RV_E_TIMEOUT by rv_sync_status. */
 rv_status rv_tree_forces_mlp(rv_ctx *ctx, const void *params, float theta, float theta_rec, float eps_star,
                              float *ax, float *ay, float *az, float *pot, int32_t *pairs, int32_t pair_cap,
                              int32_t *npairs, float *gcorr, void *stream);

@@ -40,11 +40,13 @@ constexpr int oW1t = 0;                 // [64][16]
 constexpr int oW2t = oW1t + kHid * kInPad;   // [64][64]
 constexpr int oW3t = oW2t + kHid * kHid;     // [8][64]
 constexpr int kBf16 = oW3t + kOutPad * kHid;  // 5632
-constexpr size_t kBlockBytes = sizeof(float) * 3 * kParams + sizeof(__nv_bfloat16) * kBf16;
+// then the feature box: lo[16], hi[16] (FP32)
+constexpr size_t kBlockBytes = sizeof(float) * 3 * kParams + sizeof(__nv_bfloat16) * kBf16 + sizeof(float) * 2 * kInPad;
 
 struct MlpBlock {
     float *w, *m, *v;      // master weights, Adam moments
     __nv_bfloat16 *wb;     // bfloat16 copies
+    float *box;            // features the network was trained on: lo[16], hi[16]
 };
 
 __host__ __device__ inline MlpBlock mlp_block(void *p) {
@@ -53,6 +55,7 @@ __host__ __device__ inline MlpBlock mlp_block(void *p) {
     b.m = b.w + kParams;
     b.v = b.m + kParams;
     b.wb = reinterpret_cast<__nv_bfloat16 *>(b.v + kParams);
+    b.box = reinterpret_cast<float *>(b.wb + kBf16);
     return b;
 }
 
@@ -199,6 +202,37 @@ __global__ void mlp_init_k(MlpBlock P, unsigned long long seed) {
         P.w[i] = use ? a * (2.f * u - 1.f) : 0.f;
         P.m[i] = 0.f;
         P.v[i] = 0.f;
+    }
+    // no feature box yet: every feature is inside
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 2 * kInPad) P.box[i] = __int_as_float(i < kInPad ? 0xff800000 : 0x7f800000);
+}
+
+// The box of the features x[n][16] (n >= 1): per feature the smallest and the
+// largest value. One block of 512 threads: thread t takes feature t % 16 of
+// rows t / 16, t / 16 + 32, ...
+__global__ void __launch_bounds__(512) mlp_box_k(MlpBlock P, int64_t n, const float *x) {
+    __shared__ float lo[512], hi[512];
+    const int t = threadIdx.x, k = t & (kInPad - 1);
+    float a = __int_as_float(0x7f800000), b = __int_as_float(0xff800000);
+    for (int64_t r = t >> 4; r < n; r += 512 / kInPad) {
+        const float v = x[r * kInPad + k];
+        a = fminf(a, v);
+        b = fmaxf(b, v);
+    }
+    lo[t] = a;
+    hi[t] = b;
+    __syncthreads();
+    for (int h = 256; h >= kInPad; h >>= 1) {
+        if (t < h) {
+            lo[t] = fminf(lo[t], lo[t + h]);
+            hi[t] = fmaxf(hi[t], hi[t + h]);
+        }
+        __syncthreads();
+    }
+    if (t < kInPad) {
+        P.box[t] = lo[t];
+        P.box[kInPad + t] = hi[t];
     }
 }
 
@@ -492,6 +526,7 @@ struct TcSmem {
     alignas(128) __nv_bfloat16 w2[kHid * kHid];        // W2^T: 64 x 64
     alignas(128) __nv_bfloat16 w3[kTcOutN * kHid];     // W3^T: 16 x 64 (rows 8 .. 15 zero)
     float b1[kHid], b2[kHid], b3[kOutPad];
+    float blo[kInPad], bhi[kInPad];                    // the feature box of the training data
     float red[4][32][3];                               // pair rows: per-warp terms for the group sums
     unsigned long long bar;                            // MMA completion
     unsigned tmem;                                     // TMEM base address from tcgen05.alloc
@@ -596,6 +631,10 @@ __device__ void tc_load_weights(const MlpBlock &P, TcSmem &S) {
         S.b2[i] = P.w[ob2 + i];
     }
     if (threadIdx.x < kOutPad) S.b3[threadIdx.x] = P.w[ob3 + threadIdx.x];
+    if (threadIdx.x < kInPad) {
+        S.blo[threadIdx.x] = P.box[threadIdx.x];
+        S.bhi[threadIdx.x] = P.box[kInPad + threadIdx.x];
+    }
 }
 
 // This thread's 16 features into row r of the layer-1 operand.
@@ -808,6 +847,15 @@ __global__ void __launch_bounds__(kTcRows) mlp_pairs_tc_k(MlpBlock P, CellGeo T,
                                  -((c0[2] - gcen[2]) + q.w)};
             const float side = unit * (float)(1 << (kMaxLevel - b.w));
             norm = pair_features(q, q0, q1, side, eps, rr, f);
+            // outside the features the network was trained on: no correction (the plain tree)
+            bool inside = true;
+#pragma unroll
+            for (int k = 0; k < kIn; k++) inside &= (f[k] >= S.blo[k]) && (f[k] <= S.bhi[k]);
+            if (!inside) {
+                norm = 0.f;
+#pragma unroll
+                for (int k = 0; k < kInPad; k++) f[k] = 0.f;
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < kInPad; k++) f[k] = 0.f;
@@ -911,6 +959,24 @@ rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kTcRows - 1) / kTcRows, (int64_t)sms * kTcCtas));
     mlp_forward_tc_k<<<grid, kTcRows, 0, s>>>(P, n, x, y);
     return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_mlp_fit_feature_box(void *params, int64_t n, const float *x, void *stream) {
+    if (!params || n < 1 || !x) return RV_E_INVAL;
+    mlp_box_k<<<1, 512, 0, (cudaStream_t)stream>>>(mlp_block(params), n, x);
+    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_mlp_set_feature_box(void *params, const float *lo, const float *hi, void *stream) {
+    if (!params || !lo || !hi) return RV_E_INVAL;
+    for (int k = 0; k < kInPad; k++)
+        if (!(lo[k] <= hi[k])) return RV_E_INVAL;
+    MlpBlock P = mlp_block(params);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(P.box, lo, sizeof(float) * kInPad, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.box + kInPad, hi, sizeof(float) * kInPad, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host arrays may go out of scope after return
+    return e == cudaSuccess ? RV_OK : RV_E_CUDA;
 }
 
 rv_status rv_wait_selftest(int64_t limit_cycles, int32_t arrive, int32_t *gave_up, void *stream) {

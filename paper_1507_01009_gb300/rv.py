@@ -30,7 +30,8 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_block_start", "rv_block_steps", "rv_block_levels", "rv_block_count", "rv_chain_start_radius", "rv_get_tree", "rv_walk_stats", "rv_sync_status",
            "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
            "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
-           "rv_mlp_samples", "rv_tree_forces_mlp", "rv_wait_selftest"]
+           "rv_mlp_samples", "rv_tree_forces_mlp", "rv_wait_selftest", "rv_mlp_fit_feature_box",
+           "rv_mlp_set_feature_box", "rv_direct_fp64_scratch_bytes", "rv_direct_fp64"]
 
 
 class RvError(RuntimeError):
@@ -134,6 +135,11 @@ def _declare(L):
     L.rv_mlp_samples.argtypes = [vp, f32, f32, i64, C.c_uint64, vp, vp, vp, vp]
     L.rv_tree_forces_mlp.argtypes = [vp, vp, f32, f32, f32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
     L.rv_wait_selftest.argtypes = [i64, i32, vp, vp]
+    L.rv_mlp_fit_feature_box.argtypes = [vp, i64, vp, vp]
+    L.rv_mlp_set_feature_box.argtypes = [vp, vp, vp, vp]
+    L.rv_direct_fp64_scratch_bytes.argtypes = [i64]
+    L.rv_direct_fp64_scratch_bytes.restype = C.c_size_t
+    L.rv_direct_fp64.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
     L.rv_launch_count.argtypes = [vp]
     L.rv_launch_count.restype = C.c_int64
     L.rv_last_error.argtypes = [vp]
@@ -141,7 +147,7 @@ def _declare(L):
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("rv_default_config", "rv_workspace_size", "rv_destroy", "rv_last_error", "rv_launch_count",
-                        "rv_mlp_param_bytes", "rv_mlp_scratch_bytes"):
+                        "rv_mlp_param_bytes", "rv_mlp_scratch_bytes", "rv_direct_fp64_scratch_bytes"):
             f.restype = C.c_int
 
 
@@ -593,8 +599,32 @@ class Mlp:
         if st != RV_OK:
             raise RvError(st, "rv_mlp_adam")
 
+    def fit_feature_box(self, x, stream=None):
+        """The feature box becomes the per-feature range of the rows x (n, 16)."""
+        st = self.L.rv_mlp_fit_feature_box(_ptr(self.block), int(x.shape[0]), _ptr(x), _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_fit_feature_box")
+
+    def set_feature_box(self, lo, hi, stream=None):
+        """Sets the feature box from 16 lower and 16 upper bounds (host)."""
+        import numpy as np
+        lo = np.ascontiguousarray(lo, dtype=np.float32)
+        hi = np.ascontiguousarray(hi, dtype=np.float32)
+        if lo.shape != (16,) or hi.shape != (16,):
+            raise ValueError("feature box bounds need 16 values each")
+        st = self.L.rv_mlp_set_feature_box(_ptr(self.block), lo.ctypes.data_as(C.c_void_p),
+                                           hi.ctypes.data_as(C.c_void_p), _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_set_feature_box")
+
+    def feature_box(self):
+        """(lo, hi) as numpy arrays of 16."""
+        box = self.block[-4 * 32:].view(torch_float32()).cpu().numpy()
+        return box[:16].copy(), box[16:].copy()
+
     def train(self, x, t, steps, batch=4096, lr=1e-3, seed=0, stream=None):
-        """Adam on minibatches drawn in a seeded order; returns the losses."""
+        """Adam on minibatches drawn in a seeded order; returns the losses. The
+        feature box becomes the range of the training rows x."""
         import torch
         g = torch.Generator(device="cpu").manual_seed(int(seed))
         n = int(x.shape[0])
@@ -604,12 +634,41 @@ class Mlp:
             grad, loss = self.gradient(x[idx].contiguous(), t[idx].contiguous(), stream)
             self.adam(grad, lr=lr, stream=stream)
             losses.append(loss)
+        self.fit_feature_box(x, stream)
         return [float(l.item()) for l in losses]
 
 
 def torch_float32():
     import torch
     return torch.float32
+
+
+def direct_fp64(pos, mass, eps, targets, stream=None):
+    """FP64 direct-summation acceleration and potential on `targets` from all
+    bodies (see rv_direct_fp64). pos (3, n), mass (n,), eps scalar or (n,)
+    (0: unsoftened), targets (nt,) indices; numpy or torch. Returns numpy
+    (acc (3, nt), pot (nt,))."""
+    import numpy as np
+    import torch
+    dev = dict(dtype=torch.float64, device="cuda")
+    pos = torch.as_tensor(pos).to(**dev)
+    n = int(pos.shape[1])
+    x, y, z = (pos[a].contiguous() for a in range(3))
+    m = torch.as_tensor(mass).to(**dev).contiguous()
+    e = torch.as_tensor(eps, dtype=torch.float64)
+    e = (e.expand(n) if e.dim() == 0 else e).to(**dev).contiguous()
+    t = torch.as_tensor(np.asarray(targets, dtype=np.int64)).to(device="cuda").contiguous()
+    nt = int(t.shape[0])
+    out = [torch.empty(nt, **dev) for _ in range(4)]
+    L = load()
+    need = int(L.rv_direct_fp64_scratch_bytes(nt))
+    scratch = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+    st = L.rv_direct_fp64(n, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(e), nt, _ptr(t), *[_ptr(o) for o in out],
+                          _ptr(scratch), need, _stream(stream))
+    if st != RV_OK:
+        raise RvError(st, "rv_direct_fp64")
+    o = [u.cpu().numpy() for u in out]
+    return np.stack(o[:3]), o[3]
 
 
 def wait_selftest(limit_cycles, arrive, stream=None):

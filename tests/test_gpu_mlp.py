@@ -191,9 +191,30 @@ def test_training_reduces_loss(rvmod):
     assert float(l1.item()) < 2.0 * zero
 
 
-def test_correction_applied_as_the_oracle_says(rvmod):
+def test_feature_box_fit_and_set(rvmod):
+    """The fitted feature box is the exact per-feature range of the rows; a
+    box with lo > hi is rejected; a fresh network's box is unbounded."""
+    import torch
+    mlp = rvmod.Mlp(seed=13)
+    lo, hi = mlp.feature_box()
+    assert np.all(np.isneginf(lo)) and np.all(np.isposinf(hi))
+    X = _features(70001, 14)
+    mlp.fit_feature_box(torch.from_numpy(X).cuda())
+    lo, hi = mlp.feature_box()
+    np.testing.assert_array_equal(lo, X.min(0))
+    np.testing.assert_array_equal(hi, X.max(0))
+    bad = np.zeros(16, np.float32)
+    bad[2] = 1.0
+    with pytest.raises(rvmod.RvError):
+        mlp.set_feature_box(bad, np.zeros(16, np.float32))
+
+
+@pytest.mark.parametrize("boxed", [False, True])
+def test_correction_applied_as_the_oracle_says(rvmod, boxed):
     """The correction the walk adds equals the oracle's network evaluated at
-    each recorded pair's group centre, summed per group."""
+    each recorded pair's group centre, summed per group. boxed: the feature
+    box cuts s/|r| at a value between two recorded pairs' features (well
+    apart); pairs beyond it add nothing."""
     import torch
     p32, m32 = hernquist32(30000, 23)
     eps = float(np.float32(0.005))
@@ -201,7 +222,8 @@ def test_correction_applied_as_the_oracle_says(rvmod):
     gpu_tree(ctx, p32, m32)
     mlp = rvmod.Mlp(seed=4)
     plain = [u.cpu().numpy() for u in ctx.tree_forces(theta=0.9, eps_star=eps)]
-    ax, ay, az, pot, pairs, npairs = rvmod.tree_forces_mlp(ctx, mlp, 0.9, 0.5, eps, pair_cap=1 << 22)
+    # the recorded pairs (the box does not change which pairs are recorded)
+    _, _, _, _, pairs, npairs = rvmod.tree_forces_mlp(ctx, mlp, 0.9, 0.5, eps, pair_cap=1 << 22)
     ctx.sync_status()
     k = int(npairs.item())
     assert k > 0
@@ -226,9 +248,26 @@ def test_correction_applied_as_the_oracle_says(rvmod):
         f, nm = oracle.cell_features(T, c, centre, eps)
         feats.append(np.concatenate([f, np.zeros(5)]))
         norms.append(nm)
-    y, _ = oracle.mlp_forward(params, np.array(feats))
+    feats, norms = np.array(feats), np.array(norms)
+    if boxed:
+        f3 = np.sort(feats[:, 3])
+        i = int(0.6 * len(f3))
+        while i + 1 < len(f3) and f3[i + 1] - f3[i] <= 1e-4 * f3[i]:
+            i += 1
+        assert i + 1 < len(f3)
+        cut = 0.5 * (f3[i] + f3[i + 1])
+        hi = np.full(16, np.inf, np.float32)
+        hi[3] = cut
+        mlp.set_feature_box(np.full(16, -np.inf, np.float32), hi)
+        norms = np.where(feats[:, 3] <= cut, norms, 0.0)
+        assert 0 < (norms == 0).sum() < len(norms)
+    ax, ay, az, pot, pairs2, npairs2 = rvmod.tree_forces_mlp(ctx, mlp, 0.9, 0.5, eps, pair_cap=1 << 22)
+    ctx.sync_status()
+    assert int(npairs2.item()) == k
+    assert set(map(tuple, pairs2[:k].cpu().numpy())) == set(map(tuple, pr))   # same pairs, any order
+    y, _ = oracle.mlp_forward(params, feats)
     corr = np.zeros((len(groups), 3))
-    np.add.at(corr, pr[:, 0], y * np.array(norms)[:, None])
+    np.add.at(corr, pr[:, 0], y * norms[:, None])
     got = np.stack([ax.cpu().numpy() - plain[0], ay.cpu().numpy() - plain[1], az.cpu().numpy() - plain[2]])
     want = np.zeros((3, p32.shape[1]))
     for gi, (first, cnt, *_) in enumerate(groups):
