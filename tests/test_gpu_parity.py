@@ -405,7 +405,7 @@ def test_kdk_plummer_100_steps(rvmod):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("G,n_leaf,tile", [(32, 16, 64), (64, 32, 128), (64, 16, 128)])
+@pytest.mark.parametrize("G,n_leaf,tile", [(32, 16, 64), (64, 32, 128), (64, 16, 128), (64, 24, 128)])
 def test_full_size_hernquist_bh_sampled(rvmod, G, n_leaf, tile):
     """The 2^20-star Hernquist + SMBH workload in the launch configurations the
     benchmark's autotuner picks from: sampled stars against the oracle tree

@@ -98,7 +98,7 @@ def test_relmac_rejects_bad_arguments(rvmod):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("G,n_leaf,tile", [(64, 32, 128)])
+@pytest.mark.parametrize("G,n_leaf,tile", [(64, 32, 128), (64, 24, 128)])
 def test_relmac_full_size_sampled(rvmod, G, n_leaf, tile):
     """2^20 Hernquist stars at the paper's tolerance 1e-3, reference |a| from
     the oracle tree at theta = 0.5: sampled stars against the oracle under the
