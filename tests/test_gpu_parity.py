@@ -433,6 +433,63 @@ def test_full_size_hernquist_bh_sampled(rvmod, G, n_leaf, tile):
     assert p99 <= P99_DIRECT
 
 
+@pytest.mark.slow
+def test_full_size_hernquist_binary_sampled(rvmod):
+    """The 2^22-star Hernquist + SMBH-binary workload in the benchmark's launch
+    configuration (group 64, n_leaf 24, tile 128; the 256 nearest stars as
+    perturbers): sampled stars, some of them perturbers, against the oracle
+    running the same method (tree with the binary's centre of mass as one
+    unsoftened particle, resolved corrections on the perturbers, Eq. 3)."""
+    w = ics.hernquist_binary_workload(1 << 22, seed=3)
+    p32, m32 = stars32(w.stars.pos, w.stars.mass)
+    eps = float(np.float32(w.eps_star))
+    n = p32.shape[1]
+    ctx = _ctx(rvmod, n, theta=0.5, eps_star=eps, group=64, n_leaf=24, tile=128)
+    S = _system(rvmod, w, n, pert_mode=2, pert_k=256)
+    ctx.system_forces(S)
+    ctx.sync_status()
+    a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
+    pert = oracle.knn(p32, w.chain.com.astype(np.float32), 256)
+    tg = np.union1d(ics.subsample(n, 512, seed=21), pert[::8])
+    ao, _, _, _, o = _oracle_system_forces(w, p32, m32, 0.5, eps, sub=tg, pert=pert, n_leaf=24, G=64)
+    ao[:, pert] += o["a_pert"].T
+    med, _, mx = err_stats(a[:, tg], ao[:, tg])
+    assert med <= MED_TOL and mx <= MAX_TOL, (med, mx)
+
+
+@pytest.mark.slow
+def test_full_size_ensemble_sampled(rvmod):
+    """The 64-member ensemble (7.67 M stars of log-uniform member sizes, a
+    central SMBH pair each) in one system, benchmark configuration: for the
+    smallest, a middle and the largest member, sampled stars against the
+    oracle running that member alone with the same method."""
+    e = ics.ensemble_workload(64, seed=4)
+    off = e["offsets"]
+    p32, m32 = stars32(e["pos"], e["mass"])
+    eps = float(np.float32(0.005))
+    n = p32.shape[1]
+    ctx = _ctx(rvmod, n, theta=0.5, eps_star=eps, group=64, n_leaf=24, tile=128)
+    S = rvmod.System(e["pos"], e["vel"], e["mass"], chain_m=e["chain_m"], chain_x=e["chain_x"],
+                     chain_v=e["chain_v"], pert_mode=2, pert_k=256, member_offsets=off)
+    ctx.system_forces(S)
+    ctx.sync_status()
+    a = np.stack([t.cpu().numpy() for t in (S.ax, S.ay, S.az)]).astype(np.float64)
+    sizes = np.diff(off)
+    for k in (int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2]), int(np.argmax(sizes))):
+        s0, s1 = int(off[k]), int(off[k + 1])
+        mw = ics.Workload(name="member", stars=ics.Particles(pos=e["pos"][:, s0:s1], vel=e["vel"][:, s0:s1],
+                                                             mass=e["mass"][s0:s1]),
+                          chain=ics.Chain(mass=e["chain_m"][2 * k:2 * k + 2], pos=e["chain_x"][2 * k:2 * k + 2],
+                                          vel=e["chain_v"][2 * k:2 * k + 2]), eps_star=0.005, theta=0.5)
+        mp, mm = p32[:, s0:s1], m32[s0:s1]
+        pert = oracle.knn(mp, mw.chain.com.astype(np.float32), 256)
+        tg = np.union1d(ics.subsample(s1 - s0, 128, seed=30 + k), pert[::16])
+        ao, _, _, _, o = _oracle_system_forces(mw, mp, mm, 0.5, eps, sub=tg, pert=pert, n_leaf=24, G=64)
+        ao[:, pert] += o["a_pert"].T
+        med, _, mx = err_stats(a[:, s0 + tg], ao[:, tg])
+        assert med <= MED_TOL and mx <= MAX_TOL, (k, med, mx)
+
+
 def test_radius_overflow_reported(rvmod):
     """More stars inside the radius than the output holds: the first `cap`
     ascending indices are written and rv_sync_status reports RV_E_WORKSPACE."""
