@@ -276,6 +276,42 @@ def test_correction_applied_as_the_oracle_says(rvmod, boxed):
     assert np.abs(got - want).max() <= 2e-3 * scale + 1e-6 * np.abs(plain[0]).max()
 
 
+@pytest.mark.slow
+def test_full_size_learned_workload(rvmod):
+    """The 2^24-star Hernquist workload of the learned correction, in the
+    benchmark's launch configuration (theta 0.8, theta_rec 0.7, n_leaf 32,
+    group 64): the plain tree on sampled stars against the oracle tree, and
+    the learned pass adding one correction per group on top of it."""
+    import torch
+    n = 1 << 24
+    w = ics.hernquist(n, 5)
+    p32 = w.pos.astype(np.float32)
+    m32 = w.mass.astype(np.float32)
+    eps = float(np.float32(0.005))
+    ctx = rvmod.Context(n, theta=0.8, eps_star=eps, n_leaf=32, group=64)
+    gpu_tree(ctx, p32, m32)
+    plain = np.stack([u.cpu().numpy() for u in ctx.tree_forces(theta=0.8, eps_star=eps)[:3]]).astype(np.float64)
+    ctx.sync_status()
+    tg = ics.subsample(n, 256, seed=51)
+    ao, _, _, _ = oracle.Tree(p32, m32, 32, 64).forces(0.8, eps, targets=tg)
+    e = oracle.rel_err(plain[:, tg], ao[:, tg])
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+    mlp = rvmod.Mlp(seed=8)
+    out = rvmod.tree_forces_mlp(ctx, mlp, 0.8, 0.7, eps, pair_cap=1 << 29)
+    ctx.sync_status()
+    assert int(out[5].item()) > 0
+    d = np.stack([u.cpu().numpy() for u in out[:3]]).astype(np.float64) - plain
+    v = ctx.tree_view()
+    groups = v["groups"].cpu().numpy()
+    perm = v["perm"].cpu().numpy()
+    for gi in ics.subsample(len(groups), 300, seed=52):
+        first, cnt = int(groups[gi, 0]), int(groups[gi, 1])
+        dd = d[:, perm[first:first + cnt]]
+        # one correction vector per group (each star's own rounding of plain + correction aside)
+        scale = np.abs(plain[:, perm[first:first + cnt]]).max() + np.abs(dd).max()
+        assert np.abs(dd - dd[:, :1]).max() <= 4e-7 * scale
+
+
 def test_what_the_trained_network_gains(rvmod):
     """p99 relative error against the FP64 direct sum of: the tree at theta,
     the tree at theta + trained correction, the tree at theta + untrained
