@@ -408,6 +408,8 @@ def run_gpu(args):
             ctx.block_start(S, B, stream=stream)
         else:
             ctx.system_forces(S, stream=stream)
+        ctx.energy(S, out=energy_out, stream=stream)
+        e_first = energy_out.view(M, 10)[:, 2].sum().item()   # total energy before the first step
         for _ in range(max(3, args.warmup)):
             step()
     ctx.sync_status(stream=stream)
@@ -439,6 +441,10 @@ def run_gpu(args):
     ctx.profile_walk(False)
     sampler.stop()
     ctx.sync_status(stream=stream)
+    e_last = energy_out.view(M, 10)[:, 2].sum().item()   # after the last timed step
+    n_steps = max(3, args.warmup) + args.steps
+    energy_drift = {"rel": (e_last - e_first) / abs(e_first), "steps": n_steps,
+                    "dt": (blk["dt_max"] if blk else d["dt"]), "E0": e_first}
     total_ms = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev])), dev)
     ms_per_step = total_ms / args.steps
     if blk:   # particles = active star force updates
@@ -553,7 +559,8 @@ def run_gpu(args):
                 "p99_vs_fp64_direct_of_the_method_model": p99_model, "clocks": sampler.summary(),
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": float(np.mean(e2e_ms))},
-                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu}
+                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+                "energy_drift": energy_drift}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

@@ -434,6 +434,33 @@ def test_full_size_hernquist_bh_sampled(rvmod, G, n_leaf, tile):
 
 
 @pytest.mark.slow
+def test_energy_conserved_over_1000_steps(rvmod):
+    """The 2^20-star Hernquist galaxy (the benchmark's stars, without the SMBH)
+    through 1000 KDK steps of 1e-3, replayed from the captured step: the total
+    energy drifts by less than 1e-5 (measured: 1.5e-6 at most)."""
+    import torch
+    w = ics.hernquist_bh_workload(1 << 20, seed=2)
+    eps = float(np.float32(0.005))
+    ctx = _ctx(rvmod, 1 << 20, theta=0.5, eps_star=eps, n_leaf=24, group=64, tile=128)
+    S = rvmod.System(w.stars.pos, w.stars.vel, w.stars.mass)
+    stream = torch.cuda.Stream()
+    e = torch.zeros(10, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        ctx.system_forces(S, stream=stream)
+        ctx.energy(S, out=e, stream=stream)
+    torch.cuda.synchronize()
+    E0 = e[2].item()
+    drift = []
+    for _ in range(10):
+        with torch.cuda.stream(stream):
+            ctx.kdk_step_graph(S, 1e-3, 100, energy_out=e, stream=stream)
+        torch.cuda.synchronize()
+        drift.append(abs(e[2].item() / E0 - 1))
+    ctx.sync_status(stream=stream)
+    assert max(drift) <= 1e-5, drift
+
+
+@pytest.mark.slow
 def test_full_size_hernquist_binary_sampled(rvmod):
     """The 2^22-star Hernquist + SMBH-binary workload in the benchmark's launch
     configuration (group 64, n_leaf 24, tile 128; the 256 nearest stars as
