@@ -207,6 +207,7 @@ rv_status rv_set_workspace(rv_ctx *c, void *dev, size_t bytes) {
 
 rv_status rv_build_tree(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z, const float *m,
                         void *stream) {
+    NvtxRange nvtx_range("rv_build_tree");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (n < 0 || n > c->n_max) return set_err(c, RV_E_INVAL, "n = %lld outside [0, %lld]", (long long)n, (long long)c->n_max);
@@ -225,6 +226,7 @@ static rv_status check_offsets(rv_ctx *c, int M, const int64_t *off, int64_t n) 
 
 rv_status rv_build_tree_members(rv_ctx *c, int32_t n_members, const int64_t *offsets, const float *x,
                                 const float *y, const float *z, const float *m, void *stream) {
+    NvtxRange nvtx_range("rv_build_tree_members");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (!offsets || n_members < 1) return set_err(c, RV_E_INVAL, "bad members");
@@ -239,6 +241,7 @@ rv_status rv_build_tree_members(rv_ctx *c, int32_t n_members, const int64_t *off
 rv_status rv_tree_forces(rv_ctx *c, float theta, float eps_star, int32_t n_extra, const float *extra_xyzm,
                          const float *extra_eps, float *ax, float *ay, float *az, float *pot, float *extra_out,
                          void *stream) {
+    NvtxRange nvtx_range("rv_tree_forces");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces before rv_build_tree");
@@ -252,6 +255,7 @@ rv_status rv_tree_forces(rv_ctx *c, float theta, float eps_star, int32_t n_extra
 
 rv_status rv_tree_forces_rel(rv_ctx *c, float alpha, float eps_star, const float *ref_ax, const float *ref_ay,
                              const float *ref_az, float *ax, float *ay, float *az, float *pot, void *stream) {
+    NvtxRange nvtx_range("rv_tree_forces_rel");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces_rel before rv_build_tree");
@@ -267,6 +271,7 @@ rv_status rv_tree_forces_rel(rv_ctx *c, float alpha, float eps_star, const float
 rv_status rv_tree_forces_members(rv_ctx *c, float theta, float eps_star, int32_t n_extra, const float *extra_xyzm,
                                  const float *extra_eps, const int32_t *extra_member, float *ax, float *ay, float *az,
                                  float *pot, float *extra_out, void *stream) {
+    NvtxRange nvtx_range("rv_tree_forces_members");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces_members before a build");
@@ -281,6 +286,7 @@ rv_status rv_tree_forces_members(rv_ctx *c, float theta, float eps_star, int32_t
 rv_status rv_perturber_forces(rv_ctx *c, int32_t n_ch, const double *chain_m, const double *chain_x,
                               int32_t n_pert, const double *pert_m, const double *pert_x, double *a_pert,
                               double *pot_pert, double *a_chain, double *pot_chain, double *out8, void *stream) {
+    NvtxRange nvtx_range("rv_perturber_forces");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (n_ch < 1 || n_ch > kMaxChain || n_pert < 0 || n_pert > kMaxPert)
@@ -317,6 +323,7 @@ static rv_status check_system(rv_ctx *c, const rv_system *s) {
 }
 
 rv_status rv_system_forces(rv_ctx *c, rv_system *sys, void *stream) {
+    NvtxRange nvtx_range("rv_system_forces");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     rv_status r = check_system(c, sys);
@@ -325,6 +332,7 @@ rv_status rv_system_forces(rv_ctx *c, rv_system *sys, void *stream) {
 }
 
 rv_status rv_kdk_step(rv_ctx *c, rv_system *sys, double dt, int32_t nsteps, void *stream) {
+    NvtxRange nvtx_range("rv_kdk_step");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     rv_status r = check_system(c, sys);
@@ -335,6 +343,7 @@ rv_status rv_kdk_step(rv_ctx *c, rv_system *sys, double dt, int32_t nsteps, void
 
 rv_status rv_kdk_step_graph(rv_ctx *c, rv_system *sys, double dt, int32_t nsteps, double *energy_out,
                             void *stream) {
+    NvtxRange nvtx_range("rv_kdk_step_graph");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     rv_status r = check_system(c, sys);
@@ -347,6 +356,7 @@ rv_status rv_kdk_step_graph(rv_ctx *c, rv_system *sys, double dt, int32_t nsteps
 }
 
 rv_status rv_energy(rv_ctx *c, const rv_system *sys, double *out, void *stream) {
+    NvtxRange nvtx_range("rv_energy");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     rv_status r = check_system(c, sys);
@@ -358,6 +368,7 @@ rv_status rv_energy(rv_ctx *c, const rv_system *sys, double *out, void *stream) 
 rv_status rv_select_perturbers(rv_ctx *c, int64_t n, const float *x, const float *y, const float *z,
                                const float centre[3], int32_t mode, float radius, int32_t k, int32_t cap,
                                int32_t *idx, int32_t *count, void *stream) {
+    NvtxRange nvtx_range("rv_select_perturbers");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (n < 0 || n > c->n_max || !centre || !idx || !count || cap < 0 || (mode != 1 && mode != 2))
@@ -391,6 +402,7 @@ static rv_status check_blocks(rv_ctx *c, const rv_system *sys, const rv_blocks *
 }
 
 rv_status rv_block_start(rv_ctx *c, rv_system *sys, rv_blocks *b, void *stream) {
+    NvtxRange nvtx_range("rv_block_start");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     rv_status r = check_system(c, sys);
@@ -400,6 +412,7 @@ rv_status rv_block_start(rv_ctx *c, rv_system *sys, rv_blocks *b, void *stream) 
 }
 
 rv_status rv_block_steps(rv_ctx *c, rv_system *sys, rv_blocks *b, int32_t nsub, void *stream) {
+    NvtxRange nvtx_range("rv_block_steps");
     if (!c) return RV_E_INVAL;
     if (!ready(c)) return set_err(c, RV_E_WORKSPACE, "no workspace");
     rv_status r = check_system(c, sys);

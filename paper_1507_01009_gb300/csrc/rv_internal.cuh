@@ -7,6 +7,8 @@
 
 #include "rv.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace rv {
 
 constexpr int kMaxLevel = 21;           // 21 bits per axis, levels 0..21
@@ -206,6 +208,15 @@ rv_status energy(rv_ctx *c, const rv_system *sys, double *out, cudaStream_t s);
 rv_status kdk_graph(rv_ctx *c, rv_system *sys, double dt, int nsteps, double *eout, cudaStream_t s);
 
 inline void count_launch(rv_ctx *c) { c->launches++; }
+
+// A named NVTX range for the lifetime of the object: the library's entry points
+// show up as ranges in a timeline profiler (a few nanoseconds without one).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Member holding star i: the largest m < M with moff[m] <= i (empty members
 // are skipped because their successor has the same offset).
