@@ -78,3 +78,20 @@ def test_workspace_too_small_rejected(lib):
     assert lib.rv_set_workspace(h, C.c_void_p((1 << 20) + 8), need) == rv.RV_E_WORKSPACE
     assert b"need" in lib.rv_last_error(h)
     lib.rv_destroy(h)
+
+
+def test_new_entry_points_reject_bad_arguments(lib):
+    """Argument checks that run before any device work: the FP64 direct sum,
+    the network's feature box and the wait self-test."""
+    from paper_1507_01009_gb300 import rv
+    assert lib.rv_direct_fp64_scratch_bytes(0) == 0
+    assert lib.rv_direct_fp64_scratch_bytes(10) == 8 * 4 * 128 * 10
+    nul = [None] * 5
+    assert lib.rv_direct_fp64(0, *nul, 1, None, None, None, None, None, None, 0, None) == rv.RV_E_INVAL
+    assert lib.rv_direct_fp64(5, *nul, 1, None, None, None, None, None, None, 0, None) == rv.RV_E_INVAL
+    assert lib.rv_mlp_fit_feature_box(None, 10, None, None) == rv.RV_E_INVAL
+    lo = (C.c_float * 16)(*([1.0] * 16))
+    hi = (C.c_float * 16)(*([0.0] * 16))
+    assert lib.rv_mlp_set_feature_box(None, lo, hi, None) == rv.RV_E_INVAL
+    assert lib.rv_wait_selftest(-1, 0, None, None) == rv.RV_E_INVAL
+    assert lib.rv_wait_selftest(10, 2, None, None) == rv.RV_E_INVAL
