@@ -120,7 +120,9 @@ FORCE_CASES = [("plummer", 4096, 0.5, 0.01, 16, 32, 64, True), ("hernquist", 656
                ("ghosts", 5000, 0.5, 0.005, 16, 32, 64, True), ("two_clusters", 3000, 0.6, 0.001, 4, 8, 64, True),
                ("hernquist", 1000, 0.5, 0.0, 16, 32, 64, True), ("hernquist", 65659, 0.5, 0.005, 32, 64, 128, True),
                ("plummer", 4096, 0.6, 0.01, 16, 64, 64, True), ("two_clusters", 3000, 0.5, 0.001, 8, 47, 32, True),
-               ("ghosts", 5000, 0.5, 0.005, 16, 64, 64, False)]
+               ("ghosts", 5000, 0.5, 0.005, 16, 64, 64, False),
+               # the configuration limits: largest leaf, group and tile; one star per leaf and group
+               ("hernquist", 65659, 0.5, 0.005, 64, 64, 256, True), ("plummer", 4096, 0.5, 0.01, 1, 1, 32, True)]
 
 
 @pytest.mark.parametrize("kind,n,theta,eps,n_leaf,G,tile,quad", FORCE_CASES)
