@@ -47,10 +47,6 @@
 #ifndef RV_WALK_MIN_BLOCKS
 #define RV_WALK_MIN_BLOCKS 4
 #endif
-// 1: load a tested cell's box, links and multipole record together
-#ifndef RV_WALK_PREFETCH
-#define RV_WALK_PREFETCH 1
-#endif
 
 namespace rv {
 
@@ -472,9 +468,6 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = r0, q2 = r0;
         if (c >= 0) {
             b = __ldg(&A.cbox[c]);
-#if !RV_WALK_PREFETCH
-            if (REL) r0 = __ldg(&A.cmom[3 * c + 0]);   // the relative test needs the cell's mass
-#else
             // every record of the cell at once: one L2 round trip per pass
             lk = __ldg(&A.clink[c]);
             r0 = __ldg(&A.cmom[3 * c + 0]);
@@ -482,7 +475,6 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                 q1 = __ldg(&A.cmom[3 * c + 1]);
                 q2 = __ldg(&A.cmom[3 * c + 2]);
             }
-#endif
             int side = 1 << (kMaxLevel - b.w);
             long long gx = gap1(blo[0], bhi[0], b.x, b.x + side);
             long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
@@ -504,9 +496,6 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
             }
             if (REC) band = accept && d2 < thr_rec[b.w];
             if (!accept) {
-#if !RV_WALK_PREFETCH
-                lk = __ldg(&A.clink[c]);
-#endif
                 leaf = (lk.x == lk.y);
                 open = !leaf;
             }
@@ -528,13 +517,6 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         unsigned am = __ballot_sync(0xffffffffu, accept);
         if (accept) {
             int p = nm + __popc(am & lt);
-#if !RV_WALK_PREFETCH
-            if (!REL) r0 = __ldg(&A.cmom[3 * c + 0]);
-            if (QUAD) {
-                q1 = __ldg(&A.cmom[3 * c + 1]);
-                q2 = __ldg(&A.cmom[3 * c + 2]);
-            }
-#endif
             float c0[3];
             geo_centre(b, G.lo, G.unit, c0);
             *staged(m2p, kCellPairF4, p, 0) = r0.x;
