@@ -35,14 +35,15 @@
 #include "rv_internal.cuh"
 
 // Unrolling of the evaluation loops (list pairs in flight per lane, each on
-// two targets) and the resident blocks per SM the walk kernel is compiled for
-// (register budget: 4 blocks of 128 threads leave 128 registers a thread,
-// enough for two targets' sums and two cell pairs in flight without spills).
+// two targets; measured on GB300: star pairs 1, cell pairs 3) and the resident
+// blocks per SM the walk kernel is compiled for (register budget: 4 blocks of
+// 128 threads leave 128 registers a thread, enough for two targets' sums and
+// three cell pairs in flight without spills).
 #ifndef RV_P2P_UNROLL
-#define RV_P2P_UNROLL 2
+#define RV_P2P_UNROLL 1
 #endif
 #ifndef RV_M2P_UNROLL
-#define RV_M2P_UNROLL 2
+#define RV_M2P_UNROLL 3
 #endif
 #ifndef RV_WALK_MIN_BLOCKS
 #define RV_WALK_MIN_BLOCKS 4
