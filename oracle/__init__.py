@@ -294,6 +294,16 @@ def radius(pos32, centre32, r2_32):
     return out[:got]
 
 
+def a_hard(m1, m2, r_infl):
+    """Semi-major axis at which an SMBH binary becomes hard (Eq. 13, Sect. 5):
+    a_hard = mu / (M1 + M2) * r_infl / 4 with the reduced mass
+    mu = (1/M1 + 1/M2)^-1 and r_infl the influence radius of the pair. The
+    method starts its chain with a radius of a few a_hard (Sect. 5). FP64."""
+    m1, m2, r_infl = float(m1), float(m2), float(r_infl)
+    mu = 1.0 / (1.0 / m1 + 1.0 / m2)
+    return mu / (m1 + m2) * r_infl / 4.0
+
+
 def chain_start_radius(pos32, vel32, mass32, centre32, m_bh, alpha, beta, eps, n_sigma=50):
     """The chain's start radius of Eq. 1, r_chain,0 = max(alpha r_infl, beta eps),
     r_infl = min(r(<2 M_bh), G M_bh / sigma^2), sigma the velocity dispersion

@@ -47,6 +47,11 @@ def _inputs(kind, n, seed=0):
         m = m.copy()
         m[::5] = 1e-30
         return p, m
+    if kind == "lattice":                                     # stars exactly on cell boundaries
+        k = round(n ** (1 / 3))
+        g = np.arange(k, dtype=np.float64) / (k - 1)          # 0 .. 1: the bounding cube's corners
+        q = np.stack(np.meshgrid(g, g, g, indexing="ij")).reshape(3, -1)
+        return q.astype(np.float32), np.full(q.shape[1], 1.0 / q.shape[1], dtype=np.float32)
     raise ValueError(kind)
 
 
@@ -55,7 +60,7 @@ TREE_CASES = [("hernquist", 1, 16, 32), ("hernquist", 2, 16, 32), ("hernquist", 
               ("hernquist", 65659, 16, 32), ("plummer", 4096, 16, 32), ("coincident", 100, 16, 32),
               ("two_clusters", 3000, 16, 32), ("ghosts", 5000, 16, 32), ("hernquist", 20000, 32, 32),
               ("hernquist", 20000, 4, 8), ("hernquist", 20000, 16, 64), ("hernquist", 4097, 8, 48),
-              ("coincident", 100, 16, 64)]
+              ("coincident", 100, 16, 64), ("lattice", 4913, 8, 32), ("lattice", 4096, 1, 1)]
 
 
 @pytest.mark.parametrize("kind,n,n_leaf,G", TREE_CASES)

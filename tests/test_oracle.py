@@ -668,3 +668,16 @@ def test_spline_tree_matches_direct(plummer_case):
     np.testing.assert_allclose(p, pd, rtol=1e-12)
     a, _, _, _ = T.forces(0.5, 0.01, kind=1)
     assert oracle.percentile(oracle.rel_err(a, ad), 0.99) <= 1e-3
+
+
+def test_a_hard_worked_example():
+    """Eq. 13 against the value the paper prints (tests/golden/a_hard.txt), the
+    closed form mu/(M1+M2) = M1 M2/(M1+M2)^2 for unequal masses, and its
+    independence of the mass unit."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "a_hard.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for m1, m2, r, a in rows:
+        assert oracle.a_hard(float(m1), float(m2), float(r)) == pytest.approx(float(a), rel=1e-15)
+    assert oracle.a_hard(1.0, 3.0, 2.0) == pytest.approx(3.0 / 16.0 * 2.0 / 4.0, rel=1e-15)
+    assert oracle.a_hard(7e-3, 2e-3, 0.3) == pytest.approx(oracle.a_hard(7.0, 2.0, 0.3), rel=1e-14)
