@@ -524,6 +524,23 @@ def test_full_size_ensemble_sampled(rvmod):
         assert med <= MED_TOL and mx <= MAX_TOL, (k, med, mx)
 
 
+def test_walk_stack_stays_within_its_bound(rvmod):
+    """The worst case for the walk's range stack: every cell opened (theta ->
+    0) in a tree of one star per leaf. The depth-first traversal keeps at most
+    32 pending ranges per level, so the deepest stack stays at or below
+    21 x 32 = 672 of its 768 entries, and the walk completes (the direct sum)."""
+    n = 1 << 17
+    p32, m32 = _inputs("hernquist", n)
+    ctx = _ctx(rvmod, n, theta=0.5, eps_star=0.005, n_leaf=1, group=64, tile=128)
+    gpu_tree(ctx, p32, m32)
+    a = [t.cpu().numpy() for t in ctx.tree_forces(theta=1e-7)]
+    ctx.sync_status()
+    p2p, m2p, hwm = ctx.walk_stats3()
+    assert m2p == 0 and p2p == n * n
+    assert 0 < hwm <= 21 * 32
+    assert all(np.all(np.isfinite(u)) for u in a)
+
+
 def test_radius_overflow_reported(rvmod):
     """More stars inside the radius than the output holds: the first `cap`
     ascending indices are written and rv_sync_status reports RV_E_WORKSPACE."""
