@@ -25,3 +25,18 @@ def test_reference_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_bench_error_helpers_match_the_oracle_definitions():
+    """The bench's own relative error and nearest-rank 99th percentile (used
+    with the GPU direct sum) agree with the oracle's definitions."""
+    import numpy as np
+
+    import bench
+    import oracle
+    g = np.random.default_rng(3)
+    for k in (1, 2, 99, 100, 101, 2048, 5000):
+        a, ref = g.normal(size=(3, k)), g.normal(size=(3, k))
+        e = bench._rel_err(a, ref)
+        np.testing.assert_array_equal(e, oracle.rel_err(a, ref))
+        assert bench._p99(e) == oracle.percentile(e, 0.99)
