@@ -105,6 +105,55 @@ static void p2p(double xi, double yi, double zi, double xj, double yj, double zj
     p2p_k(0, xi, yi, zi, xj, yj, zj, mj, e, ax, ay, az, ph);
 }
 
+/* Quadrupole part of the field of a particle that carries a traceless moment
+ * q = (xx, yy, zz, xy, xz, yz) about its own position (a chain seen from
+ * outside: its members' second moment about their centre of mass), at the
+ * offset r = x_target - x_source, with the Plummer length e of the pair. Same
+ * two-term expansion about the centre of mass as the cells' (Sect. 1):
+ *   a = Q r / rho^5 - 5 (r.Q.r) r / (2 rho^7),  phi = -(r.Q.r) / (2 rho^5),
+ * rho^2 = r.r + e^2 (the monopole is the point-mass pair term). */
+static void quad_term(double rx, double ry, double rz, double e, const double *q,
+                      nsum *ax, nsum *ay, nsum *az, nsum *ph) {
+    double r2 = rx * rx + ry * ry + rz * rz + e * e;
+    if (r2 <= 0.0) return;
+    double rinv = 1.0 / sqrt(r2), rinv2 = rinv * rinv, rinv5 = rinv * rinv2 * rinv2, rinv7 = rinv5 * rinv2;
+    double qx = q[0] * rx + q[3] * ry + q[4] * rz;
+    double qy = q[3] * rx + q[1] * ry + q[5] * rz;
+    double qz = q[4] * rx + q[5] * ry + q[2] * rz;
+    double rqr = rx * qx + ry * qy + rz * qz;
+    nadd(ax, qx * rinv5 - 2.5 * rqr * rx * rinv7);
+    nadd(ay, qy * rinv5 - 2.5 * rqr * ry * rinv7);
+    nadd(az, qz * rinv5 - 2.5 * rqr * rz * rinv7);
+    nadd(ph, -0.5 * rqr * rinv5);
+}
+
+/* Total mass, centre of mass and traceless quadrupole of a chain of nch
+ * members (masses cm, positions cx[3k..]) about its centre of mass:
+ *   Q_ab = sum_k m_k (3 d_a d_b - |d|^2 delta_ab),  d = x_k - com,
+ * out = (M, com x, y, z, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz); com = 0 if M = 0. */
+void orc_chain_moments(int32_t nch, const double *cm, const double *cx, double out[10]) {
+    double M = 0.0, c[3] = {0.0, 0.0, 0.0};
+    for (int32_t k = 0; k < nch; k++) {
+        M += cm[k];
+        for (int a = 0; a < 3; a++) c[a] += cm[k] * cx[3 * k + a];
+    }
+    for (int a = 0; a < 3; a++) c[a] = (M > 0.0) ? c[a] / M : 0.0;
+    double q[6] = {0, 0, 0, 0, 0, 0};
+    for (int32_t k = 0; k < nch; k++) {
+        double d[3] = {cx[3 * k] - c[0], cx[3 * k + 1] - c[1], cx[3 * k + 2] - c[2]};
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        q[0] += cm[k] * (3.0 * d[0] * d[0] - d2);
+        q[1] += cm[k] * (3.0 * d[1] * d[1] - d2);
+        q[2] += cm[k] * (3.0 * d[2] * d[2] - d2);
+        q[3] += cm[k] * 3.0 * d[0] * d[1];
+        q[4] += cm[k] * 3.0 * d[0] * d[2];
+        q[5] += cm[k] * 3.0 * d[1] * d[2];
+    }
+    out[0] = M;
+    for (int a = 0; a < 3; a++) out[1 + a] = c[a];
+    for (int a = 0; a < 6; a++) out[4 + a] = q[a];
+}
+
 /* ------------------------------------------------------------------ */
 /* 1. Direct sum                                                        */
 /* ------------------------------------------------------------------ */
@@ -589,14 +638,19 @@ static void walk_cell(walk_state *w, int64_t c) {
  * tolerance alpha and reference accelerations (rx, ry, rz)[i] (caller order,
  * FP32); the extra particles always use the opening angle. kind selects the
  * stars' softening: 0 Plummer, 1 spline (see p2p_k; the extra particles'
- * pairs use Plummer's rule with their own lengths). */
+ * pairs use Plummer's rule with their own lengths). xq (optional, 6 per
+ * extra particle) gives each extra particle a traceless quadrupole about its
+ * position, whose field (quad_term) is added wherever that particle acts
+ * (reading: a chain seen from outside is its centre of mass plus its
+ * quadrupole, the same two-term expansion as a tree cell). */
 void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t quad,
                      int32_t nx, const float *xx, const float *xy, const float *xz, const double *xm,
                      const double *xeps,
                      double *ax, double *ay, double *az, double *pot,
                      double *xax, double *xay, double *xaz, double *xpot, int64_t *counts,
                      int64_t nsub, const int64_t *sub,
-                     float alpha, const float *rx, const float *ry, const float *rz, int32_t kind) {
+                     float alpha, const float *rx, const float *ry, const float *rz, int32_t kind,
+                     const double *xq) {
     double theta2 = theta * theta;
     const float u = (float)(t->L / ORC_GRID);
     /* optional subset: only sorted slots whose caller index is flagged */
@@ -631,8 +685,12 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
             memcpy(w.blo, blo, sizeof blo); memcpy(w.bhi, bhi, sizeof bhi);
             w.px = t->x[i]; w.py = t->y[i]; w.pz = t->z[i];
             if (t->ncell > 0) walk_cell(&w, 0);
-            for (int32_t k = 0; k < nx; k++)
+            for (int32_t k = 0; k < nx; k++) {
                 p2p(w.px, w.py, w.pz, xx[k], xy[k], xz[k], xm[k], pair_eps(eps_star, xeps[k]), &w.ax, &w.ay, &w.az, &w.ph);
+                if (xq)
+                    quad_term(w.px - xx[k], w.py - xy[k], w.pz - xz[k], pair_eps(eps_star, xeps[k]), xq + 6 * k,
+                              &w.ax, &w.ay, &w.az, &w.ph);
+            }
             int64_t o = t->perm[i];
             ax[o] = nval(&w.ax); ay[o] = nval(&w.ay); az[o] = nval(&w.az); pot[o] = nval(&w.ph);
             if (counts) { counts[2 * o] = w.n_p2p; counts[2 * o + 1] = w.n_m2p; }
@@ -656,6 +714,9 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
         for (int32_t j = 0; j < nx; j++) {
             if (j == k) continue;
             p2p(w.px, w.py, w.pz, xx[j], xy[j], xz[j], xm[j], pair_eps(xeps[k], xeps[j]), &w.ax, &w.ay, &w.az, &w.ph);
+            if (xq)
+                quad_term(w.px - xx[j], w.py - xy[j], w.pz - xz[j], pair_eps(xeps[k], xeps[j]), xq + 6 * j, &w.ax,
+                          &w.ay, &w.az, &w.ph);
         }
         xax[k] = nval(&w.ax); xay[k] = nval(&w.ay); xaz[k] = nval(&w.az); xpot[k] = nval(&w.ph);
     }
@@ -684,10 +745,16 @@ static void kepler_pot(double rx, double ry, double rz, double m, double out[4])
  *   out[3..6) sub  = sum_p pm_p f(x_p - com), the direct unsoftened terms of the
  *                perturbers on the centre-of-mass particle, to subtract;
  *   out[6] = (1/M) sum_k cm_k pot_chain[k], out[7] = potential of sub;
- *   out[8..11) com, out[11] M. */
+ *   out[8..11) com, out[11] M.
+ * With quad = 1 the stars outside the perturber set feel the chain as its
+ * centre of mass plus its quadrupole (orc_chain_moments, quad_term), so the
+ * perturbers' correction removes both: a_pert = sum_k cm_k f(x_k - x_p) -
+ * M f(com - x_p) - (quadrupole field at x_p). */
 void orc_perturber(int32_t nch, const double *cm, const double *cx, int32_t np, const double *pm,
                    const double *px, double *a_pert, double *pot_pert, double *a_chain, double *pot_chain,
-                   double out[12]) {
+                   double out[12], int32_t quad) {
+    double mom[10];
+    orc_chain_moments(nch, cm, cx, mom);
     double M = 0, com[3] = {0, 0, 0};
     for (int32_t k = 0; k < nch; k++) {
         M += cm[k];
@@ -704,6 +771,12 @@ void orc_perturber(int32_t nch, const double *cm, const double *cx, int32_t np, 
         }
         kepler_pot(com[0] - px[3 * p], com[1] - px[3 * p + 1], com[2] - px[3 * p + 2], M, f);
         for (int a = 0; a < 4; a++) nadd(&s[a], -f[a]);
+        if (quad) {
+            nsum qs[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            quad_term(px[3 * p] - mom[1], px[3 * p + 1] - mom[2], px[3 * p + 2] - mom[3], 0.0, mom + 4,
+                      &qs[0], &qs[1], &qs[2], &qs[3]);
+            for (int a = 0; a < 4; a++) nadd(&s[a], -nval(&qs[a]));
+        }
         for (int a = 0; a < 3; a++) a_pert[3 * p + a] = nval(&s[a]);
         pot_pert[p] = nval(&s[3]);
     }

@@ -479,6 +479,94 @@ def test_perturber_binary_newton_third_law():
     np.testing.assert_allclose(M * r["corr"], f_members, rtol=1e-13)
 
 
+def _probe_tree(points):
+    """A tree of massless probe stars (they feel the extra particles only)."""
+    pos = np.asarray(points, dtype=np.float32).T.copy()
+    return oracle.Tree(pos, np.zeros(pos.shape[1], np.float32), 16, 32), pos
+
+
+def test_chain_quadrupole_two_point_closed_form():
+    """Chain of two masses m at +-s on z: Q_zz = 4 m s^2, Q_xx = Q_yy = -2 m s^2.
+    With x = s/r, the exact field on the axis is -(m/r^2)(1/(1-x)^2 + 1/(1+x)^2)
+    = -(m/r^2)(2 + 6x^2 + 10x^4 + ...), potential -(m/r)(2 + 2x^2 + 2x^4 ...);
+    in the plane -(2m/r^2)(1 - 3/2 x^2 + ...), potential -(2m/r)(1 - x^2/2 + ...).
+    Centre of mass plus quadrupole must give exactly the first two terms, on
+    stars and on another extra particle."""
+    m, s, r = 0.005, 0.0055, 0.05
+    x = s / r
+    mom = oracle.chain_moments([m, m], [[0, 0, s], [0, 0, -s]])
+    assert mom["M"] == 2 * m
+    np.testing.assert_allclose(mom["com"], 0.0, atol=1e-18)
+    np.testing.assert_allclose(mom["Q"], [-2 * m * s * s, -2 * m * s * s, 4 * m * s * s, 0, 0, 0], rtol=1e-14,
+                               atol=1e-20)
+    T, pos = _probe_tree([[0.0, 0.0, r], [r, 0.0, 0.0]])
+    xpos = np.array([[0.0, 0.0], [0.0, 0.0], [0.0, 3 * r]], np.float32)
+    a, p, xa, xp = T.forces(0.5, 0.0, True, xpos, [2 * m, 0.0], [0.0, 0.0],
+                            extra_quad=[mom["Q"], np.zeros(6)])
+    rz, rx = float(pos[2, 0]), float(pos[0, 1])      # the FP32 probe positions
+    xz, xx = s / rz, s / rx
+    np.testing.assert_allclose(a[:, 0], [0, 0, -(m / rz ** 2) * (2 + 6 * xz * xz)], rtol=1e-13, atol=1e-18)
+    np.testing.assert_allclose(p[0], -(m / rz) * (2 + 2 * xz * xz), rtol=1e-13)
+    np.testing.assert_allclose(a[:, 1], [-(m / rx ** 2) * (2 - 3 * xx * xx), 0, 0], rtol=1e-13, atol=1e-18)
+    np.testing.assert_allclose(p[1], -(m / rx) * (2 - xx * xx), rtol=1e-13)
+    r3 = float(xpos[2, 1])
+    x3 = s / r3
+    np.testing.assert_allclose(xa[:, 1], [0, 0, -(m / r3 ** 2) * (2 + 6 * x3 * x3)], rtol=1e-13, atol=1e-18)
+    # the exact two-body field differs by the next (x^4) term only
+    exact_axis = -m / (rz - s) ** 2 - m / (rz + s) ** 2
+    assert abs(a[2, 0] - exact_axis) == pytest.approx(10 * m / rz ** 2 * xz ** 4, rel=0.1)
+    assert x < 0.2
+
+
+def test_chain_quadrupole_far_field_order():
+    """Three unequal chain members: against the resolved field, the centre of
+    mass alone errs by O((s/r)^2) of the monopole and the centre of mass plus
+    quadrupole by O((s/r)^3): doubling r divides the errors by ~4 and ~8."""
+    g = ics.rng(31)
+    cm = np.array([0.004, 0.001, 0.0025])
+    cx = g.uniform(-0.01, 0.01, (3, 3))
+    mom = oracle.chain_moments(cm, cx)
+    direction = np.array([0.6, -0.48, 0.64])
+    errs = {}
+    for R in (1.0, 2.0):
+        probe = mom["com"] + R * direction
+        T, pos = _probe_tree([probe])
+        xp = mom["com"].astype(np.float32).reshape(3, 1)
+        allp = np.concatenate([pos.astype(np.float64), cx.T], 1)
+        ad, _ = oracle.direct(allp, np.concatenate([[0.0], cm]), 0.0, targets=[0])
+        mono = np.linalg.norm(ad[:, 0])
+        for quad in (False, True):
+            a = T.forces(0.5, 0.0, True, xp, [mom["M"]], [0.0], extra_quad=[mom["Q"]] if quad else None)[0]
+            errs[quad, R] = np.linalg.norm(a[:, 0] - ad[:, 0]) / mono
+    assert errs[True, 1.0] < 0.05 * errs[False, 1.0]
+    assert 3.5 < errs[False, 1.0] / errs[False, 2.0] < 4.5
+    assert 7.0 < errs[True, 1.0] / errs[True, 2.0] < 9.0
+
+
+def test_perturber_correction_with_quadrupole_closed_form():
+    """Binary of masses m at +-s on z, perturbers on the axis and in the plane:
+    with the quadrupole the perturber correction is the exact two-body field
+    minus the first two expansion terms (2 + 6x^2 on the axis, 2 - 3x^2 in the
+    plane, times -m/r^2); without it, minus the first term only."""
+    m, s = 0.005, 0.0055
+    cx = np.array([[0, 0, s], [0, 0, -s]])
+    px = np.array([[0, 0, 0.02], [0.03, 0, 0]])
+    pm = np.array([1e-6, 2e-6])
+    rq = oracle.perturber([m, m], cx, pm, px, quad=True)
+    r0 = oracle.perturber([m, m], cx, pm, px, quad=False)
+    rz, rx = 0.02, 0.03
+    ez = -m / (rz - s) ** 2 - m / (rz + s) ** 2
+    ex = -2 * m * rx / (rx * rx + s * s) ** 1.5
+    np.testing.assert_allclose(rq["a_pert"][0, 2], ez + (m / rz ** 2) * (2 + 6 * (s / rz) ** 2), rtol=1e-9)
+    np.testing.assert_allclose(rq["a_pert"][1, 0], ex + (m / rx ** 2) * (2 - 3 * (s / rx) ** 2), rtol=1e-9)
+    np.testing.assert_allclose(r0["a_pert"][0, 2], ez + 2 * m / rz ** 2, rtol=1e-12)
+    ep = -m / (rz - s) - m / (rz + s)
+    np.testing.assert_allclose(rq["pot_pert"][0], ep + (m / rz) * (2 + 2 * (s / rz) ** 2), rtol=1e-9)
+    # the members' side and Eq. 3 do not change
+    np.testing.assert_allclose(rq["a_chain"], r0["a_chain"], rtol=0, atol=0)
+    np.testing.assert_allclose(rq["corr"], r0["corr"], rtol=0, atol=0)
+
+
 def test_tidal_selection_closed_form():
     """Eq. 2: with equal masses the criterion is a sphere of radius
     R = (2 m / (gamma M))^(1/3) r_crit; a star 8 times heavier reaches twice as
