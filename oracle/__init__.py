@@ -71,8 +71,8 @@ def _declare(L):
     L.orc_tree_groups.argtypes = [C.c_void_p, _i64]
     L.orc_tree_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int32, C.c_int32,
                                   _f, _f, _f, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _i64, C.c_int64, _i64,
-                                  C.c_float, _f, _f, _f, C.c_int32, _d]
-    L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d, _d, C.c_int32]
+                                  C.c_float, _f, _f, _f, C.c_int32, _d, C.POINTER(C.c_int8)]
+    L.orc_perturber.argtypes = [C.c_int32, _d, _d, C.c_int32, _d, _d, _d, _d, _d, _d, _d]
     L.orc_chain_moments.argtypes = [C.c_int32, _d, _d, _d]
     L.orc_knn.argtypes = [C.c_int64, _f, _f, _f, _f, C.c_int64, _i64]
     L.orc_knn.restype = C.c_int64
@@ -196,7 +196,7 @@ class Tree:
 
     def forces(self, theta: float, eps_star: float, quadrupole: bool = True,
                extra_pos32=None, extra_mass=None, extra_eps=None, counts: bool = False, targets=None, rel=None,
-               kind: int = 0, extra_quad=None):
+               kind: int = 0, extra_quad=None, quad_skip=None):
         """Tree acceleration/potential on every star (caller order), FP64.
 
         Walk under the box-box opening-angle test at ``theta``; ``extra_*``
@@ -212,7 +212,9 @@ class Tree:
         than h = 2.8 eps act as softened monopoles). ``extra_quad`` (k, 6)
         gives each extra particle a traceless quadrupole (xx, yy, zz, xy, xz,
         yz) about its position, whose field it adds wherever it acts (a chain
-        seen from outside: ``chain_moments``)."""
+        seen from outside: ``chain_moments``) except on the stars whose caller
+        indices ``quad_skip`` lists (the chain's perturbers, which feel the
+        resolved members through ``perturber`` instead)."""
         k = 0 if extra_mass is None else int(np.asarray(extra_mass).shape[0])
         ex = np.zeros((3, max(k, 1)), dtype=np.float32)
         xm = np.zeros(max(k, 1))
@@ -225,6 +227,10 @@ class Tree:
         xq = None
         if extra_quad is not None and k:
             xq = _c(np.asarray(extra_quad, dtype=np.float64).reshape(k, 6), np.float64)
+        skip = None
+        if quad_skip is not None:
+            skip = np.zeros(max(self.n, 1), dtype=np.int8)
+            skip[np.asarray(quad_skip, dtype=np.int64)] = 1
         ar = [_c(np.asarray(rel[1][a], dtype=np.float32), np.float32) for a in range(3)] if rel is not None else None
         out = [np.zeros(self.n) for _ in range(4)]
         xout = [np.zeros(max(k, 1)) for _ in range(4)]
@@ -237,7 +243,8 @@ class Tree:
                               None if targets is None else _p(_c(targets, np.int64), _i64),
                               float(np.float32(rel[0])) if rel is not None else 0.0,
                               *([_p(v, _f) for v in ar] if rel is not None else [None, None, None]), int(kind),
-                              None if xq is None else _p(xq, _d))
+                              None if xq is None else _p(xq, _d),
+                              None if skip is None else skip.ctypes.data_as(C.POINTER(C.c_int8)))
         res = (np.stack(out[:3]), out[3], np.stack(xout[:3])[:, :k], xout[3][:k])
         return res + (cnt,) if counts else res
 
@@ -271,14 +278,12 @@ def chain_moments(chain_mass, chain_pos):
     return {"M": float(out[0]), "com": out[1:4].copy(), "Q": out[4:10].copy()}
 
 
-def perturber(chain_mass, chain_pos, pert_mass, pert_pos, quad=False):
+def perturber(chain_mass, chain_pos, pert_mass, pert_pos):
     """Unsoftened FP64 couplings of a chain (k members, pos (k,3)) and its
     perturbers (p, pos (p,3)), Sect. 2 and Eq. 3. Returns dict with a_pert
     (p,3), pot_pert (p,), a_chain (k,3), pot_chain (k,), corr (3,) = Eq. 3
     correction, sub (3,) = perturbers' direct terms on the centre-of-mass
-    particle, corr_pot, sub_pot, com (3,), M. With quad=True the stars beyond
-    the perturbers feel the chain's centre of mass plus its quadrupole
-    (``chain_moments``), and a_pert removes both."""
+    particle, corr_pot, sub_pot, com (3,), M."""
     cm = _c(chain_mass, np.float64)
     cx = _c(chain_pos, np.float64).reshape(-1)
     pm = _c(pert_mass, np.float64)
@@ -290,7 +295,7 @@ def perturber(chain_mass, chain_pos, pert_mass, pert_pos, quad=False):
     pc = np.zeros(max(nch, 1))
     out = np.zeros(12)
     lib().orc_perturber(nch, _p(cm, _d), _p(cx, _d), npt, _p(pm, _d), _p(px, _d), _p(ap, _d), _p(pp, _d),
-                        _p(ac, _d), _p(pc, _d), _p(out, _d), int(bool(quad)))
+                        _p(ac, _d), _p(pc, _d), _p(out, _d))
     return {"a_pert": ap[:3 * npt].reshape(npt, 3), "pot_pert": pp[:npt],
             "a_chain": ac[:3 * nch].reshape(nch, 3), "pot_chain": pc[:nch],
             "corr": out[0:3].copy(), "sub": out[3:6].copy(), "corr_pot": float(out[6]),

@@ -642,7 +642,10 @@ static void walk_cell(walk_state *w, int64_t c) {
  * extra particle) gives each extra particle a traceless quadrupole about its
  * position, whose field (quad_term) is added wherever that particle acts
  * (reading: a chain seen from outside is its centre of mass plus its
- * quadrupole, the same two-term expansion as a tree cell). */
+ * quadrupole, the same two-term expansion as a tree cell), except on the
+ * stars flagged in xq_skip (caller order, optional): the chain's perturbers,
+ * which feel the resolved members instead (Sect. 2) and so keep the
+ * centre-of-mass point mass that their correction replaces. */
 void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t quad,
                      int32_t nx, const float *xx, const float *xy, const float *xz, const double *xm,
                      const double *xeps,
@@ -650,7 +653,7 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
                      double *xax, double *xay, double *xaz, double *xpot, int64_t *counts,
                      int64_t nsub, const int64_t *sub,
                      float alpha, const float *rx, const float *ry, const float *rz, int32_t kind,
-                     const double *xq) {
+                     const double *xq, const int8_t *xq_skip) {
     double theta2 = theta * theta;
     const float u = (float)(t->L / ORC_GRID);
     /* optional subset: only sorted slots whose caller index is flagged */
@@ -687,7 +690,7 @@ void orc_tree_forces(const orc_tree *t, double theta, double eps_star, int32_t q
             if (t->ncell > 0) walk_cell(&w, 0);
             for (int32_t k = 0; k < nx; k++) {
                 p2p(w.px, w.py, w.pz, xx[k], xy[k], xz[k], xm[k], pair_eps(eps_star, xeps[k]), &w.ax, &w.ay, &w.az, &w.ph);
-                if (xq)
+                if (xq && !(xq_skip && xq_skip[t->perm[i]]))
                     quad_term(w.px - xx[k], w.py - xy[k], w.pz - xz[k], pair_eps(eps_star, xeps[k]), xq + 6 * k,
                               &w.ax, &w.ay, &w.az, &w.ph);
             }
@@ -745,16 +748,10 @@ static void kepler_pot(double rx, double ry, double rz, double m, double out[4])
  *   out[3..6) sub  = sum_p pm_p f(x_p - com), the direct unsoftened terms of the
  *                perturbers on the centre-of-mass particle, to subtract;
  *   out[6] = (1/M) sum_k cm_k pot_chain[k], out[7] = potential of sub;
- *   out[8..11) com, out[11] M.
- * With quad = 1 the stars outside the perturber set feel the chain as its
- * centre of mass plus its quadrupole (orc_chain_moments, quad_term), so the
- * perturbers' correction removes both: a_pert = sum_k cm_k f(x_k - x_p) -
- * M f(com - x_p) - (quadrupole field at x_p). */
+ *   out[8..11) com, out[11] M. */
 void orc_perturber(int32_t nch, const double *cm, const double *cx, int32_t np, const double *pm,
                    const double *px, double *a_pert, double *pot_pert, double *a_chain, double *pot_chain,
-                   double out[12], int32_t quad) {
-    double mom[10];
-    orc_chain_moments(nch, cm, cx, mom);
+                   double out[12]) {
     double M = 0, com[3] = {0, 0, 0};
     for (int32_t k = 0; k < nch; k++) {
         M += cm[k];
@@ -771,12 +768,6 @@ void orc_perturber(int32_t nch, const double *cm, const double *cx, int32_t np, 
         }
         kepler_pot(com[0] - px[3 * p], com[1] - px[3 * p + 1], com[2] - px[3 * p + 2], M, f);
         for (int a = 0; a < 4; a++) nadd(&s[a], -f[a]);
-        if (quad) {
-            nsum qs[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-            quad_term(px[3 * p] - mom[1], px[3 * p + 1] - mom[2], px[3 * p + 2] - mom[3], 0.0, mom + 4,
-                      &qs[0], &qs[1], &qs[2], &qs[3]);
-            for (int a = 0; a < 4; a++) nadd(&s[a], -nval(&qs[a]));
-        }
         for (int a = 0; a < 3; a++) a_pert[3 * p + a] = nval(&s[a]);
         pot_pert[p] = nval(&s[3]);
     }

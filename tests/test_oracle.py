@@ -543,28 +543,23 @@ def test_chain_quadrupole_far_field_order():
     assert 7.0 < errs[True, 1.0] / errs[True, 2.0] < 9.0
 
 
-def test_perturber_correction_with_quadrupole_closed_form():
-    """Binary of masses m at +-s on z, perturbers on the axis and in the plane:
-    with the quadrupole the perturber correction is the exact two-body field
-    minus the first two expansion terms (2 + 6x^2 on the axis, 2 - 3x^2 in the
-    plane, times -m/r^2); without it, minus the first term only."""
+def test_chain_quadrupole_skips_perturbers_closed_form():
+    """Binary of masses m at +-s on z, two probe stars on the axis: the one
+    flagged as a perturber keeps the centre-of-mass point mass (-2m/r^2), and
+    with its perturber correction it gets the exact two-body field; the other
+    gets the centre of mass plus the quadrupole (-(m/r^2)(2 + 6 x^2))."""
     m, s = 0.005, 0.0055
     cx = np.array([[0, 0, s], [0, 0, -s]])
-    px = np.array([[0, 0, 0.02], [0.03, 0, 0]])
-    pm = np.array([1e-6, 2e-6])
-    rq = oracle.perturber([m, m], cx, pm, px, quad=True)
-    r0 = oracle.perturber([m, m], cx, pm, px, quad=False)
-    rz, rx = 0.02, 0.03
-    ez = -m / (rz - s) ** 2 - m / (rz + s) ** 2
-    ex = -2 * m * rx / (rx * rx + s * s) ** 1.5
-    np.testing.assert_allclose(rq["a_pert"][0, 2], ez + (m / rz ** 2) * (2 + 6 * (s / rz) ** 2), rtol=1e-9)
-    np.testing.assert_allclose(rq["a_pert"][1, 0], ex + (m / rx ** 2) * (2 - 3 * (s / rx) ** 2), rtol=1e-9)
-    np.testing.assert_allclose(r0["a_pert"][0, 2], ez + 2 * m / rz ** 2, rtol=1e-12)
-    ep = -m / (rz - s) - m / (rz + s)
-    np.testing.assert_allclose(rq["pot_pert"][0], ep + (m / rz) * (2 + 2 * (s / rz) ** 2), rtol=1e-9)
-    # the members' side and Eq. 3 do not change
-    np.testing.assert_allclose(rq["a_chain"], r0["a_chain"], rtol=0, atol=0)
-    np.testing.assert_allclose(rq["corr"], r0["corr"], rtol=0, atol=0)
+    mom = oracle.chain_moments([m, m], cx)
+    T, pos = _probe_tree([[0.0, 0.0, 0.02], [0.0, 0.0, -0.03]])
+    xp = np.zeros((3, 1), np.float32)
+    a = T.forces(0.5, 0.0, True, xp, [2 * m], [0.0], extra_quad=[mom["Q"]], quad_skip=[0])[0]
+    r0, r1 = float(pos[2, 0]), float(-pos[2, 1])
+    np.testing.assert_allclose(a[2, 0], -2 * m / r0 ** 2, rtol=1e-14)
+    np.testing.assert_allclose(a[2, 1], (m / r1 ** 2) * (2 + 6 * (s / r1) ** 2), rtol=1e-13)
+    o = oracle.perturber([m, m], cx, [0.0], pos[:, :1].T.astype(np.float64))
+    exact = -m / (r0 - s) ** 2 - m / (r0 + s) ** 2
+    np.testing.assert_allclose(a[2, 0] + o["a_pert"][0, 2], exact, rtol=1e-12)
 
 
 def test_tidal_selection_closed_form():
