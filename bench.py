@@ -77,7 +77,8 @@ def make_workload(name: str, rank: int = 0) -> dict:
         d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=w.chain.mass,
                  chain_x=w.chain.pos, chain_v=w.chain.vel, pert_mode=2, pert_radius=0.0, pert_k=256)
         cfg = {"workload": "hernquist_gamma1_n4194304_smbh_binary", "n_stars": 1 << 22, "binary_a": 0.01,
-               "binary_e": 0.1, "smbh_mass": 0.005, "perturbers": "256 nearest"}
+               "binary_e": 0.1, "smbh_mass": 0.005, "perturbers": "256 nearest",
+               "chain_field_beyond_perturbers": "centre of mass + quadrupole"}
     elif name == "plummer":
         w = ics.plummer_workload(4096, seed=1 + base)
         d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=None, chain_x=None,
@@ -88,7 +89,8 @@ def make_workload(name: str, rank: int = 0) -> dict:
         d = dict(pos=e["pos"], vel=e["vel"], mass=e["mass"], offsets=e["offsets"], chain_m=e["chain_m"],
                  chain_x=e["chain_x"], chain_v=e["chain_v"], pert_mode=2, pert_radius=0.0, pert_k=256)
         cfg = {"workload": "ensemble64_hernquist_gamma1_smbh_binary", "n_stars": int(e["offsets"][-1]),
-               "members": 64, "member_sizes": "log-uniform 8192..524288 (seed 4)", "perturbers": "256 nearest"}
+               "members": 64, "member_sizes": "log-uniform 8192..524288 (seed 4)", "perturbers": "256 nearest",
+               "chain_field_beyond_perturbers": "centre of mass + quadrupole"}
     else:
         raise ValueError(name)
     d["eps"] = 0.01 if name == "plummer" else 0.005
@@ -299,15 +301,11 @@ def _p99(e):
     return float(s[max(0, math.ceil(0.99 * s.size) - 1)]) if s.size else float("nan")
 
 
-def p99_vs_direct(d, S, ctx, sample=2048, seed=77, model=False):
+def p99_vs_direct(d, S, sample=2048, seed=77):
     """p99 relative acceleration error of the current GPU forces against the
-    FP64 direct sum (the library's rv_direct_fp64, on the GPU) over each
-    sampled star's own member (stars softened, chain members unsoftened).
-    With model=True the reference is the direct sum of the method's own model
-    (Sect. 2): perturbers (the library's own selection) feel each chain
-    member, every other star feels the chain's centre of mass as one point
-    mass."""
-    import torch
+    fully resolved FP64 direct sum (the library's rv_direct_fp64, on the GPU)
+    over each sampled star's own member: stars softened, every chain member
+    an unsoftened body of its own (no chain model)."""
     import ics
     from paper_1507_01009_gb300 import rv
     xs = np.stack([t.cpu().numpy() for t in (S.x, S.y, S.z)]).astype(np.float64)
@@ -323,35 +321,18 @@ def p99_vs_direct(d, S, ctx, sample=2048, seed=77, model=False):
         if len(t) == 0:
             continue
         pos, mass, epsv = xs[:, s:e], m32[s:e], np.full(e - s, eps)
-        if cx is None:
-            ad, _ = rv.direct_fp64(pos, mass, epsv, t - s)
-            errs.append(_rel_err(a[:, t], ad))
-            continue
-        nch = S.n_chain
-        cm = d["chain_m"][k * nch:(k + 1) * nch]
-        cpos = cx[k * nch:(k + 1) * nch]
-        res_pos = np.concatenate([pos, cpos.T], 1)
-        res_m = np.concatenate([mass, cm])
-        res_e = np.concatenate([epsv, np.zeros(nch)])
-        ad, _ = rv.direct_fp64(res_pos, res_m, res_e, t - s)
-        if model:
-            com = (cm[:, None] * cpos).sum(0) / cm.sum()
-            xyz = [torch.from_numpy(np.ascontiguousarray(pos[q].astype(np.float32))).cuda() for q in range(3)]
-            c32 = [float(v) for v in com.astype(np.float32)]
-            if d["pert_mode"] == 1:
-                idx, cnt = ctx.select_perturbers(*xyz, c32, 1, radius=float(d["pert_radius"]), cap=e - s)
-            else:
-                idx, cnt = ctx.select_perturbers(*xyz, c32, 2, k=int(d["pert_k"]), cap=e - s)
-            ctx.sync_status()
-            pert = idx[:int(cnt.item())].cpu().numpy()
-            far = ~np.isin(t - s, pert)
-            if far.any():
-                com_pos = np.concatenate([pos, com[:, None]], 1)
-                acom, _ = rv.direct_fp64(com_pos, np.concatenate([mass, [cm.sum()]]), np.concatenate([epsv, [0.0]]),
-                                         (t - s)[far])
-                ad[:, far] = acom
+        if cx is not None:
+            nch = S.n_chain
+            cm = d["chain_m"][k * nch:(k + 1) * nch]
+            pos = np.concatenate([pos, cx[k * nch:(k + 1) * nch].T], 1)
+            mass = np.concatenate([mass, cm])
+            epsv = np.concatenate([epsv, np.zeros(nch)])
+        ad, _ = rv.direct_fp64(pos, mass, epsv, t - s)
         errs.append(_rel_err(a[:, t], ad))
     return _p99(np.concatenate(errs))
+
+
+P99_BOUND = 1e-3   # the metric's accuracy condition
 
 
 def run_gpu(args):
@@ -452,8 +433,7 @@ def run_gpu(args):
         value = job_throughput(ws, upd / args.steps, args.steps, total_ms)
     else:
         value = job_throughput(ws, n, args.steps, total_ms)
-    p99 = p99_vs_direct(d, S, ctx) if rank == 0 else None
-    p99_model = p99_vs_direct(d, S, ctx, model=True) if rank == 0 and S.n_chain > 0 else p99
+    p99 = p99_vs_direct(d, S) if rank == 0 else None
 
     # ---- dominant kernel: the walk. Its launches inside the timed steps were timed
     # with CUDA events on the launching stream (not possible inside a replayed
@@ -555,8 +535,8 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-                "p99_rel_err_vs_fp64_direct": p99,
-                "p99_vs_fp64_direct_of_the_method_model": p99_model, "clocks": sampler.summary(),
+                "p99_rel_err_vs_fp64_direct": p99, "meets_p99": bool(p99 is not None and p99 <= P99_BOUND),
+                "clocks": sampler.summary(),
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": float(np.mean(e2e_ms))},
                 "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,

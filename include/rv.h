@@ -204,7 +204,16 @@ rv_status rv_perturber_forces(rv_ctx *ctx, int32_t n_ch, const double *chain_m, 
  * index), 3 = the tidal criterion of Eq. 2 with r_crit = pert_radius and
  * gamma_crit = pert_gamma (see rv_select_perturbers_tidal); at most
  * min(5000, 65536 / n_members) per member (overflow of a radius or tidal
- * search is reported by rv_sync_status as RV_E_WORKSPACE). */
+ * search is reported by rv_sync_status as RV_E_WORKSPACE).
+ * chain_quad: 0 = the stars that are not perturbers feel each chain as its
+ * centre-of-mass point mass (Sect. 2 as written); 1 = they also feel the
+ * chain's traceless quadrupole about its centre of mass, Q_ab = sum_k m_k
+ * (3 d_a d_b - |d|^2 delta_ab), d = x_k - centre, with the cells' expansion
+ * (Sect. 1; unsoftened, FP32). Perturbers never get it: they feel the
+ * resolved members (FP64) as before. (Without it, the stars around a pair of
+ * SMBHs 0.01 apart miss 1e-3 in their force out to r ~ 0.15.) The quadrupole
+ * acts on the stars only: the chain members' forces are those of
+ * chain_quad = 0. Chains of one member have no quadrupole. */
 typedef struct {
     int64_t n;
     float *x, *y, *z, *vx, *vy, *vz;
@@ -219,6 +228,7 @@ typedef struct {
     const int64_t *member_offsets;
     float pert_gamma;
     int32_t n_chains;  /* chains per member (0 or 1: one); chain c belongs to member c / n_chains */
+    int32_t chain_quad;
 } rv_system;
 
 /* One full force evaluation of a system: tree build, perturber selection,

@@ -260,9 +260,13 @@ __device__ __forceinline__ void kep(double rx, double ry, double rz, double m, d
 // Per member m (out8 + 16 m): [0..3) corr (Eq. 3), [3..6) sub, [6] sum_k m_k
 // pot_chain[k] / M, [7] sub potential, [8..11) centre of mass, [11] M.
 // With xyzm, the centre of mass also becomes member m's extra particle m
-// (FP32, unsoftened).
+// (FP32, unsoftened). With xq, the chain's traceless quadrupole about its
+// centre of mass, Q_ab = sum_k m_k (3 d_a d_b - |d|^2 delta_ab), d = x_k - c
+// (the expansion of Sect. 1 applied to the chain), computed in FP64, goes
+// rounded to FP32 to xq[2 m] = (xx, yy, zz, xy), xq[2 m + 1] = (xz, yz, 0, 0)
+// for the walk.
 __global__ void chain_com_k(int M, int n_ch, const double *cm, const double *cx, double *out8, float *xyzm,
-                            float *xeps) {
+                            float *xeps, float4 *xq = nullptr) {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
         const double *mm = cm + (int64_t)m * n_ch, *xx = cx + 3 * (int64_t)m * n_ch;
         double Mt = 0, c[3] = {0, 0, 0};
@@ -278,6 +282,21 @@ __global__ void chain_com_k(int M, int n_ch, const double *cm, const double *cx,
             xyzm[4 * m + 3] = (float)Mt;
             xeps[m] = 0.f;
         }
+        if (xq) {
+            double q[6] = {0, 0, 0, 0, 0, 0};
+            for (int k = 0; k < n_ch; k++) {
+                const double d0 = xx[3 * k] - c[0], d1 = xx[3 * k + 1] - c[1], d2 = xx[3 * k + 2] - c[2];
+                const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+                q[0] += mm[k] * (3.0 * d0 * d0 - dd);
+                q[1] += mm[k] * (3.0 * d1 * d1 - dd);
+                q[2] += mm[k] * (3.0 * d2 * d2 - dd);
+                q[3] += mm[k] * 3.0 * d0 * d1;
+                q[4] += mm[k] * 3.0 * d0 * d2;
+                q[5] += mm[k] * 3.0 * d1 * d2;
+            }
+            xq[2 * m] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+            xq[2 * m + 1] = make_float4((float)q[4], (float)q[5], 0.f, 0.f);
+        }
     }
 }
 
@@ -292,7 +311,8 @@ struct ChainView {
 
 __device__ __forceinline__ int npert_of(const ChainView &V, int m) { return V.npert ? min(V.npert[m], V.cap) : V.cap; }
 
-// perturbers: resolved members minus the centre-of-mass point mass
+// perturbers: resolved members minus the centre-of-mass point mass (the walk
+// gives perturbers the point mass only, never the chain's quadrupole)
 __global__ void pert_on_stars_k(ChainView V, const double *out8, double *a_pert, double *pot_pert) {
     const int m = blockIdx.y;
     const int np = npert_of(V, m);
@@ -412,6 +432,15 @@ __global__ void gather_pert_k(int cap, const int *idx, const int *npert, const f
     }
 }
 
+// flag[i] = 1 for every star that is a perturber of some chain (the walk gives
+// those no chain quadrupole: they feel the resolved members instead)
+__global__ void mark_pert_k(int cap, const int *idx, const int *npert, uint8_t *flag) {
+    const int mb = blockIdx.y;
+    const int np = min(npert[mb], cap);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x)
+        flag[idx[(int64_t)mb * cap + p]] = 1;
+}
+
 // perturbers of the last selection predicted to first order, dt after the force pass
 // (Sect. 2: the chain integrator predicts them at each of its force evaluations):
 // x_p(dt) = x_p + v_p dt in FP64, one rounding per operation
@@ -513,9 +542,11 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s, const BlockSe
     int64_t tmp[2];
     const int64_t *off = system_offsets(sys, tmp);
     const int cap = member_cap(std::max(1, NC));
+    // the chain's quadrupole acts on the stars beyond its perturbers (rv_system.chain_quad)
+    const bool quad = chain && sys->chain_quad != 0 && sys->n_chain > 1;
     if (chain) {
         chain_com_k<<<ceil_div(NC, 128), 128, 0, s>>>(NC, sys->n_chain, sys->chain_m, sys->chain_x, w.out8,
-                                                      w.extra_xyzm, w.extra_eps);
+                                                      w.extra_xyzm, w.extra_eps, quad ? w.extra_quad : nullptr);
         count_launch(c);
     }
     if ((r = upload_offsets(c, M, off, s)) != RV_OK) return r;
@@ -546,6 +577,11 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s, const BlockSe
     } else if (chain) {
         cudaMemsetAsync(w.npert, 0, sizeof(int) * NC, s);
     }
+    if (quad) {
+        cudaMemsetAsync(w.pflag, 0, (size_t)std::max<int64_t>(sys->n, 1), s);
+        mark_pert_k<<<dim3(ceil_div(cap, 128), NC), 128, 0, s>>>(cap, w.pert_idx, w.npert, w.pflag);
+        count_launch(c);
+    }
     if ((r = build_tree(c, M, off, sys->x, sys->y, sys->z, sys->m, s)) != RV_OK) return r;
     const uint8_t *gact = nullptr;
     if (blk) {
@@ -557,7 +593,8 @@ rv_status system_forces(rv_ctx *c, rv_system *sys, cudaStream_t s, const BlockSe
     const RelMac rel{c->cfg.alpha, sys->ax, sys->ay, sys->az};
     if ((r = tree_walk(c, c->cfg.theta, c->cfg.eps_star, NC, w.extra_xyzm, w.extra_eps, nullptr, C,
                        sys->ax, sys->ay, sys->az, sys->pot, w.extra_out, s, nullptr,
-                       c->cfg.mac == 1 ? &rel : nullptr, gact)) != RV_OK)
+                       c->cfg.mac == 1 ? &rel : nullptr, gact, quad ? w.extra_quad : nullptr,
+                       quad ? w.pflag : nullptr)) != RV_OK)
         return r;
     c->pert_members = NC;
     if (chain) {

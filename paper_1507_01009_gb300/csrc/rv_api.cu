@@ -88,6 +88,8 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.extra_xyzm = (float *)take(16 * kExtraTotal);
     t.extra_eps = (float *)take(4 * kExtraTotal);
     t.extra_out = (float *)take(16 * kExtraTotal);
+    t.extra_quad = (float4 *)take(32 * kExtraTotal);
+    t.pflag = (uint8_t *)take(n);
     t.red = (double *)take(8 * 9 * kRedSlots);
     t.sel_flag = (int *)take(4 * n);
     t.moff = (int64_t *)take(8 * (kMaxMembers + 1));

@@ -81,6 +81,8 @@ struct Workspace {
     double *chain_ext_a, *chain_ext_pot;  // [3 kMaxChain], [kMaxChain]
     double *out8;         // Eq. 3 correction, sub, potentials
     float *extra_xyzm, *extra_eps, *extra_out;  // [4 kMaxExtra], [kMaxExtra], [4 kMaxExtra]
+    float4 *extra_quad;   // [2 kExtraTotal]: each chain's traceless quadrupole (xx, yy, zz, xy), (xz, yz, 0, 0)
+    uint8_t *pflag;       // [n]: 1 for the stars that are perturbers of a chain (caller order)
     double *red;          // energy partial sums
     int *sel_flag;        // perturber selection flags (n)
     // members (independent systems sharing one build and one walk)
@@ -168,7 +170,8 @@ struct RelMac {
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, int extras_per_member, float *ax, float *ay, float *az, float *pot,
                     float *xout, cudaStream_t s, const PairRecord *rec = nullptr, const RelMac *rel = nullptr,
-                    const uint8_t *gact = nullptr);
+                    const uint8_t *gact = nullptr, const float4 *xquad = nullptr,
+                    const uint8_t *xq_skip = nullptr);
 
 // chain.cu
 // mode 1 radius, 2 k nearest, 3 tidal (Eq. 2: radius = r_crit, star masses m, gamma);

@@ -79,6 +79,8 @@ struct WalkArgs {
     int n_extra;
     const float *xyzm;   // extra particles (x, y, z, m)
     const float *xeps;
+    const float4 *xquad; // optional: each extra particle's traceless quadrupole, 2 float4 (see extra_terms)
+    const uint8_t *xq_skip;  // optional, per star (caller order): 1 = no quadrupole terms (a chain's perturber)
     float *ax, *ay, *az, *pot;
     float *xout;
     // optional record of accepted (group, cell) pairs that a walk at the
@@ -639,9 +641,14 @@ __device__ __forceinline__ void combine_shares(const Acc *acc, int s, int p, int
 
 // Direct terms of the extra particles of `member` on one target (pair
 // softening rule of Sect. 3: max(eps_i, eps_j), none if either is
-// unsoftened), absolute FP32.
+// unsoftened), absolute FP32. With A.xquad, an extra particle (a chain seen
+// from outside) also carries a traceless quadrupole Q about its position,
+// (xx, yy, zz, xy), (xz, yz, 0, 0), whose field is added as for a cell: with
+// d = x_extra - x_i = -r and rho^2 = d.d + e^2,
+//   a += -Q d / rho^5 + 5/2 (d.Q.d) d / rho^7,  phi -= (d.Q.d) / (2 rho^5),
+// unless use_quad is false (a target that is a chain's perturber).
 __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float yi, float zi, float ei, int skip,
-                                            int member, Acc &acc) {
+                                            int member, Acc &acc, bool use_quad = true) {
     float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
     const int k0 = A.extra_per_member ? member * A.extra_per_member : 0;
     const int k1 = A.extra_per_member ? min(k0 + A.extra_per_member, A.n_extra) : A.n_extra;
@@ -658,6 +665,20 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
         float mr3 = mr * rinv * rinv;
         tx = fmaf(mr3, dx, tx); ty = fmaf(mr3, dy, ty); tz = fmaf(mr3, dz, tz);
         tp -= mr;
+        if (A.xquad && use_quad) {
+            const float4 q1 = A.xquad[2 * k], q2 = A.xquad[2 * k + 1];
+            const float qx = fmaf(q1.x, dx, fmaf(q1.w, dy, q2.x * dz));
+            const float qy = fmaf(q1.w, dx, fmaf(q1.y, dy, q2.y * dz));
+            const float qz = fmaf(q2.x, dx, fmaf(q2.y, dy, q1.z * dz));
+            const float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
+            const float u = rinv * rinv;
+            const float r5 = rinv * u * u;
+            const float b = 2.5f * dqd * r5 * u;
+            tx = fmaf(b, dx, fmaf(-r5, qx, tx));
+            ty = fmaf(b, dy, fmaf(-r5, qy, ty));
+            tz = fmaf(b, dz, fmaf(-r5, qz, tz));
+            tp = fmaf(-0.5f * dqd, r5, tp);
+        }
     }
     nadd(acc.ax, acc.cx, tx); nadd(acc.ay, acc.cy, ty); nadd(acc.az, acc.cz, tz); nadd(acc.ph, acc.cp, tp);
 }
@@ -802,8 +823,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
             // the star's own pair was evaluated at r = 0: remove its -m/eps (the product
             // rounded on its own, as in the pair, so that the two cancel exactly)
             if (SOFT) tot.ph += __fmul_rn(ps.w, rsqrtf(A.eps2));
-            if (A.n_extra > 0) extra_terms(A, ps.x, ps.y, ps.z, A.eps_star, -1, mg, tot);
             int o = A.perm[grp.first + i];
+            if (A.n_extra > 0) extra_terms(A, ps.x, ps.y, ps.z, A.eps_star, -1, mg, tot, !(A.xq_skip && A.xq_skip[o]));
             A.ax[o] = tot.ax + tot.cx;
             A.ay[o] = tot.ay + tot.cy;
             A.az[o] = tot.az + tot.cz;
@@ -929,7 +950,8 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
 
 rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const float *xyzm, const float *xeps,
                     const int *xmem, int extras_per_member, float *ax, float *ay, float *az, float *pot,
-                    float *xout, cudaStream_t s, const PairRecord *rec, const RelMac *rel, const uint8_t *gact) {
+                    float *xout, cudaStream_t s, const PairRecord *rec, const RelMac *rel, const uint8_t *gact,
+                    const float4 *xquad, const uint8_t *xq_skip) {
     Workspace &w = c->w;
     WalkArgs A;
     A.pos = w.pos;
@@ -954,6 +976,8 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.n_extra = n_extra;
     A.xyzm = xyzm;
     A.xeps = xeps;
+    A.xquad = n_extra > 0 ? xquad : nullptr;
+    A.xq_skip = xq_skip;
     A.ax = ax; A.ay = ay; A.az = az; A.pot = pot;
     A.xout = xout;
     A.pairs = rec ? rec->pairs : nullptr;

@@ -65,7 +65,7 @@ class rv_system(C.Structure):
                 ("chain_x", C.c_void_p), ("chain_v", C.c_void_p), ("chain_a", C.c_void_p),
                 ("chain_pot", C.c_void_p), ("pert_mode", C.c_int32), ("pert_radius", C.c_float),
                 ("pert_k", C.c_int32), ("n_members", C.c_int32), ("member_offsets", C.c_void_p),
-                ("pert_gamma", C.c_float), ("n_chains", C.c_int32)]
+                ("pert_gamma", C.c_float), ("n_chains", C.c_int32), ("chain_quad", C.c_int32)]
 
 
 def lib_path() -> str:
@@ -460,14 +460,15 @@ class System:
     """Device state of stars (FP32, caller order) and an optional chain (FP64)."""
 
     def __init__(self, pos, vel, mass, chain_m=None, chain_x=None, chain_v=None, pert_mode=0, pert_radius=0.0,
-                 pert_k=0, member_offsets=None, pert_gamma=0.0, chains_per_member=1):
+                 pert_k=0, member_offsets=None, pert_gamma=0.0, chains_per_member=1, chain_quad=True):
         """pos/vel (3, n); mass (n,). member_offsets: host ints [M + 1] for M
         independent members stored one after another (None: one member).
         chain_* are member-major: chain_m (M n_ch,) or (n_ch,), chain_x/v
         (M n_ch, 3). pert_mode 1 radius, 2 k nearest, 3 tidal (Eq. 2,
         r_crit = pert_radius, gamma_crit = pert_gamma). chains_per_member: C
         chains in every member (chain arrays hold M C chains of n_ch members,
-        member by member)."""
+        member by member). chain_quad: the stars beyond the perturbers also
+        feel each chain's quadrupole (rv_system.chain_quad)."""
         import torch
         f32 = dict(dtype=torch.float32, device="cuda")
         f64 = dict(dtype=torch.float64, device="cuda")
@@ -496,6 +497,7 @@ class System:
             self.member_offsets = np.ascontiguousarray(member_offsets, dtype=np.int64)
             self.n_members = int(len(self.member_offsets) - 1)
         self.chains_per_member = int(chains_per_member)
+        self.chain_quad = int(bool(chain_quad))
         if self.n_chain:
             self.n_chain //= self.n_members * self.chains_per_member   # members of each chain
         self._c = None
@@ -512,6 +514,7 @@ class System:
         s.pert_mode, s.pert_radius, s.pert_k = self.pert_mode, self.pert_radius, self.pert_k
         s.pert_gamma = self.pert_gamma
         s.n_chains = self.chains_per_member
+        s.chain_quad = self.chain_quad
         s.n_members = self.n_members
         s.member_offsets = None if self.member_offsets is None else self.member_offsets.ctypes.data
         self._c = s
