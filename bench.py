@@ -1,36 +1,44 @@
 """Benchmark: tree-force particles/s on one GB300 at p99 relative force
 error <= 1e-3 against the FP64 direct sum.
 
-Default workload (the one the metric is quoted on): a Hernquist (Dehnen
-gamma = 1) galaxy of 2^20 equal-mass stars, total mass 1, scale radius 1,
-plus one SMBH of mass 0.005 on a circular orbit at r = 0.5; star softening
-0.005; SMBH-star forces unsoftened, FP64 for the stars within 0.02 of the
-SMBH; opening angle 0.5 with quadrupoles.
-
-One step = the whole force path once: kick/drift, perturber selection, tree
-build (bounds, keys, sort, topology, multipoles, groups), tree walk, FP64
-perturber coupling and chain hand-off, kick, FP64 energy/momentum totals.
+Default workload (the largest configuration the metric names that fits one
+GPU): a Hernquist (Dehnen gamma = 1) galaxy of 2^24 equal-mass stars, total
+mass 1, scale radius 1, isotropic velocities from the distribution function;
+star softening 0.005; opening angle 0.8 with quadrupoles (the tree of the
+learned-correction configuration). One step = the whole force path once:
+kick/drift, tree build (bounds, keys, sort, topology, multipoles, groups),
+tree walk, kick, FP64 energy/momentum totals, replayed from a CUDA graph.
+Reported beside the value: the learned cell-force correction (the network is
+trained first, untimed, on samples the code generates) as a force pass at
+theta 0.8 and at theta 1.0, the plain tree's force pass at the same angles,
+and the network kernel's tensor-core roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload hernquist_bh|hernquist_bh_relmac|hernquist_binary|plummer|ensemble|learned]
+                  [--workload learned|hernquist_bh|hernquist_bh_relmac|hernquist_bh_block|hernquist_binary|plummer|ensemble]
 
-Other workloads: `hernquist_bh_block` (the default workload on block time
-steps: levels 0..4 below dt_max = 1/64 from tau_acc = tau_vel = 0.3, walks of
-the groups holding an active star; particles = active star updates),
-`hernquist_bh_relmac` (the default workload with the
-relative opening criterion the paper's runs use, tolerance 1e-3, the previous
-step's accelerations as references), `hernquist_binary` (2^22 stars, central SMBH pair, 256
-nearest perturbers), `plummer` (4096 stars), `ensemble` (64 independent
-Hernquist realisations, sizes log-uniform in 8192..524288, each with a
-central SMBH pair, all members in one build and one walk per step). Every
-step except the block scheme's is captured once as a CUDA graph and
-replayed (--no-graph launches its kernels one by one); walk parameters come
-from the autotuner.
+Other workloads: `hernquist_bh` (2^20 stars plus one SMBH of mass 0.005 on a
+circular orbit at r = 0.5, its FP64 perturbers within r < 0.02, theta 0.5),
+`hernquist_bh_block` (the same on block time steps: levels 0..4 below
+dt_max = 1/64 from tau_acc = tau_vel = 0.3, walks of the groups holding an
+active star; particles = active star updates), `hernquist_bh_relmac` (the
+same with the relative opening criterion the paper's runs use, tolerance
+1e-3, the previous step's accelerations as references), `hernquist_binary`
+(2^22 stars, central SMBH pair, 256 nearest perturbers, the pair's
+quadrupole on the other stars), `plummer` (4096 stars), `ensemble` (64
+independent Hernquist realisations, sizes log-uniform in 8192..524288, each
+with a central SMBH pair, all members in one build and one walk per step).
+Every step except the block scheme's is captured once as a CUDA graph and
+replayed (--no-graph launches its kernels one by one). Each workload fixes
+its tree (leaf size, walk group); the autotuner picks the interaction tile,
+and a wider sweep over (group, leaf, tile) is reported beside.
 
 Under torchrun (N > 1) every rank runs its own realisation (replicas: no
 data exchange); the value is the sum of particles over ranks / max time.
 --impl reference times the CPU oracle (FP64, all host cores) on the same
-workload, on a bounded sample per step.
+workload: its tree of all stars is built once (timed, reported), and each
+step walks a fresh seeded sample of 8192 stars on it; ms_per_step is the
+measured wall time of a step, and the value is the whole-pass throughput
+n / (build + n x walk time per star) with the scale stated in the line.
 """
 from __future__ import annotations
 
@@ -66,7 +74,12 @@ def _dist():
 def make_workload(name: str, rank: int = 0) -> dict:
     import ics
     base = 1000 * rank
-    if name in ("hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block"):
+    if name == "learned":
+        w = ics.hernquist(1 << 24, seed=5 + base)
+        d = dict(pos=w.pos, vel=w.vel, mass=w.mass, offsets=None, chain_m=None, chain_x=None, chain_v=None,
+                 pert_mode=0, pert_radius=0.0, pert_k=0)
+        cfg = {"workload": "hernquist_gamma1_n16777216", "n_stars": 1 << 24}
+    elif name in ("hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block"):
         w = ics.hernquist_bh_workload(1 << 20, seed=2 + base)
         d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=w.chain.mass,
                  chain_x=w.chain.pos, chain_v=w.chain.vel, pert_mode=1, pert_radius=0.02, pert_k=0)
@@ -94,13 +107,19 @@ def make_workload(name: str, rank: int = 0) -> dict:
     else:
         raise ValueError(name)
     d["eps"] = 0.01 if name == "plummer" else 0.005
-    d["theta"] = 0.5
+    d["theta"] = 0.8 if name == "learned" else 0.5
     d["dt"] = 1e-3
     d["name"] = name
     d["n"] = int(d["mass"].shape[0])
+    # the workload's tree (both arms build the same one); the walk's tile is tuned
+    d["n_leaf"], d["group"] = (16, 32) if name == "plummer" else (24, 64)
+    star_mb = 44 * d["n"] / 1e6   # x, y, z, vx, vy, vz, m, ax, ay, az, pot (FP32)
+    cfg["l2"] = (f"star arrays {star_mb:.1f} MB" + (" (larger than the 129 MB L2)" if star_mb > 129 else "") + "; " +
+                 "GPU arm: 256 MiB written between timed steps (L2 flush)")
     # the paper's runs open cells by a relative ("Gadget") criterion with tolerance 1e-3 (Sect. 3)
     d["mac"], d["alpha"] = (1, 1e-3) if name.endswith("_relmac") else (0, 1e-3)
-    cfg.update({"eps_star": d["eps"], "theta": 0.5, "quadrupole": True, "dt": 1e-3})
+    cfg.update({"eps_star": d["eps"], "theta": d["theta"], "quadrupole": True, "dt": 1e-3,
+                "n_leaf": d["n_leaf"], "walk_group": d["group"]})
     if d["mac"] == 1:
         cfg.update({"workload": cfg["workload"] + "_relative_mac", "mac": "relative (M s^2 <= alpha |a| d^4)",
                     "alpha": d["alpha"], "theta_for_first_pass_and_smbh": 0.5})
@@ -179,56 +198,71 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reported baseline; never tuned)
 # ---------------------------------------------------------------------------
-def oracle_step_time(d, sample=65536, seed=0, max_stars=1 << 20):
-    """Seconds for one oracle force pass over the whole workload, from a
-    bounded sample: oracle trees of the members covering the first
-    <= max_stars stars, walks of `sample` of their stars, both scaled to all
-    stars. Returns (seconds, description)."""
-    import ics
-    import oracle
-    p32 = d["pos"].astype(np.float32)
-    m32 = d["mass"].astype(np.float32)
-    ranges = member_ranges(d)
-    chosen, tot = [], 0
-    for (s, e) in ranges:
-        if e == s:
-            continue
-        if chosen and tot + (e - s) > max_stars:
-            break
-        chosen.append((s, e))
-        tot += e - s
-    per = max(1, sample // len(chosen))
-    t_build = t_walk = 0.0
-    walked = 0
-    for k, (s, e) in enumerate(chosen):
+REF_SAMPLE = 8192   # stars walked per oracle step (both the reference arm and the cpu_baseline leg)
+
+
+class OracleRun:
+    """The CPU oracle on a workload, with the workload's tree (leaf size, walk
+    group) and the same method as the GPU path (each chain's centre of mass an
+    unsoftened extra particle carrying the chain's quadrupole). The trees of
+    the members are built once, timed; each step walks a seeded sample of
+    stars on them and is timed. full_pass_s() scales both to one pass over
+    all stars."""
+
+    def __init__(self, d, max_stars=1 << 24):
+        import oracle
+        self.d = d
+        p32 = d["pos"].astype(np.float32)
+        m32 = d["mass"].astype(np.float32)
+        self.ranges = [(s, e) for (s, e) in member_ranges(d) if e > s]
+        chosen, tot = [], 0
+        for (s, e) in self.ranges:
+            if chosen and tot + (e - s) > max_stars:
+                break
+            chosen.append((s, e))
+            tot += e - s
+        self.chosen, self.tot = chosen, tot
         t0 = time.perf_counter()
-        T = oracle.Tree(p32[:, s:e], m32[s:e], 16, 32)
-        t1 = time.perf_counter()
-        tg = ics.subsample(e - s, per, seed=seed + k)
-        rel = None
-        if d.get("mac") == 1:
-            # references for the relative criterion: the Hernquist field -x / (r (r + 1)^2) (G = M = a = 1)
-            x = p32[:, s:e].astype(np.float64)
-            r = np.maximum(np.linalg.norm(x, axis=0), 1e-12)
-            rel = (d["alpha"], (-x / (r * (r + 1.0) ** 2)).astype(np.float32))
-        if d["chain_m"] is not None:
-            nch = len(d["chain_m"]) // len(ranges)
-            mi = ranges.index((s, e))
-            cm = d["chain_m"][mi * nch:(mi + 1) * nch]
-            cx = d["chain_x"][mi * nch:(mi + 1) * nch]
-            com = (cm[:, None] * cx).sum(0) / cm.sum()
-            T.forces(d["theta"], float(np.float32(d["eps"])), True, com.astype(np.float32).reshape(3, 1),
-                     np.array([float(np.float32(cm.sum()))]), [0.0], targets=tg, rel=rel)
-        else:
-            T.forces(d["theta"], float(np.float32(d["eps"])), True, targets=tg, rel=rel)
-        t2 = time.perf_counter()
-        t_build += t1 - t0
-        t_walk += t2 - t1
-        walked += len(tg)
-    full = (t_build * d["n"] / tot) + t_walk * d["n"] / walked
-    desc = (f"oracle trees of {len(chosen)} member(s) ({tot} stars) + walks of {walked} sampled stars; "
-            f"build scaled x{d['n'] / tot:.2f}, walk scaled x{d['n'] / walked:.1f}")
-    return full, desc
+        self.trees = [oracle.Tree(p32[:, s:e], m32[s:e], d["n_leaf"], d["group"]) for (s, e) in chosen]
+        self.build_s = time.perf_counter() - t0
+        self.p32 = p32
+
+    def step(self, sample, seed):
+        """Walks of `sample` stars spread over the built members; returns (seconds, stars walked)."""
+        import ics
+        import oracle
+        d = self.d
+        per = max(1, sample // len(self.chosen))
+        walked, t = 0, 0.0
+        for k, ((s, e), T) in enumerate(zip(self.chosen, self.trees)):
+            tg = ics.subsample(e - s, min(per, e - s), seed=seed * 1000 + k)
+            rel = None
+            if d.get("mac") == 1:
+                # references for the relative criterion: the Hernquist field -x / (r (r + 1)^2) (G = M = a = 1)
+                x = self.p32[:, s:e].astype(np.float64)
+                r = np.maximum(np.linalg.norm(x, axis=0), 1e-12)
+                rel = (d["alpha"], (-x / (r * (r + 1.0) ** 2)).astype(np.float32))
+            t0 = time.perf_counter()
+            if d["chain_m"] is not None:
+                nch = len(d["chain_m"]) // len(self.ranges)
+                mi = member_ranges(d).index((s, e))
+                mom = oracle.chain_moments(d["chain_m"][mi * nch:(mi + 1) * nch], d["chain_x"][mi * nch:(mi + 1) * nch])
+                xq = [mom["Q"]] if nch > 1 else None
+                T.forces(d["theta"], float(np.float32(d["eps"])), True, mom["com"].astype(np.float32).reshape(3, 1),
+                         np.array([float(np.float32(mom["M"]))]), [0.0], targets=tg, rel=rel, extra_quad=xq)
+            else:
+                T.forces(d["theta"], float(np.float32(d["eps"])), True, targets=tg, rel=rel)
+            t += time.perf_counter() - t0
+            walked += len(tg)
+        return t, walked
+
+    def full_pass_s(self, walk_s, walked):
+        return self.build_s * self.d["n"] / self.tot + walk_s * self.d["n"] / walked
+
+    def describe(self, walked):
+        return (f"oracle trees (n_leaf {self.d['n_leaf']}, group {self.d['group']}) of {len(self.chosen)} member(s) "
+                f"({self.tot} stars, built once in {self.build_s:.2f} s) + walks of {walked} seeded stars per step; "
+                f"whole pass = build x {self.d['n'] / self.tot:.3f} + walk x {self.d['n'] / walked:.1f}")
 
 
 def run_reference(args):
@@ -236,18 +270,23 @@ def run_reference(args):
     if rank != 0:
         return 0
     d = make_workload(args.workload, 0)
+    orc = OracleRun(d)
     for i in range(args.warmup):
-        oracle_step_time(d, sample=8192, seed=100 + i)
-    times, desc = [], ""
+        orc.step(REF_SAMPLE, seed=100 + i)
+    step_s, walked = [], 0
     for i in range(args.steps):
-        t, desc = oracle_step_time(d, sample=8192, seed=i)
-        times.append(t)
-    ms = 1e3 * float(np.mean(times))
-    value = d["n"] / (ms / 1e3)
+        t, walked = orc.step(REF_SAMPLE, seed=i)
+        step_s.append(t)
+    walk_s = float(np.mean(step_s))
+    value = d["n"] / orc.full_pass_s(walk_s, walked)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * walk_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": d["config"],
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc},
+            "step": f"oracle walk of {walked} sampled stars (measured wall time)",
+            "scale": {"build_s": orc.build_s, "build_scale": d["n"] / orc.tot, "walk_scale": d["n"] / walked,
+                      "whole_pass_s": orc.full_pass_s(walk_s, walked)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": orc.describe(walked)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -352,15 +391,20 @@ def run_gpu(args):
     use_graph = args.workload not in ("hernquist_bh_block",) and not args.no_graph
     blk = d["block"]
 
-    # walk parameters (not part of the workload): the autotuner's pick over a small grid, untimed
+    # the walk's interaction tile: the autotuner's pick for the workload's tree (untimed); a wider
+    # sweep over (group, leaf, tile) is reported beside
     from paper_1507_01009_gb300 import autotune
     p32 = d["pos"].astype(np.float32)
     xs = [torch.from_numpy(np.ascontiguousarray(p32[a])).to(dev) for a in range(3)]
     ms = torch.from_numpy(d["mass"].astype(np.float32)).to(dev)
-    tuned = autotune.autotune(*xs, ms, offsets=d["offsets"], theta=d["theta"], eps_star=float(np.float32(d["eps"])),
-                              grid=autotune.candidates(groups=(32, 64), leaves=(16, 24, 32), tiles=(64, 128)), reps=2)
+    tkw = dict(offsets=d["offsets"], theta=d["theta"], eps_star=float(np.float32(d["eps"])), reps=2, cache_path=None)
+    tuned = autotune.autotune(*xs, ms, grid=autotune.candidates(groups=(d["group"],), leaves=(d["n_leaf"],),
+                                                                 tiles=autotune.GRID_TILE), **tkw)
+    wide = autotune.autotune(*xs, ms, grid=autotune.candidates(groups=(32, 64), leaves=(8, 16, 24, 32),
+                                                                tiles=(64, 128, 256)), **tkw) if not args.no_sweep else None
     tune = tuned["config"]
-    del xs, ms
+    if d["name"] != "learned":
+        del xs, ms
     ctx = rv.Context(n, theta=d["theta"], eps_star=float(np.float32(d["eps"])), mac=d["mac"], alpha=d["alpha"],
                      **tune)
     S = rv.System(d["pos"], d["vel"], d["mass"], chain_m=d["chain_m"], chain_x=d["chain_x"], chain_v=d["chain_v"],
@@ -516,31 +560,48 @@ def run_gpu(args):
     ctx.sync_status(stream=stream)
     e2e_val = ws * (upd / args.steps if blk else n) / (float(np.mean(e2e_ms)) / 1e3)
 
+    learned, roof_net = None, None
+    if d["name"] == "learned" and rank == 0 and not args.no_learned:
+        del S, ctx
+        torch.cuda.empty_cache()
+        learned, roof_net = learned_leg(d, xs, ms, tune, flush, args.steps, max(3, args.warmup))
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        sec, desc = oracle_step_time(d, sample=65536, seed=3)
-        cpu = {"value": n / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+        orc = OracleRun(d)
+        orc.step(REF_SAMPLE, seed=2)                      # warm-up
+        st = [orc.step(REF_SAMPLE, seed=3 + k) for k in range(2)]
+        cs, walked = float(np.mean([t for t, _ in st])), st[0][1]
+        cpu = {"value": n / orc.full_pass_s(cs, walked), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": orc.describe(walked) + "; 1 warm-up + 2 timed walks",
+               "measured_s": orc.build_s + 3 * cs}
 
     if rank == 0:
-        cfg = dict(d["config"])
-        cfg.update({"n_leaf": tune["n_leaf"], "walk_group": tune["group"], "tile": tune["tile"],
-                    "step": ("16 block substeps (drift, perturber select, build, walk of active groups, fp64 "
-                             "perturber/chain, kicks and levels of active stars) + energy" if blk else
-                             "kdk + perturber select + build + walk + fp64 perturber/chain + energy"),
-                    "parallelism": f"replicas{ws}" if ws > 1 else "single", "graph_captured": bool(use_graph),
-                    "l2": "flushed (256 MiB write) before every timed step"})
-        cfg["autotuned"] = {"cached": tuned["cached"], "candidates": len(tuned["table"]),
-                            "walk_ms_by_group_leaf_tile": {f'{r["group"]}/{r["n_leaf"]}/{r["tile"]}': round(r["walk_ms"], 3)
-                                                           for r in tuned["table"]}}
+        cfg = dict(d["config"])   # the workload, identical in the reference arm's line
+        run = {"tile": tune["tile"],
+               "step": ("16 block substeps (drift, perturber select, build, walk of active groups, fp64 "
+                        "perturber/chain, kicks and levels of active stars) + energy" if blk else
+                        "kdk + perturber select + build + walk + fp64 perturber/chain + energy"
+                        if d["chain_m"] is not None else "kdk + build + walk + energy"),
+               "parallelism": f"replicas{ws}" if ws > 1 else "single", "graph_captured": bool(use_graph)}
+        tuning = {"tile_grid_walk_ms": {str(r["tile"]): round(r["walk_ms"], 3) for r in tuned["table"]}}
+        if wide is not None:
+            best = min(wide["table"], key=lambda r: r["total_ms"])
+            tuning["wide_sweep_build_plus_walk_ms"] = {f'{r["group"]}/{r["n_leaf"]}/{r["tile"]}':
+                                                       round(r["total_ms"], 3) for r in wide["table"]}
+            tuning["wide_sweep_best"] = {k: best[k] for k in ("group", "n_leaf", "tile")}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-                "p99_rel_err_vs_fp64_direct": p99, "meets_p99": bool(p99 is not None and p99 <= P99_BOUND),
+                "run": run, "p99_rel_err_vs_fp64_direct": p99, "meets_p99": bool(p99 is not None and p99 <= P99_BOUND),
                 "clocks": sampler.summary(),
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": float(np.mean(e2e_ms))},
                 "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
-                "energy_drift": energy_drift}
+                "energy_drift": energy_drift, "autotune": tuning}
+        if learned is not None:
+            line["learned_correction"] = learned
+            line["roofline_network"] = roof_net
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -557,100 +618,96 @@ def _measured_peaks():
         return {}
 
 
-def run_learned(args):
-    """One step = tree build + walk at theta = 0.8 with the (group, cell) pair
-    record + network correction. The network is trained first (untimed) on
-    2^20 samples the code generates at theta = 0.8. Reported beside: the plain
-    tree at 0.8 and at 0.5 (p99 vs FP64 direct on a 2048-star sample)."""
+def learned_leg(d, xs, ms, tune, flush, steps, warmup):
+    """The learned cell-force correction beside the plain tree, as force
+    passes (build + walk [+ pair record + network + correction]) on the
+    workload's stars: at the workload's theta and at theta 1.0 (where the
+    plain tree misses p99 1e-3). At each angle a fresh network is trained
+    first (untimed) on 2^20 samples the code generates at that angle (400 Adam
+    steps of 8192 rows). p99 against the FP64 direct sum on 2048 seeded
+    stars; the network kernel alone is timed on the recorded pairs' row count."""
     import torch
     import ics
     from paper_1507_01009_gb300 import rv
-    ws, rank, local = _dist()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(local)
-    n = 1 << 24
-    th, trec = 0.8, 0.7
-    eps = float(np.float32(0.005))
-    w = ics.hernquist(n, 5)
-    p32 = w.pos.astype(np.float32)
-    m32 = w.mass.astype(np.float32)
-    x, y, z = (torch.from_numpy(np.ascontiguousarray(p32[a])).cuda() for a in range(3))
-    m = torch.from_numpy(m32).cuda()
-    ctx = rv.Context(n, theta=th, eps_star=eps, n_leaf=32, group=64)
-    ctx.build_tree(x, y, z, m)
-    xs, ts, _ = rv.mlp_samples(ctx, th, eps, 1 << 20, seed=7)
-    net = rv.Mlp(seed=8)
-    losses = net.train(xs, ts, steps=400, batch=8192, lr=2e-3, seed=2)
-    pair_cap = 1 << 29
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    n = d["n"]
+    eps = float(np.float32(d["eps"]))
+    x, y, z = xs
+    m = ms
+    ctx = rv.Context(n, theta=d["theta"], eps_star=eps, n_leaf=d["n_leaf"], group=d["group"], tile=tune["tile"])
+    tg = ics.subsample(n, 2048, seed=17)
+    ad, _ = rv.direct_fp64(d["pos"].astype(np.float32).astype(np.float64),
+                           d["mass"].astype(np.float32).astype(np.float64), eps, tg)
 
-    def step():
+    def p99(o):
+        a = np.stack([u[tg].cpu().numpy() for u in o[:3]]).astype(np.float64)
+        return _p99(_rel_err(a, ad))
+
+    def timed(fn):
+        for _ in range(warmup):
+            o = fn()
+        torch.cuda.synchronize()
+        t = []
+        for k in range(steps):
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            o = fn()
+            e1.record()
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        ctx.sync_status()
+        return float(np.mean(t)), o
+
+    out, net_rows, net = {}, 0, None
+    for th, trec in ((d["theta"], 0.7), (1.0, 0.7)):
         ctx.build_tree(x, y, z, m)
-        return rv.tree_forces_mlp(ctx, net, th, trec, eps, pair_cap=pair_cap)
+        fx, ft, _ = rv.mlp_samples(ctx, th, eps, 1 << 20, seed=7)
+        net = rv.Mlp(seed=8)
+        losses = net.train(fx, ft, steps=400, batch=8192, lr=2e-3, seed=2)
+        del fx, ft
 
-    for _ in range(max(3, args.warmup)):
-        out = step()
-    torch.cuda.synchronize()
-    ms = []
-    for k in range(args.steps):
-        flush.fill_(k & 255)
+        def learned_pass():
+            ctx.build_tree(x, y, z, m)
+            return rv.tree_forces_mlp(ctx, net, th, trec, eps, pair_cap=1 << 28)
+
+        def plain_pass():
+            ctx.build_tree(x, y, z, m)
+            return ctx.tree_forces(theta=th, eps_star=eps)
+
+        t_l, o_l = timed(learned_pass)
+        npairs = int(o_l[5].item())
+        net_rows = max(net_rows, npairs)
+        p_l = p99(o_l)
+        del o_l
+        t_p, o_p = timed(plain_pass)
+        p_p = p99(o_p)
+        del o_p
+        out[f"theta_{th}"] = {
+            "plain": {"ms": t_p, "particles_per_s": n / (t_p / 1e3), "p99": p_p, "meets_p99": p_p <= P99_BOUND},
+            "learned": {"ms": t_l, "particles_per_s": n / (t_l / 1e3), "p99": p_l, "meets_p99": p_l <= P99_BOUND,
+                        "theta_rec": trec, "pairs": npairs, "train_loss_first_last": [losses[0], losses[-1]]}}
+    # the network kernel alone (tcgen05, bf16) on as many rows as the largest pair record
+    feats = torch.zeros((max(net_rows, 1), 16), dtype=torch.float32, device="cuda")
+    t_net = []
+    for k in range(4):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        out = step()
-        e1.record()
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    ctx.sync_status()
-    npairs = int(out[5].item())
-    ms_step = float(np.mean(ms))
-    # the network kernel alone, on the recorded pairs
-    t_mlp = []
-    for k in range(3):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        feats = torch.zeros((npairs, 16), dtype=torch.float32, device="cuda")
         e0.record()
         net.forward(feats)
         e1.record()
         e1.synchronize()
-        t_mlp.append(e0.elapsed_time(e1))
-    flop_pair = 2 * (11 * 64 + 64 * 64 + 64 * 3)   # the network's own multiply-adds (padding not counted)
-    mlp_tflops = npairs * flop_pair / (np.median(t_mlp) / 1e3) / 1e12
+        t_net.append(e0.elapsed_time(e1))
+    del feats
+    flop_row = 2 * (11 * 64 + 64 * 64 + 64 * 3)   # the network's own multiply-adds (padding not counted)
+    tflops = net_rows * flop_row / (float(np.median(t_net[1:])) / 1e3) / 1e12
     peaks = _measured_peaks()
-    bf16 = peaks.get("bf16_tflops") or 1900.0
-    tg = ics.subsample(n, 2048, seed=17)
-    ad, _ = rv.direct_fp64(p32.astype(np.float64), m32.astype(np.float64), eps, tg)
-
-    def p99(a):
-        return _p99(_rel_err(np.stack([u.cpu().numpy() for u in a[:3]])[:, tg].astype(np.float64), ad))
-
-    def plain(theta):
-        ctx.build_tree(x, y, z, m)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        o = ctx.tree_forces(theta=theta, eps_star=eps)
-        e1.record()
-        e1.synchronize()
-        return o, e0.elapsed_time(e1)
-
-    o8, t8 = plain(th)
-    o5, t5 = plain(0.5)
-    line = {"metric": METRIC, "value": n / (ms_step / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
-            "config": {"workload": "hernquist_gamma1_n16777216_learned_correction", "n_stars": n, "theta": th,
-                       "theta_rec": trec, "eps_star": eps, "mlp": "11-64-64-3 SiLU, bf16 weights, fp32 accumulate",
-                       "training": "2^20 samples at theta 0.8, 400 Adam steps of 8192",
-                       "step": "build + walk with pair record + network correction"},
-            "p99_rel_err_vs_fp64_direct": p99(out), "train_loss_first_last": [losses[0], losses[-1]],
-            "pairs": npairs,
-            "plain_tree": {"theta_0.8": {"walk_ms": t8, "p99": p99(o8)}, "theta_0.5": {"walk_ms": t5, "p99": p99(o5)}},
-            "roofline": {"bound": "tensor", "kernel": "mlp_forward_tc_k (tcgen05 bf16, on the recorded pairs)",
-                         "achieved": mlp_tflops, "peak": bf16, "unit": "TFLOP/s", "frac": mlp_tflops / bf16,
-                         "traffic": None, "peak_note": "bf16_tflops of MEASURED_PEAKS.json (burst)"}}
-    print(json.dumps(line), flush=True)
-    return 0
+    bf16 = peaks.get("bf16_tflops")
+    roof = {"bound": "tensor", "kernel": "mlp_forward_tc_k (tcgen05, bf16 operands, fp32 accumulate)",
+            "rows": net_rows, "flop_per_row": flop_row, "ms": float(np.median(t_net[1:])), "achieved": tflops,
+            "peak": bf16 or 1900.0, "unit": "TFLOP/s", "frac": tflops / (bf16 or 1900.0), "traffic": None,
+            "peak_note": "bf16_tflops of MEASURED_PEAKS.json (burst)" if bf16 else "fallback 1.9 PFLOP/s bf16"}
+    del ctx
+    torch.cuda.empty_cache()
+    return out, roof
 
 
 def main():
@@ -659,16 +716,16 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="hernquist_bh",
-                    choices=["hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block", "hernquist_binary", "plummer",
-                             "ensemble", "learned"])
+    ap.add_argument("--workload", default="learned",
+                    choices=["learned", "hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block", "hernquist_binary",
+                             "plummer", "ensemble"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the wide (group, leaf, tile) sweep")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction leg")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel of a step (no CUDA graph)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "learned":
-        return run_learned(args)
     return run_gpu(args)
 
 

@@ -25,6 +25,12 @@ def test_reference_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the step time is what ran (a sampled walk), the whole-pass scale is stated
+    sc = d["scale"]
+    assert sc["walk_scale"] >= 1 and sc["build_s"] > 0
+    assert abs(sc["whole_pass_s"] - 4096 / d["value"]) <= 1e-9 * sc["whole_pass_s"]
+    assert d["ms_per_step"] / 1e3 < sc["whole_pass_s"] * sc["walk_scale"]
+    assert d["config"]["n_leaf"] == 16 and d["config"]["walk_group"] == 32
 
 
 def test_bench_error_helpers_match_the_oracle_definitions():
