@@ -437,11 +437,12 @@ rv_status rv_tree_forces_mlp(rv_ctx *ctx, const void *params, float theta, float
  * perturbers from inside its own step or from a host callback, or a host
  * application that forbids device allocation after start-up.)
  *
- * Same result as rv_select_perturbers(mode 1): the indices of the stars
- * whose FP32 squared distance to centre, ((dx*dx + dy*dy) + dz*dz) with every
- * operation rounded once, is below radius*radius (one FP32 product), in
- * ascending order; at most cap indices are written to device idx[cap] and
- * min(total, cap) to device count[1].
+ * Same indices as rv_select_perturbers(mode 1): the stars whose FP32
+ * squared distance to centre, ((dx*dx + dy*dy) + dz*dz) with every operation
+ * rounded once, is below radius*radius (one FP32 product), in ascending
+ * order; the first min(total, cap) of them are written to device idx[cap].
+ * Device count[1] receives the untruncated total: count > cap means the
+ * search was truncated to its first cap indices.
  *
  * Scratch: a fixed 32 KiB device array inside librv (one count per block of
  * 2048 stars), held by every GPU that loads the library until the process
@@ -452,7 +453,11 @@ rv_status rv_tree_forces_mlp(rv_ctx *ctx, const void *params, float theta, float
  * part of the array it uses before reading it, so no clearing is needed, but
  * all calls share the one array: calls whose GPU work overlaps (different
  * streams, or other host threads) race and may return wrong results. x, y, z
- * are device FP32 [n]; centre is a host FP32 point; stream as elsewhere. */
+ * are device FP32 [n]; centre is a host FP32 point; stream as elsewhere.
+ * Returns RV_E_CUDA if one of its own launches fails (an error left by
+ * earlier, unrelated work is neither reported nor cleared). The cached
+ * address does not survive cudaDeviceReset: do not reset a device while this
+ * library is loaded. */
 rv_status rv_select_radius_static(int64_t n, const float *x, const float *y, const float *z,
                                   const float centre[3], float radius, int32_t cap, int32_t *idx,
                                   int32_t *count, void *stream);

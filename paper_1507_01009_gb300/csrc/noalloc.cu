@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(256) static_sel_count_k(int64_t n, const float
     if (threadIdx.x == 0) scratch[blockIdx.x] = total;
 }
 
-// Pass 2: exclusive scan of the block counts; total and the clamped count.
-__global__ void __launch_bounds__(1024) static_sel_scan_k(int nb, int cap, int *scratch, int *count) {
+// Pass 2: exclusive scan of the block counts; the total goes to scratch and to
+// *count (untruncated: a total above cap tells the caller that only the first
+// cap indices were written).
+__global__ void __launch_bounds__(1024) static_sel_scan_k(int nb, int *scratch, int *count) {
     __shared__ int sw[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int carry = 0;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(1024) static_sel_scan_k(int nb, int cap, int *
     }
     if (threadIdx.x == 0) {
         scratch[kStaticSelMaxBlocks] = carry;
-        *count = carry < cap ? carry : cap;
+        *count = carry;
     }
 }
 
@@ -162,11 +164,23 @@ extern "C" rv_status rv_select_radius_static(int64_t n, const float *x, const fl
     rv_status st = scratch_address(&scratch);
     if (st != RV_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const float3 c = make_float3(centre[0], centre[1], centre[2]);
-    const float r2 = radius * radius;  // one FP32 product
-    const int nb = (int)((n + kStaticSelChunk - 1) / kStaticSelChunk);
-    if (nb > 0) static_sel_count_k<<<nb, 256, 0, s>>>(n, x, y, z, c, r2, scratch);
-    static_sel_scan_k<<<1, 1024, 0, s>>>(nb, cap, scratch, count);
-    if (nb > 0) static_sel_write_k<<<nb, 256, 0, s>>>(n, x, y, z, c, r2, cap, scratch, idx);
-    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+    float3 c = make_float3(centre[0], centre[1], centre[2]);
+    float r2 = radius * radius;  // one FP32 product
+    int nb = (int)((n + kStaticSelChunk - 1) / kStaticSelChunk);
+    // each launch's own status (cudaLaunchKernel returns it), so that an error
+    // left by unrelated earlier work is neither reported nor cleared here
+    cudaError_t e = cudaSuccess;
+    if (nb > 0) {
+        void *a[] = {&n, &x, &y, &z, &c, &r2, &scratch};
+        e = cudaLaunchKernel((const void *)static_sel_count_k, dim3(nb), dim3(256), a, 0, s);
+    }
+    if (e == cudaSuccess) {
+        void *a[] = {&nb, &scratch, &count};
+        e = cudaLaunchKernel((const void *)static_sel_scan_k, dim3(1), dim3(1024), a, 0, s);
+    }
+    if (e == cudaSuccess && nb > 0) {
+        void *a[] = {&n, &x, &y, &z, &c, &r2, &cap, &scratch, &idx};
+        e = cudaLaunchKernel((const void *)static_sel_write_k, dim3(nb), dim3(256), a, 0, s);
+    }
+    return e == cudaSuccess ? RV_OK : RV_E_CUDA;
 }

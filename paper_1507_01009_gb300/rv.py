@@ -187,7 +187,8 @@ def select_radius_static(x, y, z, centre, radius, cap=5000, idx=None, count=None
     device allocation inside librv (its scratch is a fixed array in the
     library). ``idx`` (int32 [cap]) and ``count`` (int32 [1]) may be passed in
     by a caller that must not allocate either; otherwise they are created here.
-    Returns (idx, count)."""
+    Returns (idx, count); count holds the untruncated total (above cap: only
+    the first cap indices were written)."""
     import torch
     _need_cuda(x, y, z, idx, count)
     if idx is None:

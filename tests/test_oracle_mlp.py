@@ -17,6 +17,50 @@ def test_bf16_round_hand_values():
     assert abs(r[4] / 3.0e38 - 1) < 2 ** -8
 
 
+def _round8(v):
+    """Nearest value with 8 significant bits (bfloat16's), ties to even,
+    written from frexp: an implementation independent of oracle.bf16_round."""
+    import math
+    m, e = math.frexp(v)                 # v = m 2^e, 0.5 <= |m| < 1
+    q = m * 256.0                        # 8 significant bits
+    fl = math.floor(q)
+    r = fl + 1 if (q - fl > 0.5 or (q - fl == 0.5 and fl % 2 == 1)) else fl
+    return math.ldexp(r / 256.0, e)
+
+
+def test_mlp_forward_rounding_points_one_row_by_hand():
+    """One row through a network whose only nonzero path is x0 -> h1_0 -> h2_0
+    -> y0: the input and the weights 1 + 2^-9 round to 1 in bfloat16, and the
+    hidden activations silu(1) and silu(2 h1 + b) are rounded to 8 significant
+    bits (b = -1.4609375 + 2^-5 puts the second layer's input near 0, where the
+    first rounding is not hidden by the second), so y0 = r(silu(2 r(silu(1)) +
+    b)) + 1/4 exactly; every other output is its bias. Without the roundings
+    the same row gives the plain FP64 value."""
+    import math
+    p = {k: np.zeros(v) for k, v in (("W1", (16, 64)), ("b1", 64), ("W2", (64, 64)), ("b2", 64), ("W3", (64, 8)),
+                                     ("b3", 8))}
+    a = 1 + 2 ** -9
+    p["W1"][0, 0] = a
+    p["W2"][0, 0] = 2.0
+    b = -1.4609375 + 2 ** -5
+    p["b2"][0] = b
+    p["W3"][0, 0] = a
+    p["b3"][:3] = [0.25, -0.5, 0.125]
+    X = np.zeros((1, 16))
+    X[0, 0] = a
+    silu = lambda z: z / (1.0 + math.exp(-z))
+    h1 = _round8(silu(1.0))
+    h2 = _round8(silu(2.0 * h1 + b))
+    y, _ = oracle.mlp_forward(p, X, rounding=True)
+    assert h1 != silu(1.0) and h2 != silu(2.0 * h1 + b)        # both roundings change the value
+    assert _round8(silu(2.0 * silu(1.0) + b)) != h2             # and the first is visible after the second
+    # the other hidden units are silu(0) = 0 and add nothing
+    np.testing.assert_array_equal(y[0], [h2 + 0.25, -0.5, 0.125])
+    y0, _ = oracle.mlp_forward(p, X, rounding=False)
+    z1 = a * a
+    np.testing.assert_allclose(y0[0], [silu(2.0 * silu(z1) + b) * a + 0.25, -0.5, 0.125], rtol=1e-14)
+
+
 def _params(seed):
     g = ics.rng(seed)
     p = {"W1": g.normal(0, 0.3, (16, 64)), "b1": g.normal(0, 0.1, 64), "W2": g.normal(0, 0.15, (64, 64)),

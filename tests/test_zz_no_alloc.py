@@ -50,6 +50,45 @@ def test_static_radius_search_matches_allocating_search():
         np.testing.assert_array_equal(idx[:k].cpu().numpy(), ref_idx[:k].cpu().numpy())
 
 
+def _static(L, x, y, z, n, centre, radius, cap):
+    import torch
+    idx = torch.full((max(cap, 1),), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    c3 = (C.c_float * 3)(*centre)
+    st = L.rv_select_radius_static(n, C.c_void_p(x.data_ptr() if x is not None else 0),
+                                   C.c_void_p(y.data_ptr() if y is not None else 0),
+                                   C.c_void_p(z.data_ptr() if z is not None else 0), c3, float(radius), cap,
+                                   C.c_void_p(idx.data_ptr()), C.c_void_p(cnt.data_ptr()),
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    return st, idx, int(cnt.item())
+
+
+def test_static_radius_search_truncation_is_visible():
+    """A sphere holding more stars than cap: the first cap indices match the
+    allocating search's, and count carries the untruncated total so the
+    caller sees the truncation. Then an empty input gives count 0."""
+    import torch
+    from paper_1507_01009_gb300 import rv
+    L = rv.load()
+    n = 50000
+    p32 = _stars(n, 13)
+    x, y, z = (torch.from_numpy(np.ascontiguousarray(p32[a])).cuda() for a in range(3))
+    ctx = rv.Context(n)
+    centre, radius = (0.0, 0.0, 0.0), 0.3
+    full_idx, full_cnt = ctx.select_perturbers(x, y, z, centre, 1, radius=radius, cap=n)
+    ctx.sync_status()
+    total = int(full_cnt.item())
+    cap = 100
+    assert total > 4 * cap
+    st, idx, cnt = _static(L, x, y, z, n, centre, radius, cap)
+    assert st == rv.RV_OK and cnt == total
+    np.testing.assert_array_equal(idx[:cap].cpu().numpy(), full_idx[:cap].cpu().numpy())
+    st, idx, cnt = _static(L, None, None, None, 0, centre, radius, cap)
+    assert st == rv.RV_OK and cnt == 0
+    assert (idx.cpu().numpy() == -1).all()
+
+
 def test_static_radius_search_rejects_too_many_stars():
     import torch
     from paper_1507_01009_gb300 import rv
