@@ -596,3 +596,40 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         vh = v / (1 - b2 ** t)
         params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
     return params
+
+
+# ---------------------------------------------------------------------------
+# Training loop of the network (not in the paper): seeded minibatches + Adam
+# ---------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x):
+    """SplitMix64 output for the counter value x (Steele, Lea & Flood 2014):
+    z = x + 0x9E3779B97F4A7C15, then two xor-shift-multiply rounds and a final
+    xor-shift, all modulo 2^64 (Python integers)."""
+    z = (int(x) + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def minibatch_rows(seed, step, batch, n):
+    """Rows of minibatch `step`: row i is floor(h n / 2^64) with
+    h = splitmix64(seed + step * batch + i) (64-bit wrap-around)."""
+    return np.array([(splitmix64((int(seed) + int(step) * int(batch) + i) & _M64) * int(n)) >> 64
+                     for i in range(batch)], dtype=np.int64)
+
+
+def mlp_train(params, X, T, steps, batch, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, seed=0, rounding=True):
+    """Adam on minibatches drawn by minibatch_rows: for each step the loss and
+    analytic gradient of mlp_loss_grad on the drawn rows, then adam_step.
+    Returns (losses, params) with params updated (FP64)."""
+    state, losses = {}, []
+    params = {k: np.array(v, dtype=np.float64) for k, v in params.items()}
+    for k in range(steps):
+        rows = minibatch_rows(seed, k, batch, X.shape[0])
+        loss, g = mlp_loss_grad(params, X[rows], T[rows], rounding)
+        losses.append(loss)
+        params = adam_step(params, g, state, lr, b1, b2, eps)
+    return losses, params

@@ -122,3 +122,39 @@ def test_cell_residual_special_cases():
     assert res[0] / res[1] > 12.0   # octupole ~ (s/r)^5 relative scaling of the force: ~32x per doubling
     f, norm = oracle.cell_features(T, big, com + np.array([4 * s, 0.0, 0.0]), 0.0)
     assert abs(np.linalg.norm(f[:3]) - 1) < 1e-12 and abs(f[3] - 0.25) < 1e-12 and f[4] == 0.0
+
+
+def test_splitmix64_published_outputs():
+    """The first outputs of SplitMix64 from state 0 (state advancing by the
+    golden-ratio increment), as published with the generator."""
+    g = 0x9E3779B97F4A7C15
+    assert oracle.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(g) == 0x6E789E6AA1B965F4
+    assert oracle.splitmix64((2 * g) % (1 << 64)) == 0x06C45D188009454F
+
+
+def test_minibatch_rows_uniform_and_in_range():
+    """The draw covers 0..n-1 uniformly (chi-square over 16 bins) and is a
+    function of (seed, step, row) only."""
+    n = 1000
+    r = np.concatenate([oracle.minibatch_rows(7, k, 500, n) for k in range(8)])
+    assert r.min() >= 0 and r.max() < n
+    h = np.bincount(r * 16 // n, minlength=16)
+    chi2 = ((h - r.size / 16) ** 2 / (r.size / 16)).sum()
+    assert chi2 < 40.0                                    # 15 degrees of freedom: p ~ 5e-4
+    np.testing.assert_array_equal(oracle.minibatch_rows(7, 3, 500, n), r[1500:2000])
+    assert not np.array_equal(oracle.minibatch_rows(8, 3, 500, n), r[1500:2000])
+
+
+def test_mlp_train_lowers_the_loss_of_a_learnable_target():
+    """Trained on targets a small network of the same shape produces, the
+    loop's loss falls by more than 10x within 300 steps."""
+    tp = _params(41)
+    X = np.zeros((512, 16))
+    X[:, :11] = ics.rng(42).normal(0, 1, (512, 11))
+    T, _ = oracle.mlp_forward(tp, X, rounding=False)
+    start = _params(43)
+    for k in start:
+        start[k] = 0.3 * start[k]
+    losses, _ = oracle.mlp_train(start, X, T, steps=300, batch=64, lr=3e-3, seed=5, rounding=False)
+    assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:5])
