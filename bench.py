@@ -60,7 +60,7 @@ METRIC = "tree-force particles/s on 1 GB300 at p99 rel. force err ≤1e-3 vs FP6
 UNIT = "particles/s"
 FLOP_P2P, FLOP_M2P = 20, 54   # per interaction, counted from the walk kernel's source
 L2_FLUSH_BYTES = 256 << 20
-WALK_PROFILE = os.path.join(ROOT, "profiles", "walk_tree_k_hernquist_n1048576.md")
+WALK_PROFILE = os.path.join(ROOT, "profiles", "walk_tree_k_hernquist_n4194304_theta0.8.md")
 
 
 def _dist():
@@ -71,14 +71,17 @@ def _dist():
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def make_workload(name: str, rank: int = 0) -> dict:
+def make_workload(name: str, rank: int = 0, stars: int | None = None) -> dict:
+    """The workload `name`; `stars` (default workload only) scales its galaxy
+    down, e.g. for a profiler capture of the same kernels on a smaller case."""
     import ics
     base = 1000 * rank
     if name == "learned":
-        w = ics.hernquist(1 << 24, seed=5 + base)
+        ns = int(stars) if stars else 1 << 24
+        w = ics.hernquist(ns, seed=5 + base)
         d = dict(pos=w.pos, vel=w.vel, mass=w.mass, offsets=None, chain_m=None, chain_x=None, chain_v=None,
                  pert_mode=0, pert_radius=0.0, pert_k=0)
-        cfg = {"workload": "hernquist_gamma1_n16777216", "n_stars": 1 << 24}
+        cfg = {"workload": f"hernquist_gamma1_n{ns}", "n_stars": ns}
     elif name in ("hernquist_bh", "hernquist_bh_relmac", "hernquist_bh_block"):
         w = ics.hernquist_bh_workload(1 << 20, seed=2 + base)
         d = dict(pos=w.stars.pos, vel=w.stars.vel, mass=w.stars.mass, offsets=None, chain_m=w.chain.mass,
@@ -269,7 +272,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    d = make_workload(args.workload, 0)
+    d = make_workload(args.workload, 0, args.stars)
     orc = OracleRun(d)
     for i in range(args.warmup):
         orc.step(REF_SAMPLE, seed=100 + i)
@@ -295,8 +298,10 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def _walk_traffic():
-    """dram bytes per walk launch from the committed ncu summary, if it was
+def _walk_traffic(n):
+    """DRAM bytes per walk launch on n stars of the default workload's galaxy
+    from the committed ncu summary (captured on a smaller galaxy of the same
+    kind and scaled by the stars: the traffic grows with them), if it was
     taken on the current walk.cu (else None)."""
     import hashlib
     import re
@@ -308,9 +313,10 @@ def _walk_traffic():
     h = hashlib.sha256(src).hexdigest()[:16]
     m = re.search(r"walk.cu sha256 prefix: `([0-9a-f]+)`", txt)
     t = re.search(r"= \*\*([0-9.]+) MB per launch\*\*", txt)
-    if not m or not t or m.group(1) != h:
+    c = re.search(r"captured stars: `([0-9]+)`", txt)
+    if not m or not t or not c or m.group(1) != h:
         return None
-    return float(t.group(1)) * 1e6
+    return float(t.group(1)) * 1e6 * n / float(c.group(1))
 
 
 def max_over_ranks(ms: float, device=None) -> float:
@@ -385,7 +391,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    d = make_workload(args.workload, rank)
+    d = make_workload(args.workload, rank, args.stars)
     n = d["n"]
     # every step but the block scheme's is captured once as a CUDA graph and replayed
     use_graph = args.workload not in ("hernquist_bh_block",) and not args.no_graph
@@ -401,7 +407,7 @@ def run_gpu(args):
     tuned = autotune.autotune(*xs, ms, grid=autotune.candidates(groups=(d["group"],), leaves=(d["n_leaf"],),
                                                                  tiles=autotune.GRID_TILE), **tkw)
     wide = autotune.autotune(*xs, ms, grid=autotune.candidates(groups=(32, 64), leaves=(8, 16, 24, 32),
-                                                                tiles=(64, 128, 256)), **tkw) if not args.no_sweep else None
+                                                                tiles=(64, 96, 128, 256)), **tkw) if not args.no_sweep else None
     tune = tuned["config"]
     if d["name"] != "learned":
         del xs, ms
@@ -515,9 +521,11 @@ def run_gpu(args):
     achieved = flop / (walk_ms / 1e3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * 2 * 2.07e9 / 1e12   # FP32 lanes x FMA x max SM clock
-    traffic = _walk_traffic() if args.workload == "hernquist_bh" else None
+    traffic = _walk_traffic(n) if d["name"] == "learned" else None
     roofline = {"bound": "alu", "kernel": "walk_tree_k", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": ("dram read + write bytes per launch from the committed ncu capture of the same "
+                                 "walk.cu on the 2^22-star galaxy, scaled by the stars" if traffic else None),
                 "peak_note": f"{sms} SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz (derived, not measured)",
                 "walk_ms": walk_ms, "walk_timing": walk_src, "flop_per_launch": float(flop),
                 "interactions_per_star": float((n_p2p + n_m2p) / max(n, 1)),
@@ -722,6 +730,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the wide (group, leaf, tile) sweep")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction leg")
+    ap.add_argument("--stars", type=int, default=None,
+                    help="stars of the default workload's galaxy (default 2^24), e.g. a smaller case to profile")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel of a step (no CUDA graph)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -411,6 +411,40 @@ rv_status rv_mlp_gradient(const void *params, int64_t n, const float *x, const f
 /* One Adam step (step >= 1) on the master weights; refreshes the copies. */
 rv_status rv_mlp_adam(void *params, const float *grad, int32_t step, float lr, float beta1, float beta2,
                       float adam_eps, void *stream);
+/* Training of the network on device rows in one call: `steps` Adam steps
+ * (Kingma & Ba; Adam step numbers step0, step0 + 1, ...) on minibatches of
+ * `batch` rows drawn with replacement: row i of step k is row
+ * floor(h n / 2^64) of (x, t), h = SplitMix64(seed + k batch + i) (64-bit
+ * wrap-around; SplitMix64 of Steele, Lea & Flood 2014), each step the mean
+ * squared error and its gradient as rv_mlp_gradient computes them. With
+ * fit_box = 1 the feature box becomes the range of all n rows afterwards
+ * (rv_mlp_fit_feature_box). x: device [n][16], 16-byte aligned; t: device
+ * [n][3]. */
+typedef struct {
+    int64_t n;
+    const float *x, *t;
+    int32_t steps, batch;
+    int32_t step0;
+    float lr, beta1, beta2, adam_eps;
+    uint64_t seed;
+    int32_t fit_box;
+} rv_mlp_train_cfg;
+/* Device scratch rv_mlp_train needs for minibatches of `batch` rows (0 if batch < 1). */
+size_t rv_mlp_train_scratch_bytes(int32_t batch);
+/* losses: device FP32 [steps] receiving each step's loss, or NULL. All work is
+ * enqueued on `stream` (no host synchronisation). RV_E_INVAL on bad arguments,
+ * RV_E_WORKSPACE if the scratch is too small. */
+rv_status rv_mlp_train(void *params, const rv_mlp_train_cfg *cfg, float *losses, void *scratch,
+                       size_t scratch_bytes, void *stream);
+/* The network's whole state (master weights, Adam moments, bfloat16 copies,
+ * feature box) to and from a host byte buffer of rv_mlp_state_bytes(): a
+ * 64-byte header (magic "rvmlp", version 1, the layer sizes, the block size)
+ * then the parameter block. Both synchronise `stream`. rv_mlp_load returns
+ * RV_E_INVAL for a buffer that is too small or whose header does not match
+ * this library's network. */
+size_t rv_mlp_state_bytes(void);
+rv_status rv_mlp_save(const void *params, void *host, size_t bytes, void *stream);
+rv_status rv_mlp_load(void *params, const void *host, size_t bytes, void *stream);
 /* Training samples from the last tree: n_samples random stars (SplitMix64 of
  * seed), each paired with a cell chosen uniformly among the cells its own
  * walk accepts at theta (its box: its grid cell). Writes features x[n][16],

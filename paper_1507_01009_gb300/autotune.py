@@ -23,7 +23,7 @@ from . import rv
 
 GRID_GROUP = (64, 32, 16)
 GRID_LEAF = (8, 16, 32, 64)
-GRID_TILE = (32, 64, 128, 256)
+GRID_TILE = (32, 64, 96, 128, 256)
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 _LOCK = threading.Lock()
 

@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <string.h>
 
 #include "rv_internal.cuh"
 
@@ -368,6 +369,23 @@ __global__ void mlp_adam_k(MlpBlock P, const float *grad, int t, float lr, float
         P.m[i] = m;
         P.v[i] = v;
         P.w[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+// Minibatch of training: row i of step k is row idx = floor(h n / 2^64) of
+// (x, t) with h = SplitMix64(seed + k batch + i) (64-bit wrap-around), copied
+// to (bx, bt).
+__global__ void mlp_draw_k(int64_t n, const float *x, const float *t, int batch, unsigned long long seed, long long k,
+                           float *bx, float *bt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch; i += gridDim.x * blockDim.x) {
+        const unsigned long long h = splitmix64(seed + (unsigned long long)k * (unsigned long long)batch + i);
+        const int64_t r = (int64_t)__umul64hi(h, (unsigned long long)n);
+        const float4 *src = reinterpret_cast<const float4 *>(x + r * kInPad);
+        float4 *dst = reinterpret_cast<float4 *>(bx + (int64_t)i * kInPad);
+#pragma unroll
+        for (int c = 0; c < kInPad / 4; c++) dst[c] = src[c];
+#pragma unroll
+        for (int q = 0; q < kOut; q++) bt[(int64_t)i * kOut + q] = t[r * kOut + q];
     }
 }
 
@@ -1010,6 +1028,92 @@ rv_status rv_mlp_adam(void *params, const float *grad, int32_t step, float lr, f
     mlp_adam_k<<<ceil_div(kParams, 256), 256, 0, s>>>(P, grad, step, lr, beta1, beta2, adam_eps);
     mlp_sync_k<<<ceil_div(kBf16, 256), 256, 0, s>>>(P);
     return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+size_t rv_mlp_train_scratch_bytes(int32_t batch) {
+    if (batch < 1) return 0;
+    const size_t rows = sizeof(float) * (size_t)batch * (kInPad + kOut);
+    return ((rows + 255) & ~(size_t)255) + ((sizeof(float) * kParams + 255) & ~(size_t)255) +
+           rv_mlp_scratch_bytes(batch);
+}
+
+rv_status rv_mlp_train(void *params, const rv_mlp_train_cfg *cfg, float *losses, void *scratch,
+                       size_t scratch_bytes, void *stream) {
+    if (!params || !cfg || !scratch) return RV_E_INVAL;
+    const rv_mlp_train_cfg &C = *cfg;
+    if (C.n < 1 || !C.x || !C.t || C.steps < 0 || C.batch < 1 || C.step0 < 1 || !(C.lr >= 0.f) ||
+        !(C.beta1 >= 0.f && C.beta1 < 1.f) || !(C.beta2 >= 0.f && C.beta2 < 1.f) || !(C.adam_eps > 0.f) ||
+        (C.fit_box != 0 && C.fit_box != 1) || (reinterpret_cast<uintptr_t>(C.x) & 15) != 0 ||
+        (int64_t)C.step0 + C.steps > (1ll << 31) - 1)
+        return RV_E_INVAL;
+    if (scratch_bytes < rv_mlp_train_scratch_bytes(C.batch)) return RV_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpBlock P = mlp_block(params);
+    char *base = reinterpret_cast<char *>(scratch);
+    const size_t rows = sizeof(float) * (size_t)C.batch * (kInPad + kOut);
+    float *bx = reinterpret_cast<float *>(base);
+    float *bt = bx + (size_t)C.batch * kInPad;
+    float *grad = reinterpret_cast<float *>(base + ((rows + 255) & ~(size_t)255));
+    char *gscr = base + ((rows + 255) & ~(size_t)255) + ((sizeof(float) * kParams + 255) & ~(size_t)255);
+    const int nblk = (int)((C.batch + 63) / 64);
+    float *partial = reinterpret_cast<float *>(gscr);
+    float *lpart = partial + (int64_t)nblk * kParams;
+    const size_t smem = sizeof(GradSmem);
+    cudaError_t e = cudaFuncSetAttribute(mlp_grad_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return RV_E_CUDA;
+    for (int k = 0; k < C.steps; k++) {
+        mlp_draw_k<<<ceil_div(C.batch, 256), 256, 0, s>>>(C.n, C.x, C.t, C.batch, C.seed, k, bx, bt);
+        mlp_grad_k<<<nblk, 128, smem, s>>>(P, C.batch, bx, bt, partial, lpart);
+        mlp_reduce_k<<<ceil_div(kParams, 256), 256, 0, s>>>(nblk, partial, lpart, grad, losses ? losses + k : nullptr,
+                                                           C.batch);
+        mlp_adam_k<<<ceil_div(kParams, 256), 256, 0, s>>>(P, grad, C.step0 + k, C.lr, C.beta1, C.beta2, C.adam_eps);
+        mlp_sync_k<<<ceil_div(kBf16, 256), 256, 0, s>>>(P);
+    }
+    if (C.fit_box) mlp_box_k<<<1, 512, 0, s>>>(P, C.n, C.x);
+    return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+// Saved network state: a 64-byte header (magic, version, the layout's sizes,
+// the block's byte count), then the parameter block as it is on the device.
+struct MlpStateHeader {
+    char magic[8];
+    uint32_t version, in, in_pad, hid, out, out_pad, params, bf16;
+    uint64_t block_bytes;
+    uint32_t pad[4];
+};
+static_assert(sizeof(MlpStateHeader) == 64, "state header is 64 bytes");
+static MlpStateHeader mlp_header() {
+    MlpStateHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "rvmlp\0\0\0", 8);
+    h.version = 1;
+    h.in = kIn; h.in_pad = kInPad; h.hid = kHid; h.out = kOut; h.out_pad = kOutPad;
+    h.params = kParams; h.bf16 = kBf16; h.block_bytes = kBlockBytes;
+    return h;
+}
+
+size_t rv_mlp_state_bytes(void) { return sizeof(MlpStateHeader) + kBlockBytes; }
+
+rv_status rv_mlp_save(const void *params, void *host, size_t bytes, void *stream) {
+    if (!params || !host || bytes < rv_mlp_state_bytes()) return RV_E_INVAL;
+    const MlpStateHeader h = mlp_header();
+    memcpy(host, &h, sizeof h);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<char *>(host) + sizeof h, params, kBlockBytes,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? RV_OK : RV_E_CUDA;
+}
+
+rv_status rv_mlp_load(void *params, const void *host, size_t bytes, void *stream) {
+    if (!params || !host || bytes < rv_mlp_state_bytes()) return RV_E_INVAL;
+    const MlpStateHeader want = mlp_header();
+    if (memcmp(host, &want, sizeof want) != 0) return RV_E_INVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(params, reinterpret_cast<const char *>(host) + sizeof want, kBlockBytes,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host buffer may be freed after return
+    return e == cudaSuccess ? RV_OK : RV_E_CUDA;
 }
 
 rv_status rv_mlp_samples(rv_ctx *c, float theta, float eps_star, int64_t n_samples, uint64_t seed, float *x,

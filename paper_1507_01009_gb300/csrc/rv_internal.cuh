@@ -20,7 +20,10 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per tile
 constexpr int kTopoBlock = 256;
 constexpr int kScanChunk = 2048;        // elements per scan block
-constexpr int kWalkWarps = 4;           // warps per walk block
+#ifndef RV_WALK_WARPS
+#define RV_WALK_WARPS 1
+#endif
+constexpr int kWalkWarps = RV_WALK_WARPS;  // warps per walk block (each warp walks its own groups)
 constexpr int kMaxGroup = 64;           // stars per walk group (two per lane)
 constexpr int kStackCap = 768;          // walk traversal stack entries per warp
 constexpr int kMaxExtra = 8;            // extra particles through rv_tree_forces

@@ -35,18 +35,26 @@
 #include "rv_internal.cuh"
 
 // Unrolling of the evaluation loops (list pairs in flight per lane, each on
-// two targets; measured on GB300: star pairs 1, cell pairs 3) and the resident
-// blocks per SM the walk kernel is compiled for (register budget: 4 blocks of
-// 128 threads leave 128 registers a thread, enough for two targets' sums and
-// three cell pairs in flight without spills).
+// two targets; measured on GB300: star pairs 1, cell pairs 3) and the
+// register budget of the walk kernel. The kernel runs one warp per block, so
+// the register budget alone sets the resident warps: 104 registers a thread
+// (the running sums live in shared memory) give 18-19 warps per SM, against
+// 16 at 128 registers; 96 registers spill, 112 and 128 were slower
+// (2^24 stars at theta 0.8 and tile 96: 80.9 ms at 104 registers, 84.8 at
+// 112, 84.8 at 128, 88.6 at 96).
 #ifndef RV_P2P_UNROLL
 #define RV_P2P_UNROLL 1
 #endif
 #ifndef RV_M2P_UNROLL
 #define RV_M2P_UNROLL 3
 #endif
-#ifndef RV_WALK_MIN_BLOCKS
-#define RV_WALK_MIN_BLOCKS 4
+#ifndef RV_WALK_MAXNREG
+#define RV_WALK_MAXNREG 104
+#endif
+#ifdef RV_WALK_MIN_BLOCKS
+#define RV_WALK_BOUNDS __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS)
+#else
+#define RV_WALK_BOUNDS __maxnreg__(RV_WALK_MAXNREG)
 #endif
 
 namespace rv {
@@ -102,16 +110,19 @@ struct WalkArgs {
     Spline spl;
 };
 
-// Per-warp shared memory: stack | lane_cell[32] | cell staging | star staging.
-// Cell staging: (tile + 32) / 2 pairs of multipole records, 5 float4 per pair
-// holding (M, cx), (cy, cz), (-Qxx, -Qyy), (-Qzz, -Qxy), (-Qxz, -Qyz) of both
-// entries side by side (cx.. = centre of mass relative to the group centre).
-// Star staging: (tile + 32) / 2 pairs, 2 float4 per pair: (x, y), (z, m).
+// Per-warp shared memory: stack | lane_cell[32] | cell staging | star staging |
+// running sums. Cell staging: (tile + 32) / 2 pairs of multipole records, 5
+// float4 per pair holding (M, cx), (cy, cz), (-Qxx, -Qyy), (-Qzz, -Qxy),
+// (-Qxz, -Qyz) of both entries side by side (cx.. = centre of mass relative
+// to the group centre). Star staging: (tile + 32) / 2 pairs, 2 float4 per
+// pair: (x, y), (z, m). Running sums: 16 floats per lane (AccSm).
 constexpr int kCellPairF4 = 5, kStarPairF4 = 2;
+constexpr int kAccWords = 16 * 32;
 constexpr int kP2PUnroll = RV_P2P_UNROLL, kM2PUnroll = RV_M2P_UNROLL;
-__host__ __device__ inline size_t warp_smem_bytes(int tile) {
+__host__ __device__ inline size_t warp_staging_bytes(int tile) {
     return (size_t)kStackCap * 4 + 32 * 4 + (size_t)(tile + 32) / 2 * 16 * (kCellPairF4 + kStarPairF4);
 }
+__host__ __device__ inline size_t warp_smem_bytes(int tile) { return warp_staging_bytes(tile) + 4 * kAccWords; }
 
 // The tree of one member as the walk sees it.
 struct TreeGeo {
@@ -186,11 +197,24 @@ struct Tgt {
     int j0, k;
 };
 
-__device__ __forceinline__ void add_tile(Acc &A, f2 tx, f2 ty, f2 tz, f2 tp) {
-    nadd(A.ax, A.cx, f2_sum(tx));
-    nadd(A.ay, A.cy, f2_sum(ty));
-    nadd(A.az, A.cz, f2_sum(tz));
-    nadd(A.ph, A.cp, -f2_sum(tp));
+// A lane's running sums for its two targets, kept in the warp's shared
+// memory (not registers, which the evaluation loops need): for target q,
+// field k = ax, ay, az, ph, then their Neumaier compensations (k + 4), at
+// word (q * 8 + k) * 32 + lane, so the 32 lanes touch 32 consecutive words.
+struct AccSm {
+    float *p;   // the warp's region + lane
+    __device__ __forceinline__ float &f(int q, int k) const { return p[(q * 8 + k) * 32]; }
+};
+
+__device__ __forceinline__ void add_tile(const AccSm &A, int q, f2 tx, f2 ty, f2 tz, f2 tp) {
+    const float v[4] = {f2_sum(tx), f2_sum(ty), f2_sum(tz), -f2_sum(tp)};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float sum = A.f(q, k), comp = A.f(q, k + 4);
+        nadd(sum, comp, v[k]);
+        A.f(q, k) = sum;
+        A.f(q, k + 4) = comp;
+    }
 }
 
 // Spline softening (the "spline" option of Sect. 2): the point mass smoothed
@@ -248,7 +272,7 @@ __device__ __forceinline__ void spline_pair(f2 r2, f2 m2, const Spline &S, f2 &m
 // (SPL: the spline field instead).
 template <bool SOFT, bool SPL>
 __device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt &t, f2 eps2, const Spline &S,
-                                         Acc *A) {
+                                         const AccSm &A) {
     f2 tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0}, tp[2] = {0, 0};   // tp sums +m/r
 #pragma unroll kP2PUnroll
     for (int j = t.j0; j < npair; j += t.k) {
@@ -273,8 +297,8 @@ __device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt
             tp[q] = f2_add(tp[q], mr);
         }
     }
-    add_tile(A[0], tx[0], ty[0], tz[0], tp[0]);
-    add_tile(A[1], tx[1], ty[1], tz[1], tp[1]);
+    add_tile(A, 0, tx[0], ty[0], tz[0], tp[0]);
+    add_tile(A, 1, tx[1], ty[1], tz[1], tp[1]);
 }
 
 // Cell pairs 0 .. npair-1 of a staged cell list on this lane's targets. With
@@ -286,7 +310,7 @@ __device__ __forceinline__ void eval_p2p(const float4 *src, int npair, const Tgt
 // monopole.
 template <bool QUAD, bool SPL>
 __device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt &t, f2 eps2, const Spline &S,
-                                         Acc *A) {
+                                         const AccSm &A) {
     f2 tx[2] = {0, 0}, ty[2] = {0, 0}, tz[2] = {0, 0}, tp[2] = {0, 0};   // tp sums +(M - s/2)/rho
     if (SPL) eps2 = 0;
 #pragma unroll kM2PUnroll
@@ -381,8 +405,8 @@ __device__ __forceinline__ void eval_m2p(const float4 *src, int npair, const Tgt
             }
         }
     }
-    add_tile(A[0], tx[0], ty[0], tz[0], tp[0]);
-    add_tile(A[1], tx[1], ty[1], tz[1], tp[1]);
+    add_tile(A, 0, tx[0], ty[0], tz[0], tp[0]);
+    add_tile(A, 1, tx[1], ty[1], tz[1], tp[1]);
 }
 
 // Field f of staged entry e in a pair-interleaved list whose pairs are
@@ -422,7 +446,7 @@ __device__ __forceinline__ int gap1(int blo, int bhi, int clo, int chi) {
 template <bool SOFT, bool QUAD, bool REC, bool REL, bool SPL>
 __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, const unsigned long long *thr,
                                            const unsigned long long *thr_rec, int gid, char *wsm, const int blo[3],
-                                           const int bhi[3], const float g[3], const Tgt &tg, f2 eps2, Acc *acc,
+                                           const int bhi[3], const float g[3], const Tgt &tg, f2 eps2, const AccSm &acc,
                                            unsigned long long &np2p, unsigned long long &nm2p, float K) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
@@ -611,17 +635,10 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
 
 // Lane l serves target pair t = l % p (stars 2t and 2t + 1) with share
 // l / p; the k lanes t, t + p, ..., t + (k - 1) p of a pair add their partial
-// totals in that order through the warp's (now free) staging memory. Returns
-// the totals of stars `lane` and `lane + 32`.
-__device__ __forceinline__ void combine_shares(const Acc *acc, int s, int p, int k, float *scr, Acc out[2]) {
+// totals in that order, read from the warp's running sums (AccSm). Returns the
+// totals of stars `lane` and `lane + 32`.
+__device__ __forceinline__ void combine_shares(const float *accw, int s, int p, int k, Acc out[2]) {
     const int lane = threadIdx.x & 31;
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-        float *d = scr + 8 * (2 * lane + q);
-        d[0] = acc[q].ax; d[1] = acc[q].ay; d[2] = acc[q].az; d[3] = acc[q].ph;
-        d[4] = acc[q].cx; d[5] = acc[q].cy; d[6] = acc[q].cz; d[7] = acc[q].cp;
-    }
     __syncwarp();
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -629,10 +646,10 @@ __device__ __forceinline__ void combine_shares(const Acc *acc, int s, int p, int
         Acc o = {};
         if (i < s)
             for (int m = 0; m < k; m++) {
-                const float *e = scr + 8 * (2 * ((i >> 1) + m * p) + (i & 1));
-                nadd(o.ax, o.cx, e[0]); nadd(o.ay, o.cy, e[1]);
-                nadd(o.az, o.cz, e[2]); nadd(o.ph, o.cp, e[3]);
-                o.cx += e[4]; o.cy += e[5]; o.cz += e[6]; o.cp += e[7];
+                const float *e = accw + (i & 1) * 8 * 32 + (i >> 1) + m * p;
+                nadd(o.ax, o.cx, e[0]); nadd(o.ay, o.cy, e[32]);
+                nadd(o.az, o.cz, e[64]); nadd(o.ph, o.cp, e[96]);
+                o.cx += e[128]; o.cy += e[160]; o.cz += e[192]; o.cp += e[224];
             }
         out[h] = o;
     }
@@ -687,7 +704,7 @@ __device__ __forceinline__ void extra_terms(const WalkArgs &A, float xi, float y
 // is their own grid cell [q, q+1)^3, q = floor((x - min) 2^21 / L) limited
 // to +-2^23); the tree's groups follow.
 template <bool SOFT, bool QUAD, bool REC, bool REL, bool SPL>
-__global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree_k(WalkArgs A) {
+__global__ void RV_WALK_BOUNDS walk_tree_k(WalkArgs A) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // per-level opening thresholds in shared memory: lanes of a warp test cells
@@ -705,9 +722,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         if (lane == 0) gi = atomicAdd(&A.st->next_group, 1);
         gi = __shfl_sync(0xffffffffu, gi, 0);
         if (gi >= nitem) break;
-        Acc acc[2] = {};
+        float *accw = reinterpret_cast<float *>(wsm + warp_staging_bytes(A.tile));
+        const AccSm acc{accw + lane};
+#pragma unroll
+        for (int k = 0; k < 16; k++) accw[32 * k + lane] = 0.f;
+        __syncwarp();
         unsigned long long a2 = 0, a3 = 0;
-        float *scr = reinterpret_cast<float *>(wsm + kStackCap * 4 + 32 * 4);  // m2p staging, free after a walk
         if (gi < A.n_extra) {
             // ---- a particle outside the tree: all 32 lanes share its interaction list
             // (both target slots hold it; the second slot's sums are not used)
@@ -743,7 +763,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
                 continue;
             }
             Acc tots[2];
-            combine_shares(acc, 1, 1, 32, scr, tots);
+            combine_shares(accw, 1, 1, 32, tots);
             Acc &tot = tots[0];
             if (lane == 0) {
                 extra_terms(A, xi, yi, zi, ek, kx, mk, tot);
@@ -812,7 +832,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, RV_WALK_MIN_BLOCKS) walk_tree
         np2p += a2 * (unsigned long long)s;
         nm2p += a3 * (unsigned long long)s;
         Acc tots[2];
-        combine_shares(acc, s, p, k, scr, tots);
+        combine_shares(accw, s, p, k, tots);
         const float cost = (float)a2 + 2.5f * (float)a3;   // list pairs, a cell costing ~2.5 stars
 #pragma unroll
         for (int h = 0; h < 2; h++) {

@@ -31,7 +31,8 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_profile_walk", "rv_walk_time", "rv_launch_count", "rv_last_error", "rv_mlp_param_bytes",
            "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
            "rv_mlp_samples", "rv_tree_forces_mlp", "rv_wait_selftest", "rv_mlp_fit_feature_box",
-           "rv_mlp_set_feature_box", "rv_direct_fp64_scratch_bytes", "rv_direct_fp64"]
+           "rv_mlp_set_feature_box", "rv_direct_fp64_scratch_bytes", "rv_direct_fp64", "rv_mlp_train_scratch_bytes",
+           "rv_mlp_train", "rv_mlp_state_bytes", "rv_mlp_save", "rv_mlp_load"]
 
 
 class RvError(RuntimeError):
@@ -56,6 +57,12 @@ class rv_tree_view(C.Structure):
     _fields_ = [("n", C.c_int64), ("ncell", C.c_int64), ("ngroup", C.c_int64), ("keys", C.c_void_p),
                 ("perm", C.c_void_p), ("pos", C.c_void_p), ("cbox", C.c_void_p), ("clink", C.c_void_p),
                 ("cmom", C.c_void_p), ("cparent", C.c_void_p), ("groups", C.c_void_p), ("bounds", C.c_void_p)]
+
+
+class rv_mlp_train_cfg(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("t", C.c_void_p), ("steps", C.c_int32), ("batch", C.c_int32),
+                ("step0", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("adam_eps", C.c_float), ("seed", C.c_uint64), ("fit_box", C.c_int32)]
 
 
 class rv_system(C.Structure):
@@ -140,6 +147,13 @@ def _declare(L):
     L.rv_direct_fp64_scratch_bytes.argtypes = [i64]
     L.rv_direct_fp64_scratch_bytes.restype = C.c_size_t
     L.rv_direct_fp64.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
+    L.rv_mlp_train_scratch_bytes.argtypes = [i32]
+    L.rv_mlp_train_scratch_bytes.restype = C.c_size_t
+    L.rv_mlp_train.argtypes = [vp, C.POINTER(rv_mlp_train_cfg), vp, vp, C.c_size_t, vp]
+    L.rv_mlp_state_bytes.argtypes = []
+    L.rv_mlp_state_bytes.restype = C.c_size_t
+    L.rv_mlp_save.argtypes = [vp, vp, C.c_size_t, vp]
+    L.rv_mlp_load.argtypes = [vp, vp, C.c_size_t, vp]
     L.rv_launch_count.argtypes = [vp]
     L.rv_launch_count.restype = C.c_int64
     L.rv_last_error.argtypes = [vp]
@@ -147,7 +161,8 @@ def _declare(L):
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("rv_default_config", "rv_workspace_size", "rv_destroy", "rv_last_error", "rv_launch_count",
-                        "rv_mlp_param_bytes", "rv_mlp_scratch_bytes", "rv_direct_fp64_scratch_bytes"):
+                        "rv_mlp_param_bytes", "rv_mlp_scratch_bytes", "rv_direct_fp64_scratch_bytes",
+                        "rv_mlp_train_scratch_bytes", "rv_mlp_state_bytes"):
             f.restype = C.c_int
 
 
@@ -626,20 +641,45 @@ class Mlp:
         box = self.block[-4 * 32:].view(torch_float32()).cpu().numpy()
         return box[:16].copy(), box[16:].copy()
 
-    def train(self, x, t, steps, batch=4096, lr=1e-3, seed=0, stream=None):
-        """Adam on minibatches drawn in a seeded order; returns the losses. The
-        feature box becomes the range of the training rows x."""
+    def train(self, x, t, steps, batch=4096, lr=1e-3, seed=0, b1=0.9, b2=0.999, eps=1e-8, fit_box=True,
+              stream=None):
+        """rv_mlp_train: `steps` Adam steps on SplitMix64-drawn minibatches of
+        (x [n,16], t [n,3]), all on the device in one call; returns the
+        per-step losses. With fit_box the feature box becomes the range of x."""
         import torch
-        g = torch.Generator(device="cpu").manual_seed(int(seed))
-        n = int(x.shape[0])
-        losses = []
-        for k in range(steps):
-            idx = torch.randint(0, n, (batch,), generator=g).to(x.device)
-            grad, loss = self.gradient(x[idx].contiguous(), t[idx].contiguous(), stream)
-            self.adam(grad, lr=lr, stream=stream)
-            losses.append(loss)
-        self.fit_feature_box(x, stream)
-        return [float(l.item()) for l in losses]
+        x = x.contiguous()
+        t = t.contiguous()
+        need = int(self.L.rv_mlp_train_scratch_bytes(int(batch)))
+        scratch = torch.empty(max(need, 1), dtype=torch.uint8, device=x.device)
+        losses = torch.empty(max(int(steps), 1), dtype=torch.float32, device=x.device)
+        cfg = rv_mlp_train_cfg(n=int(x.shape[0]), x=_ptr(x), t=_ptr(t), steps=int(steps), batch=int(batch),
+                               step0=self.step + 1, lr=float(lr), beta1=float(b1), beta2=float(b2),
+                               adam_eps=float(eps), seed=int(seed), fit_box=int(bool(fit_box)))
+        st = self.L.rv_mlp_train(_ptr(self.block), C.byref(cfg), _ptr(losses), _ptr(scratch), need,
+                                 _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_train")
+        self.step += int(steps)
+        return [float(v) for v in losses[:int(steps)].cpu().tolist()]
+
+    def save(self, stream=None) -> bytes:
+        """rv_mlp_save: the whole network state as bytes."""
+        n = int(self.L.rv_mlp_state_bytes())
+        buf = (C.c_char * n)()
+        st = self.L.rv_mlp_save(_ptr(self.block), C.cast(buf, C.c_void_p), n, _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_save")
+        return bytes(buf)
+
+    def load(self, state: bytes, step=None, stream=None):
+        """rv_mlp_load: restores a state from save(); `step` sets the Adam step
+        count the next training continues from."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        st = self.L.rv_mlp_load(_ptr(self.block), C.cast(buf, C.c_void_p), len(state), _stream(stream))
+        if st != RV_OK:
+            raise RvError(st, "rv_mlp_load")
+        if step is not None:
+            self.step = int(step)
 
 
 def torch_float32():

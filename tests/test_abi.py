@@ -95,3 +95,29 @@ def test_new_entry_points_reject_bad_arguments(lib):
     assert lib.rv_mlp_set_feature_box(None, lo, hi, None) == rv.RV_E_INVAL
     assert lib.rv_wait_selftest(-1, 0, None, None) == rv.RV_E_INVAL
     assert lib.rv_wait_selftest(10, 2, None, None) == rv.RV_E_INVAL
+
+
+def test_training_and_state_entry_points_reject_bad_arguments(lib):
+    """rv_mlp_train, rv_mlp_save and rv_mlp_load check their arguments (and a
+    saved state's header) before any device work."""
+    from paper_1507_01009_gb300 import rv
+    assert lib.rv_mlp_train_scratch_bytes(0) == 0
+    assert lib.rv_mlp_train_scratch_bytes(64) > lib.rv_mlp_scratch_bytes(64)
+    n = int(lib.rv_mlp_state_bytes())
+    assert n == 64 + int(lib.rv_mlp_param_bytes())
+    fake = C.c_void_p(1 << 20)        # never dereferenced: every call below fails its checks first
+    cfg = rv.rv_mlp_train_cfg(n=100, x=C.c_void_p(1 << 20), t=C.c_void_p(1 << 21), steps=10, batch=32, step0=1,
+                              lr=1e-3, beta1=0.9, beta2=0.999, adam_eps=1e-8, seed=1, fit_box=1)
+    need = lib.rv_mlp_train_scratch_bytes(32)
+    assert lib.rv_mlp_train(None, C.byref(cfg), None, fake, need, None) == rv.RV_E_INVAL
+    assert lib.rv_mlp_train(fake, None, None, fake, need, None) == rv.RV_E_INVAL
+    assert lib.rv_mlp_train(fake, C.byref(cfg), None, fake, need - 1, None) == rv.RV_E_WORKSPACE
+    for field, bad in (("step0", 0), ("batch", 0), ("n", 0), ("beta1", 1.0), ("adam_eps", 0.0), ("fit_box", 2),
+                       ("x", C.c_void_p((1 << 20) + 4))):
+        b = rv.rv_mlp_train_cfg.from_buffer_copy(cfg)
+        setattr(b, field, bad)
+        assert lib.rv_mlp_train(fake, C.byref(b), None, fake, need, None) == rv.RV_E_INVAL, field
+    buf = (C.c_char * n)()
+    assert lib.rv_mlp_save(fake, buf, n - 1, None) == rv.RV_E_INVAL
+    assert lib.rv_mlp_load(fake, buf, n, None) == rv.RV_E_INVAL            # zero header: not a saved state
+    assert lib.rv_mlp_load(None, buf, n, None) == rv.RV_E_INVAL
