@@ -81,6 +81,8 @@ def _declare(L):
     L.orc_influence.argtypes = [C.c_int64, _f, _f, _f, _f, _f, _f, _f, _f, C.c_double, C.c_int64, _d]
     L.orc_tidal.argtypes = [C.c_int64, _f, _f, _f, _f, _f, C.c_float, C.c_float, C.c_float, C.c_int64, _i64]
     L.orc_tidal.restype = C.c_int64
+    L.orc_absorb.argtypes = [C.c_int64, _f, _f, _f, C.c_int32, _d, _d, C.c_int64, _i64, _d]
+    L.orc_absorb.restype = C.c_int64
 
 
 def _p(a, ty):
@@ -360,6 +362,75 @@ def tidal(pos32, mass32, centre32, mchain32, gamma, rcrit):
     got = lib().orc_tidal(n, _p(x, _f), _p(y, _f), _p(z, _f), _p(m, _f), _p(c, _f), np.float32(mchain32),
                           np.float32(gamma), np.float32(rcrit), n, _p(out, _i64))
     return out[:got]
+
+
+def absorb(pos32, chain_mass, chain_pos):
+    """Eq. 4: indices (ascending) of the stars closer to the chain's centre of
+    mass than the chain radius (its largest member distance), decided in FP64
+    on squared distances (see orc_absorb). Returns (idx, r_chain)."""
+    x, y, z = (_c(pos32[a], np.float32) for a in range(3))
+    cm = _c(chain_mass, np.float64)
+    cx = _c(chain_pos, np.float64).reshape(-1)
+    n = x.shape[0]
+    out = np.zeros(max(n, 1), dtype=np.int64)
+    o2 = np.zeros(2)
+    got = lib().orc_absorb(n, _p(x, _f), _p(y, _f), _p(z, _f), cm.shape[0], _p(cm, _d), _p(cx, _d), n, _p(out, _i64),
+                           _p(o2, _d))
+    return out[:got], float(o2[0])
+
+
+def chain_escape(mass, pos, vel, massive, designated, r_chain0, gamma, n_absorbing):
+    """Escape from the chain (Eq. 5) and the membership rules around it
+    (Sect. 2, Sect. 3), FP64 on the members in index order:
+      - c, v_c: the members' centre-of-mass position and velocity;
+      - member k recedes if (d . u) > 0 with d = x_k - c, u = v_k - v_c, summed
+        (d_x u_x + d_y u_y) + d_z u_z, and escapes if also
+        (d_x d_x + d_y d_y) + d_z d_z > r_esc^2, r_esc = gamma r_chain0 (Eq. 5);
+      - absorption goes first: while perturbers are being absorbed
+        (n_absorbing > 0) escapes wait, unless the chain radius (largest member
+        distance) exceeds the escape radius by more than 5 %;
+      - the chain ends if fewer than 2 members remain, or if the designated
+        massive member escapes and no other massive member remains; if another
+        does, the most massive remaining massive member (lowest index on ties)
+        becomes the designated one.
+    Returns dict escape (bool array), terminate, designated, r_chain, r_escape."""
+    m = np.asarray(mass, np.float64)
+    x = np.asarray(pos, np.float64).reshape(-1, 3)
+    v = np.asarray(vel, np.float64).reshape(-1, 3)
+    k = m.shape[0]
+    M = 0.0
+    c = [0.0, 0.0, 0.0]
+    vc = [0.0, 0.0, 0.0]
+    for i in range(k):
+        M += m[i]
+        for a in range(3):
+            c[a] += m[i] * x[i, a]
+            vc[a] += m[i] * v[i, a]
+    for a in range(3):
+        c[a] = c[a] / M if M > 0 else 0.0
+        vc[a] = vc[a] / M if M > 0 else 0.0
+    r_esc = gamma * r_chain0
+    re2 = r_esc * r_esc
+    rc2 = 0.0
+    cand = np.zeros(k, dtype=bool)
+    for i in range(k):
+        d = [x[i, a] - c[a] for a in range(3)]
+        u = [v[i, a] - vc[a] for a in range(3)]
+        d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+        du = (d[0] * u[0] + d[1] * u[1]) + d[2] * u[2]
+        rc2 = max(rc2, d2)
+        cand[i] = d2 > re2 and du > 0.0
+    grown = 1.05 * r_esc
+    esc = cand if (n_absorbing <= 0 or rc2 > grown * grown) else np.zeros(k, dtype=bool)
+    terminate = int(k - int(esc.sum()) < 2)
+    des = int(designated)
+    if esc[des]:
+        rest = [i for i in range(k) if massive[i] and not esc[i]]
+        if rest:
+            des = max(rest, key=lambda i: (m[i], -i))
+        else:
+            terminate = 1
+    return {"escape": esc, "terminate": terminate, "designated": des, "r_chain": math.sqrt(rc2), "r_escape": r_esc}
 
 
 # ---------------------------------------------------------------------------

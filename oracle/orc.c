@@ -897,3 +897,39 @@ int64_t orc_radius(int64_t n, const float *x, const float *y, const float *z, co
         if (dist2_f32(x[i], y[i], z[i], c[0], c[1], c[2]) < r2) { if (k < cap) out[k] = i; k++; }
     return k;
 }
+
+/* ------------------------------------------------------------------ */
+/* 8. Chain membership: absorption (Eq. 4)                              */
+/* ------------------------------------------------------------------ */
+/* The chain's centre of mass c = sum_k m_k x_k / M (FP64, members in index
+ * order) and its radius, the largest member distance from c (Sect. 2: the
+ * chain radius of the last chain step). Star j (FP32 position) is absorbed
+ * when r_j,CoM < r_chain (Eq. 4), decided without a square root in FP64 with
+ * one rounding per operation: d_a = (double)x_a - c_a, d2 = (d_x d_x + d_y d_y)
+ * + d_z d_z, absorbed iff d2 < rc2 with rc2 the largest member d2 (same
+ * formula). Writes the first cap ascending indices to out, returns the count;
+ * out2 = (sqrt(rc2), rc2). */
+int64_t orc_absorb(int64_t n, const float *x, const float *y, const float *z, int32_t nch, const double *cm,
+                   const double *cx, int64_t cap, int64_t *out, double out2[2]) {
+    double M = 0.0, c[3] = {0.0, 0.0, 0.0};
+    for (int32_t k = 0; k < nch; k++) {
+        M += cm[k];
+        for (int a = 0; a < 3; a++) c[a] += cm[k] * cx[3 * k + a];
+    }
+    for (int a = 0; a < 3; a++) c[a] = (M > 0.0) ? c[a] / M : 0.0;
+    double rc2 = 0.0;
+    for (int32_t k = 0; k < nch; k++) {
+        double dx = cx[3 * k] - c[0], dy = cx[3 * k + 1] - c[1], dz = cx[3 * k + 2] - c[2];
+        double d2 = (dx * dx + dy * dy) + dz * dz;
+        if (d2 > rc2) rc2 = d2;
+    }
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; i++) {
+        double dx = (double)x[i] - c[0], dy = (double)y[i] - c[1], dz = (double)z[i] - c[2];
+        double d2 = (dx * dx + dy * dy) + dz * dz;
+        if (d2 < rc2) { if (cnt < cap) out[cnt] = i; cnt++; }
+    }
+    out2[0] = sqrt(rc2);
+    out2[1] = rc2;
+    return cnt;
+}

@@ -562,6 +562,60 @@ def test_chain_quadrupole_skips_perturbers_closed_form():
     np.testing.assert_allclose(a[2, 0] + o["a_pert"][0, 2], exact, rtol=1e-12)
 
 
+def test_absorption_closed_form():
+    """Eq. 4: a chain of two equal masses at +-0.006 on x (centre 0, chain
+    radius 0.006) absorbs exactly the stars closer than 0.006: stars placed at
+    radii 0.0059 and 0.0061 in several directions, plus one at the FP32 value
+    of 0.006 itself (just above 0.006, so outside: the test is strict)."""
+    cm = np.array([0.005, 0.005])
+    cx = np.array([[0.006, 0.0, 0.0], [-0.006, 0.0, 0.0]])
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, -1], [0.6, 0.8, 0.0], [0.0, -0.6, 0.8]])
+    pts, want = [], []
+    for r in (0.0059, 0.0061):
+        for d in dirs:
+            pts.append(r * d)
+            want.append(r < 0.006)
+    pts.append([0.006, 0.0, 0.0])
+    want.append(False)
+    pos = np.array(pts, dtype=np.float32).T.copy()
+    idx, rch = oracle.absorb(pos, cm, cx)
+    assert rch == 0.006
+    np.testing.assert_array_equal(idx, np.flatnonzero(want))
+    assert len(idx) == 5
+
+
+def test_escape_rules_closed_form():
+    """Eq. 5 and the membership rules: r_escape = gamma r_chain0 = 1.5; a member
+    beyond it escapes only when receding; while perturbers are absorbed,
+    escapes wait unless the chain radius exceeds 1.05 r_escape; fewer than two
+    members left, or the designated SMBH leaving with no other SMBH, ends the
+    chain; with another SMBH left, the heavier remaining one takes over."""
+    eps = 1e-9                                                 # stars' masses: the centre stays at the SMBH
+    m = [1.0, eps, eps]
+    x = [[0, 0, 0], [1.55, 0, 0], [0, 2.0, 0]]
+    v = [[0, 0, 0], [1.0, 0, 0], [0, -1.0, 0]]                # star 1 recedes, star 2 approaches
+    r = oracle.chain_escape(m, x, v, [1, 0, 0], 0, 1.0, 1.5, 0)
+    assert list(r["escape"]) == [False, True, False] and r["terminate"] == 0 and r["designated"] == 0
+    assert r["r_escape"] == 1.5 and abs(r["r_chain"] - 2.0) < 1e-8
+    # absorbing while the chain radius (2.0) is above 1.05 x 1.5: the escape goes ahead
+    assert list(oracle.chain_escape(m, x, v, [1, 0, 0], 0, 1.0, 1.5, 3)["escape"]) == [False, True, False]
+    # chain radius 1.55 < 1.575: the escape waits for the absorption
+    x2 = [[0, 0, 0], [1.55, 0, 0], [0, 1.2, 0]]
+    assert not oracle.chain_escape(m, x2, v, [1, 0, 0], 0, 1.0, 1.5, 1)["escape"].any()
+    assert list(oracle.chain_escape(m, x2, v, [1, 0, 0], 0, 1.0, 1.5, 0)["escape"]) == [False, True, False]
+    # two members, the star escapes: one left, the chain ends
+    r = oracle.chain_escape([1.0, eps], [[0, 0, 0], [2.0, 0, 0]], [[0, 0, 0], [1.0, 0, 0]], [1, 0], 0, 1.0, 1.5, 0)
+    assert list(r["escape"]) == [False, True] and r["terminate"] == 1
+    # the designated SMBH (index 0) recedes from a chain dominated by two others
+    mm = [0.002, 0.005, 0.004, eps]
+    xx = [[3.0, 0, 0], [0, 0, 0], [0, 0.1, 0], [0, 0, 0.2]]
+    vv = [[1.0, 0, 0], [0, 0, 0], [0, 0, 0], [0, 0, 0]]
+    r = oracle.chain_escape(mm, xx, vv, [1, 1, 1, 0], 0, 1.0, 1.5, 0)
+    assert list(r["escape"]) == [True, False, False, False] and r["terminate"] == 0 and r["designated"] == 1
+    r = oracle.chain_escape(mm, xx, vv, [1, 0, 0, 0], 0, 1.0, 1.5, 0)
+    assert r["terminate"] == 1
+
+
 def test_tidal_selection_closed_form():
     """Eq. 2: with equal masses the criterion is a sphere of radius
     R = (2 m / (gamma M))^(1/3) r_crit; a star 8 times heavier reaches twice as
