@@ -349,6 +349,45 @@ rv_status rv_select_perturbers_tidal(rv_ctx *ctx, int64_t n, const float *x, con
                                      const float *m, const float centre[3], float m_chain, float gamma_crit,
                                      float r_crit, int32_t cap, int32_t *idx, int32_t *count, void *stream);
 
+/* Absorption into a chain (Eq. 4): the chain's centre of mass c (FP64,
+ * members in index order) and radius r_chain, the largest member distance
+ * from c (Sect. 2: the chain radius of the last chain step), from device
+ * FP64 chain_m[n_ch], chain_x[3 n_ch] (1 <= n_ch <= 250); a star j (device
+ * FP32 x, y, z [n], caller order) is absorbed when r_j,CoM < r_chain, decided
+ * in FP64 with one rounding per operation on squared distances:
+ * d = (double)x_j - c per axis, d2 = (dx dx + dy dy) + dz dz, absorbed iff
+ * d2 < max over members of the same d2. Writes the first cap absorbed
+ * indices (ascending) to device idx[cap], the untruncated count to device
+ * count[1] and, if not NULL, r_chain to device r_chain[1]. The chain's own
+ * members should not be among the stars (they are no longer tree particles). */
+rv_status rv_chain_absorb(rv_ctx *ctx, int64_t n, const float *x, const float *y, const float *z, int32_t n_ch,
+                          const double *chain_m, const double *chain_x, int32_t cap, int32_t *idx, int32_t *count,
+                          double *r_chain, void *stream);
+
+/* Escape from a chain (Eq. 5) and the membership rules around it (Sect. 2
+ * and Sect. 3), on the host for one chain of n_ch <= 250 members (host FP64
+ * m[n_ch], x[3 n_ch], v[3 n_ch]; massive[k] = 1 for an SMBH; designated = the
+ * member that is the chain's designated massive particle). With c, v_c the
+ * members' centre-of-mass position and velocity, d = x_k - c, u = v_k - v_c:
+ * member k escapes when (d.d) > (gamma r_chain0)^2 and (d.u) > 0 (receding),
+ * dot products summed (x + y) + z in FP64 with one rounding per operation;
+ * while n_absorbing > 0 perturbers are being absorbed (Eq. 4) escapes wait,
+ * unless the chain radius exceeds the escape radius by more than 5 %. The
+ * chain ends (terminate = 1) when fewer than 2 members remain, or when the
+ * designated member escapes and no other massive member remains; if another
+ * remains, the most massive one (lowest index on ties) becomes designated.
+ * Writes escape[k] (host, 1 = leaves) and *res. No device work. */
+typedef struct {
+    int32_t escape_count;
+    int32_t terminate;
+    int32_t designated;
+    double r_chain;    /* largest member distance from the centre of mass */
+    double r_escape;   /* gamma r_chain0 */
+} rv_chain_escape_result;
+rv_status rv_chain_escape(int32_t n_ch, const double *m, const double *x, const double *v, const int32_t *massive,
+                          int32_t designated, double r_chain0, double gamma, int32_t n_absorbing, int32_t *escape,
+                          rv_chain_escape_result *res);
+
 /* ---- Learned cell-force correction (not in the paper, whose tree uses the
  * multipoles alone). A network of 11 features -> 64 -> 64 -> 3 (SiLU;
  * bfloat16 weights and activations, FP32 accumulation on the tensor cores)

@@ -24,7 +24,9 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
 # The walk flushes FP32 denormals to zero: its operands are positions, masses
 # and multipoles far above the denormal range, and rsqrtf then needs no
 # denormal handling.
-FILE_FLAGS = {"walk.cu": ["-ftz=true"]}
+# The chain-membership host routine decides escapes in FP64 with one rounding
+# per operation: no contraction into fused multiply-adds on the host.
+FILE_FLAGS = {"walk.cu": ["-ftz=true"], "membership.cu": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def _nvcc() -> str:

@@ -51,6 +51,7 @@ struct DevState {
     int pad;
     unsigned long long n_p2p, n_m2p;  // interaction counts of the last walk
     double bounds[5];                 // min x, y, z, L, 2^21 / L
+    double absorb[4];                 // chain absorption: centre of mass x, y, z and the squared chain radius
     int lvoff[kLevels + 1];           // first cell of each level, then ncell
 };
 

@@ -32,7 +32,7 @@ EXPORTS = ["rv_default_config", "rv_workspace_size", "rv_create", "rv_destroy", 
            "rv_mlp_scratch_bytes", "rv_mlp_init", "rv_mlp_forward", "rv_mlp_gradient", "rv_mlp_adam",
            "rv_mlp_samples", "rv_tree_forces_mlp", "rv_wait_selftest", "rv_mlp_fit_feature_box",
            "rv_mlp_set_feature_box", "rv_direct_fp64_scratch_bytes", "rv_direct_fp64", "rv_mlp_train_scratch_bytes",
-           "rv_mlp_train", "rv_mlp_state_bytes", "rv_mlp_save", "rv_mlp_load"]
+           "rv_mlp_train", "rv_mlp_state_bytes", "rv_mlp_save", "rv_mlp_load", "rv_chain_absorb", "rv_chain_escape"]
 
 
 class RvError(RuntimeError):
@@ -63,6 +63,11 @@ class rv_mlp_train_cfg(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("t", C.c_void_p), ("steps", C.c_int32), ("batch", C.c_int32),
                 ("step0", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("adam_eps", C.c_float), ("seed", C.c_uint64), ("fit_box", C.c_int32)]
+
+
+class rv_chain_escape_result(C.Structure):
+    _fields_ = [("escape_count", C.c_int32), ("terminate", C.c_int32), ("designated", C.c_int32),
+                ("r_chain", C.c_double), ("r_escape", C.c_double)]
 
 
 class rv_system(C.Structure):
@@ -154,6 +159,8 @@ def _declare(L):
     L.rv_mlp_state_bytes.restype = C.c_size_t
     L.rv_mlp_save.argtypes = [vp, vp, C.c_size_t, vp]
     L.rv_mlp_load.argtypes = [vp, vp, C.c_size_t, vp]
+    L.rv_chain_absorb.argtypes = [vp, i64, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]
+    L.rv_chain_escape.argtypes = [i32, vp, vp, vp, vp, i32, f64, f64, i32, vp, C.POINTER(rv_chain_escape_result)]
     L.rv_launch_count.argtypes = [vp]
     L.rv_launch_count.restype = C.c_int64
     L.rv_last_error.argtypes = [vp]
@@ -421,6 +428,20 @@ class Context:
                                                      _ptr(a_chain), _ptr(pot_chain), _stream(stream)))
         return a_chain, pot_chain
 
+    def chain_absorb(self, x, y, z, chain_m, chain_x, cap=5000, stream=None):
+        """rv_chain_absorb (Eq. 4): (idx int32 [cap], count int32 [1] untruncated,
+        r_chain float64 [1]) as CUDA tensors; chain_m (n_ch,), chain_x (n_ch, 3)."""
+        import torch
+        cm = torch.as_tensor(chain_m, dtype=torch.float64).to("cuda").contiguous()
+        cx = torch.as_tensor(chain_x, dtype=torch.float64).to("cuda").reshape(-1).contiguous()
+        idx = torch.full((max(cap, 1),), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rch = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self._check(self.L.rv_chain_absorb(self.h, int(x.shape[0]), _ptr(x), _ptr(y), _ptr(z), int(cm.shape[0]),
+                                           _ptr(cm), _ptr(cx), int(cap), _ptr(idx), _ptr(cnt), _ptr(rch),
+                                           _stream(stream)))
+        return idx, cnt, rch
+
     def chain_start_radius(self, pos, vel, m, centre, m_bh, alpha, beta, eps, n_sigma=50, stream=None) -> dict:
         """Eq. 1: returns r2m, sigma, r_sigma, r_infl, r_chain0 (pos/vel: CUDA (x, y, z) tuples)."""
         _need_cuda(*pos, *vel, m)
@@ -680,6 +701,25 @@ class Mlp:
             raise RvError(st, "rv_mlp_load")
         if step is not None:
             self.step = int(step)
+
+
+def chain_escape(mass, pos, vel, massive, designated, r_chain0, gamma, n_absorbing):
+    """rv_chain_escape (Eq. 5 and the membership rules; host only): returns
+    dict escape (bool array), terminate, designated, r_chain, r_escape."""
+    import numpy as np
+    m = np.ascontiguousarray(mass, dtype=np.float64)
+    x = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1)
+    v = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1)
+    mv = np.ascontiguousarray(massive, dtype=np.int32)
+    k = int(m.shape[0])
+    esc = np.zeros(max(k, 1), dtype=np.int32)
+    res = rv_chain_escape_result()
+    st = load().rv_chain_escape(k, m.ctypes.data, x.ctypes.data, v.ctypes.data, mv.ctypes.data, int(designated),
+                                float(r_chain0), float(gamma), int(n_absorbing), esc.ctypes.data, C.byref(res))
+    if st != RV_OK:
+        raise RvError(st, "rv_chain_escape")
+    return {"escape": esc[:k].astype(bool), "terminate": int(res.terminate), "designated": int(res.designated),
+            "r_chain": float(res.r_chain), "r_escape": float(res.r_escape), "escape_count": int(res.escape_count)}
 
 
 def torch_float32():
