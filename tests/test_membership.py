@@ -73,7 +73,10 @@ def test_absorb_matches_oracle(n, seed, members):
     w = ics.hernquist(n, seed)
     p32 = w.pos.astype(np.float32)
     r = np.linalg.norm(p32.astype(np.float64), axis=0)
-    near = np.argsort(r)[:members - 2]
+    # members: stars drawn from the inner region (not the nearest ones), so that
+    # stars inside the chain radius remain in the tree
+    inner = np.flatnonzero(r < 0.04)
+    near = np.sort(ics.rng(seed).choice(inner, members - 2, replace=False))
     cm = np.concatenate([[0.005, 0.005], np.full(members - 2, 1.0 / n)])
     cx = np.concatenate([[[0.0055, 0.0, 0.0], [-0.0055, 0.0, 0.0]], p32[:, near].T.astype(np.float64)])
     keep = np.setdiff1d(np.arange(n), near)                    # members are no longer tree particles
