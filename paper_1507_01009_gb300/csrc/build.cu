@@ -259,7 +259,10 @@ __global__ void __launch_bounds__(kSortThreads) sort_upsweep_k(int64_t n, const 
 
 // Each warp ranks 256 consecutive keys in 8 rounds of 32 (warp-private digit
 // counters), so the in-tile order is (warp, round, lane) = input order and the
-// sort is stable.
+// sort is stable. The ranked tile is then staged in shared memory in digit
+// order and written out from there: consecutive threads write consecutive
+// slots of a digit's output run (coalesced), instead of each thread writing
+// its own element straight to a scattered destination.
 __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, const uint64_t *key_in,
                                                                  const int *idx_in, int shift, const int64_t *moff,
                                                                  int M, int ntiles, const int *hist,
@@ -267,12 +270,18 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, cons
     constexpr int NW = kSortThreads / 32;
     __shared__ unsigned short cnt[NW][kSortBins];
     __shared__ int gbase[kSortBins];
+    __shared__ int lstart[kSortBins];            // first staged slot of each digit
+    __shared__ uint64_t skey[kSortTile];
+    __shared__ int sidx[kSortTile];
+    __shared__ unsigned short sdig[kSortTile];
+    __shared__ int sw[NW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int b = lane; b < kSortBins; b += 32) cnt[wid][b] = 0;
     for (int b = threadIdx.x; b < kSortBins; b += kSortThreads)
         gbase[b] = hist[(int64_t)b * ntiles + blockIdx.x];
     __syncwarp();
-    int64_t base = (int64_t)blockIdx.x * kSortTile + wid * (32 * kSortItems);
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + wid * (32 * kSortItems);
     uint64_t kk[kSortItems];
     int digit[kSortItems], rank[kSortItems];
 #pragma unroll
@@ -290,12 +299,31 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, cons
         __syncwarp();
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) {
+    // per digit: the warps' counts become offsets within the digit's run of this tile
+    static_assert(kSortBins % kSortThreads == 0, "each thread owns whole digits");
+    int tot[kSortBins / kSortThreads];
+#pragma unroll
+    for (int q = 0; q < kSortBins / kSortThreads; q++) {
+        const int b = threadIdx.x * (kSortBins / kSortThreads) + q;
         int run = 0;
         for (int w = 0; w < NW; w++) {
             int t = cnt[w][b];
             cnt[w][b] = (unsigned short)run;
             run += t;
+        }
+        tot[q] = run;
+    }
+    // digit runs in digit order: exclusive scan of the tile's digit totals
+    {
+        int mine = 0;
+#pragma unroll
+        for (int q = 0; q < kSortBins / kSortThreads; q++) mine += tot[q];
+        int total;
+        int ex = block_exclusive_scan<kSortThreads>(mine, sw, total);
+#pragma unroll
+        for (int q = 0; q < kSortBins / kSortThreads; q++) {
+            lstart[threadIdx.x * (kSortBins / kSortThreads) + q] = ex;
+            ex += tot[q];
         }
     }
     __syncthreads();
@@ -303,11 +331,20 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, cons
     for (int r = 0; r < kSortItems; r++) {
         int64_t j = base + r * 32 + lane;
         if (j < n) {
-            int d = digit[r];
-            int64_t dst = (int64_t)gbase[d] + cnt[wid][d] + rank[r];
-            key_out[dst] = kk[r];
-            idx_out[dst] = idx_in ? idx_in[j] : (int)j;
+            const int d = digit[r];
+            const int slot = lstart[d] + cnt[wid][d] + rank[r];
+            skey[slot] = kk[r];
+            sidx[slot] = idx_in ? idx_in[j] : (int)j;
+            sdig[slot] = (unsigned short)d;
         }
+    }
+    __syncthreads();
+    const int tn = (int)min((int64_t)kSortTile, n - tile0);
+    for (int t = threadIdx.x; t < tn; t += kSortThreads) {
+        const int d = sdig[t];
+        const int64_t dst = (int64_t)gbase[d] + (t - lstart[d]);
+        key_out[dst] = skey[t];
+        idx_out[dst] = sidx[t];
     }
 }
 

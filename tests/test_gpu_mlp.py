@@ -72,6 +72,28 @@ def test_forward_many_tiles_ragged_and_unaligned(rvmod):
     assert np.all(np.isfinite(y))
 
 
+def test_forward_large_sampled(rvmod):
+    """4 M rows (features 256 MB, beyond L2; the size the network kernel's
+    profile is taken at): 2000 seeded rows against the oracle, and the rows
+    agree with a second call bit for bit."""
+    import torch
+    mlp = rvmod.Mlp(seed=13)
+    n = 1 << 22
+    g = torch.Generator(device="cpu").manual_seed(5)
+    xa = torch.zeros((n, 16), dtype=torch.float32)
+    xa[:, :11] = torch.randn((n, 11), generator=g)
+    xa = xa.cuda()
+    y = mlp.forward(xa)
+    assert torch.equal(y, mlp.forward(xa))
+    rows = ics.subsample(n, 2000, seed=14)
+    X = xa[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    yo, _ = oracle.mlp_forward(_params_np(mlp), X)
+    err = np.abs(y[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64) - yo)
+    scale = np.sqrt((yo ** 2).mean())
+    assert np.sqrt((err ** 2).mean()) <= 1e-3 * scale
+    assert err.max() <= 2e-2 * scale
+
+
 def test_forward_tiny_inputs(rvmod):
     """One row, a partial tile, and zero rows."""
     import torch
