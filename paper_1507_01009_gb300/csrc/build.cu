@@ -208,13 +208,13 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
     return (uint32_t)x;
 }
 
-// q = min(floor((x - min) * scale), 2^21 - 1): one FP64 subtraction, one FP64 product.
+// q = min(floor((x - min) * scale), 2^21 - 1): one FP64 subtraction, one FP64
+// product; for 0 <= t < 2^21 - 1 the floor is the conversion toward zero.
 __device__ __forceinline__ uint32_t grid_coord(float v, double lo, double scale) {
-    double t = __dmul_rn(__dsub_rn((double)v, lo), scale);
-    double f = floor(t);
-    if (f >= 2097151.0) return 2097151u;
-    if (f < 0.0) return 0u;
-    return (uint32_t)f;
+    const double t = __dmul_rn(__dsub_rn((double)v, lo), scale);
+    if (!(t >= 0.0)) return 0u;
+    if (t >= 2097151.0) return 2097151u;
+    return (uint32_t)__double2uint_rz(t);
 }
 
 // Blocks (bx, m): member m's stars with member m's bounding cube.
