@@ -524,22 +524,27 @@ __global__ void mlp_samples_k(CellGeo T, MacTable mac, int64_t n, float eps, uns
 // One CTA of 128 threads evaluates the network on tiles of 128 rows; thread i
 // owns row i of a tile, which is lane i of the accumulator in tensor memory
 // (warp w reads lanes 32w .. 32w + 31). Per tile: the features (bfloat16) go
-// to shared memory, one thread issues the MMAs of a layer (M = 128, bfloat16
-// operands from shared memory, FP32 accumulator in 64 TMEM columns) and
-// commits them to an mbarrier; every thread then reads its row back, adds the
-// bias, applies SiLU and writes the next layer's operand. Operands use the
-// no-swizzle K-major layout of the tcgen05 matrix descriptors: 8 rows x 16
-// bytes per core matrix (rows 16 bytes apart), core matrices adjacent in K 128
-// bytes apart (leading byte offset), 8-row groups K x 16 bytes apart (stride
-// byte offset).
+// to shared memory, one thread issues the MMAs of a layer (M = 128, FP32
+// accumulator in TMEM columns 0 .. 63) and commits them to an mbarrier; every
+// thread then reads its row back, adds the bias, applies SiLU and writes the
+// next layer's A operand straight into its own TMEM lane (columns 64 .. 95, two
+// bfloat16 per column, even k in the low half), so the hidden activations
+// never pass through shared memory. The weights (B) and layer 1's features
+// (A) sit in shared memory in the no-swizzle K-major layout of the tcgen05
+// matrix descriptors: 8 rows x 16 bytes per core matrix (rows 16 bytes apart),
+// core matrices adjacent in K 128 bytes apart (leading byte offset), 8-row
+// groups K x 16 bytes apart (stride byte offset).
 constexpr int kTcRows = 128;   // rows per tile (the MMA's M)
-constexpr int kTcCols = 64;    // TMEM columns of a CTA (all three layers' accumulators)
+// TMEM columns of a CTA: the three layers' FP32 accumulators (0 .. 63) and the
+// bfloat16 hidden activations as the next layer's A operand (64 .. 95, two per
+// column)
+constexpr int kTcCols = 128;
+constexpr int kTcACol = 64;
 constexpr int kTcOutN = 16;    // layer 3's N (3 outputs, padded)
-constexpr int kTcCtas = 6;     // resident CTAs per SM (shared memory ~35 KB, 6 x 64 of 512 TMEM columns)
+constexpr int kTcCtas = 4;     // resident CTAs per SM (4 x 128 of 512 TMEM columns)
 
 struct TcSmem {
     alignas(128) __nv_bfloat16 a1[kTcRows * kInPad];   // features: K = 16
-    alignas(128) __nv_bfloat16 a2[kTcRows * kHid];     // hidden activations: K = 64
     alignas(128) __nv_bfloat16 w1[kHid * kInPad];      // W1^T: N = 64 rows, K = 16
     alignas(128) __nv_bfloat16 w2[kHid * kHid];        // W2^T: 64 x 64
     alignas(128) __nv_bfloat16 w3[kTcOutN * kHid];     // W3^T: 16 x 64 (rows 8 .. 15 zero)
@@ -577,6 +582,17 @@ __device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigne
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
         :
         : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// the same with the A operand in tensor memory at column address a
+__device__ __forceinline__ void tc_mma_ta(unsigned d, unsigned a, unsigned long long b, unsigned idesc,
+                                          unsigned accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        :
+        : "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -706,40 +722,42 @@ __device__ __forceinline__ void silu_pair(float v0, float v1, float hb0, float h
     asm("mov.b64 {%0, %1}, %2;" : "=f"(s0), "=f"(s1) : "l"(o));
 }
 
-// columns c0 .. c0 + 15 (loaded into u) + half bias -> SiLU -> bfloat16 row r of a2
-__device__ __forceinline__ void tc_hidden16(TcSmem &S, const unsigned u[16], int r, int c0, const float *hbias) {
+// columns c0 .. c0 + 15 (loaded into u) + half bias -> SiLU -> bfloat16 pairs into this row's TMEM lane
+// from column a_taddr (the next layer's A operand)
+__device__ __forceinline__ void tc_hidden16(const unsigned u[16], int c0, const float *hbias, unsigned a_taddr) {
     float v[16];
 #pragma unroll
     for (int j = 0; j < 16; j += 2)
         silu_pair(__uint_as_float(u[j]), __uint_as_float(u[j + 1]), hbias[c0 + j], hbias[c0 + j + 1], v[j], v[j + 1]);
+    // this row's activations c0 .. c0 + 15 as 8 bfloat16 pairs into its TMEM lane (even k in the low half)
+    unsigned w[8];
 #pragma unroll
-    for (int c = 0; c < 2; c++) {
-        uint4 q;
-        q.x = pack_bf16(v[8 * c + 0], v[8 * c + 1]);
-        q.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
-        q.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
-        q.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
-        *reinterpret_cast<uint4 *>(S.a2 + tc_off(r, c0 + 8 * c, kHid)) = q;
-    }
+    for (int c = 0; c < 8; c++) w[c] = pack_bf16(v[2 * c], v[2 * c + 1]);
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(a_taddr + (unsigned)(c0 / 2)), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]),
+                   "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
 }
 
-// Accumulator columns 0 .. 63 of row r + bias -> SiLU -> bfloat16 row r of a2,
+// Accumulator columns 0 .. 63 of row r + bias -> SiLU -> bfloat16 A operand of the next layer,
 // 16 columns at a time, the TMEM load of the next 16 in flight while the
 // current 16 are processed.
 __device__ __forceinline__ void tc_hidden(TcSmem &S, unsigned tlane, int r, const float *hbias) {
+    const unsigned at = tlane + kTcACol;
     unsigned a[16], b[16];
     tc_ld16_issue(tlane, a);
     tc_ld_wait(a);
     tc_ld16_issue(tlane + 16, b);
-    tc_hidden16(S, a, r, 0, hbias);
+    tc_hidden16(a, 0, hbias, at);
     tc_ld_wait(b);
     tc_ld16_issue(tlane + 32, a);
-    tc_hidden16(S, b, r, 16, hbias);
+    tc_hidden16(b, 16, hbias, at);
     tc_ld_wait(a);
     tc_ld16_issue(tlane + 48, b);
-    tc_hidden16(S, a, r, 32, hbias);
+    tc_hidden16(a, 32, hbias, at);
     tc_ld_wait(b);
-    tc_hidden16(S, b, r, 48, hbias);
+    tc_hidden16(b, 48, hbias, at);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Issues layer `layer` (1, 2, 3) of the tile by one thread and waits for it
@@ -753,12 +771,12 @@ __device__ __forceinline__ bool tc_layer(TcSmem &S, int layer, unsigned tmem, un
         if (layer == 1) {
             tc_mma(tmem, tc_desc(S.a1, kInPad), tc_desc(S.w1, kInPad), tc_idesc(kTcRows, kHid), 0u);
         } else {
-            const unsigned long long da = tc_desc(S.a2, kHid);
             const unsigned long long db = layer == 2 ? tc_desc(S.w2, kHid) : tc_desc(S.w3, kHid);
             const unsigned id = layer == 2 ? tc_idesc(kTcRows, kHid) : tc_idesc(kTcRows, kTcOutN);
-            // K = 64 in four steps of 16: 2 core matrices (256 bytes) further each
+            // K = 64 in four steps of 16: A 8 TMEM columns further, B 2 core matrices (256 bytes) further each
 #pragma unroll
-            for (int s = 0; s < kHid / 16; s++) tc_mma(tmem, da + 16ull * s, db + 16ull * s, id, s > 0 ? 1u : 0u);
+            for (int s = 0; s < kHid / 16; s++)
+                tc_mma_ta(tmem, tmem + kTcACol + 8u * s, db + 16ull * s, id, s > 0 ? 1u : 0u);
         }
         tc_commit(&S.bar);
     }
