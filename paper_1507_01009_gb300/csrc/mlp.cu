@@ -996,6 +996,37 @@ __global__ void mlp_apply_k(const int4 *groups, const int *ngroup, const int *pe
     }
 }
 
+// Dynamic shared memory that keeps at most kTcCtas CTAs of `kern` on an SM.
+// Each CTA allocates kTcCols of the SM's 512 TMEM columns; a further CTA
+// that registers and shared memory would still admit would wait in
+// tcgen05.alloc until another CTA on its SM finishes, stretching the kernel's
+// tail. Padding the CTA's shared memory just past the (kTcCtas + 1)-CTA share
+// makes the scheduler place at most kTcCtas. Returns -1 on a CUDA error.
+template <typename K>
+static int tc_pad_smem(K kern) {
+    static int cached = -2;
+    if (cached != -2) return cached;
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+        return -1;
+    int pad = std::max(0, per_sm / (kTcCtas + 1) - reserved - (int)fa.sharedSizeBytes + 128);
+    pad = (pad + 127) & ~127;
+    for (int k = 0; k < 64; k++, pad += 128) {
+        if (pad > 48 * 1024 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pad) != cudaSuccess)
+            return -1;
+        int blocks = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kTcRows, pad) != cudaSuccess) return -1;
+        if (blocks <= kTcCtas) break;
+    }
+    cached = pad;
+    return pad;
+}
+
 static CellGeo cell_geo(rv_ctx *c, int ncell_host) {
     CellGeo T;
     T.pos = c->w.pos;
@@ -1053,7 +1084,9 @@ rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y
                                                   cudaSuccess)
         return RV_E_CUDA;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kTcRows - 1) / kTcRows, (int64_t)sms * kTcCtas));
-    mlp_forward_tc_k<<<grid, kTcRows, 0, s>>>(P, n, x, y);
+    const int pad = tc_pad_smem(mlp_forward_tc_k);
+    if (pad < 0) return RV_E_CUDA;
+    mlp_forward_tc_k<<<grid, kTcRows, pad, s>>>(P, n, x, y);
     return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
 }
 
@@ -1233,7 +1266,9 @@ rv_status rv_tree_forces_mlp(rv_ctx *c, const void *params, float theta, float t
     if ((r = read_ncell(c, s, &ncell, &ngroup)) != RV_OK) return r;
     MlpBlock P = mlp_block(const_cast<void *>(params));
     const int grid = std::max(1, std::min(ceil_div(pair_cap, kTcRows), c->num_sms * kTcCtas));
-    mlp_pairs_tc_k<<<grid, kTcRows, 0, s>>>(P, cell_geo(c, ncell), c->w.groups, reinterpret_cast<const int2 *>(pairs),
+    const int pad = tc_pad_smem(mlp_pairs_tc_k);
+    if (pad < 0) return set_err(c, RV_E_CUDA, "network kernel attributes");
+    mlp_pairs_tc_k<<<grid, kTcRows, pad, s>>>(P, cell_geo(c, ncell), c->w.groups, reinterpret_cast<const int2 *>(pairs),
                                             npairs, pair_cap, eps_star, gcorr, c->w.st);
     count_launch(c);
     mlp_apply_k<<<std::max(1, ceil_div(ngroup, 256)), 256, 0, s>>>(c->w.groups, &c->w.st->ngroup, c->w.perm, gcorr, ax,
