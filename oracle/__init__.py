@@ -553,7 +553,7 @@ def percentile(e, p):
 # ---------------------------------------------------------------------------
 # Learned cell-force correction (not in the paper): features, targets, MLP
 # ---------------------------------------------------------------------------
-MLP_IN, MLP_IN_PAD, MLP_HID, MLP_OUT, MLP_OUT_PAD = 11, 16, 64, 3, 8
+MLP_IN, MLP_IN_PAD, MLP_HID, MLP_OUT, MLP_OUT_PAD = 14, 16, 64, 3, 8
 
 
 def bf16_round(x):
@@ -565,17 +565,54 @@ def bf16_round(x):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def _sym3(Q6):
+    return np.array([[Q6[0], Q6[3], Q6[4]], [Q6[3], Q6[1], Q6[5]], [Q6[4], Q6[5], Q6[2]]])
+
+
+def cell_octupole(tree, cell):
+    """Traceless third moment of a cell about its centre of mass, the term the
+    quadrupole expansion leaves out (the next order of Sect. 1's expansion).
+    A leaf: from its stars, O_abc = sum_j m_j d_a d_b d_c (d = x_j - com). An
+    internal cell: from its children k (centre-of-mass offsets D_k, masses M_k,
+    traceless quadrupoles Q_k), O_abc = sum_k [M_k D_a D_b D_c + (D_a Q_k,bc +
+    D_b Q_k,ac + D_c Q_k,ab) / 3], the children's own third moments left out
+    (the trace parts of the children's second moments drop out of the
+    traceless part). Then O^T_abc = O_abc - (delta_ab t_c + delta_ac t_b +
+    delta_bc t_a) / 5 with t_a = O_akk. Returns O^T (3, 3, 3)."""
+    c = tree.cells[cell]
+    com = tree.moments[cell, 1:4]
+    O = np.zeros((3, 3, 3))
+    if c[4] == 0:      # a leaf: its stars
+        first, count = c[1], c[2]
+        d = np.stack([tree.x_sorted[first:first + count], tree.y_sorted[first:first + count],
+                      tree.z_sorted[first:first + count]]) - com[:, None]
+        O = np.einsum("j,aj,bj,cj->abc", tree.m_sorted[first:first + count], d, d, d)
+    else:
+        for k in range(c[3], c[3] + c[4]):
+            mk = tree.moments[k]
+            Mk, D, Qk = mk[0], mk[1:4] - com, _sym3(mk[4:10])
+            O += Mk * np.einsum("a,b,c->abc", D, D, D)
+            O += (np.einsum("a,bc->abc", D, Qk) + np.einsum("b,ac->abc", D, Qk) + np.einsum("c,ab->abc", D, Qk)) / 3.0
+    t = np.einsum("akk->a", O)
+    I = np.eye(3)
+    return O - (np.einsum("ab,c->abc", I, t) + np.einsum("ac,b->abc", I, t) + np.einsum("bc,a->abc", I, t)) / 5.0
+
+
 def cell_features(tree, cell, x, eps):
     """Features of one (target at x, accepted cell) pair: r/|r| (3), s/|r|,
-    eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz), with r = x - com and s the
-    cell side; and the normalisation M/|r|^2 of the output."""
+    eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz), and the cell's traceless
+    octupole contracted twice with the direction, O^T(., r^, r^) / (M s^3)
+    (3; cell_octupole), with r = x - com and s the cell side; and the
+    normalisation M/|r|^2 of the output."""
     mo = tree.moments[cell]
     M, com, Q = mo[0], mo[1:4], mo[4:10]
     lev = tree.cells[cell, 0]
     s = tree.L / 2.0 ** lev
     r = np.asarray(x, dtype=np.float64) - com
     d = np.linalg.norm(r)
-    f = np.concatenate([r / d, [s / d, eps / d], Q / (M * s * s)])
+    rh = r / d
+    v = np.einsum("abc,b,c->a", cell_octupole(tree, cell), rh, rh) / (M * s ** 3)
+    f = np.concatenate([rh, [s / d, eps / d], Q / (M * s * s), v])
     return f, M / (d * d)
 
 

@@ -158,3 +158,80 @@ def test_mlp_train_lowers_the_loss_of_a_learnable_target():
         start[k] = 0.3 * start[k]
     losses, _ = oracle.mlp_train(start, X, T, steps=300, batch=64, lr=3e-3, seed=5, rounding=False)
     assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:5])
+
+
+def _traceless_brute(pos, m):
+    """Traceless third moment of point masses about their centre of mass, by
+    plain summation (independent of oracle.cell_octupole)."""
+    com = (pos * m[:, None]).sum(0) / m.sum()
+    d = pos - com
+    O = np.zeros((3, 3, 3))
+    for j in range(len(m)):
+        for a in range(3):
+            for b in range(3):
+                for c in range(3):
+                    O[a, b, c] += m[j] * d[j, a] * d[j, b] * d[j, c]
+    t = np.array([O[a, 0, 0] + O[a, 1, 1] + O[a, 2, 2] for a in range(3)])
+    for a in range(3):
+        for b in range(3):
+            for c in range(3):
+                O[a, b, c] -= ((a == b) * t[c] + (a == c) * t[b] + (b == c) * t[a]) / 5.0
+    return O
+
+
+def test_octupole_feature_collinear_closed_form():
+    """Two masses on the x axis (one leaf, and again as two one-star children
+    of the root): O_xxx = sum m d^3, the traceless part has O_xxx (2/5) and
+    O_xyy = O_xzz = -O_xxx / 5, so the feature is (2/5) O_xxx x^ / (M s^3)
+    seen along x and -(1/5) O_xxx x^ / (M s^3) seen along y."""
+    pos = np.array([[-0.3, 0.0, 0.0], [0.5, 0.0, 0.0]], dtype=np.float32)
+    m = np.array([1.0, 3.0], dtype=np.float32)
+    x64 = pos.astype(np.float64)[:, 0]
+    com = (m * x64).sum() / m.sum()
+    Oxxx = float((m * (x64 - com) ** 3).sum())
+    for n_leaf in (4, 1):                   # one leaf, or a root with two one-star children
+        T = oracle.Tree(pos.T.copy(), m, n_leaf, 32)
+        assert (T.cells[0, 4] == 0) == (n_leaf == 4)
+        s = T.L
+        M = 4.0
+        fx, _ = oracle.cell_features(T, 0, np.array([com + 10.0, 0.0, 0.0]), 0.0)
+        fy, _ = oracle.cell_features(T, 0, np.array([com, 10.0, 0.0]), 0.0)
+        np.testing.assert_allclose(fx[11:14], [0.4 * Oxxx / (M * s ** 3), 0.0, 0.0], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(fy[11:14], [-0.2 * Oxxx / (M * s ** 3), 0.0, 0.0], rtol=1e-12, atol=1e-15)
+
+
+def test_octupole_from_children_with_quadrupoles_is_exact():
+    """A root with two children, each a leaf of two equal masses placed
+    symmetrically about the child's centre of mass (no third moment of its
+    own but a quadrupole): the children-based octupole equals the brute-force
+    traceless third moment of the four stars."""
+    cA, eA = np.array([-0.5, -0.4, -0.3]), np.array([0.1, 0.05, -0.02])
+    cB, eB = np.array([0.4, 0.3, 0.45]), np.array([-0.05, 0.1, 0.08])
+    pos = np.array([cA + eA, cA - eA, cB + eB, cB - eB], dtype=np.float32)
+    m = np.array([1.0, 1.0, 2.0, 2.0], dtype=np.float32)
+    T = oracle.Tree(pos.T.copy(), m, 2, 32)
+    assert T.cells[0, 4] == 2 and all(T.cells[k, 4] == 0 and T.cells[k, 2] == 2 for k in (1, 2))
+    ref = _traceless_brute(pos.astype(np.float64), m.astype(np.float64))
+    np.testing.assert_allclose(oracle.cell_octupole(T, 0), ref, atol=1e-12 * np.abs(ref).max())
+
+
+def test_octupole_feature_predicts_the_quadrupole_residual():
+    """Far from a lopsided cell, the quadrupole expansion's residual along the
+    line of sight is the octupole term -10 O^T(r^, r^, r^) / r^5 (from the
+    potential -(5/2) O^T(r^ r^ r^) / r^4): the relative mismatch falls as s/r."""
+    g = ics.rng(77)
+    pos = g.uniform(-0.5, 0.5, (3, 40)).astype(np.float32)
+    pos[0, :10] += 0.3                                      # lopsided: a real octupole
+    m = g.uniform(0.5, 1.5, 40).astype(np.float32)
+    T = oracle.Tree(pos, m, 64, 64)                          # one leaf
+    M, com = T.moments[0, 0], T.moments[0, 1:4]
+    s = T.L
+    rh = np.array([0.6, -0.48, 0.64])
+    mis = []
+    for R in (20.0, 40.0):
+        x = com + R * rh
+        res = oracle.cell_residual(T, 0, x, 0.0)
+        f, _ = oracle.cell_features(T, 0, x, 0.0)
+        pred = -10.0 * float(f[11:14] @ rh) * M * s ** 3 / R ** 5
+        mis.append(abs(res @ rh - pred) / abs(pred))
+    assert mis[0] < 0.1 and 1.6 < mis[0] / mis[1] < 2.4, mis
