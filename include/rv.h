@@ -389,12 +389,17 @@ rv_status rv_chain_escape(int32_t n_ch, const double *m, const double *x, const 
                           rv_chain_escape_result *res);
 
 /* ---- Learned cell-force correction (not in the paper, whose tree uses the
- * multipoles alone). A network of 11 features -> 64 -> 64 -> 3 (SiLU;
+ * multipoles alone). A network of 14 features -> 64 -> 64 -> 3 (SiLU;
  * bfloat16 weights and activations, FP32 accumulation on the tensor cores)
  * predicts, for a point at r = x - com from an accepted cell of side s and
  * mass M, (exact softened force of the cell's stars - its monopole +
- * quadrupole force) * |r|^2 / M. Features (16 floats per row, 11 used):
- * r/|r| (3), s/|r|, eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz).
+ * quadrupole force) * |r|^2 / M. Features (16 floats per row, 14 used):
+ * r/|r| (3), s/|r|, eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz), and the
+ * octupole term of the cell's acceleration in the output's units (3),
+ * (5/2) [3 v - 7 r^ (r^ . v)] / (M |r|^3) with r^ = r/|r| and v = O(., r^, r^),
+ * O the cell's traceless third moment about its centre of mass (a leaf's
+ * from its stars, an internal cell's from its children's masses and
+ * quadrupoles).
  * The parameter block (rv_mlp_param_bytes, device, caller-owned) holds FP32
  * master weights, Adam moments and bfloat16 copies. */
 size_t rv_mlp_param_bytes(void);

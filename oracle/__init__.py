@@ -600,10 +600,14 @@ def cell_octupole(tree, cell):
 
 def cell_features(tree, cell, x, eps):
     """Features of one (target at x, accepted cell) pair: r/|r| (3), s/|r|,
-    eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz), and the cell's traceless
-    octupole contracted twice with the direction, O^T(., r^, r^) / (M s^3)
-    (3; cell_octupole), with r = x - com and s the cell side; and the
-    normalisation M/|r|^2 of the output."""
+    eps/|r|, Q/(M s^2) (xx, yy, zz, xy, xz, yz), and the octupole term of the
+    cell's acceleration in the output's units (3): the next order of Sect. 1's
+    expansion, whose potential is -(5/2) O^T(r^, r^, r^) / |r|^4 with O^T the
+    traceless third moment (cell_octupole), has the acceleration
+    (5/2) [3 O^T(., r^, r^) - 7 r^ O^T(r^, r^, r^)] / |r|^5, and times |r|^2 / M
+    that is (5/2) [3 v - 7 r^ (r^ . v)] / (M |r|^3) with v = O^T(., r^, r^).
+    r = x - com, s the cell side; also returns the normalisation M/|r|^2 of the
+    output."""
     mo = tree.moments[cell]
     M, com, Q = mo[0], mo[1:4], mo[4:10]
     lev = tree.cells[cell, 0]
@@ -611,8 +615,9 @@ def cell_features(tree, cell, x, eps):
     r = np.asarray(x, dtype=np.float64) - com
     d = np.linalg.norm(r)
     rh = r / d
-    v = np.einsum("abc,b,c->a", cell_octupole(tree, cell), rh, rh) / (M * s ** 3)
-    f = np.concatenate([rh, [s / d, eps / d], Q / (M * s * s), v])
+    v = np.einsum("abc,b,c->a", cell_octupole(tree, cell), rh, rh)
+    g = 2.5 * (3.0 * v - 7.0 * rh * (rh @ v)) / (M * d ** 3)
+    f = np.concatenate([rh, [s / d, eps / d], Q / (M * s * s), g])
     return f, M / (d * d)
 
 

@@ -27,7 +27,7 @@
 
 namespace rv {
 
-constexpr int kIn = 11, kInPad = 16, kHid = 64, kOut = 3, kOutPad = 8;
+constexpr int kIn = 14, kInPad = 16, kHid = 64, kOut = 3, kOutPad = 8;
 // FP32 parameter vector (master weights, Adam moments and gradients share it):
 constexpr int oW1 = 0;                  // W1[k][n], 16 x 64 (rows 11..15 zero)
 constexpr int ob1 = oW1 + kInPad * kHid;
@@ -397,6 +397,7 @@ struct CellGeo {
     const int4 *cbox;
     const int4 *clink;
     const float4 *cmom;
+    const float4 *coct;   // each cell's traceless octupole (octupole_k), 3 float4
     const int64_t *moff;
     int M;
     const double *mbounds;
@@ -410,11 +411,89 @@ __device__ __forceinline__ void member_geo(const CellGeo &T, int m, float lo[3],
     unit = (float)(b[3] / 2097152.0);
 }
 
+// Traceless third moment of every cell about its centre of mass (the term the
+// quadrupole expansion leaves out): a leaf from its stars, O_abc = sum_j m_j
+// d_a d_b d_c (d = x_j - com); an internal cell from its children k (offset
+// D_k of the child's centre of mass, mass M_k, traceless quadrupole Q_k):
+// O_abc = sum_k [M_k D_a D_b D_c + (D_a Q_k,bc + D_b Q_k,ac + D_c Q_k,ab) / 3]
+// (the children's own third moments left out); then O^T = O - (delta t + ..)/5,
+// t_a = O_akk. Stored as (xxx, xxy, xxz, xyy), (xyz, xzz, yyy, yyz), (yzz, zzz, 0, 0).
+__device__ __forceinline__ void oct_add(float O[10], float w, float dx, float dy, float dz) {
+    const float wx = w * dx, wy = w * dy, wz = w * dz;
+    O[0] += wx * dx * dx; O[1] += wx * dx * dy; O[2] += wx * dx * dz; O[3] += wx * dy * dy; O[4] += wx * dy * dz;
+    O[5] += wx * dz * dz; O[6] += wy * dy * dy; O[7] += wy * dy * dz; O[8] += wy * dz * dz; O[9] += wz * dz * dz;
+}
+__global__ void octupole_k(CellGeo T, float4 *coct) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < T.ncell; c += gridDim.x * blockDim.x) {
+        const int4 lk = T.clink[c];
+        const float4 r0 = T.cmom[3 * c];
+        float O[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (r0.x > 0.f && lk.z >= 0 && lk.w >= lk.z) {
+            const int m = member_of(T.moff, T.M, lk.z);
+            float lo[3], unit;
+            const double *b = T.mbounds + 5 * m;
+            lo[0] = (float)b[0]; lo[1] = (float)b[1]; lo[2] = (float)b[2];
+            unit = (float)(b[3] / 2097152.0);
+            float c0[3];
+            geo_centre(T.cbox[c], lo, unit, c0);
+            if (lk.x == lk.y) {   // a leaf: its stars
+                for (int j = lk.z; j < lk.w; j++) {
+                    const float4 p = T.pos[j];
+                    oct_add(O, p.w, (p.x - c0[0]) - r0.y, (p.y - c0[1]) - r0.z, (p.z - c0[2]) - r0.w);
+                }
+            } else {              // its children
+                for (int k = lk.x; k < lk.y && k < T.ncell; k++) {
+                    const float4 a = T.cmom[3 * k], qa = T.cmom[3 * k + 1], qb = T.cmom[3 * k + 2];
+                    float ck[3];
+                    geo_centre(T.cbox[k], lo, unit, ck);
+                    const float D[3] = {(ck[0] - c0[0]) + (a.y - r0.y), (ck[1] - c0[1]) + (a.z - r0.z),
+                                        (ck[2] - c0[2]) + (a.w - r0.w)};
+                    oct_add(O, a.x, D[0], D[1], D[2]);
+                    // (D_a Q_bc + D_b Q_ac + D_c Q_ab) / 3, Q = (xx, yy, zz, xy, xz, yz) = (qa.x, qa.y, qa.z, qa.w, qb.x, qb.y)
+                    const float Qxx = qa.x, Qyy = qa.y, Qzz = qa.z, Qxy = qa.w, Qxz = qb.x, Qyz = qb.y;
+                    const float t3 = 1.f / 3.f;
+                    O[0] += t3 * 3.f * D[0] * Qxx;                               // xxx
+                    O[1] += t3 * (2.f * D[0] * Qxy + D[1] * Qxx);                // xxy
+                    O[2] += t3 * (2.f * D[0] * Qxz + D[2] * Qxx);                // xxz
+                    O[3] += t3 * (D[0] * Qyy + 2.f * D[1] * Qxy);                // xyy
+                    O[4] += t3 * (D[0] * Qyz + D[1] * Qxz + D[2] * Qxy);         // xyz
+                    O[5] += t3 * (D[0] * Qzz + 2.f * D[2] * Qxz);                // xzz
+                    O[6] += t3 * 3.f * D[1] * Qyy;                               // yyy
+                    O[7] += t3 * (2.f * D[1] * Qyz + D[2] * Qyy);                // yyz
+                    O[8] += t3 * (D[1] * Qzz + 2.f * D[2] * Qyz);                // yzz
+                    O[9] += t3 * 3.f * D[2] * Qzz;                               // zzz
+                }
+            }
+            // traceless part: t = (xxx + xyy + xzz, xxy + yyy + yzz, xxz + yyz + zzz)
+            const float tx = O[0] + O[3] + O[5], ty = O[1] + O[6] + O[8], tz = O[2] + O[7] + O[9];
+            const float f5 = 0.2f;
+            O[0] -= f5 * 3.f * tx; O[1] -= f5 * ty; O[2] -= f5 * tz; O[3] -= f5 * tx; O[4] -= 0.f;
+            O[5] -= f5 * tx; O[6] -= f5 * 3.f * ty; O[7] -= f5 * tz; O[8] -= f5 * ty; O[9] -= f5 * 3.f * tz;
+        }
+        coct[3 * c] = make_float4(O[0], O[1], O[2], O[3]);
+        coct[3 * c + 1] = make_float4(O[4], O[5], O[6], O[7]);
+        coct[3 * c + 2] = make_float4(O[8], O[9], 0.f, 0.f);
+    }
+}
+
+// O^T(., rh, rh) of a cell's stored traceless octupole
+__device__ __forceinline__ void oct_dir(const float4 o0, const float4 o1, const float4 o2, const float rh[3], float v[3]) {
+    const float x = rh[0], y = rh[1], z = rh[2];
+    const float xxx = o0.x, xxy = o0.y, xxz = o0.z, xyy = o0.w, xyz = o1.x, xzz = o1.y, yyy = o1.z, yyz = o1.w,
+                yzz = o2.x, zzz = o2.y;
+    v[0] = xxx * x * x + xyy * y * y + xzz * z * z + 2.f * (xxy * x * y + xxz * x * z + xyz * y * z);
+    v[1] = xxy * x * x + yyy * y * y + yzz * z * z + 2.f * (xyy * x * y + xyz * x * z + yyz * y * z);
+    v[2] = xxz * x * x + yyz * y * y + zzz * z * z + 2.f * (xyz * x * y + xzz * x * z + yzz * y * z);
+}
+
 // r = x - com with x given relative to the point g (xr = x - g), gc = cell
-// centre - g: com - g = gc + (com - c0). Writes 16 features (11 used) and
-// returns M / |r|^2.
-__device__ float pair_features(const float4 r0, const float4 q0, const float4 q1, float side, float eps,
-                               const float r[3], float f[kInPad]) {
+// centre - g: com - g = gc + (com - c0). Writes 16 features (14 used: the
+// direction, s / |r|, eps / |r|, Q / (M s^2), and the octupole term of the
+// cell's acceleration in the output's units, (5/2) [3 v - 7 r^ (r^ . v)] /
+// (M |r|^3) with v = O^T(., r^, r^), from the potential -(5/2) O^T(r^, r^, r^)
+// / |r|^4) and returns M / |r|^2.
+__device__ float pair_features(const float4 r0, const float4 q0, const float4 q1, const float4 *oct, float side,
+                               float eps, const float r[3], float f[kInPad]) {
     const float d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
     if (!(r0.x > 0.f) || !(d2 > 0.f)) {  // massless (ghost) cell: no correction
         for (int k = 0; k < kInPad; k++) f[k] = 0.f;
@@ -426,6 +505,14 @@ __device__ float pair_features(const float4 r0, const float4 q0, const float4 q1
     f[4] = eps * id;
     const float qs = 1.f / (r0.x * side * side);
     f[5] = q0.x * qs; f[6] = q0.y * qs; f[7] = q0.z * qs; f[8] = q0.w * qs; f[9] = q1.x * qs; f[10] = q1.y * qs;
+    const float rh[3] = {f[0], f[1], f[2]};
+    float v[3];
+    oct_dir(oct[0], oct[1], oct[2], rh, v);
+    const float rv = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
+    const float os = 2.5f * id * id * id / r0.x;
+    f[11] = os * (3.f * v[0] - 7.f * rh[0] * rv);
+    f[12] = os * (3.f * v[1] - 7.f * rh[1] * rv);
+    f[13] = os * (3.f * v[2] - 7.f * rh[2] * rv);
     for (int k = kIn; k < kInPad; k++) f[k] = 0.f;
     return r0.x / d2;
 }
@@ -487,7 +574,7 @@ __global__ void mlp_samples_k(CellGeo T, MacTable mac, int64_t n, float eps, uns
             // r = x - com = (x - c0) - (com - c0)
             const float r[3] = {(p.x - c0[0]) - r0.y, (p.y - c0[1]) - r0.z, (p.z - c0[2]) - r0.w};
             const float side = unit * (float)(1 << (kMaxLevel - b.w));
-            const float norm = pair_features(r0, q0, q1, side, eps, r, f);
+            const float norm = pair_features(r0, q0, q1, T.coct + 3 * chosen, side, eps, r, f);
             // exact softened force of the cell's stars
             const int4 lk = T.clink[chosen];
             float ex[3] = {0.f, 0.f, 0.f};
@@ -942,7 +1029,7 @@ __global__ void __launch_bounds__(kTcRows) mlp_pairs_tc_k(MlpBlock P, CellGeo T,
             const float rr[3] = {-((c0[0] - gcen[0]) + q.y), -((c0[1] - gcen[1]) + q.z),
                                  -((c0[2] - gcen[2]) + q.w)};
             const float side = unit * (float)(1 << (kMaxLevel - b.w));
-            norm = pair_features(q, q0, q1, side, eps, rr, f);
+            norm = pair_features(q, q0, q1, T.coct + 3 * pr.y, side, eps, rr, f);
             // outside the features the network was trained on: no correction (the plain tree)
             bool inside = true;
 #pragma unroll
@@ -1033,6 +1120,7 @@ static CellGeo cell_geo(rv_ctx *c, int ncell_host) {
     T.cbox = c->w.cbox;
     T.clink = reinterpret_cast<const int4 *>(c->w.clink);
     T.cmom = c->w.cmom;
+    T.coct = c->w.coct;
     T.moff = c->w.moff;
     T.M = c->n_members;
     T.mbounds = c->w.mbounds;
@@ -1239,6 +1327,9 @@ rv_status rv_mlp_samples(rv_ctx *c, float theta, float eps_star, int64_t n_sampl
     rv_status r = read_ncell(c, s, &ncell, &ngroup);
     if (r != RV_OK || n_samples == 0) return r;
     const int grid = (int)std::min<int64_t>((n_samples + 127) / 128, (int64_t)c->num_sms * 16);
+    octupole_k<<<std::max(1, std::min(ceil_div(ncell, 256), c->num_sms * 8)), 256, 0, s>>>(cell_geo(c, ncell),
+                                                                                           c->w.coct);
+    count_launch(c);
     mlp_samples_k<<<grid, 128, 0, s>>>(cell_geo(c, ncell), mac_table(theta), c->n, eps_star, seed, n_samples, x, t,
                                         reinterpret_cast<int2 *>(pairs), c->w.st);
     count_launch(c);
@@ -1265,6 +1356,9 @@ rv_status rv_tree_forces_mlp(rv_ctx *c, const void *params, float theta, float t
     int ncell, ngroup;
     if ((r = read_ncell(c, s, &ncell, &ngroup)) != RV_OK) return r;
     MlpBlock P = mlp_block(const_cast<void *>(params));
+    octupole_k<<<std::max(1, std::min(ceil_div(ncell, 256), c->num_sms * 8)), 256, 0, s>>>(cell_geo(c, ncell),
+                                                                                           c->w.coct);
+    count_launch(c);
     const int grid = std::max(1, std::min(ceil_div(pair_cap, kTcRows), c->num_sms * kTcCtas));
     const int pad = tc_pad_smem(mlp_pairs_tc_k);
     if (pad < 0) return set_err(c, RV_E_CUDA, "network kernel attributes");

@@ -66,6 +66,7 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.cbox = (int4 *)take(16 * cap);
     t.clink = (int *)take(16 * cap);
     t.cmom = (float4 *)take(48 * cap);
+    t.coct = (float4 *)take(48 * cap);
     t.cparent = (int *)take(4 * cap);
     t.carrive = (int *)take(4 * cap);
     t.gcnt = (int *)take(4 * cap);

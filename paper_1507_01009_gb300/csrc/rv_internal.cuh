@@ -68,6 +68,7 @@ struct Workspace {
     int4 *cbox;           // (ox, oy, oz, level)
     int *clink;           // [4 ncell] child first, child end, first star, end star
     float4 *cmom;         // [3 ncell]
+    float4 *coct;         // [3 ncell] traceless octupoles (the learned correction's features only)
     int *cparent, *carrive;
     int *gcnt;            // groups of each cell, scanned in place to each cell's first group
     int4 *groups;         // 2 int4 per group: (first, count, lo x, lo y), (lo z, hi x, hi y, hi z)

@@ -31,7 +31,7 @@ def _params_np(mlp):
 def _features(n, seed):
     g = ics.rng(seed)
     X = np.zeros((n, 16), dtype=np.float32)
-    X[:, :11] = g.normal(0, 1, (n, 11)).astype(np.float32)
+    X[:, :14] = g.normal(0, 1, (n, 14)).astype(np.float32)
     return X
 
 
@@ -81,7 +81,7 @@ def test_forward_large_sampled(rvmod):
     n = 1 << 22
     g = torch.Generator(device="cpu").manual_seed(5)
     xa = torch.zeros((n, 16), dtype=torch.float32)
-    xa[:, :11] = torch.randn((n, 11), generator=g)
+    xa[:, :14] = torch.randn((n, 14), generator=g)
     xa = xa.cuda()
     y = mlp.forward(xa)
     assert torch.equal(y, mlp.forward(xa))
@@ -138,7 +138,7 @@ def test_gradient_matches_oracle(rvmod):
     assert abs(float(loss.item()) / lo - 1) <= 1e-3
     assert np.linalg.norm(g - gv) <= 1e-3 * np.linalg.norm(gv)
     # padding never receives gradient
-    assert np.all(g[11 * 64:16 * 64] == 0)
+    assert np.all(g[14 * 64:16 * 64] == 0)
 
 
 def test_adam_step_matches_oracle(rvmod):
@@ -185,7 +185,7 @@ def test_samples_match_oracle(rvmod):
         gap = np.maximum(0, np.maximum(o - (q + 1), q - (o + side)))
         assert float(side * side) < th2 * float((gap * gap).sum())
         f, norm = oracle.cell_features(T, c, pos, eps)
-        np.testing.assert_allclose(x[s, :11], f, rtol=2e-4, atol=2e-6)
+        np.testing.assert_allclose(x[s, :14], f, rtol=2e-4, atol=2e-6)
         res = oracle.cell_residual(T, c, pos, eps) / norm
         assert np.abs(t[s] - res).max() <= 1e-4, (s, t[s], res)
 
@@ -205,12 +205,12 @@ def test_training_reduces_loss(rvmod):
     zero = float((tv ** 2).mean().item())
     # training works (the validation loss of the random network falls) ...
     assert float(l1.item()) < 0.5 * float(l0.item())
-    # ... but it ends near the loss of predicting no residual: the monopole +
-    # quadrupole residual is set by the cell's higher moments, which the
-    # features do not carry (measured ratio printed)
+    # ... and ends well below the loss of predicting no residual: the octupole
+    # features carry most of what the multipoles leave out (measured ratio
+    # printed; 0.26 on this galaxy)
     print(json.dumps({"val_loss_initial": float(l0.item()), "val_loss_trained": float(l1.item()),
                       "val_loss_zero_predictor": zero}))
-    assert float(l1.item()) < 2.0 * zero
+    assert float(l1.item()) < 0.5 * zero
 
 
 def test_feature_box_fit_and_set(rvmod):
@@ -268,7 +268,7 @@ def test_correction_applied_as_the_oracle_says(rvmod, boxed):
         d2 = float((gap * gap).sum())
         assert float(side * side) < th2 * d2 and not (float(side * side) < tr2 * d2)   # in the band
         f, nm = oracle.cell_features(T, c, centre, eps)
-        feats.append(np.concatenate([f, np.zeros(5)]))
+        feats.append(np.concatenate([f, np.zeros(16 - len(f))]))
         norms.append(nm)
     feats, norms = np.array(feats), np.array(norms)
     if boxed:
@@ -400,13 +400,14 @@ def test_training_learns_the_residual(rvmod):
     assert rep["p99_trained"] < 0.1 * rep["p99_untrained"]
 
 
-@pytest.mark.xfail(strict=True, reason="known gap: the correction is evaluated once per (group, cell) pair at the "
-                                       "group's centre and added to all of the group's stars; even the exact residual "
-                                       "applied that way lowers p99 by only ~15-20 % (the residual varies across the "
-                                       "group), and the network's features (monopole + quadrupole only) do not carry "
-                                       "the residual, so the trained correction does not beat the plain tree")
 def test_what_the_trained_network_gains(rvmod):
-    """The trained correction must beat the plain tree at the same theta."""
+    """The trained correction must beat the plain tree at the same theta
+    (1.2, corrections for the cells a walk at 0.6 would open). The margin is
+    small (measured 1.81e-3 against 1.85e-3): the correction is evaluated once
+    per (group, cell) pair at the group's centre and added to all of the
+    group's stars, and even the exact residual applied that way removes only
+    ~20 % of the error, because the residual varies across a group as much as
+    it is large."""
     rep = _gain(rvmod)
     assert rep["p99_trained"] < rep["p99_plain"]
 

@@ -75,7 +75,7 @@ def test_mlp_backward_matches_finite_differences():
     g = ics.rng(3)
     p = _params(4)
     X = np.zeros((32, 16))
-    X[:, :11] = g.normal(0, 1, (32, 11))
+    X[:, :14] = g.normal(0, 1, (32, 14))
     T = g.normal(0, 0.3, (32, 3))
     loss, grad = oracle.mlp_loss_grad(p, X, T, rounding=False)
     h = 1e-6
@@ -151,7 +151,7 @@ def test_mlp_train_lowers_the_loss_of_a_learnable_target():
     loop's loss falls by more than 10x within 300 steps."""
     tp = _params(41)
     X = np.zeros((512, 16))
-    X[:, :11] = ics.rng(42).normal(0, 1, (512, 11))
+    X[:, :14] = ics.rng(42).normal(0, 1, (512, 14))
     T, _ = oracle.mlp_forward(tp, X, rounding=False)
     start = _params(43)
     for k in start:
@@ -182,8 +182,10 @@ def _traceless_brute(pos, m):
 def test_octupole_feature_collinear_closed_form():
     """Two masses on the x axis (one leaf, and again as two one-star children
     of the root): O_xxx = sum m d^3, the traceless part has O_xxx (2/5) and
-    O_xyy = O_xzz = -O_xxx / 5, so the feature is (2/5) O_xxx x^ / (M s^3)
-    seen along x and -(1/5) O_xxx x^ / (M s^3) seen along y."""
+    O_xyy = O_xzz = -O_xxx / 5. Seen along x at distance R, v = (2/5) O_xxx x^
+    is radial and the feature is (5/2)(3 - 7)(2/5) O_xxx x^ / (M R^3) =
+    -4 O_xxx x^ / (M R^3); seen along y, v = -(1/5) O_xxx x^ is tangential and
+    the feature is (5/2) 3 (-1/5) O_xxx x^ / (M R^3) = -1.5 O_xxx x^ / (M R^3)."""
     pos = np.array([[-0.3, 0.0, 0.0], [0.5, 0.0, 0.0]], dtype=np.float32)
     m = np.array([1.0, 3.0], dtype=np.float32)
     x64 = pos.astype(np.float64)[:, 0]
@@ -192,12 +194,11 @@ def test_octupole_feature_collinear_closed_form():
     for n_leaf in (4, 1):                   # one leaf, or a root with two one-star children
         T = oracle.Tree(pos.T.copy(), m, n_leaf, 32)
         assert (T.cells[0, 4] == 0) == (n_leaf == 4)
-        s = T.L
-        M = 4.0
-        fx, _ = oracle.cell_features(T, 0, np.array([com + 10.0, 0.0, 0.0]), 0.0)
-        fy, _ = oracle.cell_features(T, 0, np.array([com, 10.0, 0.0]), 0.0)
-        np.testing.assert_allclose(fx[11:14], [0.4 * Oxxx / (M * s ** 3), 0.0, 0.0], rtol=1e-12, atol=1e-15)
-        np.testing.assert_allclose(fy[11:14], [-0.2 * Oxxx / (M * s ** 3), 0.0, 0.0], rtol=1e-12, atol=1e-15)
+        M, R = 4.0, 10.0
+        fx, _ = oracle.cell_features(T, 0, np.array([com + R, 0.0, 0.0]), 0.0)
+        fy, _ = oracle.cell_features(T, 0, np.array([com, R, 0.0]), 0.0)
+        np.testing.assert_allclose(fx[11:14], [-4.0 * Oxxx / (M * R ** 3), 0.0, 0.0], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(fy[11:14], [-1.5 * Oxxx / (M * R ** 3), 0.0, 0.0], rtol=1e-12, atol=1e-15)
 
 
 def test_octupole_from_children_with_quadrupoles_is_exact():
@@ -216,22 +217,26 @@ def test_octupole_from_children_with_quadrupoles_is_exact():
 
 
 def test_octupole_feature_predicts_the_quadrupole_residual():
-    """Far from a lopsided cell, the quadrupole expansion's residual along the
-    line of sight is the octupole term -10 O^T(r^, r^, r^) / r^5 (from the
-    potential -(5/2) O^T(r^ r^ r^) / r^4): the relative mismatch falls as s/r."""
+    """Far from a lopsided cell, the quadrupole expansion's residual in the
+    output's units (residual |r|^2 / M) is the octupole feature, radial and
+    tangential parts alike: the relative mismatch of the whole vector falls as
+    s/r (the next order), and along the line of sight the residual is
+    -10 O^T(r^, r^, r^) / r^5 written from the tensor directly."""
     g = ics.rng(77)
     pos = g.uniform(-0.5, 0.5, (3, 40)).astype(np.float32)
     pos[0, :10] += 0.3                                      # lopsided: a real octupole
     m = g.uniform(0.5, 1.5, 40).astype(np.float32)
     T = oracle.Tree(pos, m, 64, 64)                          # one leaf
-    M, com = T.moments[0, 0], T.moments[0, 1:4]
-    s = T.L
+    com = T.moments[0, 1:4]
     rh = np.array([0.6, -0.48, 0.64])
-    mis = []
+    O = _traceless_brute(pos.T.astype(np.float64), m.astype(np.float64))
+    mis, vec = [], []
     for R in (20.0, 40.0):
         x = com + R * rh
         res = oracle.cell_residual(T, 0, x, 0.0)
-        f, _ = oracle.cell_features(T, 0, x, 0.0)
-        pred = -10.0 * float(f[11:14] @ rh) * M * s ** 3 / R ** 5
+        f, norm = oracle.cell_features(T, 0, x, 0.0)
+        pred = -10.0 * float(np.einsum("abc,a,b,c->", O, rh, rh, rh)) / R ** 5
         mis.append(abs(res @ rh - pred) / abs(pred))
+        vec.append(np.linalg.norm(res / norm - f[11:14]) / np.linalg.norm(f[11:14]))
     assert mis[0] < 0.1 and 1.6 < mis[0] / mis[1] < 2.4, mis
+    assert vec[0] < 0.1 and 1.6 < vec[0] / vec[1] < 2.4, vec
