@@ -536,14 +536,14 @@ def run_gpu(args):
     # uses) goes in every step and the state it leaves comes back, with the
     # energy totals; the masses are constant and the potentials are reduced on
     # the device into the energy totals
-    fields_in = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
-    fields_out = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az")
-    host = {f: torch.empty(n, dtype=torch.float32, pin_memory=True) for f in set(fields_in) | set(fields_out)}
-    for f in host:
-        host[f].copy_(getattr(S, f).cpu())
+    # (rows x, y, z, vx, vy, vz, ax, ay, az of the System's state block: one
+    # copy each way)
+    dev_state = S.state[:9]
+    host_state = torch.empty((9, n), dtype=torch.float32, pin_memory=True)
+    host_state.copy_(dev_state.cpu())
     e_host = torch.empty(10 * M, dtype=torch.float64, pin_memory=True)
-    h2d = 4 * n * len(fields_in)
-    d2h = 4 * n * len(fields_out) + 80 * M
+    h2d = 4 * n * 9
+    d2h = 4 * n * 9 + 80 * M
     lv_host = None
     if blk:   # the levels are state of the block scheme too
         lv_host = torch.empty(n, dtype=torch.int8, pin_memory=True)
@@ -556,13 +556,11 @@ def run_gpu(args):
             flush.fill_(k & 255)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for f in fields_in:
-                getattr(S, f).copy_(host[f], non_blocking=True)
+            dev_state.copy_(host_state, non_blocking=True)
             if blk:
                 B.level.copy_(lv_host, non_blocking=True)
             step()
-            for f in fields_out:
-                host[f].copy_(getattr(S, f), non_blocking=True)
+            host_state.copy_(dev_state, non_blocking=True)
             if blk:
                 lv_host.copy_(B.level, non_blocking=True)
             e_host.copy_(energy_out, non_blocking=True)
@@ -710,7 +708,7 @@ def learned_leg(d, xs, ms, tune, flush, steps, warmup):
         e1.synchronize()
         t_net.append(e0.elapsed_time(e1))
     del feats
-    flop_row = 2 * (11 * 64 + 64 * 64 + 64 * 3)   # the network's own multiply-adds (padding not counted)
+    flop_row = 2 * (14 * 64 + 64 * 64 + 64 * 3)   # the network's own multiply-adds (padding not counted)
     tflops = net_rows * flop_row / (float(np.median(t_net[1:])) / 1e3) / 1e12
     peaks = _measured_peaks()
     bf16 = peaks.get("bf16_tflops")
@@ -718,6 +716,12 @@ def learned_leg(d, xs, ms, tune, flush, steps, warmup):
             "rows": net_rows, "flop_per_row": flop_row, "ms": float(np.median(t_net[1:])), "achieved": tflops,
             "peak": bf16 or 1900.0, "unit": "TFLOP/s", "frac": tflops / (bf16 or 1900.0), "traffic": None,
             "peak_note": "bf16_tflops of MEASURED_PEAKS.json (burst)" if bf16 else "fallback 1.9 PFLOP/s bf16"}
+    # the epilogue's special-function unit bounds this kernel before the tensor
+    # cores: one tanh per hidden activation (2 x 64 a row) at 16 results per
+    # clock per SM (152 SMs, 2.07 GHz maximum clock)
+    sfu_ms = net_rows * 2 * 64 / (16 * 152 * 2.07e9) * 1e3
+    roof["sfu_bound"] = {"ms": sfu_ms, "frac": sfu_ms / roof["ms"], "tflops_at_bound": net_rows * flop_row / sfu_ms / 1e9,
+                         "note": "time the tanh operations alone take on the SFU pipe; frac = that / measured ms"}
     del ctx
     torch.cuda.empty_cache()
     return out, roof

@@ -512,10 +512,14 @@ class System:
         pos = torch.as_tensor(pos)
         vel = torch.as_tensor(vel)
         self.n = int(pos.shape[1])
-        self.x, self.y, self.z = (pos[a].to(**f32).contiguous() for a in range(3))
-        self.vx, self.vy, self.vz = (vel[a].to(**f32).contiguous() for a in range(3))
+        # one block, rows x, y, z, vx, vy, vz, ax, ay, az, pot (each row a
+        # contiguous array): the whole state moves in one copy
+        self.state = torch.zeros((10, self.n), **f32)
+        self.x, self.y, self.z, self.vx, self.vy, self.vz, self.ax, self.ay, self.az, self.pot = self.state.unbind(0)
+        for a in range(3):
+            self.state[a].copy_(pos[a].to(**f32))
+            self.state[3 + a].copy_(vel[a].to(**f32))
         self.m = torch.as_tensor(mass).to(**f32).contiguous()
-        self.ax, self.ay, self.az, self.pot = (torch.zeros(self.n, **f32) for _ in range(4))
         self.n_chain = 0 if chain_m is None else int(len(chain_m))
         if self.n_chain:
             self.chain_m = torch.as_tensor(chain_m).to(**f64).contiguous()
