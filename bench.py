@@ -11,7 +11,7 @@ tree walk, kick, FP64 energy/momentum totals, replayed from a CUDA graph.
 Reported beside the value: the learned cell-force correction (the network is
 trained first, untimed, on samples the code generates) as a force pass at
 theta 0.8 and at theta 1.0, the plain tree's force pass at the same angles,
-and the network kernel's tensor-core roofline.
+the network kernel's tensor-core roofline, and the tree build's HBM roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--workload learned|hernquist_bh|hernquist_bh_relmac|hernquist_bh_block|hernquist_binary|plummer|ensemble]
@@ -530,6 +530,7 @@ def run_gpu(args):
                 "walk_ms": walk_ms, "walk_timing": walk_src, "flop_per_launch": float(flop),
                 "interactions_per_star": float((n_p2p + n_m2p) / max(n, 1)),
                 "walk_share_of_step": walk_ms / ms_per_step}
+    roof_build = build_roofline(ctx, d, S, stream, flush, args.steps, ms_per_step)
 
     # ---- end to end through the public API with host (pinned) buffers
     # the state a step reads (positions, velocities, the forces its first kick
@@ -608,8 +609,8 @@ def run_gpu(args):
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": float(np.mean(e2e_ms)), "ms_per_step_median": float(np.median(e2e_ms)),
                         "ms_per_step_max": float(np.max(e2e_ms))},
-                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
-                "energy_drift": energy_drift, "autotune": tuning}
+                "gpu_launches": int(launches), "roofline": roofline, "roofline_build": roof_build,
+                "cpu_baseline": cpu, "energy_drift": energy_drift, "autotune": tuning}
         if learned is not None:
             line["learned_correction"] = learned
             line["roofline_network"] = roof_net
@@ -622,6 +623,44 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------
 # learned cell-force correction: tree at theta 0.8 + network, 2^24 stars
 # ---------------------------------------------------------------------------
+def build_roofline(ctx, d, S, stream, flush, reps, ms_per_step):
+    """The tree build (bounding cube, keys, radix sort, permutation, topology,
+    groups, moments: all HBM-bound) timed alone with CUDA events on its
+    stream, an L2 flush before each, against the measured HBM copy bandwidth.
+    Algorithmic bytes per build: per star the cube's 12 B read; keys 12 B read
+    and 8 B written; each of the sort's passes (7 of 9 bits for 63-bit keys,
+    one more on the member when there are several) 12 B read + 8 B (the
+    up-sweep's key) + 12 B written; the permutation 20 B read + 16 B written;
+    the topology 8 B read; the moments 16 B read; per cell 42 B written by the
+    topology and 48 B read + 48 B written by the moments."""
+    import torch
+    off = d["offsets"] if d["offsets"] is not None else [0, S.n]
+    ev = []
+    with torch.cuda.stream(stream):
+        for k in range(max(4, reps)):
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.build_tree_members(off, S.x, S.y, S.z, S.m, stream=stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ctx.sync_status(stream=stream)
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev[1:]]))
+    n, ncell, _ = ctx.tree_sizes()
+    passes = 7 + (1 if len(off) > 2 else 0)
+    per_star = 12 + 20 + passes * 32 + 36 + 8 + 16
+    nbytes = n * per_star + ncell * (42 + 96)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    hbm = _measured_peaks().get("hbm_gbs")
+    peak = hbm or 6800.0
+    return {"bound": "hbm", "kernels": f"bounds, keys, sort ({passes} passes), gather, topology, groups, moments",
+            "ms": ms, "bytes": float(nbytes), "bytes_per_star": nbytes / max(n, 1), "cells": ncell,
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+            "share_of_step": ms / ms_per_step,
+            "peak_note": "hbm_gbs of MEASURED_PEAKS.json (copy)" if hbm else "fallback 6.8 TB/s"}
+
+
 def _measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

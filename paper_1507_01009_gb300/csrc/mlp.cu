@@ -767,26 +767,6 @@ __device__ __forceinline__ void tc_put_features(TcSmem &S, int r, const float f[
     }
 }
 
-// 16 FP32 columns of this thread's TMEM lane into r, without waiting (the
-// registers are valid after tc_ld_wait)
-__device__ __forceinline__ void tc_ld16_issue(unsigned taddr, unsigned r[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-// waits for every TMEM load this thread issued; r (the last one's registers)
-// is read only after it
-__device__ __forceinline__ void tc_ld_wait(unsigned r[16]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15])
-                 :
-                 : "memory");
-}
-
 // Two SiLUs at once. SiLU of z = v + b (v the accumulator, b the bias) is
 // h + h tanh(h) with h = z / 2 = v / 2 + b / 2 (z sigma(z) = z (1 + tanh(z / 2))
 // / 2): h and h + h t are packed FP32 FMAs (fma.rn.f32x2, one instruction for
@@ -809,41 +789,44 @@ __device__ __forceinline__ void silu_pair(float v0, float v1, float hb0, float h
     asm("mov.b64 {%0, %1}, %2;" : "=f"(s0), "=f"(s1) : "l"(o));
 }
 
-// columns c0 .. c0 + 15 (loaded into u) + half bias -> SiLU -> bfloat16 pairs into this row's TMEM lane
-// from column a_taddr (the next layer's A operand)
-__device__ __forceinline__ void tc_hidden16(const unsigned u[16], int c0, const float *hbias, unsigned a_taddr) {
-    float v[16];
+// 32 FP32 columns of this thread's TMEM lane into r, without waiting
+__device__ __forceinline__ void tc_ld32_issue(unsigned taddr, unsigned r[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+// waits for every TMEM load this thread issued; r is read only after it
+__device__ __forceinline__ void tc_ld_wait32(unsigned r[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) : : "memory");
+}
+
+// 32 columns c0 .. c0 + 31 (in u) + half bias -> SiLU -> 16 bfloat16 pairs into this row's TMEM lane
+__device__ __forceinline__ void tc_hidden32(const unsigned u[32], int c0, const float *hbias, unsigned a_taddr) {
+    float v[32];
 #pragma unroll
-    for (int j = 0; j < 16; j += 2)
+    for (int j = 0; j < 32; j += 2)
         silu_pair(__uint_as_float(u[j]), __uint_as_float(u[j + 1]), hbias[c0 + j], hbias[c0 + j + 1], v[j], v[j + 1]);
-    // this row's activations c0 .. c0 + 15 as 8 bfloat16 pairs into its TMEM lane (even k in the low half)
-    unsigned w[8];
+    unsigned w[16];
 #pragma unroll
-    for (int c = 0; c < 8; c++) w[c] = pack_bf16(v[2 * c], v[2 * c + 1]);
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+    for (int c = 0; c < 16; c++) w[c] = pack_bf16(v[2 * c], v[2 * c + 1]);
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
                  ::"r"(a_taddr + (unsigned)(c0 / 2)), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]),
-                   "r"(w[5]), "r"(w[6]), "r"(w[7])
+                   "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]),
+                   "r"(w[13]), "r"(w[14]), "r"(w[15])
                  : "memory");
 }
 
-// Accumulator columns 0 .. 63 of row r + bias -> SiLU -> bfloat16 A operand of the next layer,
-// 16 columns at a time, the TMEM load of the next 16 in flight while the
-// current 16 are processed.
-__device__ __forceinline__ void tc_hidden(TcSmem &S, unsigned tlane, int r, const float *hbias) {
+// All 64 accumulator columns of the row in flight at once (two 32-column
+// loads), then 32 SiLU pairs with no load between them.
+__device__ __forceinline__ void tc_hidden_wide(unsigned tlane, const float *hbias) {
     const unsigned at = tlane + kTcACol;
-    unsigned a[16], b[16];
-    tc_ld16_issue(tlane, a);
-    tc_ld_wait(a);
-    tc_ld16_issue(tlane + 16, b);
-    tc_hidden16(a, 0, hbias, at);
-    tc_ld_wait(b);
-    tc_ld16_issue(tlane + 32, a);
-    tc_hidden16(b, 16, hbias, at);
-    tc_ld_wait(a);
-    tc_ld16_issue(tlane + 48, b);
-    tc_hidden16(a, 32, hbias, at);
-    tc_ld_wait(b);
-    tc_hidden16(b, 48, hbias, at);
+    unsigned a[32], b[32];
+    tc_ld32_issue(tlane, a);
+    tc_ld32_issue(tlane + 32, b);
+    tc_ld_wait32(a);
+    tc_ld_wait32(b);
+    tc_hidden32(a, 0, hbias, at);
+    tc_hidden32(b, 32, hbias, at);
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
@@ -906,9 +889,9 @@ __device__ __forceinline__ void tc_teardown(TcSmem &S, bool ok, unsigned phase) 
 __device__ __forceinline__ bool tc_tile(TcSmem &S, unsigned tmem, unsigned tlane, int r, unsigned &phase,
                                         float out[kOut]) {
     if (!tc_layer(S, 1, tmem, phase)) return false;
-    tc_hidden(S, tlane, r, S.b1);
+    tc_hidden_wide(tlane, S.b1);
     if (!tc_layer(S, 2, tmem, phase)) return false;
-    tc_hidden(S, tlane, r, S.b2);
+    tc_hidden_wide(tlane, S.b2);
     if (!tc_layer(S, 3, tmem, phase)) return false;
     float v[16];
     tc_ld16(tlane, v);
@@ -989,6 +972,7 @@ __global__ void __launch_bounds__(kTcRows) mlp_forward_tc_k(MlpBlock P, int64_t 
     }
     tc_teardown(S, ok, phase);
 }
+
 
 // ---------------------------------------------------------------------------
 // correction of recorded (group, cell) pairs, evaluated at the group centre
@@ -1083,13 +1067,13 @@ __global__ void mlp_apply_k(const int4 *groups, const int *ngroup, const int *pe
     }
 }
 
-// Dynamic shared memory that keeps at most kTcCtas CTAs of `kern` on an SM.
+// Dynamic shared memory that keeps at most CTAS CTAs of `kern` on an SM.
 // Each CTA allocates kTcCols of the SM's 512 TMEM columns; a further CTA
 // that registers and shared memory would still admit would wait in
 // tcgen05.alloc until another CTA on its SM finishes, stretching the kernel's
-// tail. Padding the CTA's shared memory just past the (kTcCtas + 1)-CTA share
-// makes the scheduler place at most kTcCtas. Returns -1 on a CUDA error.
-template <typename K>
+// tail. Padding the CTA's shared memory just past the (CTAS + 1)-CTA share
+// makes the scheduler place at most CTAS. Returns -1 on a CUDA error.
+template <int CTAS, typename K>
 static int tc_pad_smem(K kern) {
     static int cached = -2;
     if (cached != -2) return cached;
@@ -1100,7 +1084,7 @@ static int tc_pad_smem(K kern) {
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
         cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
         return -1;
-    int pad = std::max(0, per_sm / (kTcCtas + 1) - reserved - (int)fa.sharedSizeBytes + 128);
+    int pad = std::max(0, per_sm / (CTAS + 1) - reserved - (int)fa.sharedSizeBytes + 128);
     pad = (pad + 127) & ~127;
     for (int k = 0; k < 64; k++, pad += 128) {
         if (pad > 48 * 1024 &&
@@ -1108,7 +1092,7 @@ static int tc_pad_smem(K kern) {
             return -1;
         int blocks = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kTcRows, pad) != cudaSuccess) return -1;
-        if (blocks <= kTcCtas) break;
+        if (blocks <= CTAS) break;
     }
     cached = pad;
     return pad;
@@ -1171,8 +1155,9 @@ rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                   cudaSuccess)
         return RV_E_CUDA;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kTcRows - 1) / kTcRows, (int64_t)sms * kTcCtas));
-    const int pad = tc_pad_smem(mlp_forward_tc_k);
+    const int64_t ntile = (n + kTcRows - 1) / kTcRows;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (int64_t)sms * kTcCtas));
+    const int pad = tc_pad_smem<kTcCtas>(mlp_forward_tc_k);
     if (pad < 0) return RV_E_CUDA;
     mlp_forward_tc_k<<<grid, kTcRows, pad, s>>>(P, n, x, y);
     return cudaGetLastError() == cudaSuccess ? RV_OK : RV_E_CUDA;
@@ -1360,7 +1345,7 @@ rv_status rv_tree_forces_mlp(rv_ctx *c, const void *params, float theta, float t
                                                                                            c->w.coct);
     count_launch(c);
     const int grid = std::max(1, std::min(ceil_div(pair_cap, kTcRows), c->num_sms * kTcCtas));
-    const int pad = tc_pad_smem(mlp_pairs_tc_k);
+    const int pad = tc_pad_smem<kTcCtas>(mlp_pairs_tc_k);
     if (pad < 0) return set_err(c, RV_E_CUDA, "network kernel attributes");
     mlp_pairs_tc_k<<<grid, kTcRows, pad, s>>>(P, cell_geo(c, ncell), c->w.groups, reinterpret_cast<const int2 *>(pairs),
                                             npairs, pair_cap, eps_star, gcorr, c->w.st);

@@ -334,6 +334,12 @@ class Context:
                                               *[_ptr(o) for o in out], _stream(stream)))
         return tuple(out)
 
+    def tree_sizes(self, stream=None):
+        """(stars, cells, groups) of the last tree (rv_get_tree, no copies)."""
+        v = rv_tree_view()
+        self._check(self.L.rv_get_tree(self.h, C.byref(v), _stream(stream)))
+        return int(v.n), int(v.ncell), int(v.ngroup)
+
     def tree_view(self, stream=None) -> dict:
         """Copies of the last tree's arrays (as CUDA tensors)."""
         import torch

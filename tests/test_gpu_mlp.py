@@ -11,7 +11,7 @@ import pytest
 
 import ics
 import oracle
-from gpu_helpers import gpu_tree, hernquist32
+from gpu_helpers import gpu_cells_as_oracle, gpu_tree, hernquist32, sorted_groups
 
 pytestmark = pytest.mark.gpu
 OUT = os.environ.get("RV_TEST_REPORT_DIR", "")
@@ -300,22 +300,31 @@ def test_correction_applied_as_the_oracle_says(rvmod, boxed):
 
 @pytest.mark.slow
 def test_full_size_learned_workload(rvmod):
-    """The 2^24-star Hernquist workload of the learned correction, in the
-    benchmark's launch configuration (theta 0.8, theta_rec 0.7, n_leaf 32,
-    group 64): the plain tree on sampled stars against the oracle tree, and
-    the learned pass adding one correction per group on top of it."""
+    """The 2^24-star Hernquist galaxy of the default benchmark, in its launch
+    configuration (theta 0.8, n_leaf 24, group 64, tile 96): keys,
+    permutation, cells and groups bit-exact against the oracle's tree, the
+    plain tree on sampled stars against the oracle tree, and the learned pass
+    (theta_rec 0.7) adding one correction per group on top of it."""
     import torch
     n = 1 << 24
     w = ics.hernquist(n, 5)
     p32 = w.pos.astype(np.float32)
     m32 = w.mass.astype(np.float32)
     eps = float(np.float32(0.005))
-    ctx = rvmod.Context(n, theta=0.8, eps_star=eps, n_leaf=32, group=64)
+    ctx = rvmod.Context(n, theta=0.8, eps_star=eps, n_leaf=24, group=64, tile=96)
     gpu_tree(ctx, p32, m32)
     plain = np.stack([u.cpu().numpy() for u in ctx.tree_forces(theta=0.8, eps_star=eps)[:3]]).astype(np.float64)
     ctx.sync_status()
+    T = oracle.Tree(p32, m32, 24, 64)
+    v = ctx.tree_view()
+    np.testing.assert_array_equal(v["keys"].cpu().numpy().view(np.uint64), T.key)
+    np.testing.assert_array_equal(v["perm"].cpu().numpy(), T.perm)
+    assert v["ncell"] == T.ncell and v["ngroup"] == T.ngroup
+    np.testing.assert_array_equal(gpu_cells_as_oracle(v), T.cells)
+    np.testing.assert_array_equal(sorted_groups(v["groups"].cpu().numpy()), sorted_groups(T.groups))
+    del v
     tg = ics.subsample(n, 256, seed=51)
-    ao, _, _, _ = oracle.Tree(p32, m32, 32, 64).forces(0.8, eps, targets=tg)
+    ao, _, _, _ = T.forces(0.8, eps, targets=tg)
     e = oracle.rel_err(plain[:, tg], ao[:, tg])
     assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
     mlp = rvmod.Mlp(seed=8)
