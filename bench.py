@@ -755,10 +755,10 @@ def learned_leg(d, xs, ms, tune, flush, steps, warmup):
             "rows": net_rows, "flop_per_row": flop_row, "ms": float(np.median(t_net[1:])), "achieved": tflops,
             "peak": bf16 or 1900.0, "unit": "TFLOP/s", "frac": tflops / (bf16 or 1900.0), "traffic": None,
             "peak_note": "bf16_tflops of MEASURED_PEAKS.json (burst)" if bf16 else "fallback 1.9 PFLOP/s bf16"}
-    # the epilogue's special-function unit bounds this kernel before the tensor
-    # cores: one tanh per hidden activation (2 x 64 a row) at 16 results per
-    # clock per SM (152 SMs, 2.07 GHz maximum clock)
-    sfu_ms = net_rows * 2 * 64 / (16 * 152 * 2.07e9) * 1e3
+    # the epilogue's special-function unit: one tanh per hidden activation
+    # (2 x 64 a row) at one warp instruction (32 results) per clock per SM, the
+    # XU pipe's peak as ncu counts it on GB300 (152 SMs, 2.07 GHz maximum clock)
+    sfu_ms = net_rows * 2 * 64 / (32 * 152 * 2.07e9) * 1e3
     roof["sfu_bound"] = {"ms": sfu_ms, "frac": sfu_ms / roof["ms"], "tflops_at_bound": net_rows * flop_row / sfu_ms / 1e9,
                          "note": "time the tanh operations alone take on the SFU pipe; frac = that / measured ms"}
     del ctx
