@@ -217,15 +217,71 @@ __device__ __forceinline__ uint32_t grid_coord(float v, double lo, double scale)
     return (uint32_t)__double2uint_rz(t);
 }
 
+// The same q decided in FP32 where FP32 can decide it (GB300's FP64 rate is
+// a small fraction of its FP32 rate, and the FP64 rule bound the key kernel).
+// d = x - min is formed exactly as an unevaluated pair of floats dh + dl
+// (Knuth's two-sum), scale as the pair sh + sl (sl the FP32 rounding of the
+// FP64 difference scale - sh, itself exact), and d * scale as ph + c: ph =
+// dh sh rounded, its rounding error recovered exactly by an FMA, the cross
+// terms dh sl and dl sh added by FMAs, dl sl left out. Then
+// |ph + c - d scale| < 2^-45 d scale < 2^-23 while d scale < 2^22, the FP64
+// rule's two roundings move its t by at most 2^-52 t < 2^-30 from d scale, and
+// r = (ph - floor(ph)) + c carries one more rounding (< 2^-23). So when r lies
+// farther than 2^-20 from every integer, floor(t) = floor(ph) + floor(r); next
+// to an integer (t at or near a grid boundary, d = 0), or out of range or not
+// finite, the FP64 rule is evaluated as written. Integers below 2^22 are exact
+// in FP32.
+struct GridAxis {
+    double lo, scale;
+    float lo32, sh, sl;
+    bool fast;   // lo is an FP32 value (the minimum of FP32 coordinates) and the split is finite
+};
+
+__device__ __forceinline__ GridAxis grid_axis(double lo, double scale) {
+    GridAxis g;
+    g.lo = lo;
+    g.scale = scale;
+    g.lo32 = __double2float_rn(lo);
+    g.sh = __double2float_rn(scale);
+    g.sl = __double2float_rn(__dsub_rn(scale, (double)g.sh));
+    g.fast = (double)g.lo32 == lo && isfinite(g.sh) && isfinite(g.sl);
+    return g;
+}
+
+__device__ __forceinline__ uint32_t grid_coord_fast(float v, const GridAxis &g) {
+    if (g.fast) {
+        const float b = -g.lo32;
+        const float dh = __fadd_rn(v, b);
+        const float bb = __fsub_rn(dh, v);
+        const float dl = __fadd_rn(__fsub_rn(v, __fsub_rn(dh, bb)), __fsub_rn(b, bb));
+        const float ph = __fmul_rn(dh, g.sh);
+        const float pl = __fmaf_rn(dh, g.sh, -ph);
+        const float c = __fmaf_rn(dh, g.sl, __fmaf_rn(dl, g.sh, pl));
+        if (ph >= 0.f && ph < 4194304.f) {
+            const float f = floorf(ph);
+            const float r = __fadd_rn(__fsub_rn(ph, f), c);
+            constexpr float M = 9.5367431640625e-07f;   // 2^-20
+            float q = -2.f;
+            if (r > M && r < 1.f - M) q = f;
+            else if (r > 1.f + M && r < 2.f - M) q = f + 1.f;
+            else if (r > M - 1.f && r < -M) q = f - 1.f;
+            if (q >= 0.f) return q >= 2097151.f ? 2097151u : (uint32_t)q;
+        }
+    }
+    return grid_coord(v, g.lo, g.scale);
+}
+
 // Blocks (bx, m): member m's stars with member m's bounding cube.
 __global__ void keys_k(const int64_t *moff, int bpm, const float *x, const float *y, const float *z,
                        const double *mbounds, uint64_t *key) {
     const int m = blockIdx.y;
-    const double lx = mbounds[5 * m], ly = mbounds[5 * m + 1], lz = mbounds[5 * m + 2], sc = mbounds[5 * m + 4];
+    const double sc = mbounds[5 * m + 4];
+    const GridAxis gx = grid_axis(mbounds[5 * m], sc), gy = grid_axis(mbounds[5 * m + 1], sc),
+                   gz = grid_axis(mbounds[5 * m + 2], sc);
     const int64_t s = moff[m], e = moff[m + 1];
     for (int64_t i = s + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (int64_t)bpm * blockDim.x) {
-        uint64_t k = spread3(grid_coord(x[i], lx, sc)) | (spread3(grid_coord(y[i], ly, sc)) << 1) |
-                     (spread3(grid_coord(z[i], lz, sc)) << 2);
+        uint64_t k = spread3(grid_coord_fast(x[i], gx)) | (spread3(grid_coord_fast(y[i], gy)) << 1) |
+                     (spread3(grid_coord_fast(z[i], gz)) << 2);
         key[i] = k;
     }
 }

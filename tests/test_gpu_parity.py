@@ -83,6 +83,46 @@ def test_tree_bit_exact(rvmod, kind, n, n_leaf, G):
     np.testing.assert_array_equal(sorted_groups(v["groups"].cpu().numpy()), sorted_groups(T.groups))
 
 
+def _adversarial_coords(seed, lo, hi):
+    """FP32 coordinates (3, n) that sit on, and one or two FP32 steps either
+    side of, the quantisation grid's cell boundaries (exactly on them when the
+    extent hi - lo is a power of two), with tiny magnitudes and a negative
+    minimum: the cases in which the key's floor is decided next to an
+    integer."""
+    g = ics.rng(seed)
+    lo = np.float32(lo)
+    hi = np.float32(hi)
+    L = float(hi) - float(lo)
+    k = g.integers(0, 1 << 21, 30000)
+    on = (float(lo) + k * (L / 2.0 ** 21)).astype(np.float32)
+    near = np.concatenate([on, np.nextafter(on, np.float32(np.inf)), np.nextafter(on, np.float32(-np.inf)),
+                           np.nextafter(np.nextafter(on, np.float32(np.inf)), np.float32(np.inf))])
+    extra = np.array([lo, hi, 0.0, 1e-30, -1e-30, 1e-38, np.float32(2.0 ** -149), 1.0, -1.0, 3.3333333],
+                     dtype=np.float32)
+    v = np.concatenate([near, extra, g.uniform(float(lo), float(hi), 20000).astype(np.float32)])
+    v = np.clip(v, lo, hi).astype(np.float32)
+    pos = np.stack([v, g.permutation(v), g.permutation(v)]).astype(np.float32)
+    pos[1, 0], pos[2, 0] = lo, lo       # every axis reaches the same minimum and extent
+    pos[1, 1], pos[2, 1] = hi, hi
+    return pos
+
+
+@pytest.mark.parametrize("seed,lo,hi", [(1, -4.0, 12.0), (2, -3.7, 11.3), (3, 0.0, 1.0)])
+def test_keys_exact_next_to_grid_boundaries(rvmod, seed, lo, hi):
+    """Morton keys bit-exact against the oracle's FP64 quantisation on
+    coordinates placed on and next to the grid's cell boundaries."""
+    p32 = _adversarial_coords(seed, lo, hi)
+    n = p32.shape[1]
+    m32 = np.full(n, 1.0 / n, dtype=np.float32)
+    ctx = _ctx(rvmod, n)
+    gpu_tree(ctx, p32, m32)
+    v = ctx.tree_view()
+    ctx.sync_status()
+    k = np.zeros(n, dtype=np.uint64)
+    k[v["perm"].cpu().numpy()] = v["keys"].cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(k, oracle.keys(p32))
+
+
 def test_tiny_golden_tree_on_gpu(rvmod):
     """The hand-derived five-point tree (tests/golden/tiny_tree.txt)."""
     from test_oracle import _read_sections
