@@ -627,12 +627,13 @@ def build_roofline(ctx, d, S, stream, flush, reps, ms_per_step):
     """The tree build (bounding cube, keys, radix sort, permutation, topology,
     groups, moments: all HBM-bound) timed alone with CUDA events on its
     stream, an L2 flush before each, against the measured HBM copy bandwidth.
-    Algorithmic bytes per build: per star the cube's 12 B read; keys 12 B read
-    and 8 B written; each of the sort's passes (7 of 9 bits for 63-bit keys,
-    one more on the member when there are several) 12 B read + 8 B (the
-    up-sweep's key) + 12 B written; the permutation 20 B read + 16 B written;
-    the topology 8 B read; the moments 16 B read; per cell 42 B written by the
-    topology and 48 B read + 48 B written by the moments."""
+    Algorithmic bytes per build: per star the cube's 12 B read; keys 16 B read
+    and 8 B (key) + 16 B (the packed star) written; each of the sort's passes
+    (7 of 9 bits for 63-bit keys, one more on the member when there are
+    several) 12 B read + 8 B (the up-sweep's key) + 12 B written; the
+    permutation 4 B + 16 B read and 16 B written; the topology 8 B read; the
+    moments 16 B read; per cell 42 B written by the topology and 48 B read +
+    48 B written by the moments."""
     import torch
     off = d["offsets"] if d["offsets"] is not None else [0, S.n]
     ev = []
@@ -649,7 +650,7 @@ def build_roofline(ctx, d, S, stream, flush, reps, ms_per_step):
     ms = float(np.median([a.elapsed_time(b) for a, b in ev[1:]]))
     n, ncell, _ = ctx.tree_sizes()
     passes = 7 + (1 if len(off) > 2 else 0)
-    per_star = 12 + 20 + passes * 32 + 36 + 8 + 16
+    per_star = 12 + 40 + passes * 32 + 36 + 8 + 16
     nbytes = n * per_star + ncell * (42 + 96)
     gbs = nbytes / (ms / 1e3) / 1e9
     hbm = _measured_peaks().get("hbm_gbs")

@@ -271,18 +271,23 @@ __device__ __forceinline__ uint32_t grid_coord_fast(float v, const GridAxis &g) 
     return grid_coord(v, g.lo, g.scale);
 }
 
-// Blocks (bx, m): member m's stars with member m's bounding cube.
+// Blocks (bx, m): member m's stars with member m's bounding cube. Each star's
+// (x, y, z, m) is also packed into one float4 (caller order), so that the
+// gather into key order reads one 16-byte record per star instead of four
+// scattered 4-byte values (each costing a 32-byte sector).
 __global__ void keys_k(const int64_t *moff, int bpm, const float *x, const float *y, const float *z,
-                       const double *mbounds, uint64_t *key) {
+                       const float *mass, const double *mbounds, uint64_t *key, float4 *xyzm) {
     const int m = blockIdx.y;
     const double sc = mbounds[5 * m + 4];
     const GridAxis gx = grid_axis(mbounds[5 * m], sc), gy = grid_axis(mbounds[5 * m + 1], sc),
                    gz = grid_axis(mbounds[5 * m + 2], sc);
     const int64_t s = moff[m], e = moff[m + 1];
     for (int64_t i = s + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e; i += (int64_t)bpm * blockDim.x) {
-        uint64_t k = spread3(grid_coord_fast(x[i], gx)) | (spread3(grid_coord_fast(y[i], gy)) << 1) |
-                     (spread3(grid_coord_fast(z[i], gz)) << 2);
+        const float xi = x[i], yi = y[i], zi = z[i];
+        uint64_t k = spread3(grid_coord_fast(xi, gx)) | (spread3(grid_coord_fast(yi, gy)) << 1) |
+                     (spread3(grid_coord_fast(zi, gz)) << 2);
         key[i] = k;
+        xyzm[i] = make_float4(xi, yi, zi, mass[i]);
     }
 }
 
@@ -435,12 +440,9 @@ rv_status radix_sort(rv_ctx *c, int64_t n, int passes, uint64_t **keys, int **id
 // ---------------------------------------------------------------------------
 // gather (x, y, z, m) into key order
 // ---------------------------------------------------------------------------
-__global__ void gather_k(int64_t n, const int *perm, const float *x, const float *y, const float *z,
-                         const float *m, float4 *pos) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int j = perm[i];
-        pos[i] = make_float4(x[j], y[j], z[j], m[j]);
-    }
+__global__ void gather_k(int64_t n, const int *perm, const float4 *xyzm, float4 *pos) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pos[i] = xyzm[perm[i]];
 }
 
 // ---------------------------------------------------------------------------
@@ -835,14 +837,17 @@ rv_status build_tree(rv_ctx *c, int n_members, const int64_t *offsets, const flo
     bounds_final_k<<<M, 32, 0, s>>>(bpm, w.bpart, w.mbounds, w.st);
     count_launch(c);
     const int kpm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(big, 256), (int64_t)c->num_sms * 8 / M + 1));
-    keys_k<<<dim3(kpm, M), 256, 0, s>>>(w.moff, kpm, x, y, z, w.mbounds, w.key_a);
+    // the packed stars live in the group records' space until the gather: the
+    // groups are written after it (32 B per star of room there, 16 needed)
+    float4 *xyzm = reinterpret_cast<float4 *>(w.groups);
+    keys_k<<<dim3(kpm, M), 256, 0, s>>>(w.moff, kpm, x, y, z, m, w.mbounds, w.key_a, xyzm);
     count_launch(c);
     uint64_t *skey;
     int *perm;
     if ((r = radix_sort(c, n, 7, &skey, &perm, true, s, true)) != RV_OK) return r;
     w.skey = skey;
     w.perm = perm;
-    gather_k<<<grid_for(c, n, 256), 256, 0, s>>>(n, perm, x, y, z, m, w.pos);
+    gather_k<<<grid_for(c, n, 256), 256, 0, s>>>(n, perm, xyzm, w.pos);
     count_launch(c);
     // topology
     int nblk = ceil_div(n, kTopoBlock);
