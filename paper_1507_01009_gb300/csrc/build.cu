@@ -309,11 +309,15 @@ __global__ void __launch_bounds__(kSortThreads) sort_upsweep_k(int64_t n, const 
     for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) h[b] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * kSortTile;
+    int d[kSortItems];
 #pragma unroll
-    for (int k = 0; k < kSortItems; k++) {
-        int64_t j = base + k * kSortThreads + threadIdx.x;
-        if (j < n) atomicAdd(&h[sort_digit(key, idx, j, shift, moff, M)], 1);
+    for (int k = 0; k < kSortItems; k++) {   // the tile's loads first
+        const int64_t j = base + k * kSortThreads + threadIdx.x;
+        d[k] = j < n ? sort_digit(key, idx, j, shift, moff, M) : -1;
     }
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++)
+        if (d[k] >= 0) atomicAdd(&h[d[k]], 1);
     __syncthreads();
     for (int b = threadIdx.x; b < kSortBins; b += kSortThreads) hist[(int64_t)b * ntiles + blockIdx.x] = h[b];
 }
@@ -344,13 +348,21 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, cons
     const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
     const int64_t base = tile0 + wid * (32 * kSortItems);
     uint64_t kk[kSortItems];
-    int digit[kSortItems], rank[kSortItems];
+    int ix[kSortItems], digit[kSortItems], rank[kSortItems];
+    // every load of the tile first, so that their latencies overlap (the
+    // ranking rounds below synchronise the warp)
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
-        int64_t j = base + r * 32 + lane;
-        bool ok = j < n;
+        const int64_t j = base + r * 32 + lane;
+        const bool ok = j < n;
         kk[r] = ok ? key_in[j] : 0ull;
-        int d = ok ? sort_digit(key_in, idx_in, j, shift, moff, M) : kSortBins;
+        ix[r] = ok ? (idx_in ? idx_in[j] : (int)j) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        const int64_t j = base + r * 32 + lane;
+        int d = kSortBins;
+        if (j < n) d = moff ? member_of(moff, M, (int64_t)ix[r]) : (int)((kk[r] >> shift) & (kSortBins - 1));
         digit[r] = d;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int before = (d < kSortBins) ? cnt[wid][d] : 0;
@@ -395,7 +407,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_downsweep_k(int64_t n, cons
             const int d = digit[r];
             const int slot = lstart[d] + cnt[wid][d] + rank[r];
             skey[slot] = kk[r];
-            sidx[slot] = idx_in ? idx_in[j] : (int)j;
+            sidx[slot] = ix[r];
             sdig[slot] = (unsigned short)d;
         }
     }
