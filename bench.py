@@ -574,6 +574,10 @@ def run_gpu(args):
     ctx.sync_status(stream=stream)
     e2e_val = ws * (upd / args.steps if blk else n) / (float(np.mean(e2e_ms)) / 1e3)
 
+    separate = None
+    if d["name"] == "ensemble" and rank == 0:
+        separate = ensemble_separate(d, tune, args.steps, args.warmup, flush)
+
     learned, roof_net = None, None
     if d["name"] == "learned" and rank == 0 and not args.no_learned:
         del S, ctx
@@ -614,6 +618,9 @@ def run_gpu(args):
                         "ms_per_step_max": float(np.max(e2e_ms))},
                 "gpu_launches": int(launches), "roofline": roofline, "roofline_build": roof_build,
                 "cpu_baseline": cpu, "energy_drift": energy_drift, "autotune": tuning}
+        if separate is not None:
+            line["batched_vs_separate"] = {"batched_particles_per_s": value, "batched_ms_per_step": ms_per_step,
+                                           "separate": separate, "speedup": value / separate["particles_per_s"]}
         if learned is not None:
             line["learned_correction"] = learned
             line["roofline_network"] = roof_net
@@ -626,6 +633,53 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------
 # learned cell-force correction: tree at theta 0.8 + network, 2^24 stars
 # ---------------------------------------------------------------------------
+def ensemble_separate(d, tune, steps, warmup, flush):
+    """The ensemble's members stepped one after another, each as its own
+    single-galaxy system (its own context, the same tree parameters, tile and
+    criterion, its own captured KDK step with its SMBH pair and perturbers):
+    the plain tree the batched form is compared with, in particles/s over the
+    same stars. Timed like the batched steps (CUDA events on the launching
+    stream, L2 flush before each step of all members)."""
+    import torch
+    from paper_1507_01009_gb300 import rv
+    off = d["offsets"]
+    M = len(off) - 1
+    nch = len(d["chain_m"]) // M
+    eps = float(np.float32(d["eps"]))
+    stream = torch.cuda.Stream()
+    members = []
+    for k in range(M):
+        a, b = int(off[k]), int(off[k + 1])
+        ctx = rv.Context(b - a, theta=d["theta"], eps_star=eps, mac=d["mac"], alpha=d["alpha"], **tune)
+        S = rv.System(d["pos"][:, a:b], d["vel"][:, a:b], d["mass"][a:b], chain_m=d["chain_m"][k * nch:(k + 1) * nch],
+                      chain_x=d["chain_x"][k * nch:(k + 1) * nch], chain_v=d["chain_v"][k * nch:(k + 1) * nch],
+                      pert_mode=d["pert_mode"], pert_radius=d["pert_radius"], pert_k=d["pert_k"])
+        members.append((ctx, S, torch.zeros(10, dtype=torch.float64, device="cuda")))
+    with torch.cuda.stream(stream):
+        for ctx, S, eo in members:
+            ctx.system_forces(S, stream=stream)
+        for _ in range(max(3, warmup)):
+            for ctx, S, eo in members:
+                ctx.kdk_step_graph(S, d["dt"], 1, energy_out=eo, stream=stream)
+    torch.cuda.synchronize()
+    ev = []
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(k & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for ctx, S, eo in members:
+                ctx.kdk_step_graph(S, d["dt"], 1, energy_out=eo, stream=stream)
+            e1.record(stream)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    for ctx, S, eo in members:
+        ctx.sync_status(stream=stream)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    return {"particles_per_s": d["n"] / (ms / 1e3), "ms_per_step": ms, "members": M,
+            "how": "each member its own context and captured step, members one after another on one stream"}
+
+
 def build_roofline(ctx, d, S, stream, flush, reps, ms_per_step):
     """The tree build (bounding cube, keys, radix sort, permutation, topology,
     groups, moments: all HBM-bound) timed alone with CUDA events on its
