@@ -104,6 +104,7 @@ size_t rv_direct_fp64_scratch_bytes(int64_t nt) {
 rv_status rv_direct_fp64(int64_t n, const double *x, const double *y, const double *z, const double *m,
                          const double *eps, int64_t nt, const int64_t *targets, double *ax, double *ay, double *az,
                          double *pot, void *scratch, size_t scratch_bytes, void *stream) {
+    NvtxRange nvtx_range("rv_direct_fp64");
     if (n < 1 || nt < 0 || !x || !y || !z || !m || !eps) return RV_E_INVAL;
     if (nt == 0) return RV_OK;
     if (!targets || !ax || !ay || !az || !pot || !scratch) return RV_E_INVAL;

@@ -1147,6 +1147,7 @@ rv_status rv_mlp_init(void *params, uint64_t seed, void *stream) {
 }
 
 rv_status rv_mlp_forward(const void *params, int64_t n, const float *x, float *y, void *stream) {
+    NvtxRange nvtx_range("rv_mlp_forward");
     if (!params || n < 0 || (n > 0 && (!x || !y))) return RV_E_INVAL;
     if (n == 0) return RV_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1189,6 +1190,7 @@ rv_status rv_wait_selftest(int64_t limit_cycles, int32_t arrive, int32_t *gave_u
 
 rv_status rv_mlp_gradient(const void *params, int64_t n, const float *x, const float *t, float *grad, float *loss,
                           void *scratch, size_t scratch_bytes, void *stream) {
+    NvtxRange nvtx_range("rv_mlp_gradient");
     if (!params || n <= 0 || !x || !t || !grad || !scratch) return RV_E_INVAL;
     if (scratch_bytes < rv_mlp_scratch_bytes(n)) return RV_E_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1223,6 +1225,7 @@ size_t rv_mlp_train_scratch_bytes(int32_t batch) {
 
 rv_status rv_mlp_train(void *params, const rv_mlp_train_cfg *cfg, float *losses, void *scratch,
                        size_t scratch_bytes, void *stream) {
+    NvtxRange nvtx_range("rv_mlp_train");
     if (!params || !cfg || !scratch) return RV_E_INVAL;
     const rv_mlp_train_cfg &C = *cfg;
     if (C.n < 1 || !C.x || !C.t || C.steps < 0 || C.batch < 1 || C.step0 < 1 || !(C.lr >= 0.f) ||
@@ -1302,6 +1305,7 @@ rv_status rv_mlp_load(void *params, const void *host, size_t bytes, void *stream
 
 rv_status rv_mlp_samples(rv_ctx *c, float theta, float eps_star, int64_t n_samples, uint64_t seed, float *x,
                          float *t, int32_t *pairs, void *stream) {
+    NvtxRange nvtx_range("rv_mlp_samples");
     if (!c) return RV_E_INVAL;
     if (!c->ws) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (!c->built || c->n == 0) return set_err(c, RV_E_NOTBUILT, "samples need a built, non-empty tree");
@@ -1324,6 +1328,7 @@ rv_status rv_mlp_samples(rv_ctx *c, float theta, float eps_star, int64_t n_sampl
 rv_status rv_tree_forces_mlp(rv_ctx *c, const void *params, float theta, float theta_rec, float eps_star, float *ax,
                              float *ay, float *az, float *pot, int32_t *pairs, int32_t pair_cap, int32_t *npairs,
                              float *gcorr, void *stream) {
+    NvtxRange nvtx_range("rv_tree_forces_mlp");
     if (!c) return RV_E_INVAL;
     if (!c->ws) return set_err(c, RV_E_WORKSPACE, "no workspace");
     if (!c->built) return set_err(c, RV_E_NOTBUILT, "rv_tree_forces_mlp before a build");
