@@ -55,3 +55,23 @@ def test_smbh_setups():
     assert -0.01 / (2 * E) == pytest.approx(0.01, rel=1e-12)        # semi-major axis
     sizes = ics.ensemble_sizes()
     assert sizes.shape == (64,) and sizes.min() >= 8192 and sizes.max() <= 524288
+
+
+def test_hernquist_constants_the_paper_prints():
+    """Sect. 3's model in code units (G = M = a = 1): the half-mass radius
+    1 + sqrt(2) = 2.41 and the circular speed 0.28 at r = 0.1 that the paper
+    quotes, from the generator's density by quadrature (not from the
+    enclosed-mass formula the sampler inverts), and the sample's mass
+    fraction inside the half-mass radius (truncated at u = 0.99: 0.5 / 0.99)."""
+    from scipy.integrate import quad
+
+    def mass(r):
+        return quad(lambda s: 4 * math.pi * s * s * float(ics.hernquist_density(s)), 0, r, limit=200)[0]
+
+    r_half = 1 + math.sqrt(2)
+    assert mass(r_half) == pytest.approx(0.5, rel=1e-9)
+    assert r_half == pytest.approx(2.41, abs=0.005)
+    assert math.sqrt(mass(0.1) / 0.1) == pytest.approx(0.28, abs=0.01)
+    p = ics.hernquist(1 << 16, seed=3)
+    frac = float((np.linalg.norm(p.pos, axis=0) < r_half).mean())
+    assert frac == pytest.approx(0.5 / 0.99, abs=0.01)
