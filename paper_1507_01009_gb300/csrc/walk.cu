@@ -120,7 +120,7 @@ constexpr int kCellPairF4 = 5, kStarPairF4 = 2;
 constexpr int kAccWords = 16 * 32;
 constexpr int kP2PUnroll = RV_P2P_UNROLL, kM2PUnroll = RV_M2P_UNROLL;
 __host__ __device__ inline size_t warp_staging_bytes(int tile) {
-    return (size_t)kStackCap * 4 + 32 * 4 + (size_t)(tile + 32) / 2 * 16 * (kCellPairF4 + kStarPairF4);
+    return (size_t)kStackCap * 4 + 96 * 4 + (size_t)(tile + 32) / 2 * 16 * (kCellPairF4 + kStarPairF4);
 }
 __host__ __device__ inline size_t warp_smem_bytes(int tile) { return warp_staging_bytes(tile) + 4 * kAccWords; }
 
@@ -452,7 +452,8 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
     const int T = A.tile;
     int *stack = reinterpret_cast<int *>(wsm);
     int *lane_cell = stack + kStackCap;
-    float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 32);
+    int *lf_first = lane_cell + 32, *lf_start = lane_cell + 64;   // a pass's opened leaves
+    float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 96);
     float4 *p2p = m2p + kCellPairF4 * ((T + 32) / 2);
     const unsigned lt = lanemask_lt();
     const int ncell = G.ncell;
@@ -574,17 +575,37 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                 }
             }
         }
-        // opened leaves: stage their stars relative to g
-        unsigned lm = __ballot_sync(0xffffffffu, leaf);
-        while (lm) {
-            int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            int f = __shfl_sync(0xffffffffu, lk.z, src);
-            int end = __shfl_sync(0xffffffffu, lk.w, src);
-            for (int o = f; o < end; o += 32) {
-                int cc = min(32, end - o);
+        // opened leaves: stage their stars relative to g, leaves in lane order
+        // and stars in order within each (the order the tiles take them), 32
+        // stars a round whichever leaves they come from, so that the loads of
+        // a pass's leaves overlap instead of following one another
+        const unsigned lm = __ballot_sync(0xffffffffu, leaf);
+        if (lm) {
+            const int cnt = leaf ? lk.w - lk.z : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int nl = __popc(lm);
+            if (leaf) {
+                const int k = __popc(lm & lt);
+                lf_first[k] = lk.z;
+                lf_start[k] = incl - cnt;
+            }
+            __syncwarp();
+            for (int base = 0; base < total; base += 32) {
+                const int idx = base + lane, cc = min(32, total - base);
                 if (lane < cc) {
-                    float4 s = __ldg(&A.pos[o + lane]);
+                    // the leaf holding star idx of the pass: the last one starting at or before idx
+                    int lo = 0, hi = nl - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (lf_start[mid] <= idx) lo = mid; else hi = mid - 1;
+                    }
+                    const float4 s = __ldg(&A.pos[lf_first[lo] + (idx - lf_start[lo])]);
                     const int e = np + lane;
                     *staged(p2p, kStarPairF4, e, 0) = s.x - g[0];
                     *staged(p2p, kStarPairF4, e, 1) = s.y - g[1];
