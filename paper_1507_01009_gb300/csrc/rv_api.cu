@@ -99,6 +99,7 @@ size_t layout(int64_t n_max, const rv_config &cfg, char *base, Workspace *w, int
     t.bpart = (float *)take(4 * 6 * 2048);
     t.xmem = (int *)take(4 * kExtraTotal);
     t.npert = (int *)take(4 * kMaxMembers);
+    t.gstack = (int *)take(4 * (size_t)kStackSpillWarps * kStackSpill);
     t.st = (DevState *)take(sizeof(DevState));
     if (w) *w = t;
     return off;

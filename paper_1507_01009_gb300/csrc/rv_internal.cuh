@@ -26,6 +26,9 @@ constexpr int kScanChunk = 2048;        // elements per scan block
 constexpr int kWalkWarps = RV_WALK_WARPS;  // warps per walk block (each warp walks its own groups)
 constexpr int kMaxGroup = 64;           // stars per walk group (two per lane)
 constexpr int kStackCap = 768;          // walk traversal stack entries per warp
+constexpr int kStackSm = 256;           // of them in shared memory; the deeper ones in the spill area
+constexpr int kStackSpill = kStackCap - kStackSm;
+constexpr int kStackSpillWarps = 4096;  // walk warps the spill area serves (the walk's grid is capped to it)
 constexpr int kMaxExtra = 8;            // extra particles through rv_tree_forces
 constexpr int kMaxMembers = 512;        // independent systems built and walked together (9-bit sort digit)
 constexpr int kBoundsChunk = 2048;      // stars per bounds/keys block within a member
@@ -97,6 +100,7 @@ struct Workspace {
     float *bpart;         // bounds partials
     int *xmem;            // member of each extra particle
     int *npert;           // perturbers selected per member
+    int *gstack;          // walk stack entries beyond kStackSm, kStackSpill per warp [kStackSpillWarps]
     DevState *st;
 };
 

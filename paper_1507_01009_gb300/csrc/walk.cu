@@ -108,6 +108,8 @@ struct WalkArgs {
     float *scost;
     // spline softening of the stars (h = 2.8 eps)
     Spline spl;
+    // the walk stack's entries beyond kStackSm: kStackSpill per warp of the launch
+    int *gstack;
 };
 
 // Per-warp shared memory: stack | lane_cell[32] | cell staging | star staging |
@@ -120,7 +122,7 @@ constexpr int kCellPairF4 = 5, kStarPairF4 = 2;
 constexpr int kAccWords = 16 * 32;
 constexpr int kP2PUnroll = RV_P2P_UNROLL, kM2PUnroll = RV_M2P_UNROLL;
 __host__ __device__ inline size_t warp_staging_bytes(int tile) {
-    return (size_t)kStackCap * 4 + 96 * 4 + (size_t)(tile + 32) / 2 * 16 * (kCellPairF4 + kStarPairF4);
+    return (size_t)kStackSm * 4 + 96 * 4 + (size_t)(tile + 32) / 2 * 16 * (kCellPairF4 + kStarPairF4);
 }
 __host__ __device__ inline size_t warp_smem_bytes(int tile) { return warp_staging_bytes(tile) + 4 * kAccWords; }
 
@@ -450,8 +452,13 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                                            unsigned long long &np2p, unsigned long long &nm2p, float K) {
     const int lane = threadIdx.x & 31;
     const int T = A.tile;
+    // the range stack: entries below kStackSm in shared memory, the deeper ones
+    // (rare: a pass pushes at most 32, and the walk is depth-first) in this
+    // warp's spill area in global memory; __syncwarp orders both for the warp
     int *stack = reinterpret_cast<int *>(wsm);
-    int *lane_cell = stack + kStackCap;
+    int *spill = A.gstack + (size_t)(blockIdx.x * kWalkWarps + (threadIdx.x >> 5)) * kStackSpill;
+    auto st_get = [&](int i) -> int { return i < kStackSm ? stack[i] : spill[i - kStackSm]; };
+    int *lane_cell = stack + kStackSm;
     int *lf_first = lane_cell + 32, *lf_start = lane_cell + 64;   // a pass's opened leaves
     float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 96);
     float4 *p2p = m2p + kCellPairF4 * ((T + 32) / 2);
@@ -468,7 +475,7 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         if (--guard < 0) { ok = false; break; }
         // pop whole child ranges from the top while they fit in 32 lanes
         int avail = min(top, 32);
-        int e = (lane < avail) ? stack[top - 1 - lane] : 0;
+        int e = (lane < avail) ? st_get(top - 1 - lane) : 0;
         int cnt = e & 15;
         int incl = cnt;
 #pragma unroll
@@ -536,7 +543,8 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
         unsigned om = __ballot_sync(0xffffffffu, open);
         if (open) {
             int p = top + __popc(om & lt);
-            if (p < kStackCap) stack[p] = (lk.x << 4) | (lk.y - lk.x);
+            if (p < kStackSm) stack[p] = (lk.x << 4) | (lk.y - lk.x);
+            else if (p < kStackCap) spill[p - kStackSm] = (lk.x << 4) | (lk.y - lk.x);
         }
         top += __popc(om);
         hwm = max(hwm, top);
@@ -983,7 +991,8 @@ static cudaError_t launch_walk(rv_ctx *c, const WalkArgs &A, cudaStream_t s) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkWarps * 32, smem);
     if (e != cudaSuccess) return e;
-    int grid = std::max(1, per_sm) * c->num_sms;
+    // every warp of the launch has its stack spill area
+    int grid = std::min(std::max(1, per_sm) * c->num_sms, kStackSpillWarps / kWalkWarps);
     kern<<<grid, kWalkWarps * 32, smem, s>>>(A);
     count_launch(c);
     return cudaGetLastError();
@@ -1026,6 +1035,7 @@ rv_status tree_walk(rv_ctx *c, float theta, float eps_star, int n_extra, const f
     A.pair_cap = rec ? rec->cap : 0;
     if (rec) A.rec = mac_table(rec->theta_rec);
     A.gact = gact;
+    A.gstack = w.gstack;
     // systems with fewer groups than resident walk warps gain nothing from an order
     A.order = c->n >= kOrderMinStars ? w.gorder : nullptr;
     A.scost = w.scost;
