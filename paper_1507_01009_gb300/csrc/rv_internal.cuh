@@ -25,7 +25,7 @@ constexpr int kScanChunk = 2048;        // elements per scan block
 #endif
 constexpr int kWalkWarps = RV_WALK_WARPS;  // warps per walk block (each warp walks its own groups)
 constexpr int kMaxGroup = 64;           // stars per walk group (two per lane)
-constexpr int kStackCap = 768;          // walk traversal stack entries per warp
+constexpr int kStackCap = 1408;         // walk traversal stack entries per warp (64 a level, 22 levels)
 constexpr int kStackSm = 256;           // of them in shared memory; the deeper ones in the spill area
 constexpr int kStackSpill = kStackCap - kStackSm;
 constexpr int kStackSpillWarps = 4096;  // walk warps the spill area serves (the walk's grid is capped to it)

@@ -122,7 +122,8 @@ constexpr int kCellPairF4 = 5, kStarPairF4 = 2;
 constexpr int kAccWords = 16 * 32;
 constexpr int kP2PUnroll = RV_P2P_UNROLL, kM2PUnroll = RV_M2P_UNROLL;
 __host__ __device__ inline size_t warp_staging_bytes(int tile) {
-    return (size_t)kStackSm * 4 + 96 * 4 + (size_t)(tile + 32) / 2 * 16 * (kCellPairF4 + kStarPairF4);
+    return (size_t)kStackSm * 4 + 192 * 4 + (size_t)(tile + 64) / 2 * 16 * kCellPairF4 +
+           (size_t)(tile + 32) / 2 * 16 * kStarPairF4;
 }
 __host__ __device__ inline size_t warp_smem_bytes(int tile) { return warp_staging_bytes(tile) + 4 * kAccWords; }
 
@@ -458,10 +459,10 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
     int *stack = reinterpret_cast<int *>(wsm);
     int *spill = A.gstack + (size_t)(blockIdx.x * kWalkWarps + (threadIdx.x >> 5)) * kStackSpill;
     auto st_get = [&](int i) -> int { return i < kStackSm ? stack[i] : spill[i - kStackSm]; };
-    int *lane_cell = stack + kStackSm;
-    int *lf_first = lane_cell + 32, *lf_start = lane_cell + 64;   // a pass's opened leaves
-    float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 96);
-    float4 *p2p = m2p + kCellPairF4 * ((T + 32) / 2);
+    int *lane_cell = stack + kStackSm;                             // a pass's 64 cells
+    int *lf_first = lane_cell + 64, *lf_start = lane_cell + 128;   // a pass's opened leaves
+    float4 *m2p = reinterpret_cast<float4 *>(lane_cell + 192);
+    float4 *p2p = m2p + kCellPairF4 * ((T + 64) / 2);
     const unsigned lt = lanemask_lt();
     const int ncell = G.ncell;
 
@@ -471,50 +472,39 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
     // every pass tests at least one new cell, so a walk ends within ncell passes
     int guard = ncell + 1;
     __syncwarp();
-    while (top > 0) {
-        if (--guard < 0) { ok = false; break; }
-        // pop whole child ranges from the top while they fit in 32 lanes
-        int avail = min(top, 32);
-        int e = (lane < avail) ? st_get(top - 1 - lane) : 0;
-        int cnt = e & 15;
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        unsigned fit = __ballot_sync(0xffffffffu, lane < avail && incl <= 32);
-        int kk = __popc(fit);
-        int total = __shfl_sync(0xffffffffu, incl, kk - 1);
-        __syncwarp();
-        if (lane < kk) {
-            int b = incl - cnt, c0 = e >> 4;
-            for (int t = 0; t < cnt; t++) lane_cell[b + t] = c0 + t;
-        }
-        top -= kk;
-        __syncwarp();
-        int c = (lane < total) ? lane_cell[lane] : -1;
-        __syncwarp();
-        if (__any_sync(0xffffffffu, c >= ncell)) { ok = false; break; }
-
-        bool accept = false, leaf = false, open = false, band = false;
-        int4 lk = make_int4(0, 0, 0, 0);
-        int4 b = make_int4(0, 0, 0, 0);
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = r0, q2 = r0;
-        if (c >= 0) {
-            b = __ldg(&A.cbox[c]);
+    // a cell's records, opening test and link check (one of a pass's two slots per lane)
+    struct Slot {
+        int c;
+        bool accept, leaf, open, band;
+        int4 lk, b;
+        float4 r0, q1, q2;
+    };
+    auto load_slot = [&](Slot &x) {
+        x.accept = x.leaf = x.open = x.band = false;
+        x.lk = make_int4(0, 0, 0, 0);
+        x.b = make_int4(0, 0, 0, 0);
+        x.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        x.q1 = x.r0;
+        x.q2 = x.r0;
+        if (x.c >= 0) {
             // every record of the cell at once: one L2 round trip per pass
-            lk = __ldg(&A.clink[c]);
-            r0 = __ldg(&A.cmom[3 * c + 0]);
+            x.b = __ldg(&A.cbox[x.c]);
+            x.lk = __ldg(&A.clink[x.c]);
+            x.r0 = __ldg(&A.cmom[3 * x.c + 0]);
             if (QUAD) {
-                q1 = __ldg(&A.cmom[3 * c + 1]);
-                q2 = __ldg(&A.cmom[3 * c + 2]);
+                x.q1 = __ldg(&A.cmom[3 * x.c + 1]);
+                x.q2 = __ldg(&A.cmom[3 * x.c + 2]);
             }
-            int side = 1 << (kMaxLevel - b.w);
-            long long gx = gap1(blo[0], bhi[0], b.x, b.x + side);
-            long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
-            long long gz = gap1(blo[2], bhi[2], b.z, b.z + side);
-            unsigned long long d2 = (unsigned long long)(gx * gx + gy * gy + gz * gz);
+        }
+    };
+    auto test_slot = [&](Slot &x) -> bool {   // returns "bad link"
+        if (x.c >= 0) {
+            const int4 b = x.b;
+            const int side = 1 << (kMaxLevel - b.w);
+            const long long gx = gap1(blo[0], bhi[0], b.x, b.x + side);
+            const long long gy = gap1(blo[1], bhi[1], b.y, b.y + side);
+            const long long gz = gap1(blo[2], bhi[2], b.z, b.z + side);
+            const unsigned long long d2 = (unsigned long long)(gx * gx + gy * gy + gz * gz);
             if (REL && K >= 0.f) {
                 // relative criterion: the group's box outside the cell's box grown by
                 // side/10 per side (integers x 10), and M s^2 <= (K d^2) d^2 in FP32
@@ -525,87 +515,149 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                     outside |= (10 * bhi[a] <= 10 * bo[a] - side) || (10 * blo[a] >= 10 * (bo[a] + side) + side);
                 const float d2f = __ull2float_rn(d2);
                 const float s2 = __fmul_rn((float)side, (float)side);
-                accept = outside && (__fmul_rn(r0.x, s2) <= __fmul_rn(__fmul_rn(K, d2f), d2f));
+                x.accept = outside && (__fmul_rn(x.r0.x, s2) <= __fmul_rn(__fmul_rn(K, d2f), d2f));
             } else {
-                accept = d2 >= thr[b.w];
+                x.accept = d2 >= thr[b.w];
             }
-            if (REC) band = accept && d2 < thr_rec[b.w];
-            if (!accept) {
-                leaf = (lk.x == lk.y);
-                open = !leaf;
+            if (REC) x.band = x.accept && d2 < thr_rec[b.w];
+            if (!x.accept) {
+                x.leaf = (x.lk.x == x.lk.y);
+                x.open = !x.leaf;
             }
         }
         // links must stay inside the tree (a violated bound ends the walk with an error)
-        bool bad = (open && (lk.x <= c || lk.y > ncell || lk.y - lk.x > 8)) ||
-                   (leaf && (lk.z < 0 || lk.w > A.n || lk.z > lk.w));
-        if (__any_sync(0xffffffffu, bad)) { ok = false; break; }
-        // opened internal cells: push their child ranges
-        unsigned om = __ballot_sync(0xffffffffu, open);
-        if (open) {
-            int p = top + __popc(om & lt);
-            if (p < kStackSm) stack[p] = (lk.x << 4) | (lk.y - lk.x);
-            else if (p < kStackCap) spill[p - kStackSm] = (lk.x << 4) | (lk.y - lk.x);
+        return (x.open && (x.lk.x <= x.c || x.lk.y > ncell || x.lk.y - x.lk.x > 8)) ||
+               (x.leaf && (x.lk.z < 0 || x.lk.w > A.n || x.lk.z > x.lk.w));
+    };
+    auto stage_cell = [&](const Slot &x, int p) {
+        float c0[3];
+        geo_centre(x.b, G.lo, G.unit, c0);
+        *staged(m2p, kCellPairF4, p, 0) = x.r0.x;
+        *staged(m2p, kCellPairF4, p, 1) = (c0[0] - g[0]) + x.r0.y;
+        *staged(m2p, kCellPairF4, p, 2) = (c0[1] - g[1]) + x.r0.z;
+        *staged(m2p, kCellPairF4, p, 3) = (c0[2] - g[2]) + x.r0.w;
+        if (QUAD) {   // q1 = (Qxx, Qyy, Qzz, Qxy), q2 = (Qxz, Qyz, 0, 0)
+            *staged(m2p, kCellPairF4, p, 4) = -x.q1.x;
+            *staged(m2p, kCellPairF4, p, 5) = -x.q1.y;
+            *staged(m2p, kCellPairF4, p, 6) = -x.q1.z;
+            *staged(m2p, kCellPairF4, p, 7) = -x.q1.w;
+            *staged(m2p, kCellPairF4, p, 8) = -x.q2.x;
+            *staged(m2p, kCellPairF4, p, 9) = -x.q2.y;
         }
-        top += __popc(om);
+    };
+    auto push = [&](int p, const int4 lk) {
+        if (p < kStackSm) stack[p] = (lk.x << 4) | (lk.y - lk.x);
+        else if (p < kStackCap) spill[p - kStackSm] = (lk.x << 4) | (lk.y - lk.x);
+    };
+    while (top > 0) {
+        if (--guard < 0) { ok = false; break; }
+        // pop whole child ranges from the top while they fit in the pass's 64
+        // slots (slot s: lane s % 32, its first or second cell)
+        const int avail = min(top, 64);
+        const int e0 = (lane < avail) ? st_get(top - 1 - lane) : 0;
+        const int e1 = (lane + 32 < avail) ? st_get(top - 33 - lane) : 0;
+        const int n0 = e0 & 15, n1 = e1 & 15;
+        int in0 = n0, in1 = n1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y0 = __shfl_up_sync(0xffffffffu, in0, o);
+            const int y1 = __shfl_up_sync(0xffffffffu, in1, o);
+            if (lane >= o) {
+                in0 += y0;
+                in1 += y1;
+            }
+        }
+        in1 += __shfl_sync(0xffffffffu, in0, 31);
+        const unsigned fit0 = __ballot_sync(0xffffffffu, lane < avail && in0 <= 64);
+        const unsigned fit1 = __ballot_sync(0xffffffffu, lane + 32 < avail && in1 <= 64);
+        const int kk = __popc(fit0) + __popc(fit1);
+        const int tA = __shfl_sync(0xffffffffu, in0, min(kk, 32) - 1);
+        const int tB = __shfl_sync(0xffffffffu, in1, max(kk - 33, 0));
+        const int total = kk <= 32 ? tA : tB;
+        __syncwarp();
+        if (lane < kk) {
+            const int b0 = in0 - n0, c0 = e0 >> 4;
+            for (int t = 0; t < n0; t++) lane_cell[b0 + t] = c0 + t;
+        }
+        if (lane + 32 < kk) {
+            const int b1 = in1 - n1, c1 = e1 >> 4;
+            for (int t = 0; t < n1; t++) lane_cell[b1 + t] = c1 + t;
+        }
+        top -= kk;
+        __syncwarp();
+        Slot xa, xb;
+        xa.c = (lane < total) ? lane_cell[lane] : -1;
+        xb.c = (lane + 32 < total) ? lane_cell[lane + 32] : -1;
+        __syncwarp();
+        if (__any_sync(0xffffffffu, xa.c >= ncell || xb.c >= ncell)) { ok = false; break; }
+        load_slot(xa);
+        load_slot(xb);
+        const bool bad_a = test_slot(xa), bad_b = test_slot(xb);
+        if (__any_sync(0xffffffffu, bad_a || bad_b)) { ok = false; break; }
+        // opened internal cells: push their child ranges (slot order)
+        const unsigned oma = __ballot_sync(0xffffffffu, xa.open), omb = __ballot_sync(0xffffffffu, xb.open);
+        if (xa.open) push(top + __popc(oma & lt), xa.lk);
+        if (xb.open) push(top + __popc(oma) + __popc(omb & lt), xb.lk);
+        top += __popc(oma) + __popc(omb);
         hwm = max(hwm, top);
         if (top > kStackCap) { ok = false; break; }
         // accepted cells: stage their multipole records, centre of mass relative to g, -Q
-        unsigned am = __ballot_sync(0xffffffffu, accept);
-        if (accept) {
-            int p = nm + __popc(am & lt);
-            float c0[3];
-            geo_centre(b, G.lo, G.unit, c0);
-            *staged(m2p, kCellPairF4, p, 0) = r0.x;
-            *staged(m2p, kCellPairF4, p, 1) = (c0[0] - g[0]) + r0.y;
-            *staged(m2p, kCellPairF4, p, 2) = (c0[1] - g[1]) + r0.z;
-            *staged(m2p, kCellPairF4, p, 3) = (c0[2] - g[2]) + r0.w;
-            if (QUAD) {   // q1 = (Qxx, Qyy, Qzz, Qxy), q2 = (Qxz, Qyz, 0, 0)
-                *staged(m2p, kCellPairF4, p, 4) = -q1.x;
-                *staged(m2p, kCellPairF4, p, 5) = -q1.y;
-                *staged(m2p, kCellPairF4, p, 6) = -q1.z;
-                *staged(m2p, kCellPairF4, p, 7) = -q1.w;
-                *staged(m2p, kCellPairF4, p, 8) = -q2.x;
-                *staged(m2p, kCellPairF4, p, 9) = -q2.y;
-            }
-        }
-        nm += __popc(am);
-        nm2p += __popc(am);
+        const unsigned ama = __ballot_sync(0xffffffffu, xa.accept), amb = __ballot_sync(0xffffffffu, xb.accept);
+        if (xa.accept) stage_cell(xa, nm + __popc(ama & lt));
+        if (xb.accept) stage_cell(xb, nm + __popc(ama) + __popc(amb & lt));
+        nm += __popc(ama) + __popc(amb);
+        nm2p += __popc(ama) + __popc(amb);
         if (REC) {
-            unsigned bm = __ballot_sync(0xffffffffu, band);
-            if (bm) {
+            const unsigned bma = __ballot_sync(0xffffffffu, xa.band), bmb = __ballot_sync(0xffffffffu, xb.band);
+            if (bma | bmb) {
                 int base = 0;
-                if (lane == 0) base = atomicAdd(A.npairs, __popc(bm));
+                if (lane == 0) base = atomicAdd(A.npairs, __popc(bma) + __popc(bmb));
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (band) {
-                    int p = base + __popc(bm & lt);
-                    if (p < A.pair_cap) A.pairs[p] = make_int2(gid, c);
+                if (xa.band) {
+                    const int p = base + __popc(bma & lt);
+                    if (p < A.pair_cap) A.pairs[p] = make_int2(gid, xa.c);
+                    else latch_err(A.st, kErrPairs);
+                }
+                if (xb.band) {
+                    const int p = base + __popc(bma) + __popc(bmb & lt);
+                    if (p < A.pair_cap) A.pairs[p] = make_int2(gid, xb.c);
                     else latch_err(A.st, kErrPairs);
                 }
             }
         }
-        // opened leaves: stage their stars relative to g, leaves in lane order
+        // opened leaves: stage their stars relative to g, leaves in slot order
         // and stars in order within each (the order the tiles take them), 32
         // stars a round whichever leaves they come from, so that the loads of
         // a pass's leaves overlap instead of following one another
-        const unsigned lm = __ballot_sync(0xffffffffu, leaf);
-        if (lm) {
-            const int cnt = leaf ? lk.w - lk.z : 0;
-            int incl = cnt;
+        const unsigned lma = __ballot_sync(0xffffffffu, xa.leaf), lmb = __ballot_sync(0xffffffffu, xb.leaf);
+        if (lma | lmb) {
+            const int ca = xa.leaf ? xa.lk.w - xa.lk.z : 0, cb = xb.leaf ? xb.lk.w - xb.lk.z : 0;
+            int ia = ca, ib = cb;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+                const int ya = __shfl_up_sync(0xffffffffu, ia, o);
+                const int yb = __shfl_up_sync(0xffffffffu, ib, o);
+                if (lane >= o) {
+                    ia += ya;
+                    ib += yb;
+                }
             }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int nl = __popc(lm);
-            if (leaf) {
-                const int k = __popc(lm & lt);
-                lf_first[k] = lk.z;
-                lf_start[k] = incl - cnt;
+            ib += __shfl_sync(0xffffffffu, ia, 31);
+            const int total_stars = __shfl_sync(0xffffffffu, ib, 31);
+            const int nla = __popc(lma), nl = nla + __popc(lmb);
+            if (xa.leaf) {
+                const int k = __popc(lma & lt);
+                lf_first[k] = xa.lk.z;
+                lf_start[k] = ia - ca;
+            }
+            if (xb.leaf) {
+                const int k = nla + __popc(lmb & lt);
+                lf_first[k] = xb.lk.z;
+                lf_start[k] = ib - cb;
             }
             __syncwarp();
-            for (int base = 0; base < total; base += 32) {
-                const int idx = base + lane, cc = min(32, total - base);
+            for (int base = 0; base < total_stars; base += 32) {
+                const int idx = base + lane, cc = min(32, total_stars - base);
                 if (lane < cc) {
                     // the leaf holding star idx of the pass: the last one starting at or before idx
                     int lo = 0, hi = nl - 1;
@@ -636,14 +688,20 @@ __device__ __forceinline__ bool walk_group(const WalkArgs &A, const TreeGeo &G, 
                 }
             }
         }
-        if (nm >= T) {
+        // a pass adds up to 64 cells: flush while a full tile is staged (nm < T
+        // before every pass, so at most T + 63 entries are ever staged)
+        while (nm >= T) {
             __syncwarp();
             eval_m2p<QUAD, SPL>(m2p, T / 2, tg, eps2, A.spl, acc);
             __syncwarp();
-            if (lane < (nm - T + 1) / 2) {
-#pragma unroll
-                for (int f = 0; f < kCellPairF4; f++)
-                    m2p[kCellPairF4 * lane + f] = m2p[kCellPairF4 * (T / 2 + lane) + f];
+            // the leftover (up to 32 pairs) to the front; read all before writing any,
+            // as source and destination overlap when T < 64
+            const int mv = (nm - T + 1) / 2;
+            for (int f = 0; f < kCellPairF4; f++) {   // field by field: every read of a field before its writes
+                const float4 v = lane < mv ? m2p[kCellPairF4 * (T / 2 + lane) + f] : make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                if (lane < mv) m2p[kCellPairF4 * lane + f] = v;
+                __syncwarp();
             }
             nm -= T;
         }
