@@ -1,7 +1,7 @@
 // walk.cu -- Barnes-Hut tree walk and interaction evaluation (FP32).
 //
 // One warp walks the tree for one group of up to 64 consecutive stars. Cells
-// are tested 32 at a time, one per lane, under the box-box opening test;
+// are tested up to 64 a pass, two per lane, under the box-box opening test;
 // accepted cells are staged in shared memory as multipole records, opened
 // leaves stage their stars, opened internal cells push their child range on
 // a per-warp stack. Whenever a staged list holds a full tile, the warp
